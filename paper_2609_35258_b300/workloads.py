@@ -1,0 +1,110 @@
+"""Seeded synthetic workloads shaped like the paper's benchmarks.
+
+Each function returns a plain description: mesh, boundary kinds, gas constants, velocity
+grid and the initial primitive fields (rho, u, v, T) per cell.  Nothing here evaluates the
+kinetic method; the same description feeds the CUDA library and the test-side oracle.
+
+Units are dimensionless: R = 1, T_ref = 1, rho_ref = 1, L_ref = 1, so velocity ranges are
+multiples of sqrt(R T_ref).
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+SEED = 20261202
+
+
+def _desc(name, dim, nx, ny, Lx, Ly, bc, init, *, wall=((0.0, 0.0, 1.0),) * 4, R=1.0, K=0.0,
+          Pr=2.0 / 3.0, omega=0.81, Kn=None, mu_ref=None, n_base=101, umin=-6.0, umax=6.0,
+          rule="boole", cfl=0.5, storage="f32", limiter="vanleer"):
+    return {"name": name, "dim": dim, "nx": nx, "ny": ny, "Lx": Lx, "Ly": Ly, "bc": tuple(bc),
+            "wall": tuple(tuple(float(x) for x in w) for w in wall), "R": R, "K": K, "Pr": Pr,
+            "omega": omega, "Kn": Kn, "mu_ref": mu_ref, "n_base": n_base, "umin": umin,
+            "umax": umax, "rule": rule, "cfl": cfl, "storage": storage, "limiter": limiter,
+            "init": np.ascontiguousarray(init, dtype=np.float64)}
+
+
+def sod_1d(ncell=200, n_base=101, umax=10.0, Kn=1e-3, storage="f64"):
+    """1-D shock tube: (rho, p) = (1, 1) | (0.125, 0.1) at rest on [0, 1], BGK, gamma = 5/3."""
+    x = (np.arange(ncell) + 0.5) / ncell
+    rho = np.where(x < 0.5, 1.0, 0.125)
+    p = np.where(x < 0.5, 1.0, 0.1)
+    init = np.zeros((1, ncell, 4))
+    init[0, :, 0] = rho
+    init[0, :, 3] = p / rho
+    return _desc("sod1d", 1, ncell, 1, 1.0, 1.0, ("zerograd", "zerograd", "periodic", "periodic"),
+                 init, Pr=1.0, Kn=Kn, n_base=n_base, umin=-umax, umax=umax, storage=storage)
+
+
+def cavity(n=64, n_base=101, umax=6.0, Kn=0.075, lid_mach=0.16, storage="f32"):
+    """Lid-driven cavity on [0,1]^2, diffuse isothermal walls at T_w = 1, gas at rest, T = 1.
+
+    The lid (y-high side) moves at U_w = Ma sqrt(gamma R T_w), gamma = 5/3; Shakhov Pr = 2/3.
+    """
+    Uw = lid_mach * math.sqrt(5.0 / 3.0)
+    init = np.zeros((n, n, 4))
+    init[..., 0] = 1.0
+    init[..., 3] = 1.0
+    wall = ((0.0, 0.0, 1.0), (0.0, 0.0, 1.0), (0.0, 0.0, 1.0), (Uw, 0.0, 1.0))
+    return _desc("cavity", 2, n, n, 1.0, 1.0, ("wall",) * 4, init, wall=wall, Kn=Kn,
+                 n_base=n_base, umin=-umax, umax=umax, storage=storage)
+
+
+def periodic_random(nx, ny, n_base=25, umax=6.0, seed=SEED, amp=0.2, Kn=0.1, Pr=2.0 / 3.0,
+                    storage="f32", dim=2, bc=None):
+    """Smooth random periodic fields: a few seeded Fourier modes of rho, u, v, T."""
+    rng = np.random.default_rng(seed)
+    y = (np.arange(ny) + 0.5) / ny
+    x = (np.arange(nx) + 0.5) / nx
+    X, Y = np.meshgrid(x, y)
+    init = np.zeros((ny, nx, 4))
+    base = (1.0, 0.0, 0.0, 1.0)
+    scale = (amp, 0.3 * amp * 2, 0.3 * amp * 2, amp)
+    for f in range(4):
+        field = np.full_like(X, base[f])
+        for _ in range(3):
+            kx, ky = rng.integers(0, 3, size=2)
+            ph = rng.uniform(0, 2 * np.pi)
+            a = rng.uniform(-1, 1) * scale[f]
+            field += a * np.sin(2 * np.pi * (kx * X + (ky * Y if dim == 2 else 0)) + ph)
+        init[..., f] = field
+    if dim == 1:
+        init[..., 2] = 0.0
+    if bc is None:
+        bc = ("periodic",) * 4
+    return _desc("periodic_random", dim, nx, ny, 1.0, 1.0 if dim == 2 else 1.0, bc, init, Kn=Kn,
+                 Pr=Pr, n_base=n_base, umin=-umax, umax=umax, storage=storage)
+
+
+def uniform_flow(nx=100, ny=10, n_base=89, R=0.5, Kn=0.1, storage="f32"):
+    """Uniform flow on the periodic box [0,1] x [0,0.1]: rho = 1, u = (0.1, 0), T = 1."""
+    init = np.zeros((ny, nx, 4))
+    init[..., 0] = 1.0
+    init[..., 1] = 0.1
+    init[..., 3] = 1.0
+    um = 4.0 * math.sqrt(2.0 * R * 1.0)
+    return _desc("uniform", 2, nx, ny, 1.0, 0.1, ("periodic",) * 4, init, R=R, Kn=Kn,
+                 n_base=n_base, umin=-um, umax=um, storage=storage)
+
+
+def sine_wave(nx=100, ny=10, n_base=89, R=0.5, Kn=0.1, storage="f32"):
+    """Density wave at constant pressure: rho = 1 + 0.2 sin(2 pi x), u = (0.1, 0), p = 0.5."""
+    x = (np.arange(nx) + 0.5) / nx
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+    init = np.zeros((ny, nx, 4))
+    init[..., 0] = rho[None, :]
+    init[..., 1] = 0.1
+    init[..., 3] = (0.5 / (rho * R))[None, :]
+    um = 4.0 * math.sqrt(2.0 * R * 1.0)
+    return _desc("sine", 2, nx, ny, 1.0, 0.1, ("periodic",) * 4, init, R=R, Kn=Kn,
+                 n_base=n_base, umin=-um, umax=um, storage=storage)
+
+
+def batched_cavities(n_inst=64, seed=SEED, sizes=(32, 48, 64, 96, 128)):
+    """Independent cavity instances: Kn log-uniform in [1e-3, 10], grid size drawn from sizes."""
+    rng = np.random.default_rng(seed)
+    kn = 10.0 ** rng.uniform(-3.0, 1.0, size=n_inst)
+    n = rng.choice(np.asarray(sizes), size=n_inst)
+    return [cavity(int(n[i]), Kn=float(kn[i])) for i in range(n_inst)]

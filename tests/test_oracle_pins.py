@@ -1,0 +1,253 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by the mathematics.
+
+Nothing here compares the oracle with itself: closed-form Gaussian integrals, polynomial
+exactness of the quadrature, the definitions of the transformed distributions (Sec. 2.2),
+the Shakhov heat-flux property (Sec. 2.1), the compatibility-recovery test state of Sec. 4.1.1,
+conservation of the finite-volume update, and a brute-force free-molecular advection.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dugks, kinetic, vspace
+from paper_2609_35258_b300 import workloads
+from tests.helpers import oracle_run, oracle_setup
+
+
+# ---------------------------------------------------------------- quadrature (Sec. 2.3)
+
+@pytest.mark.parametrize("n", [5, 9, 101])
+def test_boole_polynomial_exactness(n):
+    a, b = -3.0, 5.0
+    x, w = vspace.newton_cotes_1d(n, a, b, "boole")
+    for k in range(6):
+        exact = (b ** (k + 1) - a ** (k + 1)) / (k + 1)
+        assert abs(np.sum(w * x ** k) - exact) <= 1e-12 * max(1.0, abs(exact))
+    if n == 5:   # degree 6 is not integrated exactly by one Boole panel
+        exact6 = (b ** 7 - a ** 7) / 7
+        assert abs(np.sum(w * x ** 6) - exact6) > 1e-6
+
+
+def test_simpson_trapz_exactness():
+    x, w = vspace.newton_cotes_1d(11, 0.0, 2.0, "simpson")
+    assert abs(np.sum(w * x ** 3) - 4.0) < 1e-13
+    x, w = vspace.newton_cotes_1d(11, 0.0, 2.0, "trapz")
+    assert abs(np.sum(w * x) - 2.0) < 1e-13
+
+
+@pytest.mark.parametrize("n,sizes", [(101, [101, 51, 25, 13]), (201, [201, 101, 51, 25]),
+                                     (89, [89, 45, 23, 11])])
+def test_level_sizes_and_nesting(n, sizes):
+    for L, s in enumerate(sizes):
+        g = vspace.axis_groups(n, L)
+        assert len(g) == s
+        assert sorted(i for grp in g for i in grp) == list(range(n))
+        # symmetric under xi -> -xi
+        assert [len(x) for x in g] == [len(x) for x in reversed(g)]
+        if L > 0:   # each group is a union of level L-1 groups
+            prev = vspace.axis_groups(n, L - 1)
+            starts = {grp[0] for grp in prev}
+            ends = {grp[-1] for grp in prev}
+            for grp in g:
+                assert grp[0] in starts and grp[-1] in ends
+
+
+def test_merged_space_preserves_weight_and_first_moment():
+    base = vspace.make_base(101, -6, 6, D=2)
+    s0 = vspace.uniform_space(base, 0)
+    for L in (1, 2, 3):
+        s = vspace.uniform_space(base, L)
+        assert abs(s.w.sum() - s0.w.sum()) < 1e-12
+        # weighted mean coordinates reproduce the first moments of the base grid exactly
+        np.testing.assert_allclose(s.w @ s.xi, s0.w @ s0.xi, atol=1e-12)
+
+
+# ---------------------------------------------------------------- model (Sec. 2.1)
+
+def _fine_space(D, n=401, um=12.0):
+    base = vspace.make_base(n, -um, um, D=D)
+    return vspace.uniform_space(base, 0)
+
+
+@pytest.mark.parametrize("D", [1, 2])
+def test_maxwellian_moments_closed_form(D):
+    sp = _fine_space(D)
+    gas = kinetic.Gas(D=D, K=0.0, R=1.0, Pr=1.0)
+    rho, T = 1.3, 0.8
+    u = np.array([0.4, -0.2])[:D]
+    g, h = kinetic.maxwell_gh(np.array(rho), u, np.array(T), sp.xi, gas)
+    m = kinetic.moments(g, h, sp.xi, sp.w, gas)
+    assert abs(m["rho"] - rho) < 1e-12
+    np.testing.assert_allclose(m["u"], u, atol=1e-12)
+    assert abs(m["T"] - T) < 1e-12
+    np.testing.assert_allclose(m["q"], 0.0, atol=1e-12)
+    np.testing.assert_allclose(m["P"], rho * T * np.eye(D), atol=1e-11)
+    # internal energy carried by h: (3 - D + K)/2 rho R T
+    assert abs(0.5 * np.sum(sp.w * h) - 0.5 * (3 - D) * rho * T) < 1e-12
+
+
+@pytest.mark.parametrize("D,K", [(2, 0.0), (1, 0.0), (2, 2.0)])
+def test_shakhov_heat_flux_property(D, K):
+    """The Shakhov distribution has the conserved moments of its state and heat flux (1-Pr) q."""
+    sp = _fine_space(D)
+    gas = kinetic.Gas(D=D, K=K, R=1.0, Pr=2.0 / 3.0)
+    rho, T = 0.9, 1.1
+    u = np.array([0.3, 0.1])[:D]
+    q = np.array([0.05, -0.03])[:D]
+    g, h = kinetic.shakhov_gh(np.array(rho), u, np.array(T), q, sp.xi, gas)
+    m = kinetic.moments(g, h, sp.xi, sp.w, gas)
+    assert abs(m["rho"] - rho) < 1e-12
+    np.testing.assert_allclose(m["u"], u, atol=1e-12)
+    assert abs(m["T"] - T) < 1e-11
+    np.testing.assert_allclose(m["q"], (1 - gas.Pr) * q, atol=1e-11)
+
+
+def test_compat_correction_E1_state():
+    """Sec. 4.1.1: (rho, u, v, T, R) = (1, 1, 0.2, 1, 0.5) on a nonuniform quadtree grid; the
+    four-moment linear correction brings the conserved moments to round-off."""
+    base = vspace.make_base(33, -4.0, 4.0, D=2)
+    N1 = len(vspace.axis_groups(33, 1))
+    yy, xx = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
+    r = np.hypot(xx - N1 // 2, yy - N1 // 2)
+    kappa = np.where(r < 3, 0, np.where(r < 5, 1, 2)).astype(np.int64)
+    sp = vspace.kappa_space(base, kappa)
+    assert sp.nv < base.n ** 2
+    gas = kinetic.Gas(D=2, R=0.5, Pr=1.0)
+    rho, u, T = np.array(1.0), np.array([1.0, 0.2]), np.array(1.0)
+    g, h = kinetic.maxwell_gh(rho, u, T, sp.xi, gas)
+    tar = np.array([1.0, 1.0, 0.2, 0.5 * (1.0 + 0.04) + 1.5 * 0.5 * 1.0])
+    def eps(g, h):
+        M = kinetic.conserved(g, h, sp.xi, sp.w)
+        return np.max(np.abs(M - tar) / np.abs(tar))
+    assert eps(g, h) > 1e-5
+    gc, hc = kinetic.compat_correct4(g, h, rho, u, T, sp.xi, sp.w, gas)
+    assert eps(gc, hc) < 1e-14
+
+
+# ---------------------------------------------------------------- DUGKS (Sec. 2.2)
+
+def test_transformed_distribution_algebra():
+    rng = np.random.default_rng(1)
+    phi, phiS = rng.random(50), rng.random(50)
+    tau, dt = 0.37, 0.11
+    s = dt / 2
+    Om = (phiS - phi) / tau
+    phit = phi - dt / 2 * Om
+    np.testing.assert_allclose(dugks.bar_plus(phit, phiS, tau, dt), phi + s / 2 * Om, rtol=1e-13)
+    np.testing.assert_allclose(dugks.tilde_plus(phi + s / 2 * Om, phit), phi + dt / 2 * Om, rtol=1e-13)
+    phib = phi - s / 2 * Om
+    np.testing.assert_allclose(dugks.recover(phib, phiS, tau, s), phi, rtol=1e-13)
+
+
+def test_discrete_heat_flux_relation():
+    """Eq. discrete_q: the q recovered from phi~ equals the heat flux of phi."""
+    sp = _fine_space(2)
+    gas = kinetic.Gas(D=2, R=1.0, Pr=2.0 / 3.0, mu_ref=0.05)
+    rho, u, T = np.array(1.0), np.array([0.2, -0.1]), np.array(1.0)
+    qphi = np.array([0.04, 0.02])
+    # a distribution phi with heat flux qphi: Shakhov form with Pr' such that (1-Pr') = 1
+    g1 = kinetic.Gas(D=2, R=1.0, Pr=0.0)
+    gphi, hphi = kinetic.shakhov_gh(rho, u, T, qphi, sp.xi, g1)
+    m = kinetic.moments(gphi, hphi, sp.xi, sp.w, gas)
+    np.testing.assert_allclose(m["q"], qphi, atol=1e-11)
+    tau = kinetic.viscosity(T, gas) / (rho * gas.R * T)
+    gS, hS = kinetic.shakhov_gh(rho, u, T, qphi, sp.xi, gas)
+    dt = 0.02
+    gt = gphi - dt / 2 * (gS - gphi) / tau
+    ht = hphi - dt / 2 * (hS - hphi) / tau
+    st = dugks.cell_state(gt, ht, sp.xi, sp.w, gas, dt)
+    np.testing.assert_allclose(st["q"], qphi, atol=1e-11)
+    assert abs(st["rho"] - 1.0) < 1e-12 and abs(st["T"] - 1.0) < 1e-11
+
+
+def test_uniform_bgk_fixed_point():
+    desc = workloads.periodic_random(6, 5, n_base=25, Pr=1.0)
+    desc["init"][..., 0] = 1.2
+    desc["init"][..., 1] = 0.3
+    desc["init"][..., 2] = -0.1
+    desc["init"][..., 3] = 0.9
+    o = oracle_setup(desc)
+    g, h = oracle_run(o, 3)
+    assert np.max(np.abs(g - o["g"])) < 1e-14 * np.max(o["g"])
+    assert np.max(np.abs(h - o["h"])) < 1e-14 * np.max(o["h"])
+
+
+def test_shakhov_rest_fixed_point():
+    desc = workloads.periodic_random(6, 5, n_base=25)
+    desc["init"][..., 0] = 1.0
+    desc["init"][..., 1:3] = 0.0
+    desc["init"][..., 3] = 1.0
+    o = oracle_setup(desc)
+    g, h = oracle_run(o, 3)
+    assert np.max(np.abs(g - o["g"])) < 1e-13 * np.max(o["g"])
+
+
+def test_periodic_conservation():
+    desc = workloads.periodic_random(8, 6, n_base=25, amp=0.2)
+    o = oracle_setup(desc)
+    sp = o["sp"]
+    W0 = kinetic.conserved(o["g"], o["h"], sp.xi, sp.w).sum(axis=(0, 1))
+    g, h = oracle_run(o, 30)
+    W1 = kinetic.conserved(g, h, sp.xi, sp.w).sum(axis=(0, 1))
+    assert np.max(np.abs(W1 - W0)) < 1e-12 * np.max(np.abs(W0))
+    assert np.max(np.abs(g - o["g"])) > 1e-4   # the state did evolve
+
+
+def test_wall_mass_conservation():
+    desc = workloads.cavity(8, n_base=25, Kn=0.075)
+    o = oracle_setup(desc)
+    sp = o["sp"]
+    M0 = kinetic.conserved(o["g"], o["h"], sp.xi, sp.w)[..., 0].sum()
+    g, h = oracle_run(o, 20)
+    M1 = kinetic.conserved(g, h, sp.xi, sp.w)[..., 0].sum()
+    assert abs(M1 - M0) < 1e-13 * M0
+    st = dugks.cell_state(g, h, sp.xi, sp.w, o["gas"], o["dt"])
+    assert np.max(st["u"][..., 0]) > 1e-3   # the lid drives the flow
+
+
+def _vanleer(a, b):
+    if (a > 0 and b > 0) or (a < 0 and b < 0):
+        return 2 * a * b / (a + b)
+    return 0.0
+
+
+def test_free_molecular_limit_matches_scalar_advection():
+    """tau -> infinity: each velocity decouples into linear advection with the characteristic
+    reconstruction; compare against a brute-force per-velocity loop (D = 1, 8 periodic cells)."""
+    desc = workloads.periodic_random(8, 1, n_base=13, umax=4.0, dim=1, Pr=1.0)
+    desc["mu_ref"] = 1e16
+    o = oracle_setup(desc, compat=False)
+    g0 = o["g"][0].copy()     # [nx, nv]
+    xi = o["sp"].xi[:, 0]
+    dt, dx = o["dt"], o["mesh"].dx
+    s = dt / 2
+    nx = 8
+    g1, _ = oracle_run(o, 1)
+    ref = np.zeros_like(g0)
+    for v in range(len(xi)):
+        f = g0[:, v]
+        sig = [_vanleer(f[(i + 1) % nx] - f[i], f[i] - f[i - 1]) / dx for i in range(nx)]
+        face = []
+        for i in range(nx):   # face i between cells i-1 and i
+            L, R = i - 1, i
+            vL = f[L] + (dx / 2 - xi[v] * s) * sig[L]
+            vR = f[R] + (-dx / 2 - xi[v] * s) * sig[R]
+            face.append(vL if xi[v] > 0 else (vR if xi[v] < 0 else 0.5 * (vL + vR)))
+        for i in range(nx):
+            ref[i, v] = f[i] - dt / dx * xi[v] * (face[(i + 1) % nx] - face[i])
+    np.testing.assert_allclose(g1[0], ref, rtol=1e-12, atol=1e-14 * np.max(np.abs(g0)))
+
+
+def test_sod_oracle_wave_structure():
+    """Kn = 1e-3 Sod: after t = 0.1 the density has the rarefaction/contact/shock ordering
+    between the two initial states (qualitative check of the 1-D path)."""
+    desc = workloads.sod_1d(ncell=100, n_base=61, umax=10.0)
+    o = oracle_setup(desc)
+    nsteps = int(round(0.1 / o["dt"]))
+    g, h = oracle_run(o, nsteps)
+    st = dugks.cell_state(g, h, o["sp"].xi, o["sp"].w, o["gas"], o["dt"])
+    rho = st["rho"][0]
+    assert rho[0] == pytest.approx(1.0, abs=1e-3) and rho[-1] == pytest.approx(0.125, abs=1e-3)
+    assert np.all(np.diff(rho) <= 1e-3)           # monotone non-increasing left to right
+    assert np.max(st["u"][0, :, 0]) > 0.5         # gas accelerated to the right
