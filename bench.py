@@ -1,0 +1,290 @@
+#!/usr/bin/env python
+"""Benchmark of the MLVS-DUGKS hot path: cell-velocity updates per second on one B300.
+
+Workload (N = 1): the 2-D lid-driven cavity, 64 x 64 cells, Kn = 0.075, lid Mach 0.16,
+Shakhov Pr = 2/3, on the 101 x 101 Boole velocity grid over [-6, 6]^2 (UVS), f stored in
+FP32 with FP64 moment sums.  One step is one DUGKS step over every (cell, velocity) pair.
+The distributions (2 x 334 MB) are larger than L2, so no flush is needed between steps.
+
+Arms:
+  (default)          the CUDA library through its C ABI
+  --impl reference   the FP64 CPU oracle as it stands, on the host cores, on a bounded
+                     sample of the same workload (a smaller cavity on the same velocity grid)
+
+Multi-GPU: the path is run as independent replicas (one cavity per rank, no collective on
+the data path); value = all ranks' updates / max-over-ranks time, scaling "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-velocity updates/s (DUGKS step, 2-D cavity 64^2 on 101^2 velocities)"
+UNIT = "updates/s"
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by workload, with
+# the hash of the kernel sources at capture time (a changed kernel reports null).
+TRAFFIC = {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2609_35258_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_rate(ncell_side, nsteps, threads=1):
+    """FP64 oracle on a ncell_side^2 cavity with the bench's velocity grid; updates/s."""
+    from threadpoolctl import threadpool_limits
+    from paper_2609_35258_b300 import workloads
+    from tests.helpers import oracle_run, oracle_setup
+    d = workloads.cavity(ncell_side, n_base=101, umax=6.0, Kn=0.075)
+    with threadpool_limits(limits=threads):
+        o = oracle_setup(d)
+        t0 = time.perf_counter()
+        oracle_run(o, nsteps)
+        t = time.perf_counter() - t0
+    upd = ncell_side * ncell_side * 101 * 101 * nsteps
+    return upd / t, t, upd
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    # sample size so that (K + W) oracle steps take about 1-2 minutes
+    per_upd = 1.1e-6
+    cells = 100.0 / ((args.steps + args.warmup) * 101 * 101 * per_upd)
+    side = int(max(2, min(16, math.floor(math.sqrt(max(cells, 4.0))))))
+    from threadpoolctl import threadpool_limits
+    from paper_2609_35258_b300 import workloads
+    from tests.helpers import oracle_run, oracle_setup
+    d = workloads.cavity(side, n_base=101, umax=6.0, Kn=0.075)
+    with threadpool_limits(limits=1):
+        o = oracle_setup(d)
+        for _ in range(args.warmup):
+            g, h = oracle_run(o, 1)
+            o["g"], o["h"] = g, h
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            g, h = oracle_run(o, 1)
+            o["g"], o["h"] = g, h
+        t = time.perf_counter() - t0
+    upd = side * side * 101 * 101 * args.steps
+    val = upd / t
+    sample = f"{side}x{side}-cell cavity on the same 101^2 velocity grid, {args.steps} oracle steps"
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "cavity64_uvs101_f32", "sample": sample},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local_rank)
+    from paper_2609_35258_b300 import mlvs as M
+    from paper_2609_35258_b300 import workloads
+    from paper_2609_35258_b300.solver import Solver
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    stream = torch.cuda.current_stream()
+    desc = workloads.cavity(64, n_base=101, umax=6.0, Kn=0.075, storage=args.storage)
+    ncell = 64 * 64
+    nv = 101 * 101
+    upd_step = ncell * nv
+    s = Solver(desc, stream=stream.cuda_stream)
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local_rank)
+    clk.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = s.step(args.steps, profile=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ms_step = ms / args.steps
+    value = world * upd_step * args.steps / (ms / 1e3)
+
+    # roofline of the dominant kernel (update pass or face-sum pass)
+    phases = list(st.ms_phase)
+    names = ["finalize_cells", "face_sums", "finalize_faces", "update"]
+    dom = max(range(4), key=lambda i: phases[i])
+    fbytes = {"f32": 4, "bf16": 2, "f64": 8}[args.storage]
+    algo_per_update = {1: 2 * fbytes, 3: 4 * fbytes}.get(dom, 0)
+    kernel_ms = phases[dom] / args.steps
+    peak, peak_kind = measured_peaks()
+    achieved = algo_per_update * upd_step / (kernel_ms / 1e3) / 1e9 if algo_per_update else None
+    key = f"cavity64_uvs101_{args.storage}:{names[dom]}"
+    tr = TRAFFIC.get(key)
+    traffic = tr[0] if tr and tr[1] == kernel_source_hash() else None
+
+    # end-to-end through the public API: host init upload, steps, host moment reads
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        ke = max(1, min(args.steps, 50))
+        t0 = time.perf_counter()
+        s2 = Solver(desc, stream=stream.cuda_stream)
+        for _ in range(ke):
+            s2.step(1)
+            _ = M.mlvs_moments(s2.h, 0, M.RHO | M.U | M.V | M.T, ncell)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        s2.close()
+        e2e = {"value": upd_step * ke / te, "unit": UNIT,
+               "h2d_bytes_per_step": int(desc["init"].nbytes / ke),
+               "d2h_bytes_per_step": int(4 * ncell * 8),
+               "steps": ke, "includes": "create + init upload + steps + per-step host moment read"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        rate, t, upd = oracle_rate(16, 4)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"16x16-cell cavity on the same 101^2 velocity grid, 4 FP64 oracle steps "
+                         f"({upd} updates, {t:.1f} s, numpy single thread)"}
+    s.close()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
+            "config": {"workload": f"cavity64_uvs101_{args.storage}", "cells": ncell,
+                       "velocities": nv, "levels": "UVS 101^2", "Kn": 0.075,
+                       "l2": "inputs larger than L2 (2 x 334 MB distributions)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
+                         "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic,
+                         "algorithmic_bytes_per_update": algo_per_update},
+            "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, phases)},
+            "clocks": clocks, "e2e": e2e, "gpu_launches": st.launches, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,142 @@
+/*
+ * mlvs.h -- C ABI of the MLVS-DUGKS hot-path library (sm_103a).
+ *
+ * The library advances the reduced distributions (g, h) of the BGK/Shakhov model with the
+ * discrete unified gas-kinetic scheme (Sec. 2.2, Eqs. phi_update ... recover_phi) over every
+ * (physical cell x discrete velocity) pair, on one or several velocity spaces built on a
+ * quadtree-structured Newton--Cotes base grid (Sec. 2.3, 3.1-3.2).  Multi-level parts follow
+ * Sec. 3.2 (criterion, grouping), Sec. 3.3 (linear moment-constrained correction) and
+ * Sec. 3.4 (inter-level coupling).
+ *
+ * Conventions
+ *  - Every entry point returns an mlvs_status; MLVS_OK is 0 and errors are negative.
+ *  - Pointers marked "host" are read (or written) during the call only; the caller keeps
+ *    ownership.  The handle owns all device memory it allocates and frees it in
+ *    mlvs_destroy.
+ *  - A handle is single-threaded: calls on one handle must not overlap.  All device work is
+ *    ordered on the stream given in mlvs_config.stream (NULL: the legacy default stream).
+ *  - Asynchronous device errors (non-finite or negative moments, an exhausted bounded wait)
+ *    surface as the status of the next mlvs_step or mlvs_moments call.  After such an
+ *    error the handle answers MLVS_ERR_STATE until destroyed.
+ *  - mlvs_last_error returns a diagnostic string describing the last failing call.
+ */
+#ifndef MLVS_H
+#define MLVS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mlvs_handle mlvs_handle;
+
+typedef enum {
+  MLVS_OK = 0,
+  MLVS_ERR_ARG = -1,        /* an argument is out of range or inconsistent              */
+  MLVS_ERR_OOM = -2,        /* a device or host allocation failed                       */
+  MLVS_ERR_CUDA = -3,       /* a CUDA runtime call failed                               */
+  MLVS_ERR_NONFINITE = -4,  /* a moment became NaN/Inf                                  */
+  MLVS_ERR_POSITIVITY = -5, /* density or temperature became non-positive               */
+  MLVS_ERR_SINGULAR = -6,   /* a moment-correction matrix is singular                   */
+  MLVS_ERR_TIMEOUT = -7,    /* a bounded device-side wait ran out                       */
+  MLVS_ERR_STATE = -8       /* call order violated, or the handle holds an earlier error */
+} mlvs_status;
+
+/* boundary kinds, per side x-low, x-high, y-low, y-high */
+enum { MLVS_BC_PERIODIC = 0, MLVS_BC_ZEROGRAD = 1, MLVS_BC_WALL = 2 };
+/* storage type of the distributions */
+enum { MLVS_F64 = 0, MLVS_F32 = 1, MLVS_BF16 = 2 };
+/* Newton--Cotes rule of the base grid (Sec. 2.3; the order is not named in the paper) */
+enum { MLVS_QUAD_BOOLE = 0, MLVS_QUAD_SIMPSON = 1, MLVS_QUAD_TRAPZ = 2 };
+/* slope limiter of Eq. reconstruction */
+enum { MLVS_LIMITER_VANLEER = 0, MLVS_LIMITER_NONE = 1 };
+
+typedef struct {
+  int dim;              /* velocity/space dimension D: 1 or 2 (Sec. 2.1)                      */
+  int n_instances;      /* independent cases advanced together (>= 1)                          */
+  int nx, ny;           /* uniform Cartesian mesh; ny = 1 when dim = 1                         */
+  double Lx, Ly;        /* domain lengths; cell sizes are Lx/nx, Ly/ny                         */
+  int bc[4];            /* MLVS_BC_* for x-low, x-high, y-low, y-high                          */
+  double wall[4][3];    /* (u_w, v_w, T_w) of each wall side (diffuse isothermal wall)         */
+  double R;             /* gas constant                                                       */
+  double K_internal;    /* internal degrees of freedom K (monatomic: 0)                        */
+  double Pr;            /* Prandtl number; 1 gives the BGK model (Eq. shakhov_eq)              */
+  double omega;         /* viscosity exponent of mu = mu_ref (T/T_ref)^omega (Sec. 4)          */
+  double Kn;            /* Knudsen number, used when mu_ref <= 0 (VHS relation, alpha = 1)      */
+  double mu_ref;        /* reference viscosity; > 0 overrides Kn                               */
+  double L_ref, T_ref, rho_ref;
+  double cfl;           /* dt = cfl * min(dx, dy) / max |xi|_inf, unless dt > 0                */
+  double dt;            /* > 0: fixed time step                                               */
+  int storage;          /* MLVS_F64 | MLVS_F32 | MLVS_BF16                                     */
+  int compat_cell;      /* 1: four-moment compatibility correction at cells (Sec. 3.3.1)      */
+  int compat_face;      /* 1: the same correction of the face model distribution              */
+  int limiter;          /* MLVS_LIMITER_*                                                     */
+  const double* init_W; /* host [n_instances][ny][nx][4] = (rho, u, v, T); copied              */
+  void* stream;         /* cudaStream_t the library orders its work on                        */
+} mlvs_config;
+
+/* One representative velocity space, described on the base grid (Sec. 3.2). */
+typedef struct {
+  int uniform_L;               /* >= 0: every axis grouped at level L; -1: use kappa         */
+  const unsigned char* kappa;  /* host [N1][N1] coarsening index per 2x2 block, 0..3         */
+} mlvs_level_desc;
+
+typedef struct {
+  int profile;               /* in: nonzero records CUDA events around every launch          */
+  double dt;                 /* out: time step in use                                        */
+  long long cell_velocity_updates; /* out: sum over levels of cells x velocities, per call   */
+  int n_levels;              /* out                                                          */
+  int launches;              /* out: kernels launched by the call                            */
+  float ms_total;            /* out: device time of the call (CUDA events), ms               */
+  float ms_phase[4];         /* out (profile): summed device time of the cell finalisation,
+                                face-sum, face finalisation and update launches, ms          */
+} mlvs_step_stats;
+
+/* Create a handle for the problem in cfg.  No velocity space exists yet.
+ * Errors: MLVS_ERR_ARG (bad sizes/kinds), MLVS_ERR_CUDA, MLVS_ERR_OOM. */
+mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out);
+
+/* Build the base grid (n_base points per axis on [umin, umax], rule `quadrature`,
+ * Sec. 2.3) and the velocity spaces `levels` (Sec. 3.2), allocate the distributions of
+ * every instance on level 0, and initialise them to the compatibility-corrected Maxwellian
+ * of cfg.init_W (phi~ = phi^eq at rest in equilibrium).  n_base must be odd.
+ * Errors: MLVS_ERR_ARG, MLVS_ERR_OOM, MLVS_ERR_CUDA, MLVS_ERR_SINGULAR. */
+mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, double umin, double umax,
+                                     int quadrature, int n_levels,
+                                     const mlvs_level_desc* levels, int adaptive);
+
+/* Advance every instance by n_steps DUGKS steps (Sec. 2.2).  stats may be NULL; when given,
+ * stats->profile is read and the other fields are written.
+ * Errors: MLVS_ERR_STATE, MLVS_ERR_NONFINITE, MLVS_ERR_POSITIVITY, MLVS_ERR_CUDA. */
+mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* stats);
+
+/* field bits for mlvs_moments; fields are written in this bit order */
+enum {
+  MLVS_RHO = 1, MLVS_U = 2, MLVS_V = 4, MLVS_T = 8, MLVS_QX = 16, MLVS_QY = 32,
+  MLVS_LEVEL = 64, MLVS_RHOE = 128
+};
+/* Cell moments of one instance at the current time (Eqs. discrete_W, discrete_q):
+ * out is [n_fields][ny*nx] doubles (row-major cells), host or device memory (out_on_device).
+ * q is the heat flux of phi (q = 2 tau/(2 tau + dt Pr) q~).
+ * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_CUDA. */
+mlvs_status mlvs_moments(mlvs_handle* h, int instance, unsigned fields, double* out,
+                         int out_on_device);
+
+/* Extra (tests): copy the distributions g~, h~ of cells [cell0, cell0+ncells) of one
+ * instance to host arrays out_g/out_h laid out [ncells][nv] (nv of the cell's level; all
+ * cells in the range must share a level).  *nv_out receives nv. */
+mlvs_status mlvs_read_cells(mlvs_handle* h, int instance, int cell0, int ncells,
+                            double* out_g, double* out_h, int cap, int* nv_out);
+
+/* Extra: the time step in use. */
+mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt);
+
+/* Release everything the handle owns.  NULL is allowed. */
+void mlvs_destroy(mlvs_handle* h);
+
+/* Diagnostic text of the last failing call on h (or of the last failing create if h is NULL). */
+const char* mlvs_last_error(const mlvs_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLVS_H */

@@ -1,0 +1,106 @@
+// Host construction of the velocity spaces (Sec. 2.3, 3.1-3.2).
+//
+// Base grid: uniform nodes on [umin, umax] with composite Newton--Cotes weights (Boole by
+// default, Simpson, trapezoid).  Level L groups one axis as follows: the centre node stays
+// alone and the nodes on each side are grouped outward from the centre in runs of 2^L, the
+// remainder joining the outermost group.  A merged cell has the summed weight and the
+// weight-averaged coordinate (the relations under Eq. hierarchical_projection_operator).
+#pragma once
+#include <cmath>
+#include <stdexcept>
+#include <vector>
+
+namespace mlvs {
+
+struct Base1D {
+  std::vector<double> x, w;
+};
+
+inline Base1D make_base_1d(int n, double umin, double umax, int rule) {
+  if (n < 3 || (n % 2) == 0) throw std::invalid_argument("base size must be odd and >= 3");
+  Base1D b;
+  b.x.resize(n);
+  b.w.assign(n, 0.0);
+  const double h = (umax - umin) / (n - 1);
+  for (int i = 0; i < n; ++i) b.x[i] = umin + h * i;
+  if (rule == 0) {  // Boole: panels of four intervals
+    if ((n - 1) % 4) throw std::invalid_argument("Boole rule needs 4k+1 nodes");
+    const double c[5] = {7.0, 32.0, 12.0, 32.0, 7.0};
+    for (int p = 0; p < (n - 1) / 4; ++p)
+      for (int j = 0; j < 5; ++j) b.w[4 * p + j] += c[j] * 2.0 * h / 45.0;
+  } else if (rule == 1) {  // Simpson
+    for (int p = 0; p < (n - 1) / 2; ++p) {
+      b.w[2 * p] += h / 3.0;
+      b.w[2 * p + 1] += 4.0 * h / 3.0;
+      b.w[2 * p + 2] += h / 3.0;
+    }
+  } else if (rule == 2) {  // trapezoid
+    for (int i = 0; i < n; ++i) b.w[i] = (i == 0 || i == n - 1) ? 0.5 * h : h;
+  } else {
+    throw std::invalid_argument("unknown quadrature rule");
+  }
+  return b;
+}
+
+// Groups of one axis at level L: ranges [lo, hi) of base indices, ascending.
+inline std::vector<std::pair<int, int>> groups_1d(int n, int L) {
+  std::vector<std::pair<int, int>> out;
+  if (L == 0) {
+    for (int i = 0; i < n; ++i) out.push_back({i, i + 1});
+    return out;
+  }
+  const int c = (n - 1) / 2;
+  const int run = 1 << L;
+  int ng = c / run;
+  if (ng < 1) ng = 1;
+  std::vector<std::pair<int, int>> right;
+  for (int g = 0; g < ng; ++g) {
+    const int lo = c + 1 + g * run;
+    const int hi = (g == ng - 1) ? n : c + 1 + (g + 1) * run;
+    right.push_back({lo, hi});
+  }
+  for (int g = ng - 1; g >= 0; --g) out.push_back({2 * c + 1 - right[g].second, 2 * c + 1 - right[g].first});
+  out.push_back({c, c + 1});
+  for (auto& r : right) out.push_back(r);
+  return out;
+}
+
+// A velocity space: points with coordinates and weights, and the base rectangle each covers.
+struct VSpace {
+  int D = 2;
+  std::vector<double> xix, xiy, w;
+  std::vector<int> rect;  // 4 per point: x0, x1, y0, y1 (D = 1: y0 = 0, y1 = 1)
+  int nv() const { return (int)w.size(); }
+};
+
+inline void merged(const Base1D& b, int lo, int hi, double& X, double& W) {
+  double sw = 0.0, sx = 0.0;
+  for (int i = lo; i < hi; ++i) { sw += b.w[i]; sx += b.w[i] * b.x[i]; }
+  W = sw;
+  X = sx / sw;
+}
+
+// Tensor-product space with both axes grouped at level L.
+inline VSpace uniform_vspace(const Base1D& b, int D, int L) {
+  VSpace s;
+  s.D = D;
+  const int n = (int)b.x.size();
+  auto gr = groups_1d(n, L);
+  std::vector<double> X(gr.size()), W(gr.size());
+  for (size_t g = 0; g < gr.size(); ++g) merged(b, gr[g].first, gr[g].second, X[g], W[g]);
+  if (D == 1) {
+    for (size_t g = 0; g < gr.size(); ++g) {
+      s.xix.push_back(X[g]); s.xiy.push_back(0.0); s.w.push_back(W[g]);
+      s.rect.insert(s.rect.end(), {gr[g].first, gr[g].second, 0, 1});
+    }
+    return s;
+  }
+  for (size_t gy = 0; gy < gr.size(); ++gy)
+    for (size_t gx = 0; gx < gr.size(); ++gx) {
+      s.xix.push_back(X[gx]); s.xiy.push_back(X[gy]); s.w.push_back(W[gx] * W[gy]);
+      s.rect.insert(s.rect.end(), {gr[gx].first, gr[gx].second, gr[gy].first, gr[gy].second});
+    }
+  return s;
+}
+
+}  // namespace mlvs

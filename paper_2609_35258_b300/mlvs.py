@@ -1,0 +1,177 @@
+"""Thin ctypes binding of the C ABI in include/mlvs.h (argument marshalling only).
+
+Every step of the solver runs in libmlvs.so.  If the library is missing the import fails;
+there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libmlvs.so")
+
+MLVS_OK = 0
+STATUS = {0: "MLVS_OK", -1: "MLVS_ERR_ARG", -2: "MLVS_ERR_OOM", -3: "MLVS_ERR_CUDA",
+          -4: "MLVS_ERR_NONFINITE", -5: "MLVS_ERR_POSITIVITY", -6: "MLVS_ERR_SINGULAR",
+          -7: "MLVS_ERR_TIMEOUT", -8: "MLVS_ERR_STATE"}
+BC_PERIODIC, BC_ZEROGRAD, BC_WALL = 0, 1, 2
+F64, F32, BF16 = 0, 1, 2
+QUAD_BOOLE, QUAD_SIMPSON, QUAD_TRAPZ = 0, 1, 2
+LIMITER_VANLEER, LIMITER_NONE = 0, 1
+RHO, U, V, T, QX, QY, LEVEL, RHOE = 1, 2, 4, 8, 16, 32, 64, 128
+
+
+class mlvs_config(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int), ("n_instances", C.c_int), ("nx", C.c_int), ("ny", C.c_int),
+        ("Lx", C.c_double), ("Ly", C.c_double), ("bc", C.c_int * 4),
+        ("wall", (C.c_double * 3) * 4), ("R", C.c_double), ("K_internal", C.c_double),
+        ("Pr", C.c_double), ("omega", C.c_double), ("Kn", C.c_double), ("mu_ref", C.c_double),
+        ("L_ref", C.c_double), ("T_ref", C.c_double), ("rho_ref", C.c_double),
+        ("cfl", C.c_double), ("dt", C.c_double), ("storage", C.c_int), ("compat_cell", C.c_int),
+        ("compat_face", C.c_int), ("limiter", C.c_int), ("init_W", C.POINTER(C.c_double)),
+        ("stream", C.c_void_p),
+    ]
+
+
+class mlvs_level_desc(C.Structure):
+    _fields_ = [("uniform_L", C.c_int), ("kappa", C.POINTER(C.c_ubyte))]
+
+
+class mlvs_step_stats(C.Structure):
+    _fields_ = [("profile", C.c_int), ("dt", C.c_double), ("cell_velocity_updates", C.c_longlong),
+                ("n_levels", C.c_int), ("launches", C.c_int), ("ms_total", C.c_float),
+                ("ms_phase", C.c_float * 4)]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libmlvs.so not built at {_LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(_LIB_PATH)
+    H = C.c_void_p
+    sig = {
+        "mlvs_create": (C.c_int, [C.POINTER(mlvs_config), C.POINTER(H)]),
+        "mlvs_set_velocity_levels": (C.c_int, [H, C.c_int, C.c_double, C.c_double, C.c_int, C.c_int,
+                                               C.POINTER(mlvs_level_desc), C.c_int]),
+        "mlvs_step": (C.c_int, [H, C.c_int, C.POINTER(mlvs_step_stats)]),
+        "mlvs_moments": (C.c_int, [H, C.c_int, C.c_uint, C.c_void_p, C.c_int]),
+        "mlvs_read_cells": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_time_step": (C.c_int, [H, C.POINTER(C.c_double)]),
+        "mlvs_destroy": (None, [H]),
+        "mlvs_last_error": (C.c_char_p, [H]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("mlvs_create", "mlvs_set_velocity_levels", "mlvs_step", "mlvs_moments",
+            "mlvs_read_cells", "mlvs_time_step", "mlvs_destroy", "mlvs_last_error")
+
+
+class MLVSError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st, h):
+    if st != MLVS_OK:
+        msg = _lib.mlvs_last_error(h)
+        raise MLVSError(st, msg.decode() if msg else "")
+
+
+def mlvs_create(cfg: mlvs_config):
+    h = C.c_void_p()
+    _check(_lib.mlvs_create(C.byref(cfg), C.byref(h)), None)
+    return h
+
+
+def mlvs_set_velocity_levels(h, n_base, umin, umax, quadrature, levels, adaptive=0):
+    arr = (mlvs_level_desc * len(levels))()
+    keep = []
+    for i, L in enumerate(levels):
+        if isinstance(L, int):
+            arr[i].uniform_L = L
+            arr[i].kappa = None
+        else:
+            k = np.ascontiguousarray(L, dtype=np.uint8)
+            keep.append(k)
+            arr[i].uniform_L = -1
+            arr[i].kappa = k.ctypes.data_as(C.POINTER(C.c_ubyte))
+    _check(_lib.mlvs_set_velocity_levels(h, n_base, umin, umax, quadrature, len(levels), arr, adaptive), h)
+
+
+def mlvs_step(h, n_steps=1, profile=False):
+    st = mlvs_step_stats()
+    st.profile = 1 if profile else 0
+    _check(_lib.mlvs_step(h, n_steps, C.byref(st)), h)
+    return st
+
+
+def mlvs_moments(h, instance, fields, ncell, out=None):
+    """Moments as a numpy [n_fields][ncell] array, or into a torch CUDA tensor `out`."""
+    nf = bin(fields).count("1")
+    if out is None:
+        res = np.zeros((nf, ncell))
+        _check(_lib.mlvs_moments(h, instance, fields, res.ctypes.data, 0), h)
+        return res
+    _check(_lib.mlvs_moments(h, instance, fields, C.c_void_p(out.data_ptr()), 1), h)
+    return out
+
+
+def mlvs_read_cells(h, instance, cell0, ncells, nv_cap):
+    g = np.zeros(ncells * nv_cap)
+    hh = np.zeros(ncells * nv_cap)
+    nv = C.c_int()
+    _check(_lib.mlvs_read_cells(h, instance, cell0, ncells, g.ctypes.data_as(C.POINTER(C.c_double)),
+                                hh.ctypes.data_as(C.POINTER(C.c_double)), ncells * nv_cap,
+                                C.byref(nv)), h)
+    n = nv.value
+    return g[: ncells * n].reshape(ncells, n), hh[: ncells * n].reshape(ncells, n)
+
+
+def mlvs_time_step(h):
+    dt = C.c_double()
+    _check(_lib.mlvs_time_step(h, C.byref(dt)), h)
+    return dt.value
+
+
+def mlvs_destroy(h):
+    _lib.mlvs_destroy(h)
+
+
+def mlvs_last_error(h=None):
+    m = _lib.mlvs_last_error(h)
+    return m.decode() if m else ""
+
+
+def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0, K=0.0,
+                Pr=2.0 / 3.0, omega=0.81, Kn=0.0, mu_ref=0.0, cfl=0.5, dt=0.0, storage=F32,
+                compat_cell=1, compat_face=1, limiter=LIMITER_VANLEER, n_instances=1,
+                stream=None, T_ref=1.0, L_ref=1.0, rho_ref=1.0):
+    """Fill an mlvs_config.  init_W: float64 array [n_instances][ny][nx][4].  The returned
+    config keeps a reference to init_W (attribute `_keep`)."""
+    cfg = mlvs_config()
+    cfg.dim, cfg.n_instances, cfg.nx, cfg.ny = dim, n_instances, nx, ny
+    cfg.Lx, cfg.Ly = Lx, Ly
+    for i in range(4):
+        cfg.bc[i] = bc[i]
+        for j in range(3):
+            cfg.wall[i][j] = wall[i][j]
+    cfg.R, cfg.K_internal, cfg.Pr, cfg.omega = R, K, Pr, omega
+    cfg.Kn, cfg.mu_ref, cfg.L_ref, cfg.T_ref, cfg.rho_ref = Kn, mu_ref, L_ref, T_ref, rho_ref
+    cfg.cfl, cfg.dt, cfg.storage = cfl, dt, storage
+    cfg.compat_cell, cfg.compat_face, cfg.limiter = compat_cell, compat_face, limiter
+    W = np.ascontiguousarray(init_W, dtype=np.float64)
+    cfg._keep = W
+    cfg.init_W = W.ctypes.data_as(C.POINTER(C.c_double))
+    cfg.stream = stream
+    return cfg

@@ -1,0 +1,147 @@
+"""GPU-vs-oracle parity of the single-space DUGKS step, through the C ABI.
+
+Tolerances:
+ * FP64 storage: the library and the oracle run the same FP64 algorithm with different
+   summation orders; relative differences of a few 1e-13 per step (1e-10 here).
+ * FP32 storage: per-velocity arithmetic and storage round at 6e-8; after a few steps the
+   moments agree to 1e-5 relative (rho, T), 1e-5 sqrt(RT) for velocity, and the heat flux to
+   1e-3 of its field maximum.
+"""
+import numpy as np
+import pytest
+
+from tests.helpers import have_gpu, oracle_moments, oracle_run, oracle_setup
+from paper_2609_35258_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+if not have_gpu():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2609_35258_b300.solver import Solver  # noqa: E402
+
+
+def _compare(gm, om, rtol_rho, atol_u, rtol_T, qfrac, D=2):
+    rho_o, T_o = om[0], om[3]
+    assert np.max(np.abs(gm[0] - rho_o) / rho_o) < rtol_rho
+    assert np.max(np.abs(gm[1] - om[1])) < atol_u
+    if D == 2:
+        assert np.max(np.abs(gm[2] - om[2])) < atol_u
+    assert np.max(np.abs(gm[3] - T_o) / T_o) < rtol_T
+    qs = max(np.max(np.abs(om[4])), np.max(np.abs(om[5])), 1e-30)
+    assert np.max(np.abs(gm[4] - om[4])) < qfrac * qs
+    if D == 2:
+        assert np.max(np.abs(gm[5] - om[5])) < qfrac * qs
+
+
+@pytest.mark.parametrize("nx,ny", [(40, 20), (3, 2)])
+def test_periodic_f64(nx, ny):
+    desc = workloads.periodic_random(nx, ny, n_base=25, storage="f64")
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    assert abs(s.dt - o["dt"]) < 1e-15
+    s.step(5)
+    g, h = oracle_run(o, 5)
+    _compare(s.moments(), oracle_moments(o, g, h), 1e-10, 1e-10, 1e-10, 1e-8)
+    gg, hh = s.read_cells(0, nx * ny, 25 * 25)
+    np.testing.assert_allclose(gg, g.reshape(nx * ny, -1), rtol=1e-9, atol=1e-12 * g.max())
+    np.testing.assert_allclose(hh, h.reshape(nx * ny, -1), rtol=1e-9, atol=1e-12 * h.max())
+
+
+def test_periodic_f32():
+    desc = workloads.periodic_random(40, 20, n_base=25, storage="f32")
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    s.step(5)
+    g, h = oracle_run(o, 5)
+    _compare(s.moments(), oracle_moments(o, g, h), 1e-5, 1e-5, 1e-5, 1e-3)
+    gg, _ = s.read_cells(0, 40 * 20, 625)
+    np.testing.assert_allclose(gg, g.reshape(800, -1), rtol=0, atol=2e-5 * g.max())
+
+
+def test_cavity_f32_ragged():
+    desc = workloads.cavity(36, n_base=25, Kn=0.075)
+    desc["init"] = desc["init"][:, :36]
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    s.step(10)
+    g, h = oracle_run(o, 10)
+    _compare(s.moments(), oracle_moments(o, g, h), 1e-5, 1e-5, 1e-5, 1e-3)
+
+
+def test_cavity_f64_walls():
+    desc = workloads.cavity(20, n_base=25, Kn=0.075, storage="f64")
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    s.step(8)
+    g, h = oracle_run(o, 8)
+    _compare(s.moments(), oracle_moments(o, g, h), 1e-10, 1e-10, 1e-10, 1e-7)
+
+
+def test_sod_1d_f64_full_config():
+    desc = workloads.sod_1d()           # 200 cells, 101 velocities, Kn = 1e-3, FP64, BGK
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    s.step(20)
+    g, h = oracle_run(o, 20)
+    gm = s.moments()
+    om = oracle_moments(o, g, h)
+    assert np.max(np.abs(gm[0] - om[0]) / om[0]) < 1e-10
+    assert np.max(np.abs(gm[1] - om[1])) < 1e-10
+    assert np.max(np.abs(gm[3] - om[3]) / om[3]) < 1e-10
+
+
+def test_options_bgk_no_limiter_no_compat():
+    desc = workloads.periodic_random(17, 9, n_base=25, storage="f64", Pr=1.0)
+    desc["limiter"] = "none"
+    o = oracle_setup(desc, compat=False)
+    s = Solver(desc, compat_cell=0, compat_face=0)
+    s.step(4)
+    g, h = oracle_run(o, 4)
+    _compare(s.moments(), oracle_moments(o, g, h), 1e-10, 1e-10, 1e-10, 1e-7)
+
+
+def test_conservation_f64_periodic():
+    desc = workloads.periodic_random(33, 17, n_base=25, storage="f64")
+    s = Solver(desc)
+    m0 = s.moments()
+    s.step(50)
+    m1 = s.moments()
+    tot0 = np.array([m0[0].sum(), (m0[0] * m0[1]).sum(), (m0[0] * m0[2]).sum(), m0[6].sum()])
+    tot1 = np.array([m1[0].sum(), (m1[0] * m1[1]).sum(), (m1[0] * m1[2]).sum(), m1[6].sum()])
+    assert np.max(np.abs(tot1 - tot0)) < 1e-12 * np.max(np.abs(tot0))
+
+
+def test_conservation_f32_periodic():
+    """FP32 storage rounds every stored value at 2^-24; the conserved totals drift only by
+    that rounding (bound: 1e-9 relative over 50 steps)."""
+    desc = workloads.periodic_random(33, 17, n_base=25, storage="f32")
+    s = Solver(desc)
+    m0 = s.moments()
+    s.step(50)
+    m1 = s.moments()
+    tot0 = np.array([m0[0].sum(), m0[6].sum()])
+    tot1 = np.array([m1[0].sum(), m1[6].sum()])
+    assert np.max(np.abs(tot1 - tot0) / tot0) < 1e-9
+
+
+def test_wall_mass_conservation_f32():
+    desc = workloads.cavity(32, n_base=25, Kn=0.075)
+    s = Solver(desc)
+    m0 = s.moments()[0].sum()
+    s.step(100)
+    m1 = s.moments()[0].sum()
+    assert abs(m1 - m0) / m0 < 1e-9
+
+
+def test_uniform_bgk_fixed_point_gpu():
+    desc = workloads.periodic_random(10, 10, n_base=25, storage="f64", Pr=1.0)
+    desc["init"][..., 0] = 1.2
+    desc["init"][..., 1] = 0.3
+    desc["init"][..., 2] = -0.1
+    desc["init"][..., 3] = 0.9
+    s = Solver(desc)
+    g0, h0 = s.read_cells(0, 100, 625)
+    s.step(3)
+    g1, h1 = s.read_cells(0, 100, 625)
+    assert np.max(np.abs(g1 - g0)) < 1e-14 * np.max(g0)
