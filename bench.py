@@ -28,6 +28,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the oracle baseline runs on one host thread (numpy elementwise; no threaded BLAS)
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 METRIC = "cell-velocity updates/s (DUGKS step, 2-D cavity 64^2 on 101^2 velocities)"
 UNIT = "updates/s"
@@ -111,15 +114,13 @@ class ClockSampler:
 
 def oracle_rate(ncell_side, nsteps, threads=1):
     """FP64 oracle on a ncell_side^2 cavity with the bench's velocity grid; updates/s."""
-    from threadpoolctl import threadpool_limits
     from paper_2609_35258_b300 import workloads
     from tests.helpers import oracle_run, oracle_setup
     d = workloads.cavity(ncell_side, n_base=101, umax=6.0, Kn=0.075)
-    with threadpool_limits(limits=threads):
-        o = oracle_setup(d)
-        t0 = time.perf_counter()
-        oracle_run(o, nsteps)
-        t = time.perf_counter() - t0
+    o = oracle_setup(d)
+    t0 = time.perf_counter()
+    oracle_run(o, nsteps)
+    t = time.perf_counter() - t0
     upd = ncell_side * ncell_side * 101 * 101 * nsteps
     return upd / t, t, upd
 
@@ -131,20 +132,18 @@ def run_reference(args, rank):
     per_upd = 1.1e-6
     cells = 100.0 / ((args.steps + args.warmup) * 101 * 101 * per_upd)
     side = int(max(2, min(16, math.floor(math.sqrt(max(cells, 4.0))))))
-    from threadpoolctl import threadpool_limits
     from paper_2609_35258_b300 import workloads
     from tests.helpers import oracle_run, oracle_setup
     d = workloads.cavity(side, n_base=101, umax=6.0, Kn=0.075)
-    with threadpool_limits(limits=1):
-        o = oracle_setup(d)
-        for _ in range(args.warmup):
-            g, h = oracle_run(o, 1)
-            o["g"], o["h"] = g, h
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            g, h = oracle_run(o, 1)
-            o["g"], o["h"] = g, h
-        t = time.perf_counter() - t0
+    o = oracle_setup(d)
+    for _ in range(args.warmup):
+        g, h = oracle_run(o, 1)
+        o["g"], o["h"] = g, h
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        g, h = oracle_run(o, 1)
+        o["g"], o["h"] = g, h
+    t = time.perf_counter() - t0
     upd = side * side * 101 * 101 * args.steps
     val = upd / t
     sample = f"{side}x{side}-cell cavity on the same 101^2 velocity grid, {args.steps} oracle steps"

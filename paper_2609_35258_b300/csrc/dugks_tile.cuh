@@ -219,7 +219,6 @@ k_tile(const TileArgs a, int limiter) {
   const T hdx = T(0.5 * k.dx), hdy = T(0.5 * k.dy);
   const T idx_ = T(1.0 / k.dx), idy_ = T(1.0 / k.dy);
   const T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
-  const T four3 = T(4.0 / 3.0), one3 = T(1.0 / 3.0);
   S* __restrict__ fout = reinterpret_cast<S*>(a.f_out);
 
   // prefetch registers
@@ -235,7 +234,7 @@ k_tile(const TileArgs a, int limiter) {
 
   int par = 0;
   for (int v = v0; v < v1; ++v) {
-    const T xix = vt[v], xiy = (D == 2) ? vt[nv + v] : T(0), wv = vt[2 * nv + v], xi2 = vt[3 * nv + v];
+    const T xix = vt[v], xiy = (D == 2) ? vt[nv + v] : T(0), wxv = vt[2 * nv + v], wyv = vt[3 * nv + v];
     const T g0 = g0n, h0 = h0n, g1 = g1n, h1 = h1n;
     if (v + 1 < v1) {
       g0n = ldf<S, T>(fin + (long)(v + 1) * nc + src0);
@@ -246,18 +245,20 @@ k_tile(const TileArgs a, int limiter) {
       }
     }
     // ---- phase 1: phi-bar-plus on the extended tile
-    T gbp0, hbp0;
+    // Written as phi~ + b (phi^S - phi~) so that the two blending weights sum to one exactly
+    // whatever their rounding: the collision then conserves the moments of phi~.
+    T dg0, dh0;
     {
       T gs, hs;
-      model_eval<T, D>(m0, xix, xiy, xi2, c0, twoK, gs, hs);
-      gbp0 = m0.c1 * g0 + m0.c2 * gs;
-      hbp0 = m0.c1 * h0 + m0.c2 * hs;
-      sPg[par][e0] = gbp0;
-      sPh[par][e0] = hbp0;
+      model_eval<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
+      dg0 = gs - g0;
+      dh0 = hs - h0;
+      sPg[par][e0] = g0 + m0.c1 * dg0;
+      sPh[par][e0] = h0 + m0.c1 * dh0;
       if (src1 >= 0) {
-        model_eval<T, D>(m1, xix, xiy, xi2, c0, twoK, gs, hs);
-        sPg[par][e1] = m1.c1 * g1 + m1.c2 * gs;
-        sPh[par][e1] = m1.c1 * h1 + m1.c2 * hs;
+        model_eval<T, D>(m1, xix, xiy, c0, twoK, gs, hs);
+        sPg[par][e1] = g1 + m1.c1 * (gs - g1);
+        sPh[par][e1] = h1 + m1.c1 * (hs - h1);
       }
     }
     __syncthreads();
@@ -316,8 +317,8 @@ k_tile(const TileArgs a, int limiter) {
           if (!fr[q].owned) continue;
           if (fr[q].kind == FK_INTERIOR) {
             const T xp = xix - fsx[q], yp = (D == 2) ? xiy - fsy[q] : T(0);
-            const T wg = wv * gb;
-            const T e = wv * ((xp * xp + yp * yp) * gb + hb);
+            const T wg = wxv * (wyv * gb);
+            const T e = wxv * (wyv * ((xp * xp + yp * yp) * gb + hb));
             acc0[q].add(wg);
             accX[q].add(wg * xp);
             accE[q].add(e);
@@ -332,20 +333,20 @@ k_tile(const TileArgs a, int limiter) {
           } else {
             // wall: outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) g-bar
             const T xin = (fr[q].kind == FK_WALL_LO) ? xn : -xn;
-            if (xin <= T(0)) acc0[q].add(wv * xin * gb);
+            if (xin <= T(0)) acc0[q].add(wxv * (wyv * (xin * gb)));
           }
         } else {
           T gf, hf;
           if (fr[q].kind == FK_INTERIOR) {
             T gs, hs;
-            model_eval<T, D>(fm[q], xix, xiy, xi2, c0, twoK, gs, hs);
-            gf = fm[q].c1 * gb + fm[q].c2 * gs;
-            hf = fm[q].c1 * hb + fm[q].c2 * hs;
+            model_eval<T, D>(fm[q], xix, xiy, c0, twoK, gs, hs);
+            gf = gb + fm[q].c2 * (gs - gb);     // Eq. recover_phi, weights summing to one
+            hf = hb + fm[q].c2 * (hs - hb);
           } else {
             const T xin = (fr[q].kind == FK_WALL_LO) ? xn : -xn;
             if (xin > T(0)) {
               T gs, hs;
-              model_eval<T, D>(fm[q], xix, xiy, xi2, c0, twoK, gs, hs);
+              model_eval<T, D>(fm[q], xix, xiy, c0, twoK, gs, hs);
               gf = fm[q].c2 * gs;
               hf = fm[q].c2 * hs;
             } else {
@@ -368,8 +369,9 @@ k_tile(const TileArgs a, int limiter) {
       // ---- phase 4: update of the tile's cells (Eq. explicit_update)
       if (own_active) {
         const int w_ = (D == 2) ? ty * (TX + 1) + tx : tx;
-        T gn = four3 * gbp0 - one3 * g0 - lamx * xix * (sFxg[w_ + 1] - sFxg[w_]);
-        T hn = four3 * hbp0 - one3 * h0 - lamx * xix * (sFxh[w_ + 1] - sFxh[w_]);
+        // phi~+ = 4/3 phi-bar-plus - 1/3 phi~ = phi~ + (4/3) b (phi^S - phi~)
+        T gn = g0 + m0.c2 * dg0 - lamx * xix * (sFxg[w_ + 1] - sFxg[w_]);
+        T hn = h0 + m0.c2 * dh0 - lamx * xix * (sFxh[w_ + 1] - sFxh[w_]);
         if (D == 2) {
           const int sI = ty * TX + tx;
           gn -= lamy * xiy * (sFyg[sI + TX] - sFyg[sI]);
@@ -380,8 +382,8 @@ k_tile(const TileArgs a, int limiter) {
         // moments of the stored value
         const T gq = ldf_round<S, T>(gn), hq = ldf_round<S, T>(hn);
         const T xp = xix - m0.ux, yp = (D == 2) ? xiy - m0.uy : T(0);
-        const T wg = wv * gq;
-        const T e = wv * ((xp * xp + yp * yp) * gq + hq);
+        const T wg = wxv * (wyv * gq);
+        const T e = wxv * (wyv * ((xp * xp + yp * yp) * gq + hq));
         acc0[0].add(wg);
         accX[0].add(wg * xp);
         accE[0].add(e);

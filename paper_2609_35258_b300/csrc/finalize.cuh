@@ -1,12 +1,22 @@
 // Point finalisation: from velocity-chunk partial moments to the model parameters of a cell
 // or a face, including the four-moment compatibility correction (Sec. 3.3.1).
 //
-// One warp per point.  The chunk partials are summed in chunk order (deterministic), the
-// macroscopic state follows Eq. discrete_W / discrete_q (cells) or Eq. W_from_bar (faces),
-// and the correction sums of Eq. joint_gh_correction_matrix / Eq. linear_moment_defect run
-// over the velocities with the same per-velocity evaluation (model_eval, compute type T)
-// that the tile kernels use, so the corrected model distribution they evaluate carries the
-// target moments up to the rounding of its own arithmetic.
+// One thread per point.  The chunk partials are summed in chunk order (deterministic); the
+// macroscopic state follows Eq. discrete_W / discrete_q (cells) or Eq. W_from_bar (faces).
+//
+// Compatibility correction (Eq. gh_model_correction, chi^g = g^S, chi^h = h^S).  The basis
+// {1, xi_x, xi_y, E_xi} of Eq. eq_four_basis spans the same functions as {1, c_x, c_y, |c|^2}
+// with c = xi - u, and the constraint rows (1, xi, (xi^2 g + h)/2) combine into the peculiar
+// rows (1, c, (|c|^2 g + h)/2) with targets (rho, rho(u - u_p), rho e + rho|u - u_p|^2/2), u_p
+// the velocity stored in the parameters.  The corrected distribution is therefore the same
+// as with the paper's basis.  The sums of Eq. joint_gh_correction_matrix and
+// Eq. linear_moment_defect are evaluated
+//   * on tensor-product spaces, from one-axis sums S_a = sum_i W_i e_i c_i^a (a <= 7) of the
+//     same per-axis Gaussian factors e_i that the tile kernels multiply (Num::gauss), so
+//     sum_{ij} W_i W_j e_i e_j c_x^a c_y^b = S_a S_b and the correction matches the values
+//     the tile kernels evaluate up to the rounding of their own products;
+//   * otherwise, directly over the velocities with the tile kernels' model_eval.
+// Sums that enter the moment defect are compensated (FP32) and combined in FP64.
 #pragma once
 #include "mlvs_common.cuh"
 
@@ -24,8 +34,9 @@ struct PointArgs {
   int is_face;          // 0: cells, 1: faces
   const void* cprm;     // [NP][ncell] current cell params (T): shift source
   void* prm_out;        // [NP][npt] (T)
-  double* W;            // cells: [8][ncell] rho,u,v,T,qx,qy,rhoE,tau (may be null for faces)
+  double* W;            // cells: [8][ncell] rho,u,v,T,qx,qy,rhoE,tau (null for faces)
   const void* vt;       // [4][nv] (T)
+  const void* ax;       // [2][nax] (T) when k.nax > 0
   int compat;
   double wall[4][3];    // (u_w, v_w, T_w)
   int* err;             // device error bits
@@ -33,120 +44,183 @@ struct PointArgs {
 
 enum { ERR_NONFINITE = 1, ERR_POSITIVITY = 2, ERR_SINGULAR = 4 };
 
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-
-// Gaussian elimination with partial pivoting, n <= 4.  Returns false if singular.
-__device__ inline bool solve_small(double A[4][4], double b[4], int n) {
+// Gaussian elimination with partial pivoting on the rows/columns listed in idx.
+__device__ inline bool solve_small(double A[4][4], double b[4], const int* idx, int n) {
+  double M[4][4], r[4];
+  for (int i = 0; i < n; ++i) {
+    r[i] = b[idx[i]];
+    for (int j = 0; j < n; ++j) M[i][j] = A[idx[i]][idx[j]];
+  }
   for (int c = 0; c < n; ++c) {
     int p = c;
-    double best = fabs(A[c][c]);
-    for (int r = c + 1; r < n; ++r)
-      if (fabs(A[r][c]) > best) { best = fabs(A[r][c]); p = r; }
+    double best = fabs(M[c][c]);
+    for (int q = c + 1; q < n; ++q)
+      if (fabs(M[q][c]) > best) { best = fabs(M[q][c]); p = q; }
     if (!(best > 1e-300)) return false;
     if (p != c) {
-      for (int j = 0; j < n; ++j) { double t = A[c][j]; A[c][j] = A[p][j]; A[p][j] = t; }
-      double t = b[c]; b[c] = b[p]; b[p] = t;
+      for (int j = 0; j < n; ++j) { double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
+      double t = r[c]; r[c] = r[p]; r[p] = t;
     }
-    for (int r = c + 1; r < n; ++r) {
-      const double f = A[r][c] / A[c][c];
-      for (int j = c; j < n; ++j) A[r][j] -= f * A[c][j];
-      b[r] -= f * b[c];
+    for (int q = c + 1; q < n; ++q) {
+      const double f = M[q][c] / M[c][c];
+      for (int j = c; j < n; ++j) M[q][j] -= f * M[c][j];
+      r[q] -= f * r[c];
     }
   }
   for (int c = n - 1; c >= 0; --c) {
-    double s = b[c];
-    for (int j = c + 1; j < n; ++j) s -= A[c][j] * b[j];
-    b[c] = s / A[c][c];
+    double s = r[c];
+    for (int j = c + 1; j < n; ++j) s -= M[c][j] * r[j];
+    r[c] = s / M[c][c];
   }
+  for (int i = 0; i < 4; ++i) b[i] = 0.0;
+  for (int i = 0; i < n; ++i) b[idx[i]] = r[i];
   return true;
 }
 
-// Model parameters of a point with state (rho, u, T, q) and compatibility coefficients.
-// All lanes of the warp call this with identical arguments; every lane returns the same mp.
+// One-axis sums S[a] = sum_i W_i gauss(X_i - u) (X_i - u)^a, a = 0..7.
+template <class T>
+__device__ inline void axis_sums(const T* ax, int nax, T u, T inv2RT, T lnh, double S[8]) {
+  KSum<T> acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a].zero();
+  for (int i = 0; i < nax; ++i) {
+    const T c = ax[i] - u;
+    T p = ax[nax + i] * Num<T>::gauss(c, inv2RT, lnh);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      acc[a].add(p);
+      p *= c;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) S[a] = acc[a].val();
+}
+
+// Peculiar moments of the uncorrected model of mp:
+//   G[a][b] = sum w g^S c_x^a c_y^b (a+b <= 4),  H[a][b] = sum w h^S c_x^a c_y^b (a+b <= 2).
 template <class T, int D>
-__device__ inline bool point_model(const PointArgs& a, double rho, double ux, double uy, double Tm,
+__device__ inline void model_moments(const PointArgs& A, const MP<T>& mp, double G[5][5], double H[3][3]) {
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) G[a][b] = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) H[a][b] = 0.0;
+  const StepConst& k = A.k;
+  if (k.nax > 0) {
+    const T* ax = reinterpret_cast<const T*>(A.ax);
+    double Sx[8], Sy[8];
+    axis_sums<T>(ax, k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
+    if (D == 2) {
+      axis_sums<T>(ax, k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
+    } else {
+      Sy[0] = 1.0;
+      for (int b = 1; b < 8; ++b) Sy[b] = 0.0;
+    }
+    const double kx = (double)mp.kqx, ky = (double)mp.kqy;
+    const double i2 = 2.0 * (double)mp.inv2RT;      // 1/RT as the tile kernels form it
+    const double RT = (double)mp.RT, c0 = k.c0;
+    const double al = RT * c0 * i2, be = RT * (D * c0 + k.twoK);
+    for (int a = 0; a < 5; ++a)
+      for (int b = 0; a + b < 5; ++b) {
+        const double cub = kx * (Sx[a + 3] * Sy[b] + Sx[a + 1] * Sy[b + 2]) +
+                           ky * (Sx[a + 2] * Sy[b + 1] + Sx[a] * Sy[b + 3]);
+        const double lin = kx * Sx[a + 1] * Sy[b] + ky * Sx[a] * Sy[b + 1];
+        G[a][b] = Sx[a] * Sy[b] - (D + 2) * lin + i2 * cub;
+        if (a + b < 3) H[a][b] = RT * c0 * Sx[a] * Sy[b] + al * cub - be * lin;
+      }
+    return;
+  }
+  // direct sums over the velocities
+  const T* vt = reinterpret_cast<const T*>(A.vt);
+  const int nv = k.nv;
+  const T c0 = T(k.c0), twoK = T(k.twoK);
+  KSum<T> g00, g10, g01, e0;
+  g00.zero(); g10.zero(); g01.zero(); e0.zero();
+  T gs[15], hs[6];
+  for (int j = 0; j < 15; ++j) gs[j] = T(0);
+  for (int j = 0; j < 6; ++j) hs[j] = T(0);
+  for (int v = 0; v < nv; ++v) {
+    const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0), wxv = vt[2 * nv + v], wyv = vt[3 * nv + v];
+    T gv, hv;
+    model_eval<T, D>(mp, xx, yy, c0, twoK, gv, hv);
+    const T cx = xx - mp.ux, cy = (D == 2) ? yy - mp.uy : T(0);
+    const T wg = wxv * (wyv * gv), wh = wxv * (wyv * hv);
+    g00.add(wg);
+    g10.add(wg * cx);
+    g01.add(wg * cy);
+    e0.add(T(0.5) * ((cx * cx + cy * cy) * wg + wh));
+    int j = 0, jh = 0;
+    T px = wg, qx = wh;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+      T p = px, q = qx;
+#pragma unroll
+      for (int b = 0; a + b < 5; ++b) {
+        gs[j++] += p;
+        if (a + b < 3) hs[jh++] += q;
+        p *= cy;
+        q *= cy;
+      }
+      px *= cx;
+      qx *= cx;
+    }
+  }
+  int j = 0, jh = 0;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; a + b < 5; ++b) {
+      G[a][b] = (double)gs[j++];
+      if (a + b < 3) H[a][b] = (double)hs[jh++];
+    }
+  G[0][0] = g00.val();
+  G[1][0] = g10.val();
+  G[0][1] = g01.val();
+  // keep the compensated energy-row sum: fold it into the H[0][0] slot
+  H[0][0] = 2.0 * e0.val() - G[2][0] - G[0][2];
+}
+
+// Model parameters of a point with state (rho, u, T, q), with the compatibility correction.
+template <class T, int D>
+__device__ inline bool point_model(const PointArgs& A, double rho, double ux, double uy, double Tm,
                                    double qx, double qy, MP<T>& mp) {
-  const GasDev& g = a.gas;
+  const GasDev& g = A.gas;
   const double RT = g.R * Tm;
   const double p = rho * RT;
   const double kap = (1.0 - g.Pr) / (5.0 * p * RT);
   mp.ux = T(ux); mp.uy = T(uy);
-  mp.lnn = T(log(rho) - 0.5 * D * log(2.0 * 3.14159265358979323846 * RT));
+  mp.lnh = T((log(rho) - 0.5 * D * log(2.0 * 3.14159265358979323846 * RT)) / D);
   mp.inv2RT = T(0.5 / RT);
   mp.kqx = T(kap * qx); mp.kqy = T(kap * qy);
   mp.RT = T(RT);
-  mp.p0 = T(1); mp.a1 = T(0); mp.a2 = T(0); mp.p3 = T(0);
-  if (!a.compat) return true;
-  // correction sums (Eq. joint_gh_correction_matrix and Eq. linear_moment_defect)
-  const T* vt = reinterpret_cast<const T*>(a.vt);
-  const int nv = a.k.nv;
-  const T c0 = T(a.k.c0), twoK = T(a.k.twoK);
-  KSum<T> s0, s1, s2, e3;        // sum w g, w xi_x g, w xi_y g, 1/2 w (xi^2 g + h)
-  s0.zero(); s1.zero(); s2.zero(); e3.zero();
-  T sg[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};  // indices 3..9 used
-  T sh[4] = {0, 0, 0, 0};                     // indices 1..3 used
-  const int lane = threadIdx.x & 31;
-  for (int v = lane; v < nv; v += 32) {
-    const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0), w = vt[2 * nv + v], x2 = vt[3 * nv + v];
-    T gv, hv;
-    model_eval<T, D>(mp, xx, yy, x2, c0, twoK, gv, hv);
-    const T wg = w * gv, wh = w * hv;
-    s0.add(wg);
-    s1.add(wg * xx);
-    s2.add(wg * yy);
-    e3.add(T(0.5) * (x2 * wg + wh));
-    sg[3] += wg * x2;
-    sg[4] += wg * xx * xx;
-    sg[5] += wg * xx * yy;
-    sg[6] += wg * yy * yy;
-    sg[7] += wg * xx * x2;
-    sg[8] += wg * yy * x2;
-    sg[9] += wg * x2 * x2;
-    sh[1] += wh * xx;
-    sh[2] += wh * yy;
-    sh[3] += wh * x2;
-  }
-  double S0 = warp_sum(s0.val()), S1 = warp_sum(s1.val()), S2 = warp_sum(s2.val());
-  double E3 = warp_sum(e3.val());
-  double G[10], H[4];
-  for (int i = 3; i < 10; ++i) G[i] = warp_sum((double)sg[i]);
-  for (int i = 1; i < 4; ++i) H[i] = warp_sum((double)sh[i]);
-  const double hc = 0.5 * a.k.c0 * RT;   // 1/2 (3-D+K) R T of E_xi
-  // rows: kernels (g, xi_x g, xi_y g, 1/2(xi^2 g + h)); columns: basis (1, xi_x, xi_y, E_xi)
-  double A[4][4], b[4];
-  const double rhoE = rho * (0.5 * (ux * ux + uy * uy) + 0.5 * (3.0 + g.K) * g.R * Tm);
-  if (D == 2) {
-    A[0][0] = S0; A[0][1] = S1;   A[0][2] = S2;   A[0][3] = hc * S0 + 0.5 * G[3];
-    A[1][0] = S1; A[1][1] = G[4]; A[1][2] = G[5]; A[1][3] = hc * S1 + 0.5 * G[7];
-    A[2][0] = S2; A[2][1] = G[5]; A[2][2] = G[6]; A[2][3] = hc * S2 + 0.5 * G[8];
-    A[3][0] = E3; A[3][1] = 0.5 * (G[7] + H[1]); A[3][2] = 0.5 * (G[8] + H[2]);
-    A[3][3] = hc * E3 + 0.25 * (G[9] + H[3]);
-    b[0] = rho - S0; b[1] = rho * ux - S1; b[2] = rho * uy - S2; b[3] = rhoE - E3;
-    if (!solve_small(A, b, 4)) return false;
-    mp.p0 = T(1.0 + b[0] + b[3] * hc);
-    mp.a1 = T(b[1]); mp.a2 = T(b[2]); mp.p3 = T(0.5 * b[3]);
-  } else {
-    A[0][0] = S0; A[0][1] = S1;   A[0][2] = hc * S0 + 0.5 * G[3];
-    A[1][0] = S1; A[1][1] = G[4]; A[1][2] = hc * S1 + 0.5 * G[7];
-    A[2][0] = E3; A[2][1] = 0.5 * (G[7] + H[1]); A[2][2] = hc * E3 + 0.25 * (G[9] + H[3]);
-    b[0] = rho - S0; b[1] = rho * ux - S1; b[2] = rhoE - E3;
-    if (!solve_small(A, b, 3)) return false;
-    mp.p0 = T(1.0 + b[0] + b[2] * hc);
-    mp.a1 = T(b[1]); mp.a2 = T(0); mp.p3 = T(0.5 * b[2]);
-  }
+  mp.b0 = T(0); mp.b1 = T(0); mp.b2 = T(0); mp.b3 = T(0);
+  if (!A.compat) return true;
+  double G[5][5], H[3][3];
+  model_moments<T, D>(A, mp, G, H);
+  // rows: (g, c_x g, c_y g, (|c|^2 g + h)/2); columns: basis (1, c_x, c_y, |c|^2)
+  double M[4][4], b[4];
+  M[0][0] = G[0][0]; M[0][1] = G[1][0]; M[0][2] = G[0][1]; M[0][3] = G[2][0] + G[0][2];
+  M[1][0] = G[1][0]; M[1][1] = G[2][0]; M[1][2] = G[1][1]; M[1][3] = G[3][0] + G[1][2];
+  M[2][0] = G[0][1]; M[2][1] = G[1][1]; M[2][2] = G[0][2]; M[2][3] = G[2][1] + G[0][3];
+  M[3][0] = 0.5 * (G[2][0] + G[0][2] + H[0][0]);
+  M[3][1] = 0.5 * (G[3][0] + G[1][2] + H[1][0]);
+  M[3][2] = 0.5 * (G[2][1] + G[0][3] + H[0][1]);
+  M[3][3] = 0.5 * (G[4][0] + 2.0 * G[2][2] + G[0][4] + H[2][0] + H[0][2]);
+  const double dux = ux - (double)mp.ux, duy = (D == 2) ? uy - (double)mp.uy : 0.0;
+  const double rhoe = 0.5 * (3.0 + g.K) * rho * RT + 0.5 * rho * (dux * dux + duy * duy);
+  b[0] = rho - M[0][0];
+  b[1] = rho * dux - M[1][0];
+  b[2] = rho * duy - M[2][0];
+  b[3] = rhoe - M[3][0];
+  const int idx2[4] = {0, 1, 2, 3}, idx1[3] = {0, 1, 3};
+  if (!solve_small(M, b, D == 2 ? idx2 : idx1, D == 2 ? 4 : 3)) return false;
+  mp.b0 = T(b[0]); mp.b1 = T(b[1]); mp.b2 = T(b[2]); mp.b3 = T(b[3]);
   return true;
 }
 
 template <class T>
 __device__ __forceinline__ void store_mp(T* P, long n, long i, const MP<T>& m, T kind) {
-  P[P_UX * n + i] = m.ux; P[P_UY * n + i] = m.uy; P[P_LNN * n + i] = m.lnn;
+  P[P_UX * n + i] = m.ux; P[P_UY * n + i] = m.uy; P[P_LNH * n + i] = m.lnh;
   P[P_INV2RT * n + i] = m.inv2RT; P[P_KQX * n + i] = m.kqx; P[P_KQY * n + i] = m.kqy;
-  P[P_RT * n + i] = m.RT; P[P_P0 * n + i] = m.p0; P[P_A1 * n + i] = m.a1;
-  P[P_A2 * n + i] = m.a2; P[P_P3 * n + i] = m.p3; P[P_C1 * n + i] = m.c1;
+  P[P_RT * n + i] = m.RT; P[P_B0 * n + i] = m.b0; P[P_B1 * n + i] = m.b1;
+  P[P_B2 * n + i] = m.b2; P[P_B3 * n + i] = m.b3; P[P_C1 * n + i] = m.c1;
   P[P_C2 * n + i] = m.c2; P[P_KIND * n + i] = kind;
 }
 
@@ -155,156 +229,170 @@ __device__ __forceinline__ int wrap_or_clamp_h(int g, int n, int periodic) {
   return g < 0 ? 0 : (g >= n ? n - 1 : g);
 }
 
+// Normal mass flux of the unit-density wall Maxwellian over the velocities entering the
+// domain: den = sum_{xi.n_in > 0} w (xi.n_in) g_w, with the tile kernels' evaluation.
+template <class T, int D>
+__device__ inline double wall_den(const PointArgs& A, const MP<T>& mp, bool xdir, T sgn) {
+  const StepConst& k = A.k;
+  if (k.nax > 0) {
+    const T* ax = reinterpret_cast<const T*>(A.ax);
+    KSum<T> nrm, tan_;
+    nrm.zero(); tan_.zero();
+    const T un = xdir ? mp.ux : mp.uy, ut = xdir ? mp.uy : mp.ux;
+    for (int i = 0; i < k.nax; ++i) {
+      const T X = ax[i], Wt = ax[k.nax + i];
+      const T xin = sgn * X;
+      if (xin > T(0)) nrm.add(Wt * xin * Num<T>::gauss(X - un, mp.inv2RT, mp.lnh));
+      if (D == 2) tan_.add(Wt * Num<T>::gauss(X - ut, mp.inv2RT, mp.lnh));
+    }
+    return D == 2 ? nrm.val() * tan_.val() : nrm.val();
+  }
+  const T* vt = reinterpret_cast<const T*>(A.vt);
+  const int nv = k.nv;
+  KSum<T> den;
+  den.zero();
+  for (int v = 0; v < nv; ++v) {
+    const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0);
+    const T xin = sgn * (xdir ? xx : yy);
+    if (xin > T(0)) {
+      T gv, hv;
+      model_eval<T, D>(mp, xx, yy, T(k.c0), T(k.twoK), gv, hv);
+      den.add(vt[2 * nv + v] * (vt[3 * nv + v] * (xin * gv)));
+    }
+  }
+  return den.val();
+}
+
 // Cells (is_face = 0): Eq. discrete_W, Eq. discrete_q, tau = mu(T)/p, blending of phi-bar-plus.
 // Faces (is_face = 1): Eq. W_from_bar, q = 2 tau/(2 tau + s Pr) q-bar, Eq. recover_phi weights;
 // wall faces: rho_w from the zero net normal mass flux.
 template <class T, int D>
 __global__ void k_finalize(const PointArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.npt) return;
   const StepConst& k = a.k;
   const T* cp = reinterpret_cast<const T*>(a.cprm);
   T* po = reinterpret_cast<T*>(a.prm_out);
   const long nc = k.ncell;
-  for (int i = warp; i < a.npt; i += nwarps) {
-    // chunk sums in chunk order: lane m sums moment m
-    double mom = 0.0;
-    if (lane < NMOM)
-      for (int c = 0; c < k.nchunk; ++c) mom += a.part[((long)c * NMOM + lane) * a.npt + i];
-    double M[NMOM];
+  double M[NMOM];
 #pragma unroll
-    for (int m = 0; m < NMOM; ++m) M[m] = __shfl_sync(0xffffffffu, mom, m);
+  for (int m = 0; m < NMOM; ++m) M[m] = 0.0;
+  for (int c = 0; c < k.nchunk; ++c)
+#pragma unroll
+    for (int m = 0; m < NMOM; ++m) M[m] += a.part[((long)c * NMOM + m) * a.npt + i];
 
-    // shift and face kind
-    T shx, shy;
-    int kind = FK_INTERIOR;
-    int side = -1;
-    if (!a.is_face) {
-      shx = cp[P_UX * nc + i];
-      shy = cp[P_UY * nc + i];
+  T shx, shy;
+  int kind = FK_INTERIOR;
+  int side = -1;
+  if (!a.is_face) {
+    shx = cp[P_UX * nc + i];
+    shy = cp[P_UY * nc + i];
+  } else {
+    int sL, sR;
+    const int nxf = k.nfx * k.ny;
+    if (i < nxf) {
+      const int gj = i / k.nfx, gi = i % k.nfx;
+      sL = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi - 1, k.nx, k.px);
+      sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi, k.nx, k.px);
+      if (!k.px && gi == 0 && k.bc[0] == BC_WALL) { kind = FK_WALL_LO; side = 0; }
+      if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) { kind = FK_WALL_HI; side = 1; }
     } else {
-      int sL, sR;
-      const int nxf = k.nfx * k.ny;
-      if (i < nxf) {
-        const int gj = i / k.nfx, gi = i % k.nfx;
-        sL = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi - 1, k.nx, k.px);
-        sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi, k.nx, k.px);
-        if (!k.px && gi == 0 && k.bc[0] == BC_WALL) { kind = FK_WALL_LO; side = 0; }
-        if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) { kind = FK_WALL_HI; side = 1; }
-      } else {
-        const int r = i - nxf;
-        const int gj = r / k.nx, gi = r % k.nx;
-        sL = wrap_or_clamp_h(gj - 1, k.ny, k.py) * k.nx + gi;
-        sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + gi;
-        if (!k.py && gj == 0 && k.bc[2] == BC_WALL) { kind = FK_WALL_LO; side = 2; }
-        if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) { kind = FK_WALL_HI; side = 3; }
-      }
-      shx = T(0.5) * (cp[P_UX * nc + sL] + cp[P_UX * nc + sR]);
-      shy = (D == 2) ? T(0.5) * (cp[P_UY * nc + sL] + cp[P_UY * nc + sR]) : T(0);
+      const int r = i - nxf;
+      const int gj = r / k.nx, gi = r % k.nx;
+      sL = wrap_or_clamp_h(gj - 1, k.ny, k.py) * k.nx + gi;
+      sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + gi;
+      if (!k.py && gj == 0 && k.bc[2] == BC_WALL) { kind = FK_WALL_LO; side = 2; }
+      if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) { kind = FK_WALL_HI; side = 3; }
     }
-    const GasDev& g = a.gas;
-    MP<T> mp;
-    if (kind != FK_INTERIOR) {
-      // diffuse wall: unit-density wall Maxwellian, rho_w = -M_out / den
-      const double uw = a.wall[side][0], vw = a.wall[side][1], Tw = a.wall[side][2];
-      const double RT = g.R * Tw;
-      mp.ux = T(uw); mp.uy = T(vw);
-      mp.lnn = T(-0.5 * D * log(2.0 * 3.14159265358979323846 * RT));
-      mp.inv2RT = T(0.5 / RT); mp.kqx = T(0); mp.kqy = T(0); mp.RT = T(RT);
-      mp.p0 = T(1); mp.a1 = T(0); mp.a2 = T(0); mp.p3 = T(0);
-      const T* vt = reinterpret_cast<const T*>(a.vt);
-      const int nv = k.nv;
-      const bool xdir = (side < 2);
-      const T sgn = (kind == FK_WALL_LO) ? T(1) : T(-1);
-      KSum<T> den;
-      den.zero();
-      for (int v = lane; v < nv; v += 32) {
-        const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0);
-        const T xin = sgn * (xdir ? xx : yy);
-        if (xin > T(0)) {
-          T gv, hv;
-          model_eval<T, D>(mp, xx, yy, vt[3 * nv + v], T(k.c0), T(k.twoK), gv, hv);
-          den.add(vt[2 * nv + v] * xin * gv);
-        }
-      }
-      const double dsum = warp_sum(den.val());
-      const double rw = -M[MO_0] / dsum;
-      mp.c1 = T(0);
-      mp.c2 = T(rw);
-      if (lane == 0) {
-        store_mp<T>(po, a.npt, i, mp, T(kind));
-        po[P_SHX * (long)a.npt + i] = shx;
-        po[P_SHY * (long)a.npt + i] = shy;
-        if (!(rw >= 0.0) || !isfinite(rw)) atomicOr(a.err, ERR_POSITIVITY);
-      }
-      continue;
-    }
-    const double rho = M[MO_0];
-    const double upx = M[MO_X] / rho, upy = (D == 2) ? M[MO_Y] / rho : 0.0;
-    const double u2 = upx * upx + upy * upy;
-    const double ux = (double)shx + upx, uy = (D == 2) ? (double)shy + upy : 0.0;
-    const double Tm = (M[MO_E] - rho * u2) / ((3.0 + g.K) * rho * g.R);
-    // q = 1/2 [J - 2 u'.G - u' E' + 2 rho |u'|^2 u']  in the shifted frame
-    double qx = 0.5 * (M[MO_JX] - 2.0 * (upx * M[MO_GXX] + upy * M[MO_GXY]) - upx * M[MO_E] + 2.0 * rho * u2 * upx);
-    double qy = (D == 2) ? 0.5 * (M[MO_JY] - 2.0 * (upx * M[MO_GXY] + upy * M[MO_GYY]) - upy * M[MO_E] + 2.0 * rho * u2 * upy) : 0.0;
-    const double p = rho * g.R * Tm;
-    const double mu = g.mu_ref * pow(Tm / g.T_ref, g.omega);
-    const double tau = mu / p;
-    const double hdt = a.is_face ? 0.5 * k.dt : k.dt;    // dt at cells, s at faces
-    const double qf = 2.0 * tau / (2.0 * tau + hdt * g.Pr);
-    qx *= qf;
-    qy *= qf;
-    bool ok = point_model<T, D>(a, rho, ux, uy, Tm, qx, qy, mp);
-    const double s = 0.5 * k.dt;
-    if (!a.is_face) {
-      mp.c1 = T((2.0 * tau - s) / (2.0 * tau + k.dt));
-      mp.c2 = T(3.0 * s / (2.0 * tau + k.dt));
-    } else {
-      mp.c1 = T(2.0 * tau / (2.0 * tau + s));
-      mp.c2 = T(s / (2.0 * tau + s));
-    }
-    if (lane == 0) {
-      store_mp<T>(po, a.npt, i, mp, T(kind));
-      po[P_SHX * (long)a.npt + i] = shx;
-      po[P_SHY * (long)a.npt + i] = shy;
-      if (a.W) {
-        a.W[0 * nc + i] = rho;
-        a.W[1 * nc + i] = ux;
-        a.W[2 * nc + i] = uy;
-        a.W[3 * nc + i] = Tm;
-        a.W[4 * nc + i] = qx;
-        a.W[5 * nc + i] = qy;
-        a.W[6 * nc + i] = rho * (0.5 * (ux * ux + uy * uy) + 0.5 * (3.0 + g.K) * g.R * Tm);
-        a.W[7 * nc + i] = tau;
-      }
-      if (!ok) atomicOr(a.err, ERR_SINGULAR);
-      if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.err, ERR_NONFINITE);
-      else if (!(rho > 0.0) || !(Tm > 0.0)) atomicOr(a.err, ERR_POSITIVITY);
-    }
+    shx = T(0.5) * (cp[P_UX * nc + sL] + cp[P_UX * nc + sR]);
+    shy = (D == 2) ? T(0.5) * (cp[P_UY * nc + sL] + cp[P_UY * nc + sR]) : T(0);
   }
+  const GasDev& g = a.gas;
+  MP<T> mp;
+  if (kind != FK_INTERIOR) {
+    // diffuse wall: unit-density wall Maxwellian, rho_w = -M_out / den
+    const double uw = a.wall[side][0], vw = a.wall[side][1], Tw = a.wall[side][2];
+    const double RT = g.R * Tw;
+    mp.ux = T(uw); mp.uy = T(vw);
+    mp.lnh = T(-0.5 * log(2.0 * 3.14159265358979323846 * RT));
+    mp.inv2RT = T(0.5 / RT); mp.kqx = T(0); mp.kqy = T(0); mp.RT = T(RT);
+    mp.b0 = T(0); mp.b1 = T(0); mp.b2 = T(0); mp.b3 = T(0);
+    const double den = wall_den<T, D>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1));
+    const double rw = -M[MO_0] / den;
+    mp.c1 = T(0);
+    mp.c2 = T(rw);
+    store_mp<T>(po, a.npt, i, mp, T(kind));
+    po[P_SHX * (long)a.npt + i] = shx;
+    po[P_SHY * (long)a.npt + i] = shy;
+    if (!(rw >= 0.0) || !isfinite(rw)) atomicOr(a.err, ERR_POSITIVITY);
+    return;
+  }
+  const double rho = M[MO_0];
+  const double upx = M[MO_X] / rho, upy = (D == 2) ? M[MO_Y] / rho : 0.0;
+  const double u2 = upx * upx + upy * upy;
+  const double ux = (double)shx + upx, uy = (D == 2) ? (double)shy + upy : 0.0;
+  const double Tm = (M[MO_E] - rho * u2) / ((3.0 + g.K) * rho * g.R);
+  // q = 1/2 [J - 2 u'.G - u' E' + 2 rho |u'|^2 u']  in the shifted frame
+  double qx = 0.5 * (M[MO_JX] - 2.0 * (upx * M[MO_GXX] + upy * M[MO_GXY]) - upx * M[MO_E] + 2.0 * rho * u2 * upx);
+  double qy = (D == 2) ? 0.5 * (M[MO_JY] - 2.0 * (upx * M[MO_GXY] + upy * M[MO_GYY]) - upy * M[MO_E] + 2.0 * rho * u2 * upy) : 0.0;
+  const double p = rho * g.R * Tm;
+  const double mu = g.mu_ref * pow(Tm / g.T_ref, g.omega);
+  const double tau = mu / p;
+  const double hdt = a.is_face ? 0.5 * k.dt : k.dt;    // dt at cells, s at faces
+  const double qf = 2.0 * tau / (2.0 * tau + hdt * g.Pr);
+  qx *= qf;
+  qy *= qf;
+  const bool state_ok = isfinite(rho) && isfinite(Tm) && isfinite(ux) && isfinite(uy) && rho > 0.0 && Tm > 0.0;
+  bool ok = true;
+  if (state_ok) {
+    ok = point_model<T, D>(a, rho, ux, uy, Tm, qx, qy, mp);
+  } else {
+    mp.ux = mp.uy = mp.lnh = mp.inv2RT = mp.kqx = mp.kqy = mp.RT = T(0);
+    mp.b0 = mp.b1 = mp.b2 = mp.b3 = T(0);
+  }
+  const double s = 0.5 * k.dt;
+  if (!a.is_face) {
+    mp.c1 = T(3.0 * s / (2.0 * tau + k.dt));
+    mp.c2 = T(4.0 * s / (2.0 * tau + k.dt));
+  } else {
+    mp.c1 = T(2.0 * tau / (2.0 * tau + s));
+    mp.c2 = T(s / (2.0 * tau + s));
+  }
+  store_mp<T>(po, a.npt, i, mp, T(kind));
+  po[P_SHX * (long)a.npt + i] = shx;
+  po[P_SHY * (long)a.npt + i] = shy;
+  if (a.W) {
+    a.W[0 * nc + i] = rho;
+    a.W[1 * nc + i] = ux;
+    a.W[2 * nc + i] = uy;
+    a.W[3 * nc + i] = Tm;
+    a.W[4 * nc + i] = qx;
+    a.W[5 * nc + i] = qy;
+    a.W[6 * nc + i] = rho * (0.5 * (ux * ux + uy * uy) + 0.5 * (3.0 + g.K) * g.R * Tm);
+    a.W[7 * nc + i] = tau;
+  }
+  if (!ok) atomicOr(a.err, ERR_SINGULAR);
+  if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.err, ERR_NONFINITE);
+  else if (!(rho > 0.0) || !(Tm > 0.0)) atomicOr(a.err, ERR_POSITIVITY);
 }
 
 // Initial parameters from (rho, u, v, T) with q = 0 (phi~ = phi^eq at t = 0).
 template <class T, int D>
 __global__ void k_init_params(const PointArgs a, const double* W0 /* [ncell][4] */) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.npt) return;
   T* po = reinterpret_cast<T*>(a.prm_out);
-  for (int i = warp; i < a.npt; i += nwarps) {
-    const double rho = W0[4 * i], ux = W0[4 * i + 1], uy = (D == 2) ? W0[4 * i + 2] : 0.0, Tm = W0[4 * i + 3];
-    MP<T> mp;
-    bool ok = point_model<T, D>(a, rho, ux, uy, Tm, 0.0, 0.0, mp);
-    mp.c1 = T(1); mp.c2 = T(0);
-    if (lane == 0) {
-      store_mp<T>(po, a.npt, i, mp, T(0));
-      if (!ok) atomicOr(a.err, ERR_SINGULAR);
-    }
-  }
+  const double rho = W0[4 * i], ux = W0[4 * i + 1], uy = (D == 2) ? W0[4 * i + 2] : 0.0, Tm = W0[4 * i + 3];
+  MP<T> mp;
+  bool ok = point_model<T, D>(a, rho, ux, uy, Tm, 0.0, 0.0, mp);
+  mp.c1 = T(0); mp.c2 = T(0);
+  store_mp<T>(po, a.npt, i, mp, T(0));
+  po[P_SHX * (long)a.npt + i] = mp.ux;
+  po[P_SHY * (long)a.npt + i] = mp.uy;
+  if (!ok) atomicOr(a.err, ERR_SINGULAR);
 }
 
-// phi~ = corrected Maxwellian of the initial parameters, and the chunk partial moments.
+// phi~ = corrected Maxwellian of the initial parameters.
 template <class S, class T, int D>
 __global__ void k_init_f(StepConst k, const T* __restrict__ prm, const T* __restrict__ vt,
                          S* __restrict__ f) {
@@ -316,7 +404,7 @@ __global__ void k_init_f(StepConst k, const T* __restrict__ prm, const T* __rest
   const T c0 = T(k.c0), twoK = T(k.twoK);
   for (int v = blockIdx.y; v < k.nv; v += gridDim.y) {
     T g, h;
-    model_eval<T, D>(m, vt[v], (D == 2) ? vt[k.nv + v] : T(0), vt[3 * k.nv + v], c0, twoK, g, h);
+    model_eval<T, D>(m, vt[v], (D == 2) ? vt[k.nv + v] : T(0), c0, twoK, g, h);
     stf<S, T>(f + (long)v * nc + c, g);
     stf<S, T>(f + ((long)k.nv + v) * nc + c, h);
   }
@@ -339,9 +427,9 @@ __global__ void k_moments(StepConst k, const T* __restrict__ prm, const T* __res
   for (int v = v0; v < v1; ++v) {
     const T gq = ldf<S, T>(f + (long)v * nc + c), hq = ldf<S, T>(f + (nv + v) * nc + c);
     const T xp = vt[v] - ux, yp = (D == 2) ? vt[nv + v] - uy : T(0);
-    const T wv = vt[2 * nv + v];
-    const T wg = wv * gq;
-    const T e = wv * ((xp * xp + yp * yp) * gq + hq);
+    const T wxv = vt[2 * nv + v], wyv = vt[3 * nv + v];
+    const T wg = wxv * (wyv * gq);
+    const T e = wxv * (wyv * ((xp * xp + yp * yp) * gq + hq));
     a0.add(wg); ax.add(wg * xp); ae.add(e);
     gxx += wg * xp * xp; jx += e * xp;
     if (D == 2) { ay.add(wg * yp); gxy += wg * xp * yp; gyy += wg * yp * yp; jy += e * yp; }

@@ -61,6 +61,8 @@ struct LevelInst {
 struct LevelData {
   VSpace vs;
   DevBuf vt;        // [4][nv] compute type
+  DevBuf ax;        // [2][nax] one axis of a tensor-product space (compute type)
+  int uniform_L = -1;
   StepConst k;
   std::vector<LevelInst> inst;
 };
@@ -143,6 +145,7 @@ template <class S, class T, int D> struct Runner {
     a.npt = face ? L.k.nface : L.k.ncell;
     a.part = face ? I.fpart.as<double>() : I.cpart.as<double>();
     a.vt = L.vt.p;
+    a.ax = L.ax.p;
     a.compat = face ? h->cfg.compat_face : h->cfg.compat_cell;
     for (int s = 0; s < 4; ++s)
       for (int j = 0; j < 3; ++j) a.wall[s][j] = h->cfg.wall[s][j];
@@ -153,16 +156,15 @@ template <class S, class T, int D> struct Runner {
     return a;
   }
 
-  static int fin_grid(int npt) {
-    int blocks = (npt + 7) / 8;
-    return std::max(1, std::min(blocks, 148 * 32));
-  }
+  // finalisation: one thread per point
+  static constexpr int FIN_BLOCK = 64;
+  static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
 
   static cudaError_t init(mlvs_handle* h, LevelData& L, LevelInst& I, const double* dW0) {
     PointArgs a = pargs(h, L, I, false);
     a.compat = h->cfg.compat_cell;
     a.prm_out = I.prm[0].p;
-    k_init_params<T, D><<<fin_grid(L.k.ncell), 256, 0, h->stream>>>(a, dW0);
+    k_init_params<T, D><<<fin_grid(L.k.ncell), FIN_BLOCK, 0, h->stream>>>(a, dW0);
     dim3 g((L.k.ncell + 127) / 128, std::min(L.k.nv, 1024));
     k_init_f<S, T, D><<<g, 128, 0, h->stream>>>(L.k, I.prm[0].as<T>(), L.vt.as<T>(), I.f[0].as<S>());
     dim3 gm((L.k.ncell + 127) / 128, L.k.nchunk);
@@ -193,7 +195,7 @@ template <class S, class T, int D> struct Runner {
     a.prm_out = I.prm[I.pcur ^ 1].p;
     a.W = I.W.as<double>();
     mark_begin(h, 0);
-    k_finalize<T, D><<<fin_grid(a.npt), 256, 0, h->stream>>>(a);
+    k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
     mark_end(h);
     I.pcur ^= 1;
     I.fresh = true;
@@ -223,7 +225,7 @@ template <class S, class T, int D> struct Runner {
     a.cprm = I.prm[I.pcur].p;
     a.prm_out = I.fprm.p;
     mark_begin(h, 2);
-    k_finalize<T, D><<<fin_grid(a.npt), 256, 0, h->stream>>>(a);
+    k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
     mark_end(h);
     t.part = I.cpart.as<double>();
     mark_begin(h, 3);
@@ -410,15 +412,28 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
     for (int v = 0; v < k.nv; ++v) {
       vt[v] = L.vs.xix[v];
       vt[k.nv + v] = L.vs.xiy[v];
-      vt[2 * k.nv + v] = L.vs.w[v];
-      vt[3 * k.nv + v] = L.vs.xix[v] * L.vs.xix[v] + L.vs.xiy[v] * L.vs.xiy[v];
+      vt[2 * k.nv + v] = L.vs.wx[v];
+      vt[3 * k.nv + v] = L.vs.wy[v];
     }
-    if (L.vt.alloc(vt.size() * h->tsize) != cudaSuccess) return fail(h, MLVS_ERR_OOM, "velocity table");
+    // one axis of the tensor-product space (uniform levels): coordinates and weights
+    L.uniform_L = levels[l].uniform_L;
+    std::vector<double> axd;
+    {
+      auto gr = groups_1d(n_base, L.uniform_L);
+      k.nax = (int)gr.size();
+      axd.resize(2 * gr.size());
+      for (size_t g = 0; g < gr.size(); ++g) merged(b, gr[g].first, gr[g].second, axd[g], axd[gr.size() + g]);
+    }
+    if (L.vt.alloc(vt.size() * h->tsize) != cudaSuccess || L.ax.alloc(axd.size() * h->tsize) != cudaSuccess)
+      return fail(h, MLVS_ERR_OOM, "velocity table");
     if (h->tsize == 8) {
       CK(cudaMemcpy(L.vt.p, vt.data(), vt.size() * 8, cudaMemcpyHostToDevice));
+      CK(cudaMemcpy(L.ax.p, axd.data(), axd.size() * 8, cudaMemcpyHostToDevice));
     } else {
       std::vector<float> vf(vt.begin(), vt.end());
       CK(cudaMemcpy(L.vt.p, vf.data(), vf.size() * 4, cudaMemcpyHostToDevice));
+      std::vector<float> af(axd.begin(), axd.end());
+      CK(cudaMemcpy(L.ax.p, af.data(), af.size() * 4, cudaMemcpyHostToDevice));
     }
     if (l != 0) continue;  // distributions live on level 0 in this build
     L.inst.resize(h->cfg.n_instances);

@@ -4,7 +4,11 @@
 //   f      [comp in {g~, h~}][v][cell]        storage type S (double | float | bf16), cells row-major
 //   params [NP][point]                        compute type T, one point = a cell or a face
 //   part   [chunk][NMOM][point]               double, per-velocity-chunk partial moments
-//   vt     [4][v] = (xi_x, xi_y, w, |xi|^2)    compute type T (and a double copy)
+//   vt     [4][v] = (xi_x, xi_y, w_x, w_y)    compute type T; the weight is w = w_x w_y and
+//                                             every velocity sum forms w_x (w_y x), so the
+//                                             rounding of the weight product never repeats
+//                                             systematically over the velocities
+//   ax     [2][n_axis] = (X, W)                compute type T, 1-D axis of a tensor-product space
 #pragma once
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -13,12 +17,17 @@
 namespace mlvs {
 
 // Per-point parameters of the model distribution (Eq. g_h_eq_Pr with the compatibility
-// factor of Eq. gh_model_correction folded in) plus two blending coefficients:
-//   cells: C1 = (2 tau - s)/(2 tau + dt), C2 = 3 s/(2 tau + dt)  (phi-bar-plus from phi~, phi^S)
-//   faces: C1 = 2 tau/(2 tau + s),       C2 = s/(2 tau + s)      (Eq. recover_phi)
+// correction of Eq. gh_model_correction folded in) plus two blending coefficients:
+//   cells: C1 = b = 3 s/(2 tau + dt), C2 = 4 b / 3, with
+//          phi-bar-plus = phi~ + b (phi^S - phi~),  phi~+ = phi~ + (4/3) b (phi^S - phi~)
+//          (the derived conversions of Sec. 2.2 with their weights summing to one)
+//   faces: C1 = 2 tau/(2 tau + s), C2 = s/(2 tau + s):  phi = phi-bar + C2 (phi^S - phi-bar)
+//          (Eq. recover_phi)
 //   wall faces: C2 = rho_w multiplies the unit-density wall Maxwellian.
+// The correction factor is 1 + B0 + B1 c_x + B2 c_y + B3 |c|^2 with c = xi - u: the span of
+// the basis of Eq. eq_four_basis {1, xi_x, xi_y, E_xi} written in peculiar velocity.
 enum {
-  P_UX = 0, P_UY, P_LNN, P_INV2RT, P_KQX, P_KQY, P_RT, P_P0, P_A1, P_A2, P_P3, P_C1, P_C2,
+  P_UX = 0, P_UY, P_LNH, P_INV2RT, P_KQX, P_KQY, P_RT, P_B0, P_B1, P_B2, P_B3, P_C1, P_C2,
   P_KIND, P_SHX, P_SHY, NP
 };
 // face kinds
@@ -32,12 +41,20 @@ enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2 };
 
 template <class T> struct Num;
 template <> struct Num<float> {
-  static __device__ __forceinline__ float ex(float x) { return __expf(x); }
   static __device__ __forceinline__ float dv(float a, float b) { return __fdividef(a, b); }
+  // exp(l - c^2 k) with the operation order pinned (no contraction freedom), so every
+  // kernel that evaluates this factor gets the same bits for the same inputs.
+  static __device__ __forceinline__ float gauss(float c, float k, float l) {
+    return __expf(__fmaf_rn(__fmul_rn(c, c), -k, l));
+  }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
 };
 template <> struct Num<double> {
-  static __device__ __forceinline__ double ex(double x) { return exp(x); }
   static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double gauss(double c, double k, double l) {
+    return exp(__fma_rn(__dmul_rn(c, c), -k, l));
+  }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
 };
 
 template <class S, class T> __device__ __forceinline__ T ldf(const S* p);
@@ -61,38 +78,47 @@ template <> __device__ __forceinline__ float ldf_round<__nv_bfloat16, float>(flo
 
 // Model parameters of one point, held in registers.
 template <class T> struct MP {
-  T ux, uy, lnn, inv2RT, kqx, kqy, RT, p0, a1, a2, p3, c1, c2;
+  T ux, uy, lnh, inv2RT, kqx, kqy, RT, b0, b1, b2, b3, c1, c2;
   __device__ __forceinline__ void load(const T* __restrict__ P, long n, long i) {
-    ux = P[P_UX * n + i];     uy = P[P_UY * n + i];   lnn = P[P_LNN * n + i];
+    ux = P[P_UX * n + i];     uy = P[P_UY * n + i];   lnh = P[P_LNH * n + i];
     inv2RT = P[P_INV2RT * n + i]; kqx = P[P_KQX * n + i]; kqy = P[P_KQY * n + i];
-    RT = P[P_RT * n + i];     p0 = P[P_P0 * n + i];   a1 = P[P_A1 * n + i];
-    a2 = P[P_A2 * n + i];     p3 = P[P_P3 * n + i];   c1 = P[P_C1 * n + i];
+    RT = P[P_RT * n + i];     b0 = P[P_B0 * n + i];   b1 = P[P_B1 * n + i];
+    b2 = P[P_B2 * n + i];     b3 = P[P_B3 * n + i];   c1 = P[P_C1 * n + i];
     c2 = P[P_C2 * n + i];
   }
 };
 
-// Shakhov model distribution times the compatibility factor at velocity xi:
-//   g^eq = exp(lnn - |c|^2/(2RT)),  c = xi - u                          (Eq. g_h_eq_Pr)
-//   g^S  = g^eq [1 + kq.c (|c|^2/RT - D - 2)]
-//   h^S  = RT g^eq [c0 + kq.c ((|c|^2/RT - D) c0 - 2K)],  c0 = K + 3 - D, kq = (1-Pr) q/(5 p RT)
-//   factor = 1 + sum_m a_m phi_m(xi) = p0 + a1 xi_x + a2 xi_y + p3 |xi|^2   (Eq. eq_four_basis)
+// Maxwellian of a point as a product of one factor per axis (D = 2) or one factor (D = 1):
+//   g^eq = rho/(2 pi R T)^{D/2} exp(-|c|^2/(2RT)) = exp(lnh - c_x^2/(2RT)) exp(lnh - c_y^2/(2RT))
+// with lnh = ln(rho/(2 pi R T)^{D/2}) / D  (Eq. g_h_eq_Pr, first line).
 template <class T, int D>
-__device__ __forceinline__ void model_eval(const MP<T>& p, T xix, T xiy, T xi2, T c0, T twoK,
-                                           T& g, T& h) {
-  T cx = xix - p.ux;
-  T cy = (D == 2) ? (xiy - p.uy) : T(0);
-  T cc = cx * cx + cy * cy;
-  T geq = Num<T>::ex(p.lnn - cc * p.inv2RT);
-  T cq = p.kqx * cx + p.kqy * cy;
-  T t = T(2) * p.inv2RT * cc;
-  T gs = geq * (T(1) + cq * (t - T(D + 2)));
-  T hs = p.RT * geq * (c0 + cq * ((t - T(D)) * c0 - twoK));
-  T fac = p.p0 + p.a1 * xix + p.a2 * xiy + p.p3 * xi2;
-  g = gs * fac;
-  h = hs * fac;
+__device__ __forceinline__ T maxwell_sep(const MP<T>& p, T cx, T cy) {
+  const T ex = Num<T>::gauss(cx, p.inv2RT, p.lnh);
+  if (D == 1) return ex;
+  const T ey = Num<T>::gauss(cy, p.inv2RT, p.lnh);
+  return Num<T>::mul(ex, ey);
 }
 
-// Compensated (Kahan) accumulation for the conserved-moment sums in FP32; plain in FP64.
+// Shakhov model distribution times the compatibility factor at velocity xi:
+//   g^S = g^eq [1 + kq.c (|c|^2/RT - D - 2)]
+//   h^S = RT g^eq [c0 + kq.c ((|c|^2/RT - D) c0 - 2K)],  c0 = K + 3 - D, kq = (1-Pr) q/(5 p RT)
+//   (Eq. g_h_eq_Pr), then multiplied by 1 + B0 + B1 c_x + B2 c_y + B3 |c|^2.
+template <class T, int D>
+__device__ __forceinline__ void model_eval(const MP<T>& p, T xix, T xiy, T c0, T twoK, T& g, T& h) {
+  const T cx = xix - p.ux;
+  const T cy = (D == 2) ? (xiy - p.uy) : T(0);
+  const T geq = maxwell_sep<T, D>(p, cx, cy);
+  const T cc = cx * cx + cy * cy;
+  const T cq = p.kqx * cx + p.kqy * cy;
+  const T t = T(2) * p.inv2RT * cc;
+  const T gs = geq * (T(1) + cq * (t - T(D + 2)));
+  const T hs = p.RT * geq * (c0 + cq * ((t - T(D)) * c0 - twoK));
+  const T corr = p.b0 + p.b1 * cx + p.b2 * cy + p.b3 * cc;
+  g = gs + gs * corr;
+  h = hs + hs * corr;
+}
+
+// Compensated (Kahan) accumulation for sums that must keep FP64-level accuracy in FP32.
 template <class T> struct KSum {
   T s, c;
   __device__ __forceinline__ void zero() { s = T(0); c = T(0); }
@@ -117,6 +143,7 @@ struct StepConst {
   int px, py;          // periodic flags
   int bc[4];
   int nv, vpc, nchunk;  // velocities, velocities per chunk, chunks
+  int nax;             // > 0: the space is the tensor product of one axis of nax points
   double dx, dy, dt;
   double c0, twoK;      // K + 3 - D, 2K
 };

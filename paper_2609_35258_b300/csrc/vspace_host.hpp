@@ -69,6 +69,7 @@ inline std::vector<std::pair<int, int>> groups_1d(int n, int L) {
 struct VSpace {
   int D = 2;
   std::vector<double> xix, xiy, w;
+  std::vector<double> wx, wy;  // w = wx * wy: every merged cell is a product of axis ranges
   std::vector<int> rect;  // 4 per point: x0, x1, y0, y1 (D = 1: y0 = 0, y1 = 1)
   int nv() const { return (int)w.size(); }
 };
@@ -91,6 +92,7 @@ inline VSpace uniform_vspace(const Base1D& b, int D, int L) {
   if (D == 1) {
     for (size_t g = 0; g < gr.size(); ++g) {
       s.xix.push_back(X[g]); s.xiy.push_back(0.0); s.w.push_back(W[g]);
+      s.wx.push_back(W[g]); s.wy.push_back(1.0);
       s.rect.insert(s.rect.end(), {gr[g].first, gr[g].second, 0, 1});
     }
     return s;
@@ -98,6 +100,7 @@ inline VSpace uniform_vspace(const Base1D& b, int D, int L) {
   for (size_t gy = 0; gy < gr.size(); ++gy)
     for (size_t gx = 0; gx < gr.size(); ++gx) {
       s.xix.push_back(X[gx]); s.xiy.push_back(X[gy]); s.w.push_back(W[gx] * W[gy]);
+      s.wx.push_back(W[gx]); s.wy.push_back(W[gy]);
       s.rect.insert(s.rect.end(), {gr[gx].first, gr[gx].second, gr[gy].first, gr[gy].second});
     }
   return s;
