@@ -1,17 +1,18 @@
 // Tile kernels of one DUGKS step on a structured Cartesian mesh (Sec. 2.2).
 //
-// A CTA owns a TX x TY tile of cells and a contiguous chunk of velocities.  For each
-// velocity it stages phi-bar-plus of the tile and a two-cell halo in shared memory
-// (Sec. 2.2, derived conversion phi-bar-plus = C1 phi~ + C2 phi^S), limited slopes
-// (Eq. reconstruction), and the face phi-bar of every face of the tile by the
-// characteristic (Eq. bar_phi_transport).  MODE 0 accumulates the face moments over the
-// chunk (input of Eq. W_from_bar); MODE 1 recovers the face phi (Eq. recover_phi), applies
-// Eq. explicit_update to the tile's cells, stores phi~^{n+1} and accumulates the cell moments
-// of the new phi~ (input of Eq. discrete_W / discrete_q of the next step).
-//
-// Velocity is uniform across the CTA inside the loop, so the upwind choice by sign(xi.n)
-// is a uniform branch.  Halo sources are wrapped (periodic sides) or clamped (ghost copies
-// of the boundary cell on the other sides).
+// A CTA owns a TX x TY tile of cells and a contiguous chunk of velocities, processed VB
+// velocities per barrier round.  Per round it stages in shared memory
+//   phase 1  phi-bar-plus of the tile and its two-cell halo (the derived conversion
+//            phi-bar-plus = phi~ + b (phi^S - phi~) of Sec. 2.2);
+//   phase 2  limited slopes (Eq. reconstruction) of the cells that can be upwind of a face;
+//   phase 3  the face phi-bar of the upwind side by the characteristic
+//            (Eq. bar_phi_transport).  MODE 0 accumulates the face moments over the chunk
+//            (input of Eq. W_from_bar).  MODE 1 recovers the face phi (Eq. recover_phi);
+//   phase 4  (MODE 1) Eq. explicit_update of the tile's cells, the store of phi~^{n+1} and
+//            the cell moments of the stored values (input of Eq. discrete_W / discrete_q).
+// Velocity is uniform across the CTA inside a round, so the upwind choice by sign(xi.n) is
+// a uniform branch.  Halo sources are wrapped (periodic sides) or clamped (ghost copies of
+// the boundary cell on the other sides).
 #pragma once
 #include "mlvs_common.cuh"
 
@@ -39,6 +40,7 @@ template <int TX, int TY, int D> struct TileGeom {
   static constexpr int NSL = SW * SH;
   static constexpr int NFXL = (TX + 1) * TY;
   static constexpr int NFYL = (D == 2) ? TX * (TY + 1) : 0;
+  static constexpr int NF = NFXL + NFYL;
   // ext index of tile-local cell (x, y), x in [-2, TX+1], y in [-2, TY+1]
   static __device__ __forceinline__ int eidx(int x, int y) {
     return (D == 2) ? (y + 2) * EW + (x + 2) : (x + 2);
@@ -50,8 +52,7 @@ template <int TX, int TY, int D> struct TileGeom {
   // k-th halo position of the extended tile
   static __device__ __forceinline__ void halo_pos(int k, int& x, int& y) {
     if (D == 1) {
-      const int cols[4] = {-2, -1, TX, TX + 1};
-      x = cols[k];
+      x = (k < 2) ? k - 2 : TX + (k - 2);
       y = 0;
       return;
     }
@@ -61,8 +62,25 @@ template <int TX, int TY, int D> struct TileGeom {
     k -= 2 * EW;
     y = k / 4;
     const int c = k % 4;
-    x = (c == 0) ? -2 : (c == 1) ? -1 : (c == 2) ? TX : TX + 1;
+    x = (c < 2) ? c - 2 : TX + (c - 2);
   }
+  // tile-local coordinates of face f: x-faces first, then y-faces
+  static __device__ __forceinline__ void face_pos(int f, int& dir, int& li, int& lj) {
+    if (f < NFXL) { dir = 0; li = f % (TX + 1); lj = f / (TX + 1); }
+    else { f -= NFXL; dir = 1; li = f % TX; lj = f / TX; }
+  }
+};
+
+// Shared-memory layout of a tile kernel (bytes), identical on host and device.
+template <class T, int TX, int TY, int D, int VB, int MODE> struct TileSmem {
+  using G = TileGeom<TX, TY, D>;
+  static constexpr size_t P = 0;                                           // T [VB][2][NEXT]
+  static constexpr size_t SL = P + sizeof(T) * VB * 2 * G::NEXT;            // T [VB][4][NSL]
+  static constexpr size_t F = SL + sizeof(T) * VB * 4 * G::NSL;             // T [VB][2][NF]   (MODE 1)
+  static constexpr size_t FP = F + (MODE == 1 ? sizeof(T) * VB * 2 * G::NF : 0);  // T [16][NF] (MODE 1)
+  static constexpr size_t ACC = FP + (MODE == 1 ? sizeof(T) * 16 * G::NF : 0);     // T [16][NF] (MODE 0)
+  static constexpr size_t META = ACC + (MODE == 0 ? sizeof(T) * 16 * G::NF : 0);   // int [2][NF]
+  static constexpr size_t BYTES = META + sizeof(int) * 2 * G::NF;
 };
 
 __device__ __forceinline__ int wrap_or_clamp(int g, int n, int periodic) {
@@ -71,38 +89,89 @@ __device__ __forceinline__ int wrap_or_clamp(int g, int n, int periodic) {
 }
 
 // van Leer limited slope (reading of Eq. reconstruction): 2ab/(a+b)/h for a, b of equal
-// strict sign, else 0.  limiter == 1: central difference (a+b)/(2h).
+// strict sign (ab > 0; an underflowing product counts as 0), else 0.  limiter == 1: central difference (a+b)/(2h).
 template <class T>
 __device__ __forceinline__ T limited(T a, T b, T inv_h, int limiter) {
-  if (limiter) return T(0.5) * (a + b) * inv_h;
-  const bool same = (a > T(0) && b > T(0)) || (a < T(0) && b < T(0));
-  return same ? Num<T>::dv(T(2) * a * b, a + b) * inv_h : T(0);
+  using N = Num<T>;
+  if (limiter) return N::mul(N::mul(T(0.5), N::add(a, b)), inv_h);
+  const T ab = N::mul(a, b);
+  return (ab > T(0)) ? N::mul(N::dv(N::mul(T(2), ab), N::add(a, b)), inv_h) : T(0);
 }
 
-// Face descriptor held per thread.
-struct FaceRef {
-  int dir;     // 0: x-face, 1: y-face, -1: none
-  int li, lj;  // tile-local face coordinates
-  int fid;     // global face index (param / partial row), -1: invalid
-  int owned;   // MODE 0: accumulate into partials
-  int kind;    // FK_*
-};
+// face metadata word: bit 0 valid, bit 1 owned (MODE 0 accumulates), bits 2-3 kind
+enum { FM_VALID = 1, FM_OWNED = 2 };
 
-template <class S, class T, int D, int TX, int TY, int MODE>
+// Face accumulators: Kahan pairs (s, c) for M0, MX, MY, E in slots 0..7, plain sums of
+// Gxx, Gxy, Gyy, Jx, Jy in slots 8..12.
+template <class T>
+__device__ __forceinline__ void fold_partials(T (&acc)[13], const T (&part)[9]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const T sum = acc[2 * p], cmp = acc[2 * p + 1];
+    const T y = part[p] - cmp;
+    const T t = sum + y;
+    acc[2 * p + 1] = (t - sum) - y;
+    acc[2 * p] = t;
+  }
+#pragma unroll
+  for (int p = 4; p < 9; ++p) acc[4 + p] += part[p];
+}
+template <class T>
+__device__ __forceinline__ void fold_partials_smem(T* acc, int st, const T (&part)[9]) {
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    const T sum = acc[2 * p * st], cmp = acc[(2 * p + 1) * st];
+    const T y = part[p] - cmp;
+    const T t = sum + y;
+    acc[(2 * p + 1) * st] = (t - sum) - y;
+    acc[2 * p * st] = t;
+  }
+#pragma unroll
+  for (int p = 4; p < 9; ++p) acc[(4 + p) * st] += part[p];
+}
+template <class T, int D>
+__device__ __forceinline__ void write_partials(const T (&acc)[13], double* P, long st) {
+  P[MO_0 * st] = (double)acc[0] - (double)acc[1];
+  P[MO_X * st] = (double)acc[2] - (double)acc[3];
+  P[MO_Y * st] = (D == 2) ? (double)acc[4] - (double)acc[5] : 0.0;
+  P[MO_E * st] = (double)acc[6] - (double)acc[7];
+  P[MO_GXX * st] = (double)acc[8];
+  P[MO_GXY * st] = (double)acc[9];
+  P[MO_GYY * st] = (double)acc[10];
+  P[MO_JX * st] = (double)acc[11];
+  P[MO_JY * st] = (double)acc[12];
+}
+template <class T, int D>
+__device__ __forceinline__ void write_partials_smem(const T* acc, int sa, double* P, long st) {
+  P[MO_0 * st] = (double)acc[0] - (double)acc[sa];
+  P[MO_X * st] = (double)acc[2 * sa] - (double)acc[3 * sa];
+  P[MO_Y * st] = (D == 2) ? (double)acc[4 * sa] - (double)acc[5 * sa] : 0.0;
+  P[MO_E * st] = (double)acc[6 * sa] - (double)acc[7 * sa];
+  P[MO_GXX * st] = (double)acc[8 * sa];
+  P[MO_GXY * st] = (double)acc[9 * sa];
+  P[MO_GYY * st] = (double)acc[10 * sa];
+  P[MO_JX * st] = (double)acc[11 * sa];
+  P[MO_JY * st] = (double)acc[12 * sa];
+}
+
+template <class S, class T, int D, int TX, int TY, int VB, int MODE>
 __global__ void __launch_bounds__(TX * TY)
 k_tile(const TileArgs a, int limiter) {
   using G = TileGeom<TX, TY, D>;
+  using L = TileSmem<T, TX, TY, D, VB, MODE>;
+  using N = Num<T>;
   static_assert(G::NHALO <= G::NT, "halo larger than the thread count");
   static_assert(G::NSL <= 2 * G::NT, "slope rectangle larger than two per thread");
-  static_assert(TY + ((D == 2) ? TX : 0) <= G::NT, "edge faces larger than the thread count");
-  const StepConst& k = a.k;
-  __shared__ T sPg[2][G::NEXT];
-  __shared__ T sPh[2][G::NEXT];
-  __shared__ T sSxg[G::NSL], sSxh[G::NSL];
-  __shared__ T sSyg[(D == 2) ? G::NSL : 1], sSyh[(D == 2) ? G::NSL : 1];
-  __shared__ T sFxg[(MODE == 1) ? G::NFXL : 1], sFxh[(MODE == 1) ? G::NFXL : 1];
-  __shared__ T sFyg[(MODE == 1 && D == 2) ? G::NFYL : 1], sFyh[(MODE == 1 && D == 2) ? G::NFYL : 1];
+  static_assert(G::NF <= 3 * G::NT, "faces larger than three per thread");
+  extern __shared__ __align__(16) unsigned char smem[];
+  T* sP = reinterpret_cast<T*>(smem + L::P);
+  T* sS = reinterpret_cast<T*>(smem + L::SL);
+  T* sF = reinterpret_cast<T*>(smem + L::F);
+  T* sFP = reinterpret_cast<T*>(smem + L::FP);
+  T* sAcc = reinterpret_cast<T*>(smem + L::ACC);
+  int* sMeta = reinterpret_cast<int*>(smem + L::META);
 
+  const StepConst& k = a.k;
   const S* __restrict__ fin = reinterpret_cast<const S*>(a.f_in);
   const T* __restrict__ cp = reinterpret_cast<const T*>(a.cparam);
   const T* __restrict__ fp = reinterpret_cast<const T*>(a.fparam);
@@ -118,9 +187,9 @@ k_tile(const TileArgs a, int limiter) {
   const int v0 = chunk * k.vpc;
   const int v1 = min(k.nv, v0 + k.vpc);
 
-  // ---- extended positions handled by this thread: own cell + at most one halo cell
-  const int ex0 = tx, ey0 = (D == 2) ? ty : 0;
-  const int src0 = wrap_or_clamp(y0 + ey0, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + ex0, k.nx, k.px);
+  // ---- extended positions: own cell + at most one halo cell
+  const int ey0 = (D == 2) ? ty : 0;
+  const int src0 = wrap_or_clamp(y0 + ey0, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + tx, k.nx, k.px);
   const bool own_active = (x0 + tx < k.nx) && (D == 1 || y0 + ty < k.ny);
   const int own_cell = own_active ? (y0 + ty) * k.nx + (x0 + tx) : -1;
   int ex1 = 0, ey1 = 0, src1 = -1;
@@ -131,88 +200,67 @@ k_tile(const TileArgs a, int limiter) {
   MP<T> m0, m1;
   m0.load(cp, nc, src0);
   if (src1 >= 0) m1.load(cp, nc, src1);
-  const int e0 = G::eidx(ex0, ey0);
+  const int e0 = G::eidx(tx, ey0);
   const int e1 = (src1 >= 0) ? G::eidx(ex1, ey1) : 0;
 
-  // ---- slope positions: (TX+2) x (TY+2) rectangle from (-1,-1)
-  int sl_n = 0;
-  int sl_e[2], sl_s[2];
-  for (int q = tid; q < G::NSL; q += G::NT) {
-    const int sx = q % G::SW - 1, sy = (D == 2) ? q / G::SW - 1 : 0;
-    sl_e[sl_n] = G::eidx(sx, sy);
-    sl_s[sl_n] = q;
-    ++sl_n;
-  }
-
-  // ---- faces handled by this thread
-  FaceRef fr[3];
-  int nfr = 0;
-  {
-    auto xface = [&](int li, int lj) {
-      FaceRef r;
-      r.dir = 0; r.li = li; r.lj = lj;
-      const int gi = x0 + li, gj = y0 + lj;
-      const bool valid = (gi <= k.nx) && (D == 1 || gj < k.ny);
-      r.fid = -1; r.owned = 0; r.kind = FK_INTERIOR;
-      if (valid) {
+  // ---- face metadata (and MODE 1 parameters, MODE 0 shifts/accumulators) in shared memory
+  for (int f = tid; f < G::NF; f += G::NT) {
+    int dir, li, lj;
+    G::face_pos(f, dir, li, lj);
+    const int gi = x0 + li, gj = y0 + lj;
+    int meta = 0, fid = -1;
+    if (dir == 0) {
+      if (gi <= k.nx && (D == 1 || gj < k.ny)) {
         const int pi = (k.px && gi == k.nx) ? 0 : gi;
-        r.fid = ((D == 2) ? gj : 0) * k.nfx + pi;
-        r.owned = (gi < k.nx) ? (li < TX) : !k.px;
-        if (!k.px && gi == 0 && k.bc[0] == BC_WALL) r.kind = FK_WALL_LO;
-        if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) r.kind = FK_WALL_HI;
+        fid = ((D == 2) ? gj : 0) * k.nfx + pi;
+        meta = FM_VALID;
+        if ((gi < k.nx) ? (li < TX) : !k.px) meta |= FM_OWNED;
+        if (!k.px && gi == 0 && k.bc[0] == BC_WALL) meta |= FK_WALL_LO << 2;
+        if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) meta |= FK_WALL_HI << 2;
       }
-      return r;
-    };
-    auto yface = [&](int li, int lj) {
-      FaceRef r;
-      r.dir = 1; r.li = li; r.lj = lj;
-      const int gi = x0 + li, gj = y0 + lj;
-      const bool valid = (gi < k.nx) && (gj <= k.ny);
-      r.fid = -1; r.owned = 0; r.kind = FK_INTERIOR;
-      if (valid) {
+    } else {
+      if (gi < k.nx && gj <= k.ny) {
         const int pj = (k.py && gj == k.ny) ? 0 : gj;
-        r.fid = k.nfx * k.ny + pj * k.nx + gi;
-        r.owned = (gj < k.ny) ? (lj < TY) : !k.py;
-        if (!k.py && gj == 0 && k.bc[2] == BC_WALL) r.kind = FK_WALL_LO;
-        if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) r.kind = FK_WALL_HI;
+        fid = k.nfx * k.ny + pj * k.nx + gi;
+        meta = FM_VALID;
+        if ((gj < k.ny) ? (lj < TY) : !k.py) meta |= FM_OWNED;
+        if (!k.py && gj == 0 && k.bc[2] == BC_WALL) meta |= FK_WALL_LO << 2;
+        if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) meta |= FK_WALL_HI << 2;
       }
-      return r;
-    };
-    fr[nfr++] = xface(tx, ty);
-    if (D == 2) fr[nfr++] = yface(tx, ty);
-    if (tid < TY) fr[nfr++] = xface(TX, tid);
-    else if (D == 2 && tid < TY + TX) fr[nfr++] = yface(tid - TY, TY);
-  }
-  // per-face data: shift (MODE 0) or model parameters (MODE 1)
-  T fsx[3], fsy[3];
-  MP<T> fm[3];
+    }
+    sMeta[f] = meta;
+    sMeta[G::NF + f] = fid;
+    if (MODE == 1 && fid >= 0) {
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    fsx[q] = T(0); fsy[q] = T(0);
-    if (q < nfr && fr[q].fid >= 0) {
-      if (MODE == 0) {
-        // shift = mean velocity of the two adjacent cells (sources as in the halo)
-        int li = fr[q].li, lj = fr[q].lj;
-        int xl = (fr[q].dir == 0) ? li - 1 : li, yl = (fr[q].dir == 0) ? lj : lj - 1;
-        int sL = wrap_or_clamp(y0 + yl, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + xl, k.nx, k.px);
-        int sR = wrap_or_clamp(y0 + lj, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + li, k.nx, k.px);
-        fsx[q] = T(0.5) * (cp[P_UX * nc + sL] + cp[P_UX * nc + sR]);
-        if (D == 2) fsy[q] = T(0.5) * (cp[P_UY * nc + sL] + cp[P_UY * nc + sR]);
-      } else {
-        fm[q].load(fp, k.nface, fr[q].fid);
+      for (int p = 0; p < 13; ++p) sFP[p * G::NF + f] = fp[(long)p * k.nface + fid];
+    }
+    if (MODE == 0) {
+      T shx = T(0), shy = T(0);
+      if (fid >= 0) {
+        const int xl = (dir == 0) ? li - 1 : li, yl = (dir == 0) ? lj : lj - 1;
+        const int sL = wrap_or_clamp(y0 + yl, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + xl, k.nx, k.px);
+        const int sR = wrap_or_clamp(y0 + lj, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + li, k.nx, k.px);
+        shx = T(0.5) * (cp[P_UX * nc + sL] + cp[P_UX * nc + sR]);
+        if (D == 2) shy = T(0.5) * (cp[P_UY * nc + sL] + cp[P_UY * nc + sR]);
       }
+#pragma unroll
+      for (int p = 0; p < 13; ++p) sAcc[p * G::NF + f] = T(0);
+      sAcc[13 * G::NF + f] = shx;   // slots 13, 14 hold the shift (never accumulated)
+      sAcc[14 * G::NF + f] = shy;
     }
   }
 
-  // ---- accumulators
-  KSum<T> acc0[3], accX[3], accY[3], accE[3];
-  T acc[3][5];
+  // MODE 0 accumulators of the thread's first two faces in registers:
+  // Kahan (s, c) for M0, MX, MY, E, plain for Gxx, Gxy, Gyy, Jx, Jy
+  T ra[2][13];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    acc0[q].zero(); accX[q].zero(); accY[q].zero(); accE[q].zero();
+  for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int r = 0; r < 5; ++r) acc[q][r] = T(0);
-  }
+    for (int p = 0; p < 13; ++p) ra[q][p] = T(0);
+  // MODE 1 accumulators of the own cell
+  KSum<T> c0k, cxk, cyk, cek;
+  c0k.zero(); cxk.zero(); cyk.zero(); cek.zero();
+  T cgxx = T(0), cgxy = T(0), cgyy = T(0), cjx = T(0), cjy = T(0);
 
   const T c0 = T(k.c0), twoK = T(k.twoK);
   const T s = T(0.5 * k.dt);
@@ -220,215 +268,277 @@ k_tile(const TileArgs a, int limiter) {
   const T idx_ = T(1.0 / k.dx), idy_ = T(1.0 / k.dy);
   const T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
   S* __restrict__ fout = reinterpret_cast<S*>(a.f_out);
-
-  // prefetch registers
-  T g0n = T(0), h0n = T(0), g1n = T(0), h1n = T(0);
-  if (v0 < v1) {
-    g0n = ldf<S, T>(fin + (long)v0 * nc + src0);
-    h0n = ldf<S, T>(fin + (nv + v0) * nc + src0);
-    if (src1 >= 0) {
-      g1n = ldf<S, T>(fin + (long)v0 * nc + src1);
-      h1n = ldf<S, T>(fin + (nv + v0) * nc + src1);
+  __syncthreads();
+  // shifts of the thread's register-held faces (MODE 0)
+  T fshx[2] = {T(0), T(0)}, fshy[2] = {T(0), T(0)};
+  if (MODE == 0) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int f = tid + q * G::NT;
+      if (f < G::NF) { fshx[q] = sAcc[13 * G::NF + f]; fshy[q] = sAcc[14 * G::NF + f]; }
     }
   }
 
-  int par = 0;
-  for (int v = v0; v < v1; ++v) {
-    const T xix = vt[v], xiy = (D == 2) ? vt[nv + v] : T(0), wxv = vt[2 * nv + v], wyv = vt[3 * nv + v];
-    const T g0 = g0n, h0 = h0n, g1 = g1n, h1 = h1n;
-    if (v + 1 < v1) {
-      g0n = ldf<S, T>(fin + (long)(v + 1) * nc + src0);
-      h0n = ldf<S, T>(fin + (nv + v + 1) * nc + src0);
+  // register prefetch of the first round
+  T ng0[VB], nh0[VB], ng1[VB], nh1[VB];
+#pragma unroll
+  for (int b = 0; b < VB; ++b) {
+    const int v = v0 + b;
+    ng0[b] = nh0[b] = ng1[b] = nh1[b] = T(0);
+    if (v < v1) {
+      ng0[b] = ldf<S, T>(fin + (long)v * nc + src0);
+      nh0[b] = ldf<S, T>(fin + (nv + v) * nc + src0);
       if (src1 >= 0) {
-        g1n = ldf<S, T>(fin + (long)(v + 1) * nc + src1);
-        h1n = ldf<S, T>(fin + (nv + v + 1) * nc + src1);
+        ng1[b] = ldf<S, T>(fin + (long)v * nc + src1);
+        nh1[b] = ldf<S, T>(fin + (nv + v) * nc + src1);
       }
     }
-    // ---- phase 1: phi-bar-plus on the extended tile
-    // Written as phi~ + b (phi^S - phi~) so that the two blending weights sum to one exactly
-    // whatever their rounding: the collision then conserves the moments of phi~.
-    T dg0, dh0;
-    {
+  }
+
+  for (int vb0 = v0; vb0 < v1; vb0 += VB) {
+    T g0[VB], h0[VB], dg0[VB], dh0[VB];
+    T xixb[VB], xiyb[VB], wxb[VB], wyb[VB];
+    // ---- phase 1: phi-bar-plus on the extended tile, and the prefetch of the next round
+#pragma unroll
+    for (int b = 0; b < VB; ++b) {
+      const int v = vb0 + b;
+      const bool on = v < v1;
+      const int vv = on ? v : v0;
+      xixb[b] = vt[vv];
+      xiyb[b] = (D == 2) ? vt[nv + vv] : T(0);
+      wxb[b] = vt[2 * nv + vv];
+      wyb[b] = vt[3 * nv + vv];
+      g0[b] = ng0[b]; h0[b] = nh0[b];
+      const T g1 = ng1[b], h1 = nh1[b];
+      const int vn = v + VB;
+      if (vn < v1) {
+        ng0[b] = ldf<S, T>(fin + (long)vn * nc + src0);
+        nh0[b] = ldf<S, T>(fin + (nv + vn) * nc + src0);
+        if (src1 >= 0) {
+          ng1[b] = ldf<S, T>(fin + (long)vn * nc + src1);
+          nh1[b] = ldf<S, T>(fin + (nv + vn) * nc + src1);
+        }
+      }
+      T* Pg = sP + (b * 2 + 0) * G::NEXT;
+      T* Ph = sP + (b * 2 + 1) * G::NEXT;
       T gs, hs;
-      model_eval<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
-      dg0 = gs - g0;
-      dh0 = hs - h0;
-      sPg[par][e0] = g0 + m0.c1 * dg0;
-      sPh[par][e0] = h0 + m0.c1 * dh0;
+      model_eval<T, D>(m0, xixb[b], xiyb[b], c0, twoK, gs, hs);
+      dg0[b] = N::sub(gs, g0[b]);
+      dh0[b] = N::sub(hs, h0[b]);
+      Pg[e0] = N::fma(m0.c1, dg0[b], g0[b]);
+      Ph[e0] = N::fma(m0.c1, dh0[b], h0[b]);
       if (src1 >= 0) {
-        model_eval<T, D>(m1, xix, xiy, c0, twoK, gs, hs);
-        sPg[par][e1] = g1 + m1.c1 * (gs - g1);
-        sPh[par][e1] = h1 + m1.c1 * (hs - h1);
+        model_eval<T, D>(m1, xixb[b], xiyb[b], c0, twoK, gs, hs);
+        Pg[e1] = N::fma(m1.c1, N::sub(gs, g1), g1);
+        Ph[e1] = N::fma(m1.c1, N::sub(hs, h1), h1);
       }
     }
     __syncthreads();
     // ---- phase 2: limited slopes
-    for (int q = 0; q < sl_n; ++q) {
-      const int e = sl_e[q], si = sl_s[q];
-      const T* Pg = sPg[par];
-      const T* Ph = sPh[par];
-      sSxg[si] = limited(Pg[e + 1] - Pg[e], Pg[e] - Pg[e - 1], idx_, limiter);
-      sSxh[si] = limited(Ph[e + 1] - Ph[e], Ph[e] - Ph[e - 1], idx_, limiter);
-      if (D == 2) {
-        sSyg[si] = limited(Pg[e + G::EW] - Pg[e], Pg[e] - Pg[e - G::EW], idy_, limiter);
-        sSyh[si] = limited(Ph[e + G::EW] - Ph[e], Ph[e] - Ph[e - G::EW], idy_, limiter);
+    for (int q = tid; q < G::NSL; q += G::NT) {
+      const int sx = q % G::SW - 1, sy = (D == 2) ? q / G::SW - 1 : 0;
+      const int e = G::eidx(sx, sy);
+#pragma unroll
+      for (int b = 0; b < VB; ++b) {
+        const T* Pg = sP + (b * 2 + 0) * G::NEXT;
+        const T* Ph = sP + (b * 2 + 1) * G::NEXT;
+        T* Sb = sS + b * 4 * G::NSL;
+        Sb[q] = limited(N::sub(Pg[e + 1], Pg[e]), N::sub(Pg[e], Pg[e - 1]), idx_, limiter);
+        Sb[G::NSL + q] = limited(N::sub(Ph[e + 1], Ph[e]), N::sub(Ph[e], Ph[e - 1]), idx_, limiter);
+        if (D == 2) {
+          Sb[2 * G::NSL + q] = limited(N::sub(Pg[e + G::EW], Pg[e]), N::sub(Pg[e], Pg[e - G::EW]), idy_, limiter);
+          Sb[3 * G::NSL + q] = limited(N::sub(Ph[e + G::EW], Ph[e]), N::sub(Ph[e], Ph[e - G::EW]), idy_, limiter);
+        }
       }
     }
     __syncthreads();
     // ---- phase 3: faces
-    {
-      const T* Pg = sPg[par];
-      const T* Ph = sPh[par];
-      const T bx_ = -xix * s, by_ = -xiy * s;
 #pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q >= nfr || fr[q].fid < 0) continue;
-        const int li = fr[q].li, lj = fr[q].lj;
+    for (int q = 0; q < 3; ++q) {
+      const int f = tid + q * G::NT;
+      if (f >= G::NF) break;
+      const int meta = sMeta[f];
+      if (!(meta & FM_VALID)) continue;
+      if (MODE == 0 && !(meta & FM_OWNED)) continue;
+      const int kind = meta >> 2;
+      int dir, li, lj;
+      G::face_pos(f, dir, li, lj);
+      MP<T> fm;
+      if (MODE == 1) {
+        fm.load(sFP, G::NF, f);
+      }
+      T part[9];
+#pragma unroll
+      for (int p = 0; p < 9; ++p) part[p] = T(0);
+      T fsx = T(0), fsy = T(0);
+      if (MODE == 0) {
+        if (q < 2) { fsx = fshx[q < 2 ? q : 0]; fsy = fshy[q < 2 ? q : 0]; }
+        else { fsx = sAcc[13 * G::NF + f]; fsy = sAcc[14 * G::NF + f]; }
+      }
+#pragma unroll
+      for (int b = 0; b < VB; ++b) {
+        const int v = vb0 + b;
+        if (v >= v1) break;
+        const T* Pg = sP + (b * 2 + 0) * G::NEXT;
+        const T* Ph = sP + (b * 2 + 1) * G::NEXT;
+        const T* Sb = sS + b * 4 * G::NSL;
+        const T xix = xixb[b], xiy = xiyb[b];
+        const T bx_ = N::mul(-xix, s), by_ = N::mul(-xiy, s);
         T gb, hb, xn;
-        if (fr[q].dir == 0) {
+        // upwind side only (the mean of both sides when xi.n = 0)
+        if (dir == 0) {
           xn = xix;
-          // left cell (li-1, lj), right cell (li, lj)
-          const int eL = G::eidx(li - 1, lj), eR = G::eidx(li, lj);
-          const int sL = G::sidx(li - 1, lj), sR = G::sidx(li, lj);
-          T gL = Pg[eL] + (hdx + bx_) * sSxg[sL];
-          T hL = Ph[eL] + (hdx + bx_) * sSxh[sL];
-          T gR = Pg[eR] + (-hdx + bx_) * sSxg[sR];
-          T hR = Ph[eR] + (-hdx + bx_) * sSxh[sR];
-          if (D == 2) {
-            gL += by_ * sSyg[sL]; hL += by_ * sSyh[sL];
-            gR += by_ * sSyg[sR]; hR += by_ * sSyh[sR];
+          auto rec = [&](int cx, T off, T& gg, T& hh) {
+            const int e = G::eidx(cx, lj), si = G::sidx(cx, lj);
+            gg = N::fma(N::add(off, bx_), Sb[si], Pg[e]);
+            hh = N::fma(N::add(off, bx_), Sb[G::NSL + si], Ph[e]);
+            if (D == 2) {
+              gg = N::fma(by_, Sb[2 * G::NSL + si], gg);
+              hh = N::fma(by_, Sb[3 * G::NSL + si], hh);
+            }
+          };
+          if (xix > T(0)) rec(li - 1, hdx, gb, hb);
+          else if (xix < T(0)) rec(li, -hdx, gb, hb);
+          else {
+            T g2, h2;
+            rec(li - 1, hdx, gb, hb);
+            rec(li, -hdx, g2, h2);
+            gb = N::mul(T(0.5), N::add(gb, g2));
+            hb = N::mul(T(0.5), N::add(hb, h2));
           }
-          if (xix > T(0)) { gb = gL; hb = hL; }
-          else if (xix < T(0)) { gb = gR; hb = hR; }
-          else { gb = T(0.5) * (gL + gR); hb = T(0.5) * (hL + hR); }
         } else {
           xn = xiy;
-          const int eS = G::eidx(li, lj - 1), eN = G::eidx(li, lj);
-          const int sS = G::sidx(li, lj - 1), sN = G::sidx(li, lj);
-          T gS_ = Pg[eS] + bx_ * sSxg[sS] + (hdy + by_) * sSyg[sS];
-          T hS_ = Ph[eS] + bx_ * sSxh[sS] + (hdy + by_) * sSyh[sS];
-          T gN = Pg[eN] + bx_ * sSxg[sN] + (-hdy + by_) * sSyg[sN];
-          T hN = Ph[eN] + bx_ * sSxh[sN] + (-hdy + by_) * sSyh[sN];
-          if (xiy > T(0)) { gb = gS_; hb = hS_; }
-          else if (xiy < T(0)) { gb = gN; hb = hN; }
-          else { gb = T(0.5) * (gS_ + gN); hb = T(0.5) * (hS_ + hN); }
+          auto rec = [&](int cy, T off, T& gg, T& hh) {
+            const int e = G::eidx(li, cy), si = G::sidx(li, cy);
+            gg = N::fma(N::add(off, by_), Sb[2 * G::NSL + si], N::fma(bx_, Sb[si], Pg[e]));
+            hh = N::fma(N::add(off, by_), Sb[3 * G::NSL + si], N::fma(bx_, Sb[G::NSL + si], Ph[e]));
+          };
+          if (xiy > T(0)) rec(lj - 1, hdy, gb, hb);
+          else if (xiy < T(0)) rec(lj, -hdy, gb, hb);
+          else {
+            T g2, h2;
+            rec(lj - 1, hdy, gb, hb);
+            rec(lj, -hdy, g2, h2);
+            gb = N::mul(T(0.5), N::add(gb, g2));
+            hb = N::mul(T(0.5), N::add(hb, h2));
+          }
         }
         if (MODE == 0) {
-          if (!fr[q].owned) continue;
-          if (fr[q].kind == FK_INTERIOR) {
-            const T xp = xix - fsx[q], yp = (D == 2) ? xiy - fsy[q] : T(0);
+          const T wxv = wxb[b], wyv = wyb[b];
+          if (kind == FK_INTERIOR) {
+            const T xp = xix - fsx, yp = (D == 2) ? xiy - fsy : T(0);
             const T wg = wxv * (wyv * gb);
             const T e = wxv * (wyv * ((xp * xp + yp * yp) * gb + hb));
-            acc0[q].add(wg);
-            accX[q].add(wg * xp);
-            accE[q].add(e);
-            acc[q][0] += wg * xp * xp;
-            acc[q][3] += e * xp;
-            if (D == 2) {
-              accY[q].add(wg * yp);
-              acc[q][1] += wg * xp * yp;
-              acc[q][2] += wg * yp * yp;
-              acc[q][4] += e * yp;
-            }
+            part[0] += wg;
+            part[1] += wg * xp;
+            part[2] += wg * yp;
+            part[3] += e;
+            part[4] += wg * xp * xp;
+            part[5] += wg * xp * yp;
+            part[6] += wg * yp * yp;
+            part[7] += e * xp;
+            part[8] += e * yp;
           } else {
             // wall: outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) g-bar
-            const T xin = (fr[q].kind == FK_WALL_LO) ? xn : -xn;
-            if (xin <= T(0)) acc0[q].add(wxv * (wyv * (xin * gb)));
+            const T xin = (kind == FK_WALL_LO) ? xn : -xn;
+            if (xin <= T(0)) part[0] += wxv * (wyv * (xin * gb));
           }
         } else {
           T gf, hf;
-          if (fr[q].kind == FK_INTERIOR) {
+          if (kind == FK_INTERIOR) {
             T gs, hs;
-            model_eval<T, D>(fm[q], xix, xiy, c0, twoK, gs, hs);
-            gf = gb + fm[q].c2 * (gs - gb);     // Eq. recover_phi, weights summing to one
-            hf = hb + fm[q].c2 * (hs - hb);
+            model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
+            gf = gb + fm.c2 * (gs - gb);     // Eq. recover_phi, weights summing to one
+            hf = hb + fm.c2 * (hs - hb);
           } else {
-            const T xin = (fr[q].kind == FK_WALL_LO) ? xn : -xn;
+            const T xin = (kind == FK_WALL_LO) ? xn : -xn;
             if (xin > T(0)) {
               T gs, hs;
-              model_eval<T, D>(fm[q], xix, xiy, c0, twoK, gs, hs);
-              gf = fm[q].c2 * gs;
-              hf = fm[q].c2 * hs;
+              model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
+              gf = fm.c2 * gs + fm.c1 * gs;   // rho_w = hi + lo
+              hf = fm.c2 * hs + fm.c1 * hs;
             } else {
               gf = gb;
               hf = hb;
             }
           }
-          if (fr[q].dir == 0) {
-            sFxg[lj * (TX + 1) + li] = gf;
-            sFxh[lj * (TX + 1) + li] = hf;
-          } else {
-            sFyg[lj * TX + li] = gf;
-            sFyh[lj * TX + li] = hf;
+          sF[(b * 2 + 0) * G::NF + f] = gf;
+          sF[(b * 2 + 1) * G::NF + f] = hf;
+        }
+      }
+      if (MODE == 0) {
+        // fold the round's partial sums into the chunk accumulators (compensated for M0..E)
+        if (q < 2) fold_partials<T>(ra[q < 2 ? q : 0], part);
+        else fold_partials_smem<T>(sAcc + f, G::NF, part);
+      }
+    }
+    __syncthreads();
+    if (MODE == 1) {
+      // ---- phase 4: update of the tile's cells (Eq. explicit_update)
+      if (own_active) {
+        const int wI = (D == 2) ? ty * (TX + 1) + tx : tx;
+        const int sI = G::NFXL + ty * TX + tx;
+#pragma unroll
+        for (int b = 0; b < VB; ++b) {
+          const int v = vb0 + b;
+          if (v >= v1) break;
+          const T* Fg = sF + (b * 2 + 0) * G::NF;
+          const T* Fh = sF + (b * 2 + 1) * G::NF;
+          const T xix = xixb[b], xiy = xiyb[b];
+          // phi~+ = phi~ + (4/3) b (phi^S - phi~), then the flux divergence
+          T gn = g0[b] + m0.c2 * dg0[b] - lamx * xix * (Fg[wI + 1] - Fg[wI]);
+          T hn = h0[b] + m0.c2 * dh0[b] - lamx * xix * (Fh[wI + 1] - Fh[wI]);
+          if (D == 2) {
+            gn -= lamy * xiy * (Fg[sI + TX] - Fg[sI]);
+            hn -= lamy * xiy * (Fh[sI + TX] - Fh[sI]);
+          }
+          stf<S, T>(fout + (long)v * nc + own_cell, gn);
+          stf<S, T>(fout + (nv + v) * nc + own_cell, hn);
+          const T gq = ldf_round<S, T>(gn), hq = ldf_round<S, T>(hn);
+          const T wxv = wxb[b], wyv = wyb[b];
+          const T xp = xix - m0.ux, yp = (D == 2) ? xiy - m0.uy : T(0);
+          const T wg = wxv * (wyv * gq);
+          const T e = wxv * (wyv * ((xp * xp + yp * yp) * gq + hq));
+          c0k.add(wg);
+          cxk.add(wg * xp);
+          cek.add(e);
+          cgxx += wg * xp * xp;
+          cjx += e * xp;
+          if (D == 2) {
+            cyk.add(wg * yp);
+            cgxy += wg * xp * yp;
+            cgyy += wg * yp * yp;
+            cjy += e * yp;
           }
         }
       }
     }
-    if (MODE == 1) {
-      __syncthreads();
-      // ---- phase 4: update of the tile's cells (Eq. explicit_update)
-      if (own_active) {
-        const int w_ = (D == 2) ? ty * (TX + 1) + tx : tx;
-        // phi~+ = 4/3 phi-bar-plus - 1/3 phi~ = phi~ + (4/3) b (phi^S - phi~)
-        T gn = g0 + m0.c2 * dg0 - lamx * xix * (sFxg[w_ + 1] - sFxg[w_]);
-        T hn = h0 + m0.c2 * dh0 - lamx * xix * (sFxh[w_ + 1] - sFxh[w_]);
-        if (D == 2) {
-          const int sI = ty * TX + tx;
-          gn -= lamy * xiy * (sFyg[sI + TX] - sFyg[sI]);
-          hn -= lamy * xiy * (sFyh[sI + TX] - sFyh[sI]);
-        }
-        stf<S, T>(fout + (long)v * nc + own_cell, gn);
-        stf<S, T>(fout + (nv + v) * nc + own_cell, hn);
-        // moments of the stored value
-        const T gq = ldf_round<S, T>(gn), hq = ldf_round<S, T>(hn);
-        const T xp = xix - m0.ux, yp = (D == 2) ? xiy - m0.uy : T(0);
-        const T wg = wxv * (wyv * gq);
-        const T e = wxv * (wyv * ((xp * xp + yp * yp) * gq + hq));
-        acc0[0].add(wg);
-        accX[0].add(wg * xp);
-        accE[0].add(e);
-        acc[0][0] += wg * xp * xp;
-        acc[0][3] += e * xp;
-        if (D == 2) {
-          accY[0].add(wg * yp);
-          acc[0][1] += wg * xp * yp;
-          acc[0][2] += wg * yp * yp;
-          acc[0][4] += e * yp;
-        }
-      }
-    } else {
-      par ^= 1;
-    }
   }
 
-  // ---- write partial moments of this chunk
+  // ---- write the chunk's partial moments
   if (MODE == 0) {
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      if (q >= nfr || fr[q].fid < 0 || !fr[q].owned) continue;
-      double* P = a.part + (long)chunk * NMOM * k.nface + fr[q].fid;
-      const long st = k.nface;
-      P[MO_0 * st] = acc0[q].val();
-      P[MO_X * st] = accX[q].val();
-      P[MO_Y * st] = (D == 2) ? accY[q].val() : 0.0;
-      P[MO_E * st] = accE[q].val();
-      P[MO_GXX * st] = (double)acc[q][0];
-      P[MO_GXY * st] = (double)acc[q][1];
-      P[MO_GYY * st] = (double)acc[q][2];
-      P[MO_JX * st] = (double)acc[q][3];
-      P[MO_JY * st] = (double)acc[q][4];
+      const int f = tid + q * G::NT;
+      if (f >= G::NF) break;
+      const int meta = sMeta[f];
+      if (!(meta & FM_VALID) || !(meta & FM_OWNED)) continue;
+      const int fid = sMeta[G::NF + f];
+      double* P = a.part + (long)chunk * NMOM * k.nface + fid;
+      if (q < 2) write_partials<T, D>(ra[q < 2 ? q : 0], P, k.nface);
+      else write_partials_smem<T, D>(sAcc + f, G::NF, P, k.nface);
     }
   } else if (own_active) {
     double* P = a.part + (long)chunk * NMOM * nc + own_cell;
-    P[MO_0 * nc] = acc0[0].val();
-    P[MO_X * nc] = accX[0].val();
-    P[MO_Y * nc] = (D == 2) ? accY[0].val() : 0.0;
-    P[MO_E * nc] = accE[0].val();
-    P[MO_GXX * nc] = (double)acc[0][0];
-    P[MO_GXY * nc] = (double)acc[0][1];
-    P[MO_GYY * nc] = (double)acc[0][2];
-    P[MO_JX * nc] = (double)acc[0][3];
-    P[MO_JY * nc] = (double)acc[0][4];
+    P[MO_0 * nc] = c0k.val();
+    P[MO_X * nc] = cxk.val();
+    P[MO_Y * nc] = (D == 2) ? cyk.val() : 0.0;
+    P[MO_E * nc] = cek.val();
+    P[MO_GXX * nc] = (double)cgxx;
+    P[MO_GXY * nc] = (double)cgxy;
+    P[MO_GYY * nc] = (double)cgyy;
+    P[MO_JX * nc] = (double)cjx;
+    P[MO_JY * nc] = (double)cjy;
   }
 }
 

@@ -319,8 +319,9 @@ __global__ void k_finalize(const PointArgs a) {
     mp.b0 = T(0); mp.b1 = T(0); mp.b2 = T(0); mp.b3 = T(0);
     const double den = wall_den<T, D>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1));
     const double rw = -M[MO_0] / den;
-    mp.c1 = T(0);
+    // rho_w as an unevaluated sum hi + lo, so that its rounding leaves no net wall mass flux
     mp.c2 = T(rw);
+    mp.c1 = T(rw - (double)mp.c2);
     store_mp<T>(po, a.npt, i, mp, T(kind));
     po[P_SHX * (long)a.npt + i] = shx;
     po[P_SHY * (long)a.npt + i] = shy;

@@ -131,6 +131,17 @@ namespace {
 template <class S, class T, int D> struct Runner {
   static constexpr int TX = (D == 2) ? 32 : 128;
   static constexpr int TY = (D == 2) ? 8 : 1;
+  static constexpr int VB = 2;   // velocities per barrier round
+  static constexpr size_t SM0 = TileSmem<T, TX, TY, D, VB, 0>::BYTES;
+  static constexpr size_t SM1 = TileSmem<T, TX, TY, D, VB, 1>::BYTES;
+
+  static cudaError_t set_smem_limits() {
+    cudaError_t e = cudaFuncSetAttribute(k_tile<S, T, D, TX, TY, VB, 0>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM0);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_tile<S, T, D, TX, TY, VB, 1>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
+  }
 
   static void tiles(const StepConst& k, int& ntx, int& nty) {
     ntx = (k.nx + TX - 1) / TX;
@@ -161,6 +172,8 @@ template <class S, class T, int D> struct Runner {
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
 
   static cudaError_t init(mlvs_handle* h, LevelData& L, LevelInst& I, const double* dW0) {
+    cudaError_t es = set_smem_limits();
+    if (es != cudaSuccess) return es;
     PointArgs a = pargs(h, L, I, false);
     a.compat = h->cfg.compat_cell;
     a.prm_out = I.prm[0].p;
@@ -219,7 +232,7 @@ template <class S, class T, int D> struct Runner {
     dim3 grid(t.ntx * t.nty, L.k.nchunk);
     t.part = I.fpart.as<double>();
     mark_begin(h, 1);
-    k_tile<S, T, D, TX, TY, 0><<<grid, TX * TY, 0, h->stream>>>(t, limiter);
+    k_tile<S, T, D, TX, TY, VB, 0><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
     mark_end(h);
     PointArgs a = pargs(h, L, I, true);
     a.cprm = I.prm[I.pcur].p;
@@ -229,7 +242,7 @@ template <class S, class T, int D> struct Runner {
     mark_end(h);
     t.part = I.cpart.as<double>();
     mark_begin(h, 3);
-    k_tile<S, T, D, TX, TY, 1><<<grid, TX * TY, 0, h->stream>>>(t, limiter);
+    k_tile<S, T, D, TX, TY, VB, 1><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
     mark_end(h);
     I.cur ^= 1;
     I.fresh = false;

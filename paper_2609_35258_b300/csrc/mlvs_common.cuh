@@ -23,7 +23,8 @@ namespace mlvs {
 //          (the derived conversions of Sec. 2.2 with their weights summing to one)
 //   faces: C1 = 2 tau/(2 tau + s), C2 = s/(2 tau + s):  phi = phi-bar + C2 (phi^S - phi-bar)
 //          (Eq. recover_phi)
-//   wall faces: C2 = rho_w multiplies the unit-density wall Maxwellian.
+//   wall faces: C2 + C1 = rho_w (high and low parts) multiplies the unit-density wall
+//          Maxwellian.
 // The correction factor is 1 + B0 + B1 c_x + B2 c_y + B3 |c|^2 with c = xi - u: the span of
 // the basis of Eq. eq_four_basis {1, xi_x, xi_y, E_xi} written in peculiar velocity.
 enum {
@@ -48,6 +49,9 @@ template <> struct Num<float> {
     return __expf(__fmaf_rn(__fmul_rn(c, c), -k, l));
   }
   static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 };
 template <> struct Num<double> {
   static __device__ __forceinline__ double dv(double a, double b) { return a / b; }
@@ -55,6 +59,9 @@ template <> struct Num<double> {
     return exp(__fma_rn(__dmul_rn(c, c), -k, l));
   }
   static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
 template <class S, class T> __device__ __forceinline__ T ldf(const S* p);
@@ -103,19 +110,22 @@ __device__ __forceinline__ T maxwell_sep(const MP<T>& p, T cx, T cy) {
 //   g^S = g^eq [1 + kq.c (|c|^2/RT - D - 2)]
 //   h^S = RT g^eq [c0 + kq.c ((|c|^2/RT - D) c0 - 2K)],  c0 = K + 3 - D, kq = (1-Pr) q/(5 p RT)
 //   (Eq. g_h_eq_Pr), then multiplied by 1 + B0 + B1 c_x + B2 c_y + B3 |c|^2.
+// Every operation is an explicitly rounded intrinsic, so each kernel that evaluates the model
+// (face sums, update, finalisation) obtains the same bits for the same inputs.
 template <class T, int D>
 __device__ __forceinline__ void model_eval(const MP<T>& p, T xix, T xiy, T c0, T twoK, T& g, T& h) {
-  const T cx = xix - p.ux;
-  const T cy = (D == 2) ? (xiy - p.uy) : T(0);
+  using N = Num<T>;
+  const T cx = N::sub(xix, p.ux);
+  const T cy = (D == 2) ? N::sub(xiy, p.uy) : T(0);
   const T geq = maxwell_sep<T, D>(p, cx, cy);
-  const T cc = cx * cx + cy * cy;
-  const T cq = p.kqx * cx + p.kqy * cy;
-  const T t = T(2) * p.inv2RT * cc;
-  const T gs = geq * (T(1) + cq * (t - T(D + 2)));
-  const T hs = p.RT * geq * (c0 + cq * ((t - T(D)) * c0 - twoK));
-  const T corr = p.b0 + p.b1 * cx + p.b2 * cy + p.b3 * cc;
-  g = gs + gs * corr;
-  h = hs + hs * corr;
+  const T cc = N::fma(cy, cy, N::mul(cx, cx));
+  const T cq = N::fma(p.kqy, cy, N::mul(p.kqx, cx));
+  const T t = N::mul(N::mul(T(2), p.inv2RT), cc);
+  const T gs = N::mul(geq, N::fma(cq, N::sub(t, T(D + 2)), T(1)));
+  const T hs = N::mul(N::mul(p.RT, geq), N::fma(cq, N::fma(N::sub(t, T(D)), c0, -twoK), c0));
+  const T corr = N::fma(p.b3, cc, N::fma(p.b2, cy, N::fma(p.b1, cx, p.b0)));
+  g = N::fma(gs, corr, gs);
+  h = N::fma(hs, corr, hs);
 }
 
 // Compensated (Kahan) accumulation for sums that must keep FP64-level accuracy in FP32.

@@ -112,9 +112,17 @@ def test_conservation_f64_periodic():
     assert np.max(np.abs(tot1 - tot0)) < 1e-12 * np.max(np.abs(tot0))
 
 
+# FP32 storage rounds every stored value to nearest at 2^-24: a relative error with standard
+# deviation 2^-24/sqrt(12) = 1.7e-8 per value, unbiased.  A cell total sum_v w phi then moves
+# by about 1.7e-8/sqrt(N_eff) (N_eff ~ 100 effective velocities), and the domain total by that
+# over sqrt(n_cells) per step, as a random walk over the steps: ~6e-11 per step for 561 cells,
+# ~4e-10 after 50 steps.  The bound is 3e-9: anything systematic (weights that do not sum to
+# one, rounded wall densities, correction sums that disagree with the evaluated model) shows
+# up at 1e-7 or more over these runs.
+FP32_DRIFT_BOUND = 3e-9
+
+
 def test_conservation_f32_periodic():
-    """FP32 storage rounds every stored value at 2^-24; the conserved totals drift only by
-    that rounding (bound: 1e-9 relative over 50 steps)."""
     desc = workloads.periodic_random(33, 17, n_base=25, storage="f32")
     s = Solver(desc)
     m0 = s.moments()
@@ -122,16 +130,30 @@ def test_conservation_f32_periodic():
     m1 = s.moments()
     tot0 = np.array([m0[0].sum(), m0[6].sum()])
     tot1 = np.array([m1[0].sum(), m1[6].sum()])
-    assert np.max(np.abs(tot1 - tot0) / tot0) < 1e-9
+    assert np.max(np.abs(tot1 - tot0) / tot0) < FP32_DRIFT_BOUND
 
 
+def test_wall_mass_conservation_f64():
+    """Diffuse walls carry no net mass flux: exact up to FP64 rounding."""
+    desc = workloads.cavity(32, n_base=25, Kn=0.075, storage="f64")
+    s = Solver(desc)
+    m0 = s.moments()[0].sum()
+    s.step(100)
+    m1 = s.moments()[0].sum()
+    assert abs(m1 - m0) / m0 < 1e-13
+
+
+# Near a steady state the FP32 rounding of phi~^{n+1} stops being random: the same sub-ulp
+# increments are lost every step, so the drift grows linearly instead of as a random walk,
+# about 3e-8 / sqrt(n_cells * N_eff) per step (1e-10 for 1024 cells) -> 1e-8 per 100 steps.
+# The FP64 test above shows the wall treatment itself is exact; the bound here is 1e-7.
 def test_wall_mass_conservation_f32():
     desc = workloads.cavity(32, n_base=25, Kn=0.075)
     s = Solver(desc)
     m0 = s.moments()[0].sum()
     s.step(100)
     m1 = s.moments()[0].sum()
-    assert abs(m1 - m0) / m0 < 1e-9
+    assert abs(m1 - m0) / m0 < 1e-7
 
 
 def test_uniform_bgk_fixed_point_gpu():
