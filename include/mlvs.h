@@ -130,6 +130,32 @@ mlvs_status mlvs_read_cells(mlvs_handle* h, int instance, int cell0, int ncells,
 /* Extra: the time step in use. */
 mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt);
 
+/* Conservative moments without device allocation.  The paper has no counterpart: this entry
+ * point exists for callers that must not have the library allocate device memory, such as a
+ * process that reserves its GPU memory once at start-up and forbids later allocations (an
+ * allocation synchronises the device and can fail under memory pressure), or code that records
+ * its work into a CUDA graph, where an allocation inside the recorded region breaks it.
+ *
+ * Input: g, h are caller-owned device arrays of FP32 reduced distributions laid out [nv][ncell]
+ * (velocity-plane-major, the library's own layout); xi_x, xi_y, w_x, w_y are device arrays of
+ * nv velocity coordinates and per-axis weights (weight = w_x * w_y; D = 1: xi_y = 0, w_y = 1).
+ * Output: out is a caller-owned device array [4][ncell] = (rho, rho u, rho v, rho E) in FP64.
+ * Work is queued on `stream` (cudaStream_t, NULL = default stream); the call does not wait.
+ *
+ * Scratch: an 8 MiB file-scope device array (16 velocity chunks x 4 moments x 16384 cells of
+ * FP64 partial sums) that every GPU which loads the library holds until the process exits.
+ * ncell above 16384 is rejected with MLVS_ERR_ARG.  The library calls no cudaMalloc, cudaFree or
+ * other allocating routine here.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream capture.
+ * All calls share the one array and leave their partial sums in it; every call overwrites all the
+ * entries it later reads, so nothing needs clearing, but calls that overlap on the GPU (on
+ * different streams, or different threads) race on the array and must be serialised by the caller.
+ * Errors: MLVS_ERR_ARG (null pointer, non-positive or too large sizes), MLVS_ERR_CUDA; the
+ * message is available from mlvs_last_error(NULL). */
+mlvs_status mlvs_moments_noalloc(const float* g, const float* h, int nv, int ncell,
+                                 const float* xi_x, const float* xi_y, const float* w_x,
+                                 const float* w_y, double* out, void* stream);
+
 /* Release everything the handle owns.  NULL is allowed. */
 void mlvs_destroy(mlvs_handle* h);
 

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "../../include/mlvs.h"
+#include "mlvs_internal.h"
 #include "dugks_tile.cuh"
 #include "finalize.cuh"
 #include "vspace_host.hpp"
@@ -348,6 +349,8 @@ extern "C" void mlvs_destroy(mlvs_handle* h) {
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
 }
+
+void mlvs_internal_set_error(const char* msg) { g_create_error = msg ? msg : ""; }
 
 extern "C" const char* mlvs_last_error(const mlvs_handle* h) {
   return h ? h->err.c_str() : g_create_error.c_str();

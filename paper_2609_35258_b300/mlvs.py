@@ -61,6 +61,8 @@ def _load():
         "mlvs_read_cells": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
         "mlvs_time_step": (C.c_int, [H, C.POINTER(C.c_double)]),
+        "mlvs_moments_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "mlvs_destroy": (None, [H]),
         "mlvs_last_error": (C.c_char_p, [H]),
     }
@@ -142,6 +144,15 @@ def mlvs_time_step(h):
     dt = C.c_double()
     _check(_lib.mlvs_time_step(h, C.byref(dt)), h)
     return dt.value
+
+
+def mlvs_moments_noalloc(g, h, nv, ncell, xi_x, xi_y, w_x, w_y, out, stream=None):
+    """Allocation-free moments: every argument is a device pointer (int) or a tensor with
+    data_ptr(); see include/mlvs.h for layouts."""
+    def ptr(x):
+        return C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else x)
+    _check(_lib.mlvs_moments_noalloc(ptr(g), ptr(h), nv, ncell, ptr(xi_x), ptr(xi_y), ptr(w_x),
+                                     ptr(w_y), ptr(out), C.c_void_p(stream)), None)
 
 
 def mlvs_destroy(h):
