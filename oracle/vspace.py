@@ -137,6 +137,13 @@ def uniform_space(base: Base, L: int) -> Space:
     return Space(xi, w, rect, owner, base)
 
 
+def aniso_space(base: Base, Lx: int, Ly: int) -> Space:
+    """Tensor-product space with the x axis grouped at level Lx and the y axis at Ly (2-D)."""
+    gx, gy = axis_groups(base.n, Lx), axis_groups(base.n, Ly)
+    rect = np.array([(a[0], a[-1] + 1, b[0], b[-1] + 1) for b in gy for a in gx], dtype=np.int64)
+    return space_from_rects(base, rect)
+
+
 def level1_parent_maps(n: int, max_level: int = 3):
     """For each level L (1..max_level) the level-L group index of every level-1 group."""
     g1 = axis_groups(n, 1)

@@ -1,0 +1,229 @@
+"""Pins of the multi-level parts of the oracle (Sec. 3.2-3.4).
+
+Projection and mapping are checked against their defining properties (aggregation preserves
+mass and energy, refinement inverts coarsening, the corrections hit their targets), the
+repeated-projection test of Sec. 4.1.2 against its closed-form invariants, the criterion and
+clustering against brute force and the limits the paper states, and the multi-level step
+against the single-space oracle and exact conservation.
+"""
+import numpy as np
+import pytest
+
+from oracle import cluster, criterion, dugks, kinetic, mapping, mlvs, vspace
+from paper_2609_35258_b300 import workloads
+from tests.helpers import oracle_run, oracle_setup
+
+
+def _rand_gh(sp, seed=0):
+    rng = np.random.default_rng(seed)
+    return 0.1 + rng.random(sp.nv), 0.1 + rng.random(sp.nv)
+
+
+def test_projection_preserves_mass_energy_and_refine_inverts():
+    base = vspace.make_base(33, -5, 5, D=2)
+    fine, coarse = vspace.uniform_space(base, 0), vspace.uniform_space(base, 2)
+    g, h = _rand_gh(fine)
+    gc, hc = mapping.project(g, h, fine, coarse)
+    x2f = np.sum(fine.xi ** 2, -1)
+    x2c = np.sum(coarse.xi ** 2, -1)
+    assert abs(np.sum(coarse.w * gc) - np.sum(fine.w * g)) < 1e-13
+    assert abs(np.sum(coarse.w * (hc + x2c * gc)) - np.sum(fine.w * (h + x2f * g))) < 1e-12
+    gr, hr = mapping.project(gc, hc, coarse, fine)
+    g2, h2 = mapping.project(gr, hr, fine, coarse)
+    np.testing.assert_allclose(g2, gc, rtol=1e-14)
+    np.testing.assert_allclose(h2, hc, rtol=1e-13, atol=1e-14)
+
+
+def test_correct4_hits_targets():
+    base = vspace.make_base(33, -5, 5, D=2)
+    src, dst = vspace.uniform_space(base, 0), vspace.uniform_space(base, 1)
+    gas = kinetic.Gas(D=2, R=1.0)
+    g, h = kinetic.maxwell_gh(np.array(1.1), np.array([0.3, -0.2]), np.array(0.9), src.xi, gas)
+    g2, h2 = mapping.map4(g, h, src, dst, gas)
+    np.testing.assert_allclose(kinetic.conserved(g2, h2, dst.xi, dst.w),
+                               kinetic.conserved(g, h, src.xi, src.w), rtol=1e-13)
+
+
+def _e2_initial(base, kind, eps):
+    """Sec. 4.1.2 state (rho, U, V, T, R) = (1, 1, 0, 1, 0.5) with g = g_eq (1 + eps delta),
+    delta orthogonalised on the initial space against (1, xi_x, xi_y, xi^2)."""
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2, R=0.5)
+    rho, u, T = np.array(1.0), np.array([1.0, 0.0]), np.array(1.0)
+    g, h = kinetic.maxwell_gh(rho, u, T, sp.xi, gas)
+    g, h = kinetic.compat_correct4(g, h, rho, u, T, sp.xi, sp.w, gas)   # exact initial moments
+    c = sp.xi - np.array([1.0, 0.0])
+    d = c[:, 0] * (np.sum(c * c, -1) - 5 * 0.5) if kind == "heat" else c[:, 0] ** 2 - c[:, 1] ** 2
+    B = np.stack([np.ones(sp.nv), sp.xi[:, 0], sp.xi[:, 1], np.sum(sp.xi ** 2, -1)])
+    Wg = sp.w * g
+    coef = np.linalg.solve((B * Wg) @ B.T, (B * Wg) @ d)
+    d = d - coef @ B
+    return sp, gas, g * (1 + eps * d), h
+
+
+def _e2_sequence(base):
+    return [(1, 0), (1, 1), (2, 1), (2, 2), (3, 2), (3, 3), (0, 0)]
+
+
+@pytest.mark.parametrize("kind", ["heat", "stress"])
+@pytest.mark.parametrize("eps", [1e-5, 1e-3, 1e-1])
+def test_repeated_projection_invariants(kind, eps):
+    """Four-moment mapping keeps rho = 1, rho U = 1, rho E = 1.25 (Table of Sec. 4.1.2);
+    nine-moment mapping also returns q_x and Pi_xx - Pi_yy to their initial values."""
+    base = vspace.make_base(65, -6, 6, D=2)
+    sp0, gas, g, h = _e2_initial(base, kind, eps)
+    m0 = kinetic.moments(g, h, sp0.xi, sp0.w, gas)
+    assert abs(m0["rho"] - 1) < 1e-12 and abs(m0["mom"][0] - 1) < 1e-12
+    assert abs(m0["rhoE"] - 1.25) < 1e-12             # 1/2 rho U^2 + 3/2 rho R T
+    cur, g4, h4, g9, h9 = sp0, g, h, g, h
+    for Lx, Ly in _e2_sequence(base):
+        nxt = vspace.aniso_space(base, Lx, Ly)
+        g4, h4 = mapping.map4(g4, h4, cur, nxt, gas)
+        g9, h9 = mapping.map9(g9, h9, cur, nxt)
+        cur = nxt
+    m4 = kinetic.moments(g4, h4, cur.xi, cur.w, gas)
+    assert abs(m4["rho"] - 1) < 1e-12 and abs(m4["mom"][0] - 1) < 1e-12
+    assert abs(m4["rhoE"] - 1.25) < 1e-12
+    m9 = kinetic.moments(g9, h9, cur.xi, cur.w, gas)
+    assert abs(m9["rhoE"] - 1.25) < 1e-12
+    d0 = m0["P"][0, 0] - m0["P"][1, 1]
+    d9 = m9["P"][0, 0] - m9["P"][1, 1]
+    assert abs(m9["q"][0] - m0["q"][0]) < 1e-12 * max(1.0, abs(m0["q"][0]) / eps)
+    assert abs(d9 - d0) < 1e-12 * max(1.0, abs(d0) / eps)
+    if kind == "heat":
+        assert abs(m0["q"][0]) > 0.1 * eps          # the perturbation carries a heat flux
+
+
+# ------------------------------------------------------------------ criterion and clustering
+
+def test_criterion_uniform_maxwellian():
+    base = vspace.make_base(33, -6, 6, D=2)
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2)
+    g, h = kinetic.maxwell_gh(np.array(1.0), np.array([0.0, 0.0]), np.array(1.0), sp.xi, gas)
+    g2, h2 = g.reshape(33, 33), h.reshape(33, 33)
+    N1 = len(vspace.axis_groups(33, 1))
+    kap = criterion.criterion_2d(g2, h2, base, np.zeros((N1, N1), int), 5e-3, 2.5e-3)
+    # symmetric under xi -> -xi, fine at the centre, merged in the far tails
+    np.testing.assert_array_equal(kap, kap[::-1, ::-1])
+    np.testing.assert_array_equal(kap, kap.T)
+    assert kap[N1 // 2, N1 // 2] == 0
+    assert kap[0, 0] == 3
+    # brute force: every level-1 block left fine has I_B >= C_merge
+    M1, M2 = criterion._contrib(g2, h2, base)
+    g1 = vspace.axis_groups(33, 1)
+    for by in range(N1):
+        for bx in range(N1):
+            if kap[by, bx] == 0:
+                sl = (slice(g1[by][0], g1[by][-1] + 1), slice(g1[bx][0], g1[bx][-1] + 1))
+                assert max(M1[sl].sum(), M2[sl].sum()) >= 2.5e-3
+
+
+def test_criterion_hysteresis_band():
+    base = vspace.make_base(33, -6, 6, D=2)
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2)
+    g, h = kinetic.maxwell_gh(np.array(1.0), np.array([0.0, 0.0]), np.array(1.0), sp.xi, gas)
+    g2, h2 = g.reshape(33, 33), h.reshape(33, 33)
+    N1 = len(vspace.axis_groups(33, 1))
+    big = 10.0       # every block in the band [C_merge, C_split]
+    k_prev0 = criterion.criterion_2d(g2, h2, base, np.zeros((N1, N1), int), big, 0.0)
+    k_prev3 = criterion.criterion_2d(g2, h2, base, np.full((N1, N1), 3), big, 0.0)
+    assert np.all(k_prev0 == 0) and np.all(k_prev3 == 3)
+
+
+def test_transport_test_only_rejects():
+    base = vspace.make_base(33, -6, 6, D=2)
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2)
+    g, h = kinetic.maxwell_gh(np.array(1.0), np.array([0.5, 0.0]), np.array(1.0), sp.xi, gas)
+    g2, h2 = g.reshape(33, 33), h.reshape(33, 33)
+    N1 = len(vspace.axis_groups(33, 1))
+    z = np.zeros((N1, N1), int)
+    k_free = criterion.criterion_2d(g2, h2, base, z, 5e-3, 2.5e-3)
+    k_tr = criterion.criterion_2d(g2, h2, base, z, 5e-3, 2.5e-3, eps_merge=1e-6)
+    assert np.all(k_tr <= k_free)
+    assert np.sum(k_tr) < np.sum(k_free)
+
+
+def test_graded_distance_properties():
+    a = np.zeros(10, int)
+    b = np.full(10, 3)
+    assert cluster.graded_distance(a, a) == 0
+    assert cluster.graded_distance(a, b) == 1
+    rng = np.random.default_rng(3)
+    x, y = rng.integers(0, 4, 10), rng.integers(0, 4, 10)
+    assert cluster.graded_distance(x, y) == cluster.graded_distance(y, x)
+    assert cluster.graded_distance(x, y) == np.sum(np.abs(x - y)) / 30
+
+
+def test_clustering_limits_and_enclosure():
+    rng = np.random.default_rng(5)
+    pats = rng.integers(0, 4, size=(6, 12))
+    K = pats[rng.integers(0, 6, size=200)]
+    lab1, rep1 = cluster.cluster(K, 1.0)
+    assert rep1.shape[0] == 1 and np.all(lab1 == 0)
+    lab0, rep0 = cluster.cluster(K, 0.0)
+    assert rep0.shape[0] == len(np.unique(K, axis=0))
+    for tau in (0.0, 0.1, 0.3, 1.0):
+        lab, rep = cluster.cluster(K, tau)
+        for c in range(rep.shape[0]):
+            assert np.all(rep[c] <= K[lab == c])          # kappa_rep <= kappa_M for members
+    # uniform requirement -> one space
+    lab, rep = cluster.cluster(np.tile(pats[0], (50, 1)), 0.0)
+    assert rep.shape[0] == 1
+
+
+# ------------------------------------------------------------------ multi-level step
+
+def _mlvs_from_desc(desc, levels_of_cell, Ls):
+    o = oracle_setup(desc)
+    book = mlvs.SpaceBook(o["base"])
+    keys = [book.uniform(L) for L in Ls]
+    init = desc["init"]
+    st = mlvs.MLVSState.from_primitives(o["mesh"], o["gas"], book, [keys[l] for l in levels_of_cell],
+                                        init[..., 0], init[..., 1:3], init[..., 3], o["dt"], o["opt"])
+    return o, st
+
+
+def test_single_level_mlvs_equals_uvs():
+    desc = workloads.periodic_random(6, 5, n_base=13, umax=5.0)
+    o, st = _mlvs_from_desc(desc, [0] * 30, [0])
+    for _ in range(2):
+        mlvs.step(st)
+    g, h = oracle_run(o, 2)
+    np.testing.assert_allclose(np.stack(st.g), g.reshape(30, -1), rtol=1e-12, atol=1e-15)
+
+
+def test_single_level_mlvs_equals_uvs_walls():
+    desc = workloads.cavity(5, n_base=13, umax=5.0)
+    o, st = _mlvs_from_desc(desc, [0] * 25, [0])
+    for _ in range(2):
+        mlvs.step(st)
+    g, h = oracle_run(o, 2)
+    np.testing.assert_allclose(np.stack(st.g), g.reshape(25, -1), rtol=1e-12, atol=1e-15)
+
+
+def test_two_level_conservation_and_flux_matching():
+    """Mixed levels on a periodic density wave: cross-level faces conserve exactly (Sec. 3.4)."""
+    desc = workloads.periodic_random(8, 4, n_base=17, umax=5.0)
+    lev = [0 if (c % 8) < 4 else 1 for c in range(32)]
+    o, st = _mlvs_from_desc(desc, lev, [0, 1])
+    W0 = st.totals()
+    for _ in range(4):
+        mlvs.step(st)
+    W1 = st.totals()
+    assert np.max(np.abs(W1 - W0)) < 1e-12 * np.max(np.abs(W0))
+    # the coarse side really is coarser
+    assert st.book.space(st.sp[7]).nv < st.book.space(st.sp[0]).nv
+
+
+def test_remap_preserves_moments():
+    desc = workloads.periodic_random(4, 4, n_base=17, umax=5.0)
+    o, st = _mlvs_from_desc(desc, [0] * 16, [0])
+    before = st.totals()
+    k1 = st.book.uniform(2)
+    for c in range(0, 16, 2):
+        mlvs.remap(st, c, k1)
+    after = st.totals()
+    np.testing.assert_allclose(after, before, rtol=1e-13)
