@@ -87,8 +87,9 @@ typedef struct {
   int n_levels;              /* out                                                          */
   int launches;              /* out: kernels launched by the call                            */
   float ms_total;            /* out: device time of the call (CUDA events), ms               */
-  float ms_phase[4];         /* out (profile): summed device time of the cell finalisation,
-                                face-sum, face finalisation and update launches, ms          */
+  float ms_phase[6];         /* out (profile): summed device time, ms, of the cell
+                                finalisation, face-sum, face finalisation, update, ghost
+                                mapping and flux mapping launches                            */
 } mlvs_step_stats;
 
 /* Create a handle for the problem in cfg.  No velocity space exists yet.
@@ -108,6 +109,20 @@ mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, double umin, do
  * stats->profile is read and the other fields are written.
  * Errors: MLVS_ERR_STATE, MLVS_ERR_NONFINITE, MLVS_ERR_POSITIVITY, MLVS_ERR_CUDA. */
 mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* stats);
+
+/* Assign every cell of one instance to a velocity level (host levels[ny*nx], values in
+ * 0..n_levels-1, copied).  A cell whose space changes is remapped by the hierarchical
+ * projection and the four-moment correction with its own moments as targets
+ * (Sec. 3.3.2, Eq. level_switch_conservation).  Cross-level faces are then evaluated on the
+ * common refinement of the two spaces and their fluxes mapped back with the four-moment flux
+ * correction (Sec. 3.4).
+ * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
+mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const int* levels);
+
+/* Extra: number of velocities of a level and (if the arrays are non-NULL, capacity cap) its
+ * coordinates and weights. */
+mlvs_status mlvs_level_info(const mlvs_handle* h, int level, int* nv, double* xi_x, double* xi_y,
+                            double* w, int cap);
 
 /* field bits for mlvs_moments; fields are written in this bit order */
 enum {

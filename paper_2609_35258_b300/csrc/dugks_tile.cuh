@@ -19,15 +19,31 @@
 namespace mlvs {
 
 struct TileArgs {
-  StepConst k;
-  const void* f_in;      // [2][nv][ncell]
-  void* f_out;           // [2][nv][ncell] (MODE 1)
-  const void* cparam;    // [NP][ncell]  type T
+  StepConst k;           // mesh-wide constants (k.ncell, k.nface: the whole mesh)
+  const void* f_in;      // [2][nv][nslot] phi~ of this level's cells (storage type)
+  void* f_out;           // [2][nv][nslot] (MODE 1)
+  int nslot;             // cells on this level
+  const void* cparam;    // [NP][nslot]  type T
   const void* fparam;    // [NP][nface]  type T (MODE 1)
   const void* vt;        // [4][nv]      type T
-  double* part;          // MODE 0: [nchunk][NMOM][nface], MODE 1: [nchunk][NMOM][ncell]
-  int ntx, nty;          // tiles per axis
+  double* part;          // MODE 0: [nchunk][NMOM][nface], MODE 1: [nchunk][NMOM][nslot]
+  const int* tiles;      // tile ids launched for this level
+  int ntx, nty;          // tiles per axis of the mesh
+  int level;
+  const int* lvl_of;     // [ncell] level of every cell
+  const int* slot_of;    // [ncell] column of every cell in its level's arrays
+  const int* ghost_of;   // [ncell] column in this level's ghost array, or -1 (may be null)
+  const void* ghost;     // (T) [2][nv][nghost] phi-bar-plus of other-level stencil cells on this space
+  int nghost;
+  const unsigned char* frole;  // [nface] role of every face on this level (FR_*)
+  const int* fslot;      // [nface] column in X (FR_CROSS) or Y (FR_RECV)
+  void* X;               // (T) [2][nv][nX] microfluxes of the cross faces evaluated here
+  int nX;
+  const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
+  int nY;
+  const void* ucell;     // (T) [2][ncell] cell velocities (face moment shifts)
 };
+
 
 template <int TX, int TY, int D> struct TileGeom {
   static constexpr int NT = TX * TY;
@@ -176,43 +192,59 @@ k_tile(const TileArgs a, int limiter) {
   const T* __restrict__ cp = reinterpret_cast<const T*>(a.cparam);
   const T* __restrict__ fp = reinterpret_cast<const T*>(a.fparam);
   const T* __restrict__ vt = reinterpret_cast<const T*>(a.vt);
-  const long nc = k.ncell;
+  const T* __restrict__ gst = reinterpret_cast<const T*>(a.ghost);
+  const T* __restrict__ uc = reinterpret_cast<const T*>(a.ucell);
+  const long ns = a.nslot;
+  const long ng = a.nghost;
   const long nv = k.nv;
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int bx = blockIdx.x % a.ntx, by = blockIdx.x / a.ntx;
+  const int tile = a.tiles[blockIdx.x];
+  const int bx = tile % a.ntx, by = tile / a.ntx;
   const int x0 = bx * TX, y0 = by * TY;
   const int chunk = blockIdx.y;
   const int v0 = chunk * k.vpc;
   const int v1 = min(k.nv, v0 + k.vpc);
 
-  // ---- extended positions: own cell + at most one halo cell
+  // ---- extended positions: own cell + at most one halo cell.  A position holds a cell of
+  // this level (phi~ + parameters -> phi-bar-plus), a ghost (phi-bar-plus mapped to this
+  // space), or nothing (never read by a face evaluated here).
+  auto classify = [&](int ex, int ey, int& kind, long& base, long& ld) {
+    const int c = wrap_or_clamp(y0 + ey, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + ex, k.nx, k.px);
+    kind = 0; base = 0; ld = 0;
+    if (a.lvl_of[c] == a.level) { kind = 1; base = a.slot_of[c]; ld = ns; }
+    else if (a.ghost_of && a.ghost_of[c] >= 0) { kind = 2; base = a.ghost_of[c]; ld = ng; }
+    return c;
+  };
   const int ey0 = (D == 2) ? ty : 0;
-  const int src0 = wrap_or_clamp(y0 + ey0, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + tx, k.nx, k.px);
-  const bool own_active = (x0 + tx < k.nx) && (D == 1 || y0 + ty < k.ny);
-  const int own_cell = own_active ? (y0 + ty) * k.nx + (x0 + tx) : -1;
-  int ex1 = 0, ey1 = 0, src1 = -1;
+  int kind0, kind1 = 0;
+  long col0, ld0, col1 = 0, ld1 = 0;
+  const int c0g = classify(tx, ey0, kind0, col0, ld0);
+  const bool own_active = (x0 + tx < k.nx) && (D == 1 || y0 + ty < k.ny) && kind0 == 1 &&
+                          c0g == (y0 + ey0) * k.nx + (x0 + tx);
+  int ex1 = 0, ey1 = 0;
   if (tid < G::NHALO) {
     G::halo_pos(tid, ex1, ey1);
-    src1 = wrap_or_clamp(y0 + ey1, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + ex1, k.nx, k.px);
+    classify(ex1, ey1, kind1, col1, ld1);
   }
   MP<T> m0, m1;
-  m0.load(cp, nc, src0);
-  if (src1 >= 0) m1.load(cp, nc, src1);
+  if (kind0 == 1) m0.load(cp, ns, col0);
+  if (kind1 == 1) m1.load(cp, ns, col1);
   const int e0 = G::eidx(tx, ey0);
-  const int e1 = (src1 >= 0) ? G::eidx(ex1, ey1) : 0;
+  const int e1 = (tid < G::NHALO) ? G::eidx(ex1, ey1) : 0;
 
   // ---- face metadata (and MODE 1 parameters, MODE 0 shifts/accumulators) in shared memory
   for (int f = tid; f < G::NF; f += G::NT) {
     int dir, li, lj;
     G::face_pos(f, dir, li, lj);
     const int gi = x0 + li, gj = y0 + lj;
-    int meta = 0, fid = -1;
+    int meta = 0, fid = -1, role = FR_NONE;
     if (dir == 0) {
       if (gi <= k.nx && (D == 1 || gj < k.ny)) {
         const int pi = (k.px && gi == k.nx) ? 0 : gi;
         fid = ((D == 2) ? gj : 0) * k.nfx + pi;
+        role = a.frole[fid];
         meta = FM_VALID;
         if ((gi < k.nx) ? (li < TX) : !k.px) meta |= FM_OWNED;
         if (!k.px && gi == 0 && k.bc[0] == BC_WALL) meta |= FK_WALL_LO << 2;
@@ -222,15 +254,18 @@ k_tile(const TileArgs a, int limiter) {
       if (gi < k.nx && gj <= k.ny) {
         const int pj = (k.py && gj == k.ny) ? 0 : gj;
         fid = k.nfx * k.ny + pj * k.nx + gi;
+        role = a.frole[fid];
         meta = FM_VALID;
         if ((gj < k.ny) ? (lj < TY) : !k.py) meta |= FM_OWNED;
         if (!k.py && gj == 0 && k.bc[2] == BC_WALL) meta |= FK_WALL_LO << 2;
         if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) meta |= FK_WALL_HI << 2;
       }
     }
+    if (role == FR_NONE) meta = 0;
+    meta |= role << 4;
     sMeta[f] = meta;
-    sMeta[G::NF + f] = fid;
-    if (MODE == 1 && fid >= 0) {
+    sMeta[G::NF + f] = (role == FR_CROSS || role == FR_RECV) ? a.fslot[fid] : fid;
+    if (MODE == 1 && (role == FR_NORMAL || role == FR_CROSS)) {
 #pragma unroll
       for (int p = 0; p < 13; ++p) sFP[p * G::NF + f] = fp[(long)p * k.nface + fid];
     }
@@ -240,13 +275,15 @@ k_tile(const TileArgs a, int limiter) {
         const int xl = (dir == 0) ? li - 1 : li, yl = (dir == 0) ? lj : lj - 1;
         const int sL = wrap_or_clamp(y0 + yl, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + xl, k.nx, k.px);
         const int sR = wrap_or_clamp(y0 + lj, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + li, k.nx, k.px);
-        shx = T(0.5) * (cp[P_UX * nc + sL] + cp[P_UX * nc + sR]);
-        if (D == 2) shy = T(0.5) * (cp[P_UY * nc + sL] + cp[P_UY * nc + sR]);
+        shx = T(0.5) * (uc[sL] + uc[sR]);
+        if (D == 2) shy = T(0.5) * (uc[k.ncell + sL] + uc[k.ncell + sR]);
       }
 #pragma unroll
       for (int p = 0; p < 13; ++p) sAcc[p * G::NF + f] = T(0);
       sAcc[13 * G::NF + f] = shx;   // slots 13, 14 hold the shift (never accumulated)
       sAcc[14 * G::NF + f] = shy;
+      // the face partials of this level are read only where the role says so
+      if (fid >= 0 && (role == FR_NORMAL || role == FR_CROSS)) sMeta[G::NF + f] = fid;
     }
   }
 
@@ -268,6 +305,8 @@ k_tile(const TileArgs a, int limiter) {
   const T idx_ = T(1.0 / k.dx), idy_ = T(1.0 / k.dy);
   const T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
   S* __restrict__ fout = reinterpret_cast<S*>(a.f_out);
+  T* __restrict__ Xo = reinterpret_cast<T*>(a.X);
+  const T* __restrict__ Yi = reinterpret_cast<const T*>(a.Y);
   __syncthreads();
   // shifts of the thread's register-held faces (MODE 0)
   T fshx[2] = {T(0), T(0)}, fshy[2] = {T(0), T(0)};
@@ -279,6 +318,20 @@ k_tile(const TileArgs a, int limiter) {
     }
   }
 
+  // loads of one velocity for a position of each kind
+  auto load_pos = [&](int kind, long col, int v, T& g, T& h) {
+    if (kind == 1) {
+      g = ldf<S, T>(fin + (long)v * ns + col);
+      h = ldf<S, T>(fin + (nv + v) * ns + col);
+    } else if (kind == 2) {
+      g = gst[(long)v * ng + col];
+      h = gst[(nv + v) * ng + col];
+    } else {
+      g = T(0);
+      h = T(0);
+    }
+  };
+
   // register prefetch of the first round
   T ng0[VB], nh0[VB], ng1[VB], nh1[VB];
 #pragma unroll
@@ -286,12 +339,8 @@ k_tile(const TileArgs a, int limiter) {
     const int v = v0 + b;
     ng0[b] = nh0[b] = ng1[b] = nh1[b] = T(0);
     if (v < v1) {
-      ng0[b] = ldf<S, T>(fin + (long)v * nc + src0);
-      nh0[b] = ldf<S, T>(fin + (nv + v) * nc + src0);
-      if (src1 >= 0) {
-        ng1[b] = ldf<S, T>(fin + (long)v * nc + src1);
-        nh1[b] = ldf<S, T>(fin + (nv + v) * nc + src1);
-      }
+      load_pos(kind0, col0, v, ng0[b], nh0[b]);
+      load_pos(kind1, col1, v, ng1[b], nh1[b]);
     }
   }
 
@@ -312,25 +361,33 @@ k_tile(const TileArgs a, int limiter) {
       const T g1 = ng1[b], h1 = nh1[b];
       const int vn = v + VB;
       if (vn < v1) {
-        ng0[b] = ldf<S, T>(fin + (long)vn * nc + src0);
-        nh0[b] = ldf<S, T>(fin + (nv + vn) * nc + src0);
-        if (src1 >= 0) {
-          ng1[b] = ldf<S, T>(fin + (long)vn * nc + src1);
-          nh1[b] = ldf<S, T>(fin + (nv + vn) * nc + src1);
-        }
+        load_pos(kind0, col0, vn, ng0[b], nh0[b]);
+        load_pos(kind1, col1, vn, ng1[b], nh1[b]);
       }
       T* Pg = sP + (b * 2 + 0) * G::NEXT;
       T* Ph = sP + (b * 2 + 1) * G::NEXT;
       T gs, hs;
-      model_eval<T, D>(m0, xixb[b], xiyb[b], c0, twoK, gs, hs);
-      dg0[b] = N::sub(gs, g0[b]);
-      dh0[b] = N::sub(hs, h0[b]);
-      Pg[e0] = N::fma(m0.c1, dg0[b], g0[b]);
-      Ph[e0] = N::fma(m0.c1, dh0[b], h0[b]);
-      if (src1 >= 0) {
-        model_eval<T, D>(m1, xixb[b], xiyb[b], c0, twoK, gs, hs);
-        Pg[e1] = N::fma(m1.c1, N::sub(gs, g1), g1);
-        Ph[e1] = N::fma(m1.c1, N::sub(hs, h1), h1);
+      if (kind0 == 1) {
+        model_eval<T, D>(m0, xixb[b], xiyb[b], c0, twoK, gs, hs);
+        dg0[b] = N::sub(gs, g0[b]);
+        dh0[b] = N::sub(hs, h0[b]);
+        Pg[e0] = N::fma(m0.c1, dg0[b], g0[b]);
+        Ph[e0] = N::fma(m0.c1, dh0[b], h0[b]);
+      } else {
+        dg0[b] = T(0);
+        dh0[b] = T(0);
+        Pg[e0] = g0[b];
+        Ph[e0] = h0[b];
+      }
+      if (tid < G::NHALO) {
+        if (kind1 == 1) {
+          model_eval<T, D>(m1, xixb[b], xiyb[b], c0, twoK, gs, hs);
+          Pg[e1] = N::fma(m1.c1, N::sub(gs, g1), g1);
+          Ph[e1] = N::fma(m1.c1, N::sub(hs, h1), h1);
+        } else {
+          Pg[e1] = g1;
+          Ph[e1] = h1;
+        }
       }
     }
     __syncthreads();
@@ -359,10 +416,23 @@ k_tile(const TileArgs a, int limiter) {
       if (f >= G::NF) break;
       const int meta = sMeta[f];
       if (!(meta & FM_VALID)) continue;
-      if (MODE == 0 && !(meta & FM_OWNED)) continue;
-      const int kind = meta >> 2;
+      const int role = meta >> 4;
+      if (MODE == 0 && (!(meta & FM_OWNED) || role == FR_RECV)) continue;
+      const int kind = (meta >> 2) & 3;
       int dir, li, lj;
       G::face_pos(f, dir, li, lj);
+      if (MODE == 1 && role == FR_RECV) {
+        // microflux mapped from the face's own space (Eq. native_flux_moment_matching)
+        const int col = sMeta[G::NF + f];
+#pragma unroll
+        for (int b = 0; b < VB; ++b) {
+          const int v = vb0 + b;
+          if (v >= v1) break;
+          sF[(b * 2 + 0) * G::NF + f] = Yi[(long)v * a.nY + col];
+          sF[(b * 2 + 1) * G::NF + f] = Yi[(nv + v) * a.nY + col];
+        }
+        continue;
+      }
       MP<T> fm;
       if (MODE == 1) {
         fm.load(sFP, G::NF, f);
@@ -448,22 +518,31 @@ k_tile(const TileArgs a, int limiter) {
           if (kind == FK_INTERIOR) {
             T gs, hs;
             model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
-            gf = gb + fm.c2 * (gs - gb);     // Eq. recover_phi, weights summing to one
-            hf = hb + fm.c2 * (hs - hb);
+            // Eq. recover_phi with weights summing to one; explicitly rounded so the two tiles
+            // that evaluate a shared face produce the same bits (exact flux telescoping)
+            gf = N::fma(fm.c2, N::sub(gs, gb), gb);
+            hf = N::fma(fm.c2, N::sub(hs, hb), hb);
           } else {
             const T xin = (kind == FK_WALL_LO) ? xn : -xn;
             if (xin > T(0)) {
               T gs, hs;
               model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
-              gf = fm.c2 * gs + fm.c1 * gs;   // rho_w = hi + lo
-              hf = fm.c2 * hs + fm.c1 * hs;
+              gf = N::fma(fm.c1, gs, N::mul(fm.c2, gs));   // rho_w = hi + lo
+              hf = N::fma(fm.c1, hs, N::mul(fm.c2, hs));
             } else {
               gf = gb;
               hf = hb;
             }
           }
-          sF[(b * 2 + 0) * G::NF + f] = gf;
-          sF[(b * 2 + 1) * G::NF + f] = hf;
+          // microflux (xi.n) phi on this space (Eq. interface_reduced_fluxes)
+          const T Fg = N::mul(xn, gf), Fh = N::mul(xn, hf);
+          sF[(b * 2 + 0) * G::NF + f] = Fg;
+          sF[(b * 2 + 1) * G::NF + f] = Fh;
+          if (role == FR_CROSS && (meta & FM_OWNED)) {
+            const int col = sMeta[G::NF + f];
+            Xo[(long)v * a.nX + col] = Fg;
+            Xo[(nv + v) * a.nX + col] = Fh;
+          }
         }
       }
       if (MODE == 0) {
@@ -474,7 +553,7 @@ k_tile(const TileArgs a, int limiter) {
     }
     __syncthreads();
     if (MODE == 1) {
-      // ---- phase 4: update of the tile's cells (Eq. explicit_update)
+      // ---- phase 4: update of the tile's cells of this level (Eq. explicit_update)
       if (own_active) {
         const int wI = (D == 2) ? ty * (TX + 1) + tx : tx;
         const int sI = G::NFXL + ty * TX + tx;
@@ -485,15 +564,15 @@ k_tile(const TileArgs a, int limiter) {
           const T* Fg = sF + (b * 2 + 0) * G::NF;
           const T* Fh = sF + (b * 2 + 1) * G::NF;
           const T xix = xixb[b], xiy = xiyb[b];
-          // phi~+ = phi~ + (4/3) b (phi^S - phi~), then the flux divergence
-          T gn = g0[b] + m0.c2 * dg0[b] - lamx * xix * (Fg[wI + 1] - Fg[wI]);
-          T hn = h0[b] + m0.c2 * dh0[b] - lamx * xix * (Fh[wI + 1] - Fh[wI]);
+          // phi~+ = phi~ + (4/3) b (phi^S - phi~), then the microflux divergence
+          T gn = g0[b] + m0.c2 * dg0[b] - lamx * (Fg[wI + 1] - Fg[wI]);
+          T hn = h0[b] + m0.c2 * dh0[b] - lamx * (Fh[wI + 1] - Fh[wI]);
           if (D == 2) {
-            gn -= lamy * xiy * (Fg[sI + TX] - Fg[sI]);
-            hn -= lamy * xiy * (Fh[sI + TX] - Fh[sI]);
+            gn -= lamy * (Fg[sI + TX] - Fg[sI]);
+            hn -= lamy * (Fh[sI + TX] - Fh[sI]);
           }
-          stf<S, T>(fout + (long)v * nc + own_cell, gn);
-          stf<S, T>(fout + (nv + v) * nc + own_cell, hn);
+          stf<S, T>(fout + (long)v * ns + col0, gn);
+          stf<S, T>(fout + (nv + v) * ns + col0, hn);
           const T gq = ldf_round<S, T>(gn), hq = ldf_round<S, T>(hn);
           const T wxv = wxb[b], wyv = wyb[b];
           const T xp = xix - m0.ux, yp = (D == 2) ? xiy - m0.uy : T(0);
@@ -522,23 +601,24 @@ k_tile(const TileArgs a, int limiter) {
       const int f = tid + q * G::NT;
       if (f >= G::NF) break;
       const int meta = sMeta[f];
-      if (!(meta & FM_VALID) || !(meta & FM_OWNED)) continue;
+      const int role = meta >> 4;
+      if (!(meta & FM_VALID) || !(meta & FM_OWNED) || role == FR_RECV) continue;
       const int fid = sMeta[G::NF + f];
       double* P = a.part + (long)chunk * NMOM * k.nface + fid;
       if (q < 2) write_partials<T, D>(ra[q < 2 ? q : 0], P, k.nface);
       else write_partials_smem<T, D>(sAcc + f, G::NF, P, k.nface);
     }
   } else if (own_active) {
-    double* P = a.part + (long)chunk * NMOM * nc + own_cell;
-    P[MO_0 * nc] = c0k.val();
-    P[MO_X * nc] = cxk.val();
-    P[MO_Y * nc] = (D == 2) ? cyk.val() : 0.0;
-    P[MO_E * nc] = cek.val();
-    P[MO_GXX * nc] = (double)cgxx;
-    P[MO_GXY * nc] = (double)cgxy;
-    P[MO_GYY * nc] = (double)cgyy;
-    P[MO_JX * nc] = (double)cjx;
-    P[MO_JY * nc] = (double)cjy;
+    double* P = a.part + (long)chunk * NMOM * ns + col0;
+    P[MO_0 * ns] = c0k.val();
+    P[MO_X * ns] = cxk.val();
+    P[MO_Y * ns] = (D == 2) ? cyk.val() : 0.0;
+    P[MO_E * ns] = cek.val();
+    P[MO_GXX * ns] = (double)cgxx;
+    P[MO_GXY * ns] = (double)cgxy;
+    P[MO_GYY * ns] = (double)cgyy;
+    P[MO_JX * ns] = (double)cjx;
+    P[MO_JY * ns] = (double)cjy;
   }
 }
 

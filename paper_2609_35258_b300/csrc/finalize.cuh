@@ -37,6 +37,9 @@ struct PointArgs {
   double* W;            // cells: [8][ncell] rho,u,v,T,qx,qy,rhoE,tau (null for faces)
   const void* vt;       // [4][nv] (T)
   const void* ax;       // [2][nax] (T) when k.nax > 0
+  const int* ids;       // cells: global cell id of every point (null: identity)
+  const unsigned char* frole;  // faces: role on this level (null: every face)
+  const void* ucell;    // faces: (T) [2][ncell] cell velocities for the moment shift
   int compat;
   double wall[4][3];    // (u_w, v_w, T_w)
   int* err;             // device error bits
@@ -270,10 +273,13 @@ template <class T, int D>
 __global__ void k_finalize(const PointArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.npt) return;
+  if (a.is_face && a.frole && a.frole[i] != FR_NORMAL && a.frole[i] != FR_CROSS) return;
   const StepConst& k = a.k;
   const T* cp = reinterpret_cast<const T*>(a.cprm);
+  const T* uc = reinterpret_cast<const T*>(a.ucell);
   T* po = reinterpret_cast<T*>(a.prm_out);
   const long nc = k.ncell;
+  const long wi = (!a.is_face && a.ids) ? a.ids[i] : i;   // global cell id of a cell point
   double M[NMOM];
 #pragma unroll
   for (int m = 0; m < NMOM; ++m) M[m] = 0.0;
@@ -285,8 +291,8 @@ __global__ void k_finalize(const PointArgs a) {
   int kind = FK_INTERIOR;
   int side = -1;
   if (!a.is_face) {
-    shx = cp[P_UX * nc + i];
-    shy = cp[P_UY * nc + i];
+    shx = cp[P_UX * (long)a.npt + i];
+    shy = cp[P_UY * (long)a.npt + i];
   } else {
     int sL, sR;
     const int nxf = k.nfx * k.ny;
@@ -304,8 +310,8 @@ __global__ void k_finalize(const PointArgs a) {
       if (!k.py && gj == 0 && k.bc[2] == BC_WALL) { kind = FK_WALL_LO; side = 2; }
       if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) { kind = FK_WALL_HI; side = 3; }
     }
-    shx = T(0.5) * (cp[P_UX * nc + sL] + cp[P_UX * nc + sR]);
-    shy = (D == 2) ? T(0.5) * (cp[P_UY * nc + sL] + cp[P_UY * nc + sR]) : T(0);
+    shx = T(0.5) * (uc[sL] + uc[sR]);
+    shy = (D == 2) ? T(0.5) * (uc[nc + sL] + uc[nc + sR]) : T(0);
   }
   const GasDev& g = a.gas;
   MP<T> mp;
@@ -363,14 +369,14 @@ __global__ void k_finalize(const PointArgs a) {
   po[P_SHX * (long)a.npt + i] = shx;
   po[P_SHY * (long)a.npt + i] = shy;
   if (a.W) {
-    a.W[0 * nc + i] = rho;
-    a.W[1 * nc + i] = ux;
-    a.W[2 * nc + i] = uy;
-    a.W[3 * nc + i] = Tm;
-    a.W[4 * nc + i] = qx;
-    a.W[5 * nc + i] = qy;
-    a.W[6 * nc + i] = rho * (0.5 * (ux * ux + uy * uy) + 0.5 * (3.0 + g.K) * g.R * Tm);
-    a.W[7 * nc + i] = tau;
+    a.W[0 * nc + wi] = rho;
+    a.W[1 * nc + wi] = ux;
+    a.W[2 * nc + wi] = uy;
+    a.W[3 * nc + wi] = Tm;
+    a.W[4 * nc + wi] = qx;
+    a.W[5 * nc + wi] = qy;
+    a.W[6 * nc + wi] = rho * (0.5 * (ux * ux + uy * uy) + 0.5 * (3.0 + g.K) * g.R * Tm);
+    a.W[7 * nc + wi] = tau;
   }
   if (!ok) atomicOr(a.err, ERR_SINGULAR);
   if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.err, ERR_NONFINITE);
@@ -395,9 +401,9 @@ __global__ void k_init_params(const PointArgs a, const double* W0 /* [ncell][4] 
 
 // phi~ = corrected Maxwellian of the initial parameters.
 template <class S, class T, int D>
-__global__ void k_init_f(StepConst k, const T* __restrict__ prm, const T* __restrict__ vt,
+__global__ void k_init_f(StepConst k, int n, const T* __restrict__ prm, const T* __restrict__ vt,
                          S* __restrict__ f) {
-  const long nc = k.ncell;
+  const long nc = n;   // cells of the level
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   MP<T> m;
@@ -413,9 +419,9 @@ __global__ void k_init_f(StepConst k, const T* __restrict__ prm, const T* __rest
 
 // Chunk partial moments of f in the frame of the cell velocity in prm (used after init).
 template <class S, class T, int D>
-__global__ void k_moments(StepConst k, const T* __restrict__ prm, const T* __restrict__ vt,
+__global__ void k_moments(StepConst k, int n, const T* __restrict__ prm, const T* __restrict__ vt,
                           const S* __restrict__ f, double* __restrict__ part) {
-  const long nc = k.ncell;
+  const long nc = n;   // cells of the level
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= nc) return;
   const int chunk = blockIdx.y;

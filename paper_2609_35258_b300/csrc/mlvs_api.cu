@@ -1,11 +1,20 @@
-// C ABI of the MLVS-DUGKS library: handle, memory and the per-step launch sequence.
+// C ABI of the MLVS-DUGKS library: handle, velocity spaces, levels and the step sequence.
 //
-// One DUGKS step (Sec. 2.2) per level is four launches on the handle's stream:
-//   1. k_finalize (cells): chunk partials of phi~ -> W, tau, q, model parameters with the
-//      compatibility correction (Eqs. discrete_W, discrete_q, Sec. 3.3.1)
-//   2. k_tile MODE 0: face phi-bar by the characteristic, face moment partials
-//   3. k_finalize (faces): Eq. W_from_bar, Eq. recover_phi weights, wall densities
-//   4. k_tile MODE 1: face phi, Eq. explicit_update, phi~^{n+1}, cell moment partials
+// Every cell carries its distributions on the space of its level (Sec. 3.1-3.2).  A face is
+// evaluated on the common refinement of its two cells' spaces (V^int, Sec. 3.4): on a level
+// that has cells, or on a cell-less face level.  Stencil cells of another level enter a
+// level's kernels as ghosts: their phi-bar-plus mapped to the level's space with the
+// four-moment correction (Eq. interface_state_moment_matching).  The microflux of a
+// cross-level face is mapped back to the native space of each side and corrected so that its
+// mass, momentum and energy fluxes are those of the face (Eq. native_flux_moment_matching).
+//
+// One step (Sec. 2.2) per instance, on the handle's stream:
+//   1. k_finalize (cells) per level: W, tau, q, model parameters + compatibility correction
+//   2. k_map (SRC_BARP) per (source level, level): ghosts
+//   3. k_tile MODE 0 per level: face phi-bar, face moment partials
+//   4. k_finalize (faces) per level: Eq. W_from_bar, Eq. recover_phi weights, wall densities
+//   5. per level, finest space first: k_tile MODE 1 (microfluxes, Eq. explicit_update), then
+//      k_map (SRC_FLUX) of its cross-level fluxes to the levels that receive them
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -13,7 +22,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <map>
 #include <memory>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -21,6 +33,7 @@
 #include "mlvs_internal.h"
 #include "dugks_tile.cuh"
 #include "finalize.cuh"
+#include "mapping.cuh"
 #include "vspace_host.hpp"
 
 using namespace mlvs;
@@ -32,43 +45,72 @@ thread_local std::string g_create_error;
 struct DevBuf {
   void* p = nullptr;
   size_t n = 0;
-  ~DevBuf() { if (p) cudaFree(p); }
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), n(o.n) { o.p = nullptr; o.n = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; n = o.n; o.p = nullptr; o.n = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() { if (p) cudaFree(p); p = nullptr; n = 0; }
   cudaError_t alloc(size_t bytes) {
-    if (p) { cudaFree(p); p = nullptr; }
+    release();
     n = bytes;
-    return cudaMalloc(&p, bytes ? bytes : 1);
+    return cudaMalloc(&p, bytes ? bytes : 16);
   }
   template <class X> X* as() const { return reinterpret_cast<X*>(p); }
 };
 
-struct Launch {
-  int tx, ty;
-};
+template <class X> cudaError_t upload(DevBuf& d, const std::vector<X>& v, cudaStream_t s) {
+  cudaError_t e = d.alloc(v.size() * sizeof(X));
+  if (e != cudaSuccess || v.empty()) return e;
+  e = cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return e;
+  return cudaStreamSynchronize(s);
+}
 
-// Per level, per instance device state.
-struct LevelInst {
-  DevBuf f[2];      // [2][nv][ncell] storage type
-  DevBuf prm[2];    // [NP][ncell] compute type
-  DevBuf fprm;      // [NP][nface]
-  DevBuf W;         // [8][ncell] double
-  DevBuf cpart;     // [nchunk][NMOM][ncell]
-  DevBuf fpart;     // [nchunk][NMOM][nface]
-  DevBuf err;       // int
-  int cur = 0;      // f[cur] holds the current phi~
-  int pcur = 0;     // prm[pcur] are the parameters used by the current f's last update
-  bool fresh = false;  // prm[pcur] already finalised from the current f
-};
-
-struct LevelData {
+// A velocity space on the base grid.
+struct SpaceRt {
+  std::vector<int> keff;     // consistent coarsening index per 2x2 block
   VSpace vs;
-  DevBuf vt;        // [4][nv] compute type
-  DevBuf ax;        // [2][nax] one axis of a tensor-product space (compute type)
-  int uniform_L = -1;
-  StepConst k;
-  std::vector<LevelInst> inst;
+  std::vector<int> owner;    // base node -> point
+  int nax = 0;               // > 0: tensor product of one axis of nax points
+  DevBuf vt, ax, ainv;
 };
 
-}  // namespace
+struct CSR {
+  DevBuf off, idx, wgt;
+};
+
+// A level: the cells that carry their distributions on one space, or (real = false) a
+// cell-less face level for cross-level faces whose common refinement is no cell level.
+struct LevelRt {
+  int space = 0;
+  bool real = true;
+  std::vector<int> cells;    // global cell id of every slot
+  StepConst k;
+  DevBuf f[2], prm[2], fprm, cpart, fpart, ids, frole, fslot, ghost_of, ghost, X, Y, tiles;
+  int nghost = 0, nX = 0, nY = 0, ntiles = 0;
+  int cur = 0, pcur = 0;
+  bool fresh = false;
+  std::vector<int> ghost_cells;
+};
+
+struct Route {               // mapped items from level src to level dst
+  int src, dst;
+  std::vector<MapItem> items;
+  DevBuf items_d;
+};
+
+struct Inst {
+  std::vector<LevelRt> lv;   // cell levels first (ids 0..n_levels-1), face levels after
+  std::vector<int> lvl_of, slot_of;
+  DevBuf lvl_of_d, slot_of_d, ucell, W, err;
+  std::vector<Route> ghosts, fluxes;
+  std::vector<int> order;    // levels by decreasing velocity count
+};
 
 // Event pairs recorded around launches when a step is profiled.
 struct Prof {
@@ -88,6 +130,8 @@ struct Prof {
   }
 };
 
+}  // namespace
+
 struct mlvs_handle {
   mlvs_config cfg;
   Prof prof;
@@ -101,7 +145,14 @@ struct mlvs_handle {
   GasDev gas{};
   int tsize = 8;    // sizeof compute type
   int ssize = 4;    // sizeof storage type
-  std::vector<LevelData> lv;
+  Base1D base;
+  int n_base = 0;
+  std::vector<SpaceRt> spaces;
+  std::map<std::vector<int>, int> space_of_key;
+  std::map<std::pair<int, int>, CSR> csr;
+  int n_levels = 0;
+  std::vector<int> level_space;   // space of every cell level
+  std::vector<Inst> inst;
   bool ready = false;
   int sticky = MLVS_OK;
   std::string err;
@@ -109,11 +160,8 @@ struct mlvs_handle {
 };
 
 static mlvs_status fail(mlvs_handle* h, mlvs_status s, const std::string& msg) {
-  if (h) {
-    h->err = msg;
-  } else {
-    g_create_error = msg;
-  }
+  if (h) h->err = msg;
+  else g_create_error = msg;
   return s;
 }
 
@@ -124,17 +172,156 @@ static mlvs_status fail(mlvs_handle* h, mlvs_status s, const std::string& msg) {
       return fail(h, MLVS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+namespace {
+
+constexpr int kTX2 = 32, kTY2 = 8, kTX1 = 128;
+int tile_w(int D) { return D == 2 ? kTX2 : kTX1; }
+int tile_h(int D) { return D == 2 ? kTY2 : 1; }
+
+double vhs_mu_ref(double Kn, double omega, double rho_ref, double R, double T_ref, double L_ref) {
+  const double alpha = 1.0;
+  const double c = 5.0 * (alpha + 1.0) * (alpha + 2.0) * std::sqrt(M_PI) /
+                   (4.0 * alpha * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
+  return c * Kn * rho_ref * std::sqrt(2.0 * R * T_ref) * L_ref;
+}
+
+// Inverse of the T-independent four-moment mapping matrix of a space (raw basis, unit
+// weighting): rows (sum w phi, sum w xi_x phi, sum w xi_y phi, 1/2 sum w xi^2 phi),
+// phi = (1, xi_x, xi_y, xi^2).  In 1-D the y row/column is the identity.
+bool mapping_inverse(const VSpace& vs, int D, double inv[16]) {
+  double A[4][4] = {{0}};
+  for (int v = 0; v < vs.nv(); ++v) {
+    const double w = vs.wx[v] * vs.wy[v], x = vs.xix[v], y = vs.xiy[v], x2 = x * x + y * y;
+    const double phi[4] = {1.0, x, y, x2};
+    const double psi[4] = {1.0, x, y, 0.5 * x2};
+    for (int r = 0; r < 4; ++r)
+      for (int c = 0; c < 4; ++c) A[r][c] += w * psi[r] * phi[c];
+  }
+  if (D == 1) {
+    for (int c = 0; c < 4; ++c) { A[2][c] = 0.0; A[c][2] = 0.0; }
+    A[2][2] = 1.0;
+  }
+  double M[4][8];
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 8; ++c) M[r][c] = (c < 4) ? A[r][c] : (c - 4 == r ? 1.0 : 0.0);
+  for (int c = 0; c < 4; ++c) {
+    int p = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
+    if (!(std::fabs(M[p][c]) > 1e-300)) return false;
+    for (int j = 0; j < 8; ++j) std::swap(M[c][j], M[p][j]);
+    const double d = M[c][c];
+    for (int j = 0; j < 8; ++j) M[c][j] /= d;
+    for (int r = 0; r < 4; ++r)
+      if (r != c) {
+        const double f = M[r][c];
+        for (int j = 0; j < 8; ++j) M[r][j] -= f * M[c][j];
+      }
+  }
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) inv[4 * r + c] = M[r][4 + c];
+  return true;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// spaces and projection tables
+
+static mlvs_status get_space(mlvs_handle* h, const std::vector<int>& kappa, int* out) {
+  std::vector<int> keff = enforce_consistency(kappa, h->n_base, h->D);
+  auto it = h->space_of_key.find(keff);
+  if (it != h->space_of_key.end()) { *out = it->second; return MLVS_OK; }
+  SpaceRt S;
+  S.keff = keff;
+  S.vs = kappa_vspace(h->base, h->D, keff, S.owner);
+  bool uni = true;
+  for (int x : keff) uni = uni && (x == keff[0]);
+  std::vector<double> axd;
+  if (uni) {
+    auto gr = groups_1d(h->n_base, keff[0]);
+    S.nax = (int)gr.size();
+    axd.resize(2 * gr.size());
+    for (size_t g = 0; g < gr.size(); ++g) merged(h->base, gr[g].first, gr[g].second, axd[g], axd[gr.size() + g]);
+  }
+  const int nv = S.vs.nv();
+  std::vector<double> vt(4 * (size_t)nv);
+  for (int v = 0; v < nv; ++v) {
+    vt[v] = S.vs.xix[v];
+    vt[nv + v] = S.vs.xiy[v];
+    vt[2 * nv + v] = S.vs.wx[v];
+    vt[3 * nv + v] = S.vs.wy[v];
+  }
+  std::vector<double> inv(16);
+  if (!mapping_inverse(S.vs, h->D, inv.data())) return fail(h, MLVS_ERR_SINGULAR, "singular mapping matrix");
+  if (h->tsize == 8) {
+    CK(upload(S.vt, vt, h->stream));
+    CK(upload(S.ax, axd, h->stream));
+  } else {
+    CK(upload(S.vt, std::vector<float>(vt.begin(), vt.end()), h->stream));
+    CK(upload(S.ax, std::vector<float>(axd.begin(), axd.end()), h->stream));
+  }
+  CK(upload(S.ainv, inv, h->stream));
+  h->spaces.push_back(std::move(S));
+  *out = (int)h->spaces.size() - 1;
+  h->space_of_key[keff] = *out;
+  return MLVS_OK;
+}
+
+// Projection table P_{s->t} (Sec. 3.3.2): every target point inherits from the one source
+// point containing it (refinement) or averages the source points it is made of (coarsening).
+static mlvs_status get_csr(mlvs_handle* h, int s, int t, CSR** out) {
+  auto key = std::make_pair(s, t);
+  auto it = h->csr.find(key);
+  if (it != h->csr.end()) { *out = &it->second; return MLVS_OK; }
+  const SpaceRt& S = h->spaces[s];
+  const SpaceRt& Tt = h->spaces[t];
+  const int n = h->n_base;
+  std::vector<int> off(1, 0), idx;
+  std::vector<double> wgt;
+  for (int i = 0; i < Tt.vs.nv(); ++i) {
+    const int xa = Tt.vs.rect[4 * i], xb = Tt.vs.rect[4 * i + 1];
+    const int ya = Tt.vs.rect[4 * i + 2], yb = Tt.vs.rect[4 * i + 3];
+    std::vector<int> own;
+    for (int iy = ya; iy < yb; ++iy)
+      for (int ix = xa; ix < xb; ++ix) own.push_back(S.owner[(h->D == 2 ? iy * n : 0) + ix]);
+    std::sort(own.begin(), own.end());
+    own.erase(std::unique(own.begin(), own.end()), own.end());
+    if (own.size() == 1) {
+      idx.push_back(own[0]);
+      wgt.push_back(1.0);
+    } else {
+      double area = 0.0;
+      for (int o : own) area += S.vs.w[o];
+      if (std::fabs(area - Tt.vs.w[i]) > 1e-10 * Tt.vs.w[i])
+        return fail(h, MLVS_ERR_ARG, "velocity spaces are not nested");
+      for (int o : own) { idx.push_back(o); wgt.push_back(S.vs.w[o] / area); }
+    }
+    off.push_back((int)idx.size());
+  }
+  CSR c;
+  CK(upload(c.off, off, h->stream));
+  CK(upload(c.idx, idx, h->stream));
+  if (h->tsize == 8) { CK(upload(c.wgt, wgt, h->stream)); }
+  else { CK(upload(c.wgt, std::vector<float>(wgt.begin(), wgt.end()), h->stream)); }
+  auto res = h->csr.emplace(key, std::move(c));
+  *out = &res.first->second;
+  return MLVS_OK;
+}
+
 // ---------------------------------------------------------------------------------------
 // typed launchers
 
 namespace {
 
 template <class S, class T, int D> struct Runner {
-  static constexpr int TX = (D == 2) ? 32 : 128;
-  static constexpr int TY = (D == 2) ? 8 : 1;
+  static constexpr int TX = (D == 2) ? kTX2 : kTX1;
+  static constexpr int TY = (D == 2) ? kTY2 : 1;
   static constexpr int VB = 2;   // velocities per barrier round
   static constexpr size_t SM0 = TileSmem<T, TX, TY, D, VB, 0>::BYTES;
   static constexpr size_t SM1 = TileSmem<T, TX, TY, D, VB, 1>::BYTES;
+  static constexpr int FIN_BLOCK = 64;
+  static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
 
   static cudaError_t set_smem_limits() {
     cudaError_t e = cudaFuncSetAttribute(k_tile<S, T, D, TX, TY, VB, 0>,
@@ -144,53 +331,6 @@ template <class S, class T, int D> struct Runner {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
   }
 
-  static void tiles(const StepConst& k, int& ntx, int& nty) {
-    ntx = (k.nx + TX - 1) / TX;
-    nty = (D == 2) ? (k.ny + TY - 1) / TY : 1;
-  }
-
-  static PointArgs pargs(mlvs_handle* h, LevelData& L, LevelInst& I, bool face) {
-    PointArgs a;
-    a.k = L.k;
-    a.gas = h->gas;
-    a.is_face = face ? 1 : 0;
-    a.npt = face ? L.k.nface : L.k.ncell;
-    a.part = face ? I.fpart.as<double>() : I.cpart.as<double>();
-    a.vt = L.vt.p;
-    a.ax = L.ax.p;
-    a.compat = face ? h->cfg.compat_face : h->cfg.compat_cell;
-    for (int s = 0; s < 4; ++s)
-      for (int j = 0; j < 3; ++j) a.wall[s][j] = h->cfg.wall[s][j];
-    a.err = I.err.as<int>();
-    a.W = nullptr;
-    a.cprm = nullptr;
-    a.prm_out = nullptr;
-    return a;
-  }
-
-  // finalisation: one thread per point
-  static constexpr int FIN_BLOCK = 64;
-  static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
-
-  static cudaError_t init(mlvs_handle* h, LevelData& L, LevelInst& I, const double* dW0) {
-    cudaError_t es = set_smem_limits();
-    if (es != cudaSuccess) return es;
-    PointArgs a = pargs(h, L, I, false);
-    a.compat = h->cfg.compat_cell;
-    a.prm_out = I.prm[0].p;
-    k_init_params<T, D><<<fin_grid(L.k.ncell), FIN_BLOCK, 0, h->stream>>>(a, dW0);
-    dim3 g((L.k.ncell + 127) / 128, std::min(L.k.nv, 1024));
-    k_init_f<S, T, D><<<g, 128, 0, h->stream>>>(L.k, I.prm[0].as<T>(), L.vt.as<T>(), I.f[0].as<S>());
-    dim3 gm((L.k.ncell + 127) / 128, L.k.nchunk);
-    k_moments<S, T, D><<<gm, 128, 0, h->stream>>>(L.k, I.prm[0].as<T>(), L.vt.as<T>(), I.f[0].as<S>(),
-                                                   I.cpart.as<double>());
-    I.cur = 0;
-    I.pcur = 0;
-    I.fresh = false;
-    return cudaGetLastError();
-  }
-
-  // profiling marks around a launch of phase ph
   static void mark_begin(mlvs_handle* h, int ph) {
     ++h->launches;
     if (!h->profiling) return;
@@ -202,71 +342,276 @@ template <class S, class T, int D> struct Runner {
     cudaEventRecord(h->prof.next(), h->stream);
   }
 
-  // cell finalisation into prm[pcur^1]; afterwards pcur flips and fresh = true
-  static cudaError_t finalize_cells(mlvs_handle* h, LevelData& L, LevelInst& I) {
-    PointArgs a = pargs(h, L, I, false);
-    a.cprm = I.prm[I.pcur].p;
-    a.prm_out = I.prm[I.pcur ^ 1].p;
-    a.W = I.W.as<double>();
-    mark_begin(h, 0);
-    k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
-    mark_end(h);
-    I.pcur ^= 1;
-    I.fresh = true;
-    return cudaGetLastError();
+  static PointArgs pargs(mlvs_handle* h, Inst& I, LevelRt& L, bool face) {
+    PointArgs a;
+    a.k = L.k;
+    a.gas = h->gas;
+    a.is_face = face ? 1 : 0;
+    a.npt = face ? L.k.nface : (int)L.cells.size();
+    a.part = face ? L.fpart.as<double>() : L.cpart.as<double>();
+    const SpaceRt& sp = h->spaces[L.space];
+    a.vt = sp.vt.p;
+    a.ax = sp.ax.p;
+    a.ids = L.ids.as<int>();
+    a.frole = L.frole.as<unsigned char>();
+    a.ucell = I.ucell.p;
+    a.compat = face ? h->cfg.compat_face : h->cfg.compat_cell;
+    for (int s = 0; s < 4; ++s)
+      for (int j = 0; j < 3; ++j) a.wall[s][j] = h->cfg.wall[s][j];
+    a.err = I.err.as<int>();
+    a.W = nullptr;
+    a.cprm = nullptr;
+    a.prm_out = nullptr;
+    return a;
   }
 
-  static cudaError_t step(mlvs_handle* h, LevelData& L, LevelInst& I, int limiter) {
-    cudaError_t e;
-    if (!I.fresh) {
-      e = finalize_cells(h, L, I);
-      if (e != cudaSuccess) return e;
-    }
+  static TileArgs targs(mlvs_handle* h, Inst& I, LevelRt& L, int lid) {
     TileArgs t;
     t.k = L.k;
-    tiles(L.k, t.ntx, t.nty);
-    t.f_in = I.f[I.cur].p;
-    t.f_out = I.f[I.cur ^ 1].p;
-    t.cparam = I.prm[I.pcur].p;
-    t.fparam = I.fprm.p;
-    t.vt = L.vt.p;
-    dim3 grid(t.ntx * t.nty, L.k.nchunk);
-    t.part = I.fpart.as<double>();
-    mark_begin(h, 1);
-    k_tile<S, T, D, TX, TY, VB, 0><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+    const int nc = (int)L.cells.size();
+    t.f_in = L.f[L.cur].p;
+    t.f_out = L.f[L.cur ^ 1].p;
+    t.nslot = nc;
+    t.cparam = L.prm[L.pcur].p;
+    t.fparam = L.fprm.p;
+    t.vt = h->spaces[L.space].vt.p;
+    t.part = nullptr;
+    t.tiles = L.tiles.as<int>();
+    t.ntx = (h->nx + TX - 1) / TX;
+    t.nty = (D == 2) ? (h->ny + TY - 1) / TY : 1;
+    t.level = lid;
+    t.lvl_of = I.lvl_of_d.as<int>();
+    t.slot_of = I.slot_of_d.as<int>();
+    t.ghost_of = L.nghost ? L.ghost_of.as<int>() : nullptr;
+    t.ghost = L.ghost.p;
+    t.nghost = L.nghost;
+    t.frole = L.frole.as<unsigned char>();
+    t.fslot = L.fslot.as<int>();
+    t.X = L.X.p;
+    t.nX = L.nX;
+    t.Y = L.Y.p;
+    t.nY = L.nY;
+    t.ucell = I.ucell.p;
+    return t;
+  }
+
+  // cells of one level: params into prm[pcur^1], W and the cell velocities
+  static cudaError_t finalize_cells(mlvs_handle* h, Inst& I, LevelRt& L) {
+    const int n = (int)L.cells.size();
+    if (n == 0) { L.fresh = true; return cudaSuccess; }
+    PointArgs a = pargs(h, I, L, false);
+    a.cprm = L.prm[L.pcur].p;
+    a.prm_out = L.prm[L.pcur ^ 1].p;
+    a.W = I.W.as<double>();
+    mark_begin(h, 0);
+    k_finalize<T, D><<<fin_grid(n), FIN_BLOCK, 0, h->stream>>>(a);
+    k_scatter_velocity<T><<<(n + 127) / 128, 128, 0, h->stream>>>(L.prm[L.pcur ^ 1].as<T>(), n, L.ids.as<int>(),
+                                                                 I.ucell.as<T>(), h->nx * h->ny);
     mark_end(h);
-    PointArgs a = pargs(h, L, I, true);
-    a.cprm = I.prm[I.pcur].p;
-    a.prm_out = I.fprm.p;
-    mark_begin(h, 2);
-    k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
-    mark_end(h);
-    t.part = I.cpart.as<double>();
-    mark_begin(h, 3);
-    k_tile<S, T, D, TX, TY, VB, 1><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
-    mark_end(h);
-    I.cur ^= 1;
-    I.fresh = false;
+    L.pcur ^= 1;
+    L.fresh = true;
     return cudaGetLastError();
   }
 
-  static int tile_ctas(const StepConst& k) {
-    int ntx, nty;
-    tiles(k, ntx, nty);
-    return ntx * nty;
+  static MapArgs margs(mlvs_handle* h, int s, int t, CSR* c) {
+    MapArgs m;
+    const SpaceRt& Ss = h->spaces[s];
+    const SpaceRt& St = h->spaces[t];
+    m.s.nv = Ss.vs.nv(); m.s.vt = Ss.vt.p; m.s.ainv = Ss.ainv.as<double>();
+    m.t.nv = St.vs.nv(); m.t.vt = St.vt.p; m.t.ainv = St.ainv.as<double>();
+    m.off = c->off.as<int>();
+    m.idx = c->idx.as<int>();
+    m.wgt = c->wgt.p;
+    m.R = h->gas.R;
+    m.c0 = h->gas.K + 3.0 - D;
+    m.cv = 0.5 * (3.0 + h->gas.K) * h->gas.R;
+    m.twoK = 2.0 * h->gas.K;
+    m.correct = 1;
+    return m;
+  }
+
+  static int map_grid(int n) { return std::max(1, std::min(n, 148 * 8)); }
+
+  static cudaError_t run_ghosts(mlvs_handle* h, Inst& I) {
+    for (auto& r : I.ghosts) {
+      if (r.items.empty()) continue;
+      LevelRt& Ls = I.lv[r.src];
+      LevelRt& Ld = I.lv[r.dst];
+      CSR* c = nullptr;
+      if (get_csr(h, Ls.space, Ld.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
+      MapArgs m = margs(h, Ls.space, Ld.space, c);
+      m.src = Ls.f[Ls.cur].p;
+      m.src_ld = (int)Ls.cells.size();
+      m.dst = Ld.ghost.p;
+      m.dst_ld = Ld.nghost;
+      m.prm = Ls.prm[Ls.pcur].p;
+      m.prm_ld = (int)Ls.cells.size();
+      m.items = r.items_d.as<MapItem>();
+      m.nitems = (int)r.items.size();
+      mark_begin(h, 4);
+      k_map<S, T, T, D, SRC_BARP><<<map_grid(m.nitems), 256, 0, h->stream>>>(m);
+      mark_end(h);
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t run_fluxes(mlvs_handle* h, Inst& I, int src) {
+    for (auto& r : I.fluxes) {
+      if (r.src != src || r.items.empty()) continue;
+      LevelRt& Ls = I.lv[r.src];
+      LevelRt& Ld = I.lv[r.dst];
+      CSR* c = nullptr;
+      if (get_csr(h, Ls.space, Ld.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
+      MapArgs m = margs(h, Ls.space, Ld.space, c);
+      m.src = Ls.X.p;
+      m.src_ld = Ls.nX;
+      m.dst = Ld.Y.p;
+      m.dst_ld = Ld.nY;
+      m.prm = Ls.fprm.p;
+      m.prm_ld = Ls.k.nface;
+      m.items = r.items_d.as<MapItem>();
+      m.nitems = (int)r.items.size();
+      mark_begin(h, 5);
+      k_map<T, T, T, D, SRC_FLUX><<<map_grid(m.nitems), 256, 0, h->stream>>>(m);
+      mark_end(h);
+    }
+    return cudaGetLastError();
+  }
+
+  static cudaError_t step(mlvs_handle* h, Inst& I) {
+    cudaError_t e;
+    for (int l = 0; l < h->n_levels; ++l)
+      if (!I.lv[l].fresh && (e = finalize_cells(h, I, I.lv[l])) != cudaSuccess) return e;
+    if ((e = run_ghosts(h, I)) != cudaSuccess) return e;
+    const int limiter = h->cfg.limiter;
+    for (int l = 0; l < (int)I.lv.size(); ++l) {
+      LevelRt& L = I.lv[l];
+      if (L.ntiles == 0) continue;
+      TileArgs t = targs(h, I, L, l);
+      t.part = L.fpart.as<double>();
+      dim3 grid(L.ntiles, L.k.nchunk);
+      mark_begin(h, 1);
+      k_tile<S, T, D, TX, TY, VB, 0><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+      mark_end(h);
+    }
+    for (int l = 0; l < (int)I.lv.size(); ++l) {
+      LevelRt& L = I.lv[l];
+      if (L.ntiles == 0) continue;
+      PointArgs a = pargs(h, I, L, true);
+      a.cprm = L.prm[L.pcur].p;
+      a.prm_out = L.fprm.p;
+      mark_begin(h, 2);
+      k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+      mark_end(h);
+    }
+    for (int l : I.order) {
+      LevelRt& L = I.lv[l];
+      if (L.ntiles > 0) {
+        TileArgs t = targs(h, I, L, l);
+        t.part = L.cpart.as<double>();
+        dim3 grid(L.ntiles, L.k.nchunk);
+        mark_begin(h, 3);
+        k_tile<S, T, D, TX, TY, VB, 1><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
+        mark_end(h);
+      }
+      if ((e = run_fluxes(h, I, l)) != cudaSuccess) return e;
+    }
+    for (int l = 0; l < h->n_levels; ++l) {
+      LevelRt& L = I.lv[l];
+      if (L.cells.empty()) continue;
+      L.cur ^= 1;
+      L.fresh = false;
+    }
+    return cudaGetLastError();
+  }
+
+  // parameters from (rho, u, v, T) with q = 0 and phi~ = the corrected Maxwellian (level 0)
+  static cudaError_t init_state(mlvs_handle* h, Inst& I, const double* dW0) {
+    cudaError_t e = set_smem_limits();
+    if (e != cudaSuccess) return e;
+    LevelRt& L = I.lv[0];
+    const int n = (int)L.cells.size();
+    PointArgs a = pargs(h, I, L, false);
+    a.prm_out = L.prm[0].p;
+    k_init_params<T, D><<<fin_grid(n), FIN_BLOCK, 0, h->stream>>>(a, dW0);
+    dim3 g((n + 127) / 128, std::min(L.k.nv, 1024));
+    k_init_f<S, T, D><<<g, 128, 0, h->stream>>>(L.k, n, L.prm[0].as<T>(), h->spaces[L.space].vt.as<T>(),
+                                                 L.f[0].as<S>());
+    k_scatter_velocity<T><<<(n + 127) / 128, 128, 0, h->stream>>>(L.prm[0].as<T>(), n, L.ids.as<int>(),
+                                                                 I.ucell.as<T>(), h->nx * h->ny);
+    L.cur = 0;
+    L.pcur = 0;
+    return moments_of_levels(h, I);
+  }
+
+  // chunk partials of every cell level from f[cur] in the frame of the cell velocities
+  static cudaError_t moments_of_levels(mlvs_handle* h, Inst& I) {
+    for (int l = 0; l < h->n_levels; ++l) {
+      LevelRt& L = I.lv[l];
+      const int n = (int)L.cells.size();
+      if (n == 0) continue;
+      k_set_shift<T><<<(n + 127) / 128, 128, 0, h->stream>>>(L.prm[L.pcur].as<T>(), n, L.ids.as<int>(),
+                                                            I.ucell.as<T>(), h->nx * h->ny);
+      dim3 gm((n + 127) / 128, L.k.nchunk);
+      k_moments<S, T, D><<<gm, 128, 0, h->stream>>>(L.k, n, L.prm[L.pcur].as<T>(), h->spaces[L.space].vt.as<T>(),
+                                                     L.f[L.cur].as<S>(), L.cpart.as<double>());
+      L.fresh = false;
+    }
+    return cudaGetLastError();
+  }
+
+  // move every cell's phi~ from the old levels to the new ones (copy or level switch)
+  static cudaError_t transfer(mlvs_handle* h, Inst& Old, Inst& New) {
+    const int ncell = h->nx * h->ny;
+    std::map<std::pair<int, int>, std::vector<MapItem>> groups;
+    for (int c = 0; c < ncell; ++c) {
+      const int lo = Old.lvl_of[c], ln = New.lvl_of[c];
+      groups[{lo, ln}].push_back({Old.slot_of[c], New.slot_of[c], Old.slot_of[c]});
+    }
+    for (auto& g : groups) {
+      LevelRt& Lo = Old.lv[g.first.first];
+      LevelRt& Ln = New.lv[g.first.second];
+      DevBuf items;
+      cudaError_t e = upload(items, g.second, h->stream);
+      if (e != cudaSuccess) return e;
+      const int ni = (int)g.second.size();
+      if (Lo.space == Ln.space) {
+        k_copy_cols<S><<<map_grid(ni), 256, 0, h->stream>>>(Lo.f[Lo.cur].as<S>(), (int)Lo.cells.size(),
+                                                          Ln.f[0].as<S>(), (int)Ln.cells.size(), 2 * Ln.k.nv,
+                                                          items.as<MapItem>(), ni);
+      } else {
+        CSR* c = nullptr;
+        if (get_csr(h, Lo.space, Ln.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
+        MapArgs m = margs(h, Lo.space, Ln.space, c);
+        m.src = Lo.f[Lo.cur].p;
+        m.src_ld = (int)Lo.cells.size();
+        m.dst = Ln.f[0].p;
+        m.dst_ld = (int)Ln.cells.size();
+        m.prm = nullptr;
+        m.prm_ld = 0;
+        m.items = items.as<MapItem>();
+        m.nitems = ni;
+        k_map<S, S, T, D, SRC_TILDE><<<map_grid(ni), 256, 0, h->stream>>>(m);
+      }
+      e = cudaStreamSynchronize(h->stream);   // items freed at scope end
+      if (e != cudaSuccess) return e;
+    }
+    for (auto& L : New.lv) { L.cur = 0; L.pcur = 0; }
+    return cudaGetLastError();
   }
 };
 
 struct Ops {
-  cudaError_t (*init)(mlvs_handle*, LevelData&, LevelInst&, const double*);
-  cudaError_t (*finalize_cells)(mlvs_handle*, LevelData&, LevelInst&);
-  cudaError_t (*step)(mlvs_handle*, LevelData&, LevelInst&, int);
-  int (*tile_ctas)(const StepConst&);
+  cudaError_t (*init_state)(mlvs_handle*, Inst&, const double*);
+  cudaError_t (*finalize_cells)(mlvs_handle*, Inst&, LevelRt&);
+  cudaError_t (*step)(mlvs_handle*, Inst&);
+  cudaError_t (*transfer)(mlvs_handle*, Inst&, Inst&);
+  cudaError_t (*moments_of_levels)(mlvs_handle*, Inst&);
 };
 
 template <class S, class T, int D> Ops make_ops() {
-  return Ops{&Runner<S, T, D>::init, &Runner<S, T, D>::finalize_cells, &Runner<S, T, D>::step,
-             &Runner<S, T, D>::tile_ctas};
+  using R = Runner<S, T, D>;
+  return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels};
 }
 
 Ops ops_for(int storage, int D) {
@@ -275,14 +620,230 @@ Ops ops_for(int storage, int D) {
   return D == 2 ? make_ops<__nv_bfloat16, float, 2>() : make_ops<__nv_bfloat16, float, 1>();
 }
 
-double vhs_mu_ref(double Kn, double omega, double rho_ref, double R, double T_ref, double L_ref) {
-  const double alpha = 1.0;
-  const double c = 5.0 * (alpha + 1.0) * (alpha + 2.0) * std::sqrt(M_PI) /
-                   (4.0 * alpha * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
-  return c * Kn * rho_ref * std::sqrt(2.0 * R * T_ref) * L_ref;
+int choose_vpc(int tile_ctas, int nv) {
+  // about four CTAs per SM of the 148, at most 384 velocities per chunk
+  const int target = 148 * 4;
+  int nchunk = std::max(1, (target + std::max(tile_ctas, 1) - 1) / std::max(tile_ctas, 1));
+  nchunk = std::min(nchunk, nv);
+  int vpc = (nv + nchunk - 1) / nchunk;
+  return std::max(1, std::min(vpc, 384));
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------------------------------
+// level structure of one instance
+
+static int wrapc(int g, int n, int periodic) {
+  if (periodic) { g %= n; return g < 0 ? g + n : g; }
+  return g < 0 ? 0 : (g >= n ? n - 1 : g);
+}
+
+// Build the level structure of an instance for a cell -> level assignment (host only).
+static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, Inst& I) {
+  const int D = h->D, nx = h->nx, ny = h->ny, ncell = nx * ny;
+  const int px = h->cfg.bc[0] == MLVS_BC_PERIODIC;
+  const int py = D == 2 ? (h->cfg.bc[2] == MLVS_BC_PERIODIC) : 1;
+  const int nfx = px ? nx : nx + 1;
+  const int nfy = D == 2 ? (py ? ny : ny + 1) : 0;
+  const int nface = nfx * ny + (D == 2 ? nx * nfy : 0);
+  const int TX = tile_w(D), TY = tile_h(D);
+  const int ntx = (nx + TX - 1) / TX;
+  I.lvl_of = lvl_of;
+  I.slot_of.assign(ncell, -1);
+  I.lv.clear();
+  I.lv.resize(h->n_levels);
+  for (int l = 0; l < h->n_levels; ++l) I.lv[l].space = h->level_space[l];
+  for (int c = 0; c < ncell; ++c) {
+    const int l = lvl_of[c];
+    I.slot_of[c] = (int)I.lv[l].cells.size();
+    I.lv[l].cells.push_back(c);
+  }
+  // faces: roles, cross-level routes
+  std::map<int, int> face_level_of_space;   // face levels (no cells) by space
+  std::vector<std::vector<unsigned char>> role(h->n_levels);
+  std::vector<std::vector<int>> slot(h->n_levels);
+  auto ensure = [&](int l) {
+    if ((int)role.size() <= l) { role.resize(l + 1); slot.resize(l + 1); }
+    if (role[l].empty()) { role[l].assign(nface, FR_NONE); slot[l].assign(nface, -1); }
+  };
+  for (int l = 0; l < h->n_levels; ++l) ensure(l);
+  std::vector<int> nX, nY;
+  auto bump = [&](std::vector<int>& v, int l) { if ((int)v.size() <= l) v.resize(l + 1, 0); return v[l]++; };
+  std::map<std::pair<int, int>, std::vector<MapItem>> flux_items;
+  std::vector<std::array<int, 3>> face_cells(nface);   // cL, cR, wall-side (-1 none)
+  for (int f = 0; f < nface; ++f) {
+    int cL, cR, wall = -1;
+    if (f < nfx * ny) {
+      const int gj = f / nfx, gi = f % nfx;
+      cL = wrapc(gj, ny, py) * nx + wrapc(gi - 1, nx, px);
+      cR = wrapc(gj, ny, py) * nx + wrapc(gi, nx, px);
+      if (!px && gi == 0 && h->cfg.bc[0] == MLVS_BC_WALL) wall = 0;
+      if (!px && gi == nx && h->cfg.bc[1] == MLVS_BC_WALL) wall = 1;
+    } else {
+      const int r = f - nfx * ny, gj = r / nx, gi = r % nx;
+      cL = wrapc(gj - 1, ny, py) * nx + gi;
+      cR = wrapc(gj, ny, py) * nx + gi;
+      if (!py && gj == 0 && h->cfg.bc[2] == MLVS_BC_WALL) wall = 2;
+      if (!py && gj == ny && h->cfg.bc[3] == MLVS_BC_WALL) wall = 3;
+    }
+    face_cells[f] = {cL, cR, wall};
+    const int lL = lvl_of[cL], lR = lvl_of[cR];
+    if (wall >= 0) {
+      const int c = (wall == 0 || wall == 2) ? cR : cL;
+      role[lvl_of[c]][f] = FR_NORMAL;
+      continue;
+    }
+    if (lL == lR) { role[lL][f] = FR_NORMAL; continue; }
+    // cross-level face: evaluated on the common refinement of the two spaces (Sec. 3.4)
+    const SpaceRt& SL = h->spaces[h->level_space[lL]];
+    const SpaceRt& SR = h->spaces[h->level_space[lR]];
+    std::vector<int> km(SL.keff.size());
+    for (size_t b = 0; b < km.size(); ++b) km[b] = std::min(SL.keff[b], SR.keff[b]);
+    int sf;
+    mlvs_status st = get_space(h, km, &sf);
+    if (st != MLVS_OK) return st;
+    int lf;
+    if (sf == h->level_space[lL]) lf = lL;
+    else if (sf == h->level_space[lR]) lf = lR;
+    else {
+      auto it = face_level_of_space.find(sf);
+      if (it == face_level_of_space.end()) {
+        lf = (int)I.lv.size();
+        I.lv.emplace_back();
+        I.lv[lf].space = sf;
+        I.lv[lf].real = false;
+        face_level_of_space[sf] = lf;
+      } else {
+        lf = it->second;
+      }
+    }
+    ensure(lf);
+    role[lf][f] = FR_CROSS;
+    slot[lf][f] = bump(nX, lf);
+    for (int c : {cL, cR}) {
+      const int lc = lvl_of[c];
+      if (lc == lf) continue;
+      if (role[lc][f] == FR_RECV) continue;       // both sides on one level
+      role[lc][f] = FR_RECV;
+      slot[lc][f] = bump(nY, lc);
+      flux_items[{lf, lc}].push_back({slot[lf][f], slot[lc][f], f});
+    }
+  }
+  const int nlev = (int)I.lv.size();
+  nX.resize(nlev, 0);
+  nY.resize(nlev, 0);
+  // ghosts: stencil cells of the faces evaluated on a level that live on another level
+  std::vector<std::vector<int>> ghost_col(nlev);
+  for (int l = 0; l < nlev; ++l) {
+    std::set<int> gset;
+    for (int f = 0; f < nface; ++f) {
+      if (role[l][f] != FR_NORMAL && role[l][f] != FR_CROSS) continue;
+      std::vector<int> st;
+      if (f < nfx * ny) {
+        const int gj = f / nfx, gi = f % nfx;
+        for (int d = -2; d <= 1; ++d) st.push_back(wrapc(gj, ny, py) * nx + wrapc(gi + d, nx, px));
+        if (D == 2)
+          for (int d : {-1, 1})
+            for (int e : {-1, 0}) st.push_back(wrapc(gj + d, ny, py) * nx + wrapc(gi + e, nx, px));
+      } else {
+        const int r = f - nfx * ny, gj = r / nx, gi = r % nx;
+        for (int d = -2; d <= 1; ++d) st.push_back(wrapc(gj + d, ny, py) * nx + gi);
+        for (int d : {-1, 1})
+          for (int e : {-1, 0}) st.push_back(wrapc(gj + e, ny, py) * nx + wrapc(gi + d, nx, px));
+      }
+      for (int c : st)
+        if (lvl_of[c] != l) gset.insert(c);
+    }
+    I.lv[l].ghost_cells.assign(gset.begin(), gset.end());
+    ghost_col[l].assign(ncell, -1);
+    for (size_t g = 0; g < I.lv[l].ghost_cells.size(); ++g) ghost_col[l][I.lv[l].ghost_cells[g]] = (int)g;
+    I.lv[l].nghost = (int)I.lv[l].ghost_cells.size();
+  }
+  // routes
+  I.ghosts.clear();
+  for (int l = 0; l < nlev; ++l) {
+    std::map<int, std::vector<MapItem>> by_src;
+    for (size_t g = 0; g < I.lv[l].ghost_cells.size(); ++g) {
+      const int c = I.lv[l].ghost_cells[g];
+      by_src[lvl_of[c]].push_back({I.slot_of[c], (int)g, I.slot_of[c]});
+    }
+    for (auto& s : by_src) {
+      Route r;
+      r.src = s.first;
+      r.dst = l;
+      r.items = s.second;
+      I.ghosts.push_back(std::move(r));
+    }
+  }
+  I.fluxes.clear();
+  for (auto& fi : flux_items) {
+    Route r;
+    r.src = fi.first.first;
+    r.dst = fi.first.second;
+    r.items = fi.second;
+    I.fluxes.push_back(std::move(r));
+  }
+  // tiles: tiles with a cell of the level or owning a face evaluated on it
+  for (int l = 0; l < nlev; ++l) {
+    std::set<int> ts;
+    for (int c : I.lv[l].cells) ts.insert(((c / nx) / TY) * ntx + (c % nx) / TX);
+    for (int f = 0; f < nface; ++f) {
+      if (role[l][f] == FR_NONE) continue;
+      int col, row;
+      if (f < nfx * ny) { row = f / nfx; col = std::min(f % nfx, nx - 1); }
+      else { const int r = f - nfx * ny; col = r % nx; row = std::min(r / nx, ny - 1); }
+      ts.insert((row / TY) * ntx + col / TX);
+    }
+    std::vector<int> tl(ts.begin(), ts.end());
+    I.lv[l].ntiles = (int)tl.size();
+    I.lv[l].nX = nX[l];
+    I.lv[l].nY = nY[l];
+    LevelRt& L = I.lv[l];
+    StepConst& k = L.k;
+    k.nx = nx; k.ny = ny; k.px = px; k.py = py;
+    for (int s = 0; s < 4; ++s) k.bc[s] = h->cfg.bc[s];
+    if (D == 1) k.bc[2] = k.bc[3] = MLVS_BC_PERIODIC;
+    k.nfx = nfx; k.nfy = nfy; k.ncell = ncell; k.nface = nface;
+    const SpaceRt& sp = h->spaces[L.space];
+    k.nv = sp.vs.nv();
+    k.nax = sp.nax;
+    k.dx = h->dx; k.dy = h->dy; k.dt = h->dt;
+    k.c0 = h->gas.K + 3.0 - D;
+    k.twoK = 2.0 * h->gas.K;
+    k.vpc = choose_vpc(L.ntiles, k.nv);
+    k.nchunk = (k.nv + k.vpc - 1) / k.vpc;
+    // device tables
+    CK(upload(L.tiles, tl, h->stream));
+    CK(upload(L.ids, L.cells, h->stream));
+    CK(upload(L.frole, role[l], h->stream));
+    CK(upload(L.fslot, slot[l], h->stream));
+    CK(upload(L.ghost_of, ghost_col[l], h->stream));
+    const size_t nc = L.cells.size();
+    const size_t fbytes = 2ull * k.nv * nc * h->ssize;
+    if (L.f[0].alloc(fbytes) != cudaSuccess || L.f[1].alloc(fbytes) != cudaSuccess ||
+        L.prm[0].alloc((size_t)NP * std::max<size_t>(nc, 1) * h->tsize) != cudaSuccess ||
+        L.prm[1].alloc((size_t)NP * std::max<size_t>(nc, 1) * h->tsize) != cudaSuccess ||
+        L.fprm.alloc((size_t)NP * nface * h->tsize) != cudaSuccess ||
+        L.cpart.alloc((size_t)k.nchunk * NMOM * std::max<size_t>(nc, 1) * 8) != cudaSuccess ||
+        L.fpart.alloc((size_t)k.nchunk * NMOM * nface * 8) != cudaSuccess ||
+        L.ghost.alloc(2ull * k.nv * L.nghost * h->tsize) != cudaSuccess ||
+        L.X.alloc(2ull * k.nv * L.nX * h->tsize) != cudaSuccess ||
+        L.Y.alloc(2ull * k.nv * L.nY * h->tsize) != cudaSuccess)
+      return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
+    CK(cudaMemsetAsync(L.fprm.p, 0, L.fprm.n, h->stream));
+  }
+  for (auto& r : I.ghosts) CK(upload(r.items_d, r.items, h->stream));
+  for (auto& r : I.fluxes) CK(upload(r.items_d, r.items, h->stream));
+  I.order.resize(nlev);
+  for (int l = 0; l < nlev; ++l) I.order[l] = l;
+  std::stable_sort(I.order.begin(), I.order.end(), [&](int a, int b) {
+    return h->spaces[I.lv[a].space].vs.nv() > h->spaces[I.lv[b].space].vs.nv();
+  });
+  CK(upload(I.lvl_of_d, I.lvl_of, h->stream));
+  CK(upload(I.slot_of_d, I.slot_of, h->stream));
+  return MLVS_OK;
+}
 
 // ---------------------------------------------------------------------------------------
 
@@ -363,14 +924,19 @@ extern "C" mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt) {
   return MLVS_OK;
 }
 
-static int choose_chunks(int tile_ctas, int nv) {
-  // aim at about four CTAs per SM of the 148, with at most 384 velocities per chunk
-  const int target = 148 * 4;
-  int nchunk = std::max(1, (target + tile_ctas - 1) / tile_ctas);
-  nchunk = std::min(nchunk, nv);
-  int vpc = (nv + nchunk - 1) / nchunk;
-  vpc = std::min(vpc, 384);
-  return vpc;
+static mlvs_status check_flags(mlvs_handle* h) {
+  for (auto& I : h->inst) {
+    int eflag = 0;
+    CK(cudaMemcpyAsync(&eflag, I.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (eflag) {
+      mlvs_status s = (eflag & ERR_NONFINITE) ? MLVS_ERR_NONFINITE
+                      : (eflag & ERR_POSITIVITY) ? MLVS_ERR_POSITIVITY : MLVS_ERR_SINGULAR;
+      h->sticky = s;
+      return fail(h, s, "device reported a non-finite, non-positive or singular state");
+    }
+  }
+  return MLVS_OK;
 }
 
 extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, double umin, double umax,
@@ -378,124 +944,91 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
                                                 int adaptive) {
   if (!h) return MLVS_ERR_ARG;
   if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  if (h->ready) return fail(h, MLVS_ERR_STATE, "velocity levels are already set");
   if (n_levels < 1 || !levels) return fail(h, MLVS_ERR_ARG, "need at least one level");
   if (!(umax > umin)) return fail(h, MLVS_ERR_ARG, "umax must exceed umin");
-  if (adaptive != 0) return fail(h, MLVS_ERR_ARG, "adaptive level construction is not available in this build");
-  if (n_levels != 1) return fail(h, MLVS_ERR_ARG, "this build advances a single velocity space");
-  Base1D b;
+  if (adaptive != 0) return fail(h, MLVS_ERR_ARG, "use mlvs_set_cell_levels / mlvs_adapt for level changes");
   try {
-    b = make_base_1d(n_base, umin, umax, quadrature);
+    h->base = make_base_1d(n_base, umin, umax, quadrature);
   } catch (const std::exception& e) {
     return fail(h, MLVS_ERR_ARG, e.what());
   }
-  h->lv.clear();
-  h->lv.resize(n_levels);
+  h->n_base = n_base;
   const int D = h->D;
-  for (int l = 0; l < n_levels; ++l) {
-    if (levels[l].uniform_L < 0 || levels[l].uniform_L > 3)
-      return fail(h, MLVS_ERR_ARG, "uniform_L must be in 0..3 in this build");
-    h->lv[l].vs = uniform_vspace(b, D, levels[l].uniform_L);
-  }
+  const int N1 = (int)groups_1d(n_base, 1).size();
+  const int nb = D == 2 ? N1 * N1 : N1;
+  h->n_levels = n_levels;
+  h->level_space.assign(n_levels, 0);
   // time step (reading of CFL = 0.5): dt = cfl * min(dx, dy) / max |xi|_inf on the base grid
   const double vmax = std::max(std::fabs(umin), std::fabs(umax));
   const double hmin = D == 2 ? std::min(h->dx, h->dy) : h->dx;
   h->dt = h->cfg.dt > 0 ? h->cfg.dt : h->cfg.cfl * hmin / vmax;
-
-  Ops ops = ops_for(h->cfg.storage, D);
   for (int l = 0; l < n_levels; ++l) {
-    LevelData& L = h->lv[l];
-    StepConst& k = L.k;
-    k.nx = h->nx;
-    k.ny = h->ny;
-    k.px = h->cfg.bc[0] == MLVS_BC_PERIODIC;
-    k.py = D == 2 ? (h->cfg.bc[2] == MLVS_BC_PERIODIC) : 1;
-    for (int s = 0; s < 4; ++s) k.bc[s] = h->cfg.bc[s];
-    if (D == 1) { k.bc[2] = k.bc[3] = MLVS_BC_PERIODIC; }
-    k.nfx = k.px ? k.nx : k.nx + 1;
-    k.nfy = D == 2 ? (k.py ? k.ny : k.ny + 1) : 0;
-    k.ncell = k.nx * k.ny;
-    k.nface = k.nfx * k.ny + (D == 2 ? k.nx * k.nfy : 0);
-    k.nv = L.vs.nv();
-    k.dx = h->dx;
-    k.dy = h->dy;
-    k.dt = h->dt;
-    k.c0 = h->gas.K + 3.0 - D;
-    k.twoK = 2.0 * h->gas.K;
-    k.vpc = choose_chunks(ops.tile_ctas(k), k.nv);
-    k.nchunk = (k.nv + k.vpc - 1) / k.vpc;
-    // velocity table
-    std::vector<double> vt(4 * (size_t)k.nv);
-    for (int v = 0; v < k.nv; ++v) {
-      vt[v] = L.vs.xix[v];
-      vt[k.nv + v] = L.vs.xiy[v];
-      vt[2 * k.nv + v] = L.vs.wx[v];
-      vt[3 * k.nv + v] = L.vs.wy[v];
-    }
-    // one axis of the tensor-product space (uniform levels): coordinates and weights
-    L.uniform_L = levels[l].uniform_L;
-    std::vector<double> axd;
-    {
-      auto gr = groups_1d(n_base, L.uniform_L);
-      k.nax = (int)gr.size();
-      axd.resize(2 * gr.size());
-      for (size_t g = 0; g < gr.size(); ++g) merged(b, gr[g].first, gr[g].second, axd[g], axd[gr.size() + g]);
-    }
-    if (L.vt.alloc(vt.size() * h->tsize) != cudaSuccess || L.ax.alloc(axd.size() * h->tsize) != cudaSuccess)
-      return fail(h, MLVS_ERR_OOM, "velocity table");
-    if (h->tsize == 8) {
-      CK(cudaMemcpy(L.vt.p, vt.data(), vt.size() * 8, cudaMemcpyHostToDevice));
-      CK(cudaMemcpy(L.ax.p, axd.data(), axd.size() * 8, cudaMemcpyHostToDevice));
+    std::vector<int> kap(nb);
+    if (levels[l].uniform_L >= 0) {
+      if (levels[l].uniform_L > 3) return fail(h, MLVS_ERR_ARG, "uniform_L must be in 0..3");
+      std::fill(kap.begin(), kap.end(), levels[l].uniform_L);
     } else {
-      std::vector<float> vf(vt.begin(), vt.end());
-      CK(cudaMemcpy(L.vt.p, vf.data(), vf.size() * 4, cudaMemcpyHostToDevice));
-      std::vector<float> af(axd.begin(), axd.end());
-      CK(cudaMemcpy(L.ax.p, af.data(), af.size() * 4, cudaMemcpyHostToDevice));
+      if (!levels[l].kappa) return fail(h, MLVS_ERR_ARG, "kappa is null");
+      for (int b = 0; b < nb; ++b) {
+        if (levels[l].kappa[b] > 3) return fail(h, MLVS_ERR_ARG, "kappa values must be in 0..3");
+        kap[b] = levels[l].kappa[b];
+      }
     }
-    if (l != 0) continue;  // distributions live on level 0 in this build
-    L.inst.resize(h->cfg.n_instances);
-    for (int i = 0; i < h->cfg.n_instances; ++i) {
-      LevelInst& I = L.inst[i];
-      const size_t fbytes = 2ull * k.nv * k.ncell * h->ssize;
-      if (I.f[0].alloc(fbytes) != cudaSuccess || I.f[1].alloc(fbytes) != cudaSuccess ||
-          I.prm[0].alloc((size_t)NP * k.ncell * h->tsize) != cudaSuccess ||
-          I.prm[1].alloc((size_t)NP * k.ncell * h->tsize) != cudaSuccess ||
-          I.fprm.alloc((size_t)NP * k.nface * h->tsize) != cudaSuccess ||
-          I.W.alloc(8ull * k.ncell * 8) != cudaSuccess ||
-          I.cpart.alloc((size_t)k.nchunk * NMOM * k.ncell * 8) != cudaSuccess ||
-          I.fpart.alloc((size_t)k.nchunk * NMOM * k.nface * 8) != cudaSuccess ||
-          I.err.alloc(sizeof(int)) != cudaSuccess)
-        return fail(h, MLVS_ERR_OOM, "device allocation of the distributions failed");
-      CK(cudaMemsetAsync(I.err.p, 0, sizeof(int), h->stream));
-      CK(cudaMemsetAsync(I.W.p, 0, I.W.n, h->stream));
-      DevBuf dW0;
-      if (dW0.alloc(4ull * k.ncell * 8) != cudaSuccess) return fail(h, MLVS_ERR_OOM, "init W");
-      CK(cudaMemcpyAsync(dW0.p, h->initW.data() + 4ull * k.ncell * i, 4ull * k.ncell * 8,
-                         cudaMemcpyHostToDevice, h->stream));
-      CK(ops.init(h, L, I, dW0.as<double>()));
-      CK(cudaStreamSynchronize(h->stream));
-      int eflag = 0;
-      CK(cudaMemcpy(&eflag, I.err.p, sizeof(int), cudaMemcpyDeviceToHost));
-      if (eflag & ERR_SINGULAR) return fail(h, MLVS_ERR_SINGULAR, "singular compatibility matrix at init");
-    }
+    mlvs_status st = get_space(h, kap, &h->level_space[l]);
+    if (st != MLVS_OK) return st;
+  }
+  Ops ops = ops_for(h->cfg.storage, D);
+  const int ncell = h->nx * h->ny;
+  h->inst.clear();
+  h->inst.resize(h->cfg.n_instances);
+  for (int i = 0; i < h->cfg.n_instances; ++i) {
+    Inst& I = h->inst[i];
+    mlvs_status st = build_levels(h, std::vector<int>(ncell, 0), I);
+    if (st != MLVS_OK) return st;
+    if (I.ucell.alloc(2ull * ncell * h->tsize) != cudaSuccess || I.W.alloc(8ull * ncell * 8) != cudaSuccess ||
+        I.err.alloc(sizeof(int)) != cudaSuccess)
+      return fail(h, MLVS_ERR_OOM, "device allocation failed");
+    CK(cudaMemsetAsync(I.err.p, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(I.W.p, 0, I.W.n, h->stream));
+    DevBuf dW0;
+    CK(upload(dW0, std::vector<double>(h->initW.begin() + 4ull * ncell * i, h->initW.begin() + 4ull * ncell * (i + 1)),
+              h->stream));
+    CK(ops.init_state(h, I, dW0.as<double>()));
+    CK(cudaStreamSynchronize(h->stream));
+    int eflag = 0;
+    CK(cudaMemcpy(&eflag, I.err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (eflag & ERR_SINGULAR) return fail(h, MLVS_ERR_SINGULAR, "singular compatibility matrix at init");
   }
   h->ready = true;
   return MLVS_OK;
 }
 
-static mlvs_status check_flags(mlvs_handle* h) {
-  for (auto& L : h->lv)
-    for (auto& I : L.inst) {
-      int eflag = 0;
-      CK(cudaMemcpyAsync(&eflag, I.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-      if (eflag) {
-        mlvs_status s = (eflag & ERR_NONFINITE) ? MLVS_ERR_NONFINITE
-                        : (eflag & ERR_POSITIVITY) ? MLVS_ERR_POSITIVITY : MLVS_ERR_SINGULAR;
-        h->sticky = s;
-        return fail(h, s, "device reported a non-finite, non-positive or singular state");
-      }
-    }
-  return MLVS_OK;
+extern "C" mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const int* levels) {
+  if (!h || !levels) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  if (instance < 0 || instance >= h->cfg.n_instances) return fail(h, MLVS_ERR_ARG, "instance out of range");
+  const int ncell = h->nx * h->ny;
+  std::vector<int> lv(levels, levels + ncell);
+  for (int x : lv)
+    if (x < 0 || x >= h->n_levels) return fail(h, MLVS_ERR_ARG, "cell level out of range");
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  Inst& Old = h->inst[instance];
+  // the moments of the current state (for the shifts) and its parameters
+  for (int l = 0; l < h->n_levels; ++l)
+    if (!Old.lv[l].fresh) CK(ops.finalize_cells(h, Old, Old.lv[l]));
+  Inst New;
+  mlvs_status st = build_levels(h, lv, New);
+  if (st != MLVS_OK) return st;
+  New.ucell = std::move(Old.ucell);
+  New.W = std::move(Old.W);
+  New.err = std::move(Old.err);
+  CK(ops.transfer(h, Old, New));
+  CK(ops.moments_of_levels(h, New));
+  CK(cudaStreamSynchronize(h->stream));
+  h->inst[instance] = std::move(New);
+  return check_flags(h);
 }
 
 extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* stats) {
@@ -510,8 +1043,7 @@ extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* s
   h->launches = 0;
   CK(cudaEventRecord(h->ev0, h->stream));
   for (int n = 0; n < n_steps; ++n)
-    for (auto& L : h->lv)
-      for (auto& I : L.inst) CK(ops.step(h, L, I, h->cfg.limiter));
+    for (auto& I : h->inst) CK(ops.step(h, I));
   CK(cudaEventRecord(h->ev1, h->stream));
   mlvs_status s = check_flags(h);
   if (s != MLVS_OK) return s;
@@ -521,12 +1053,12 @@ extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* s
     stats->ms_total = ms;
     stats->dt = h->dt;
     long long upd = 0;
-    for (auto& L : h->lv)
-      if (!L.inst.empty()) upd += (long long)L.k.ncell * L.k.nv * (long long)L.inst.size();
+    for (auto& I : h->inst)
+      for (int l = 0; l < h->n_levels; ++l) upd += (long long)I.lv[l].cells.size() * I.lv[l].k.nv;
     stats->cell_velocity_updates = upd * n_steps;
-    stats->n_levels = (int)h->lv.size();
+    stats->n_levels = h->n_levels;
     stats->launches = h->launches;
-    for (int p = 0; p < 4; ++p) stats->ms_phase[p] = 0.f;
+    for (int p = 0; p < 6; ++p) stats->ms_phase[p] = 0.f;
     if (h->profiling) {
       for (auto& m : h->prof.marks) {
         float t = 0.f;
@@ -545,30 +1077,30 @@ extern "C" mlvs_status mlvs_moments(mlvs_handle* h, int instance, unsigned field
   if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
   if (instance < 0 || instance >= h->cfg.n_instances) return fail(h, MLVS_ERR_ARG, "instance out of range");
   Ops ops = ops_for(h->cfg.storage, h->D);
-  LevelData& L = h->lv[0];
-  LevelInst& I = L.inst[instance];
-  if (!I.fresh) CK(ops.finalize_cells(h, L, I));
+  Inst& I = h->inst[instance];
+  for (int l = 0; l < h->n_levels; ++l)
+    if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
   mlvs_status s = check_flags(h);
   if (s != MLVS_OK) return s;
-  const size_t nc = L.k.ncell;
+  const size_t nc = (size_t)h->nx * h->ny;
   // field order: RHO U V T QX QY LEVEL RHOE
   const int src[8] = {0, 1, 2, 3, 4, 5, -1, 6};
+  std::vector<double> lev(nc);
+  for (size_t c = 0; c < nc; ++c) lev[c] = I.lvl_of[c];
   int j = 0;
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   for (int b = 0; b < 8; ++b) {
     if (!(fields & (1u << b))) continue;
     double* dst = out + j * nc;
     if (src[b] < 0) {
-      std::vector<double> z(nc, 0.0);
-      CK(cudaMemcpyAsync(dst, z.data(), nc * 8, out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
+      CK(cudaMemcpyAsync(dst, lev.data(), nc * 8, out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost,
                          h->stream));
-      CK(cudaStreamSynchronize(h->stream));
     } else {
       CK(cudaMemcpyAsync(dst, I.W.as<double>() + src[b] * nc, nc * 8, kind, h->stream));
     }
+    CK(cudaStreamSynchronize(h->stream));
     ++j;
   }
-  CK(cudaStreamSynchronize(h->stream));
   return MLVS_OK;
 }
 
@@ -577,28 +1109,45 @@ extern "C" mlvs_status mlvs_read_cells(mlvs_handle* h, int instance, int cell0, 
   if (!h || !out_g || !out_h || !nv_out) return MLVS_ERR_ARG;
   if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
   if (instance < 0 || instance >= h->cfg.n_instances) return fail(h, MLVS_ERR_ARG, "instance out of range");
-  LevelData& L = h->lv[0];
-  const int nc = L.k.ncell, nv = L.k.nv;
-  if (cell0 < 0 || ncells < 0 || cell0 + ncells > nc) return fail(h, MLVS_ERR_ARG, "cell range out of bounds");
+  Inst& I = h->inst[instance];
+  const int nc = h->nx * h->ny;
+  if (cell0 < 0 || ncells < 1 || cell0 + ncells > nc) return fail(h, MLVS_ERR_ARG, "cell range out of bounds");
+  const int l = I.lvl_of[cell0];
+  for (int c = cell0; c < cell0 + ncells; ++c)
+    if (I.lvl_of[c] != l) return fail(h, MLVS_ERR_ARG, "cells of the range are on different levels");
+  LevelRt& L = I.lv[l];
+  const int nv = L.k.nv, ns = (int)L.cells.size();
   if ((long long)cap < (long long)ncells * nv) return fail(h, MLVS_ERR_ARG, "output capacity too small");
   *nv_out = nv;
-  LevelInst& I = L.inst[instance];
-  std::vector<char> buf((size_t)ncells * h->ssize);
+  std::vector<char> buf((size_t)2 * nv * ns * h->ssize);
+  CK(cudaMemcpyAsync(buf.data(), L.f[L.cur].p, buf.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
   for (int comp = 0; comp < 2; ++comp) {
     double* dst = comp == 0 ? out_g : out_h;
-    for (int v = 0; v < nv; ++v) {
-      const char* src = reinterpret_cast<const char*>(I.f[I.cur].p) +
-                        (((size_t)comp * nv + v) * nc + cell0) * h->ssize;
-      CK(cudaMemcpyAsync(buf.data(), src, (size_t)ncells * h->ssize, cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
-      for (int c = 0; c < ncells; ++c) {
+    for (int c = 0; c < ncells; ++c) {
+      const size_t s = I.slot_of[cell0 + c];
+      for (int v = 0; v < nv; ++v) {
+        const size_t o = ((size_t)comp * nv + v) * ns + s;
         double x;
-        if (h->ssize == 8) x = reinterpret_cast<const double*>(buf.data())[c];
-        else if (h->ssize == 4) x = reinterpret_cast<const float*>(buf.data())[c];
-        else x = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(buf.data())[c]);
+        if (h->ssize == 8) x = reinterpret_cast<const double*>(buf.data())[o];
+        else if (h->ssize == 4) x = reinterpret_cast<const float*>(buf.data())[o];
+        else x = (double)__bfloat162float(reinterpret_cast<const __nv_bfloat16*>(buf.data())[o]);
         dst[(size_t)c * nv + v] = x;
       }
     }
+  }
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_level_info(const mlvs_handle* h, int level, int* nv, double* xi_x, double* xi_y,
+                                       double* w, int cap) {
+  if (!h || !nv) return MLVS_ERR_ARG;
+  if (!h->ready || level < 0 || level >= h->n_levels) return MLVS_ERR_ARG;
+  const VSpace& vs = h->spaces[h->level_space[level]].vs;
+  *nv = vs.nv();
+  if (xi_x && xi_y && w) {
+    if (cap < vs.nv()) return MLVS_ERR_ARG;
+    for (int v = 0; v < vs.nv(); ++v) { xi_x[v] = vs.xix[v]; xi_y[v] = vs.xiy[v]; w[v] = vs.w[v]; }
   }
   return MLVS_OK;
 }

@@ -37,6 +37,10 @@ enum { FK_INTERIOR = 0, FK_WALL_LO = 1, FK_WALL_HI = 2 };
 //   M0 = sum w g, MX/MY = sum w xi' g, E = sum w (|xi'|^2 g + h), G = sum w xi' xi' g,
 //   J = sum w xi' (|xi'|^2 g + h)
 enum { MO_0 = 0, MO_X, MO_Y, MO_E, MO_GXX, MO_GXY, MO_GYY, MO_JX, MO_JY, NMOM };
+// Role of a face on a level: evaluated here between two cells of this level (or a wall of a
+// cell of this level), evaluated here as a cross-level face on its common refinement
+// (V^int, Sec. 3.4) with the flux exported, or received as a mapped flux.
+enum { FR_NONE = 0, FR_NORMAL = 1, FR_CROSS = 2, FR_RECV = 3 };
 // boundary kinds (match mlvs.h)
 enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2 };
 

@@ -6,6 +6,7 @@
 // remainder joining the outermost group.  A merged cell has the summed weight and the
 // weight-averaged coordinate (the relations under Eq. hierarchical_projection_operator).
 #pragma once
+#include <algorithm>
 #include <cmath>
 #include <stdexcept>
 #include <vector>
@@ -103,6 +104,119 @@ inline VSpace uniform_vspace(const Base1D& b, int D, int L) {
       s.wx.push_back(W[gx]); s.wy.push_back(W[gy]);
       s.rect.insert(s.rect.end(), {gr[gx].first, gr[gx].second, gr[gy].first, gr[gy].second});
     }
+  return s;
+}
+
+// Level-L group index of every level-1 group of one axis.
+inline std::vector<int> level1_parent(int n, int L) {
+  auto g1 = groups_1d(n, 1);
+  auto gL = groups_1d(n, L);
+  std::vector<int> out(g1.size());
+  for (size_t b = 0; b < g1.size(); ++b)
+    for (size_t q = 0; q < gL.size(); ++q)
+      if (g1[b].first >= gL[q].first && g1[b].first < gL[q].second) { out[b] = (int)q; break; }
+  return out;
+}
+
+// Parent-child consistency of a block coarsening index (Sec. 3.2): kappa_eff(b) is the
+// largest L <= kappa(b) such that every level-1 block of b's level-L parent has kappa >= L.
+// kappa is [N1*N1] (row by, column bx) in 2-D or [N1] in 1-D.
+inline std::vector<int> enforce_consistency(const std::vector<int>& kappa, int n, int D) {
+  const int N1 = (int)groups_1d(n, 1).size();
+  std::vector<std::vector<int>> par(4);
+  for (int L = 1; L <= 3; ++L) par[L] = level1_parent(n, L);
+  std::vector<int> out(kappa.size(), 0);
+  if (D == 1) {
+    for (int b = 0; b < N1; ++b) {
+      int best = 0;
+      for (int L = 1; L <= kappa[b]; ++L) {
+        bool ok = true;
+        for (int c = 0; c < N1 && ok; ++c)
+          if (par[L][c] == par[L][b] && kappa[c] < L) ok = false;
+        if (ok) best = L;
+      }
+      out[b] = best;
+    }
+    return out;
+  }
+  for (int by = 0; by < N1; ++by)
+    for (int bx = 0; bx < N1; ++bx) {
+      int best = 0;
+      for (int L = 1; L <= kappa[by * N1 + bx]; ++L) {
+        bool ok = true;
+        for (int cy = 0; cy < N1 && ok; ++cy) {
+          if (par[L][cy] != par[L][by]) continue;
+          for (int cx = 0; cx < N1 && ok; ++cx)
+            if (par[L][cx] == par[L][bx] && kappa[cy * N1 + cx] < L) ok = false;
+        }
+        if (ok) best = L;
+      }
+      out[by * N1 + bx] = best;
+    }
+  return out;
+}
+
+// Space of a (consistent) coarsening index: one point per merged cell, ordered by the
+// lower-left base index (y major, x minor); the merged cell carries the summed weight and the
+// weight-averaged coordinate.  Also fills owner[iy * n + ix] (2-D) or owner[ix] (1-D).
+inline VSpace kappa_vspace(const Base1D& b, int D, const std::vector<int>& keff, std::vector<int>& owner) {
+  const int n = (int)b.x.size();
+  auto g1 = groups_1d(n, 1);
+  const int N1 = (int)g1.size();
+  std::vector<std::vector<std::pair<int, int>>> gl(4);
+  std::vector<std::vector<int>> par(4);
+  for (int L = 0; L <= 3; ++L) gl[L] = groups_1d(n, L);
+  for (int L = 1; L <= 3; ++L) par[L] = level1_parent(n, L);
+  struct Cell { int y0, x0, xa, xb, ya, yb; };
+  std::vector<Cell> cells;
+  if (D == 1) {
+    std::vector<char> seen(4 * N1, 0);
+    for (int bx = 0; bx < N1; ++bx) {
+      const int L = keff[bx];
+      if (L == 0) {
+        for (int i = g1[bx].first; i < g1[bx].second; ++i) cells.push_back({0, i, i, i + 1, 0, 1});
+      } else {
+        const int p = par[L][bx];
+        if (seen[L * N1 + p]) continue;
+        seen[L * N1 + p] = 1;
+        cells.push_back({0, gl[L][p].first, gl[L][p].first, gl[L][p].second, 0, 1});
+      }
+    }
+  } else {
+    std::vector<char> seen(4 * N1 * N1, 0);
+    for (int by = 0; by < N1; ++by)
+      for (int bx = 0; bx < N1; ++bx) {
+        const int L = keff[by * N1 + bx];
+        if (L == 0) {
+          for (int iy = g1[by].first; iy < g1[by].second; ++iy)
+            for (int ix = g1[bx].first; ix < g1[bx].second; ++ix) cells.push_back({iy, ix, ix, ix + 1, iy, iy + 1});
+        } else {
+          const int px = par[L][bx], py = par[L][by];
+          const int key = (L * N1 + py) * N1 + px;
+          if (seen[key]) continue;
+          seen[key] = 1;
+          cells.push_back({gl[L][py].first, gl[L][px].first, gl[L][px].first, gl[L][px].second,
+                           gl[L][py].first, gl[L][py].second});
+        }
+      }
+  }
+  std::sort(cells.begin(), cells.end(), [](const Cell& a, const Cell& c) {
+    return a.y0 != c.y0 ? a.y0 < c.y0 : a.x0 < c.x0;
+  });
+  VSpace s;
+  s.D = D;
+  owner.assign(D == 2 ? n * n : n, -1);
+  for (size_t k = 0; k < cells.size(); ++k) {
+    const Cell& c = cells[k];
+    double X, WX, Y = 0.0, WY = 1.0;
+    merged(b, c.xa, c.xb, X, WX);
+    if (D == 2) merged(b, c.ya, c.yb, Y, WY);
+    s.xix.push_back(X); s.xiy.push_back(Y); s.w.push_back(WX * WY);
+    s.wx.push_back(WX); s.wy.push_back(WY);
+    s.rect.insert(s.rect.end(), {c.xa, c.xb, c.ya, c.yb});
+    for (int iy = c.ya; iy < c.yb; ++iy)
+      for (int ix = c.xa; ix < c.xb; ++ix) owner[(D == 2 ? iy * n : 0) + ix] = (int)k;
+  }
   return s;
 }
 

@@ -44,7 +44,7 @@ class mlvs_level_desc(C.Structure):
 class mlvs_step_stats(C.Structure):
     _fields_ = [("profile", C.c_int), ("dt", C.c_double), ("cell_velocity_updates", C.c_longlong),
                 ("n_levels", C.c_int), ("launches", C.c_int), ("ms_total", C.c_float),
-                ("ms_phase", C.c_float * 4)]
+                ("ms_phase", C.c_float * 6)]
 
 
 def _load():
@@ -61,6 +61,9 @@ def _load():
         "mlvs_read_cells": (C.c_int, [H, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                       C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_int)]),
         "mlvs_time_step": (C.c_int, [H, C.POINTER(C.c_double)]),
+        "mlvs_set_cell_levels": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_level_info": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
         "mlvs_moments_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
         "mlvs_destroy": (None, [H]),
@@ -153,6 +156,22 @@ def mlvs_moments_noalloc(g, h, nv, ncell, xi_x, xi_y, w_x, w_y, out, stream=None
         return C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else x)
     _check(_lib.mlvs_moments_noalloc(ptr(g), ptr(h), nv, ncell, ptr(xi_x), ptr(xi_y), ptr(w_x),
                                      ptr(w_y), ptr(out), C.c_void_p(stream)), None)
+
+
+def mlvs_set_cell_levels(h, instance, levels):
+    lv = np.ascontiguousarray(levels, dtype=np.int32)
+    _check(_lib.mlvs_set_cell_levels(h, instance, lv.ctypes.data_as(C.POINTER(C.c_int))), h)
+
+
+def mlvs_level_info(h, level):
+    nv = C.c_int()
+    _check(_lib.mlvs_level_info(h, level, C.byref(nv), None, None, None, 0), h)
+    n = nv.value
+    x, y, w = np.zeros(n), np.zeros(n), np.zeros(n)
+    P = C.POINTER(C.c_double)
+    _check(_lib.mlvs_level_info(h, level, C.byref(nv), x.ctypes.data_as(P), y.ctypes.data_as(P),
+                                w.ctypes.data_as(P), n), h)
+    return x, y, w
 
 
 def mlvs_destroy(h):

@@ -1,0 +1,131 @@
+"""GPU-vs-oracle parity of the multi-level step (Sec. 3.3-3.4), through the C ABI.
+
+Cells are put on different velocity spaces with mlvs_set_cell_levels; the oracle's
+mlvs.MLVSState runs the same assignment.  Covered: two uniform levels (cross faces evaluated
+on the finer space), two kappa spaces whose common refinement is neither (a cell-less face
+space), walls next to level interfaces, and the level switch of cells (remap).
+Tolerances as in test_gpu_parity: FP64 1e-10 relative, FP32 1e-5.
+"""
+import numpy as np
+import pytest
+
+from tests.helpers import have_gpu, oracle_setup
+from paper_2609_35258_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+if not have_gpu():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import kinetic, mlvs as omlvs, vspace  # noqa: E402
+from paper_2609_35258_b300 import mlvs as M  # noqa: E402
+from paper_2609_35258_b300.solver import Solver  # noqa: E402
+
+
+def _oracle_state(desc, o, keys_of_cell, book):
+    init = desc["init"]
+    return omlvs.MLVSState.from_primitives(o["mesh"], o["gas"], book, keys_of_cell, init[..., 0],
+                                           init[..., 1:3], init[..., 3], o["dt"], o["opt"])
+
+
+def _kappa_pair(n_base):
+    """Two coarsening patterns, fine near the origin and coarser towards +x (a) or +y (b),
+    whose blockwise minimum is neither of them."""
+    N1 = len(vspace.axis_groups(n_base, 1))
+    yy, xx = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
+    r = np.hypot(xx - N1 // 2, yy - N1 // 2)
+    a = np.where(r < N1 / 4, 0, np.where(xx > N1 // 2, 2, 1)).astype(np.uint8)
+    b = np.where(r < N1 / 4, 0, np.where(yy > N1 // 2, 2, 1)).astype(np.uint8)
+    return a, b
+
+
+def _compare_cells(s, st, ncell, atol_rel):
+    for c in range(ncell):
+        g, h = s.read_cells(c, 1, 10000)
+        gref = st.g[c]
+        assert g.shape[1] == gref.shape[0]
+        np.testing.assert_allclose(g[0], gref, rtol=0, atol=atol_rel * np.max(np.abs(gref)))
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 2e-5)])
+def test_two_uniform_levels_periodic(storage, tol):
+    desc = workloads.periodic_random(16, 8, n_base=17, umax=5.0, storage=storage)
+    lev = np.array([0 if (c % 16) < 8 else 1 for c in range(128)], dtype=np.int32)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(0), book.uniform(1)]
+    # the oracle starts every cell on level 0 and switches like the library does
+    st = _oracle_state(desc, o, [keys[0]] * 128, book)
+    for c in range(128):
+        omlvs.remap(st, c, keys[lev[c]])
+    s = Solver(desc, levels=(0, 1))
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    _compare_cells(s, st, 128, tol)
+    for _ in range(3):
+        omlvs.step(st)
+    s.step(3)
+    _compare_cells(s, st, 128, tol * 10)
+    m = s.moments(M.RHO | M.RHOE | M.LEVEL)      # written in bit order: RHO, LEVEL, RHOE
+    np.testing.assert_array_equal(m[1], lev)
+
+
+def test_kappa_levels_with_face_space_conserve():
+    """Cross faces between two kappa spaces are evaluated on a third (cell-less) space."""
+    desc = workloads.periodic_random(12, 6, n_base=25, umax=6.0, storage="f64")
+    ka, kb = _kappa_pair(25)
+    lev = np.array([0 if (c % 12) < 6 else 1 for c in range(72)], dtype=np.int32)
+    s = Solver(desc, levels=(ka, kb))
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    m0 = s.moments(M.RHO | M.U | M.V | M.RHOE)
+    tot0 = np.array([m0[0].sum(), (m0[0] * m0[1]).sum(), (m0[0] * m0[2]).sum(), m0[3].sum()])
+    s.step(4)
+    m1 = s.moments(M.RHO | M.U | M.V | M.RHOE)
+    tot1 = np.array([m1[0].sum(), (m1[0] * m1[1]).sum(), (m1[0] * m1[2]).sum(), m1[3].sum()])
+    assert np.max(np.abs(tot1 - tot0)) < 1e-12 * np.max(np.abs(tot0))
+    # and it agrees with the oracle
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.get(ka.astype(np.int64)), book.get(kb.astype(np.int64))]
+    st = _oracle_state(desc, o, [keys[0]] * 72, book)
+    for c in range(72):
+        omlvs.remap(st, c, keys[lev[c]])
+    for _ in range(4):
+        omlvs.step(st)
+    _compare_cells(s, st, 72, 1e-9)
+
+
+def test_three_levels_cavity_walls():
+    desc = workloads.cavity(12, n_base=17, umax=5.0, storage="f64")
+    lev = np.zeros(144, dtype=np.int32)
+    for c in range(144):
+        j, i = divmod(c, 12)
+        lev[c] = 0 if j >= 8 else (1 if i < 6 else 2)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(L) for L in (0, 1, 2)]
+    st = _oracle_state(desc, o, [keys[0]] * 144, book)
+    for c in range(144):
+        omlvs.remap(st, c, keys[lev[c]])
+    s = Solver(desc, levels=(0, 1, 2))
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    for _ in range(3):
+        omlvs.step(st)
+    s.step(3)
+    _compare_cells(s, st, 144, 1e-9)
+    m = s.moments(M.RHO)
+    assert abs(m[0].sum() - st.totals()[0]) < 1e-12 * 144
+
+
+def test_level_switch_conserves_and_matches():
+    desc = workloads.periodic_random(8, 8, n_base=17, umax=5.0, storage="f64")
+    s = Solver(desc, levels=(0, 2))
+    s.step(2)
+    before = s.moments(M.RHO | M.U | M.V | M.RHOE)
+    lev = np.array([(c // 3) % 2 for c in range(64)], dtype=np.int32)
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    after = s.moments(M.RHO | M.U | M.V | M.RHOE)
+    np.testing.assert_allclose(after, before, rtol=1e-12, atol=1e-13)
+    # back to the fine level everywhere: moments still preserved
+    M.mlvs_set_cell_levels(s.h, 0, np.zeros(64, dtype=np.int32))
+    back = s.moments(M.RHO | M.U | M.V | M.RHOE)
+    np.testing.assert_allclose(back, before, rtol=1e-12, atol=1e-13)
