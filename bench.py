@@ -201,8 +201,8 @@ def run_ours(args, rank, world, local_rank):
 
     # roofline of the dominant kernel (update pass or face-sum pass)
     phases = list(st.ms_phase)
-    names = ["finalize_cells", "face_sums", "finalize_faces", "update"]
-    dom = max(range(4), key=lambda i: phases[i])
+    names = ["finalize_cells", "face_sums", "finalize_faces", "update", "ghost_map", "flux_map"]
+    dom = max(range(len(names)), key=lambda i: phases[i])
     fbytes = {"f32": 4, "bf16": 2, "f64": 8}[args.storage]
     algo_per_update = {1: 2 * fbytes, 3: 4 * fbytes}.get(dom, 0)
     kernel_ms = phases[dom] / args.steps

@@ -170,7 +170,10 @@ __device__ __forceinline__ void write_partials_smem(const T* acc, int sa, double
   P[MO_JY * st] = (double)acc[12 * sa];
 }
 
-template <class S, class T, int D, int TX, int TY, int VB, int MODE>
+// ML = false: the level holds every cell of the mesh (one velocity space), so every stencil
+// position is an own cell in natural order and every face is a normal face; the level
+// tables are not read.
+template <class S, class T, int D, int TX, int TY, int VB, int MODE, bool ML>
 __global__ void __launch_bounds__(TX * TY)
 k_tile(const TileArgs a, int limiter) {
   using G = TileGeom<TX, TY, D>;
@@ -213,7 +216,8 @@ k_tile(const TileArgs a, int limiter) {
   auto classify = [&](int ex, int ey, int& kind, long& base, long& ld) {
     const int c = wrap_or_clamp(y0 + ey, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + ex, k.nx, k.px);
     kind = 0; base = 0; ld = 0;
-    if (a.lvl_of[c] == a.level) { kind = 1; base = a.slot_of[c]; ld = ns; }
+    if (!ML) { kind = 1; base = c; ld = ns; }
+    else if (a.lvl_of[c] == a.level) { kind = 1; base = a.slot_of[c]; ld = ns; }
     else if (a.ghost_of && a.ghost_of[c] >= 0) { kind = 2; base = a.ghost_of[c]; ld = ng; }
     return c;
   };
@@ -244,7 +248,7 @@ k_tile(const TileArgs a, int limiter) {
       if (gi <= k.nx && (D == 1 || gj < k.ny)) {
         const int pi = (k.px && gi == k.nx) ? 0 : gi;
         fid = ((D == 2) ? gj : 0) * k.nfx + pi;
-        role = a.frole[fid];
+        role = ML ? a.frole[fid] : FR_NORMAL;
         meta = FM_VALID;
         if ((gi < k.nx) ? (li < TX) : !k.px) meta |= FM_OWNED;
         if (!k.px && gi == 0 && k.bc[0] == BC_WALL) meta |= FK_WALL_LO << 2;
@@ -254,7 +258,7 @@ k_tile(const TileArgs a, int limiter) {
       if (gi < k.nx && gj <= k.ny) {
         const int pj = (k.py && gj == k.ny) ? 0 : gj;
         fid = k.nfx * k.ny + pj * k.nx + gi;
-        role = a.frole[fid];
+        role = ML ? a.frole[fid] : FR_NORMAL;
         meta = FM_VALID;
         if ((gj < k.ny) ? (lj < TY) : !k.py) meta |= FM_OWNED;
         if (!k.py && gj == 0 && k.bc[2] == BC_WALL) meta |= FK_WALL_LO << 2;
@@ -320,7 +324,7 @@ k_tile(const TileArgs a, int limiter) {
 
   // loads of one velocity for a position of each kind
   auto load_pos = [&](int kind, long col, int v, T& g, T& h) {
-    if (kind == 1) {
+    if (!ML || kind == 1) {
       g = ldf<S, T>(fin + (long)v * ns + col);
       h = ldf<S, T>(fin + (nv + v) * ns + col);
     } else if (kind == 2) {
@@ -367,7 +371,7 @@ k_tile(const TileArgs a, int limiter) {
       T* Pg = sP + (b * 2 + 0) * G::NEXT;
       T* Ph = sP + (b * 2 + 1) * G::NEXT;
       T gs, hs;
-      if (kind0 == 1) {
+      if (!ML || kind0 == 1) {
         model_eval<T, D>(m0, xixb[b], xiyb[b], c0, twoK, gs, hs);
         dg0[b] = N::sub(gs, g0[b]);
         dh0[b] = N::sub(hs, h0[b]);
@@ -380,7 +384,7 @@ k_tile(const TileArgs a, int limiter) {
         Ph[e0] = h0[b];
       }
       if (tid < G::NHALO) {
-        if (kind1 == 1) {
+        if (!ML || kind1 == 1) {
           model_eval<T, D>(m1, xixb[b], xiyb[b], c0, twoK, gs, hs);
           Pg[e1] = N::fma(m1.c1, N::sub(gs, g1), g1);
           Ph[e1] = N::fma(m1.c1, N::sub(hs, h1), h1);
@@ -417,11 +421,11 @@ k_tile(const TileArgs a, int limiter) {
       const int meta = sMeta[f];
       if (!(meta & FM_VALID)) continue;
       const int role = meta >> 4;
-      if (MODE == 0 && (!(meta & FM_OWNED) || role == FR_RECV)) continue;
+      if (MODE == 0 && (!(meta & FM_OWNED) || (ML && role == FR_RECV))) continue;
       const int kind = (meta >> 2) & 3;
       int dir, li, lj;
       G::face_pos(f, dir, li, lj);
-      if (MODE == 1 && role == FR_RECV) {
+      if (ML && MODE == 1 && role == FR_RECV) {
         // microflux mapped from the face's own space (Eq. native_flux_moment_matching)
         const int col = sMeta[G::NF + f];
 #pragma unroll
@@ -538,7 +542,7 @@ k_tile(const TileArgs a, int limiter) {
           const T Fg = N::mul(xn, gf), Fh = N::mul(xn, hf);
           sF[(b * 2 + 0) * G::NF + f] = Fg;
           sF[(b * 2 + 1) * G::NF + f] = Fh;
-          if (role == FR_CROSS && (meta & FM_OWNED)) {
+          if (ML && role == FR_CROSS && (meta & FM_OWNED)) {
             const int col = sMeta[G::NF + f];
             Xo[(long)v * a.nX + col] = Fg;
             Xo[(nv + v) * a.nX + col] = Fh;

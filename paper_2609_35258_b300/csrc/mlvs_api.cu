@@ -324,11 +324,21 @@ template <class S, class T, int D> struct Runner {
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
 
   static cudaError_t set_smem_limits() {
-    cudaError_t e = cudaFuncSetAttribute(k_tile<S, T, D, TX, TY, VB, 0>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM0);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_tile<S, T, D, TX, TY, VB, 1>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM1);
+    const void* fn[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false>,
+                         (const void*)k_tile<S, T, D, TX, TY, VB, 0, true>,
+                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, false>,
+                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, true>};
+    for (int i = 0; i < 4; ++i) {
+      cudaError_t e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(i < 2 ? SM0 : SM1));
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+
+  // a level that holds every cell runs the tile kernels without level tables
+  static bool single(const mlvs_handle* h, const LevelRt& L) {
+    return L.cells.size() == (size_t)h->nx * h->ny && L.nghost == 0 && L.nX == 0 && L.nY == 0;
   }
 
   static void mark_begin(mlvs_handle* h, int ph) {
@@ -404,6 +414,7 @@ template <class S, class T, int D> struct Runner {
     a.prm_out = L.prm[L.pcur ^ 1].p;
     a.W = I.W.as<double>();
     mark_begin(h, 0);
+    ++h->launches;
     k_finalize<T, D><<<fin_grid(n), FIN_BLOCK, 0, h->stream>>>(a);
     k_scatter_velocity<T><<<(n + 127) / 128, 128, 0, h->stream>>>(L.prm[L.pcur ^ 1].as<T>(), n, L.ids.as<int>(),
                                                                  I.ucell.as<T>(), h->nx * h->ny);
@@ -491,7 +502,8 @@ template <class S, class T, int D> struct Runner {
       t.part = L.fpart.as<double>();
       dim3 grid(L.ntiles, L.k.nchunk);
       mark_begin(h, 1);
-      k_tile<S, T, D, TX, TY, VB, 0><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+      if (single(h, L)) k_tile<S, T, D, TX, TY, VB, 0, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+      else k_tile<S, T, D, TX, TY, VB, 0, true><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
       mark_end(h);
     }
     for (int l = 0; l < (int)I.lv.size(); ++l) {
@@ -511,7 +523,8 @@ template <class S, class T, int D> struct Runner {
         t.part = L.cpart.as<double>();
         dim3 grid(L.ntiles, L.k.nchunk);
         mark_begin(h, 3);
-        k_tile<S, T, D, TX, TY, VB, 1><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
+        if (single(h, L)) k_tile<S, T, D, TX, TY, VB, 1, false><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
+        else k_tile<S, T, D, TX, TY, VB, 1, true><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
         mark_end(h);
       }
       if ((e = run_fluxes(h, I, l)) != cudaSuccess) return e;
