@@ -124,6 +124,61 @@ mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const int* levels
 mlvs_status mlvs_level_info(const mlvs_handle* h, int level, int* nv, double* xi_x, double* xi_y,
                             double* w, int cap);
 
+/* Adaptation thresholds (Sec. 3.2). */
+typedef struct {
+  double C_split;    /* I_B above C_split: the block stays fine (Eq. block-hysteresis-rule)  */
+  double C_merge;    /* I_B below C_merge: the block merges, subject to the transport test  */
+  double eps_merge;  /* tolerance of Eq. merge-transport-error; <= 0 switches the test off   */
+  double tau_clust;  /* graded-distance threshold of the grouping                          */
+  int max_level;     /* coarsest candidate block: 1 (2x2), 2 (4x4) or 3 (8x8)              */
+} mlvs_adapt_params;
+
+typedef struct {
+  int n_levels;                  /* representative spaces after the call                  */
+  int n_distinct;                /* distinct cell masks                                   */
+  int n_changed;                 /* cells (all instances) whose velocity space changed    */
+  long long updates_per_step;    /* sum over levels of cells x velocities, all instances  */
+  float ms_criterion;            /* device time of the criterion kernels                  */
+  float ms_total;                /* wall time of the call                                 */
+} mlvs_adapt_stats;
+
+/* Velocity-space requirement of every cell of one instance (Sec. 3.2, criterion only): the
+ * cell's (g~, h~) is read on the base grid by inheritance, the block indicator I_B of
+ * Eq. block-contribution-indicator is compared with C_split / C_merge with hysteresis
+ * against the cell's current space, the transport test applies below C_merge, and the
+ * candidate blocks are scanned 8x8 -> 4x4 -> 2x2.  kappa_out is [ny*nx][N1*N1] bytes (N1 =
+ * level-1 groups per axis of the base grid; row-major blocks, y major), host or device memory
+ * (out_on_device).  2-D only.
+ * Errors: MLVS_ERR_ARG (1-D, bad thresholds), MLVS_ERR_STATE, MLVS_ERR_CUDA. */
+mlvs_status mlvs_criterion(mlvs_handle* h, int instance, const mlvs_adapt_params* p,
+                           unsigned char* kappa_out, int out_on_device);
+
+/* Adapt the velocity levels (Sec. 3.2): the criterion on every cell of every instance,
+ * the grouping of the cell masks (mlvs_cluster), one level per distinct representative
+ * space (the blockwise minimum of its members, made parent-child consistent), and the
+ * conservative remap of every cell whose space changed.  The level set is replaced: level
+ * indices refer to the new set afterwards.  stats may be NULL.
+ * Errors: as mlvs_criterion, and MLVS_ERR_OOM. */
+mlvs_status mlvs_adapt(mlvs_handle* h, const mlvs_adapt_params* p, mlvs_adapt_stats* stats);
+
+/* Run mlvs_adapt with p after every `interval` steps taken by mlvs_step (interval 0: never).
+ * p is copied. */
+mlvs_status mlvs_set_adaptation(mlvs_handle* h, const mlvs_adapt_params* p, int interval);
+
+/* Host-only grouping of nrow masks of nb bytes each (Sec. 3.2): distinct masks by decreasing
+ * frequency (ties: lexicographic order), each joins the nearest existing centre when the
+ * graded distance sum|ka - kb| / (3 nb) is <= tau (ties: lowest cluster), else it seeds a new
+ * cluster.  labels[nrow] receives the cluster of every row, reps[reps_cap][nb] the blockwise
+ * minimum over the members of each cluster, *n_reps the cluster count.  Needs no GPU.
+ * Errors: MLVS_ERR_ARG (null pointers, nb < 1, reps_cap < *n_reps). */
+mlvs_status mlvs_cluster(const unsigned char* kappa, long nrow, int nb, double tau, int* labels,
+                         unsigned char* reps, int reps_cap, int* n_reps);
+
+/* Extra: the parent-child consistent coarsening index of a level's space.  *nb_out receives
+ * its length (N1*N1 in 2-D, N1 in 1-D); out (capacity cap) may be NULL to query it. */
+mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out, int cap,
+                             int* nb_out);
+
 /* field bits for mlvs_moments; fields are written in this bit order */
 enum {
   MLVS_RHO = 1, MLVS_U = 2, MLVS_V = 4, MLVS_T = 8, MLVS_QX = 16, MLVS_QY = 32,

@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <chrono>
 #include <map>
 #include <memory>
 #include <set>
@@ -34,6 +35,8 @@
 #include "dugks_tile.cuh"
 #include "finalize.cuh"
 #include "mapping.cuh"
+#include "criterion.cuh"
+#include "cluster_host.hpp"
 #include "vspace_host.hpp"
 
 using namespace mlvs;
@@ -78,6 +81,7 @@ struct SpaceRt {
   std::vector<int> owner;    // base node -> point
   int nax = 0;               // > 0: tensor product of one axis of nax points
   DevBuf vt, ax, ainv;
+  DevBuf owner_d, xid, kp_d; // criterion tables: owner, FP64 coordinates, keff (bytes)
 };
 
 struct CSR {
@@ -153,10 +157,17 @@ struct mlvs_handle {
   int n_levels = 0;
   std::vector<int> level_space;   // space of every cell level
   std::vector<Inst> inst;
+  // criterion tables of the base grid (2-D)
+  int N1 = 0;
+  int ng[4] = {0, 0, 0, 0};
+  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, kbuf;
+  mlvs_adapt_params adapt{};
+  int adapt_interval = 0;
+  long long steps_done = 0;
   bool ready = false;
   int sticky = MLVS_OK;
   std::string err;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, ea0 = nullptr, ea1 = nullptr;
 };
 
 static mlvs_status fail(mlvs_handle* h, mlvs_status s, const std::string& msg) {
@@ -262,6 +273,13 @@ static mlvs_status get_space(mlvs_handle* h, const std::vector<int>& kappa, int*
     CK(upload(S.ax, std::vector<float>(axd.begin(), axd.end()), h->stream));
   }
   CK(upload(S.ainv, inv, h->stream));
+  {
+    std::vector<double> xid(2 * (size_t)nv);
+    for (int v = 0; v < nv; ++v) { xid[v] = S.vs.xix[v]; xid[nv + v] = S.vs.xiy[v]; }
+    CK(upload(S.xid, xid, h->stream));
+    CK(upload(S.owner_d, S.owner, h->stream));
+    CK(upload(S.kp_d, std::vector<unsigned char>(keff.begin(), keff.end()), h->stream));
+  }
   h->spaces.push_back(std::move(S));
   *out = (int)h->spaces.size() - 1;
   h->space_of_key[keff] = *out;
@@ -612,6 +630,43 @@ template <class S, class T, int D> struct Runner {
     for (auto& L : New.lv) { L.cur = 0; L.pcur = 0; }
     return cudaGetLastError();
   }
+
+  // masks of the criterion (Sec. 3.2) of every cell of an instance into kout[ncell][N1*N1]
+  static cudaError_t criterion(mlvs_handle* h, Inst& I, const mlvs_adapt_params& p, unsigned char* kout) {
+    const int nb = h->N1 * h->N1;
+    const size_t smem = 2ull * nb * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_criterion<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    for (int l = 0; l < h->n_levels; ++l) {
+      LevelRt& L = I.lv[l];
+      if (L.cells.empty()) continue;
+      const SpaceRt& sp = h->spaces[L.space];
+      CritArgs a;
+      a.f = L.f[L.cur].p;
+      a.ns = (int)L.cells.size();
+      a.nv = L.k.nv;
+      a.ids = L.ids.as<int>();
+      a.owner = sp.owner_d.as<int>();
+      a.xi = sp.xid.as<double>();
+      a.bx = h->bx_d.as<double>();
+      a.bw = h->bw_d.as<double>();
+      a.n = h->n_base;
+      a.N1 = h->N1;
+      a.g1 = h->g1_d.as<int>();
+      a.pstart = h->pstart_d.as<int>();
+      a.cstart = h->cstart_d.as<int>();
+      for (int q = 0; q < 4; ++q) a.ng[q] = h->ng[q];
+      a.kprev = sp.kp_d.as<unsigned char>();
+      a.C_split = p.C_split;
+      a.C_merge = p.C_merge;
+      a.eps = p.eps_merge;
+      a.max_level = p.max_level;
+      a.kout = kout;
+      ++h->launches;
+      k_criterion<S><<<a.ns, CRIT_THREADS, smem, h->stream>>>(a);
+    }
+    return cudaGetLastError();
+  }
 };
 
 struct Ops {
@@ -620,11 +675,12 @@ struct Ops {
   cudaError_t (*step)(mlvs_handle*, Inst&);
   cudaError_t (*transfer)(mlvs_handle*, Inst&, Inst&);
   cudaError_t (*moments_of_levels)(mlvs_handle*, Inst&);
+  cudaError_t (*criterion)(mlvs_handle*, Inst&, const mlvs_adapt_params&, unsigned char*);
 };
 
 template <class S, class T, int D> Ops make_ops() {
   using R = Runner<S, T, D>;
-  return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels};
+  return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion};
 }
 
 Ops ops_for(int storage, int D) {
@@ -921,6 +977,8 @@ extern "C" void mlvs_destroy(mlvs_handle* h) {
   else cudaDeviceSynchronize();
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
+  if (h->ea0) cudaEventDestroy(h->ea0);
+  if (h->ea1) cudaEventDestroy(h->ea1);
   delete h;
 }
 
@@ -952,6 +1010,46 @@ static mlvs_status check_flags(mlvs_handle* h) {
   return MLVS_OK;
 }
 
+// Base-grid tables of the criterion: nodes, weights, level-1 group starts, and for every
+// level L the first level-1 block (pstart) and first level-(L-1) group (cstart) of each
+// level-L group.  The groups are nested, so both are exact starts.
+static mlvs_status build_criterion_tables(mlvs_handle* h, int n) {
+  auto g1 = groups_1d(n, 1);
+  const int N1 = (int)g1.size();
+  h->N1 = N1;
+  std::vector<int> g1s(N1 + 1), ps(4 * (N1 + 1), 0), cs(4 * (N1 + 1), 0);
+  for (int b = 0; b < N1; ++b) g1s[b] = g1[b].first;
+  g1s[N1] = n;
+  std::vector<std::vector<std::pair<int, int>>> gl(4);
+  for (int L = 0; L <= 3; ++L) gl[L] = groups_1d(n, L);
+  h->ng[0] = n;
+  for (int L = 1; L <= 3; ++L) {
+    const int ngL = (int)gl[L].size();
+    h->ng[L] = ngL;
+    for (int q = 0; q < ngL; ++q) {
+      int b = 0;
+      while (b < N1 && g1[b].first != gl[L][q].first) ++b;
+      if (b == N1) return fail(h, MLVS_ERR_ARG, "velocity groups are not nested");
+      ps[L * (N1 + 1) + q] = b;
+      if (L >= 2) {
+        int c = 0;
+        const int ngc = (int)gl[L - 1].size();
+        while (c < ngc && gl[L - 1][c].first != gl[L][q].first) ++c;
+        if (c == ngc) return fail(h, MLVS_ERR_ARG, "velocity groups are not nested");
+        cs[L * (N1 + 1) + q] = c;
+      }
+    }
+    ps[L * (N1 + 1) + ngL] = N1;
+    if (L >= 2) cs[L * (N1 + 1) + ngL] = (int)gl[L - 1].size();
+  }
+  CK(upload(h->bx_d, h->base.x, h->stream));
+  CK(upload(h->bw_d, h->base.w, h->stream));
+  CK(upload(h->g1_d, g1s, h->stream));
+  CK(upload(h->pstart_d, ps, h->stream));
+  CK(upload(h->cstart_d, cs, h->stream));
+  return MLVS_OK;
+}
+
 extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, double umin, double umax,
                                                 int quadrature, int n_levels, const mlvs_level_desc* levels,
                                                 int adaptive) {
@@ -970,6 +1068,10 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
   const int D = h->D;
   const int N1 = (int)groups_1d(n_base, 1).size();
   const int nb = D == 2 ? N1 * N1 : N1;
+  if (D == 2) {
+    mlvs_status st = build_criterion_tables(h, n_base);
+    if (st != MLVS_OK) return st;
+  }
   h->n_levels = n_levels;
   h->level_space.assign(n_levels, 0);
   // time step (reading of CFL = 0.5): dt = cfl * min(dx, dy) / max |xi|_inf on the base grid
@@ -1044,6 +1146,168 @@ extern "C" mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const 
   return check_flags(h);
 }
 
+static mlvs_status check_adapt_params(mlvs_handle* h, const mlvs_adapt_params* p) {
+  if (!p) return fail(h, MLVS_ERR_ARG, "null adaptation parameters");
+  if (h->D != 2) return fail(h, MLVS_ERR_ARG, "the criterion is implemented for 2-D velocity spaces");
+  if (!(p->C_merge >= 0) || !(p->C_split >= p->C_merge)) return fail(h, MLVS_ERR_ARG, "need 0 <= C_merge <= C_split");
+  if (p->max_level < 1 || p->max_level > 3) return fail(h, MLVS_ERR_ARG, "max_level must be 1, 2 or 3");
+  if (!(p->tau_clust >= 0)) return fail(h, MLVS_ERR_ARG, "tau_clust must be >= 0");
+  return MLVS_OK;
+}
+
+static mlvs_status ensure_kbuf(mlvs_handle* h, size_t bytes) {
+  if (h->kbuf.n >= bytes) return MLVS_OK;
+  if (h->kbuf.alloc(bytes) != cudaSuccess) return fail(h, MLVS_ERR_OOM, "device allocation of the masks failed");
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_criterion(mlvs_handle* h, int instance, const mlvs_adapt_params* p,
+                                      unsigned char* kappa_out, int out_on_device) {
+  if (!h || !kappa_out) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  if (instance < 0 || instance >= h->cfg.n_instances) return fail(h, MLVS_ERR_ARG, "instance out of range");
+  mlvs_status st = check_adapt_params(h, p);
+  if (st != MLVS_OK) return st;
+  const size_t bytes = (size_t)h->nx * h->ny * h->N1 * h->N1;
+  unsigned char* dst = kappa_out;
+  if (!out_on_device) {
+    if ((st = ensure_kbuf(h, bytes)) != MLVS_OK) return st;
+    dst = h->kbuf.as<unsigned char>();
+  }
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  CK(ops.criterion(h, h->inst[instance], *p, dst));
+  if (!out_on_device) CK(cudaMemcpyAsync(kappa_out, dst, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MLVS_OK;
+}
+
+// Criterion on every cell, grouping, one level per distinct representative space, remap.
+static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_adapt_stats* stats) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int ncell = h->nx * h->ny, nb = h->N1 * h->N1, ninst = h->cfg.n_instances;
+  const size_t per = (size_t)ncell * nb;
+  mlvs_status st = ensure_kbuf(h, per * ninst);
+  if (st != MLVS_OK) return st;
+  if (!h->ea0) {
+    CK(cudaEventCreate(&h->ea0));
+    CK(cudaEventCreate(&h->ea1));
+  }
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  CK(cudaEventRecord(h->ea0, h->stream));
+  for (int i = 0; i < ninst; ++i) CK(ops.criterion(h, h->inst[i], p, h->kbuf.as<unsigned char>() + per * i));
+  CK(cudaEventRecord(h->ea1, h->stream));
+  std::vector<unsigned char> kap(per * ninst);
+  CK(cudaMemcpyAsync(kap.data(), h->kbuf.p, kap.size(), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  float ms_crit = 0.f;
+  CK(cudaEventElapsedTime(&ms_crit, h->ea0, h->ea1));
+  Clustering C = cluster_masks(kap.data(), (long)ncell * ninst, nb, p.tau_clust);
+  // one level per distinct (consistent) representative space
+  std::vector<int> lev_of_cluster(C.reps.size()), new_space;
+  std::map<int, int> level_of_space;
+  for (size_t c = 0; c < C.reps.size(); ++c) {
+    int sp;
+    st = get_space(h, std::vector<int>(C.reps[c].begin(), C.reps[c].end()), &sp);
+    if (st != MLVS_OK) return st;
+    auto it = level_of_space.find(sp);
+    if (it == level_of_space.end()) {
+      it = level_of_space.emplace(sp, (int)new_space.size()).first;
+      new_space.push_back(sp);
+    }
+    lev_of_cluster[c] = it->second;
+  }
+  // the current state's moments and parameters (for the shifts), then the new level set
+  for (auto& I : h->inst)
+    for (int l = 0; l < h->n_levels; ++l)
+      if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
+  const int old_n = h->n_levels;
+  const std::vector<int> old_space = h->level_space;
+  h->n_levels = (int)new_space.size();
+  h->level_space = new_space;
+  int changed = 0;
+  long long upd = 0;
+  for (int i = 0; i < ninst; ++i) {
+    Inst& Old = h->inst[i];
+    std::vector<int> lv(ncell);
+    for (int c = 0; c < ncell; ++c) {
+      lv[c] = lev_of_cluster[C.labels[(size_t)i * ncell + c]];
+      if (h->level_space[lv[c]] != old_space[Old.lvl_of[c]]) ++changed;
+    }
+    Inst New;
+    st = build_levels(h, lv, New);
+    if (st != MLVS_OK) { h->sticky = st; return st; }
+    New.ucell = std::move(Old.ucell);
+    New.W = std::move(Old.W);
+    New.err = std::move(Old.err);
+    cudaError_t e = ops.transfer(h, Old, New);
+    if (e == cudaSuccess) e = ops.moments_of_levels(h, New);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+      h->sticky = MLVS_ERR_CUDA;
+      return fail(h, MLVS_ERR_CUDA, std::string("adaptation remap: ") + cudaGetErrorString(e));
+    }
+    h->inst[i] = std::move(New);
+    for (int l = 0; l < h->n_levels; ++l) upd += (long long)h->inst[i].lv[l].cells.size() * h->inst[i].lv[l].k.nv;
+  }
+  (void)old_n;
+  if (stats) {
+    stats->n_levels = h->n_levels;
+    stats->n_distinct = C.n_distinct;
+    stats->n_changed = changed;
+    stats->updates_per_step = upd;
+    stats->ms_criterion = ms_crit;
+    stats->ms_total = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return check_flags(h);
+}
+
+extern "C" mlvs_status mlvs_adapt(mlvs_handle* h, const mlvs_adapt_params* p, mlvs_adapt_stats* stats) {
+  if (!h) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  mlvs_status st = check_adapt_params(h, p);
+  if (st != MLVS_OK) return st;
+  return adapt_impl(h, *p, stats);
+}
+
+extern "C" mlvs_status mlvs_set_adaptation(mlvs_handle* h, const mlvs_adapt_params* p, int interval) {
+  if (!h) return MLVS_ERR_ARG;
+  if (interval < 0) return fail(h, MLVS_ERR_ARG, "interval < 0");
+  if (interval > 0) {
+    mlvs_status st = check_adapt_params(h, p);
+    if (st != MLVS_OK) return st;
+    h->adapt = *p;
+  }
+  h->adapt_interval = interval;
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_cluster(const unsigned char* kappa, long nrow, int nb, double tau, int* labels,
+                                    unsigned char* reps, int reps_cap, int* n_reps) {
+  if (!kappa || !labels || !reps || !n_reps || nb < 1 || nrow < 0 || !(tau >= 0))
+    return fail(nullptr, MLVS_ERR_ARG, "mlvs_cluster: bad argument");
+  Clustering C = cluster_masks(kappa, nrow, nb, tau);
+  *n_reps = (int)C.reps.size();
+  if ((int)C.reps.size() > reps_cap) return fail(nullptr, MLVS_ERR_ARG, "mlvs_cluster: reps_cap too small");
+  for (long r = 0; r < nrow; ++r) labels[r] = C.labels[r];
+  for (size_t c = 0; c < C.reps.size(); ++c) std::memcpy(reps + c * nb, C.reps[c].data(), nb);
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out, int cap,
+                                        int* nb_out) {
+  if (!h || !nb_out) return MLVS_ERR_ARG;
+  if (!h->ready) return MLVS_ERR_STATE;
+  if (level < 0 || level >= h->n_levels) return MLVS_ERR_ARG;
+  const auto& k = h->spaces[h->level_space[level]].keff;
+  *nb_out = (int)k.size();
+  if (!out) return MLVS_OK;
+  if (cap < (int)k.size()) return MLVS_ERR_ARG;
+  for (size_t b = 0; b < k.size(); ++b) out[b] = (unsigned char)k[b];
+  return MLVS_OK;
+}
+
 extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* stats) {
   if (!h) return MLVS_ERR_ARG;
   if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
@@ -1055,8 +1319,14 @@ extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* s
   h->prof.used = 0;
   h->launches = 0;
   CK(cudaEventRecord(h->ev0, h->stream));
-  for (int n = 0; n < n_steps; ++n)
+  for (int n = 0; n < n_steps; ++n) {
     for (auto& I : h->inst) CK(ops.step(h, I));
+    ++h->steps_done;
+    if (h->adapt_interval > 0 && h->steps_done % h->adapt_interval == 0) {
+      mlvs_status st = adapt_impl(h, h->adapt, nullptr);
+      if (st != MLVS_OK) return st;
+    }
+  }
   CK(cudaEventRecord(h->ev1, h->stream));
   mlvs_status s = check_flags(h);
   if (s != MLVS_OK) return s;

@@ -120,39 +120,32 @@ inline std::vector<int> level1_parent(int n, int L) {
 
 // Parent-child consistency of a block coarsening index (Sec. 3.2): kappa_eff(b) is the
 // largest L <= kappa(b) such that every level-1 block of b's level-L parent has kappa >= L.
-// kappa is [N1*N1] (row by, column bx) in 2-D or [N1] in 1-D.
+// kappa is [N1*N1] (row by, column bx) in 2-D or [N1] in 1-D, values 0..3.
 inline std::vector<int> enforce_consistency(const std::vector<int>& kappa, int n, int D) {
   const int N1 = (int)groups_1d(n, 1).size();
-  std::vector<std::vector<int>> par(4);
-  for (int L = 1; L <= 3; ++L) par[L] = level1_parent(n, L);
-  std::vector<int> out(kappa.size(), 0);
-  if (D == 1) {
-    for (int b = 0; b < N1; ++b) {
-      int best = 0;
-      for (int L = 1; L <= kappa[b]; ++L) {
-        bool ok = true;
-        for (int c = 0; c < N1 && ok; ++c)
-          if (par[L][c] == par[L][b] && kappa[c] < L) ok = false;
-        if (ok) best = L;
-      }
-      out[b] = best;
-    }
-    return out;
+  std::vector<std::vector<int>> par(4), pmin(4);
+  std::vector<int> ng(4, 0);
+  for (int L = 1; L <= 3; ++L) {
+    par[L] = level1_parent(n, L);
+    ng[L] = (int)groups_1d(n, L).size();
+    pmin[L].assign(D == 2 ? ng[L] * ng[L] : ng[L], 1 << 30);
   }
-  for (int by = 0; by < N1; ++by)
-    for (int bx = 0; bx < N1; ++bx) {
-      int best = 0;
-      for (int L = 1; L <= kappa[by * N1 + bx]; ++L) {
-        bool ok = true;
-        for (int cy = 0; cy < N1 && ok; ++cy) {
-          if (par[L][cy] != par[L][by]) continue;
-          for (int cx = 0; cx < N1 && ok; ++cx)
-            if (par[L][cx] == par[L][bx] && kappa[cy * N1 + cx] < L) ok = false;
-        }
-        if (ok) best = L;
-      }
-      out[by * N1 + bx] = best;
+  auto parent = [&](int L, int b) {
+    return D == 2 ? par[L][b / N1] * ng[L] + par[L][b % N1] : par[L][b];
+  };
+  const int nb = D == 2 ? N1 * N1 : N1;
+  for (int L = 1; L <= 3; ++L)
+    for (int b = 0; b < nb; ++b) {
+      int& m = pmin[L][parent(L, b)];
+      m = std::min(m, kappa[b]);
     }
+  std::vector<int> out(kappa.size(), 0);
+  for (int b = 0; b < nb; ++b) {
+    int best = 0;
+    for (int L = 1; L <= std::min(kappa[b], 3); ++L)
+      if (pmin[L][parent(L, b)] >= L) best = L;
+    out[b] = best;
+  }
   return out;
 }
 

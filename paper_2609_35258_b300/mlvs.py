@@ -47,6 +47,17 @@ class mlvs_step_stats(C.Structure):
                 ("ms_phase", C.c_float * 6)]
 
 
+class mlvs_adapt_params(C.Structure):
+    _fields_ = [("C_split", C.c_double), ("C_merge", C.c_double), ("eps_merge", C.c_double),
+                ("tau_clust", C.c_double), ("max_level", C.c_int)]
+
+
+class mlvs_adapt_stats(C.Structure):
+    _fields_ = [("n_levels", C.c_int), ("n_distinct", C.c_int), ("n_changed", C.c_int),
+                ("updates_per_step", C.c_longlong), ("ms_criterion", C.c_float),
+                ("ms_total", C.c_float)]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libmlvs.so not built at {_LIB_PATH}; run __graft_entry__.build()")
@@ -66,6 +77,12 @@ def _load():
                                       C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int]),
         "mlvs_moments_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+        "mlvs_criterion": (C.c_int, [H, C.c_int, C.POINTER(mlvs_adapt_params), C.c_void_p, C.c_int]),
+        "mlvs_adapt": (C.c_int, [H, C.POINTER(mlvs_adapt_params), C.POINTER(mlvs_adapt_stats)]),
+        "mlvs_set_adaptation": (C.c_int, [H, C.POINTER(mlvs_adapt_params), C.c_int]),
+        "mlvs_cluster": (C.c_int, [C.c_void_p, C.c_long, C.c_int, C.c_double, C.POINTER(C.c_int),
+                                   C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_level_kappa": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_destroy": (None, [H]),
         "mlvs_last_error": (C.c_char_p, [H]),
     }
@@ -172,6 +189,48 @@ def mlvs_level_info(h, level):
     _check(_lib.mlvs_level_info(h, level, C.byref(nv), x.ctypes.data_as(P), y.ctypes.data_as(P),
                                 w.ctypes.data_as(P), n), h)
     return x, y, w
+
+
+def adapt_params(C_split, C_merge, eps_merge=0.0, tau_clust=0.05, max_level=3):
+    return mlvs_adapt_params(C_split, C_merge, eps_merge, tau_clust, max_level)
+
+
+def mlvs_level_kappa(h, level):
+    nb = C.c_int()
+    _check(_lib.mlvs_level_kappa(h, level, None, 0, C.byref(nb)), h)
+    out = np.zeros(nb.value, dtype=np.uint8)
+    _check(_lib.mlvs_level_kappa(h, level, out.ctypes.data, nb.value, C.byref(nb)), h)
+    return out
+
+
+def mlvs_criterion(h, instance, params, ncell, nb):
+    """Masks [ncell][nb] (uint8) of the criterion for every cell of one instance."""
+    out = np.zeros((ncell, nb), dtype=np.uint8)
+    _check(_lib.mlvs_criterion(h, instance, C.byref(params), out.ctypes.data, 0), h)
+    return out
+
+
+def mlvs_adapt(h, params):
+    st = mlvs_adapt_stats()
+    _check(_lib.mlvs_adapt(h, C.byref(params), C.byref(st)), h)
+    return st
+
+
+def mlvs_set_adaptation(h, params, interval):
+    _check(_lib.mlvs_set_adaptation(h, C.byref(params) if params is not None else None, interval), h)
+
+
+def mlvs_cluster(kappa, tau):
+    """Host grouping of masks [nrow][nb]: (labels [nrow], reps [ncluster][nb])."""
+    k = np.ascontiguousarray(kappa, dtype=np.uint8)
+    nrow, nb = k.shape
+    labels = np.zeros(nrow, dtype=np.int32)
+    cap = max(nrow, 1)
+    reps = np.zeros((cap, nb), dtype=np.uint8)
+    n = C.c_int()
+    _check(_lib.mlvs_cluster(k.ctypes.data, nrow, nb, tau, labels.ctypes.data_as(C.POINTER(C.c_int)),
+                             reps.ctypes.data, cap, C.byref(n)), None)
+    return labels, reps[: n.value].copy()
 
 
 def mlvs_destroy(h):

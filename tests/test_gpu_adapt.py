@@ -1,0 +1,138 @@
+"""GPU criterion (Sec. 3.2) and adaptation through the C ABI, against the oracle.
+
+The masks are integers decided by FP64 sums compared with thresholds: the kernel and the
+oracle take every decision in FP64, and the masks must agree exactly.  The adaptation
+(criterion + grouping + remap) is checked against the oracle's masks and grouping: every
+cell must end on the space of its oracle cluster's representative mask, and the remap must
+conserve mass, momentum and energy to FP64 rounding.
+"""
+import numpy as np
+import pytest
+
+from tests.helpers import have_gpu, oracle_run, oracle_setup
+from paper_2609_35258_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+if not have_gpu():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from oracle import cluster as ocl, criterion as ocrit, mapping, mlvs as omlvs, vspace  # noqa: E402
+from paper_2609_35258_b300 import mlvs as M  # noqa: E402
+from paper_2609_35258_b300.solver import Solver  # noqa: E402
+
+# thresholds of the cavity runs (C_split, C_merge, eps_merge), Sec. 4
+PAPER = dict(C_split=5e-3, C_merge=2.5e-3, eps_merge=5e-5)
+
+
+def _oracle_masks(base, cells_g, cells_h, spaces, kprevs, C_split, C_merge, eps, max_level=3):
+    """Masks of the oracle criterion for every cell: project to the base grid, then scan."""
+    n = base.n
+    bsp = vspace.uniform_space(base, 0)
+    out = []
+    for g, h, sp, kp in zip(cells_g, cells_h, spaces, kprevs):
+        gb, hb = mapping.project(g, h, sp, bsp)
+        k = ocrit.criterion_2d(gb.reshape(n, n), hb.reshape(n, n), base, kp, C_split, C_merge,
+                               eps_merge=eps if eps > 0 else None, max_level=max_level)
+        out.append(k.ravel())
+    return np.array(out, dtype=np.uint8)
+
+
+def _totals(s):
+    m = s.moments(M.RHO | M.U | M.V | M.RHOE)
+    return np.array([m[0].sum(), (m[0] * m[1]).sum(), (m[0] * m[2]).sum(), m[3].sum()])
+
+
+@pytest.mark.parametrize("n_base,eps,steps", [(41, 5e-5, 3), (41, 0.0, 0), (101, 5e-5, 2)])
+def test_criterion_matches_oracle_uniform(n_base, eps, steps):
+    desc = workloads.cavity(8, n_base=n_base, Kn=0.075, storage="f64")
+    o = oracle_setup(desc)
+    g, h = oracle_run(o, steps)
+    s = Solver(desc)
+    s.step(steps)
+    N1 = len(vspace.axis_groups(n_base, 1))
+    p = M.adapt_params(PAPER["C_split"], PAPER["C_merge"], eps, 0.05, 3)
+    km = M.mlvs_criterion(s.h, 0, p, 64, N1 * N1)
+    kp = np.zeros((N1, N1), dtype=np.int64)
+    ko = _oracle_masks(o["base"], g.reshape(64, -1), h.reshape(64, -1), [o["sp"]] * 64, [kp] * 64,
+                       PAPER["C_split"], PAPER["C_merge"], eps)
+    assert ko.max() > 0                      # something merges
+    np.testing.assert_array_equal(km, ko)
+
+
+def test_criterion_hysteresis_and_inheritance():
+    """Cells on coarse spaces: the criterion reads them on the base grid by inheritance, and
+    blocks in the band [C_merge, C_split] keep the cell's current coarsening."""
+    desc = workloads.periodic_random(6, 4, n_base=41, umax=6.0, storage="f64", amp=0.3)
+    lev = np.array([(c % 3) for c in range(24)], dtype=np.int32)     # levels 0, 1, 2
+    s = Solver(desc, levels=(0, 1, 2))
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(L) for L in (0, 1, 2)]
+    st = omlvs.MLVSState.from_primitives(o["mesh"], o["gas"], book, [keys[0]] * 24,
+                                         desc["init"][..., 0], desc["init"][..., 1:3],
+                                         desc["init"][..., 3], o["dt"], o["opt"])
+    for c in range(24):
+        omlvs.remap(st, c, keys[lev[c]])
+    N1 = len(vspace.axis_groups(41, 1))
+    # a wide band so that the previous status decides many blocks
+    C_split, C_merge = 2e-2, 1e-3
+    p = M.adapt_params(C_split, C_merge, 0.0, 0.05, 3)
+    km = M.mlvs_criterion(s.h, 0, p, 24, N1 * N1)
+    spaces = [book.space(st.sp[c]) for c in range(24)]
+    kprev = [np.full((N1, N1), lev[c], dtype=np.int64) for c in range(24)]
+    ko = _oracle_masks(o["base"], [st.g[c] for c in range(24)], [st.h[c] for c in range(24)], spaces,
+                       kprev, C_split, C_merge, 0.0)
+    np.testing.assert_array_equal(km, ko)
+    # the previous status matters: the same state judged from level 0 differs somewhere
+    km0 = _oracle_masks(o["base"], [st.g[c] for c in range(24)], [st.h[c] for c in range(24)], spaces,
+                        [np.zeros((N1, N1), dtype=np.int64)] * 24, C_split, C_merge, 0.0)
+    assert np.any(km0 != ko)
+
+
+def test_adapt_matches_oracle_grouping_and_conserves():
+    # 64 distinct masks (all of frequency one), five clusters at tau = 0.05
+    desc = workloads.periodic_random(8, 8, n_base=41, umax=6.0, storage="f64", amp=0.3)
+    o = oracle_setup(desc)
+    g, h = oracle_run(o, 2)
+    s = Solver(desc)
+    s.step(2)
+    N1 = len(vspace.axis_groups(41, 1))
+    tau = 0.05
+    p = M.adapt_params(PAPER["C_split"], PAPER["C_merge"], PAPER["eps_merge"], tau, 3)
+    tot0 = _totals(s)
+    st = M.mlvs_adapt(s.h, p)
+    tot1 = _totals(s)
+    assert np.max(np.abs(tot1 - tot0)) < 1e-12 * np.max(np.abs(tot0))
+    # oracle: masks, grouping, representative masks made consistent
+    kp = np.zeros((N1, N1), dtype=np.int64)
+    ko = _oracle_masks(o["base"], g.reshape(64, -1), h.reshape(64, -1), [o["sp"]] * 64, [kp] * 64,
+                       PAPER["C_split"], PAPER["C_merge"], PAPER["eps_merge"])
+    lab, reps = ocl.cluster(ko, tau)
+    keff = [vspace.enforce_consistency(r.reshape(N1, N1).astype(np.int64), 41).ravel() for r in reps]
+    distinct = {tuple(k) for k in keff}
+    assert st.n_levels == len(distinct)
+    lv = s.moments(M.LEVEL)[0].astype(int)
+    for c in range(64):
+        np.testing.assert_array_equal(M.mlvs_level_kappa(s.h, lv[c]), keff[lab[c]])
+    assert st.n_distinct == len(np.unique(ko, axis=0))
+    # and the adapted run keeps conserving
+    assert st.n_levels > 1
+    s.step(5)
+    tot2 = _totals(s)
+    assert np.max(np.abs(tot2 - tot0)) < 1e-12 * np.max(np.abs(tot0))
+
+
+def test_adaptation_interval_runs_inside_step():
+    desc = workloads.cavity(16, n_base=41, Kn=0.075, storage="f32")
+    s = Solver(desc)
+    p = M.adapt_params(PAPER["C_split"], PAPER["C_merge"], PAPER["eps_merge"], 0.05, 3)
+    M.mlvs_set_adaptation(s.h, p, 5)
+    m0 = s.moments(M.RHO)[0].sum()
+    st = s.step(12)
+    assert st.n_levels >= 1
+    lv = s.moments(M.LEVEL)[0]
+    assert lv.max() < st.n_levels
+    m1 = s.moments(M.RHO)[0].sum()
+    assert abs(m1 - m0) / m0 < 1e-6
