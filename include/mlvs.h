@@ -100,6 +100,10 @@ mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out);
  * Sec. 2.3) and the velocity spaces `levels` (Sec. 3.2), allocate the distributions of
  * every instance on level 0, and initialise them to the compatibility-corrected Maxwellian
  * of cfg.init_W (phi~ = phi^eq at rest in equilibrium).  n_base must be odd.
+ * adaptive selects what mlvs_adapt does with the cell masks of the criterion: 1 groups them
+ * into new representative spaces (Sec. 3.2; the level set is replaced); 0 keeps this level
+ * set and moves every cell to the coarsest level (fewest velocities) whose space encloses
+ * its mask, the finest level when none does.
  * Errors: MLVS_ERR_ARG, MLVS_ERR_OOM, MLVS_ERR_CUDA, MLVS_ERR_SINGULAR. */
 mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, double umin, double umax,
                                      int quadrature, int n_levels,
@@ -153,11 +157,13 @@ typedef struct {
 mlvs_status mlvs_criterion(mlvs_handle* h, int instance, const mlvs_adapt_params* p,
                            unsigned char* kappa_out, int out_on_device);
 
-/* Adapt the velocity levels (Sec. 3.2): the criterion on every cell of every instance,
- * the grouping of the cell masks (mlvs_cluster), one level per distinct representative
- * space (the blockwise minimum of its members, made parent-child consistent), and the
- * conservative remap of every cell whose space changed.  The level set is replaced: level
- * indices refer to the new set afterwards.  stats may be NULL.
+/* Adapt the velocity levels (Sec. 3.2): the criterion on every cell of every instance, then
+ * (adaptive = 1) the grouping of the cell masks (mlvs_cluster) with one level per distinct
+ * representative space (the blockwise minimum of its members, made parent-child
+ * consistent), the level set being replaced so that level indices refer to the new set
+ * afterwards; or (adaptive = 0) the coarsest enclosing level of the fixed set per cell.
+ * Every cell whose space changed is remapped conservatively.  stats may be NULL
+ * (n_distinct is 0 with adaptive = 0).
  * Errors: as mlvs_criterion, and MLVS_ERR_OOM. */
 mlvs_status mlvs_adapt(mlvs_handle* h, const mlvs_adapt_params* p, mlvs_adapt_stats* stats);
 

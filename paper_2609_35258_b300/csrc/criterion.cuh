@@ -12,6 +12,15 @@
 //     does not merge, then their level-1 blocks; a merged block writes its level into kappa
 //     of every level-1 block it holds, a level-1 block that does not merge writes 0.
 // "Previous status" is the consistent coarsening index of the space the cell is on.
+//
+// FP64 throughout (the decisions compare sums with thresholds).  The transport test needs,
+// per candidate block, sums of w xi_d m_r over the nodes on each side of xi_d = 0; a level-1
+// block never straddles xi = 0 (the centre node is a group of its own), so these sums add up
+// over level-1 blocks: the node pass stores seven more per-block sums (x g, y g, x^2 g,
+// x y g, y^2 g, x H, y H) when shared memory holds them (tblk), and a candidate block adds
+// its members' sums.  Otherwise the test walks the block's nodes.  The scale S_r of the test
+// uses per-point geometric sums of the cell's space (inherited values are constant on a
+// point's rectangle).
 #pragma once
 #include "mlvs_common.cuh"
 
@@ -31,10 +40,16 @@ struct CritArgs {
   const int* cstart;           // [4][N1+1] row L: first level-(L-1) group of every level-L group
   int ng[4];                   // groups per axis at level L
   const unsigned char* kprev;  // [N1*N1] consistent coarsening index of this space
+  const double* W1;            // [N1] sum of w over every level-1 group
+  const double* X1;            // [N1] sum of w x over every level-1 group
+  const double* geo;           // [5][nv] per point: sum w|x|, sum w|y|, sum w x^2, sum w y^2, sum w|x||y|
   double C_split, C_merge, eps;
   int max_level;
+  int tblk;                    // 1: per-block transport sums in shared memory
   unsigned char* kout;         // [ncell][N1*N1]
 };
+
+enum { CB_XG = 0, CB_YG, CB_XXG, CB_XYG, CB_YYG, CB_XH, CB_YH, CB_N };
 
 constexpr int CRIT_THREADS = 256;
 
@@ -42,6 +57,7 @@ struct CritCtx {
   const CritArgs* a;
   const double* S1;
   const double* S2;
+  const double* TB;            // [CB_N][nb] when a->tblk
   double T1, T2;
   double Sr[4];
   int slot;
@@ -117,6 +133,61 @@ __device__ bool crit_transport_ok(const CritCtx& c, int xa, int xb, int ya, int 
   return err <= a.eps;
 }
 
+// The same test from the per-block sums of the member blocks.
+__device__ inline bool crit_transport_blocks(const CritCtx& c, int bxa, int bxb, int bya, int byb) {
+  const CritArgs& a = *c.a;
+  const int nb = a.N1 * a.N1, mid = a.N1 / 2;   // the centre group has x = 0
+  double wsum = 0, sxw = 0, syw = 0, sg = 0, sH = 0;
+  double F[2][2][4];
+#pragma unroll
+  for (int d = 0; d < 2; ++d)
+#pragma unroll
+    for (int s = 0; s < 2; ++s)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) F[d][s][r] = 0.0;
+  for (int by = bya; by < byb; ++by)
+    for (int bx = bxa; bx < bxb; ++bx) {
+      const int b = by * a.N1 + bx;
+      wsum += a.W1[bx] * a.W1[by];
+      sxw += a.X1[bx] * a.W1[by];
+      syw += a.W1[bx] * a.X1[by];
+      sg += c.S1[b];
+      sH += c.S2[b];
+      const double t[CB_N] = {c.TB[CB_XG * nb + b], c.TB[CB_YG * nb + b], c.TB[CB_XXG * nb + b],
+                              c.TB[CB_XYG * nb + b], c.TB[CB_YYG * nb + b], c.TB[CB_XH * nb + b],
+                              c.TB[CB_YH * nb + b]};
+      const double mx[4] = {t[CB_XG], t[CB_XXG], t[CB_XYG], 0.5 * t[CB_XH]};
+      const double my[4] = {t[CB_YG], t[CB_XYG], t[CB_YYG], 0.5 * t[CB_YH]};
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        if (bx >= mid) F[0][0][r] += mx[r];
+        if (bx <= mid) F[0][1][r] += mx[r];
+        if (by >= mid) F[1][0][r] += my[r];
+        if (by <= mid) F[1][1][r] += my[r];
+      }
+    }
+  const double xbar = sxw / wsum, ybar = syw / wsum;
+  const double gb = sg / wsum, Hb = sH / wsum;
+  const double xb2 = xbar * xbar + ybar * ybar;
+  const double hb = Hb - xb2 * gb;
+  const double mb[4] = {gb, xbar * gb, ybar * gb, 0.5 * (hb + xb2 * gb)};
+  double err = 0.0;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const double xd = d ? ybar : xbar;
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const bool on = (s == 0) ? (xd >= 0.0) : (-xd >= 0.0);
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const double Ft = on ? wsum * xd * mb[r] : 0.0;
+        err = fmax(err, fabs(F[d][s][r] - Ft) / c.Sr[r]);
+      }
+    }
+  }
+  return err <= a.eps;
+}
+
 template <class S>
 __device__ bool crit_decide(const CritCtx& c, int L, int px, int py) {
   const CritArgs& a = *c.a;
@@ -131,6 +202,7 @@ __device__ bool crit_decide(const CritCtx& c, int L, int px, int py) {
   const double IB = fmax(s1 / c.T1, s2 / c.T2);
   if (IB < a.C_merge) {
     if (!(a.eps > 0.0)) return true;
+    if (a.tblk) return crit_transport_blocks(c, bxa, bxb, bya, byb);
     return crit_transport_ok<S>(c, a.g1[bxa], a.g1[bxb], a.g1[bya], a.g1[byb]);
   }
   if (IB <= a.C_split) {
@@ -170,41 +242,57 @@ __global__ void __launch_bounds__(CRIT_THREADS) k_criterion(const CritArgs a) {
   __shared__ double red[10][CRIT_THREADS / 32];
   const int slot = blockIdx.x;
   const int tid = threadIdx.x;
-  // level-1 block sums of w g and w H on the base grid
+  double* TB = csm + 2 * nb;   // [CB_N][nb] when tblk
+  // level-1 block sums of w g and w H (and of the transport moments) on the base grid
   for (int b = tid; b < nb; b += CRIT_THREADS) {
     const int by = b / a.N1, bx = b % a.N1;
     double s1 = 0.0, s2 = 0.0;
+    double t[CB_N];
+#pragma unroll
+    for (int r = 0; r < CB_N; ++r) t[r] = 0.0;
     for (int iy = a.g1[by]; iy < a.g1[by + 1]; ++iy)
       for (int ix = a.g1[bx]; ix < a.g1[bx + 1]; ++ix) {
         double g, H;
         crit_point<S>(a, slot, iy, ix, g, H);
         const double w = a.bw[iy] * a.bw[ix];
-        s1 += w * g;
-        s2 += w * H;
+        const double wg = w * g, wH = w * H;
+        s1 += wg;
+        s2 += wH;
+        if (a.tblk) {
+          const double x = a.bx[ix], y = a.bx[iy];
+          t[CB_XG] += x * wg;
+          t[CB_YG] += y * wg;
+          t[CB_XXG] += x * x * wg;
+          t[CB_XYG] += x * y * wg;
+          t[CB_YYG] += y * y * wg;
+          t[CB_XH] += x * wH;
+          t[CB_YH] += y * wH;
+        }
       }
     S1[b] = s1;
     S2[b] = s2;
+    if (a.tblk)
+#pragma unroll
+      for (int r = 0; r < CB_N; ++r) TB[r * nb + b] = t[r];
   }
   __syncthreads();
-  // totals, and S_r = max_d sum w |xi_d| |m_r| over the base grid for the transport test
+  // totals, and S_r = max_d sum w |xi_d| |m_r| over the base grid for the transport test:
+  // per point of the cell's space, |g| and |H| times the geometric sums of its rectangle
   double v[10];
 #pragma unroll
   for (int r = 0; r < 10; ++r) v[r] = 0.0;
   for (int b = tid; b < nb; b += CRIT_THREADS) { v[0] += S1[b]; v[1] += S2[b]; }
   if (a.eps > 0.0) {
-    for (int i = tid; i < a.n * a.n; i += CRIT_THREADS) {
-      const int iy = i / a.n, ix = i % a.n;
-      double g, H;
-      crit_point<S>(a, slot, iy, ix, g, H);
-      const double x = a.bx[ix], y = a.bx[iy], w = a.bw[iy] * a.bw[ix];
-      const double x2 = x * x + y * y;
-      const double hi = H - x2 * g;
-      const double m[4] = {g, x * g, y * g, 0.5 * (hi + x2 * g)};
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        v[2 + r] += w * fabs(x) * fabs(m[r]);
-        v[6 + r] += w * fabs(y) * fabs(m[r]);
-      }
+    const S* f = reinterpret_cast<const S*>(a.f);
+    for (int k = tid; k < a.nv; k += CRIT_THREADS) {
+      const double g = ld_d<S>(f + (long)k * a.ns + slot);
+      const double h = ld_d<S>(f + ((long)a.nv + k) * a.ns + slot);
+      const double x = a.xi[k], y = a.xi[a.nv + k];
+      const double ag = fabs(g), aH = fabs(h + (x * x + y * y) * g);
+      const double Ax = a.geo[k], Ay = a.geo[a.nv + k], Bx = a.geo[2 * a.nv + k];
+      const double By = a.geo[3 * a.nv + k], Cxy = a.geo[4 * a.nv + k];
+      v[2] += ag * Ax;  v[3] += ag * Bx;  v[4] += ag * Cxy; v[5] += 0.5 * aH * Ax;
+      v[6] += ag * Ay;  v[7] += ag * Cxy; v[8] += ag * By;  v[9] += 0.5 * aH * Ay;
     }
   }
 #pragma unroll
@@ -219,6 +307,7 @@ __global__ void __launch_bounds__(CRIT_THREADS) k_criterion(const CritArgs a) {
   c.a = &a;
   c.S1 = S1;
   c.S2 = S2;
+  c.TB = TB;
   double tot[10];
 #pragma unroll
   for (int r = 0; r < 10; ++r) {

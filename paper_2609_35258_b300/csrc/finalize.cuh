@@ -17,6 +17,11 @@
 //     the tile kernels evaluate up to the rounding of their own products;
 //   * otherwise, directly over the velocities with the tile kernels' model_eval.
 // Sums that enter the moment defect are compensated (FP32) and combined in FP64.
+//
+// On spaces that are not tensor products the direct sums run over every velocity of the
+// point; there a warp serves one point (LANES = 32): each lane sums a strided share of the
+// velocities and the shares are combined by an xor butterfly, which leaves the same bits in
+// every lane.
 #pragma once
 #include "mlvs_common.cuh"
 
@@ -43,9 +48,24 @@ struct PointArgs {
   int compat;
   double wall[4][3];    // (u_w, v_w, T_w)
   int* err;             // device error bits
+  double* scr;          // split finalisation: [FIN_SCR][npt] state and velocity sums
+  int* need;            // split finalisation: [npt] what the velocity sums are for
 };
 
+// Split finalisation of spaces that are not tensor products: k_fin_pre (thread per point:
+// state, uncorrected model), k_fin_sums (warp per point: the velocity sums), k_fin_post
+// (thread per point: correction).  Scratch rows: rho ux uy T, then G[5][5], H[3][3], den.
+enum { FS_RHO = 0, FS_UX, FS_UY, FS_T, FS_G = 4, FS_H = 29, FS_DEN = 38, FIN_SCR = 39 };
+
 enum { ERR_NONFINITE = 1, ERR_POSITIVITY = 2, ERR_SINGULAR = 4 };
+
+// Sum over the LANES lanes of a warp segment (all lanes receive the same value).
+template <int LANES>
+__device__ __forceinline__ double lane_sum(double x) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
 
 // Gaussian elimination with partial pivoting on the rows/columns listed in idx.
 __device__ inline bool solve_small(double A[4][4], double b[4], const int* idx, int n) {
@@ -99,49 +119,64 @@ __device__ inline void axis_sums(const T* ax, int nax, T u, T inv2RT, T lnh, dou
   for (int a = 0; a < 8; ++a) S[a] = acc[a].val();
 }
 
+// Sum over the LANES lanes of a warp segment in the compute type (all lanes receive it).
+template <int LANES, class T>
+__device__ __forceinline__ T lane_sum_t(T x) {
+#pragma unroll
+  for (int o = LANES / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
 // Peculiar moments of the uncorrected model of mp:
-//   G[a][b] = sum w g^S c_x^a c_y^b (a+b <= 4),  H[a][b] = sum w h^S c_x^a c_y^b (a+b <= 2).
+//   G[a][b] = sum w g^S c_x^a c_y^b (a+b <= 4),  H[a][b] = sum w h^S c_x^a c_y^b (a+b <= 2),
+// on a tensor-product space from the one-axis sums.
 template <class T, int D>
-__device__ inline void model_moments(const PointArgs& A, const MP<T>& mp, double G[5][5], double H[3][3]) {
+__device__ inline void axis_moments(const PointArgs& A, const MP<T>& mp, double G[5][5], double H[3][3]) {
+  const StepConst& k = A.k;
+  const T* ax = reinterpret_cast<const T*>(A.ax);
+  double Sx[8], Sy[8];
+  axis_sums<T>(ax, k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
+  if (D == 2) {
+    axis_sums<T>(ax, k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
+  } else {
+    Sy[0] = 1.0;
+    for (int b = 1; b < 8; ++b) Sy[b] = 0.0;
+  }
+  const double kx = (double)mp.kqx, ky = (double)mp.kqy;
+  const double i2 = 2.0 * (double)mp.inv2RT;      // 1/RT as the tile kernels form it
+  const double RT = (double)mp.RT, c0 = k.c0;
+  const double al = RT * c0 * i2, be = RT * (D * c0 + k.twoK);
   for (int a = 0; a < 5; ++a)
     for (int b = 0; b < 5; ++b) G[a][b] = 0.0;
   for (int a = 0; a < 3; ++a)
     for (int b = 0; b < 3; ++b) H[a][b] = 0.0;
-  const StepConst& k = A.k;
-  if (k.nax > 0) {
-    const T* ax = reinterpret_cast<const T*>(A.ax);
-    double Sx[8], Sy[8];
-    axis_sums<T>(ax, k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
-    if (D == 2) {
-      axis_sums<T>(ax, k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
-    } else {
-      Sy[0] = 1.0;
-      for (int b = 1; b < 8; ++b) Sy[b] = 0.0;
+  for (int a = 0; a < 5; ++a)
+    for (int b = 0; a + b < 5; ++b) {
+      const double cub = kx * (Sx[a + 3] * Sy[b] + Sx[a + 1] * Sy[b + 2]) +
+                         ky * (Sx[a + 2] * Sy[b + 1] + Sx[a] * Sy[b + 3]);
+      const double lin = kx * Sx[a + 1] * Sy[b] + ky * Sx[a] * Sy[b + 1];
+      G[a][b] = Sx[a] * Sy[b] - (D + 2) * lin + i2 * cub;
+      if (a + b < 3) H[a][b] = RT * c0 * Sx[a] * Sy[b] + al * cub - be * lin;
     }
-    const double kx = (double)mp.kqx, ky = (double)mp.kqy;
-    const double i2 = 2.0 * (double)mp.inv2RT;      // 1/RT as the tile kernels form it
-    const double RT = (double)mp.RT, c0 = k.c0;
-    const double al = RT * c0 * i2, be = RT * (D * c0 + k.twoK);
-    for (int a = 0; a < 5; ++a)
-      for (int b = 0; a + b < 5; ++b) {
-        const double cub = kx * (Sx[a + 3] * Sy[b] + Sx[a + 1] * Sy[b + 2]) +
-                           ky * (Sx[a + 2] * Sy[b + 1] + Sx[a] * Sy[b + 3]);
-        const double lin = kx * Sx[a + 1] * Sy[b] + ky * Sx[a] * Sy[b + 1];
-        G[a][b] = Sx[a] * Sy[b] - (D + 2) * lin + i2 * cub;
-        if (a + b < 3) H[a][b] = RT * c0 * Sx[a] * Sy[b] + al * cub - be * lin;
-      }
-    return;
-  }
-  // direct sums over the velocities
+}
+
+// The same moments summed directly over the velocities [lane, nv) with stride LANES and
+// combined over the lanes (compensated sums in FP64, the others in the compute type).
+template <class T, int D, int LANES>
+__device__ inline void direct_moments(const PointArgs& A, const MP<T>& mp, int lane, double G[5][5],
+                                      double H[3][3]) {
+  const StepConst& k = A.k;
   const T* vt = reinterpret_cast<const T*>(A.vt);
   const int nv = k.nv;
   const T c0 = T(k.c0), twoK = T(k.twoK);
   KSum<T> g00, g10, g01, e0;
   g00.zero(); g10.zero(); g01.zero(); e0.zero();
   T gs[15], hs[6];
+#pragma unroll
   for (int j = 0; j < 15; ++j) gs[j] = T(0);
+#pragma unroll
   for (int j = 0; j < 6; ++j) hs[j] = T(0);
-  for (int v = 0; v < nv; ++v) {
+  for (int v = lane; v < nv; v += LANES) {
     const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0), wxv = vt[2 * nv + v], wyv = vt[3 * nv + v];
     T gv, hv;
     model_eval<T, D>(mp, xx, yy, c0, twoK, gv, hv);
@@ -167,24 +202,29 @@ __device__ inline void model_moments(const PointArgs& A, const MP<T>& mp, double
       qx *= cx;
     }
   }
-  int j = 0, jh = 0;
   for (int a = 0; a < 5; ++a)
+    for (int b = 0; b < 5; ++b) G[a][b] = 0.0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) H[a][b] = 0.0;
+  int j = 0, jh = 0;
+#pragma unroll
+  for (int a = 0; a < 5; ++a)
+#pragma unroll
     for (int b = 0; a + b < 5; ++b) {
-      G[a][b] = (double)gs[j++];
-      if (a + b < 3) H[a][b] = (double)hs[jh++];
+      G[a][b] = (double)lane_sum_t<LANES, T>(gs[j++]);
+      if (a + b < 3) H[a][b] = (double)lane_sum_t<LANES, T>(hs[jh++]);
     }
-  G[0][0] = g00.val();
-  G[1][0] = g10.val();
-  G[0][1] = g01.val();
+  G[0][0] = lane_sum<LANES>(g00.val());
+  G[1][0] = lane_sum<LANES>(g10.val());
+  G[0][1] = lane_sum<LANES>(g01.val());
   // keep the compensated energy-row sum: fold it into the H[0][0] slot
-  H[0][0] = 2.0 * e0.val() - G[2][0] - G[0][2];
+  H[0][0] = 2.0 * lane_sum<LANES>(e0.val()) - G[2][0] - G[0][2];
 }
 
-// Model parameters of a point with state (rho, u, T, q), with the compatibility correction.
+// Model parameters of a point with state (rho, u, T, q), before the correction.
 template <class T, int D>
-__device__ inline bool point_model(const PointArgs& A, double rho, double ux, double uy, double Tm,
-                                   double qx, double qy, MP<T>& mp) {
-  const GasDev& g = A.gas;
+__device__ inline void point_params(const GasDev& g, double rho, double ux, double uy, double Tm, double qx,
+                                    double qy, MP<T>& mp) {
   const double RT = g.R * Tm;
   const double p = rho * RT;
   const double kap = (1.0 - g.Pr) / (5.0 * p * RT);
@@ -194,9 +234,13 @@ __device__ inline bool point_model(const PointArgs& A, double rho, double ux, do
   mp.kqx = T(kap * qx); mp.kqy = T(kap * qy);
   mp.RT = T(RT);
   mp.b0 = T(0); mp.b1 = T(0); mp.b2 = T(0); mp.b3 = T(0);
-  if (!A.compat) return true;
-  double G[5][5], H[3][3];
-  model_moments<T, D>(A, mp, G, H);
+}
+
+// The four-moment compatibility correction (b0..b3 of mp) from the model moments.
+template <class T, int D>
+__device__ inline bool point_correct(const GasDev& g, double rho, double ux, double uy, double Tm,
+                                     const double G[5][5], const double H[3][3], MP<T>& mp) {
+  const double RT = g.R * Tm;
   // rows: (g, c_x g, c_y g, (|c|^2 g + h)/2); columns: basis (1, c_x, c_y, |c|^2)
   double M[4][4], b[4];
   M[0][0] = G[0][0]; M[0][1] = G[1][0]; M[0][2] = G[0][1]; M[0][3] = G[2][0] + G[0][2];
@@ -218,6 +262,18 @@ __device__ inline bool point_model(const PointArgs& A, double rho, double ux, do
   return true;
 }
 
+// Model parameters of a point with state (rho, u, T, q), with the compatibility correction.
+template <class T, int D>
+__device__ inline bool point_model(const PointArgs& A, double rho, double ux, double uy, double Tm,
+                                   double qx, double qy, MP<T>& mp) {
+  point_params<T, D>(A.gas, rho, ux, uy, Tm, qx, qy, mp);
+  if (!A.compat) return true;
+  double G[5][5], H[3][3];
+  if (A.k.nax > 0) axis_moments<T, D>(A, mp, G, H);
+  else direct_moments<T, D, 1>(A, mp, 0, G, H);
+  return point_correct<T, D>(A.gas, rho, ux, uy, Tm, G, H, mp);
+}
+
 template <class T>
 __device__ __forceinline__ void store_mp(T* P, long n, long i, const MP<T>& m, T kind) {
   P[P_UX * n + i] = m.ux; P[P_UY * n + i] = m.uy; P[P_LNH * n + i] = m.lnh;
@@ -234,8 +290,8 @@ __device__ __forceinline__ int wrap_or_clamp_h(int g, int n, int periodic) {
 
 // Normal mass flux of the unit-density wall Maxwellian over the velocities entering the
 // domain: den = sum_{xi.n_in > 0} w (xi.n_in) g_w, with the tile kernels' evaluation.
-template <class T, int D>
-__device__ inline double wall_den(const PointArgs& A, const MP<T>& mp, bool xdir, T sgn) {
+template <class T, int D, int LANES>
+__device__ inline double wall_den(const PointArgs& A, const MP<T>& mp, bool xdir, T sgn, int lane) {
   const StepConst& k = A.k;
   if (k.nax > 0) {
     const T* ax = reinterpret_cast<const T*>(A.ax);
@@ -254,7 +310,7 @@ __device__ inline double wall_den(const PointArgs& A, const MP<T>& mp, bool xdir
   const int nv = k.nv;
   KSum<T> den;
   den.zero();
-  for (int v = 0; v < nv; ++v) {
+  for (int v = lane; v < nv; v += LANES) {
     const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0);
     const T xin = sgn * (xdir ? xx : yy);
     if (xin > T(0)) {
@@ -263,67 +319,121 @@ __device__ inline double wall_den(const PointArgs& A, const MP<T>& mp, bool xdir
       den.add(vt[2 * nv + v] * (vt[3 * nv + v] * (xin * gv)));
     }
   }
-  return den.val();
+  return lane_sum<LANES>(den.val());
 }
 
 // Cells (is_face = 0): Eq. discrete_W, Eq. discrete_q, tau = mu(T)/p, blending of phi-bar-plus.
 // Faces (is_face = 1): Eq. W_from_bar, q = 2 tau/(2 tau + s Pr) q-bar, Eq. recover_phi weights;
 // wall faces: rho_w from the zero net normal mass flux.
-template <class T, int D>
-__global__ void k_finalize(const PointArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.npt) return;
-  if (a.is_face && a.frole && a.frole[i] != FR_NORMAL && a.frole[i] != FR_CROSS) return;
+// One thread per point.  PART 0: everything (tensor-product spaces); PART 1: k_fin_pre's
+// share of the split path (state and uncorrected model into the parameters and scratch).
+template <class T, int D, int PART>
+__device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
+  bool valid = i < a.npt;
+  if (valid && a.is_face && a.frole && a.frole[i] != FR_NORMAL && a.frole[i] != FR_CROSS) valid = false;
+  if (!valid) return;
   const StepConst& k = a.k;
   const T* cp = reinterpret_cast<const T*>(a.cprm);
   const T* uc = reinterpret_cast<const T*>(a.ucell);
   T* po = reinterpret_cast<T*>(a.prm_out);
   const long nc = k.ncell;
-  const long wi = (!a.is_face && a.ids) ? a.ids[i] : i;   // global cell id of a cell point
+  const GasDev& g = a.gas;
   double M[NMOM];
 #pragma unroll
   for (int m = 0; m < NMOM; ++m) M[m] = 0.0;
-  for (int c = 0; c < k.nchunk; ++c)
-#pragma unroll
-    for (int m = 0; m < NMOM; ++m) M[m] += a.part[((long)c * NMOM + m) * a.npt + i];
-
-  T shx, shy;
+  T shx = T(0), shy = T(0);
   int kind = FK_INTERIOR;
   int side = -1;
-  if (!a.is_face) {
-    shx = cp[P_UX * (long)a.npt + i];
-    shy = cp[P_UY * (long)a.npt + i];
-  } else {
-    int sL, sR;
-    const int nxf = k.nfx * k.ny;
-    if (i < nxf) {
-      const int gj = i / k.nfx, gi = i % k.nfx;
-      sL = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi - 1, k.nx, k.px);
-      sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi, k.nx, k.px);
-      if (!k.px && gi == 0 && k.bc[0] == BC_WALL) { kind = FK_WALL_LO; side = 0; }
-      if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) { kind = FK_WALL_HI; side = 1; }
+  {
+    for (int c = 0; c < k.nchunk; ++c)
+#pragma unroll
+      for (int m = 0; m < NMOM; ++m) M[m] += a.part[((long)c * NMOM + m) * a.npt + i];
+    if (!a.is_face) {
+      shx = cp[P_UX * (long)a.npt + i];
+      shy = cp[P_UY * (long)a.npt + i];
     } else {
-      const int r = i - nxf;
-      const int gj = r / k.nx, gi = r % k.nx;
-      sL = wrap_or_clamp_h(gj - 1, k.ny, k.py) * k.nx + gi;
-      sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + gi;
-      if (!k.py && gj == 0 && k.bc[2] == BC_WALL) { kind = FK_WALL_LO; side = 2; }
-      if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) { kind = FK_WALL_HI; side = 3; }
+      int sL, sR;
+      const int nxf = k.nfx * k.ny;
+      if (i < nxf) {
+        const int gj = i / k.nfx, gi = i % k.nfx;
+        sL = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi - 1, k.nx, k.px);
+        sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi, k.nx, k.px);
+        if (!k.px && gi == 0 && k.bc[0] == BC_WALL) { kind = FK_WALL_LO; side = 0; }
+        if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) { kind = FK_WALL_HI; side = 1; }
+      } else {
+        const int r = i - nxf;
+        const int gj = r / k.nx, gi = r % k.nx;
+        sL = wrap_or_clamp_h(gj - 1, k.ny, k.py) * k.nx + gi;
+        sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + gi;
+        if (!k.py && gj == 0 && k.bc[2] == BC_WALL) { kind = FK_WALL_LO; side = 2; }
+        if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) { kind = FK_WALL_HI; side = 3; }
+      }
+      shx = T(0.5) * (uc[sL] + uc[sR]);
+      shy = (D == 2) ? T(0.5) * (uc[nc + sL] + uc[nc + sR]) : T(0);
     }
-    shx = T(0.5) * (uc[sL] + uc[sR]);
-    shy = (D == 2) ? T(0.5) * (uc[nc + sL] + uc[nc + sR]) : T(0);
   }
-  const GasDev& g = a.gas;
+  // the state and the uncorrected model; need: 1 = wall density sum, 2 = model moments
   MP<T> mp;
+  mp.ux = mp.uy = mp.lnh = mp.inv2RT = mp.kqx = mp.kqy = mp.RT = T(0);
+  mp.b0 = mp.b1 = mp.b2 = mp.b3 = mp.c1 = mp.c2 = T(0);
+  int need = 0;
+  double rho = 0, ux = 0, uy = 0, Tm = 0, qx = 0, qy = 0, tau = 0;
+  bool state_ok = false;
   if (kind != FK_INTERIOR) {
-    // diffuse wall: unit-density wall Maxwellian, rho_w = -M_out / den
     const double uw = a.wall[side][0], vw = a.wall[side][1], Tw = a.wall[side][2];
     const double RT = g.R * Tw;
     mp.ux = T(uw); mp.uy = T(vw);
     mp.lnh = T(-0.5 * log(2.0 * 3.14159265358979323846 * RT));
-    mp.inv2RT = T(0.5 / RT); mp.kqx = T(0); mp.kqy = T(0); mp.RT = T(RT);
-    mp.b0 = T(0); mp.b1 = T(0); mp.b2 = T(0); mp.b3 = T(0);
-    const double den = wall_den<T, D>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1));
+    mp.inv2RT = T(0.5 / RT); mp.RT = T(RT);
+    need = 1;
+  } else {
+    rho = M[MO_0];
+    const double upx = M[MO_X] / rho, upy = (D == 2) ? M[MO_Y] / rho : 0.0;
+    const double u2 = upx * upx + upy * upy;
+    ux = (double)shx + upx;
+    uy = (D == 2) ? (double)shy + upy : 0.0;
+    Tm = (M[MO_E] - rho * u2) / ((3.0 + g.K) * rho * g.R);
+    // q = 1/2 [J - 2 u'.G - u' E' + 2 rho |u'|^2 u']  in the shifted frame
+    qx = 0.5 * (M[MO_JX] - 2.0 * (upx * M[MO_GXX] + upy * M[MO_GXY]) - upx * M[MO_E] + 2.0 * rho * u2 * upx);
+    qy = (D == 2) ? 0.5 * (M[MO_JY] - 2.0 * (upx * M[MO_GXY] + upy * M[MO_GYY]) - upy * M[MO_E] + 2.0 * rho * u2 * upy) : 0.0;
+    const double p = rho * g.R * Tm;
+    const double mu = g.mu_ref * pow(Tm / g.T_ref, g.omega);
+    tau = mu / p;
+    const double hdt = a.is_face ? 0.5 * k.dt : k.dt;    // dt at cells, s at faces
+    const double qf = 2.0 * tau / (2.0 * tau + hdt * g.Pr);
+    qx *= qf;
+    qy *= qf;
+    state_ok = isfinite(rho) && isfinite(Tm) && isfinite(ux) && isfinite(uy) && rho > 0.0 && Tm > 0.0;
+    if (state_ok) {
+      point_params<T, D>(g, rho, ux, uy, Tm, qx, qy, mp);
+      if (a.compat) need = 2;
+    }
+  }
+  if (PART == 1) {
+    // split path: the uncorrected model and what k_fin_sums / k_fin_post need
+    a.need[i] = need == 1 ? 16 + 4 * side + kind : need;
+    a.scr[FS_RHO * (long)a.npt + i] = kind != FK_INTERIOR ? M[MO_0] : rho;
+    a.scr[FS_UX * (long)a.npt + i] = ux;
+    a.scr[FS_UY * (long)a.npt + i] = uy;
+    a.scr[FS_T * (long)a.npt + i] = Tm;
+  }
+  double den = 0.0;
+  double G[5][5], H[3][3];
+  if (PART == 0) {
+    if (need == 1) den = wall_den<T, D, 1>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1), 0);
+    if (need == 2) {
+      if (k.nax > 0) axis_moments<T, D>(a, mp, G, H);
+      else direct_moments<T, D, 1>(a, mp, 0, G, H);
+    }
+  }
+  if (kind != FK_INTERIOR) {
+    if (PART == 1) {   // rho_w in k_fin_post
+      store_mp<T>(po, a.npt, i, mp, T(kind));
+      po[P_SHX * (long)a.npt + i] = shx;
+      po[P_SHY * (long)a.npt + i] = shy;
+      return;
+    }
+    // diffuse wall: unit-density wall Maxwellian, rho_w = -M_out / den
     const double rw = -M[MO_0] / den;
     // rho_w as an unevaluated sum hi + lo, so that its rounding leaves no net wall mass flux
     mp.c2 = T(rw);
@@ -334,29 +444,8 @@ __global__ void k_finalize(const PointArgs a) {
     if (!(rw >= 0.0) || !isfinite(rw)) atomicOr(a.err, ERR_POSITIVITY);
     return;
   }
-  const double rho = M[MO_0];
-  const double upx = M[MO_X] / rho, upy = (D == 2) ? M[MO_Y] / rho : 0.0;
-  const double u2 = upx * upx + upy * upy;
-  const double ux = (double)shx + upx, uy = (D == 2) ? (double)shy + upy : 0.0;
-  const double Tm = (M[MO_E] - rho * u2) / ((3.0 + g.K) * rho * g.R);
-  // q = 1/2 [J - 2 u'.G - u' E' + 2 rho |u'|^2 u']  in the shifted frame
-  double qx = 0.5 * (M[MO_JX] - 2.0 * (upx * M[MO_GXX] + upy * M[MO_GXY]) - upx * M[MO_E] + 2.0 * rho * u2 * upx);
-  double qy = (D == 2) ? 0.5 * (M[MO_JY] - 2.0 * (upx * M[MO_GXY] + upy * M[MO_GYY]) - upy * M[MO_E] + 2.0 * rho * u2 * upy) : 0.0;
-  const double p = rho * g.R * Tm;
-  const double mu = g.mu_ref * pow(Tm / g.T_ref, g.omega);
-  const double tau = mu / p;
-  const double hdt = a.is_face ? 0.5 * k.dt : k.dt;    // dt at cells, s at faces
-  const double qf = 2.0 * tau / (2.0 * tau + hdt * g.Pr);
-  qx *= qf;
-  qy *= qf;
-  const bool state_ok = isfinite(rho) && isfinite(Tm) && isfinite(ux) && isfinite(uy) && rho > 0.0 && Tm > 0.0;
   bool ok = true;
-  if (state_ok) {
-    ok = point_model<T, D>(a, rho, ux, uy, Tm, qx, qy, mp);
-  } else {
-    mp.ux = mp.uy = mp.lnh = mp.inv2RT = mp.kqx = mp.kqy = mp.RT = T(0);
-    mp.b0 = mp.b1 = mp.b2 = mp.b3 = T(0);
-  }
+  if (PART == 0 && need == 2) ok = point_correct<T, D>(g, rho, ux, uy, Tm, G, H, mp);
   const double s = 0.5 * k.dt;
   if (!a.is_face) {
     mp.c1 = T(3.0 * s / (2.0 * tau + k.dt));
@@ -369,6 +458,7 @@ __global__ void k_finalize(const PointArgs a) {
   po[P_SHX * (long)a.npt + i] = shx;
   po[P_SHY * (long)a.npt + i] = shy;
   if (a.W) {
+    const long wi = a.ids ? a.ids[i] : i;   // global cell id of a cell point
     a.W[0 * nc + wi] = rho;
     a.W[1 * nc + wi] = ux;
     a.W[2 * nc + wi] = uy;
@@ -381,6 +471,80 @@ __global__ void k_finalize(const PointArgs a) {
   if (!ok) atomicOr(a.err, ERR_SINGULAR);
   if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.err, ERR_NONFINITE);
   else if (!(rho > 0.0) || !(Tm > 0.0)) atomicOr(a.err, ERR_POSITIVITY);
+}
+
+template <class T, int D>
+__global__ void k_finalize(const PointArgs a) {
+  finalize_point<T, D, 0>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+template <class T, int D>
+__global__ void k_fin_pre(const PointArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < a.npt) a.need[i] = 0;
+  finalize_point<T, D, 1>(a, i);
+}
+
+// Velocity sums of the split path, a warp per point (blockDim a multiple of 32).
+template <class T, int D>
+__global__ void k_fin_sums(const PointArgs a) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (i >= a.npt) return;
+  const int need = a.need[i];
+  if (need == 0) return;
+  const T* P = reinterpret_cast<const T*>(a.prm_out);
+  MP<T> q;
+  q.load(P, a.npt, i);
+  q.b0 = q.b1 = q.b2 = q.b3 = T(0);
+  const long n = a.npt;
+  if (need >= 16) {
+    const int side = (need - 16) >> 2, kind = (need - 16) & 3;
+    const double d = wall_den<T, D, 32>(a, q, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1), lane);
+    if (lane == 0) a.scr[FS_DEN * n + i] = d;
+    return;
+  }
+  double G[5][5], H[3][3];
+  direct_moments<T, D, 32>(a, q, lane, G, H);
+  if (lane == 0) {
+#pragma unroll
+    for (int r = 0; r < 25; ++r) a.scr[(FS_G + r) * n + i] = G[r / 5][r % 5];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) a.scr[(FS_H + r) * n + i] = H[r / 3][r % 3];
+  }
+}
+
+// Correction of the split path: wall densities and the four-moment solve.
+template <class T, int D>
+__global__ void k_fin_post(const PointArgs a) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.npt) return;
+  const int need = a.need[i];
+  if (need == 0) return;
+  T* po = reinterpret_cast<T*>(a.prm_out);
+  const long n = a.npt;
+  if (need >= 16) {
+    const double rw = -a.scr[FS_RHO * n + i] / a.scr[FS_DEN * n + i];
+    const T hi = T(rw);
+    po[P_C2 * n + i] = hi;
+    po[P_C1 * n + i] = T(rw - (double)hi);
+    if (!(rw >= 0.0) || !isfinite(rw)) atomicOr(a.err, ERR_POSITIVITY);
+    return;
+  }
+  MP<T> mp;
+  mp.load(po, n, i);
+  double G[5][5], H[3][3];
+#pragma unroll
+  for (int r = 0; r < 25; ++r) G[r / 5][r % 5] = a.scr[(FS_G + r) * n + i];
+#pragma unroll
+  for (int r = 0; r < 9; ++r) H[r / 3][r % 3] = a.scr[(FS_H + r) * n + i];
+  const bool ok = point_correct<T, D>(a.gas, a.scr[FS_RHO * n + i], a.scr[FS_UX * n + i], a.scr[FS_UY * n + i],
+                                      a.scr[FS_T * n + i], G, H, mp);
+  po[P_B0 * n + i] = mp.b0;
+  po[P_B1 * n + i] = mp.b1;
+  po[P_B2 * n + i] = mp.b2;
+  po[P_B3 * n + i] = mp.b3;
+  if (!ok) atomicOr(a.err, ERR_SINGULAR);
 }
 
 // Initial parameters from (rho, u, v, T) with q = 0 (phi~ = phi^eq at t = 0).

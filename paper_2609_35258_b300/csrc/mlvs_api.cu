@@ -82,6 +82,7 @@ struct SpaceRt {
   int nax = 0;               // > 0: tensor product of one axis of nax points
   DevBuf vt, ax, ainv;
   DevBuf owner_d, xid, kp_d; // criterion tables: owner, FP64 coordinates, keff (bytes)
+  DevBuf geo;                // [5][nv] geometric sums of every point's rectangle
 };
 
 struct CSR {
@@ -96,6 +97,7 @@ struct LevelRt {
   std::vector<int> cells;    // global cell id of every slot
   StepConst k;
   DevBuf f[2], prm[2], fprm, cpart, fpart, ids, frole, fslot, ghost_of, ghost, X, Y, tiles;
+  DevBuf fscr, fneed;        // split finalisation scratch (spaces that are not tensor products)
   int nghost = 0, nX = 0, nY = 0, ntiles = 0;
   int cur = 0, pcur = 0;
   bool fresh = false;
@@ -160,8 +162,9 @@ struct mlvs_handle {
   // criterion tables of the base grid (2-D)
   int N1 = 0;
   int ng[4] = {0, 0, 0, 0};
-  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, kbuf;
+  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, kbuf;
   mlvs_adapt_params adapt{};
+  int adaptive = 0;          // 1: mlvs_adapt groups the masks; 0: fixed level set
   int adapt_interval = 0;
   long long steps_done = 0;
   bool ready = false;
@@ -279,6 +282,27 @@ static mlvs_status get_space(mlvs_handle* h, const std::vector<int>& kappa, int*
     CK(upload(S.xid, xid, h->stream));
     CK(upload(S.owner_d, S.owner, h->stream));
     CK(upload(S.kp_d, std::vector<unsigned char>(keff.begin(), keff.end()), h->stream));
+    // per point: sum w|x|, sum w|y|, sum w x^2, sum w y^2, sum w|x||y| over its rectangle
+    std::vector<double> geo(5 * (size_t)nv, 0.0);
+    if (h->D == 2) {
+      const auto& bx = h->base.x;
+      const auto& bw = h->base.w;
+      for (int v = 0; v < nv; ++v) {
+        double w0x = 0, w1x = 0, w2x = 0, w0y = 0, w1y = 0, w2y = 0;
+        for (int i = S.vs.rect[4 * v]; i < S.vs.rect[4 * v + 1]; ++i) {
+          w0x += bw[i]; w1x += bw[i] * std::fabs(bx[i]); w2x += bw[i] * bx[i] * bx[i];
+        }
+        for (int i = S.vs.rect[4 * v + 2]; i < S.vs.rect[4 * v + 3]; ++i) {
+          w0y += bw[i]; w1y += bw[i] * std::fabs(bx[i]); w2y += bw[i] * bx[i] * bx[i];
+        }
+        geo[v] = w1x * w0y;
+        geo[nv + v] = w0x * w1y;
+        geo[2 * (size_t)nv + v] = w2x * w0y;
+        geo[3 * (size_t)nv + v] = w0x * w2y;
+        geo[4 * (size_t)nv + v] = w1x * w1y;
+      }
+    }
+    CK(upload(S.geo, geo, h->stream));
   }
   h->spaces.push_back(std::move(S));
   *out = (int)h->spaces.size() - 1;
@@ -340,6 +364,20 @@ template <class S, class T, int D> struct Runner {
   static constexpr size_t SM1 = TileSmem<T, TX, TY, D, VB, 1>::BYTES;
   static constexpr int FIN_BLOCK = 64;
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
+  // tensor-product spaces: one kernel (one-axis sums per thread); others: the split path
+  // (state per thread, velocity sums per warp, correction per thread)
+  static void launch_finalize(mlvs_handle* h, PointArgs a, LevelRt& L) {
+    if (a.k.nax > 0) {
+      k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+      return;
+    }
+    a.scr = L.fscr.as<double>();
+    a.need = L.fneed.as<int>();
+    h->launches += 2;
+    k_fin_pre<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+    k_fin_sums<T, D><<<std::max(1, (a.npt * 32 + 127) / 128), 128, 0, h->stream>>>(a);
+    k_fin_post<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+  }
 
   static cudaError_t set_smem_limits() {
     const void* fn[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false>,
@@ -390,6 +428,8 @@ template <class S, class T, int D> struct Runner {
     a.W = nullptr;
     a.cprm = nullptr;
     a.prm_out = nullptr;
+    a.scr = nullptr;
+    a.need = nullptr;
     return a;
   }
 
@@ -433,7 +473,7 @@ template <class S, class T, int D> struct Runner {
     a.W = I.W.as<double>();
     mark_begin(h, 0);
     ++h->launches;
-    k_finalize<T, D><<<fin_grid(n), FIN_BLOCK, 0, h->stream>>>(a);
+    launch_finalize(h, a, L);
     k_scatter_velocity<T><<<(n + 127) / 128, 128, 0, h->stream>>>(L.prm[L.pcur ^ 1].as<T>(), n, L.ids.as<int>(),
                                                                  I.ucell.as<T>(), h->nx * h->ny);
     mark_end(h);
@@ -531,7 +571,7 @@ template <class S, class T, int D> struct Runner {
       a.cprm = L.prm[L.pcur].p;
       a.prm_out = L.fprm.p;
       mark_begin(h, 2);
-      k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+      launch_finalize(h, a, L);
       mark_end(h);
     }
     for (int l : I.order) {
@@ -634,7 +674,9 @@ template <class S, class T, int D> struct Runner {
   // masks of the criterion (Sec. 3.2) of every cell of an instance into kout[ncell][N1*N1]
   static cudaError_t criterion(mlvs_handle* h, Inst& I, const mlvs_adapt_params& p, unsigned char* kout) {
     const int nb = h->N1 * h->N1;
-    const size_t smem = 2ull * nb * sizeof(double);
+    // per-block transport sums in shared memory when they fit
+    const int tblk = (p.eps_merge > 0.0 && (2ull + CB_N) * nb * sizeof(double) <= 220ull * 1024) ? 1 : 0;
+    const size_t smem = (2ull + (tblk ? CB_N : 0)) * nb * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_criterion<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int l = 0; l < h->n_levels; ++l) {
@@ -657,6 +699,10 @@ template <class S, class T, int D> struct Runner {
       a.cstart = h->cstart_d.as<int>();
       for (int q = 0; q < 4; ++q) a.ng[q] = h->ng[q];
       a.kprev = sp.kp_d.as<unsigned char>();
+      a.W1 = h->w1_d.as<double>();
+      a.X1 = h->x1_d.as<double>();
+      a.geo = sp.geo.as<double>();
+      a.tblk = tblk;
       a.C_split = p.C_split;
       a.C_merge = p.C_merge;
       a.eps = p.eps_merge;
@@ -901,6 +947,11 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
         L.Y.alloc(2ull * k.nv * L.nY * h->tsize) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     CK(cudaMemsetAsync(L.fprm.p, 0, L.fprm.n, h->stream));
+    if (sp.nax == 0) {
+      const size_t np = std::max<size_t>(std::max<size_t>(nface, nc), 1);
+      if (L.fscr.alloc(FIN_SCR * np * sizeof(double)) != cudaSuccess || L.fneed.alloc(np * sizeof(int)) != cudaSuccess)
+        return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
+    }
   }
   for (auto& r : I.ghosts) CK(upload(r.items_d, r.items, h->stream));
   for (auto& r : I.fluxes) CK(upload(r.items_d, r.items, h->stream));
@@ -1047,6 +1098,14 @@ static mlvs_status build_criterion_tables(mlvs_handle* h, int n) {
   CK(upload(h->g1_d, g1s, h->stream));
   CK(upload(h->pstart_d, ps, h->stream));
   CK(upload(h->cstart_d, cs, h->stream));
+  std::vector<double> W1(N1, 0.0), X1(N1, 0.0);
+  for (int b = 0; b < N1; ++b)
+    for (int i = g1[b].first; i < g1[b].second; ++i) {
+      W1[b] += h->base.w[i];
+      X1[b] += h->base.w[i] * h->base.x[i];
+    }
+  CK(upload(h->w1_d, W1, h->stream));
+  CK(upload(h->x1_d, X1, h->stream));
   return MLVS_OK;
 }
 
@@ -1058,7 +1117,8 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
   if (h->ready) return fail(h, MLVS_ERR_STATE, "velocity levels are already set");
   if (n_levels < 1 || !levels) return fail(h, MLVS_ERR_ARG, "need at least one level");
   if (!(umax > umin)) return fail(h, MLVS_ERR_ARG, "umax must exceed umin");
-  if (adaptive != 0) return fail(h, MLVS_ERR_ARG, "use mlvs_set_cell_levels / mlvs_adapt for level changes");
+  if (adaptive != 0 && adaptive != 1) return fail(h, MLVS_ERR_ARG, "adaptive must be 0 or 1");
+  h->adaptive = adaptive;
   try {
     h->base = make_base_1d(n_base, umin, umax, quadrature);
   } catch (const std::exception& e) {
@@ -1202,20 +1262,66 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
   CK(cudaStreamSynchronize(h->stream));
   float ms_crit = 0.f;
   CK(cudaEventElapsedTime(&ms_crit, h->ea0, h->ea1));
-  Clustering C = cluster_masks(kap.data(), (long)ncell * ninst, nb, p.tau_clust);
-  // one level per distinct (consistent) representative space
-  std::vector<int> lev_of_cluster(C.reps.size()), new_space;
-  std::map<int, int> level_of_space;
-  for (size_t c = 0; c < C.reps.size(); ++c) {
-    int sp;
-    st = get_space(h, std::vector<int>(C.reps[c].begin(), C.reps[c].end()), &sp);
-    if (st != MLVS_OK) return st;
-    auto it = level_of_space.find(sp);
-    if (it == level_of_space.end()) {
-      it = level_of_space.emplace(sp, (int)new_space.size()).first;
-      new_space.push_back(sp);
+  // cell -> new level, and the new level set
+  std::vector<int> cell_level((size_t)ncell * ninst), new_space;
+  int n_distinct = 0;
+  if (h->adaptive) {
+    Clustering C = cluster_masks(kap.data(), (long)ncell * ninst, nb, p.tau_clust);
+    n_distinct = C.n_distinct;
+    // one level per distinct (consistent) representative space
+    std::vector<int> lev_of_cluster(C.reps.size());
+    std::map<int, int> level_of_space;
+    for (size_t c = 0; c < C.reps.size(); ++c) {
+      int sp;
+      st = get_space(h, std::vector<int>(C.reps[c].begin(), C.reps[c].end()), &sp);
+      if (st != MLVS_OK) return st;
+      auto it = level_of_space.find(sp);
+      if (it == level_of_space.end()) {
+        it = level_of_space.emplace(sp, (int)new_space.size()).first;
+        new_space.push_back(sp);
+      }
+      lev_of_cluster[c] = it->second;
     }
-    lev_of_cluster[c] = it->second;
+    for (size_t r = 0; r < cell_level.size(); ++r) cell_level[r] = lev_of_cluster[C.labels[r]];
+  } else {
+    // fixed level set: the coarsest level (fewest velocities) whose space encloses the cell's
+    // requirement (keff <= kappa on every block); the finest level when none does
+    new_space = h->level_space;
+    std::vector<int> by_nv(h->n_levels);
+    for (int l = 0; l < h->n_levels; ++l) by_nv[l] = l;
+    std::stable_sort(by_nv.begin(), by_nv.end(), [&](int a, int b) {
+      return h->spaces[h->level_space[a]].vs.nv() < h->spaces[h->level_space[b]].vs.nv();
+    });
+    const int finest = by_nv.back();
+    for (size_t r = 0; r < cell_level.size(); ++r) {
+      const unsigned char* k = kap.data() + r * nb;
+      int pick = finest;
+      for (int l : by_nv) {
+        const std::vector<int>& ke = h->spaces[h->level_space[l]].keff;
+        bool ok = true;
+        for (int b = 0; b < nb && ok; ++b) ok = ke[b] <= k[b];
+        if (ok) { pick = l; break; }
+      }
+      cell_level[r] = pick;
+    }
+  }
+  // nothing to do when the level set and every cell's level stay
+  bool same = new_space == h->level_space;
+  for (int i = 0; i < ninst && same; ++i)
+    for (int c = 0; c < ncell && same; ++c) same = cell_level[(size_t)i * ncell + c] == h->inst[i].lvl_of[c];
+  if (same) {
+    if (stats) {
+      long long upd = 0;
+      for (auto& I : h->inst)
+        for (int l = 0; l < h->n_levels; ++l) upd += (long long)I.lv[l].cells.size() * I.lv[l].k.nv;
+      stats->n_levels = h->n_levels;
+      stats->n_distinct = n_distinct;
+      stats->n_changed = 0;
+      stats->updates_per_step = upd;
+      stats->ms_criterion = ms_crit;
+      stats->ms_total = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    return MLVS_OK;
   }
   // the current state's moments and parameters (for the shifts), then the new level set
   for (auto& I : h->inst)
@@ -1231,7 +1337,7 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
     Inst& Old = h->inst[i];
     std::vector<int> lv(ncell);
     for (int c = 0; c < ncell; ++c) {
-      lv[c] = lev_of_cluster[C.labels[(size_t)i * ncell + c]];
+      lv[c] = cell_level[(size_t)i * ncell + c];
       if (h->level_space[lv[c]] != old_space[Old.lvl_of[c]]) ++changed;
     }
     Inst New;
@@ -1253,7 +1359,7 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
   (void)old_n;
   if (stats) {
     stats->n_levels = h->n_levels;
-    stats->n_distinct = C.n_distinct;
+    stats->n_distinct = n_distinct;
     stats->n_changed = changed;
     stats->updates_per_step = upd;
     stats->ms_criterion = ms_crit;

@@ -13,7 +13,7 @@ _LIM = {"vanleer": M.LIMITER_VANLEER, "none": M.LIMITER_NONE}
 
 class Solver:
     def __init__(self, desc, levels=(0,), stream=None, storage=None, compat_cell=1, compat_face=1,
-                 n_instances=1, init=None):
+                 n_instances=1, init=None, adaptive=0):
         d = desc
         self.desc = d
         self.ncell = d["nx"] * d["ny"]
@@ -27,7 +27,7 @@ class Solver:
             limiter=_LIM[d["limiter"]], n_instances=n_instances, stream=stream)
         self.h = M.mlvs_create(self.cfg)
         M.mlvs_set_velocity_levels(self.h, d["n_base"], d["umin"], d["umax"], _RULE[d["rule"]],
-                                   list(levels), 0)
+                                   list(levels), adaptive)
         self.dt = M.mlvs_time_step(self.h)
 
     def step(self, n=1, profile=False):
