@@ -6,6 +6,13 @@ Shakhov Pr = 2/3, on the 101 x 101 Boole velocity grid over [-6, 6]^2 (UVS), f s
 FP32 with FP64 moment sums.  One step is one DUGKS step over every (cell, velocity) pair.
 The distributions (2 x 334 MB) are larger than L2, so no flush is needed between steps.
 
+value: UVS cell-velocity updates/s over K timed steps.  Beside it:
+  mlvs            the same cavity with multi-level velocity spaces (criterion, grouping and
+                  remap every 100 steps inside the timed region, Sec. 3.2 / Sec. 4 settings)
+  time_to_steady  UVS and MLVS from rest until the residual falls below 1e-6 (at most
+                  10,000 steps), their device times, and the MLVS fields' relative L2
+                  difference from the UVS fields (the "same error" check)
+
 Arms:
   (default)          the CUDA library through its C ABI
   --impl reference   the FP64 CPU oracle as it stands, on the host cores, on a bounded
@@ -32,7 +39,7 @@ sys.path.insert(0, ROOT)
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
-METRIC = "cell-velocity updates/s (DUGKS step, 2-D cavity 64^2 on 101^2 velocities)"
+METRIC = "cell-velocity updates/s & time-to-steady, MLVS vs UVS on 1 B300, same error"
 UNIT = "updates/s"
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by workload, with
@@ -157,6 +164,46 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# MLVS settings of the cavity runs (Sec. 4): C_split, C_merge, eps_merge, tau_clust, the
+# coarsest candidate block (level 2: the 101^2 / 51^2 / 25^2 quadtree depths), interval.
+MLVS_PARAMS = (5e-3, 2.5e-3, 5e-5, 0.05, 2)
+ADAPT_INTERVAL = 100
+STEADY_TOL = 1e-6        # max over rho, u, v, T of |W^n - W^(n-100)|_2 / |W^n|_2
+STEADY_MAX = 10000       # the paper's cavity runs stop at 10,000 steps
+
+
+def _steady(desc, stream, mlvs):
+    """Steps (100 at a time) until the residual falls below STEADY_TOL; device time."""
+    from paper_2609_35258_b300 import mlvs as M
+    from paper_2609_35258_b300.solver import Solver
+    import numpy as np
+    s = Solver(desc, stream=stream, adaptive=1)
+    if mlvs:
+        M.mlvs_set_adaptation(s.h, M.adapt_params(*MLVS_PARAMS), ADAPT_INTERVAL)
+    F = M.RHO | M.U | M.V | M.T
+    prev = s.moments(F)
+    ms, steps, res, upd = 0.0, 0, 1.0, 0
+    while steps < STEADY_MAX:
+        st = s.step(100)
+        ms += st.ms_total
+        upd += st.cell_velocity_updates
+        steps += 100
+        m = s.moments(F)
+        res = max(float(np.linalg.norm(m[i] - prev[i]) / np.linalg.norm(m[i])) for i in range(4))
+        prev = m
+        if res < STEADY_TOL:
+            break
+    out = s.moments(M.RHO | M.U | M.V | M.T | M.QX | M.QY)
+    s.close()
+    return {"steps": steps, "seconds": ms / 1e3, "residual": res, "converged": res < STEADY_TOL,
+            "updates": upd}, out
+
+
+def _l2(a, b):
+    import numpy as np
+    return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -211,6 +258,50 @@ def run_ours(args, rank, world, local_rank):
     key = f"cavity64_uvs101_{args.storage}:{names[dom]}"
     tr = TRAFFIC.get(key)
     traffic = tr[0] if tr and tr[1] == kernel_source_hash() else None
+    s.close()
+
+    # MLVS on the same cavity: adapt after the warm-up, then K steps with adaptation every
+    # ADAPT_INTERVAL steps inside the timed region
+    mlvs = None
+    if not args.no_mlvs:
+        sm_ = Solver(desc, stream=stream.cuda_stream, adaptive=1)
+        sm_.step(max(args.warmup, 200))
+        ast = M.mlvs_adapt(sm_.h, M.adapt_params(*MLVS_PARAMS))
+        M.mlvs_set_adaptation(sm_.h, M.adapt_params(*MLVS_PARAMS), ADAPT_INTERVAL)
+        sm_.step(args.warmup)
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        mst = sm_.step(args.steps, profile=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        mms = f0.elapsed_time(f1)
+        mupd = mst.cell_velocity_updates
+        mlvs = {"ms_per_step": mms / args.steps, "updates_per_s": mupd / (mms / 1e3),
+                "points_per_cell": mupd / args.steps / ncell, "levels": mst.n_levels,
+                "speedup_per_step_vs_uvs": ms_step / (mms / args.steps),
+                "adapt_ms": ast.ms_total, "criterion_ms": ast.ms_criterion,
+                "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, mst.ms_phase)},
+                "includes": f"adaptation every {ADAPT_INTERVAL} steps"}
+        sm_.close()
+
+    # time to steady state, UVS and MLVS from rest, and the MLVS error against UVS
+    steady = None
+    if not args.no_steady and rank == 0:
+        su, fu = _steady(desc, stream.cuda_stream, False)
+        sv, fv = _steady(desc, stream.cuda_stream, True)
+        err = {"rho": _l2(fv[0], fu[0]),
+               "u": float(np.sqrt(np.sum((fv[1] - fu[1]) ** 2 + (fv[2] - fu[2]) ** 2)) /
+                          np.sqrt(np.sum(fu[1] ** 2 + fu[2] ** 2))),
+               "T": _l2(fv[3], fu[3]),
+               "q": float(np.sqrt(np.sum((fv[4] - fu[4]) ** 2 + (fv[5] - fu[5]) ** 2)) /
+                          np.sqrt(np.sum(fu[4] ** 2 + fu[5] ** 2)))}
+        steady = {"uvs": su, "mlvs": sv, "speedup": su["seconds"] / sv["seconds"],
+                  "mlvs_vs_uvs_rel_l2": err,
+                  "same_error": bool(err["rho"] < 1e-2 and err["u"] < 1e-2 and err["T"] < 1e-2 and err["q"] < 2e-2),
+                  "criterion": f"max over rho,u,v,T of |W^n - W^(n-100)|/|W^n| < {STEADY_TOL:g}, "
+                               f"at most {STEADY_MAX} steps"}
 
     # end-to-end through the public API: host init upload, steps, host moment reads
     e2e = None
@@ -236,14 +327,14 @@ def run_ours(args, rank, world, local_rank):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"16x16-cell cavity on the same 101^2 velocity grid, 4 FP64 oracle steps "
                          f"({upd} updates, {t:.1f} s, numpy single thread)"}
-    s.close()
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
             "config": {"workload": f"cavity64_uvs101_{args.storage}", "cells": ncell,
-                       "velocities": nv, "levels": "UVS 101^2", "Kn": 0.075,
+                       "velocities": nv, "levels": "UVS 101^2 (value); MLVS quadtree 101^2/51^2/25^2",
+                       "Kn": 0.075,
                        "l2": "inputs larger than L2 (2 x 334 MB distributions)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
@@ -251,6 +342,7 @@ def run_ours(args, rank, world, local_rank):
                          "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic,
                          "algorithmic_bytes_per_update": algo_per_update},
             "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, phases)},
+            "mlvs": mlvs, "time_to_steady": steady,
             "clocks": clocks, "e2e": e2e, "gpu_launches": st.launches, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -265,6 +357,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "bf16", "f64"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mlvs", action="store_true")
+    ap.add_argument("--no-steady", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

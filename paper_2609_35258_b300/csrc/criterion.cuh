@@ -20,7 +20,10 @@
 // x y g, y^2 g, x H, y H) when shared memory holds them (tblk), and a candidate block adds
 // its members' sums.  Otherwise the test walks the block's nodes.  The scale S_r of the test
 // uses per-point geometric sums of the cell's space (inherited values are constant on a
-// point's rectangle).
+// point's rectangle).  A level-1 block inside one point of the cell's space takes its sums
+// from that point's g and H times the block's geometric sums.  Thresholds are applied as
+// products (s1 < C T1 for s1/T1 < C, |F - F~| <= eps S_r for the relative error), which is
+// the same test up to rounding.
 #pragma once
 #include "mlvs_common.cuh"
 
@@ -42,6 +45,7 @@ struct CritArgs {
   const unsigned char* kprev;  // [N1*N1] consistent coarsening index of this space
   const double* W1;            // [N1] sum of w over every level-1 group
   const double* X1;            // [N1] sum of w x over every level-1 group
+  const double* XX1;           // [N1] sum of w x^2 over every level-1 group
   const double* geo;           // [5][nv] per point: sum w|x|, sum w|y|, sum w x^2, sum w y^2, sum w|x||y|
   double C_split, C_merge, eps;
   int max_level;
@@ -60,6 +64,7 @@ struct CritCtx {
   const double* TB;            // [CB_N][nb] when a->tblk
   double T1, T2;
   double Sr[4];
+  double epsSr[4];             // eps * S_r
   int slot;
   unsigned char* out;
 };
@@ -126,11 +131,11 @@ __device__ bool crit_transport_ok(const CritCtx& c, int xa, int xb, int ya, int 
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const double Ft = on ? wsum * xd * mb[r] : 0.0;
-        err = fmax(err, fabs(F[d][s][r] - Ft) / c.Sr[r]);
+        if (!(fabs(F[d][s][r] - Ft) <= c.epsSr[r])) return false;
       }
     }
   }
-  return err <= a.eps;
+  return true;
 }
 
 // The same test from the per-block sums of the member blocks.
@@ -166,12 +171,12 @@ __device__ inline bool crit_transport_blocks(const CritCtx& c, int bxa, int bxb,
         if (by <= mid) F[1][1][r] += my[r];
       }
     }
-  const double xbar = sxw / wsum, ybar = syw / wsum;
-  const double gb = sg / wsum, Hb = sH / wsum;
+  const double iw = 1.0 / wsum;
+  const double xbar = sxw * iw, ybar = syw * iw;
+  const double gb = sg * iw, Hb = sH * iw;
   const double xb2 = xbar * xbar + ybar * ybar;
   const double hb = Hb - xb2 * gb;
   const double mb[4] = {gb, xbar * gb, ybar * gb, 0.5 * (hb + xb2 * gb)};
-  double err = 0.0;
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
     const double xd = d ? ybar : xbar;
@@ -181,11 +186,11 @@ __device__ inline bool crit_transport_blocks(const CritCtx& c, int bxa, int bxb,
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
         const double Ft = on ? wsum * xd * mb[r] : 0.0;
-        err = fmax(err, fabs(F[d][s][r] - Ft) / c.Sr[r]);
+        if (!(fabs(F[d][s][r] - Ft) <= c.epsSr[r])) return false;
       }
     }
   }
-  return err <= a.eps;
+  return true;
 }
 
 template <class S>
@@ -199,13 +204,13 @@ __device__ bool crit_decide(const CritCtx& c, int L, int px, int py) {
       s1 += c.S1[by * a.N1 + bx];
       s2 += c.S2[by * a.N1 + bx];
     }
-  const double IB = fmax(s1 / c.T1, s2 / c.T2);
-  if (IB < a.C_merge) {
+  // I_B = max(s1/T1, s2/T2) against the thresholds, as products
+  if (s1 < a.C_merge * c.T1 && s2 < a.C_merge * c.T2) {
     if (!(a.eps > 0.0)) return true;
     if (a.tblk) return crit_transport_blocks(c, bxa, bxb, bya, byb);
     return crit_transport_ok<S>(c, a.g1[bxa], a.g1[bxb], a.g1[bya], a.g1[byb]);
   }
-  if (IB <= a.C_split) {
+  if (s1 <= a.C_split * c.T1 && s2 <= a.C_split * c.T2) {
     for (int by = bya; by < byb; ++by)
       for (int bx = bxa; bx < bxb; ++bx)
         if (a.kprev[by * a.N1 + bx] < L) return false;
@@ -250,6 +255,26 @@ __global__ void __launch_bounds__(CRIT_THREADS) k_criterion(const CritArgs a) {
     double t[CB_N];
 #pragma unroll
     for (int r = 0; r < CB_N; ++r) t[r] = 0.0;
+    const int ixa = a.g1[bx], ixb = a.g1[bx + 1] - 1, iya = a.g1[by], iyb = a.g1[by + 1] - 1;
+    const int k0 = a.owner[iya * a.n + ixa];
+    if (k0 == a.owner[iyb * a.n + ixb]) {
+      // the block lies inside point k0: inherited g and H times the geometric sums
+      double g, H;
+      crit_point<S>(a, slot, iya, ixa, g, H);
+      const double W = a.W1[bx] * a.W1[by];
+      s1 = g * W;
+      s2 = H * W;
+      if (a.tblk) {
+        const double xW = a.X1[bx] * a.W1[by], yW = a.W1[bx] * a.X1[by];
+        t[CB_XG] = g * xW;
+        t[CB_YG] = g * yW;
+        t[CB_XXG] = g * (a.XX1[bx] * a.W1[by]);
+        t[CB_XYG] = g * (a.X1[bx] * a.X1[by]);
+        t[CB_YYG] = g * (a.W1[bx] * a.XX1[by]);
+        t[CB_XH] = H * xW;
+        t[CB_YH] = H * yW;
+      }
+    } else
     for (int iy = a.g1[by]; iy < a.g1[by + 1]; ++iy)
       for (int ix = a.g1[bx]; ix < a.g1[bx + 1]; ++ix) {
         double g, H;
@@ -318,7 +343,10 @@ __global__ void __launch_bounds__(CRIT_THREADS) k_criterion(const CritArgs a) {
   c.T1 = tot[0];
   c.T2 = tot[1];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) c.Sr[r] = fmax(tot[2 + r], tot[6 + r]);
+  for (int r = 0; r < 4; ++r) {
+    c.Sr[r] = fmax(tot[2 + r], tot[6 + r]);
+    c.epsSr[r] = a.eps * c.Sr[r];
+  }
   c.slot = slot;
   c.out = a.kout + (long)a.ids[slot] * nb;
   // hierarchical scan, one thread per top-level candidate block

@@ -162,7 +162,7 @@ struct mlvs_handle {
   // criterion tables of the base grid (2-D)
   int N1 = 0;
   int ng[4] = {0, 0, 0, 0};
-  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, kbuf;
+  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, xx1_d, kbuf;
   mlvs_adapt_params adapt{};
   int adaptive = 0;          // 1: mlvs_adapt groups the masks; 0: fixed level set
   int adapt_interval = 0;
@@ -701,6 +701,7 @@ template <class S, class T, int D> struct Runner {
       a.kprev = sp.kp_d.as<unsigned char>();
       a.W1 = h->w1_d.as<double>();
       a.X1 = h->x1_d.as<double>();
+      a.XX1 = h->xx1_d.as<double>();
       a.geo = sp.geo.as<double>();
       a.tblk = tblk;
       a.C_split = p.C_split;
@@ -1098,14 +1099,16 @@ static mlvs_status build_criterion_tables(mlvs_handle* h, int n) {
   CK(upload(h->g1_d, g1s, h->stream));
   CK(upload(h->pstart_d, ps, h->stream));
   CK(upload(h->cstart_d, cs, h->stream));
-  std::vector<double> W1(N1, 0.0), X1(N1, 0.0);
+  std::vector<double> W1(N1, 0.0), X1(N1, 0.0), XX1(N1, 0.0);
   for (int b = 0; b < N1; ++b)
     for (int i = g1[b].first; i < g1[b].second; ++i) {
       W1[b] += h->base.w[i];
       X1[b] += h->base.w[i] * h->base.x[i];
+      XX1[b] += h->base.w[i] * h->base.x[i] * h->base.x[i];
     }
   CK(upload(h->w1_d, W1, h->stream));
   CK(upload(h->x1_d, X1, h->stream));
+  CK(upload(h->xx1_d, XX1, h->stream));
   return MLVS_OK;
 }
 
