@@ -143,6 +143,8 @@ typedef struct {
   int n_changed;                 /* cells (all instances) whose velocity space changed    */
   long long updates_per_step;    /* sum over levels of cells x velocities, all instances  */
   float ms_criterion;            /* device time of the criterion kernels                  */
+  float ms_group;                /* wall time of the mask download and the grouping       */
+  float ms_remap;                /* wall time of the level rebuild and the remap          */
   float ms_total;                /* wall time of the call                                 */
 } mlvs_adapt_stats;
 
@@ -188,11 +190,12 @@ mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out
 /* field bits for mlvs_moments; fields are written in this bit order */
 enum {
   MLVS_RHO = 1, MLVS_U = 2, MLVS_V = 4, MLVS_T = 8, MLVS_QX = 16, MLVS_QY = 32,
-  MLVS_LEVEL = 64, MLVS_RHOE = 128
+  MLVS_LEVEL = 64, MLVS_RHOE = 128, MLVS_SXX = 256, MLVS_SXY = 512, MLVS_SYY = 1024
 };
 /* Cell moments of one instance at the current time (Eqs. discrete_W, discrete_q):
  * out is [n_fields][ny*nx] doubles (row-major cells), host or device memory (out_on_device).
- * q is the heat flux of phi (q = 2 tau/(2 tau + dt Pr) q~).
+ * q is the heat flux of phi (q = 2 tau/(2 tau + dt Pr) q~); SXX, SXY, SYY the stress
+ * deviator of phi, 2 tau/(2 tau + dt) (P~ - p I) with P~ = sum w c c g~ (c = xi - u).
  * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_CUDA. */
 mlvs_status mlvs_moments(mlvs_handle* h, int instance, unsigned fields, double* out,
                          int out_on_device);

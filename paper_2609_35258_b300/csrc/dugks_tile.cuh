@@ -42,6 +42,7 @@ struct TileArgs {
   const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
   int nY;
   const void* ucell;     // (T) [2][ncell] cell velocities (face moment shifts)
+  unsigned seed;         // per step and level: random bits of the BF16 stochastic rounding
 };
 
 
@@ -575,9 +576,12 @@ k_tile(const TileArgs a, int limiter) {
             gn -= lamy * (Fg[sI + TX] - Fg[sI]);
             hn -= lamy * (Fh[sI + TX] - Fh[sI]);
           }
-          stf<S, T>(fout + (long)v * ns + col0, gn);
-          stf<S, T>(fout + (nv + v) * ns + col0, hn);
-          const T gq = ldf_round<S, T>(gn), hq = ldf_round<S, T>(hn);
+          unsigned rb = 0;
+          if constexpr (sizeof(S) == 2) rb = hash32(a.seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)v));
+          const S sg = Stored<S, T>::enc(gn, rb), sh = Stored<S, T>::enc(hn, rb >> 16);
+          fout[(long)v * ns + col0] = sg;
+          fout[(nv + v) * ns + col0] = sh;
+          const T gq = Stored<S, T>::dec(sg), hq = Stored<S, T>::dec(sh);
           const T wxv = wxb[b], wyv = wyb[b];
           const T xp = xix - m0.ux, yp = (D == 2) ? xiy - m0.uy : T(0);
           const T wg = wxv * (wyv * gq);

@@ -39,7 +39,7 @@ struct PointArgs {
   int is_face;          // 0: cells, 1: faces
   const void* cprm;     // [NP][ncell] current cell params (T): shift source
   void* prm_out;        // [NP][npt] (T)
-  double* W;            // cells: [8][ncell] rho,u,v,T,qx,qy,rhoE,tau (null for faces)
+  double* W;            // cells: [11][ncell] rho,u,v,T,qx,qy,rhoE,tau,sxx,sxy,syy (null for faces)
   const void* vt;       // [4][nv] (T)
   const void* ax;       // [2][nax] (T) when k.nax > 0
   const int* ids;       // cells: global cell id of every point (null: identity)
@@ -467,6 +467,12 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
     a.W[5 * nc + wi] = qy;
     a.W[6 * nc + wi] = rho * (0.5 * (ux * ux + uy * uy) + 0.5 * (3.0 + g.K) * g.R * Tm);
     a.W[7 * nc + wi] = tau;
+    // stress deviator of phi: 2 tau/(2 tau + dt) (P~ - p I), P~ the central second moment of g~
+    const double upx = M[MO_X] / rho, upy = (D == 2) ? M[MO_Y] / rho : 0.0;
+    const double sf = 2.0 * tau / (2.0 * tau + k.dt), pr = rho * g.R * Tm;
+    a.W[8 * nc + wi] = sf * (M[MO_GXX] - rho * upx * upx - pr);
+    a.W[9 * nc + wi] = sf * (M[MO_GXY] - rho * upx * upy);
+    a.W[10 * nc + wi] = (D == 2) ? sf * (M[MO_GYY] - rho * upy * upy - pr) : 0.0;
   }
   if (!ok) atomicOr(a.err, ERR_SINGULAR);
   if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.err, ERR_NONFINITE);
@@ -576,8 +582,10 @@ __global__ void k_init_f(StepConst k, int n, const T* __restrict__ prm, const T*
   for (int v = blockIdx.y; v < k.nv; v += gridDim.y) {
     T g, h;
     model_eval<T, D>(m, vt[v], (D == 2) ? vt[k.nv + v] : T(0), c0, twoK, g, h);
-    stf<S, T>(f + (long)v * nc + c, g);
-    stf<S, T>(f + ((long)k.nv + v) * nc + c, h);
+    unsigned rb = 0;
+    if constexpr (sizeof(S) == 2) rb = hash32(0x5bd1e995u ^ hash32((unsigned)c * 0x9e3779b1u + (unsigned)v));
+    f[(long)v * nc + c] = Stored<S, T>::enc(g, rb);
+    f[((long)k.nv + v) * nc + c] = Stored<S, T>::enc(h, rb >> 16);
   }
 }
 

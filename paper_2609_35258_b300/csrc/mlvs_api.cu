@@ -66,12 +66,12 @@ struct DevBuf {
   template <class X> X* as() const { return reinterpret_cast<X*>(p); }
 };
 
+// Host vector -> new device buffer.  A copy from pageable memory returns once the source
+// has been staged, so v may go out of scope right after the call.
 template <class X> cudaError_t upload(DevBuf& d, const std::vector<X>& v, cudaStream_t s) {
   cudaError_t e = d.alloc(v.size() * sizeof(X));
   if (e != cudaSuccess || v.empty()) return e;
-  e = cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, s);
-  if (e != cudaSuccess) return e;
-  return cudaStreamSynchronize(s);
+  return cudaMemcpyAsync(d.p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, s);
 }
 
 // A velocity space on the base grid.
@@ -163,6 +163,8 @@ struct mlvs_handle {
   int N1 = 0;
   int ng[4] = {0, 0, 0, 0};
   DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, xx1_d, kbuf;
+  unsigned char* kbuf_host = nullptr;   // pinned copy of the masks
+  size_t kbuf_host_n = 0;
   mlvs_adapt_params adapt{};
   int adaptive = 0;          // 1: mlvs_adapt groups the masks; 0: fixed level set
   int adapt_interval = 0;
@@ -187,6 +189,15 @@ static mlvs_status fail(mlvs_handle* h, mlvs_status s, const std::string& msg) {
   } while (0)
 
 namespace {
+
+unsigned hash_host(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
 
 constexpr int kTX2 = 32, kTY2 = 8, kTX1 = 128;
 int tile_w(int D) { return D == 2 ? kTX2 : kTX1; }
@@ -460,6 +471,8 @@ template <class S, class T, int D> struct Runner {
     t.Y = L.Y.p;
     t.nY = L.nY;
     t.ucell = I.ucell.p;
+    t.seed = hash_host((unsigned)h->steps_done * 0x632be5abu + (unsigned)lid * 0x9e3779b9u +
+                       (unsigned)(&I - h->inst.data()) * 0x85ebca77u);
     return t;
   }
 
@@ -1031,6 +1044,7 @@ extern "C" void mlvs_destroy(mlvs_handle* h) {
   if (h->ev1) cudaEventDestroy(h->ev1);
   if (h->ea0) cudaEventDestroy(h->ea0);
   if (h->ea1) cudaEventDestroy(h->ea1);
+  if (h->kbuf_host) cudaFreeHost(h->kbuf_host);
   delete h;
 }
 
@@ -1164,7 +1178,7 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
     Inst& I = h->inst[i];
     mlvs_status st = build_levels(h, std::vector<int>(ncell, 0), I);
     if (st != MLVS_OK) return st;
-    if (I.ucell.alloc(2ull * ncell * h->tsize) != cudaSuccess || I.W.alloc(8ull * ncell * 8) != cudaSuccess ||
+    if (I.ucell.alloc(2ull * ncell * h->tsize) != cudaSuccess || I.W.alloc(11ull * ncell * 8) != cudaSuccess ||
         I.err.alloc(sizeof(int)) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation failed");
     CK(cudaMemsetAsync(I.err.p, 0, sizeof(int), h->stream));
@@ -1260,16 +1274,24 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
   CK(cudaEventRecord(h->ea0, h->stream));
   for (int i = 0; i < ninst; ++i) CK(ops.criterion(h, h->inst[i], p, h->kbuf.as<unsigned char>() + per * i));
   CK(cudaEventRecord(h->ea1, h->stream));
-  std::vector<unsigned char> kap(per * ninst);
-  CK(cudaMemcpyAsync(kap.data(), h->kbuf.p, kap.size(), cudaMemcpyDeviceToHost, h->stream));
+  if (h->kbuf_host_n < per * ninst) {
+    if (h->kbuf_host) cudaFreeHost(h->kbuf_host);
+    h->kbuf_host = nullptr;
+    h->kbuf_host_n = 0;
+    CK(cudaMallocHost(&h->kbuf_host, per * ninst));
+    h->kbuf_host_n = per * ninst;
+  }
+  unsigned char* kap = h->kbuf_host;
+  CK(cudaMemcpyAsync(kap, h->kbuf.p, per * ninst, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  const auto t1 = std::chrono::steady_clock::now();
   float ms_crit = 0.f;
   CK(cudaEventElapsedTime(&ms_crit, h->ea0, h->ea1));
   // cell -> new level, and the new level set
   std::vector<int> cell_level((size_t)ncell * ninst), new_space;
   int n_distinct = 0;
   if (h->adaptive) {
-    Clustering C = cluster_masks(kap.data(), (long)ncell * ninst, nb, p.tau_clust);
+    Clustering C = cluster_masks(kap, (long)ncell * ninst, nb, p.tau_clust);
     n_distinct = C.n_distinct;
     // one level per distinct (consistent) representative space
     std::vector<int> lev_of_cluster(C.reps.size());
@@ -1297,7 +1319,7 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
     });
     const int finest = by_nv.back();
     for (size_t r = 0; r < cell_level.size(); ++r) {
-      const unsigned char* k = kap.data() + r * nb;
+      const unsigned char* k = kap + r * nb;
       int pick = finest;
       for (int l : by_nv) {
         const std::vector<int>& ke = h->spaces[h->level_space[l]].keff;
@@ -1308,6 +1330,10 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
       cell_level[r] = pick;
     }
   }
+  const auto t2 = std::chrono::steady_clock::now();
+  auto ms_between = [](std::chrono::steady_clock::time_point x, std::chrono::steady_clock::time_point y) {
+    return (float)std::chrono::duration<double, std::milli>(y - x).count();
+  };
   // nothing to do when the level set and every cell's level stay
   bool same = new_space == h->level_space;
   for (int i = 0; i < ninst && same; ++i)
@@ -1322,7 +1348,9 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
       stats->n_changed = 0;
       stats->updates_per_step = upd;
       stats->ms_criterion = ms_crit;
-      stats->ms_total = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      stats->ms_group = ms_between(t1, t2);
+      stats->ms_remap = 0.f;
+      stats->ms_total = ms_between(t0, std::chrono::steady_clock::now());
     }
     return MLVS_OK;
   }
@@ -1366,7 +1394,9 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
     stats->n_changed = changed;
     stats->updates_per_step = upd;
     stats->ms_criterion = ms_crit;
-    stats->ms_total = (float)std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    stats->ms_group = ms_between(t1, t2);
+    stats->ms_remap = ms_between(t2, std::chrono::steady_clock::now());
+    stats->ms_total = ms_between(t0, std::chrono::steady_clock::now());
   }
   return check_flags(h);
 }
@@ -1475,13 +1505,13 @@ extern "C" mlvs_status mlvs_moments(mlvs_handle* h, int instance, unsigned field
   mlvs_status s = check_flags(h);
   if (s != MLVS_OK) return s;
   const size_t nc = (size_t)h->nx * h->ny;
-  // field order: RHO U V T QX QY LEVEL RHOE
-  const int src[8] = {0, 1, 2, 3, 4, 5, -1, 6};
+  // field order: RHO U V T QX QY LEVEL RHOE SXX SXY SYY
+  const int src[11] = {0, 1, 2, 3, 4, 5, -1, 6, 8, 9, 10};
   std::vector<double> lev(nc);
   for (size_t c = 0; c < nc; ++c) lev[c] = I.lvl_of[c];
   int j = 0;
   const cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  for (int b = 0; b < 8; ++b) {
+  for (int b = 0; b < 11; ++b) {
     if (!(fields & (1u << b))) continue;
     double* dst = out + j * nc;
     if (src[b] < 0) {

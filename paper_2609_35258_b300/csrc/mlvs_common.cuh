@@ -81,6 +81,35 @@ template <> __device__ __forceinline__ void stf<__nv_bfloat16, float>(__nv_bfloa
   *p = __float2bfloat16_rn(v);
 }
 
+// 32-bit integer hash (the "lowbias32" xorshift-multiply finaliser).
+__device__ __forceinline__ unsigned hash32(unsigned x) {
+  x ^= x >> 16;
+  x *= 0x7feb352du;
+  x ^= x >> 15;
+  x *= 0x846ca68bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// Rounding of an updated value into the storage type.  BF16 rounds stochastically with
+// 16 random bits r: the float's low 16 bits plus r carry into the kept bits with probability
+// (low bits)/2^16, so the stored value is unbiased and the rounding errors of successive
+// steps are independent (round to nearest repeats the same error on a slowly changing
+// state, and that error then accumulates step after step).
+template <class S, class T> struct Stored {
+  static __device__ __forceinline__ S enc(T v, unsigned) { return v; }
+  static __device__ __forceinline__ T dec(S s) { return s; }
+};
+template <> struct Stored<__nv_bfloat16, float> {
+  static __device__ __forceinline__ __nv_bfloat16 enc(float v, unsigned r) {
+    const unsigned u = __float_as_uint(v);
+    __nv_bfloat16_raw raw;
+    raw.x = (unsigned short)((u + (r & 0xffffu)) >> 16);
+    return __nv_bfloat16(raw);
+  }
+  static __device__ __forceinline__ float dec(__nv_bfloat16 s) { return __bfloat162float(s); }
+};
+
 // Value as stored (round trip through the storage type).
 template <class S, class T> __device__ __forceinline__ T ldf_round(T v) { return v; }
 template <> __device__ __forceinline__ float ldf_round<__nv_bfloat16, float>(float v) {

@@ -21,7 +21,7 @@ BC_PERIODIC, BC_ZEROGRAD, BC_WALL = 0, 1, 2
 F64, F32, BF16 = 0, 1, 2
 QUAD_BOOLE, QUAD_SIMPSON, QUAD_TRAPZ = 0, 1, 2
 LIMITER_VANLEER, LIMITER_NONE = 0, 1
-RHO, U, V, T, QX, QY, LEVEL, RHOE = 1, 2, 4, 8, 16, 32, 64, 128
+RHO, U, V, T, QX, QY, LEVEL, RHOE, SXX, SXY, SYY = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024
 
 
 class mlvs_config(C.Structure):
@@ -55,7 +55,7 @@ class mlvs_adapt_params(C.Structure):
 class mlvs_adapt_stats(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("n_distinct", C.c_int), ("n_changed", C.c_int),
                 ("updates_per_step", C.c_longlong), ("ms_criterion", C.c_float),
-                ("ms_total", C.c_float)]
+                ("ms_group", C.c_float), ("ms_remap", C.c_float), ("ms_total", C.c_float)]
 
 
 def _load():
