@@ -44,7 +44,7 @@ UNIT = "updates/s"
 
 # DRAM bytes per launch of the dominant kernel from one ncu capture, keyed by workload, with
 # the hash of the kernel sources at capture time (a changed kernel reports null).
-TRAFFIC = {}
+TRAFFIC = {"cavity64_uvs101_f32:update": (336474624 + 301846016, "447b0793ae7d")}
 
 
 def kernel_source_hash():
@@ -216,8 +216,9 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         import torch.distributed as tdist
     stream = torch.cuda.current_stream()
-    desc = workloads.cavity(64, n_base=101, umax=6.0, Kn=0.075, storage=args.storage)
-    ncell = 64 * 64
+    n = args.cells
+    desc = workloads.cavity(n, n_base=101, umax=6.0, Kn=0.075, storage=args.storage)
+    ncell = n * n
     nv = 101 * 101
     upd_step = ncell * nv
     s = Solver(desc, stream=stream.cuda_stream)
@@ -255,7 +256,8 @@ def run_ours(args, rank, world, local_rank):
     kernel_ms = phases[dom] / args.steps
     peak, peak_kind = measured_peaks()
     achieved = algo_per_update * upd_step / (kernel_ms / 1e3) / 1e9 if algo_per_update else None
-    key = f"cavity64_uvs101_{args.storage}:{names[dom]}"
+    wl = f"cavity{n}_uvs101_{args.storage}"
+    key = f"{wl}:{names[dom]}"
     tr = TRAFFIC.get(key)
     traffic = tr[0] if tr and tr[1] == kernel_source_hash() else None
     s.close()
@@ -332,10 +334,10 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-            "config": {"workload": f"cavity64_uvs101_{args.storage}", "cells": ncell,
+            "config": {"workload": wl, "cells": ncell,
                        "velocities": nv, "levels": "UVS 101^2 (value); MLVS quadtree 101^2/51^2/25^2",
                        "Kn": 0.075,
-                       "l2": "inputs larger than L2 (2 x 334 MB distributions)",
+                       "l2": f"inputs larger than L2 (2 x {2 * ncell * nv * {'f32': 4, 'bf16': 2, 'f64': 8}[args.storage] / 1e6:.0f} MB distributions)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": (achieved / peak) if achieved else None,
@@ -359,6 +361,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mlvs", action="store_true")
     ap.add_argument("--no-steady", action="store_true")
+    ap.add_argument("--cells", type=int, default=64, help="cavity cells per side (default 64)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
