@@ -182,6 +182,29 @@ mlvs_status mlvs_set_adaptation(mlvs_handle* h, const mlvs_adapt_params* p, int 
 mlvs_status mlvs_cluster(const unsigned char* kappa, long nrow, int nb, double tau, int* labels,
                          unsigned char* reps, int reps_cap, int* n_reps);
 
+/* CUDA graphs for mlvs_step: on != 0 replays the launch sequence of two steps (the
+ * ping-pong buffers return to their parity after two) as one graph, captured on first use
+ * and again whenever the levels change; an adaptation or a moments call in between falls
+ * back to regular launches for the step concerned.  Profiled steps never use graphs.
+ * The handle's stream may be any stream, including the legacy default stream. */
+mlvs_status mlvs_set_graph(mlvs_handle* h, int on);
+
+/* Advance several handles (independent cases, e.g. different meshes and Knudsen numbers) by
+ * n_steps together.  use_graph != 0: every two steps are one graph launch on hs[0]'s stream
+ * whose branches are the instances of all handles, so their kernels can run concurrently;
+ * the other handles' streams are ordered before and after it.  stats (may be NULL) sums
+ * over the group; ms_phase is not filled.  A handle may appear only once.
+ * Errors: as mlvs_step, for the first handle that fails. */
+mlvs_status mlvs_step_many(mlvs_handle* const* hs, int n_handles, int n_steps, int use_graph,
+                           mlvs_step_stats* stats);
+
+/* Autotune the velocity chunking: for each candidate number of CTAs per tile launch (148,
+ * 296, 444, 592, 888, 1184, 1776) re-chunk every level, run one warm step and `steps` timed
+ * steps, and keep the fastest (written to *cta_target if non-NULL).  The state advances by
+ * 7 (steps + 1) real steps.
+ * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
+mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target);
+
 /* Extra: the parent-child consistent coarsening index of a level's space.  *nb_out receives
  * its length (N1*N1 in 2-D, N1 in 1-D); out (capacity cap) may be NULL to query it. */
 mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out, int cap,

@@ -42,8 +42,13 @@ struct TileArgs {
   const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
   int nY;
   const void* ucell;     // (T) [2][ncell] cell velocities (face moment shifts)
-  unsigned seed;         // per step and level: random bits of the BF16 stochastic rounding
+  const unsigned* step;  // device step counter (BF16 stochastic rounding: the random bits
+  unsigned salt;         // come from hash(step, salt, cell, velocity); salt: instance, level)
 };
+
+// Advance the device step counter of an instance (one thread; part of every BF16 step, so a
+// captured graph draws new random bits on every replay).
+__global__ void k_step_counter(unsigned* c) { *c += 1u; }
 
 
 template <int TX, int TY, int D> struct TileGeom {
@@ -204,6 +209,8 @@ k_tile(const TileArgs a, int limiter) {
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
+  unsigned seed = 0;
+  if constexpr (MODE == 1 && sizeof(S) == 2) seed = hash32(*a.step * 0x632be5abu + a.salt);
   const int tile = a.tiles[blockIdx.x];
   const int bx = tile % a.ntx, by = tile / a.ntx;
   const int x0 = bx * TX, y0 = by * TY;
@@ -577,7 +584,7 @@ k_tile(const TileArgs a, int limiter) {
             hn -= lamy * (Fh[sI + TX] - Fh[sI]);
           }
           unsigned rb = 0;
-          if constexpr (sizeof(S) == 2) rb = hash32(a.seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)v));
+          if constexpr (sizeof(S) == 2) rb = hash32(seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)v));
           const S sg = Stored<S, T>::enc(gn, rb), sh = Stored<S, T>::enc(hn, rb >> 16);
           fout[(long)v * ns + col0] = sg;
           fout[(nv + v) * ns + col0] = sh;

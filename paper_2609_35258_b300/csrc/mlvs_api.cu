@@ -23,6 +23,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <atomic>
 #include <chrono>
 #include <map>
 #include <memory>
@@ -113,7 +114,7 @@ struct Route {               // mapped items from level src to level dst
 struct Inst {
   std::vector<LevelRt> lv;   // cell levels first (ids 0..n_levels-1), face levels after
   std::vector<int> lvl_of, slot_of;
-  DevBuf lvl_of_d, slot_of_d, ucell, W, err;
+  DevBuf lvl_of_d, slot_of_d, ucell, W, err, stepctr;
   std::vector<Route> ghosts, fluxes;
   std::vector<int> order;    // levels by decreasing velocity count
 };
@@ -173,6 +174,18 @@ struct mlvs_handle {
   int sticky = MLVS_OK;
   std::string err;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr, ea0 = nullptr, ea1 = nullptr;
+  // CUDA graphs and chunking
+  unsigned long long uid = 0;     // unique per handle (graph keys)
+  bool use_graph = false;
+  long long epoch = 0;            // bumped whenever the level structure or chunking changes
+  long long warm_epoch = -1;      // epoch of the last regular step (maps and tables exist)
+  int cta_target = 148 * 4;       // CTAs per tile launch the chunking aims at (autotuned)
+  std::map<std::vector<long long>, std::pair<cudaGraphExec_t, std::vector<int>>> graphs;
+  cudaStream_t cap = nullptr;     // capture stream
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> bev;   // join events, one per branch
+  cudaEvent_t ev_fork = nullptr, ev_post = nullptr;
+  std::vector<cudaEvent_t> ev_pre;
 };
 
 static mlvs_status fail(mlvs_handle* h, mlvs_status s, const std::string& msg) {
@@ -180,6 +193,13 @@ static mlvs_status fail(mlvs_handle* h, mlvs_status s, const std::string& msg) {
   else g_create_error = msg;
   return s;
 }
+
+#define CK_H(hh, call)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (call);                                                             \
+    if (e_ != cudaSuccess)                                                               \
+      return fail(hh, MLVS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
 
 #define CK(call)                                                                         \
   do {                                                                                   \
@@ -471,8 +491,8 @@ template <class S, class T, int D> struct Runner {
     t.Y = L.Y.p;
     t.nY = L.nY;
     t.ucell = I.ucell.p;
-    t.seed = hash_host((unsigned)h->steps_done * 0x632be5abu + (unsigned)lid * 0x9e3779b9u +
-                       (unsigned)(&I - h->inst.data()) * 0x85ebca77u);
+    t.step = I.stepctr.as<unsigned>();
+    t.salt = hash_host((unsigned)lid * 0x9e3779b9u + (unsigned)(&I - h->inst.data()) * 0x85ebca77u);
     return t;
   }
 
@@ -562,6 +582,10 @@ template <class S, class T, int D> struct Runner {
 
   static cudaError_t step(mlvs_handle* h, Inst& I) {
     cudaError_t e;
+    if constexpr (sizeof(S) == 2) {
+      ++h->launches;
+      k_step_counter<<<1, 1, 0, h->stream>>>(I.stepctr.as<unsigned>());
+    }
     for (int l = 0; l < h->n_levels; ++l)
       if (!I.lv[l].fresh && (e = finalize_cells(h, I, I.lv[l])) != cudaSuccess) return e;
     if ((e = run_ghosts(h, I)) != cudaSuccess) return e;
@@ -749,9 +773,8 @@ Ops ops_for(int storage, int D) {
   return D == 2 ? make_ops<__nv_bfloat16, float, 2>() : make_ops<__nv_bfloat16, float, 1>();
 }
 
-int choose_vpc(int tile_ctas, int nv) {
-  // about four CTAs per SM of the 148, at most 384 velocities per chunk
-  const int target = 148 * 4;
+int choose_vpc(int tile_ctas, int nv, int target) {
+  // about `target` CTAs (default four per SM of the 148), at most 384 velocities per chunk
   int nchunk = std::max(1, (target + std::max(tile_ctas, 1) - 1) / std::max(tile_ctas, 1));
   nchunk = std::min(nchunk, nv);
   int vpc = (nv + nchunk - 1) / nchunk;
@@ -770,6 +793,7 @@ static int wrapc(int g, int n, int periodic) {
 
 // Build the level structure of an instance for a cell -> level assignment (host only).
 static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, Inst& I) {
+  ++h->epoch;
   const int D = h->D, nx = h->nx, ny = h->ny, ncell = nx * ny;
   const int px = h->cfg.bc[0] == MLVS_BC_PERIODIC;
   const int py = D == 2 ? (h->cfg.bc[2] == MLVS_BC_PERIODIC) : 1;
@@ -940,7 +964,7 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     k.dx = h->dx; k.dy = h->dy; k.dt = h->dt;
     k.c0 = h->gas.K + 3.0 - D;
     k.twoK = 2.0 * h->gas.K;
-    k.vpc = choose_vpc(L.ntiles, k.nv);
+    k.vpc = choose_vpc(L.ntiles, k.nv, h->cta_target);
     k.nchunk = (k.nv + k.vpc - 1) / k.vpc;
     // device tables
     CK(upload(L.tiles, tl, h->stream));
@@ -1028,6 +1052,8 @@ extern "C" mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out) {
                                                Tref, cfg->L_ref > 0 ? cfg->L_ref : 1.0);
   h->tsize = cfg->storage == MLVS_F64 ? 8 : 4;
   h->ssize = cfg->storage == MLVS_F64 ? 8 : (cfg->storage == MLVS_F32 ? 4 : 2);
+  static std::atomic<unsigned long long> next_uid{1};
+  h->uid = next_uid++;
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     delete h;
     return fail(nullptr, MLVS_ERR_CUDA, "cudaEventCreate failed");
@@ -1045,6 +1071,13 @@ extern "C" void mlvs_destroy(mlvs_handle* h) {
   if (h->ea0) cudaEventDestroy(h->ea0);
   if (h->ea1) cudaEventDestroy(h->ea1);
   if (h->kbuf_host) cudaFreeHost(h->kbuf_host);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.second.first);
+  for (auto s : h->branch) cudaStreamDestroy(s);
+  for (auto e : h->bev) cudaEventDestroy(e);
+  for (auto e : h->ev_pre) cudaEventDestroy(e);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_post) cudaEventDestroy(h->ev_post);
   delete h;
 }
 
@@ -1179,9 +1212,10 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
     mlvs_status st = build_levels(h, std::vector<int>(ncell, 0), I);
     if (st != MLVS_OK) return st;
     if (I.ucell.alloc(2ull * ncell * h->tsize) != cudaSuccess || I.W.alloc(11ull * ncell * 8) != cudaSuccess ||
-        I.err.alloc(sizeof(int)) != cudaSuccess)
+        I.err.alloc(sizeof(int)) != cudaSuccess || I.stepctr.alloc(sizeof(unsigned)) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation failed");
     CK(cudaMemsetAsync(I.err.p, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(I.stepctr.p, 0, sizeof(unsigned), h->stream));
     CK(cudaMemsetAsync(I.W.p, 0, I.W.n, h->stream));
     DevBuf dW0;
     CK(upload(dW0, std::vector<double>(h->initW.begin() + 4ull * ncell * i, h->initW.begin() + 4ull * ncell * (i + 1)),
@@ -1216,6 +1250,7 @@ extern "C" mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const 
   New.ucell = std::move(Old.ucell);
   New.W = std::move(Old.W);
   New.err = std::move(Old.err);
+  New.stepctr = std::move(Old.stepctr);
   CK(ops.transfer(h, Old, New));
   CK(ops.moments_of_levels(h, New));
   CK(cudaStreamSynchronize(h->stream));
@@ -1377,6 +1412,7 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
     New.ucell = std::move(Old.ucell);
     New.W = std::move(Old.W);
     New.err = std::move(Old.err);
+    New.stepctr = std::move(Old.stepctr);
     cudaError_t e = ops.transfer(h, Old, New);
     if (e == cudaSuccess) e = ops.moments_of_levels(h, New);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
@@ -1447,39 +1483,193 @@ extern "C" mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigne
   return MLVS_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// stepping: regular launches, or two-step CUDA graphs over a group of handles
+
+// One regular step of every instance of h on its stream, then the adaptation when due.
+static mlvs_status regular_step(mlvs_handle* h) {
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  for (auto& I : h->inst) CK(ops.step(h, I));
+  ++h->steps_done;
+  h->warm_epoch = h->epoch;
+  if (h->adapt_interval > 0 && h->steps_done % h->adapt_interval == 0) {
+    mlvs_status st = adapt_impl(h, h->adapt, nullptr);
+    if (st != MLVS_OK) return st;
+  }
+  return MLVS_OK;
+}
+
+// A graph can replay the next two steps of h: its tables exist, no cell level holds finished
+// parameters from a moments call, and no adaptation falls inside the two steps.
+static bool graph_ready(const mlvs_handle* h) {
+  if (h->warm_epoch != h->epoch) return false;
+  if (h->adapt_interval > 0 &&
+      ((h->steps_done + 1) % h->adapt_interval == 0 || (h->steps_done + 2) % h->adapt_interval == 0))
+    return false;
+  for (auto& I : h->inst)
+    for (int l = 0; l < h->n_levels; ++l)
+      if (I.lv[l].fresh) return false;
+  return true;
+}
+
+// Key of the two-step graph of a group: handle ids, structure epochs and the ping-pong parity
+// of every level (after two steps every parity is back where it started).
+static std::vector<long long> graph_key(mlvs_handle* const* hs, int nh) {
+  std::vector<long long> key;
+  for (int j = 0; j < nh; ++j) {
+    key.push_back((long long)hs[j]->uid);
+    key.push_back(hs[j]->epoch);
+    for (auto& I : hs[j]->inst)
+      for (int l = 0; l < hs[j]->n_levels; ++l) key.push_back(I.lv[l].cur | (I.lv[l].pcur << 1));
+  }
+  return key;
+}
+
+static cudaError_t ensure_capture_resources(mlvs_handle* h0, int nbranch, int nh) {
+  cudaError_t e;
+  if (!h0->cap && (e = cudaStreamCreateWithFlags(&h0->cap, cudaStreamNonBlocking)) != cudaSuccess) return e;
+  if (!h0->ev_fork && (e = cudaEventCreateWithFlags(&h0->ev_fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+  if (!h0->ev_post && (e = cudaEventCreateWithFlags(&h0->ev_post, cudaEventDisableTiming)) != cudaSuccess) return e;
+  while ((int)h0->branch.size() < nbranch) {
+    cudaStream_t s;
+    cudaEvent_t ev;
+    if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    h0->branch.push_back(s);
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    h0->bev.push_back(ev);
+  }
+  while ((int)h0->ev_pre.size() < nh) {
+    cudaEvent_t ev;
+    if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return e;
+    h0->ev_pre.push_back(ev);
+  }
+  return cudaSuccess;
+}
+
+// Two steps of every handle of the group as one graph launch on hs[0]'s stream.  The graph
+// forks one branch per instance (instances and handles are independent), so their kernels
+// may run concurrently.  Captured on first use for a key, replayed afterwards.
+static mlvs_status graph_two_steps(mlvs_handle* const* hs, int nh) {
+  mlvs_handle* h0 = hs[0];
+  std::vector<long long> key = graph_key(hs, nh);
+  auto it = h0->graphs.find(key);
+  if (it == h0->graphs.end()) {
+    int nbranch = 0;
+    for (int j = 0; j < nh; ++j) nbranch += (int)hs[j]->inst.size();
+    cudaError_t e = ensure_capture_resources(h0, nbranch, nh);
+    if (e != cudaSuccess) return fail(h0, MLVS_ERR_CUDA, std::string("graph resources: ") + cudaGetErrorString(e));
+    std::vector<int> kernels(nh, 0);
+    CK_H(h0, cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t ce = cudaEventRecord(h0->ev_fork, h0->cap);
+    int b = 0;
+    for (int j = 0; j < nh && ce == cudaSuccess; ++j) {
+      mlvs_handle* h = hs[j];
+      Ops ops = ops_for(h->cfg.storage, h->D);
+      cudaStream_t saved = h->stream;
+      const int l0 = h->launches;
+      for (auto& I : h->inst) {
+        cudaStream_t s = h0->branch[b];
+        if ((ce = cudaStreamWaitEvent(s, h0->ev_fork, 0)) != cudaSuccess) break;
+        h->stream = s;
+        if ((ce = ops.step(h, I)) != cudaSuccess) break;
+        if ((ce = ops.step(h, I)) != cudaSuccess) break;
+        if ((ce = cudaEventRecord(h0->bev[b], s)) != cudaSuccess) break;
+        if ((ce = cudaStreamWaitEvent(h0->cap, h0->bev[b], 0)) != cudaSuccess) break;
+        ++b;
+      }
+      h->stream = saved;
+      kernels[j] = h->launches - l0;
+      h->launches = l0;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h0->cap, &graph);
+    if (ce == cudaSuccess) ce = ee;
+    cudaGraphExec_t exec = nullptr;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      // the host state advanced by two steps that never ran: the handles cannot continue
+      for (int j = 0; j < nh; ++j) hs[j]->sticky = MLVS_ERR_CUDA;
+      return fail(h0, MLVS_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+    }
+    it = h0->graphs.emplace(key, std::make_pair(exec, kernels)).first;
+  }
+  // order the other handles' streams before and after the launch
+  for (int j = 1; j < nh; ++j)
+    if (hs[j]->stream != h0->stream) {
+      CK_H(h0, cudaEventRecord(h0->ev_pre[j], hs[j]->stream));
+      CK_H(h0, cudaStreamWaitEvent(h0->stream, h0->ev_pre[j], 0));
+    }
+  CK_H(h0, cudaGraphLaunch(it->second.first, h0->stream));
+  bool other = false;
+  for (int j = 1; j < nh; ++j) other = other || hs[j]->stream != h0->stream;
+  if (other) {
+    CK_H(h0, cudaEventRecord(h0->ev_post, h0->stream));
+    for (int j = 1; j < nh; ++j)
+      if (hs[j]->stream != h0->stream) CK_H(h0, cudaStreamWaitEvent(hs[j]->stream, h0->ev_post, 0));
+  }
+  for (int j = 0; j < nh; ++j) {
+    hs[j]->steps_done += 2;
+    hs[j]->launches += it->second.second[j];
+  }
+  return MLVS_OK;
+}
+
+// n_steps steps of every handle of the group (graphs where allowed).
+static mlvs_status group_steps(mlvs_handle* const* hs, int nh, int n_steps, bool graphs) {
+  int done = 0;
+  while (done < n_steps) {
+    bool g = graphs && n_steps - done >= 2;
+    for (int j = 0; j < nh && g; ++j) g = graph_ready(hs[j]);
+    if (g) {
+      mlvs_status st = graph_two_steps(hs, nh);
+      if (st != MLVS_OK) return st;
+      done += 2;
+      continue;
+    }
+    for (int j = 0; j < nh; ++j) {
+      mlvs_status st = regular_step(hs[j]);
+      if (st != MLVS_OK) return st;
+    }
+    done += 1;
+  }
+  return MLVS_OK;
+}
+
+static void fill_stats(mlvs_handle* const* hs, int nh, int n_steps, float ms, mlvs_step_stats* stats) {
+  stats->ms_total = ms;
+  stats->dt = hs[0]->dt;
+  long long upd = 0;
+  int launches = 0;
+  for (int j = 0; j < nh; ++j) {
+    for (auto& I : hs[j]->inst)
+      for (int l = 0; l < hs[j]->n_levels; ++l) upd += (long long)I.lv[l].cells.size() * I.lv[l].k.nv;
+    launches += hs[j]->launches;
+  }
+  stats->cell_velocity_updates = upd * n_steps;
+  stats->n_levels = hs[0]->n_levels;
+  stats->launches = launches;
+}
+
 extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* stats) {
   if (!h) return MLVS_ERR_ARG;
   if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
   if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
   if (n_steps < 0) return fail(h, MLVS_ERR_ARG, "n_steps < 0");
-  Ops ops = ops_for(h->cfg.storage, h->D);
   h->profiling = stats && stats->profile;
   h->prof.marks.clear();
   h->prof.used = 0;
   h->launches = 0;
   CK(cudaEventRecord(h->ev0, h->stream));
-  for (int n = 0; n < n_steps; ++n) {
-    for (auto& I : h->inst) CK(ops.step(h, I));
-    ++h->steps_done;
-    if (h->adapt_interval > 0 && h->steps_done % h->adapt_interval == 0) {
-      mlvs_status st = adapt_impl(h, h->adapt, nullptr);
-      if (st != MLVS_OK) return st;
-    }
-  }
+  mlvs_status st = group_steps(&h, 1, n_steps, h->use_graph && !h->profiling);
+  if (st != MLVS_OK) { h->profiling = false; return st; }
   CK(cudaEventRecord(h->ev1, h->stream));
   mlvs_status s = check_flags(h);
   if (s != MLVS_OK) return s;
   if (stats) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    stats->ms_total = ms;
-    stats->dt = h->dt;
-    long long upd = 0;
-    for (auto& I : h->inst)
-      for (int l = 0; l < h->n_levels; ++l) upd += (long long)I.lv[l].cells.size() * I.lv[l].k.nv;
-    stats->cell_velocity_updates = upd * n_steps;
-    stats->n_levels = h->n_levels;
-    stats->launches = h->launches;
+    fill_stats(&h, 1, n_steps, ms, stats);
     for (int p = 0; p < 6; ++p) stats->ms_phase[p] = 0.f;
     if (h->profiling) {
       for (auto& m : h->prof.marks) {
@@ -1490,6 +1680,101 @@ extern "C" mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* s
     }
   }
   h->profiling = false;
+  return MLVS_OK;
+}
+
+// Re-chunk the velocities of every level for the handle's CTA target, and recompute the cell
+// partials of the current state with the new chunks (the next finalisation sums them).
+static mlvs_status rechunk(mlvs_handle* h) {
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  for (auto& I : h->inst) {
+    for (int l = 0; l < h->n_levels; ++l)
+      if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
+    for (auto& L : I.lv) {
+      StepConst& k = L.k;
+      k.vpc = choose_vpc(L.ntiles, k.nv, h->cta_target);
+      k.nchunk = (k.nv + k.vpc - 1) / k.vpc;
+      const size_t nc = std::max<size_t>(L.cells.size(), 1);
+      if (L.cpart.alloc((size_t)k.nchunk * NMOM * nc * 8) != cudaSuccess ||
+          L.fpart.alloc((size_t)k.nchunk * NMOM * k.nface * 8) != cudaSuccess)
+        return fail(h, MLVS_ERR_OOM, "device allocation of partial sums failed");
+    }
+    CK(ops.moments_of_levels(h, I));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  ++h->epoch;
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target) {
+  if (!h || steps < 1) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  // CTAs per tile launch: multiples of the 148 SMs (2 CTAs of the tile kernels fit an SM)
+  const int cand[7] = {148, 296, 444, 592, 888, 1184, 1776};
+  int best = h->cta_target;
+  float best_ms = 1e30f;
+  h->profiling = false;
+  for (int c : cand) {
+    h->cta_target = c;
+    mlvs_status st = rechunk(h);
+    if (st == MLVS_OK) st = group_steps(&h, 1, 1, false);   // warm: maps, tables
+    if (st != MLVS_OK) return st;
+    CK(cudaEventRecord(h->ev0, h->stream));
+    if ((st = group_steps(&h, 1, steps, h->use_graph)) != MLVS_OK) return st;
+    CK(cudaEventRecord(h->ev1, h->stream));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  h->cta_target = best;
+  mlvs_status st = rechunk(h);
+  if (st != MLVS_OK) return st;
+  if (cta_target) *cta_target = best;
+  return check_flags(h);
+}
+
+extern "C" mlvs_status mlvs_set_graph(mlvs_handle* h, int on) {
+  if (!h) return MLVS_ERR_ARG;
+  h->use_graph = on != 0;
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_step_many(mlvs_handle* const* hs, int nh, int n_steps, int use_graph,
+                                      mlvs_step_stats* stats) {
+  if (!hs || nh < 1 || n_steps < 0) return fail(nullptr, MLVS_ERR_ARG, "mlvs_step_many: bad argument");
+  for (int j = 0; j < nh; ++j) {
+    if (!hs[j]) return fail(nullptr, MLVS_ERR_ARG, "mlvs_step_many: null handle");
+    for (int q = 0; q < j; ++q)
+      if (hs[q] == hs[j]) return fail(nullptr, MLVS_ERR_ARG, "mlvs_step_many: a handle appears twice");
+    if (!hs[j]->ready) return fail(hs[j], MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+    if (hs[j]->sticky != MLVS_OK) return fail(hs[j], MLVS_ERR_STATE, "handle holds an earlier error");
+    hs[j]->profiling = false;
+    hs[j]->launches = 0;
+  }
+  mlvs_handle* h0 = hs[0];
+  mlvs_handle* h = h0;
+  CK(cudaEventRecord(h0->ev0, h0->stream));
+  mlvs_status st = group_steps(hs, nh, n_steps, use_graph != 0);
+  if (st != MLVS_OK) return st;
+  // the group's work ends on hs[0]'s stream
+  for (int j = 1; j < nh; ++j)
+    if (hs[j]->stream != h0->stream) {
+      CK(cudaEventRecord(hs[j]->ev1, hs[j]->stream));
+      CK(cudaStreamWaitEvent(h0->stream, hs[j]->ev1, 0));
+    }
+  CK(cudaEventRecord(h0->ev1, h0->stream));
+  for (int j = 0; j < nh; ++j) {
+    mlvs_status s = check_flags(hs[j]);
+    if (s != MLVS_OK) return s;
+  }
+  if (stats) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h0->ev0, h0->ev1));
+    fill_stats(hs, nh, n_steps, ms, stats);
+    for (int p = 0; p < 6; ++p) stats->ms_phase[p] = 0.f;
+  }
   return MLVS_OK;
 }
 

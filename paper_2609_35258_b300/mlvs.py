@@ -83,6 +83,9 @@ def _load():
         "mlvs_cluster": (C.c_int, [C.c_void_p, C.c_long, C.c_int, C.c_double, C.POINTER(C.c_int),
                                    C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_level_kappa": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_set_graph": (C.c_int, [H, C.c_int]),
+        "mlvs_step_many": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(mlvs_step_stats)]),
+        "mlvs_autotune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_destroy": (None, [H]),
         "mlvs_last_error": (C.c_char_p, [H]),
     }
@@ -231,6 +234,23 @@ def mlvs_cluster(kappa, tau):
     _check(_lib.mlvs_cluster(k.ctypes.data, nrow, nb, tau, labels.ctypes.data_as(C.POINTER(C.c_int)),
                              reps.ctypes.data, cap, C.byref(n)), None)
     return labels, reps[: n.value].copy()
+
+
+def mlvs_set_graph(h, on=True):
+    _check(_lib.mlvs_set_graph(h, 1 if on else 0), h)
+
+
+def mlvs_step_many(handles, n_steps=1, use_graph=True):
+    arr = (C.c_void_p * len(handles))(*[x.value for x in handles])
+    st = mlvs_step_stats()
+    _check(_lib.mlvs_step_many(arr, len(handles), n_steps, 1 if use_graph else 0, C.byref(st)), None)
+    return st
+
+
+def mlvs_autotune(h, steps=3):
+    t = C.c_int()
+    _check(_lib.mlvs_autotune(h, steps, C.byref(t)), h)
+    return t.value
 
 
 def mlvs_destroy(h):

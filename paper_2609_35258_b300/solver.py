@@ -18,7 +18,11 @@ class Solver:
         self.desc = d
         self.ncell = d["nx"] * d["ny"]
         init = d["init"] if init is None else init
-        W = np.broadcast_to(init, (n_instances,) + init.shape).copy()
+        # init: [ny][nx][4] for every instance, or [n_instances][ny][nx][4]
+        W = (np.ascontiguousarray(init) if init.ndim == 4
+             else np.broadcast_to(init, (n_instances,) + init.shape).copy())
+        if W.shape[0] != n_instances:
+            raise ValueError("init has the wrong number of instances")
         self.cfg = M.make_config(
             dim=d["dim"], nx=d["nx"], ny=d["ny"], Lx=d["Lx"], Ly=d["Ly"],
             bc=[_BC[b] for b in d["bc"]], wall=d["wall"], init_W=W, R=d["R"], K=d["K"], Pr=d["Pr"],
