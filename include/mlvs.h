@@ -205,6 +205,58 @@ mlvs_status mlvs_step_many(mlvs_handle* const* hs, int n_handles, int n_steps, i
  * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
 mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target);
 
+/* ----------------------------------------------------------------------------------------
+ * Level selector.  Not part of the paper: a 10 -> 64 -> 64 -> 4 ReLU network that predicts a
+ * cell's level in a fixed set of four levels from cell features, trained on labels of the
+ * criterion, used by mlvs_adapt_mlp with the criterion as fallback below a confidence
+ * threshold.  Weights: 5,124 FP32 master values (layout W1 [64][10], b1 [64], W2 [64][64],
+ * b2 [64], W3 [4][64], b3 [4]) and their BF16 copy, which the forward and backward passes
+ * read with FP32 accumulation.  Reductions run in a fixed order (results reproducible).
+ * -------------------------------------------------------------------------------------- */
+typedef struct mlvs_mlp mlvs_mlp;
+
+/* Create a network with zero weights; its work is ordered on `stream` (cudaStream_t). */
+mlvs_status mlvs_mlp_create(void* stream, mlvs_mlp** out);
+void mlvs_mlp_destroy(mlvs_mlp* m);
+/* host w[5124]: FP32 master weights (the BF16 copy is their nearest-even rounding); resets
+ * the momentum. */
+mlvs_status mlvs_mlp_set_weights(mlvs_mlp* m, const float* w, int n);
+/* host master[5124] and/or bf16_values[5124] (the BF16 weights as floats); either may be NULL. */
+mlvs_status mlvs_mlp_get_weights(const mlvs_mlp* m, float* master, float* bf16_values, int n);
+/* device X[n][10] -> device logits[n][4] and/or softmax prob[n][4] (either may be NULL);
+ * asynchronous on the network's stream. */
+mlvs_status mlvs_mlp_forward(mlvs_mlp* m, const float* X, int n, float* logits, float* prob);
+/* Gradient of the mean softmax cross-entropy of device X[n][10], labels y[n] (0..3) into
+ * device grad[5124]; *loss (host, may be NULL) receives the loss.  Synchronous.
+ * Errors: MLVS_ERR_ARG (a label outside 0..3), MLVS_ERR_OOM, MLVS_ERR_CUDA. */
+mlvs_status mlvs_mlp_gradient(mlvs_mlp* m, const float* X, const int* y, int n, float* grad, float* loss);
+/* One SGD step with momentum on the same batch: v = momentum v + grad, w -= lr v (FP32
+ * master), BF16 copy refreshed.  *loss (host, may be NULL): the loss before the step. */
+mlvs_status mlvs_mlp_train_step(mlvs_mlp* m, const float* X, const int* y, int n, float lr, float momentum,
+                                float* loss);
+
+/* The ten selector features of every cell of one instance (out [ny*nx][10] floats, host or
+ * device): log rho, u / sqrt(R T_ref), v / sqrt(R T_ref), log(T / T_ref),
+ * q / (rho (RT)^1.5) (two), dx |grad rho| / rho, dx |grad T| / T, dx |grad u| / sqrt(RT),
+ * log10 Kn_local (lambda = (mu/p) sqrt(pi R T / 2) over L_ref); gradients by central
+ * differences with neighbours wrapped on periodic sides and clamped on the others,
+ * dx = min(dx, dy).  Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_CUDA. */
+mlvs_status mlvs_features(mlvs_handle* h, int instance, float* out, int out_on_device);
+
+/* The level the fixed-level-set rule (mlvs_set_velocity_levels, adaptive = 0) gives every cell
+ * of one instance from its criterion mask (host levels[ny*nx]); the cells do not move.
+ * Errors: as mlvs_criterion. */
+mlvs_status mlvs_criterion_levels(mlvs_handle* h, int instance, const mlvs_adapt_params* p, int* levels);
+
+/* Fixed-level-set adaptation (adaptive = 0, four levels) with the selector: every cell whose
+ * largest softmax probability reaches `confidence` takes the predicted level; the others
+ * take the level of the criterion (run on those cells only).  stats->n_distinct receives the
+ * number of cells that fell back to the criterion.
+ * Errors: MLVS_ERR_ARG (not four levels, adaptive = 1, confidence outside [0, 1]), and as
+ * mlvs_adapt. */
+mlvs_status mlvs_adapt_mlp(mlvs_handle* h, mlvs_mlp* m, const mlvs_adapt_params* p, float confidence,
+                           mlvs_adapt_stats* stats);
+
 /* Extra: the parent-child consistent coarsening index of a level's space.  *nb_out receives
  * its length (N1*N1 in 2-D, N1 in 1-D); out (capacity cap) may be NULL to query it. */
 mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out, int cap,

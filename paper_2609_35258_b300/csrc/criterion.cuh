@@ -30,6 +30,7 @@
 namespace mlvs {
 
 struct CritArgs {
+  const int* sel;              // slots to judge, one CTA each (null: slot = CTA index)
   const void* f;               // [2][nv][ns] phi~ of the level (storage type)
   int ns, nv;
   const int* ids;              // [ns] global cell of every slot
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(CRIT_THREADS) k_criterion(const CritArgs a) {
   double* S1 = csm;
   double* S2 = csm + nb;
   __shared__ double red[10][CRIT_THREADS / 32];
-  const int slot = blockIdx.x;
+  const int slot = a.sel ? a.sel[blockIdx.x] : blockIdx.x;
   const int tid = threadIdx.x;
   double* TB = csm + 2 * nb;   // [CB_N][nb] when tblk
   // level-1 block sums of w g and w H (and of the transport moments) on the base grid

@@ -37,6 +37,7 @@
 #include "finalize.cuh"
 #include "mapping.cuh"
 #include "criterion.cuh"
+#include "features.cuh"
 #include "cluster_host.hpp"
 #include "vspace_host.hpp"
 
@@ -163,7 +164,7 @@ struct mlvs_handle {
   // criterion tables of the base grid (2-D)
   int N1 = 0;
   int ng[4] = {0, 0, 0, 0};
-  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, xx1_d, kbuf;
+  DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, xx1_d, kbuf, sel_d, feat_d, prob_d;
   unsigned char* kbuf_host = nullptr;   // pinned copy of the masks
   size_t kbuf_host_n = 0;
   mlvs_adapt_params adapt{};
@@ -709,8 +710,23 @@ template <class S, class T, int D> struct Runner {
   }
 
   // masks of the criterion (Sec. 3.2) of every cell of an instance into kout[ncell][N1*N1]
-  static cudaError_t criterion(mlvs_handle* h, Inst& I, const mlvs_adapt_params& p, unsigned char* kout) {
+  // sel: the global ids of the cells to judge (null: every cell)
+  static cudaError_t criterion(mlvs_handle* h, Inst& I, const mlvs_adapt_params& p, unsigned char* kout,
+                               const std::vector<int>* sel) {
     const int nb = h->N1 * h->N1;
+    // slots of the selected cells, level by level
+    std::vector<int> slots, off(h->n_levels + 1, 0);
+    if (sel) {
+      std::vector<std::vector<int>> per(h->n_levels);
+      for (int c : *sel) per[I.lvl_of[c]].push_back(I.slot_of[c]);
+      for (int l = 0; l < h->n_levels; ++l) {
+        off[l] = (int)slots.size();
+        slots.insert(slots.end(), per[l].begin(), per[l].end());
+      }
+      off[h->n_levels] = (int)slots.size();
+      cudaError_t e = upload(h->sel_d, slots, h->stream);
+      if (e != cudaSuccess) return e;
+    }
     // per-block transport sums in shared memory when they fit
     const int tblk = (p.eps_merge > 0.0 && (2ull + CB_N) * nb * sizeof(double) <= 220ull * 1024) ? 1 : 0;
     const size_t smem = (2ull + (tblk ? CB_N : 0)) * nb * sizeof(double);
@@ -718,9 +734,11 @@ template <class S, class T, int D> struct Runner {
     if (e != cudaSuccess) return e;
     for (int l = 0; l < h->n_levels; ++l) {
       LevelRt& L = I.lv[l];
-      if (L.cells.empty()) continue;
+      const int nsel = sel ? off[l + 1] - off[l] : (int)L.cells.size();
+      if (nsel == 0) continue;
       const SpaceRt& sp = h->spaces[L.space];
       CritArgs a;
+      a.sel = sel ? h->sel_d.as<int>() + off[l] : nullptr;
       a.f = L.f[L.cur].p;
       a.ns = (int)L.cells.size();
       a.nv = L.k.nv;
@@ -747,7 +765,7 @@ template <class S, class T, int D> struct Runner {
       a.max_level = p.max_level;
       a.kout = kout;
       ++h->launches;
-      k_criterion<S><<<a.ns, CRIT_THREADS, smem, h->stream>>>(a);
+      k_criterion<S><<<nsel, CRIT_THREADS, smem, h->stream>>>(a);
     }
     return cudaGetLastError();
   }
@@ -759,7 +777,7 @@ struct Ops {
   cudaError_t (*step)(mlvs_handle*, Inst&);
   cudaError_t (*transfer)(mlvs_handle*, Inst&, Inst&);
   cudaError_t (*moments_of_levels)(mlvs_handle*, Inst&);
-  cudaError_t (*criterion)(mlvs_handle*, Inst&, const mlvs_adapt_params&, unsigned char*);
+  cudaError_t (*criterion)(mlvs_handle*, Inst&, const mlvs_adapt_params&, unsigned char*, const std::vector<int>*);
 };
 
 template <class S, class T, int D> Ops make_ops() {
@@ -1288,15 +1306,22 @@ extern "C" mlvs_status mlvs_criterion(mlvs_handle* h, int instance, const mlvs_a
     dst = h->kbuf.as<unsigned char>();
   }
   Ops ops = ops_for(h->cfg.storage, h->D);
-  CK(ops.criterion(h, h->inst[instance], *p, dst));
+  CK(ops.criterion(h, h->inst[instance], *p, dst, nullptr));
   if (!out_on_device) CK(cudaMemcpyAsync(kappa_out, dst, bytes, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return MLVS_OK;
 }
 
 // Criterion on every cell, grouping, one level per distinct representative space, remap.
-static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_adapt_stats* stats) {
-  const auto t0 = std::chrono::steady_clock::now();
+using Clock = std::chrono::steady_clock;
+static float ms_between(Clock::time_point x, Clock::time_point y) {
+  return (float)std::chrono::duration<double, std::milli>(y - x).count();
+}
+
+// Criterion masks of the selected cells of every instance (sel: per instance the cells, or
+// empty for all), downloaded to the pinned host buffer [instance][cell][N1*N1].
+static mlvs_status compute_masks(mlvs_handle* h, const mlvs_adapt_params& p,
+                                 const std::vector<std::vector<int>>* sel, float* ms_crit) {
   const int ncell = h->nx * h->ny, nb = h->N1 * h->N1, ninst = h->cfg.n_instances;
   const size_t per = (size_t)ncell * nb;
   mlvs_status st = ensure_kbuf(h, per * ninst);
@@ -1307,7 +1332,8 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
   }
   Ops ops = ops_for(h->cfg.storage, h->D);
   CK(cudaEventRecord(h->ea0, h->stream));
-  for (int i = 0; i < ninst; ++i) CK(ops.criterion(h, h->inst[i], p, h->kbuf.as<unsigned char>() + per * i));
+  for (int i = 0; i < ninst; ++i)
+    CK(ops.criterion(h, h->inst[i], p, h->kbuf.as<unsigned char>() + per * i, sel ? &(*sel)[i] : nullptr));
   CK(cudaEventRecord(h->ea1, h->stream));
   if (h->kbuf_host_n < per * ninst) {
     if (h->kbuf_host) cudaFreeHost(h->kbuf_host);
@@ -1316,13 +1342,90 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
     CK(cudaMallocHost(&h->kbuf_host, per * ninst));
     h->kbuf_host_n = per * ninst;
   }
-  unsigned char* kap = h->kbuf_host;
-  CK(cudaMemcpyAsync(kap, h->kbuf.p, per * ninst, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->kbuf_host, h->kbuf.p, per * ninst, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  const auto t1 = std::chrono::steady_clock::now();
+  CK(cudaEventElapsedTime(ms_crit, h->ea0, h->ea1));
+  return MLVS_OK;
+}
+
+// Fixed level set: the coarsest level (fewest velocities) whose space encloses the mask
+// (keff <= kappa on every block); the finest level when none does.
+static int fixed_set_level(const mlvs_handle* h, const unsigned char* k) {
+  const int nb = h->N1 * h->N1;
+  int pick = -1, pick_nv = 0, finest = 0, finest_nv = -1;
+  for (int l = 0; l < h->n_levels; ++l) {
+    const SpaceRt& sp = h->spaces[h->level_space[l]];
+    const int nv = sp.vs.nv();
+    if (nv > finest_nv) { finest = l; finest_nv = nv; }
+    if (pick >= 0 && nv >= pick_nv) continue;
+    bool ok = true;
+    for (int b = 0; b < nb && ok; ++b) ok = sp.keff[b] <= k[b];
+    if (ok) { pick = l; pick_nv = nv; }
+  }
+  return pick >= 0 ? pick : finest;
+}
+
+// Move every cell to cell_level (per instance, per cell) on the level set new_space.
+static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_space, const std::vector<int>& cell_level,
+                                mlvs_adapt_stats* stats) {
+  const int ncell = h->nx * h->ny, ninst = h->cfg.n_instances;
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  bool same = new_space == h->level_space;
+  for (int i = 0; i < ninst && same; ++i)
+    for (int c = 0; c < ncell && same; ++c) same = cell_level[(size_t)i * ncell + c] == h->inst[i].lvl_of[c];
+  int changed = 0;
+  if (!same) {
+    // the current state's moments and parameters (for the shifts), then the new level set
+    for (auto& I : h->inst)
+      for (int l = 0; l < h->n_levels; ++l)
+        if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
+    const std::vector<int> old_space = h->level_space;
+    h->n_levels = (int)new_space.size();
+    h->level_space = new_space;
+    for (int i = 0; i < ninst; ++i) {
+      Inst& Old = h->inst[i];
+      std::vector<int> lv(ncell);
+      for (int c = 0; c < ncell; ++c) {
+        lv[c] = cell_level[(size_t)i * ncell + c];
+        if (h->level_space[lv[c]] != old_space[Old.lvl_of[c]]) ++changed;
+      }
+      Inst New;
+      mlvs_status st = build_levels(h, lv, New);
+      if (st != MLVS_OK) { h->sticky = st; return st; }
+      New.ucell = std::move(Old.ucell);
+      New.W = std::move(Old.W);
+      New.err = std::move(Old.err);
+      New.stepctr = std::move(Old.stepctr);
+      cudaError_t e = ops.transfer(h, Old, New);
+      if (e == cudaSuccess) e = ops.moments_of_levels(h, New);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+      if (e != cudaSuccess) {
+        h->sticky = MLVS_ERR_CUDA;
+        return fail(h, MLVS_ERR_CUDA, std::string("adaptation remap: ") + cudaGetErrorString(e));
+      }
+      h->inst[i] = std::move(New);
+    }
+  }
+  if (stats) {
+    long long upd = 0;
+    for (auto& I : h->inst)
+      for (int l = 0; l < h->n_levels; ++l) upd += (long long)I.lv[l].cells.size() * I.lv[l].k.nv;
+    stats->n_levels = h->n_levels;
+    stats->n_changed = changed;
+    stats->updates_per_step = upd;
+  }
+  return same ? MLVS_OK : check_flags(h);
+}
+
+// Criterion on every cell, then grouping (adaptive = 1) or the fixed-set rule, then remap.
+static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_adapt_stats* stats) {
+  const auto t0 = Clock::now();
+  const int ncell = h->nx * h->ny, nb = h->N1 * h->N1, ninst = h->cfg.n_instances;
   float ms_crit = 0.f;
-  CK(cudaEventElapsedTime(&ms_crit, h->ea0, h->ea1));
-  // cell -> new level, and the new level set
+  mlvs_status st = compute_masks(h, p, nullptr, &ms_crit);
+  if (st != MLVS_OK) return st;
+  const unsigned char* kap = h->kbuf_host;
+  const auto t1 = Clock::now();
   std::vector<int> cell_level((size_t)ncell * ninst), new_space;
   int n_distinct = 0;
   if (h->adaptive) {
@@ -1344,97 +1447,142 @@ static mlvs_status adapt_impl(mlvs_handle* h, const mlvs_adapt_params& p, mlvs_a
     }
     for (size_t r = 0; r < cell_level.size(); ++r) cell_level[r] = lev_of_cluster[C.labels[r]];
   } else {
-    // fixed level set: the coarsest level (fewest velocities) whose space encloses the cell's
-    // requirement (keff <= kappa on every block); the finest level when none does
     new_space = h->level_space;
-    std::vector<int> by_nv(h->n_levels);
-    for (int l = 0; l < h->n_levels; ++l) by_nv[l] = l;
-    std::stable_sort(by_nv.begin(), by_nv.end(), [&](int a, int b) {
-      return h->spaces[h->level_space[a]].vs.nv() < h->spaces[h->level_space[b]].vs.nv();
-    });
-    const int finest = by_nv.back();
-    for (size_t r = 0; r < cell_level.size(); ++r) {
-      const unsigned char* k = kap + r * nb;
-      int pick = finest;
-      for (int l : by_nv) {
-        const std::vector<int>& ke = h->spaces[h->level_space[l]].keff;
-        bool ok = true;
-        for (int b = 0; b < nb && ok; ++b) ok = ke[b] <= k[b];
-        if (ok) { pick = l; break; }
-      }
-      cell_level[r] = pick;
-    }
+    for (size_t r = 0; r < cell_level.size(); ++r) cell_level[r] = fixed_set_level(h, kap + r * nb);
   }
-  const auto t2 = std::chrono::steady_clock::now();
-  auto ms_between = [](std::chrono::steady_clock::time_point x, std::chrono::steady_clock::time_point y) {
-    return (float)std::chrono::duration<double, std::milli>(y - x).count();
-  };
-  // nothing to do when the level set and every cell's level stay
-  bool same = new_space == h->level_space;
-  for (int i = 0; i < ninst && same; ++i)
-    for (int c = 0; c < ncell && same; ++c) same = cell_level[(size_t)i * ncell + c] == h->inst[i].lvl_of[c];
-  if (same) {
-    if (stats) {
-      long long upd = 0;
-      for (auto& I : h->inst)
-        for (int l = 0; l < h->n_levels; ++l) upd += (long long)I.lv[l].cells.size() * I.lv[l].k.nv;
-      stats->n_levels = h->n_levels;
-      stats->n_distinct = n_distinct;
-      stats->n_changed = 0;
-      stats->updates_per_step = upd;
-      stats->ms_criterion = ms_crit;
-      stats->ms_group = ms_between(t1, t2);
-      stats->ms_remap = 0.f;
-      stats->ms_total = ms_between(t0, std::chrono::steady_clock::now());
-    }
-    return MLVS_OK;
-  }
-  // the current state's moments and parameters (for the shifts), then the new level set
-  for (auto& I : h->inst)
-    for (int l = 0; l < h->n_levels; ++l)
-      if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
-  const int old_n = h->n_levels;
-  const std::vector<int> old_space = h->level_space;
-  h->n_levels = (int)new_space.size();
-  h->level_space = new_space;
-  int changed = 0;
-  long long upd = 0;
-  for (int i = 0; i < ninst; ++i) {
-    Inst& Old = h->inst[i];
-    std::vector<int> lv(ncell);
-    for (int c = 0; c < ncell; ++c) {
-      lv[c] = cell_level[(size_t)i * ncell + c];
-      if (h->level_space[lv[c]] != old_space[Old.lvl_of[c]]) ++changed;
-    }
-    Inst New;
-    st = build_levels(h, lv, New);
-    if (st != MLVS_OK) { h->sticky = st; return st; }
-    New.ucell = std::move(Old.ucell);
-    New.W = std::move(Old.W);
-    New.err = std::move(Old.err);
-    New.stepctr = std::move(Old.stepctr);
-    cudaError_t e = ops.transfer(h, Old, New);
-    if (e == cudaSuccess) e = ops.moments_of_levels(h, New);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    if (e != cudaSuccess) {
-      h->sticky = MLVS_ERR_CUDA;
-      return fail(h, MLVS_ERR_CUDA, std::string("adaptation remap: ") + cudaGetErrorString(e));
-    }
-    h->inst[i] = std::move(New);
-    for (int l = 0; l < h->n_levels; ++l) upd += (long long)h->inst[i].lv[l].cells.size() * h->inst[i].lv[l].k.nv;
-  }
-  (void)old_n;
+  const auto t2 = Clock::now();
+  st = apply_levels(h, new_space, cell_level, stats);
+  if (st != MLVS_OK) return st;
   if (stats) {
-    stats->n_levels = h->n_levels;
     stats->n_distinct = n_distinct;
-    stats->n_changed = changed;
-    stats->updates_per_step = upd;
     stats->ms_criterion = ms_crit;
     stats->ms_group = ms_between(t1, t2);
-    stats->ms_remap = ms_between(t2, std::chrono::steady_clock::now());
-    stats->ms_total = ms_between(t0, std::chrono::steady_clock::now());
+    stats->ms_remap = ms_between(t2, Clock::now());
+    stats->ms_total = ms_between(t0, Clock::now());
   }
+  return MLVS_OK;
+}
+
+// Fresh cell moments of an instance (W), as mlvs_moments reads them.
+static mlvs_status fresh_moments(mlvs_handle* h, Inst& I) {
+  Ops ops = ops_for(h->cfg.storage, h->D);
+  for (int l = 0; l < h->n_levels; ++l)
+    if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
   return check_flags(h);
+}
+
+static mlvs_status features_into(mlvs_handle* h, Inst& I, float* dst) {
+  mlvs_status st = fresh_moments(h, I);
+  if (st != MLVS_OK) return st;
+  FeatArgs a;
+  a.W = I.W.as<double>();
+  a.nx = h->nx;
+  a.ny = h->ny;
+  a.px = h->cfg.bc[0] == MLVS_BC_PERIODIC;
+  a.py = h->D == 2 ? (h->cfg.bc[2] == MLVS_BC_PERIODIC) : 1;
+  a.dx = h->dx;
+  a.dy = h->dy;
+  a.R = h->gas.R;
+  a.T_ref = h->gas.T_ref;
+  a.mu_ref = h->gas.mu_ref;
+  a.omega = h->gas.omega;
+  a.L_ref = h->cfg.L_ref > 0 ? h->cfg.L_ref : 1.0;
+  a.out = dst;
+  const int nc = h->nx * h->ny;
+  k_features<<<(nc + 127) / 128, 128, 0, h->stream>>>(a);
+  CK(cudaGetLastError());
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_features(mlvs_handle* h, int instance, float* out, int out_on_device) {
+  if (!h || !out) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  if (instance < 0 || instance >= h->cfg.n_instances) return fail(h, MLVS_ERR_ARG, "instance out of range");
+  const size_t bytes = (size_t)h->nx * h->ny * 10 * sizeof(float);
+  float* dst = out;
+  if (!out_on_device) {
+    if (h->feat_d.n < bytes && h->feat_d.alloc(bytes) != cudaSuccess) return fail(h, MLVS_ERR_OOM, "features");
+    dst = h->feat_d.as<float>();
+  }
+  mlvs_status st = features_into(h, h->inst[instance], dst);
+  if (st != MLVS_OK) return st;
+  if (!out_on_device) CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_criterion_levels(mlvs_handle* h, int instance, const mlvs_adapt_params* p, int* levels) {
+  if (!h || !levels) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  if (instance < 0 || instance >= h->cfg.n_instances) return fail(h, MLVS_ERR_ARG, "instance out of range");
+  mlvs_status st = check_adapt_params(h, p);
+  if (st != MLVS_OK) return st;
+  const int ncell = h->nx * h->ny, nb = h->N1 * h->N1;
+  std::vector<std::vector<int>> sel(h->cfg.n_instances);   // only this instance's cells
+  for (int c = 0; c < ncell; ++c) sel[instance].push_back(c);
+  float ms = 0.f;
+  if ((st = compute_masks(h, *p, &sel, &ms)) != MLVS_OK) return st;
+  const unsigned char* kap = h->kbuf_host + (size_t)instance * ncell * nb;
+  for (int c = 0; c < ncell; ++c) levels[c] = fixed_set_level(h, kap + (size_t)c * nb);
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_adapt_mlp(mlvs_handle* h, mlvs_mlp* m, const mlvs_adapt_params* p, float confidence,
+                                      mlvs_adapt_stats* stats) {
+  if (!h || !m) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
+  if (h->adaptive || h->n_levels != 4) return fail(h, MLVS_ERR_ARG, "the selector needs a fixed set of four levels");
+  if (!(confidence >= 0.f && confidence <= 1.f)) return fail(h, MLVS_ERR_ARG, "confidence outside [0, 1]");
+  mlvs_status st = check_adapt_params(h, p);
+  if (st != MLVS_OK) return st;
+  const auto t0 = Clock::now();
+  const int ncell = h->nx * h->ny, nb = h->N1 * h->N1, ninst = h->cfg.n_instances;
+  const size_t fbytes = (size_t)ncell * 10 * sizeof(float), pbytes = (size_t)ncell * 4 * sizeof(float);
+  if ((h->feat_d.n < fbytes && h->feat_d.alloc(fbytes) != cudaSuccess) ||
+      (h->prob_d.n < pbytes && h->prob_d.alloc(pbytes) != cudaSuccess))
+    return fail(h, MLVS_ERR_OOM, "selector buffers");
+  // predictions, instance by instance
+  std::vector<int> cell_level((size_t)ncell * ninst);
+  std::vector<std::vector<int>> fall(ninst);
+  std::vector<float> prob((size_t)ncell * 4);
+  int nfall = 0;
+  for (int i = 0; i < ninst; ++i) {
+    if ((st = features_into(h, h->inst[i], h->feat_d.as<float>())) != MLVS_OK) return st;
+    CK(cudaStreamSynchronize(h->stream));
+    if ((st = mlvs_mlp_forward(m, h->feat_d.as<float>(), ncell, nullptr, h->prob_d.as<float>())) != MLVS_OK)
+      return fail(h, st, "selector forward pass failed");
+    CK(cudaDeviceSynchronize());   // the network orders its work on its own stream
+    CK(cudaMemcpy(prob.data(), h->prob_d.p, pbytes, cudaMemcpyDeviceToHost));
+    for (int c = 0; c < ncell; ++c) {
+      const float* q = prob.data() + (size_t)c * 4;
+      int k = 0;
+      for (int j = 1; j < 4; ++j)
+        if (q[j] > q[k]) k = j;
+      if (q[k] >= confidence) cell_level[(size_t)i * ncell + c] = k;
+      else { fall[i].push_back(c); ++nfall; }
+    }
+  }
+  const auto t1 = Clock::now();
+  float ms_crit = 0.f;
+  if (nfall > 0) {
+    if ((st = compute_masks(h, *p, &fall, &ms_crit)) != MLVS_OK) return st;
+    for (int i = 0; i < ninst; ++i)
+      for (int c : fall[i])
+        cell_level[(size_t)i * ncell + c] = fixed_set_level(h, h->kbuf_host + ((size_t)i * ncell + c) * nb);
+  }
+  const auto t2 = Clock::now();
+  if ((st = apply_levels(h, h->level_space, cell_level, stats)) != MLVS_OK) return st;
+  if (stats) {
+    stats->n_distinct = nfall;
+    stats->ms_criterion = ms_crit;
+    stats->ms_group = ms_between(t0, t1);
+    stats->ms_remap = ms_between(t2, Clock::now());
+    stats->ms_total = ms_between(t0, Clock::now());
+  }
+  return MLVS_OK;
 }
 
 extern "C" mlvs_status mlvs_adapt(mlvs_handle* h, const mlvs_adapt_params* p, mlvs_adapt_stats* stats) {

@@ -86,6 +86,17 @@ def _load():
         "mlvs_set_graph": (C.c_int, [H, C.c_int]),
         "mlvs_step_many": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(mlvs_step_stats)]),
         "mlvs_autotune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_mlp_create": (C.c_int, [C.c_void_p, C.POINTER(H)]),
+        "mlvs_mlp_destroy": (None, [H]),
+        "mlvs_mlp_set_weights": (C.c_int, [H, C.c_void_p, C.c_int]),
+        "mlvs_mlp_get_weights": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_int]),
+        "mlvs_mlp_forward": (C.c_int, [H, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+        "mlvs_mlp_gradient": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_float)]),
+        "mlvs_mlp_train_step": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_int, C.c_float, C.c_float,
+                                          C.POINTER(C.c_float)]),
+        "mlvs_features": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int]),
+        "mlvs_criterion_levels": (C.c_int, [H, C.c_int, C.POINTER(mlvs_adapt_params), C.c_void_p]),
+        "mlvs_adapt_mlp": (C.c_int, [H, H, C.POINTER(mlvs_adapt_params), C.c_float, C.POINTER(mlvs_adapt_stats)]),
         "mlvs_destroy": (None, [H]),
         "mlvs_last_error": (C.c_char_p, [H]),
     }
@@ -251,6 +262,72 @@ def mlvs_autotune(h, steps=3):
     t = C.c_int()
     _check(_lib.mlvs_autotune(h, steps, C.byref(t)), h)
     return t.value
+
+
+N_SELECTOR_PARAMS = 5124
+
+
+def _dptr(x):
+    return C.c_void_p(x.data_ptr() if hasattr(x, "data_ptr") else x)
+
+
+def mlvs_mlp_create(stream=None):
+    m = C.c_void_p()
+    _check(_lib.mlvs_mlp_create(stream, C.byref(m)), None)
+    return m
+
+
+def mlvs_mlp_destroy(m):
+    _lib.mlvs_mlp_destroy(m)
+
+
+def mlvs_mlp_set_weights(m, w):
+    a = np.ascontiguousarray(w, dtype=np.float32)
+    _check(_lib.mlvs_mlp_set_weights(m, a.ctypes.data, a.size), None)
+
+
+def mlvs_mlp_get_weights(m):
+    """(FP32 master weights, the BF16 weights as floats)"""
+    master = np.zeros(N_SELECTOR_PARAMS, dtype=np.float32)
+    b = np.zeros(N_SELECTOR_PARAMS, dtype=np.float32)
+    _check(_lib.mlvs_mlp_get_weights(m, master.ctypes.data, b.ctypes.data, N_SELECTOR_PARAMS), None)
+    return master, b
+
+
+def mlvs_mlp_forward(m, X, n, logits=None, prob=None):
+    """Device tensors: X [n][10] float32 -> logits / prob [n][4] float32 (asynchronous)."""
+    _check(_lib.mlvs_mlp_forward(m, _dptr(X), n, _dptr(logits) if logits is not None else None,
+                                 _dptr(prob) if prob is not None else None), None)
+
+
+def mlvs_mlp_gradient(m, X, y, n, grad):
+    loss = C.c_float()
+    _check(_lib.mlvs_mlp_gradient(m, _dptr(X), _dptr(y), n, _dptr(grad), C.byref(loss)), None)
+    return loss.value
+
+
+def mlvs_mlp_train_step(m, X, y, n, lr, momentum=0.9):
+    loss = C.c_float()
+    _check(_lib.mlvs_mlp_train_step(m, _dptr(X), _dptr(y), n, lr, momentum, C.byref(loss)), None)
+    return loss.value
+
+
+def mlvs_features(h, instance, ncell):
+    out = np.zeros((ncell, 10), dtype=np.float32)
+    _check(_lib.mlvs_features(h, instance, out.ctypes.data, 0), h)
+    return out
+
+
+def mlvs_criterion_levels(h, instance, params, ncell):
+    out = np.zeros(ncell, dtype=np.int32)
+    _check(_lib.mlvs_criterion_levels(h, instance, C.byref(params), out.ctypes.data), h)
+    return out
+
+
+def mlvs_adapt_mlp(h, m, params, confidence):
+    st = mlvs_adapt_stats()
+    _check(_lib.mlvs_adapt_mlp(h, m, C.byref(params), confidence, C.byref(st)), h)
+    return st
 
 
 def mlvs_destroy(h):

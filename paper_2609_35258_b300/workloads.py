@@ -108,3 +108,25 @@ def batched_cavities(n_inst=64, seed=SEED, sizes=(32, 48, 64, 96, 128)):
     kn = 10.0 ** rng.uniform(-3.0, 1.0, size=n_inst)
     n = rng.choice(np.asarray(sizes), size=n_inst)
     return [cavity(int(n[i]), Kn=float(kn[i])) for i in range(n_inst)]
+
+
+def radial_levels(n_base, radii=((4.75, 99.0, 99.0), (4.0, 5.0, 99.0), (3.25, 4.25, 5.25)), umin=-6.0, umax=6.0):
+    """Four velocity levels for the selector: level 0 fine everywhere, level L = 1..3 fine
+    inside radius r1 of the origin and coarsened to 1, 2, 3 beyond r1, r2, r3 (units of
+    sqrt(R T_ref)).  Returned as coarsening-index arrays over the 2x2 blocks of the base grid
+    ([N1][N1] uint8), the radius of a block taken at its index distance from the centre block
+    times the block width 2 (umax - umin) / (n_base - 1)."""
+    c = (n_base - 1) // 2
+    N1 = 2 * max(c // 2, 1) + 1
+    width = 2.0 * (umax - umin) / (n_base - 1)
+    b = np.arange(N1) - N1 // 2
+    BX, BY = np.meshgrid(b, b)
+    R = np.hypot(BX, BY) * width
+    out = [np.zeros((N1, N1), dtype=np.uint8)]
+    for r1, r2, r3 in radii:
+        k = np.zeros((N1, N1), dtype=np.uint8)
+        k[R > r1] = 1
+        k[R > r2] = 2
+        k[R > r3] = 3
+        out.append(k)
+    return out
