@@ -199,6 +199,78 @@ def _steady(desc, stream, mlvs):
             "updates": upd}, out
 
 
+def _selector_leg():
+    import numpy as np
+    import torch
+    from paper_2609_35258_b300 import mlvs as M
+    from paper_2609_35258_b300 import workloads
+    from paper_2609_35258_b300.solver import Solver
+    nb = 41
+    levels = list(workloads.radial_levels(nb))
+    p = M.adapt_params(5e-3, 2.5e-3, 0.0, 0.05, 3)
+
+    def labelled(d, steps):
+        s = Solver(d, levels=levels, adaptive=0)
+        n = d["nx"] * d["ny"]
+        X, y = [], []
+        for k in steps:
+            if k:
+                s.step(k)
+            X.append(M.mlvs_features(s.h, 0, n))
+            y.append(M.mlvs_criterion_levels(s.h, 0, p, n))
+        s.close()
+        return np.concatenate(X), np.concatenate(y)
+
+    X, y = [], []
+    for amp, Kn, seed in workloads.SELECTOR_TRAIN:
+        a, b = labelled(workloads.periodic_random(24, 24, n_base=nb, amp=amp, Kn=Kn, seed=seed), (0, 4, 4))
+        X.append(a)
+        y.append(b)
+    X, y = np.concatenate(X), np.concatenate(y)
+    m = M.mlvs_mlp_create()
+    M.mlvs_mlp_set_weights(m, workloads.selector_init())
+    Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    first = M.mlvs_mlp_train_step(m, Xd, yd, len(y), 0.02, 0.9)
+    epochs = 1500
+    for _ in range(epochs - 1):
+        last = M.mlvs_mlp_train_step(m, Xd, yd, len(y), 0.02, 0.9)
+    t_train = time.perf_counter() - t0
+    acc = []
+    for amp, Kn, seed in workloads.SELECTOR_HELD:
+        Xh, yh = labelled(workloads.periodic_random(24, 24, n_base=nb, amp=amp, Kn=Kn, seed=seed), (0,))
+        pr = torch.zeros(len(yh), 4, device="cuda")
+        M.mlvs_mlp_forward(m, torch.from_numpy(Xh).cuda(), len(yh), None, pr)
+        torch.cuda.synchronize()
+        acc.append(float(np.mean(np.argmax(pr.cpu().numpy(), 1) == yh)))
+    amp, Kn, seed = workloads.SELECTOR_HELD[0]
+    d = workloads.periodic_random(64, 64, n_base=nb, amp=amp, Kn=Kn, seed=seed)
+    a = Solver(d, levels=levels, adaptive=0)
+    b = Solver(d, levels=levels, adaptive=0)
+    a.step(2)
+    b.step(2)
+    ta, tb = [], []
+    for _ in range(4):
+        ta.append(M.mlvs_adapt(a.h, p).ms_total)
+        sb = M.mlvs_adapt_mlp(b.h, m, p, 0.9)
+        tb.append(sb.ms_total)
+    la, lb = a.moments(M.LEVEL)[0], b.moments(M.LEVEL)[0]
+    a.step(10)
+    b.step(10)
+    ma, mb = a.moments(M.RHO | M.T), b.moments(M.RHO | M.T)
+    a.close()
+    b.close()
+    M.mlvs_mlp_destroy(m)
+    return {"network": "10-64-64-4 ReLU, BF16 weights, FP32 accumulation", "train_samples": int(len(y)),
+            "label_counts": np.bincount(y, minlength=4).tolist(), "epochs": epochs,
+            "train_seconds": t_train, "loss_first": first, "loss_last": last, "heldout_accuracy": acc,
+            "adapt_ms_criterion": float(np.median(ta[1:])), "adapt_ms_selector": float(np.median(tb[1:])),
+            "fallback_cells": int(sb.n_distinct), "cells": 4096, "level_agreement": float(np.mean(la == lb)),
+            "rel_diff_rho_T_after_10_steps": float(np.max(np.abs(ma - mb) / ma)),
+            "workload": "periodic random states, 64^2 cells, base 41^2, four radial levels"}
+
+
 def _l2(a, b):
     import numpy as np
     return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
@@ -305,6 +377,12 @@ def run_ours(args, rank, world, local_rank):
                   "criterion": f"max over rho,u,v,T of |W^n - W^(n-100)|/|W^n| < {STEADY_TOL:g}, "
                                f"at most {STEADY_MAX} steps"}
 
+    # level selector (10-64-64-4, BF16 weights): trained on criterion labels, then used for
+    # a fixed-level-set adaptation against the criterion on a held-out 64^2 state
+    selector = None
+    if not args.no_selector and rank == 0:
+        selector = _selector_leg()
+
     # end-to-end through the public API: host init upload, steps, host moment reads
     e2e = None
     if not args.no_e2e:
@@ -344,7 +422,7 @@ def run_ours(args, rank, world, local_rank):
                          "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic,
                          "algorithmic_bytes_per_update": algo_per_update},
             "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, phases)},
-            "mlvs": mlvs, "time_to_steady": steady,
+            "mlvs": mlvs, "time_to_steady": steady, "selector": selector,
             "clocks": clocks, "e2e": e2e, "gpu_launches": st.launches, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -361,6 +439,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mlvs", action="store_true")
     ap.add_argument("--no-steady", action="store_true")
+    ap.add_argument("--no-selector", action="store_true")
     ap.add_argument("--cells", type=int, default=64, help="cavity cells per side (default 64)")
     args = ap.parse_args()
     if args.warmup < 3:

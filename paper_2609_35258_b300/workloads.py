@@ -130,3 +130,22 @@ def radial_levels(n_base, radii=((4.75, 99.0, 99.0), (4.0, 5.0, 99.0), (3.25, 4.
         k[R > r3] = 3
         out.append(k)
     return out
+
+
+def selector_init(seed=SEED):
+    """He-uniform initial weights of the 10-64-64-4 selector (biases zero), flat [5124]
+    in the layout W1 [64][10], b1 [64], W2 [64][64], b2 [64], W3 [4][64], b3 [4]."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in in ((64, 10), (64, 64), (4, 64)):
+        lim = math.sqrt(6.0 / fan_in)
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts).astype(np.float32)
+
+
+# smooth random states for the selector's training data (density and temperature stay above
+# 0.3 for these amplitudes and seeds), each at two Knudsen numbers; two held-out cases
+SELECTOR_TRAIN = [(amp, Kn, seed) for amp, seed in ((0.2, 1), (0.2, 2), (0.2, 3), (0.35, 2), (0.35, 3),
+                                                    (0.5, 2), (0.5, 3)) for Kn in (0.01, 1.0)]
+SELECTOR_HELD = [(0.35, 1.0, 4), (0.2, 0.01, 4)]

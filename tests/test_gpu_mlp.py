@@ -128,10 +128,7 @@ def test_selector_learns_criterion_levels_and_saves_time():
     nb = 41
     levels = list(workloads.radial_levels(nb))
     p = M.adapt_params(5e-3, 2.5e-3, 0.0, 0.05, 3)
-    # smooth random states (density and temperature stay above 0.3 for these seeds)
-    train = [(amp, Kn, seed) for amp, seed in ((0.2, 1), (0.2, 2), (0.2, 3), (0.35, 2), (0.35, 3),
-                                              (0.5, 2), (0.5, 3)) for Kn in (0.01, 1.0)]
-    held = [(0.35, 1.0, 4), (0.2, 0.01, 4)]
+    train, held = workloads.SELECTOR_TRAIN, workloads.SELECTOR_HELD
     X, y = [], []
     for amp, Kn, seed in train:
         d = workloads.periodic_random(24, 24, n_base=nb, amp=amp, Kn=Kn, seed=seed)
@@ -141,7 +138,7 @@ def test_selector_learns_criterion_levels_and_saves_time():
     X, y = np.concatenate(X), np.concatenate(y)
     assert len(np.unique(y)) >= 3
     m = M.mlvs_mlp_create()
-    M.mlvs_mlp_set_weights(m, omlp.init_weights(20261202).astype(np.float32))
+    M.mlvs_mlp_set_weights(m, workloads.selector_init())
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
     first = M.mlvs_mlp_train_step(m, Xd, yd, len(y), 0.02, 0.9)
     for _ in range(1500):
