@@ -198,12 +198,17 @@ mlvs_status mlvs_set_graph(mlvs_handle* h, int on);
 mlvs_status mlvs_step_many(mlvs_handle* const* hs, int n_handles, int n_steps, int use_graph,
                            mlvs_step_stats* stats);
 
-/* Autotune the velocity chunking: for each candidate number of CTAs per tile launch (148,
- * 296, 444, 592, 888, 1184, 1776) re-chunk every level, run one warm step and `steps` timed
- * steps, and keep the fastest (written to *cta_target if non-NULL).  The state advances by
- * 7 (steps + 1) real steps.
+/* Autotune the velocity chunking of the tile launches: for each candidate number of CTAs per
+ * tile launch (148, 296, 444, 592, 888, 1184, 1776) re-chunk the velocities of every level,
+ * run one warm step and `steps` timed steps, and keep the fastest.  *cta_target and
+ * ms_table[7] (ms per step of every candidate) are written when non-NULL.  The state
+ * advances by 7 (steps + 1) real steps.
  * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
-mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target);
+mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target, float* ms_table);
+
+/* Set the chunking target directly (one of the values mlvs_autotune chooses from, or any
+ * other positive CTA count). */
+mlvs_status mlvs_set_tuning(mlvs_handle* h, int cta_target);
 
 /* ----------------------------------------------------------------------------------------
  * Level selector.  Not part of the paper: a 10 -> 64 -> 64 -> 4 ReLU network that predicts a

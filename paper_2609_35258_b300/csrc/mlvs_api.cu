@@ -1854,17 +1854,17 @@ static mlvs_status rechunk(mlvs_handle* h) {
   return MLVS_OK;
 }
 
-extern "C" mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target) {
+extern "C" mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target, float* ms_table) {
   if (!h || steps < 1) return MLVS_ERR_ARG;
   if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
   if (h->sticky != MLVS_OK) return fail(h, MLVS_ERR_STATE, "handle holds an earlier error");
-  // CTAs per tile launch: multiples of the 148 SMs (2 CTAs of the tile kernels fit an SM)
+  // CTAs per tile launch: multiples of the 148 SMs (two tile CTAs fit an SM)
   const int cand[7] = {148, 296, 444, 592, 888, 1184, 1776};
   int best = h->cta_target;
   float best_ms = 1e30f;
   h->profiling = false;
-  for (int c : cand) {
-    h->cta_target = c;
+  for (int ci = 0; ci < 7; ++ci) {
+    h->cta_target = cand[ci];
     mlvs_status st = rechunk(h);
     if (st == MLVS_OK) st = group_steps(&h, 1, 1, false);   // warm: maps, tables
     if (st != MLVS_OK) return st;
@@ -1874,13 +1874,21 @@ extern "C" mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target)
     CK(cudaEventSynchronize(h->ev1));
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev0, h->ev1));
-    if (ms < best_ms) { best_ms = ms; best = c; }
+    if (ms_table) ms_table[ci] = ms / steps;
+    if (ms < best_ms) { best_ms = ms; best = cand[ci]; }
   }
   h->cta_target = best;
   mlvs_status st = rechunk(h);
   if (st != MLVS_OK) return st;
   if (cta_target) *cta_target = best;
   return check_flags(h);
+}
+
+extern "C" mlvs_status mlvs_set_tuning(mlvs_handle* h, int cta_target) {
+  if (!h || cta_target < 1) return MLVS_ERR_ARG;
+  if (!h->ready) return fail(h, MLVS_ERR_STATE, "mlvs_set_velocity_levels has not been called");
+  h->cta_target = cta_target;
+  return rechunk(h);
 }
 
 extern "C" mlvs_status mlvs_set_graph(mlvs_handle* h, int on) {

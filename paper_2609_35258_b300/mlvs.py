@@ -85,7 +85,8 @@ def _load():
         "mlvs_level_kappa": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_set_graph": (C.c_int, [H, C.c_int]),
         "mlvs_step_many": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(mlvs_step_stats)]),
-        "mlvs_autotune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_autotune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
+        "mlvs_set_tuning": (C.c_int, [H, C.c_int]),
         "mlvs_mlp_create": (C.c_int, [C.c_void_p, C.POINTER(H)]),
         "mlvs_mlp_destroy": (None, [H]),
         "mlvs_mlp_set_weights": (C.c_int, [H, C.c_void_p, C.c_int]),
@@ -259,9 +260,15 @@ def mlvs_step_many(handles, n_steps=1, use_graph=True):
 
 
 def mlvs_autotune(h, steps=3):
+    """(cta_target, ms per step of every candidate [7])"""
     t = C.c_int()
-    _check(_lib.mlvs_autotune(h, steps, C.byref(t)), h)
-    return t.value
+    table = np.zeros(7, dtype=np.float32)
+    _check(_lib.mlvs_autotune(h, steps, C.byref(t), table.ctypes.data), h)
+    return t.value, table
+
+
+def mlvs_set_tuning(h, cta_target):
+    _check(_lib.mlvs_set_tuning(h, cta_target), h)
 
 
 N_SELECTOR_PARAMS = 5124
