@@ -30,6 +30,9 @@ Readings of points the paper leaves open (the same ones the CUDA library uses):
    velocities entering it; rho_w makes the net normal mass flux zero.
  * Zero-gradient sides: the ghost copy acts as an ordinary neighbour and the face is an
    ordinary face.
+ * Freestream sides: the face distribution is the reconstructed phi-bar for velocities
+   leaving the domain and the freestream Maxwellian W_inf (with the four-moment
+   compatibility correction when it is on at faces) for velocities entering it.
 """
 from __future__ import annotations
 
@@ -39,7 +42,7 @@ import numpy as np
 
 from .kinetic import Gas, compat_correct4, moments, shakhov_gh, maxwell_gh, viscosity
 
-PERIODIC, ZEROGRAD, WALL = "periodic", "zerograd", "wall"
+PERIODIC, ZEROGRAD, WALL, FREE = "periodic", "zerograd", "wall", "freestream"
 
 
 @dataclass
@@ -52,6 +55,8 @@ class Mesh:
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC, PERIODIC)
     # wall data (u_w, v_w, T_w) per side
     wall: tuple = ((0.0, 0.0, 1.0),) * 4
+    # freestream state (rho, u, v, T) of the freestream sides
+    far: tuple = (1.0, 0.0, 0.0, 1.0)
 
 
 @dataclass
@@ -177,6 +182,16 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
             val = val + (dyb - xi[:, 1] * s) * sy[k][jj, ii, :]
         return val
 
+    def far_phi(n):
+        """The freestream distribution on n faces (corrected like the face models)."""
+        rho, ux, uy, T = mesh.far
+        vel = np.array([ux, uy]) if D == 2 else np.array([ux])
+        r, u, t = np.full(n, rho), np.repeat(vel[None, :], n, 0), np.full(n, T)
+        gf, hf = maxwell_gh(r, u, t, xi, gas)
+        if opt.compat_face:
+            gf, hf = compat_correct4(gf, hf, r, u, t, xi, w, gas)
+        return gf, hf
+
     def face_phi_x():
         """phi at the x-faces i = 0..nx (non-periodic) or 0..nx-1 (periodic); shape [ny, nfx, Nv]."""
         nfx = nx if mesh.bc[0] == PERIODIC else nx + 1
@@ -196,8 +211,14 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
             bars.append(bar)
         phig, phih = _face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face)
         out = [phig, phih]
-        # walls on the x sides
+        # freestream and walls on the x sides
         for side, idx, inward in ((0, 0, +1.0), (1, nfx - 1, -1.0)):
+            if mesh.bc[side] == FREE:
+                gf, hf = far_phi(ny)
+                in_m = inward * xi[:, 0] > 0.0
+                out[0][:, idx, :] = np.where(in_m, gf, bars[0][:, idx, :])
+                out[1][:, idx, :] = np.where(in_m, hf, bars[1][:, idx, :])
+                continue
             if mesh.bc[side] != WALL:
                 continue
             uw, vw, Tw = mesh.wall[side]
@@ -230,6 +251,12 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
         phig, phih = _face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face)
         out = [phig, phih]
         for side, idx, inward in ((2, 0, +1.0), (3, nfy - 1, -1.0)):
+            if mesh.bc[side] == FREE:
+                gf, hf = far_phi(nx)
+                in_m = inward * xi[:, 1] > 0.0
+                out[0][idx, :, :] = np.where(in_m, gf, bars[0][idx, :, :])
+                out[1][idx, :, :] = np.where(in_m, hf, bars[1][idx, :, :])
+                continue
             if mesh.bc[side] != WALL:
                 continue
             uw, vw, Tw = mesh.wall[side]

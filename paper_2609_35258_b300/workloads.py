@@ -52,6 +52,26 @@ def cavity(n=64, n_base=101, umax=6.0, Kn=0.075, lid_mach=0.16, storage="f32"):
                  n_base=n_base, umin=-umax, umax=umax, storage=storage)
 
 
+def supersonic_channel(nx=48, ny=16, mach=2.0, n_base=41, umax=8.0, Kn=0.05, storage="f32", walls=False):
+    """Channel flow: freestream inflow at x-low (rho, T = 1, u = Ma sqrt(gamma R T), gamma = 5/3),
+    freestream outflow side at x-high, periodic (or diffuse walls at T = 1) in y.  The gas
+    starts as the freestream with a density and temperature bump at the channel centre."""
+    u = mach * math.sqrt(5.0 / 3.0)
+    x = (np.arange(nx) + 0.5) / nx * (nx / ny)
+    y = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(x, y)
+    bump = np.exp(-((X - 0.5 * nx / ny) ** 2 + (Y - 0.5) ** 2) / 0.02)
+    init = np.zeros((ny, nx, 4))
+    init[..., 0] = 1.0 + 0.3 * bump
+    init[..., 1] = u
+    init[..., 3] = 1.0 + 0.2 * bump
+    ybc = ("wall", "wall") if walls else ("periodic", "periodic")
+    d = _desc("supersonic_channel", 2, nx, ny, nx / ny, 1.0, ("freestream", "freestream") + ybc, init,
+              Kn=Kn, n_base=n_base, umin=-umax, umax=umax, storage=storage)
+    d["far"] = (1.0, u, 0.0, 1.0)
+    return d
+
+
 def periodic_random(nx, ny, n_base=25, umax=6.0, seed=SEED, amp=0.2, Kn=0.1, Pr=2.0 / 3.0,
                     storage="f32", dim=2, bc=None):
     """Smooth random periodic fields: a few seeded Fourier modes of rho, u, v, T."""

@@ -13,7 +13,8 @@ def oracle_setup(desc, L=0, compat=True):
     sp = vspace.uniform_space(base, L)
     mu = d["mu_ref"] or kinetic.mu_ref_from_kn(d["Kn"], d["omega"], R=d["R"])
     gas = kinetic.Gas(D=D, K=d["K"], R=d["R"], Pr=d["Pr"], omega=d["omega"], mu_ref=mu)
-    mesh = dugks.Mesh(d["nx"], d["ny"], d["Lx"] / d["nx"], d["Ly"] / d["ny"], bc=d["bc"], wall=d["wall"])
+    mesh = dugks.Mesh(d["nx"], d["ny"], d["Lx"] / d["nx"], d["Ly"] / d["ny"], bc=d["bc"], wall=d["wall"],
+                      far=tuple(d.get("far", (1.0, 0.0, 0.0, 1.0))))
     init = d["init"]
     rho = init[..., 0]
     u = init[..., 1:1 + D]

@@ -251,3 +251,55 @@ def test_sod_oracle_wave_structure():
     assert rho[0] == pytest.approx(1.0, abs=1e-3) and rho[-1] == pytest.approx(0.125, abs=1e-3)
     assert np.all(np.diff(rho) <= 1e-3)           # monotone non-increasing left to right
     assert np.max(st["u"][0, :, 0]) > 0.5         # gas accelerated to the right
+
+
+def _far_setup(bc, far, init, nb=25, umax=7.0, Pr=2.0 / 3.0):
+    base = vspace.make_base(nb, -umax, umax, D=2)
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2, R=1.0, Pr=Pr, mu_ref=kinetic.mu_ref_from_kn(0.1, 0.81))
+    ny, nx = init.shape[:2]
+    mesh = dugks.Mesh(nx, ny, 1.0 / nx, 1.0 / ny, bc=bc, far=far)
+    g, h = dugks.initial_tilde(init[..., 0], init[..., 1:3], init[..., 3], sp.xi, sp.w, gas)
+    dt = dugks.time_step(mesh, sp.xi, 0.5, 2)
+    return sp, gas, mesh, g, h, dt
+
+
+def test_uniform_freestream_is_a_fixed_point():
+    """Freestream on every side at the state of the gas: nothing enters or leaves that differs
+    from the interior, at subsonic and supersonic speeds (BGK: the discrete heat flux of a
+    moving Maxwellian is not exactly zero, so a Shakhov state would drift by itself)."""
+    F = dugks.FREE
+    for u in (0.4, 3.0):
+        far = (1.2, u, -0.3, 0.8)
+        init = np.zeros((6, 8, 4))
+        init[...] = far
+        sp, gas, mesh, g, h, dt = _far_setup((F, F, F, F), far, init, Pr=1.0)
+        g1, h1, _ = dugks.step(g, h, mesh, sp.xi, sp.w, gas, dt)
+        assert np.max(np.abs(g1 - g)) < 1e-14 * np.max(g)
+        assert np.max(np.abs(h1 - h)) < 1e-14 * np.max(h)
+
+
+def test_freestream_sides_mirror_symmetry():
+    """Inflow from the left at +u and the mirrored problem (inflow from the right at -u) give
+    mirrored solutions: the inward normals of the two sides are consistent."""
+    F, P = dugks.FREE, dugks.PERIODIC
+    ny, nx = 4, 10
+    x = (np.arange(nx) + 0.5) / nx
+    init = np.zeros((ny, nx, 4))
+    init[..., 0] = 1.0 + 0.2 * np.exp(-(x - 0.35) ** 2 / 0.01)
+    init[..., 1] = 1.5
+    init[..., 3] = 1.0
+    sp, gas, mesh, g, h, dt = _far_setup((F, F, P, P), (1.0, 1.5, 0.0, 1.0), init)
+    for _ in range(5):
+        g, h, _ = dugks.step(g, h, mesh, sp.xi, sp.w, gas, dt)
+    m = kinetic.moments(g, h, sp.xi, sp.w, gas)
+    init2 = init[:, ::-1].copy()
+    init2[..., 1] = -1.5
+    sp, gas, mesh, g2, h2, dt = _far_setup((F, F, P, P), (1.0, -1.5, 0.0, 1.0), init2)
+    for _ in range(5):
+        g2, h2, _ = dugks.step(g2, h2, mesh, sp.xi, sp.w, gas, dt)
+    m2 = kinetic.moments(g2, h2, sp.xi, sp.w, gas)
+    np.testing.assert_allclose(m2["rho"][:, ::-1], m["rho"], rtol=1e-12)
+    np.testing.assert_allclose(m2["u"][:, ::-1, 0], -m["u"][..., 0], atol=1e-12)
+    np.testing.assert_allclose(m2["T"][:, ::-1], m["T"], rtol=1e-12)
+    assert np.max(np.abs(m["rho"] - init[..., 0])) > 1e-3           # the bump moved
