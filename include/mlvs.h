@@ -42,7 +42,7 @@ typedef enum {
 } mlvs_status;
 
 /* boundary kinds, per side x-low, x-high, y-low, y-high */
-enum { MLVS_BC_PERIODIC = 0, MLVS_BC_ZEROGRAD = 1, MLVS_BC_WALL = 2 };
+enum { MLVS_BC_PERIODIC = 0, MLVS_BC_ZEROGRAD = 1, MLVS_BC_WALL = 2, MLVS_BC_FREESTREAM = 3 };
 /* storage type of the distributions */
 enum { MLVS_F64 = 0, MLVS_F32 = 1, MLVS_BF16 = 2 };
 /* Newton--Cotes rule of the base grid (Sec. 2.3; the order is not named in the paper) */
@@ -72,6 +72,9 @@ typedef struct {
   int limiter;          /* MLVS_LIMITER_*                                                     */
   const double* init_W; /* host [n_instances][ny][nx][4] = (rho, u, v, T); copied              */
   void* stream;         /* cudaStream_t the library orders its work on                        */
+  double far[4];        /* freestream (rho, u, v, T) of MLVS_BC_FREESTREAM sides: velocities
+                           entering take its (corrected) Maxwellian, leaving ones the
+                           reconstruction                                                  */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */

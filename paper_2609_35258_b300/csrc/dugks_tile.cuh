@@ -120,7 +120,7 @@ __device__ __forceinline__ T limited(T a, T b, T inv_h, int limiter) {
   return (ab > T(0)) ? N::mul(N::dv(N::mul(T(2), ab), N::add(a, b)), inv_h) : T(0);
 }
 
-// face metadata word: bit 0 valid, bit 1 owned (MODE 0 accumulates), bits 2-3 kind
+// face metadata word: bit 0 valid, bit 1 owned (MODE 0 accumulates), bits 2-4 kind, role above
 enum { FM_VALID = 1, FM_OWNED = 2 };
 
 // Face accumulators: Kahan pairs (s, c) for M0, MX, MY, E in slots 0..7, plain sums of
@@ -261,6 +261,8 @@ k_tile(const TileArgs a, int limiter) {
         if ((gi < k.nx) ? (li < TX) : !k.px) meta |= FM_OWNED;
         if (!k.px && gi == 0 && k.bc[0] == BC_WALL) meta |= FK_WALL_LO << 2;
         if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) meta |= FK_WALL_HI << 2;
+        if (!k.px && gi == 0 && k.bc[0] == BC_FREE) meta |= FK_FREE_LO << 2;
+        if (!k.px && gi == k.nx && k.bc[1] == BC_FREE) meta |= FK_FREE_HI << 2;
       }
     } else {
       if (gi < k.nx && gj <= k.ny) {
@@ -271,10 +273,12 @@ k_tile(const TileArgs a, int limiter) {
         if ((gj < k.ny) ? (lj < TY) : !k.py) meta |= FM_OWNED;
         if (!k.py && gj == 0 && k.bc[2] == BC_WALL) meta |= FK_WALL_LO << 2;
         if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) meta |= FK_WALL_HI << 2;
+        if (!k.py && gj == 0 && k.bc[2] == BC_FREE) meta |= FK_FREE_LO << 2;
+        if (!k.py && gj == k.ny && k.bc[3] == BC_FREE) meta |= FK_FREE_HI << 2;
       }
     }
     if (role == FR_NONE) meta = 0;
-    meta |= role << 4;
+    meta |= role << 5;
     sMeta[f] = meta;
     sMeta[G::NF + f] = (role == FR_CROSS || role == FR_RECV) ? a.fslot[fid] : fid;
     if (MODE == 1 && (role == FR_NORMAL || role == FR_CROSS)) {
@@ -428,9 +432,9 @@ k_tile(const TileArgs a, int limiter) {
       if (f >= G::NF) break;
       const int meta = sMeta[f];
       if (!(meta & FM_VALID)) continue;
-      const int role = meta >> 4;
+      const int role = meta >> 5;
       if (MODE == 0 && (!(meta & FM_OWNED) || (ML && role == FR_RECV))) continue;
-      const int kind = (meta >> 2) & 3;
+      const int kind = (meta >> 2) & 7;
       int dir, li, lj;
       G::face_pos(f, dir, li, lj);
       if (ML && MODE == 1 && role == FR_RECV) {
@@ -520,7 +524,7 @@ k_tile(const TileArgs a, int limiter) {
             part[6] += wg * yp * yp;
             part[7] += e * xp;
             part[8] += e * yp;
-          } else {
+          } else if (kind == FK_WALL_LO || kind == FK_WALL_HI) {
             // wall: outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) g-bar
             const T xin = (kind == FK_WALL_LO) ? xn : -xn;
             if (xin <= T(0)) part[0] += wxv * (wyv * (xin * gb));
@@ -535,11 +539,14 @@ k_tile(const TileArgs a, int limiter) {
             gf = N::fma(fm.c2, N::sub(gs, gb), gb);
             hf = N::fma(fm.c2, N::sub(hs, hb), hb);
           } else {
-            const T xin = (kind == FK_WALL_LO) ? xn : -xn;
+            // boundary: the model enters (wall: rho_w = c1 + c2 times the unit-density wall
+            // Maxwellian; freestream: c1 = 1, c2 = 0 and the corrected freestream Maxwellian),
+            // the reconstruction leaves
+            const T xin = fk_low(kind) ? xn : -xn;
             if (xin > T(0)) {
               T gs, hs;
               model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
-              gf = N::fma(fm.c1, gs, N::mul(fm.c2, gs));   // rho_w = hi + lo
+              gf = N::fma(fm.c1, gs, N::mul(fm.c2, gs));
               hf = N::fma(fm.c1, hs, N::mul(fm.c2, hs));
             } else {
               gf = gb;
@@ -616,7 +623,7 @@ k_tile(const TileArgs a, int limiter) {
       const int f = tid + q * G::NT;
       if (f >= G::NF) break;
       const int meta = sMeta[f];
-      const int role = meta >> 4;
+      const int role = meta >> 5;
       if (!(meta & FM_VALID) || !(meta & FM_OWNED) || role == FR_RECV) continue;
       const int fid = sMeta[G::NF + f];
       double* P = a.part + (long)chunk * NMOM * k.nface + fid;

@@ -47,6 +47,7 @@ struct PointArgs {
   const void* ucell;    // faces: (T) [2][ncell] cell velocities for the moment shift
   int compat;
   double wall[4][3];    // (u_w, v_w, T_w)
+  double far[4];        // freestream (rho, u, v, T)
   int* err;             // device error bits
   double* scr;          // split finalisation: [FIN_SCR][npt] state and velocity sums
   int* need;            // split finalisation: [npt] what the velocity sums are for
@@ -360,6 +361,8 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
         sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + wrap_or_clamp_h(gi, k.nx, k.px);
         if (!k.px && gi == 0 && k.bc[0] == BC_WALL) { kind = FK_WALL_LO; side = 0; }
         if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) { kind = FK_WALL_HI; side = 1; }
+        if (!k.px && gi == 0 && k.bc[0] == BC_FREE) { kind = FK_FREE_LO; side = 0; }
+        if (!k.px && gi == k.nx && k.bc[1] == BC_FREE) { kind = FK_FREE_HI; side = 1; }
       } else {
         const int r = i - nxf;
         const int gj = r / k.nx, gi = r % k.nx;
@@ -367,6 +370,8 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
         sR = wrap_or_clamp_h(gj, k.ny, k.py) * k.nx + gi;
         if (!k.py && gj == 0 && k.bc[2] == BC_WALL) { kind = FK_WALL_LO; side = 2; }
         if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) { kind = FK_WALL_HI; side = 3; }
+        if (!k.py && gj == 0 && k.bc[2] == BC_FREE) { kind = FK_FREE_LO; side = 2; }
+        if (!k.py && gj == k.ny && k.bc[3] == BC_FREE) { kind = FK_FREE_HI; side = 3; }
       }
       shx = T(0.5) * (uc[sL] + uc[sR]);
       shy = (D == 2) ? T(0.5) * (uc[nc + sL] + uc[nc + sR]) : T(0);
@@ -379,13 +384,24 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   int need = 0;
   double rho = 0, ux = 0, uy = 0, Tm = 0, qx = 0, qy = 0, tau = 0;
   bool state_ok = false;
-  if (kind != FK_INTERIOR) {
+  const bool wall = kind == FK_WALL_LO || kind == FK_WALL_HI;
+  const bool free_ = kind == FK_FREE_LO || kind == FK_FREE_HI;
+  if (wall) {
     const double uw = a.wall[side][0], vw = a.wall[side][1], Tw = a.wall[side][2];
     const double RT = g.R * Tw;
     mp.ux = T(uw); mp.uy = T(vw);
     mp.lnh = T(-0.5 * log(2.0 * 3.14159265358979323846 * RT));
     mp.inv2RT = T(0.5 / RT); mp.RT = T(RT);
     need = 1;
+  } else if (free_) {
+    // freestream side: the model of the freestream state, entering with weight one
+    rho = a.far[0];
+    ux = a.far[1];
+    uy = (D == 2) ? a.far[2] : 0.0;
+    Tm = a.far[3];
+    state_ok = true;
+    point_params<T, D>(g, rho, ux, uy, Tm, 0.0, 0.0, mp);
+    if (a.compat) need = 2;
   } else {
     rho = M[MO_0];
     const double upx = M[MO_X] / rho, upy = (D == 2) ? M[MO_Y] / rho : 0.0;
@@ -412,7 +428,7 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   if (PART == 1) {
     // split path: the uncorrected model and what k_fin_sums / k_fin_post need
     a.need[i] = need == 1 ? 16 + 4 * side + kind : need;
-    a.scr[FS_RHO * (long)a.npt + i] = kind != FK_INTERIOR ? M[MO_0] : rho;
+    a.scr[FS_RHO * (long)a.npt + i] = wall ? M[MO_0] : rho;
     a.scr[FS_UX * (long)a.npt + i] = ux;
     a.scr[FS_UY * (long)a.npt + i] = uy;
     a.scr[FS_T * (long)a.npt + i] = Tm;
@@ -426,7 +442,7 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
       else direct_moments<T, D, 1>(a, mp, 0, G, H);
     }
   }
-  if (kind != FK_INTERIOR) {
+  if (wall) {
     if (PART == 1) {   // rho_w in k_fin_post
       store_mp<T>(po, a.npt, i, mp, T(kind));
       po[P_SHX * (long)a.npt + i] = shx;
@@ -447,7 +463,10 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   bool ok = true;
   if (PART == 0 && need == 2) ok = point_correct<T, D>(g, rho, ux, uy, Tm, G, H, mp);
   const double s = 0.5 * k.dt;
-  if (!a.is_face) {
+  if (free_) {
+    mp.c1 = T(1);
+    mp.c2 = T(0);
+  } else if (!a.is_face) {
     mp.c1 = T(3.0 * s / (2.0 * tau + k.dt));
     mp.c2 = T(4.0 * s / (2.0 * tau + k.dt));
   } else {

@@ -456,6 +456,7 @@ template <class S, class T, int D> struct Runner {
     a.compat = face ? h->cfg.compat_face : h->cfg.compat_cell;
     for (int s = 0; s < 4; ++s)
       for (int j = 0; j < 3; ++j) a.wall[s][j] = h->cfg.wall[s][j];
+    for (int j = 0; j < 4; ++j) a.far[j] = h->cfg.far[j];
     a.err = I.err.as<int>();
     a.W = nullptr;
     a.cprm = nullptr;
@@ -810,6 +811,9 @@ static int wrapc(int g, int n, int periodic) {
 }
 
 // Build the level structure of an instance for a cell -> level assignment (host only).
+// a side whose faces carry a boundary distribution (wall or freestream)
+static bool bnd(int bc) { return bc == MLVS_BC_WALL || bc == MLVS_BC_FREESTREAM; }
+
 static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, Inst& I) {
   ++h->epoch;
   const int D = h->D, nx = h->nx, ny = h->ny, ncell = nx * ny;
@@ -849,14 +853,14 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
       const int gj = f / nfx, gi = f % nfx;
       cL = wrapc(gj, ny, py) * nx + wrapc(gi - 1, nx, px);
       cR = wrapc(gj, ny, py) * nx + wrapc(gi, nx, px);
-      if (!px && gi == 0 && h->cfg.bc[0] == MLVS_BC_WALL) wall = 0;
-      if (!px && gi == nx && h->cfg.bc[1] == MLVS_BC_WALL) wall = 1;
+      if (!px && gi == 0 && bnd(h->cfg.bc[0])) wall = 0;
+      if (!px && gi == nx && bnd(h->cfg.bc[1])) wall = 1;
     } else {
       const int r = f - nfx * ny, gj = r / nx, gi = r % nx;
       cL = wrapc(gj - 1, ny, py) * nx + gi;
       cR = wrapc(gj, ny, py) * nx + gi;
-      if (!py && gj == 0 && h->cfg.bc[2] == MLVS_BC_WALL) wall = 2;
-      if (!py && gj == ny && h->cfg.bc[3] == MLVS_BC_WALL) wall = 3;
+      if (!py && gj == 0 && bnd(h->cfg.bc[2])) wall = 2;
+      if (!py && gj == ny && bnd(h->cfg.bc[3])) wall = 3;
     }
     face_cells[f] = {cL, cR, wall};
     const int lL = lvl_of[cL], lR = lvl_of[cR];
@@ -1033,7 +1037,10 @@ extern "C" mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out) {
     return fail(nullptr, MLVS_ERR_ARG, "bad mesh size (dim 1 needs ny = 1)");
   if (!(cfg->Lx > 0) || (cfg->dim == 2 && !(cfg->Ly > 0))) return fail(nullptr, MLVS_ERR_ARG, "bad domain size");
   for (int s = 0; s < 4; ++s)
-    if (cfg->bc[s] < 0 || cfg->bc[s] > 2) return fail(nullptr, MLVS_ERR_ARG, "unknown boundary kind");
+    if (cfg->bc[s] < 0 || cfg->bc[s] > 3) return fail(nullptr, MLVS_ERR_ARG, "unknown boundary kind");
+  for (int s = 0; s < 4; ++s)
+    if (cfg->bc[s] == MLVS_BC_FREESTREAM && (!(cfg->far[0] > 0) || !(cfg->far[3] > 0)))
+      return fail(nullptr, MLVS_ERR_ARG, "freestream sides need rho > 0 and T > 0 in cfg->far");
   if ((cfg->bc[0] == MLVS_BC_PERIODIC) != (cfg->bc[1] == MLVS_BC_PERIODIC) ||
       (cfg->dim == 2 && (cfg->bc[2] == MLVS_BC_PERIODIC) != (cfg->bc[3] == MLVS_BC_PERIODIC)))
     return fail(nullptr, MLVS_ERR_ARG, "periodic sides must come in pairs");

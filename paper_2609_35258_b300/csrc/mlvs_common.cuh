@@ -32,7 +32,9 @@ enum {
   P_KIND, P_SHX, P_SHY, NP
 };
 // face kinds
-enum { FK_INTERIOR = 0, FK_WALL_LO = 1, FK_WALL_HI = 2 };
+enum { FK_INTERIOR = 0, FK_WALL_LO = 1, FK_WALL_HI = 2, FK_FREE_LO = 3, FK_FREE_HI = 4 };
+// the domain lies on the +normal side of a low-side boundary face
+__host__ __device__ __forceinline__ bool fk_low(int kind) { return kind == FK_WALL_LO || kind == FK_FREE_LO; }
 // moments accumulated per point, in the frame shifted by a reference velocity xi' = xi - u_ref
 //   M0 = sum w g, MX/MY = sum w xi' g, E = sum w (|xi'|^2 g + h), G = sum w xi' xi' g,
 //   J = sum w xi' (|xi'|^2 g + h)
@@ -42,7 +44,7 @@ enum { MO_0 = 0, MO_X, MO_Y, MO_E, MO_GXX, MO_GXY, MO_GYY, MO_JX, MO_JY, NMOM };
 // (V^int, Sec. 3.4) with the flux exported, or received as a mapped flux.
 enum { FR_NONE = 0, FR_NORMAL = 1, FR_CROSS = 2, FR_RECV = 3 };
 // boundary kinds (match mlvs.h)
-enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2 };
+enum { BC_PERIODIC = 0, BC_ZEROGRAD = 1, BC_WALL = 2, BC_FREE = 3 };
 
 template <class T> struct Num;
 template <> struct Num<float> {

@@ -17,7 +17,7 @@ MLVS_OK = 0
 STATUS = {0: "MLVS_OK", -1: "MLVS_ERR_ARG", -2: "MLVS_ERR_OOM", -3: "MLVS_ERR_CUDA",
           -4: "MLVS_ERR_NONFINITE", -5: "MLVS_ERR_POSITIVITY", -6: "MLVS_ERR_SINGULAR",
           -7: "MLVS_ERR_TIMEOUT", -8: "MLVS_ERR_STATE"}
-BC_PERIODIC, BC_ZEROGRAD, BC_WALL = 0, 1, 2
+BC_PERIODIC, BC_ZEROGRAD, BC_WALL, BC_FREESTREAM = 0, 1, 2, 3
 F64, F32, BF16 = 0, 1, 2
 QUAD_BOOLE, QUAD_SIMPSON, QUAD_TRAPZ = 0, 1, 2
 LIMITER_VANLEER, LIMITER_NONE = 0, 1
@@ -33,7 +33,7 @@ class mlvs_config(C.Structure):
         ("L_ref", C.c_double), ("T_ref", C.c_double), ("rho_ref", C.c_double),
         ("cfl", C.c_double), ("dt", C.c_double), ("storage", C.c_int), ("compat_cell", C.c_int),
         ("compat_face", C.c_int), ("limiter", C.c_int), ("init_W", C.POINTER(C.c_double)),
-        ("stream", C.c_void_p),
+        ("stream", C.c_void_p), ("far", C.c_double * 4),
     ]
 
 
@@ -349,7 +349,7 @@ def mlvs_last_error(h=None):
 def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0, K=0.0,
                 Pr=2.0 / 3.0, omega=0.81, Kn=0.0, mu_ref=0.0, cfl=0.5, dt=0.0, storage=F32,
                 compat_cell=1, compat_face=1, limiter=LIMITER_VANLEER, n_instances=1,
-                stream=None, T_ref=1.0, L_ref=1.0, rho_ref=1.0):
+                stream=None, T_ref=1.0, L_ref=1.0, rho_ref=1.0, far=(1.0, 0.0, 0.0, 1.0)):
     """Fill an mlvs_config.  init_W: float64 array [n_instances][ny][nx][4].  The returned
     config keeps a reference to init_W (attribute `_keep`)."""
     cfg = mlvs_config()
@@ -367,4 +367,6 @@ def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0
     cfg._keep = W
     cfg.init_W = W.ctypes.data_as(C.POINTER(C.c_double))
     cfg.stream = stream
+    for j in range(4):
+        cfg.far[j] = far[j]
     return cfg

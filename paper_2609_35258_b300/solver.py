@@ -5,7 +5,8 @@ import numpy as np
 
 from . import mlvs as M
 
-_BC = {"periodic": M.BC_PERIODIC, "zerograd": M.BC_ZEROGRAD, "wall": M.BC_WALL}
+_BC = {"periodic": M.BC_PERIODIC, "zerograd": M.BC_ZEROGRAD, "wall": M.BC_WALL,
+       "freestream": M.BC_FREESTREAM}
 _ST = {"f64": M.F64, "f32": M.F32, "bf16": M.BF16}
 _RULE = {"boole": M.QUAD_BOOLE, "simpson": M.QUAD_SIMPSON, "trapz": M.QUAD_TRAPZ}
 _LIM = {"vanleer": M.LIMITER_VANLEER, "none": M.LIMITER_NONE}
@@ -28,7 +29,8 @@ class Solver:
             bc=[_BC[b] for b in d["bc"]], wall=d["wall"], init_W=W, R=d["R"], K=d["K"], Pr=d["Pr"],
             omega=d["omega"], Kn=d["Kn"] or 0.0, mu_ref=d["mu_ref"] or 0.0, cfl=d["cfl"],
             storage=_ST[storage or d["storage"]], compat_cell=compat_cell, compat_face=compat_face,
-            limiter=_LIM[d["limiter"]], n_instances=n_instances, stream=stream)
+            limiter=_LIM[d["limiter"]], n_instances=n_instances, stream=stream,
+            far=d.get("far", (1.0, 0.0, 0.0, 1.0)))
         self.h = M.mlvs_create(self.cfg)
         M.mlvs_set_velocity_levels(self.h, d["n_base"], d["umin"], d["umax"], _RULE[d["rule"]],
                                    list(levels), adaptive)

@@ -225,3 +225,17 @@ def test_bf16_storage_moments():
     sg = s.moments(M_SXX | M_SXY | M_SYY)
     so = _oracle_stress(o, g, h)
     assert np.max(np.abs(sg - so) / p) < 1e-3
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-5)])
+def test_supersonic_channel_freestream(walls, storage, tol):
+    """Freestream inflow (Ma 2) and outflow sides; the bump is carried towards the outflow."""
+    desc = workloads.supersonic_channel(30, 10, n_base=25, umax=8.0, storage=storage, walls=walls)
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    s.step(12)
+    g, h = oracle_run(o, 12)
+    om = oracle_moments(o, g, h)
+    _compare(s.moments(), om, tol, tol * 3, tol, 100 * tol if storage == "f64" else 1e-3)
+    assert np.max(np.abs(om[0] - desc["init"][..., 0].ravel())) > 1e-3
