@@ -303,3 +303,61 @@ def test_freestream_sides_mirror_symmetry():
     np.testing.assert_allclose(m2["u"][:, ::-1, 0], -m["u"][..., 0], atol=1e-12)
     np.testing.assert_allclose(m2["T"][:, ::-1], m["T"], rtol=1e-12)
     assert np.max(np.abs(m["rho"] - init[..., 0])) > 1e-3           # the bump moved
+
+
+# ------------------------------------------------------------------ curvilinear meshes
+
+def _curvi_vs_cartesian(bc, nx=8, ny=6, Lx=1.0, Ly=0.75, Pr=2.0 / 3.0):
+    from oracle import curvi
+    base = vspace.make_base(17, -5, 5, D=2)
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2, R=1.0, Pr=Pr, mu_ref=kinetic.mu_ref_from_kn(0.1, 0.81))
+    rng = np.random.default_rng(9)
+    rho = 1.0 + 0.1 * rng.random((ny, nx))
+    u = 0.2 * rng.standard_normal((ny, nx, 2))
+    T = 1.0 + 0.1 * rng.random((ny, nx))
+    g, h = dugks.initial_tilde(rho, u, T, sp.xi, sp.w, gas)
+    dx, dy = Lx / nx, Ly / ny
+    cart = dugks.Mesh(nx, ny, dx, dy, bc=bc, wall=((0, 0, 1.0), (0, 0, 1.0), (0.1, 0, 1.0), (0.2, 0, 1.1)),
+                      far=(1.0, 0.3, -0.1, 0.9))
+    Xn, Yn = np.meshgrid(np.arange(nx + 1) * dx, np.arange(ny + 1) * dy)
+    cm = curvi.CurviMesh(Xn, Yn, bc=bc, wall=cart.wall, far=cart.far)
+    dt = dugks.time_step(cart, sp.xi, 0.5, 2)
+    assert abs(curvi.time_step(cm, sp.xi, 0.5) - dt) < 1e-15
+    g1, h1, _ = dugks.step(g, h, cart, sp.xi, sp.w, gas, dt)
+    g2, h2, _ = curvi.step(g, h, cm, sp.xi, sp.w, gas, dt)
+    np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-13 * np.max(g1))
+    np.testing.assert_allclose(h2, h1, rtol=0, atol=1e-13 * np.max(h1))
+
+
+def test_curvilinear_step_on_cartesian_nodes_is_the_cartesian_step():
+    P, W, F, Z = dugks.PERIODIC, dugks.WALL, dugks.FREE, dugks.ZEROGRAD
+    for bc in ((P, P, P, P), (P, P, W, W), (F, F, W, W), (Z, Z, P, P)):
+        _curvi_vs_cartesian(bc)
+
+
+def test_ogrid_geometry_and_free_stream_preservation():
+    """O-grid: positive areas summing to the annulus area, closed cells (the normals of a cell
+    sum to zero with their lengths), and a uniform BGK flow with freestream sides inside and
+    outside stays uniform."""
+    from oracle import curvi
+    X, Y = curvi.ogrid(32, 12, 1.0, 4.0)
+    cm = curvi.CurviMesh(X, Y, bc=(dugks.PERIODIC, dugks.PERIODIC, dugks.FREE, dugks.FREE),
+                         far=(1.0, 0.8, 0.3, 1.0))
+    G = curvi.geometry(cm)
+    assert np.all(G["area"] > 0)
+    # polygon of 32 sides: area of the annulus between the inscribed polygons
+    poly = 0.5 * 32 * np.sin(2 * np.pi / 32)
+    assert abs(G["area"].sum() - poly * (4.0 ** 2 - 1.0)) < 1e-12
+    closure = (G["ni"][:, 1:] * G["li"][:, 1:, None] - G["ni"][:, :-1] * G["li"][:, :-1, None]
+               + G["nj"][1:] * G["lj"][1:, :, None] - G["nj"][:-1] * G["lj"][:-1, :, None])
+    assert np.max(np.abs(closure)) < 1e-13
+    base = vspace.make_base(17, -5, 5, D=2)
+    sp = vspace.uniform_space(base, 0)
+    gas = kinetic.Gas(D=2, R=1.0, Pr=1.0, mu_ref=0.05)
+    n = G["area"].shape
+    g, h = dugks.initial_tilde(np.full(n, 1.0), np.broadcast_to([0.8, 0.3], n + (2,)).copy(), np.full(n, 1.0),
+                               sp.xi, sp.w, gas)
+    dt = curvi.time_step(cm, sp.xi, 0.5)
+    g1, h1, _ = curvi.step(g, h, cm, sp.xi, sp.w, gas, dt)
+    assert np.max(np.abs(g1 - g)) < 1e-13 * np.max(g)
