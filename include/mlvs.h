@@ -75,6 +75,12 @@ typedef struct {
   double far[4];        /* freestream (rho, u, v, T) of MLVS_BC_FREESTREAM sides: velocities
                            entering take its (corrected) Maxwellian, leaving ones the
                            reconstruction                                                  */
+  int mesh_kind;        /* 0: the box Lx x Ly; 1: structured curvilinear mesh from node_xy    */
+  const double* node_xy;/* mesh_kind 1: host [ny+1][nx+1][2] node coordinates, copied. Cell
+                           (i,j) has nodes (i,j),(i+1,j),(i+1,j+1),(i,j+1) counter-clockwise;
+                           on a periodic side the last node column/row repeats the first (an
+                           O-grid) or is its translate.  Slopes along the index directions
+                           become physical through J^{-T}; dt = cfl min |V|/max|S| / max|xi| */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */

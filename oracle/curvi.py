@@ -178,6 +178,8 @@ def step(gt, ht, mesh: CurviMesh, xi, w, gas: Gas, dt: float, opt: Options = Opt
     def faces(nrm, xb, jL, iL, jR, iR, sides):
         """phi at a family of faces with normals nrm [..., 2]; sides: ((index tuple, side,
         inward sign), ...) of its boundary faces."""
+        # xi.n: its sign picks the upwind side (a tangential velocity rounds to a tiny value
+        # of either sign, so the form of the expression is part of the reading)
         xn = nrm[..., 0:1] * xi[:, 0] + nrm[..., 1:2] * xi[:, 1]          # [..., Nv]
         bars = []
         for k in range(2):

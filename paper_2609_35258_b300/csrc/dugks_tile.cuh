@@ -42,6 +42,8 @@ struct TileArgs {
   const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
   int nY;
   const void* ucell;     // (T) [2][ncell] cell velocities (face moment shifts)
+  const void* cgeo;      // curvilinear (T) [5][ncell]: J^{-T} (4, row-major), dt/|V|
+  const void* fgeo;      // curvilinear (T) [7][nface]: normal (2), |S|, x_b - x_L (2), x_b - x_R (2)
   const unsigned* step;  // device step counter (BF16 stochastic rounding: the random bits
   unsigned salt;         // come from hash(step, salt, cell, velocity); salt: instance, level)
 };
@@ -94,7 +96,7 @@ template <int TX, int TY, int D> struct TileGeom {
 };
 
 // Shared-memory layout of a tile kernel (bytes), identical on host and device.
-template <class T, int TX, int TY, int D, int VB, int MODE> struct TileSmem {
+template <class T, int TX, int TY, int D, int VB, int MODE, bool CV = false> struct TileSmem {
   using G = TileGeom<TX, TY, D>;
   static constexpr size_t P = 0;                                           // T [VB][2][NEXT]
   static constexpr size_t SL = P + sizeof(T) * VB * 2 * G::NEXT;            // T [VB][4][NSL]
@@ -102,7 +104,9 @@ template <class T, int TX, int TY, int D, int VB, int MODE> struct TileSmem {
   static constexpr size_t FP = F + (MODE == 1 ? sizeof(T) * VB * 2 * G::NF : 0);  // T [16][NF] (MODE 1)
   static constexpr size_t ACC = FP + (MODE == 1 ? sizeof(T) * 16 * G::NF : 0);     // T [16][NF] (MODE 0)
   static constexpr size_t META = ACC + (MODE == 0 ? sizeof(T) * 16 * G::NF : 0);   // int [2][NF]
-  static constexpr size_t BYTES = META + sizeof(int) * 2 * G::NF;
+  static constexpr size_t JT = META + sizeof(int) * 2 * G::NF;                      // T [4][NSL] (CV)
+  static constexpr size_t FG = JT + (CV ? sizeof(T) * 4 * G::NSL : 0);               // T [7][NF]  (CV)
+  static constexpr size_t BYTES = FG + (CV ? sizeof(T) * 7 * G::NF : 0);
 };
 
 __device__ __forceinline__ int wrap_or_clamp(int g, int n, int periodic) {
@@ -179,11 +183,16 @@ __device__ __forceinline__ void write_partials_smem(const T* acc, int sa, double
 // ML = false: the level holds every cell of the mesh (one velocity space), so every stencil
 // position is an own cell in natural order and every face is a normal face; the level
 // tables are not read.
-template <class S, class T, int D, int TX, int TY, int VB, int MODE, bool ML>
+// CV: structured curvilinear mesh (2-D): slopes along the index directions turned into
+// physical slopes with the cell's J^{-T}, faces with their own normals, areas and centroid
+// offsets (precomputed per face, so the two tiles of a face read the same values), and the
+// update scaled by dt/|V|.
+template <class S, class T, int D, int TX, int TY, int VB, int MODE, bool ML, bool CV>
 __global__ void __launch_bounds__(TX * TY)
 k_tile(const TileArgs a, int limiter) {
   using G = TileGeom<TX, TY, D>;
-  using L = TileSmem<T, TX, TY, D, VB, MODE>;
+  using L = TileSmem<T, TX, TY, D, VB, MODE, CV>;
+  static_assert(!CV || D == 2, "curvilinear meshes are two-dimensional");
   using N = Num<T>;
   static_assert(G::NHALO <= G::NT, "halo larger than the thread count");
   static_assert(G::NSL <= 2 * G::NT, "slope rectangle larger than two per thread");
@@ -195,6 +204,10 @@ k_tile(const TileArgs a, int limiter) {
   T* sFP = reinterpret_cast<T*>(smem + L::FP);
   T* sAcc = reinterpret_cast<T*>(smem + L::ACC);
   int* sMeta = reinterpret_cast<int*>(smem + L::META);
+  T* sJt = reinterpret_cast<T*>(smem + L::JT);
+  T* sFG = reinterpret_cast<T*>(smem + L::FG);
+  const T* __restrict__ cg = reinterpret_cast<const T*>(a.cgeo);
+  const T* __restrict__ fg = reinterpret_cast<const T*>(a.fgeo);
 
   const StepConst& k = a.k;
   const S* __restrict__ fin = reinterpret_cast<const S*>(a.f_in);
@@ -281,6 +294,10 @@ k_tile(const TileArgs a, int limiter) {
     meta |= role << 5;
     sMeta[f] = meta;
     sMeta[G::NF + f] = (role == FR_CROSS || role == FR_RECV) ? a.fslot[fid] : fid;
+    if constexpr (CV) {
+#pragma unroll
+      for (int p = 0; p < 7; ++p) sFG[p * G::NF + f] = fid >= 0 ? fg[(long)p * k.nface + fid] : T(0);
+    }
     if (MODE == 1 && (role == FR_NORMAL || role == FR_CROSS)) {
 #pragma unroll
       for (int p = 0; p < 13; ++p) sFP[p * G::NF + f] = fp[(long)p * k.nface + fid];
@@ -303,6 +320,15 @@ k_tile(const TileArgs a, int limiter) {
     }
   }
 
+  // curvilinear: J^{-T} of the slope rectangle (ghost positions take the boundary cell's)
+  if constexpr (CV) {
+    for (int q = tid; q < G::NSL; q += G::NT) {
+      const int sx = q % G::SW - 1, sy = q / G::SW - 1;
+      const int c = wrap_or_clamp(y0 + sy, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + sx, k.nx, k.px);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) sJt[p * G::NSL + q] = cg[(long)p * k.ncell + c];
+    }
+  }
   // MODE 0 accumulators of the thread's first two faces in registers:
   // Kahan (s, c) for M0, MX, MY, E, plain for Gxx, Gxy, Gyy, Jx, Jy
   T ra[2][13];
@@ -319,7 +345,10 @@ k_tile(const TileArgs a, int limiter) {
   const T s = T(0.5 * k.dt);
   const T hdx = T(0.5 * k.dx), hdy = T(0.5 * k.dy);
   const T idx_ = T(1.0 / k.dx), idy_ = T(1.0 / k.dy);
-  const T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
+  T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
+  if constexpr (CV) {
+    if (own_active) lamx = lamy = cg[4L * k.ncell + c0g];   // dt / |V| of the own cell
+  }
   S* __restrict__ fout = reinterpret_cast<S*>(a.f_out);
   T* __restrict__ Xo = reinterpret_cast<T*>(a.X);
   const T* __restrict__ Yi = reinterpret_cast<const T*>(a.Y);
@@ -416,6 +445,20 @@ k_tile(const TileArgs a, int limiter) {
         const T* Pg = sP + (b * 2 + 0) * G::NEXT;
         const T* Ph = sP + (b * 2 + 1) * G::NEXT;
         T* Sb = sS + b * 4 * G::NSL;
+        if constexpr (CV) {
+          // index-direction slopes (unit spacing) -> physical slopes: sigma = J^{-T} (d_i, d_j)
+          const T one = T(1);
+          const T gi = limited(N::sub(Pg[e + 1], Pg[e]), N::sub(Pg[e], Pg[e - 1]), one, limiter);
+          const T hi = limited(N::sub(Ph[e + 1], Ph[e]), N::sub(Ph[e], Ph[e - 1]), one, limiter);
+          const T gj = limited(N::sub(Pg[e + G::EW], Pg[e]), N::sub(Pg[e], Pg[e - G::EW]), one, limiter);
+          const T hj = limited(N::sub(Ph[e + G::EW], Ph[e]), N::sub(Ph[e], Ph[e - G::EW]), one, limiter);
+          const T j00 = sJt[q], j01 = sJt[G::NSL + q], j10 = sJt[2 * G::NSL + q], j11 = sJt[3 * G::NSL + q];
+          Sb[q] = N::fma(j01, gj, N::mul(j00, gi));
+          Sb[G::NSL + q] = N::fma(j01, hj, N::mul(j00, hi));
+          Sb[2 * G::NSL + q] = N::fma(j11, gj, N::mul(j10, gi));
+          Sb[3 * G::NSL + q] = N::fma(j11, hj, N::mul(j10, hi));
+          continue;
+        }
         Sb[q] = limited(N::sub(Pg[e + 1], Pg[e]), N::sub(Pg[e], Pg[e - 1]), idx_, limiter);
         Sb[G::NSL + q] = limited(N::sub(Ph[e + 1], Ph[e]), N::sub(Ph[e], Ph[e - 1]), idx_, limiter);
         if (D == 2) {
@@ -472,7 +515,29 @@ k_tile(const TileArgs a, int limiter) {
         const T bx_ = N::mul(-xix, s), by_ = N::mul(-xiy, s);
         T gb, hb, xn;
         // upwind side only (the mean of both sides when xi.n = 0)
-        if (dir == 0) {
+        if constexpr (CV) {
+          // xi.n as two rounded products and a rounded sum: its sign picks the upwind side,
+          // and a velocity tangential to the face gives the same rounded value wherever
+          // this is evaluated
+          xn = N::add(N::mul(xix, sFG[f]), N::mul(xiy, sFG[G::NF + f]));
+          auto rec = [&](int cx, int cy, T ox, T oy, T& gg, T& hh) {
+            const int e = G::eidx(cx, cy), si = G::sidx(cx, cy);
+            gg = N::fma(N::add(oy, by_), Sb[2 * G::NSL + si], N::fma(N::add(ox, bx_), Sb[si], Pg[e]));
+            hh = N::fma(N::add(oy, by_), Sb[3 * G::NSL + si], N::fma(N::add(ox, bx_), Sb[G::NSL + si], Ph[e]));
+          };
+          const int lx = dir == 0 ? li - 1 : li, ly = dir == 0 ? lj : lj - 1;
+          const T dLx = sFG[3 * G::NF + f], dLy = sFG[4 * G::NF + f];
+          const T dRx = sFG[5 * G::NF + f], dRy = sFG[6 * G::NF + f];
+          if (xn > T(0)) rec(lx, ly, dLx, dLy, gb, hb);
+          else if (xn < T(0)) rec(li, lj, dRx, dRy, gb, hb);
+          else {
+            T g2, h2;
+            rec(lx, ly, dLx, dLy, gb, hb);
+            rec(li, lj, dRx, dRy, g2, h2);
+            gb = N::mul(T(0.5), N::add(gb, g2));
+            hb = N::mul(T(0.5), N::add(hb, h2));
+          }
+        } else if (dir == 0) {
           xn = xix;
           auto rec = [&](int cx, T off, T& gg, T& hh) {
             const int e = G::eidx(cx, lj), si = G::sidx(cx, lj);
@@ -553,8 +618,11 @@ k_tile(const TileArgs a, int limiter) {
               hf = hb;
             }
           }
-          // microflux (xi.n) phi on this space (Eq. interface_reduced_fluxes)
-          const T Fg = N::mul(xn, gf), Fh = N::mul(xn, hf);
+          // microflux (xi.n) phi on this space (Eq. interface_reduced_fluxes), times |S| on
+          // curvilinear meshes
+          T xs = xn;
+          if constexpr (CV) xs = N::mul(xn, sFG[2 * G::NF + f]);
+          const T Fg = N::mul(xs, gf), Fh = N::mul(xs, hf);
           sF[(b * 2 + 0) * G::NF + f] = Fg;
           sF[(b * 2 + 1) * G::NF + f] = Fh;
           if (ML && role == FR_CROSS && (meta & FM_OWNED)) {

@@ -49,6 +49,7 @@ struct PointArgs {
   double wall[4][3];    // (u_w, v_w, T_w)
   double far[4];        // freestream (rho, u, v, T)
   int* err;             // device error bits
+  const double* wden;   // curvilinear walls: [nface] normalisation of the wall Maxwellian (or null)
   double* scr;          // split finalisation: [FIN_SCR][npt] state and velocity sums
   int* need;            // split finalisation: [npt] what the velocity sums are for
 };
@@ -284,6 +285,61 @@ __device__ __forceinline__ void store_mp(T* P, long n, long i, const MP<T>& m, T
   P[P_C2 * n + i] = m.c2; P[P_KIND * n + i] = kind;
 }
 
+// Parameters of the unit-density wall Maxwellian (u_w, v_w, T_w).
+template <class T>
+__device__ __forceinline__ void wall_mp(double R, double uw, double vw, double Tw, MP<T>& mp) {
+  const double RT = R * Tw;
+  mp.ux = T(uw); mp.uy = T(vw);
+  mp.lnh = T(-0.5 * log(2.0 * 3.14159265358979323846 * RT));
+  mp.inv2RT = T(0.5 / RT); mp.RT = T(RT);
+  mp.kqx = T(0); mp.kqy = T(0);
+  mp.b0 = T(0); mp.b1 = T(0); mp.b2 = T(0); mp.b3 = T(0); mp.c1 = T(0); mp.c2 = T(0);
+}
+
+// Curvilinear walls: den = sum_{xi.n_in > 0} w (xi.n_in) g_w of every wall face (a warp per
+// face), with xi.n formed as the tile kernels form it.  Constant in time; computed once.
+template <class T, int D>
+__global__ void k_wall_den_table(const StepConst k, GasDev gas, const T* __restrict__ vt,
+                                 const T* __restrict__ fgeo, const double* __restrict__ wallv, double* __restrict__ out) {
+  const int f = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (f >= k.nface) return;
+  int side = -1;
+  const int nxf = k.nfx * k.ny;
+  if (f < nxf) {
+    const int gi = f % k.nfx;
+    if (!k.px && gi == 0 && k.bc[0] == BC_WALL) side = 0;
+    if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) side = 1;
+  } else {
+    const int gj = (f - nxf) / k.nx;
+    if (!k.py && gj == 0 && k.bc[2] == BC_WALL) side = 2;
+    if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) side = 3;
+  }
+  if (side < 0) {
+    if (lane == 0) out[f] = 0.0;
+    return;
+  }
+  MP<T> mp;
+  wall_mp<T>(gas.R, wallv[3 * side], wallv[3 * side + 1], wallv[3 * side + 2], mp);
+  const T sgn = (side == 0 || side == 2) ? T(1) : T(-1);
+  const T nx = fgeo[f], ny = fgeo[(long)k.nface + f];
+  const int nv = k.nv;
+  KSum<T> den;
+  den.zero();
+  for (int v = lane; v < nv; v += 32) {
+    const T xx = vt[v], yy = vt[nv + v];
+    const T xn = Num<T>::add(Num<T>::mul(xx, nx), Num<T>::mul(yy, ny));   // as the tile kernels form it
+    const T xin = sgn * xn;
+    if (xin > T(0)) {
+      T gv, hv;
+      model_eval<T, D>(mp, xx, yy, T(k.c0), T(k.twoK), gv, hv);
+      den.add(vt[2 * nv + v] * (vt[3 * nv + v] * (xin * gv)));
+    }
+  }
+  const double d = lane_sum<32>(den.val());
+  if (lane == 0) out[f] = d;
+}
+
 __device__ __forceinline__ int wrap_or_clamp_h(int g, int n, int periodic) {
   if (periodic) { g %= n; return g < 0 ? g + n : g; }
   return g < 0 ? 0 : (g >= n ? n - 1 : g);
@@ -387,11 +443,7 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   const bool wall = kind == FK_WALL_LO || kind == FK_WALL_HI;
   const bool free_ = kind == FK_FREE_LO || kind == FK_FREE_HI;
   if (wall) {
-    const double uw = a.wall[side][0], vw = a.wall[side][1], Tw = a.wall[side][2];
-    const double RT = g.R * Tw;
-    mp.ux = T(uw); mp.uy = T(vw);
-    mp.lnh = T(-0.5 * log(2.0 * 3.14159265358979323846 * RT));
-    mp.inv2RT = T(0.5 / RT); mp.RT = T(RT);
+    wall_mp<T>(g.R, a.wall[side][0], a.wall[side][1], a.wall[side][2], mp);
     need = 1;
   } else if (free_) {
     // freestream side: the model of the freestream state, entering with weight one
@@ -436,7 +488,8 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   double den = 0.0;
   double G[5][5], H[3][3];
   if (PART == 0) {
-    if (need == 1) den = wall_den<T, D, 1>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1), 0);
+    if (need == 1)
+      den = a.wden ? a.wden[i] : wall_den<T, D, 1>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1), 0);
     if (need == 2) {
       if (k.nax > 0) axis_moments<T, D>(a, mp, G, H);
       else direct_moments<T, D, 1>(a, mp, 0, G, H);
@@ -524,6 +577,10 @@ __global__ void k_fin_sums(const PointArgs a) {
   q.b0 = q.b1 = q.b2 = q.b3 = T(0);
   const long n = a.npt;
   if (need >= 16) {
+    if (a.wden) {
+      if (lane == 0) a.scr[FS_DEN * n + i] = a.wden[i];
+      return;
+    }
     const int side = (need - 16) >> 2, kind = (need - 16) & 3;
     const double d = wall_den<T, D, 32>(a, q, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1), lane);
     if (lane == 0) a.scr[FS_DEN * n + i] = d;

@@ -100,6 +100,7 @@ struct LevelRt {
   StepConst k;
   DevBuf f[2], prm[2], fprm, cpart, fpart, ids, frole, fslot, ghost_of, ghost, X, Y, tiles;
   DevBuf fscr, fneed;        // split finalisation scratch (spaces that are not tensor products)
+  DevBuf wden;               // curvilinear walls: [nface] wall-Maxwellian normalisation
   int nghost = 0, nX = 0, nY = 0, ntiles = 0;
   int cur = 0, pcur = 0;
   bool fresh = false;
@@ -181,6 +182,12 @@ struct mlvs_handle {
   long long epoch = 0;            // bumped whenever the level structure or chunking changes
   long long warm_epoch = -1;      // epoch of the last regular step (maps and tables exist)
   int cta_target = 148 * 4;       // CTAs per tile launch the chunking aims at (autotuned)
+  // curvilinear mesh (mesh_kind 1): host geometry in FP64, device copies in the compute type
+  bool curvi = false;
+  std::vector<double> cgeo;       // [5][ncell]: J^{-T} (4), |V|
+  std::vector<double> fgeo;       // [7][nface]: normal (2), |S|, x_b - x_L (2), x_b - x_R (2)
+  double lmin = 0.0;              // smallest cell width |V| / max |S|
+  DevBuf cgeo_d, fgeo_d;
   std::map<std::vector<long long>, std::pair<cudaGraphExec_t, std::vector<int>>> graphs;
   cudaStream_t cap = nullptr;     // capture stream
   std::vector<cudaStream_t> branch;
@@ -394,6 +401,8 @@ template <class S, class T, int D> struct Runner {
   static constexpr int VB = 2;   // velocities per barrier round
   static constexpr size_t SM0 = TileSmem<T, TX, TY, D, VB, 0>::BYTES;
   static constexpr size_t SM1 = TileSmem<T, TX, TY, D, VB, 1>::BYTES;
+  static constexpr size_t SM0C = TileSmem<T, TX, TY, D, VB, 0, true>::BYTES;
+  static constexpr size_t SM1C = TileSmem<T, TX, TY, D, VB, 1, true>::BYTES;
   static constexpr int FIN_BLOCK = 64;
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
   // tensor-product spaces: one kernel (one-axis sums per thread); others: the split path
@@ -412,16 +421,44 @@ template <class S, class T, int D> struct Runner {
   }
 
   static cudaError_t set_smem_limits() {
-    const void* fn[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false>,
-                         (const void*)k_tile<S, T, D, TX, TY, VB, 0, true>,
-                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, false>,
-                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, true>};
+    const void* fn[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false, false>,
+                         (const void*)k_tile<S, T, D, TX, TY, VB, 0, true, false>,
+                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, false, false>,
+                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, true, false>};
     for (int i = 0; i < 4; ++i) {
       cudaError_t e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(i < 2 ? SM0 : SM1));
       if (e != cudaSuccess) return e;
     }
+    if constexpr (D == 2) {
+      const void* fc[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false, true>,
+                           (const void*)k_tile<S, T, D, TX, TY, VB, 0, true, true>,
+                           (const void*)k_tile<S, T, D, TX, TY, VB, 1, false, true>,
+                           (const void*)k_tile<S, T, D, TX, TY, VB, 1, true, true>};
+      for (int i = 0; i < 4; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(fc[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(i < 2 ? SM0C : SM1C));
+        if (e != cudaSuccess) return e;
+      }
+    }
     return cudaSuccess;
+  }
+
+  // one tile pass: with or without level tables, Cartesian or curvilinear
+  template <int MODE>
+  static void launch_tile(mlvs_handle* h, const LevelRt& L, dim3 grid, const TileArgs& t, int limiter) {
+    const bool one = single(h, L);
+    if constexpr (D == 2) {
+      if (h->curvi) {
+        constexpr size_t sm = MODE == 0 ? SM0C : SM1C;
+        if (one) k_tile<S, T, D, TX, TY, VB, MODE, false, true><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
+        else k_tile<S, T, D, TX, TY, VB, MODE, true, true><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
+        return;
+      }
+    }
+    constexpr size_t sm = MODE == 0 ? SM0 : SM1;
+    if (one) k_tile<S, T, D, TX, TY, VB, MODE, false, false><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
+    else k_tile<S, T, D, TX, TY, VB, MODE, true, false><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
   }
 
   // a level that holds every cell runs the tile kernels without level tables
@@ -463,6 +500,7 @@ template <class S, class T, int D> struct Runner {
     a.prm_out = nullptr;
     a.scr = nullptr;
     a.need = nullptr;
+    a.wden = h->curvi ? L.wden.as<double>() : nullptr;
     return a;
   }
 
@@ -493,6 +531,8 @@ template <class S, class T, int D> struct Runner {
     t.Y = L.Y.p;
     t.nY = L.nY;
     t.ucell = I.ucell.p;
+    t.cgeo = h->curvi ? h->cgeo_d.p : nullptr;
+    t.fgeo = h->curvi ? h->fgeo_d.p : nullptr;
     t.step = I.stepctr.as<unsigned>();
     t.salt = hash_host((unsigned)lid * 0x9e3779b9u + (unsigned)(&I - h->inst.data()) * 0x85ebca77u);
     return t;
@@ -599,8 +639,7 @@ template <class S, class T, int D> struct Runner {
       t.part = L.fpart.as<double>();
       dim3 grid(L.ntiles, L.k.nchunk);
       mark_begin(h, 1);
-      if (single(h, L)) k_tile<S, T, D, TX, TY, VB, 0, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
-      else k_tile<S, T, D, TX, TY, VB, 0, true><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+      launch_tile<0>(h, L, grid, t, limiter);
       mark_end(h);
     }
     for (int l = 0; l < (int)I.lv.size(); ++l) {
@@ -620,8 +659,7 @@ template <class S, class T, int D> struct Runner {
         t.part = L.cpart.as<double>();
         dim3 grid(L.ntiles, L.k.nchunk);
         mark_begin(h, 3);
-        if (single(h, L)) k_tile<S, T, D, TX, TY, VB, 1, false><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
-        else k_tile<S, T, D, TX, TY, VB, 1, true><<<grid, TX * TY, SM1, h->stream>>>(t, limiter);
+        launch_tile<1>(h, L, grid, t, limiter);
         mark_end(h);
       }
       if ((e = run_fluxes(h, I, l)) != cudaSuccess) return e;
@@ -710,6 +748,24 @@ template <class S, class T, int D> struct Runner {
     return cudaGetLastError();
   }
 
+  // curvilinear walls: the wall-Maxwellian normalisation of every face of a level (once)
+  static cudaError_t wall_table(mlvs_handle* h, LevelRt& L) {
+    if constexpr (D == 2) {
+      cudaError_t e = L.wden.alloc((size_t)L.k.nface * sizeof(double));
+      if (e != cudaSuccess) return e;
+      std::vector<double> wv(12);
+      for (int s = 0; s < 4; ++s)
+        for (int j = 0; j < 3; ++j) wv[3 * s + j] = h->cfg.wall[s][j];
+      DevBuf wd;
+      if ((e = upload(wd, wv, h->stream)) != cudaSuccess) return e;
+      k_wall_den_table<T, D><<<(L.k.nface * 32 + 127) / 128, 128, 0, h->stream>>>(
+          L.k, h->gas, h->spaces[L.space].vt.as<T>(), h->fgeo_d.as<T>(), wd.as<double>(), L.wden.as<double>());
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      return cudaStreamSynchronize(h->stream);
+    }
+    return cudaSuccess;
+  }
+
   // masks of the criterion (Sec. 3.2) of every cell of an instance into kout[ncell][N1*N1]
   // sel: the global ids of the cells to judge (null: every cell)
   static cudaError_t criterion(mlvs_handle* h, Inst& I, const mlvs_adapt_params& p, unsigned char* kout,
@@ -779,11 +835,13 @@ struct Ops {
   cudaError_t (*transfer)(mlvs_handle*, Inst&, Inst&);
   cudaError_t (*moments_of_levels)(mlvs_handle*, Inst&);
   cudaError_t (*criterion)(mlvs_handle*, Inst&, const mlvs_adapt_params&, unsigned char*, const std::vector<int>*);
+  cudaError_t (*wall_table)(mlvs_handle*, LevelRt&);
 };
 
 template <class S, class T, int D> Ops make_ops() {
   using R = Runner<S, T, D>;
-  return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion};
+  return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion,
+             &R::wall_table};
 }
 
 Ops ops_for(int storage, int D) {
@@ -1007,6 +1065,7 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
         L.Y.alloc(2ull * k.nv * L.nY * h->tsize) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     CK(cudaMemsetAsync(L.fprm.p, 0, L.fprm.n, h->stream));
+    if (h->curvi) CK(ops_for(h->cfg.storage, D).wall_table(h, L));
     if (sp.nax == 0) {
       const size_t np = std::max<size_t>(std::max<size_t>(nface, nc), 1);
       if (L.fscr.alloc(FIN_SCR * np * sizeof(double)) != cudaSuccess || L.fneed.alloc(np * sizeof(int)) != cudaSuccess)
@@ -1026,6 +1085,108 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
 }
 
 // ---------------------------------------------------------------------------------------
+
+// Geometry of a structured curvilinear mesh from its nodes [ny+1][nx+1][2] (FP64): cells
+// A=(i,j), B=(i+1,j), C=(i+1,j+1), D=(i,j+1) counter-clockwise; area from the diagonals,
+// centroid of the triangles ABC and ACD, J^{-T} from the mean edge vectors; i-faces from
+// node (i,j) to (i,j+1) with n = (e_y, -e_x)/|e|, j-faces from (i,j) to (i+1,j) with
+// n = (-e_y, e_x)/|e|; per face the offsets x_b - x_c of both neighbours, the centroid of
+// a periodic image moved by the period, the first ghost's reflected through the face.
+static mlvs_status build_geometry(mlvs_handle* h, const double* xy) {
+  const int nx = h->nx, ny = h->ny, nc = nx * ny;
+  const int px = h->cfg.bc[0] == MLVS_BC_PERIODIC, py = h->cfg.bc[2] == MLVS_BC_PERIODIC;
+  const int nfx = px ? nx : nx + 1, nfy = py ? ny : ny + 1;
+  const int nface = nfx * ny + nx * nfy;
+  auto X = [&](int j, int i) { return xy[2 * ((size_t)j * (nx + 1) + i)]; };
+  auto Y = [&](int j, int i) { return xy[2 * ((size_t)j * (nx + 1) + i) + 1]; };
+  auto cross = [](double ux, double uy, double vx, double vy) { return ux * vy - uy * vx; };
+  h->cgeo.assign(5 * (size_t)nc, 0.0);
+  std::vector<double> cx(nc), cy(nc);
+  double lmin = 1e300;
+  for (int j = 0; j < ny; ++j)
+    for (int i = 0; i < nx; ++i) {
+      const double Ax = X(j, i), Ay = Y(j, i), Bx = X(j, i + 1), By = Y(j, i + 1);
+      const double Cx = X(j + 1, i + 1), Cy = Y(j + 1, i + 1), Dx = X(j + 1, i), Dy = Y(j + 1, i);
+      const double area = 0.5 * cross(Cx - Ax, Cy - Ay, Dx - Bx, Dy - By);
+      if (!(area > 0.0)) return fail(h, MLVS_ERR_ARG, "mesh cells must be counter-clockwise with positive area");
+      const double a1 = 0.5 * cross(Bx - Ax, By - Ay, Cx - Ax, Cy - Ay);
+      const double a2 = 0.5 * cross(Cx - Ax, Cy - Ay, Dx - Ax, Dy - Ay);
+      const int c = j * nx + i;
+      cx[c] = (a1 * (Ax + Bx + Cx) + a2 * (Ax + Cx + Dx)) / (3.0 * area);
+      cy[c] = (a1 * (Ay + By + Cy) + a2 * (Ay + Cy + Dy)) / (3.0 * area);
+      const double dix = 0.5 * ((Bx - Ax) + (Cx - Dx)), diy = 0.5 * ((By - Ay) + (Cy - Dy));
+      const double djx = 0.5 * ((Dx - Ax) + (Cx - Bx)), djy = 0.5 * ((Dy - Ay) + (Cy - By));
+      const double det = dix * djy - djx * diy;
+      h->cgeo[c] = djy / det;
+      h->cgeo[nc + c] = -diy / det;
+      h->cgeo[2 * (size_t)nc + c] = -djx / det;
+      h->cgeo[3 * (size_t)nc + c] = dix / det;
+      h->cgeo[4 * (size_t)nc + c] = area;
+      const double l1 = std::hypot(Dx - Ax, Dy - Ay), l2 = std::hypot(Cx - Bx, Cy - By);
+      const double l3 = std::hypot(Bx - Ax, By - Ay), l4 = std::hypot(Cx - Dx, Cy - Dy);
+      lmin = std::min(lmin, area / std::max(std::max(l1, l2), std::max(l3, l4)));
+    }
+  h->lmin = lmin;
+  // translation of the periodic images
+  double sxx = 0, sxy = 0, syx = 0, syy = 0;
+  for (int j = 0; j <= ny; ++j) { sxx += X(j, nx) - X(j, 0); sxy += Y(j, nx) - Y(j, 0); }
+  for (int i = 0; i <= nx; ++i) { syx += X(ny, i) - X(0, i); syy += Y(ny, i) - Y(0, i); }
+  sxx /= ny + 1; sxy /= ny + 1; syx /= nx + 1; syy /= nx + 1;
+  h->fgeo.assign(7 * (size_t)nface, 0.0);
+  auto put = [&](int f, double nxv, double nyv, double len, double bx, double by, double lx, double ly,
+                 double rx, double ry) {
+    double* g = h->fgeo.data();
+    g[f] = nxv; g[nface + f] = nyv; g[2 * (size_t)nface + f] = len;
+    g[3 * (size_t)nface + f] = bx - lx; g[4 * (size_t)nface + f] = by - ly;
+    g[5 * (size_t)nface + f] = bx - rx; g[6 * (size_t)nface + f] = by - ry;
+  };
+  for (int j = 0; j < ny; ++j)
+    for (int p = 0; p < nfx; ++p) {
+      const double ex = X(j + 1, p) - X(j, p), ey = Y(j + 1, p) - Y(j, p);
+      const double len = std::hypot(ex, ey);
+      const double bx = 0.5 * (X(j, p) + X(j + 1, p)), by = 0.5 * (Y(j, p) + Y(j + 1, p));
+      double lx, ly, rx, ry;
+      if (p == 0) {
+        if (px) { lx = cx[j * nx + nx - 1] - sxx; ly = cy[j * nx + nx - 1] - sxy; }
+        else { lx = 2.0 * bx - cx[j * nx]; ly = 2.0 * by - cy[j * nx]; }
+      } else { lx = cx[j * nx + p - 1]; ly = cy[j * nx + p - 1]; }
+      if (p == nx) { rx = 2.0 * bx - cx[j * nx + nx - 1]; ry = 2.0 * by - cy[j * nx + nx - 1]; }
+      else { rx = cx[j * nx + p]; ry = cy[j * nx + p]; }
+      put(j * nfx + p, ey / len, -ex / len, len, bx, by, lx, ly, rx, ry);
+    }
+  for (int p = 0; p < nfy; ++p)
+    for (int i = 0; i < nx; ++i) {
+      const double ex = X(p, i + 1) - X(p, i), ey = Y(p, i + 1) - Y(p, i);
+      const double len = std::hypot(ex, ey);
+      const double bx = 0.5 * (X(p, i) + X(p, i + 1)), by = 0.5 * (Y(p, i) + Y(p, i + 1));
+      double lx, ly, rx, ry;
+      if (p == 0) {
+        if (py) { lx = cx[(ny - 1) * nx + i] - syx; ly = cy[(ny - 1) * nx + i] - syy; }
+        else { lx = 2.0 * bx - cx[i]; ly = 2.0 * by - cy[i]; }
+      } else { lx = cx[(p - 1) * nx + i]; ly = cy[(p - 1) * nx + i]; }
+      if (p == ny) { rx = 2.0 * bx - cx[(ny - 1) * nx + i]; ry = 2.0 * by - cy[(ny - 1) * nx + i]; }
+      else { rx = cx[p * nx + i]; ry = cy[p * nx + i]; }
+      put(nfx * ny + p * nx + i, -ey / len, ex / len, len, bx, by, lx, ly, rx, ry);
+    }
+  h->curvi = true;
+  return MLVS_OK;
+}
+
+// Device copies of the curvilinear geometry in the compute type; dt/|V| needs dt.
+static mlvs_status upload_geometry(mlvs_handle* h) {
+  const size_t nc = (size_t)h->nx * h->ny;
+  std::vector<double> c(h->cgeo);
+  for (size_t i = 0; i < nc; ++i) c[4 * nc + i] = h->dt / h->cgeo[4 * nc + i];
+  if (h->tsize == 8) {
+    CK(upload(h->cgeo_d, c, h->stream));
+    CK(upload(h->fgeo_d, h->fgeo, h->stream));
+  } else {
+    CK(upload(h->cgeo_d, std::vector<float>(c.begin(), c.end()), h->stream));
+    CK(upload(h->fgeo_d, std::vector<float>(h->fgeo.begin(), h->fgeo.end()), h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return MLVS_OK;
+}
 
 extern "C" mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out) {
   mlvs_handle* h = nullptr;
@@ -1079,6 +1240,22 @@ extern "C" mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out) {
   h->ssize = cfg->storage == MLVS_F64 ? 8 : (cfg->storage == MLVS_F32 ? 4 : 2);
   static std::atomic<unsigned long long> next_uid{1};
   h->uid = next_uid++;
+  if (cfg->mesh_kind == 1) {
+    if (!cfg->node_xy || cfg->dim != 2) {
+      delete h;
+      return fail(nullptr, MLVS_ERR_ARG, "a curvilinear mesh needs dim 2 and node_xy");
+    }
+    mlvs_status gs = build_geometry(h, cfg->node_xy);
+    if (gs != MLVS_OK) {
+      const std::string m = h->err;
+      delete h;
+      return fail(nullptr, gs, m);
+    }
+    h->cfg.node_xy = nullptr;
+  } else if (cfg->mesh_kind != 0) {
+    delete h;
+    return fail(nullptr, MLVS_ERR_ARG, "mesh_kind must be 0 (box) or 1 (curvilinear)");
+  }
   if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
     delete h;
     return fail(nullptr, MLVS_ERR_CUDA, "cudaEventCreate failed");
@@ -1211,8 +1388,12 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
   h->level_space.assign(n_levels, 0);
   // time step (reading of CFL = 0.5): dt = cfl * min(dx, dy) / max |xi|_inf on the base grid
   const double vmax = std::max(std::fabs(umin), std::fabs(umax));
-  const double hmin = D == 2 ? std::min(h->dx, h->dy) : h->dx;
+  const double hmin = h->curvi ? h->lmin : (D == 2 ? std::min(h->dx, h->dy) : h->dx);
   h->dt = h->cfg.dt > 0 ? h->cfg.dt : h->cfg.cfl * hmin / vmax;
+  if (h->curvi) {
+    mlvs_status gs = upload_geometry(h);
+    if (gs != MLVS_OK) return gs;
+  }
   for (int l = 0; l < n_levels; ++l) {
     std::vector<int> kap(nb);
     if (levels[l].uniform_L >= 0) {

@@ -33,7 +33,8 @@ class mlvs_config(C.Structure):
         ("L_ref", C.c_double), ("T_ref", C.c_double), ("rho_ref", C.c_double),
         ("cfl", C.c_double), ("dt", C.c_double), ("storage", C.c_int), ("compat_cell", C.c_int),
         ("compat_face", C.c_int), ("limiter", C.c_int), ("init_W", C.POINTER(C.c_double)),
-        ("stream", C.c_void_p), ("far", C.c_double * 4),
+        ("stream", C.c_void_p), ("far", C.c_double * 4), ("mesh_kind", C.c_int),
+        ("node_xy", C.POINTER(C.c_double)),
     ]
 
 
@@ -349,7 +350,7 @@ def mlvs_last_error(h=None):
 def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0, K=0.0,
                 Pr=2.0 / 3.0, omega=0.81, Kn=0.0, mu_ref=0.0, cfl=0.5, dt=0.0, storage=F32,
                 compat_cell=1, compat_face=1, limiter=LIMITER_VANLEER, n_instances=1,
-                stream=None, T_ref=1.0, L_ref=1.0, rho_ref=1.0, far=(1.0, 0.0, 0.0, 1.0)):
+                stream=None, T_ref=1.0, L_ref=1.0, rho_ref=1.0, far=(1.0, 0.0, 0.0, 1.0), nodes=None):
     """Fill an mlvs_config.  init_W: float64 array [n_instances][ny][nx][4].  The returned
     config keeps a reference to init_W (attribute `_keep`)."""
     cfg = mlvs_config()
@@ -369,4 +370,9 @@ def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0
     cfg.stream = stream
     for j in range(4):
         cfg.far[j] = far[j]
+    if nodes is not None:
+        xy = np.ascontiguousarray(nodes, dtype=np.float64)    # [ny+1][nx+1][2]
+        cfg._keep_nodes = xy
+        cfg.mesh_kind = 1
+        cfg.node_xy = xy.ctypes.data_as(C.POINTER(C.c_double))
     return cfg

@@ -30,7 +30,7 @@ class Solver:
             omega=d["omega"], Kn=d["Kn"] or 0.0, mu_ref=d["mu_ref"] or 0.0, cfl=d["cfl"],
             storage=_ST[storage or d["storage"]], compat_cell=compat_cell, compat_face=compat_face,
             limiter=_LIM[d["limiter"]], n_instances=n_instances, stream=stream,
-            far=d.get("far", (1.0, 0.0, 0.0, 1.0)))
+            far=d.get("far", (1.0, 0.0, 0.0, 1.0)), nodes=d.get("nodes"))
         self.h = M.mlvs_create(self.cfg)
         M.mlvs_set_velocity_levels(self.h, d["n_base"], d["umin"], d["umax"], _RULE[d["rule"]],
                                    list(levels), adaptive)

@@ -72,6 +72,46 @@ def supersonic_channel(nx=48, ny=16, mach=2.0, n_base=41, umax=8.0, Kn=0.05, sto
     return d
 
 
+def ogrid_nodes(ntheta, nr, r_in=1.0, r_out=11.0):
+    """Nodes [nr+1][ntheta+1][2] of an O-grid around a cylinder of radius r_in: ntheta cells
+    around (the node index i runs clockwise so that cells are counter-clockwise with j
+    outward; column ntheta repeats column 0), nr cells out to r_out, geometrically stretched
+    with the first cell height r_in 2 pi / ntheta (square cells at the wall)."""
+    h0 = r_in * 2.0 * math.pi / ntheta
+    lo, hi = 1.0 + 1e-12, 2.0
+    for _ in range(200):
+        q = 0.5 * (lo + hi)
+        if h0 * (q ** nr - 1.0) / (q - 1.0) > r_out - r_in:
+            hi = q
+        else:
+            lo = q
+    q = 0.5 * (lo + hi)
+    r = r_in + h0 * (q ** np.arange(nr + 1) - 1.0) / (q - 1.0)
+    r[-1] = r_out
+    th = -2.0 * math.pi * np.arange(ntheta + 1) / ntheta
+    R, TH = np.meshgrid(r, th, indexing="ij")
+    xy = np.stack([R * np.cos(TH), R * np.sin(TH)], axis=-1)
+    xy[:, -1] = xy[:, 0]
+    return xy
+
+
+def cylinder(ntheta=256, nr=128, mach=5.0, Kn=0.1, n_base=201, umax=15.0, r_out=11.0, storage="f32"):
+    """Flow past a cylinder of radius 1 on an O-grid: periodic around, a diffuse wall at
+    T_w = T_inf on the cylinder (j = 0), freestream (rho, T = 1, u = Ma sqrt(gamma R T),
+    gamma = 5/3) at the outer boundary; the gas starts as the freestream."""
+    u = mach * math.sqrt(5.0 / 3.0)
+    nodes = ogrid_nodes(ntheta, nr, 1.0, r_out)
+    init = np.zeros((nr, ntheta, 4))
+    init[..., 0] = 1.0
+    init[..., 1] = u
+    init[..., 3] = 1.0
+    d = _desc("cylinder", 2, ntheta, nr, 1.0, 1.0, ("periodic", "periodic", "wall", "freestream"), init,
+              Kn=Kn, n_base=n_base, umin=-umax, umax=umax, storage=storage)
+    d["far"] = (1.0, u, 0.0, 1.0)
+    d["nodes"] = nodes
+    return d
+
+
 def periodic_random(nx, ny, n_base=25, umax=6.0, seed=SEED, amp=0.2, Kn=0.1, Pr=2.0 / 3.0,
                     storage="f32", dim=2, bc=None):
     """Smooth random periodic fields: a few seeded Fourier modes of rho, u, v, T."""

@@ -3,7 +3,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from oracle import dugks, kinetic, vspace
+from oracle import curvi, dugks, kinetic, vspace
 
 
 def oracle_setup(desc, L=0, compat=True):
@@ -13,22 +13,30 @@ def oracle_setup(desc, L=0, compat=True):
     sp = vspace.uniform_space(base, L)
     mu = d["mu_ref"] or kinetic.mu_ref_from_kn(d["Kn"], d["omega"], R=d["R"])
     gas = kinetic.Gas(D=D, K=d["K"], R=d["R"], Pr=d["Pr"], omega=d["omega"], mu_ref=mu)
-    mesh = dugks.Mesh(d["nx"], d["ny"], d["Lx"] / d["nx"], d["Ly"] / d["ny"], bc=d["bc"], wall=d["wall"],
-                      far=tuple(d.get("far", (1.0, 0.0, 0.0, 1.0))))
+    far = tuple(d.get("far", (1.0, 0.0, 0.0, 1.0)))
+    curv = d.get("nodes") is not None
+    if curv:
+        xy = d["nodes"]
+        mesh = curvi.CurviMesh(xy[..., 0], xy[..., 1], bc=d["bc"], wall=d["wall"], far=far)
+    else:
+        mesh = dugks.Mesh(d["nx"], d["ny"], d["Lx"] / d["nx"], d["Ly"] / d["ny"], bc=d["bc"], wall=d["wall"],
+                          far=far)
     init = d["init"]
     rho = init[..., 0]
     u = init[..., 1:1 + D]
     T = init[..., 3]
     g, h = dugks.initial_tilde(rho, u, T, sp.xi, sp.w, gas, compat=compat)
-    dt = dugks.time_step(mesh, sp.xi, d["cfl"], D)
+    dt = curvi.time_step(mesh, sp.xi, d["cfl"]) if curv else dugks.time_step(mesh, sp.xi, d["cfl"], D)
     opt = dugks.Options(cfl=d["cfl"], compat_cell=compat, compat_face=compat, limiter=d["limiter"])
-    return {"base": base, "sp": sp, "gas": gas, "mesh": mesh, "g": g, "h": h, "dt": dt, "opt": opt}
+    return {"base": base, "sp": sp, "gas": gas, "mesh": mesh, "g": g, "h": h, "dt": dt, "opt": opt,
+            "curvi": curv}
 
 
 def oracle_run(o, nsteps):
     g, h = o["g"], o["h"]
+    stepper = curvi.step if o.get("curvi") else dugks.step
     for _ in range(nsteps):
-        g, h, _ = dugks.step(g, h, o["mesh"], o["sp"].xi, o["sp"].w, o["gas"], o["dt"], o["opt"])
+        g, h, _ = stepper(g, h, o["mesh"], o["sp"].xi, o["sp"].w, o["gas"], o["dt"], o["opt"])
     return g, h
 
 
