@@ -142,3 +142,44 @@ def features(rho, u, v, T, qx, qy, dx, dy, periodic_x, periodic_y, R, T_ref, mu_
                   qx / (rho * RT ** 1.5), qy / (rho * RT ** 1.5),
                   h * gr / rho, h * gT / T, h * gu / np.sqrt(RT), np.log10(lam / L_ref)], axis=-1)
     return F.reshape(-1, N_IN)
+
+
+def features_curvi(rho, u, v, T, qx, qy, Jt, width, periodic_x, periodic_y, R, T_ref, mu_ref, omega,
+                   L_ref=1.0):
+    """The same features on a structured curvilinear mesh: gradients from central differences
+    along the index directions (neighbours wrapped or clamped) turned physical with the cell's
+    J^{-T} [ny][nx][4] (row-major), and the cell width |V| / max |S| [ny][nx] for dx.  On a
+    Cartesian mesh this is `features`."""
+    def d_i(f):
+        if periodic_x:
+            fp, fm = np.roll(f, -1, axis=1), np.roll(f, 1, axis=1)
+        else:
+            fp = np.concatenate([f[:, 1:], f[:, -1:]], axis=1)
+            fm = np.concatenate([f[:, :1], f[:, :-1]], axis=1)
+        return 0.5 * (fp - fm)
+
+    def d_j(f):
+        if periodic_y:
+            fp, fm = np.roll(f, -1, axis=0), np.roll(f, 1, axis=0)
+        else:
+            fp = np.concatenate([f[1:], f[-1:]], axis=0)
+            fm = np.concatenate([f[:1], f[:-1]], axis=0)
+        return 0.5 * (fp - fm)
+
+    def grad(f):
+        a, b = d_i(f), d_j(f)
+        return Jt[..., 0] * a + Jt[..., 1] * b, Jt[..., 2] * a + Jt[..., 3] * b
+
+    RT = R * T
+    gr = np.hypot(*grad(rho))
+    gT = np.hypot(*grad(T))
+    ux, uy = grad(u)
+    vx, vy = grad(v)
+    gu = np.sqrt(ux ** 2 + uy ** 2 + vx ** 2 + vy ** 2)
+    mu = mu_ref * (T / T_ref) ** omega
+    lam = mu / (rho * RT) * np.sqrt(np.pi * RT / 2.0)
+    c = np.sqrt(R * T_ref)
+    F = np.stack([np.log(rho), u / c, v / c, np.log(T / T_ref),
+                  qx / (rho * RT ** 1.5), qy / (rho * RT ** 1.5),
+                  width * gr / rho, width * gT / T, width * gu / np.sqrt(RT), np.log10(lam / L_ref)], axis=-1)
+    return F.reshape(-1, N_IN)

@@ -9,6 +9,7 @@ namespace mlvs {
 
 struct FeatArgs {
   const double* W;       // [11][ncell]: rho, u, v, T, qx, qy, ...
+  const double* geo;     // curvilinear: [5][ncell] J^{-T} (row-major) and the width |V|/max|S|; or null
   int nx, ny, px, py;
   double dx, dy, R, T_ref, mu_ref, omega, L_ref;
   float* out;            // [ncell][10]
@@ -34,10 +35,16 @@ __global__ void k_features(const FeatArgs a) {
   const double* qy = a.W + 5 * (long)nc;
   const bool two = a.ny > 1;
   auto grad = [&](const double* f, double& gx, double& gy) {
+    if (a.geo) {   // index central differences through J^{-T}
+      const double di = 0.5 * (f[ie] - f[iw]), dj = 0.5 * (f[jn] - f[js]);
+      gx = a.geo[c] * di + a.geo[nc + c] * dj;
+      gy = a.geo[2 * (long)nc + c] * di + a.geo[3 * (long)nc + c] * dj;
+      return;
+    }
     gx = (f[ie] - f[iw]) / (2.0 * a.dx);
     gy = two ? (f[jn] - f[js]) / (2.0 * a.dy) : 0.0;
   };
-  const double h = two ? fmin(a.dx, a.dy) : a.dx;
+  const double h = a.geo ? a.geo[4 * (long)nc + c] : (two ? fmin(a.dx, a.dy) : a.dx);
   const double r = rho[c], t = T[c], RT = a.R * t;
   double gx, gy, gx2, gy2;
   grad(rho, gx, gy);

@@ -187,7 +187,8 @@ struct mlvs_handle {
   std::vector<double> cgeo;       // [5][ncell]: J^{-T} (4), |V|
   std::vector<double> fgeo;       // [7][nface]: normal (2), |S|, x_b - x_L (2), x_b - x_R (2)
   double lmin = 0.0;              // smallest cell width |V| / max |S|
-  DevBuf cgeo_d, fgeo_d;
+  DevBuf cgeo_d, fgeo_d, featgeo_d;
+  std::vector<double> width;      // |V| / max |S| per cell
   std::map<std::vector<long long>, std::pair<cudaGraphExec_t, std::vector<int>>> graphs;
   cudaStream_t cap = nullptr;     // capture stream
   std::vector<cudaStream_t> branch;
@@ -1124,7 +1125,9 @@ static mlvs_status build_geometry(mlvs_handle* h, const double* xy) {
       h->cgeo[4 * (size_t)nc + c] = area;
       const double l1 = std::hypot(Dx - Ax, Dy - Ay), l2 = std::hypot(Cx - Bx, Cy - By);
       const double l3 = std::hypot(Bx - Ax, By - Ay), l4 = std::hypot(Cx - Dx, Cy - Dy);
-      lmin = std::min(lmin, area / std::max(std::max(l1, l2), std::max(l3, l4)));
+      const double wdt = area / std::max(std::max(l1, l2), std::max(l3, l4));
+      lmin = std::min(lmin, wdt);
+      h->width.push_back(wdt);
     }
   h->lmin = lmin;
   // translation of the periodic images
@@ -1184,6 +1187,10 @@ static mlvs_status upload_geometry(mlvs_handle* h) {
     CK(upload(h->cgeo_d, std::vector<float>(c.begin(), c.end()), h->stream));
     CK(upload(h->fgeo_d, std::vector<float>(h->fgeo.begin(), h->fgeo.end()), h->stream));
   }
+  std::vector<double> fg(5 * nc);
+  for (size_t i = 0; i < 4 * nc; ++i) fg[i] = h->cgeo[i];
+  for (size_t i = 0; i < nc; ++i) fg[4 * nc + i] = h->width[i];
+  CK(upload(h->featgeo_d, fg, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return MLVS_OK;
 }
@@ -1664,6 +1671,7 @@ static mlvs_status features_into(mlvs_handle* h, Inst& I, float* dst) {
   if (st != MLVS_OK) return st;
   FeatArgs a;
   a.W = I.W.as<double>();
+  a.geo = h->curvi ? h->featgeo_d.as<double>() : nullptr;
   a.nx = h->nx;
   a.ny = h->ny;
   a.px = h->cfg.bc[0] == MLVS_BC_PERIODIC;

@@ -83,3 +83,21 @@ def test_cylinder_full_size_symmetry(storage):
     assert np.max(np.abs(m[2] + _mirror(m[2], nt))) < tol * 7
     assert np.max(np.abs(m[3] - _mirror(m[3], nt)) / m[3]) < tol
     assert np.max(m[0]) > 1.05                             # a bow shock is forming
+
+
+def test_selector_features_on_the_ogrid():
+    from oracle import curvi, dugks, mlp as omlp
+    desc = workloads.cylinder(24, 8, mach=2.0, Kn=0.1, n_base=25, umax=8.0, r_out=4.0, storage="f64")
+    o = oracle_setup(desc)
+    s = Solver(desc)
+    s.step(4)
+    g, h = oracle_run(o, 4)
+    F = M.mlvs_features(s.h, 0, 24 * 8)
+    st = dugks.cell_state(g, h, o["sp"].xi, o["sp"].w, o["gas"], o["dt"])
+    G = curvi.geometry(o["mesh"])
+    longest = np.maximum(np.maximum(G["li"][:, :-1], G["li"][:, 1:]), np.maximum(G["lj"][:-1, :], G["lj"][1:, :]))
+    Fo = omlp.features_curvi(st["rho"], st["u"][..., 0], st["u"][..., 1], st["T"], st["q"][..., 0],
+                             st["q"][..., 1], G["Jt"], G["area"] / longest, True, False, R=o["gas"].R,
+                             T_ref=1.0, mu_ref=o["gas"].mu_ref, omega=o["gas"].omega)
+    assert np.max(np.abs(F - Fo) / np.maximum(1.0, np.abs(Fo))) < 1e-5
+    assert np.max(Fo[:, 6]) > 1e-3            # gradients present

@@ -89,3 +89,19 @@ def test_features_of_uniform_and_ramped_states():
     g = F2[:, 6].reshape(ny, nx) * rho2 / 0.5
     np.testing.assert_allclose(g[:, 1:-1], 0.2, rtol=1e-12)
     np.testing.assert_allclose(g[:, [0, -1]], 0.1, rtol=1e-12)
+
+
+def test_curvilinear_features_reduce_to_cartesian():
+    rng = np.random.default_rng(8)
+    ny, nx, dx, dy = 5, 7, 0.2, 0.1
+    f = [1.0 + 0.1 * rng.random((ny, nx)) for _ in range(4)]
+    q = [0.01 * rng.standard_normal((ny, nx)) for _ in range(2)]
+    Jt = np.zeros((ny, nx, 4))
+    Jt[..., 0], Jt[..., 3] = 1.0 / dx, 1.0 / dy
+    width = np.full((ny, nx), min(dx, dy))
+    for px, py in ((True, True), (False, True), (False, False)):
+        a = mlp.features(f[0], f[1], f[2], f[3], q[0], q[1], dx, dy, px, py, R=1.0, T_ref=1.0,
+                         mu_ref=0.05, omega=0.81)
+        b = mlp.features_curvi(f[0], f[1], f[2], f[3], q[0], q[1], Jt, width, px, py, R=1.0, T_ref=1.0,
+                               mu_ref=0.05, omega=0.81)
+        np.testing.assert_allclose(b, a, rtol=1e-13, atol=1e-15)
