@@ -228,7 +228,7 @@ unsigned hash_host(unsigned x) {
   return x;
 }
 
-constexpr int kTX2 = 32, kTY2 = 8, kTX1 = 128;
+constexpr int kTX2 = 16, kTY2 = 16, kTX1 = 128;
 int tile_w(int D) { return D == 2 ? kTX2 : kTX1; }
 int tile_h(int D) { return D == 2 ? kTY2 : 1; }
 
