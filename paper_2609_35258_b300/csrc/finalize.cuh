@@ -35,6 +35,7 @@ struct PointArgs {
   StepConst k;
   GasDev gas;
   const double* part;   // [nchunk][NMOM][npt]
+  const double* msum;   // [NMOM][npt] the chunk sums of part (k_sum_chunks), or null
   int npt;              // number of points
   int is_face;          // 0: cells, 1: faces
   const void* cprm;     // [NP][ncell] current cell params (T): shift source
@@ -402,9 +403,14 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   int kind = FK_INTERIOR;
   int side = -1;
   {
-    for (int c = 0; c < k.nchunk; ++c)
+    if (a.msum) {
 #pragma unroll
-      for (int m = 0; m < NMOM; ++m) M[m] += a.part[((long)c * NMOM + m) * a.npt + i];
+      for (int m = 0; m < NMOM; ++m) M[m] = a.msum[(long)m * a.npt + i];
+    } else {
+      for (int c = 0; c < k.nchunk; ++c)
+#pragma unroll
+        for (int m = 0; m < NMOM; ++m) M[m] += a.part[((long)c * NMOM + m) * a.npt + i];
+    }
     if (!a.is_face) {
       shx = cp[P_UX * (long)a.npt + i];
       shy = cp[P_UY * (long)a.npt + i];
@@ -627,6 +633,17 @@ __global__ void k_fin_post(const PointArgs a) {
   po[P_B2 * n + i] = mp.b2;
   po[P_B3 * n + i] = mp.b3;
   if (!ok) atomicOr(a.err, ERR_SINGULAR);
+}
+
+// Sums of the velocity-chunk partials in chunk order, one thread per (moment, point): the
+// same values a finalisation thread would form, with the FP64 chains spread over many warps.
+__global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int npt, double* __restrict__ out) {
+  const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long)NMOM * npt) return;
+  const int m = (int)(t / npt), i = (int)(t % npt);
+  double s = 0.0;
+  for (int c = 0; c < nchunk; ++c) s += part[((long)c * NMOM + m) * npt + i];
+  out[t] = s;
 }
 
 // Initial parameters from (rho, u, v, T) with q = 0 (phi~ = phi^eq at t = 0).

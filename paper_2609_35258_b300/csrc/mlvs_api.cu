@@ -101,6 +101,7 @@ struct LevelRt {
   DevBuf f[2], prm[2], fprm, cpart, fpart, ids, frole, fslot, ghost_of, ghost, X, Y, tiles;
   DevBuf fscr, fneed;        // split finalisation scratch (spaces that are not tensor products)
   DevBuf wden;               // curvilinear walls: [nface] wall-Maxwellian normalisation
+  DevBuf msum;               // [NMOM][max(cells, faces)] chunk sums for the finalisation
   int nghost = 0, nX = 0, nY = 0, ntiles = 0;
   int cur = 0, pcur = 0;
   bool fresh = false;
@@ -409,6 +410,13 @@ template <class S, class T, int D> struct Runner {
   // tensor-product spaces: one kernel (one-axis sums per thread); others: the split path
   // (state per thread, velocity sums per warp, correction per thread)
   static void launch_finalize(mlvs_handle* h, PointArgs a, LevelRt& L) {
+    // chunk sums first (many threads), then the finalisation reads them
+    if (L.msum.p && a.npt > 0) {
+      ++h->launches;
+      const long nt = (long)NMOM * a.npt;
+      k_sum_chunks<<<(unsigned)((nt + 255) / 256), 256, 0, h->stream>>>(a.part, a.k.nchunk, a.npt, L.msum.as<double>());
+      a.msum = L.msum.as<double>();
+    }
     if (a.k.nax > 0) {
       k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
       return;
@@ -501,6 +509,7 @@ template <class S, class T, int D> struct Runner {
     a.prm_out = nullptr;
     a.scr = nullptr;
     a.need = nullptr;
+    a.msum = nullptr;
     a.wden = h->curvi ? L.wden.as<double>() : nullptr;
     return a;
   }
@@ -1067,6 +1076,8 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     CK(cudaMemsetAsync(L.fprm.p, 0, L.fprm.n, h->stream));
     if (h->curvi) CK(ops_for(h->cfg.storage, D).wall_table(h, L));
+    if (L.msum.alloc((size_t)NMOM * std::max<size_t>(std::max<size_t>(nface, nc), 1) * sizeof(double)) != cudaSuccess)
+      return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     if (sp.nax == 0) {
       const size_t np = std::max<size_t>(std::max<size_t>(nface, nc), 1);
       if (L.fscr.alloc(FIN_SCR * np * sizeof(double)) != cudaSuccess || L.fneed.alloc(np * sizeof(int)) != cudaSuccess)
