@@ -48,6 +48,41 @@ def test_cartesian_nodes_reproduce_cartesian_path(kind):
     assert np.max(np.abs(ma - mb)) < 1e-12 * np.max(np.abs(ma))
 
 
+def _kappa_pair(n_base):
+    """Two masked spaces, fine near the origin and coarser towards +x (a) or +y (b)."""
+    from oracle import vspace
+    N1 = len(vspace.axis_groups(n_base, 1))
+    yy, xx = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
+    r = np.hypot(xx - N1 // 2, yy - N1 // 2)
+    a = np.where(r < N1 / 4, 0, np.where(xx > N1 // 2, 2, 1)).astype(np.uint8)
+    b = np.where(r < N1 / 4, 0, np.where(yy > N1 // 2, 2, 1)).astype(np.uint8)
+    return a, b
+
+
+@pytest.mark.parametrize("kind", ["cavity", "channel"])
+def test_cartesian_nodes_reproduce_cartesian_multilevel(kind):
+    """Three spaces (uniform level 0 and two masked ones) on a checkerboard of 4x4 cell
+    blocks: walls, freestream sides, cross-level faces and ghosts on the curvilinear path
+    give the Cartesian multi-level result."""
+    if kind == "cavity":
+        desc = workloads.cavity(16, n_base=25, storage="f64")
+    else:
+        desc = workloads.supersonic_channel(24, 8, n_base=25, umax=8.0, storage="f64", walls=True)
+    ka, kb = _kappa_pair(25)
+    nx, ny = desc["nx"], desc["ny"]
+    lev = np.array([((i // 4) + 2 * (j // 4)) % 3 for j in range(ny) for i in range(nx)], dtype=np.int32)
+    runs = []
+    for d in (desc, _with_nodes(desc)):
+        s = Solver(d, levels=(0, ka, kb))
+        M.mlvs_set_cell_levels(s.h, 0, lev)
+        s.step(6)
+        runs.append(s.moments())
+        s.close()
+    ma, mb = runs
+    assert np.max(np.abs(ma - mb)) < 1e-12 * np.max(np.abs(ma))
+    assert np.max(np.abs(ma[0] - 1.0)) > 1e-4                # the flow developed
+
+
 @pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 1e-5)])
 def test_ogrid_matches_oracle(storage, tol):
     desc = workloads.cylinder(24, 8, mach=2.0, Kn=0.1, n_base=25, umax=8.0, r_out=4.0, storage=storage)
