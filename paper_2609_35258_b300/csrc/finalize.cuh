@@ -36,7 +36,9 @@ struct PointArgs {
   GasDev gas;
   const double* part;   // [nchunk][NMOM][npt]
   const double* msum;   // [NMOM][npt] the chunk sums of part (k_sum_chunks), or null
-  int npt;              // number of points
+  int npt;              // number of points (the stride of every per-point array)
+  const int* pts;       // the points to finalise (faces a level evaluates), or null: 0..npt-1
+  int nwork;            // number of points to finalise (length of pts, else npt)
   int is_face;          // 0: cells, 1: faces
   const void* cprm;     // [NP][ncell] current cell params (T): shift source
   void* prm_out;        // [NP][npt] (T)
@@ -387,9 +389,9 @@ __device__ inline double wall_den(const PointArgs& A, const MP<T>& mp, bool xdir
 // share of the split path (state and uncorrected model into the parameters and scratch).
 template <class T, int D, int PART>
 __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
-  bool valid = i < a.npt;
-  if (valid && a.is_face && a.frole && a.frole[i] != FR_NORMAL && a.frole[i] != FR_CROSS) valid = false;
-  if (!valid) return;
+  if (i >= a.nwork) return;
+  if (a.pts) i = a.pts[i];
+  if (a.is_face && a.frole && a.frole[i] != FR_NORMAL && a.frole[i] != FR_CROSS) return;
   const StepConst& k = a.k;
   const T* cp = reinterpret_cast<const T*>(a.cprm);
   const T* uc = reinterpret_cast<const T*>(a.ucell);
@@ -567,16 +569,18 @@ __global__ void k_finalize(const PointArgs a) {
 template <class T, int D>
 __global__ void k_fin_pre(const PointArgs a) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < a.npt) a.need[i] = 0;
+  if (i >= a.nwork) return;
+  a.need[a.pts ? a.pts[i] : i] = 0;
   finalize_point<T, D, 1>(a, i);
 }
 
 // Velocity sums of the split path, a warp per point (blockDim a multiple of 32).
 template <class T, int D>
 __global__ void k_fin_sums(const PointArgs a) {
-  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (i >= a.npt) return;
+  if (i >= a.nwork) return;
+  if (a.pts) i = a.pts[i];
   const int need = a.need[i];
   if (need == 0) return;
   const T* P = reinterpret_cast<const T*>(a.prm_out);
@@ -607,8 +611,9 @@ __global__ void k_fin_sums(const PointArgs a) {
 // Correction of the split path: wall densities and the four-moment solve.
 template <class T, int D>
 __global__ void k_fin_post(const PointArgs a) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.npt) return;
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.nwork) return;
+  if (a.pts) i = a.pts[i];
   const int need = a.need[i];
   if (need == 0) return;
   T* po = reinterpret_cast<T*>(a.prm_out);
@@ -639,13 +644,16 @@ __global__ void k_fin_post(const PointArgs a) {
 
 // Sums of the velocity-chunk partials in chunk order, one thread per (moment, point): the
 // same values a finalisation thread would form, with the FP64 chains spread over many warps.
-__global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int npt, double* __restrict__ out) {
+// pts (null: every point) lists the nwork points to sum; npt is the stride of part and out.
+__global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int npt, const int* __restrict__ pts,
+                             int nwork, double* __restrict__ out) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long)NMOM * npt) return;
-  const int m = (int)(t / npt), i = (int)(t % npt);
+  if (t >= (long)NMOM * nwork) return;
+  const int m = (int)(t / nwork), w = (int)(t % nwork);
+  const int i = pts ? pts[w] : w;
   double s = 0.0;
   for (int c = 0; c < nchunk; ++c) s += part[((long)c * NMOM + m) * npt + i];
-  out[t] = s;
+  out[(long)m * npt + i] = s;
 }
 
 // Initial parameters from (rho, u, v, T) with q = 0 (phi~ = phi^eq at t = 0).

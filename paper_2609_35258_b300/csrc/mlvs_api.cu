@@ -102,6 +102,8 @@ struct LevelRt {
   DevBuf fscr, fneed;        // split finalisation scratch (spaces that are not tensor products)
   DevBuf wden;               // curvilinear walls: [nface] wall-Maxwellian normalisation
   DevBuf msum;               // [NMOM][max(cells, faces)] chunk sums for the finalisation
+  DevBuf flist;              // faces the level evaluates (normal and cross), when not all
+  int nflist = 0;
   int nghost = 0, nX = 0, nY = 0, ntiles = 0;
   int cur = 0, pcur = 0;
   bool fresh = false;
@@ -114,11 +116,20 @@ struct Route {               // mapped items from level src to level dst
   DevBuf items_d;
 };
 
+// Every ghost route of an instance in one launch: route arguments for each of the four
+// (f, parameter) buffer parities of the source levels, and the item groups.
+struct MapBatch {
+  DevBuf routes[4], work;
+  int nwork = 0, G = 1;
+  bool ok = false;
+};
+
 struct Inst {
   std::vector<LevelRt> lv;   // cell levels first (ids 0..n_levels-1), face levels after
   std::vector<int> lvl_of, slot_of;
   DevBuf lvl_of_d, slot_of_d, ucell, W, err, stepctr;
   std::vector<Route> ghosts, fluxes;
+  MapBatch gb;
   std::vector<int> order;    // levels by decreasing velocity count
 };
 
@@ -411,22 +422,24 @@ template <class S, class T, int D> struct Runner {
   // (state per thread, velocity sums per warp, correction per thread)
   static void launch_finalize(mlvs_handle* h, PointArgs a, LevelRt& L) {
     // chunk sums first (many threads), then the finalisation reads them
-    if (L.msum.p && a.npt > 0) {
+    if (a.nwork <= 0) return;
+    if (L.msum.p) {
       ++h->launches;
-      const long nt = (long)NMOM * a.npt;
-      k_sum_chunks<<<(unsigned)((nt + 255) / 256), 256, 0, h->stream>>>(a.part, a.k.nchunk, a.npt, L.msum.as<double>());
+      const long nt = (long)NMOM * a.nwork;
+      k_sum_chunks<<<(unsigned)((nt + 255) / 256), 256, 0, h->stream>>>(a.part, a.k.nchunk, a.npt, a.pts, a.nwork,
+                                                                         L.msum.as<double>());
       a.msum = L.msum.as<double>();
     }
     if (a.k.nax > 0) {
-      k_finalize<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+      k_finalize<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
       return;
     }
     a.scr = L.fscr.as<double>();
     a.need = L.fneed.as<int>();
     h->launches += 2;
-    k_fin_pre<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
-    k_fin_sums<T, D><<<std::max(1, (a.npt * 32 + 127) / 128), 128, 0, h->stream>>>(a);
-    k_fin_post<T, D><<<fin_grid(a.npt), FIN_BLOCK, 0, h->stream>>>(a);
+    k_fin_pre<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
+    k_fin_sums<T, D><<<std::max(1, (a.nwork * 32 + 127) / 128), 128, 0, h->stream>>>(a);
+    k_fin_post<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
   }
 
   static cudaError_t set_smem_limits() {
@@ -492,6 +505,8 @@ template <class S, class T, int D> struct Runner {
     a.gas = h->gas;
     a.is_face = face ? 1 : 0;
     a.npt = face ? L.k.nface : (int)L.cells.size();
+    a.pts = (face && L.nflist < L.k.nface) ? L.flist.as<int>() : nullptr;
+    a.nwork = face ? L.nflist : a.npt;
     a.part = face ? L.fpart.as<double>() : L.cpart.as<double>();
     const SpaceRt& sp = h->spaces[L.space];
     a.vt = sp.vt.p;
@@ -586,7 +601,101 @@ template <class S, class T, int D> struct Runner {
 
   static int map_grid(int n) { return std::max(1, std::min(n, 148 * 8)); }
 
+  // mapping launch with the items-per-CTA choice of the route size
+  template <class SrcT, class DstT, int KIND>
+  static void launch_map(mlvs_handle* h, const MapArgs& m) {
+    const int g = map_items_per_cta(m.nitems);
+    const int nb = map_grid((m.nitems + g - 1) / g);
+    ++h->launches;
+    switch (g) {
+      case 8: k_map<SrcT, DstT, T, D, KIND, 8><<<nb, 256, 0, h->stream>>>(m); break;
+      case 4: k_map<SrcT, DstT, T, D, KIND, 4><<<nb, 256, 0, h->stream>>>(m); break;
+      case 2: k_map<SrcT, DstT, T, D, KIND, 2><<<nb, 256, 0, h->stream>>>(m); break;
+      default: k_map<SrcT, DstT, T, D, KIND, 1><<<nb, 256, 0, h->stream>>>(m); break;
+    }
+  }
+
+  // route arguments and item groups of the batched ghost launch (after the routes' items are
+  // on the device)
+  static cudaError_t ghost_batch(mlvs_handle* h, Inst& I) {
+    MapBatch& B = I.gb;
+    B.ok = false;
+    B.nwork = 0;
+    std::vector<int> rs;
+    for (int r = 0; r < (int)I.ghosts.size(); ++r)
+      if (!I.ghosts[r].items.empty()) rs.push_back(r);
+    if (rs.empty()) return cudaSuccess;
+    auto groups = [&](int g) {
+      long n = 0;
+      for (int r : rs) n += ((long)I.ghosts[r].items.size() + g - 1) / g;
+      return n;
+    };
+    int G = 1;
+    for (int g : {8, 4, 2})
+      if (groups(g) >= 148 * 4) { G = g; break; }
+    std::vector<MapWork> work;
+    for (int q = 0; q < (int)rs.size(); ++q) {
+      const int n = (int)I.ghosts[rs[q]].items.size();
+      for (int b = 0; b < n; b += G) work.push_back({q, b, std::min(G, n - b)});
+    }
+    for (int par = 0; par < 4; ++par) {
+      std::vector<MapArgs> tab;
+      for (int r : rs) {
+        Route& rt = I.ghosts[r];
+        LevelRt& Ls = I.lv[rt.src];
+        LevelRt& Ld = I.lv[rt.dst];
+        CSR* c = nullptr;
+        if (get_csr(h, Ls.space, Ld.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
+        MapArgs m = margs(h, Ls.space, Ld.space, c);
+        m.src = Ls.f[par >> 1].p;
+        m.src_ld = (int)Ls.cells.size();
+        m.dst = Ld.ghost.p;
+        m.dst_ld = Ld.nghost;
+        m.prm = Ls.prm[par & 1].p;
+        m.prm_ld = (int)Ls.cells.size();
+        m.items = rt.items_d.as<MapItem>();
+        m.nitems = (int)rt.items.size();
+        tab.push_back(m);
+      }
+      cudaError_t e = upload(B.routes[par], tab, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = upload(B.work, work, h->stream);
+    if (e != cudaSuccess) return e;
+    B.nwork = (int)work.size();
+    B.G = G;
+    B.ok = true;
+    return cudaSuccess;
+  }
+
   static cudaError_t run_ghosts(mlvs_handle* h, Inst& I) {
+    // one launch for every route when all source levels are on the same buffer parity
+    if (I.gb.ok) {
+      int par = -1;
+      bool same = true;
+      for (auto& r : I.ghosts) {
+        if (r.items.empty()) continue;
+        const LevelRt& Ls = I.lv[r.src];
+        const int p = 2 * Ls.cur + Ls.pcur;
+        if (par < 0) par = p;
+        else if (p != par) same = false;
+      }
+      if (same && par >= 0) {
+        const MapArgs* rt = I.gb.routes[par].as<MapArgs>();
+        const MapWork* wk = I.gb.work.as<MapWork>();
+        const int nb = std::max(1, std::min(I.gb.nwork, 148 * 16));
+        mark_begin(h, 4);
+        ++h->launches;
+        switch (I.gb.G) {
+          case 8: k_map_multi<S, T, T, D, SRC_BARP, 8><<<nb, 256, 0, h->stream>>>(rt, wk, I.gb.nwork); break;
+          case 4: k_map_multi<S, T, T, D, SRC_BARP, 4><<<nb, 256, 0, h->stream>>>(rt, wk, I.gb.nwork); break;
+          case 2: k_map_multi<S, T, T, D, SRC_BARP, 2><<<nb, 256, 0, h->stream>>>(rt, wk, I.gb.nwork); break;
+          default: k_map_multi<S, T, T, D, SRC_BARP, 1><<<nb, 256, 0, h->stream>>>(rt, wk, I.gb.nwork); break;
+        }
+        mark_end(h);
+        return cudaGetLastError();
+      }
+    }
     for (auto& r : I.ghosts) {
       if (r.items.empty()) continue;
       LevelRt& Ls = I.lv[r.src];
@@ -603,7 +712,7 @@ template <class S, class T, int D> struct Runner {
       m.items = r.items_d.as<MapItem>();
       m.nitems = (int)r.items.size();
       mark_begin(h, 4);
-      k_map<S, T, T, D, SRC_BARP><<<map_grid(m.nitems), 256, 0, h->stream>>>(m);
+      launch_map<S, T, SRC_BARP>(h, m);
       mark_end(h);
     }
     return cudaGetLastError();
@@ -626,7 +735,7 @@ template <class S, class T, int D> struct Runner {
       m.items = r.items_d.as<MapItem>();
       m.nitems = (int)r.items.size();
       mark_begin(h, 5);
-      k_map<T, T, T, D, SRC_FLUX><<<map_grid(m.nitems), 256, 0, h->stream>>>(m);
+      launch_map<T, T, SRC_FLUX>(h, m);
       mark_end(h);
     }
     return cudaGetLastError();
@@ -749,7 +858,7 @@ template <class S, class T, int D> struct Runner {
         m.prm_ld = 0;
         m.items = items.as<MapItem>();
         m.nitems = ni;
-        k_map<S, S, T, D, SRC_TILDE><<<map_grid(ni), 256, 0, h->stream>>>(m);
+        launch_map<S, S, SRC_TILDE>(h, m);
       }
       e = cudaStreamSynchronize(h->stream);   // items freed at scope end
       if (e != cudaSuccess) return e;
@@ -846,12 +955,13 @@ struct Ops {
   cudaError_t (*moments_of_levels)(mlvs_handle*, Inst&);
   cudaError_t (*criterion)(mlvs_handle*, Inst&, const mlvs_adapt_params&, unsigned char*, const std::vector<int>*);
   cudaError_t (*wall_table)(mlvs_handle*, LevelRt&);
+  cudaError_t (*ghost_batch)(mlvs_handle*, Inst&);
 };
 
 template <class S, class T, int D> Ops make_ops() {
   using R = Runner<S, T, D>;
   return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion,
-             &R::wall_table};
+             &R::wall_table, &R::ghost_batch};
 }
 
 Ops ops_for(int storage, int D) {
@@ -1060,6 +1170,13 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     CK(upload(L.tiles, tl, h->stream));
     CK(upload(L.ids, L.cells, h->stream));
     CK(upload(L.frole, role[l], h->stream));
+    {
+      std::vector<int> fl;
+      for (int f = 0; f < nface; ++f)
+        if (role[l][f] == FR_NORMAL || role[l][f] == FR_CROSS) fl.push_back(f);
+      L.nflist = (int)fl.size();
+      if (L.nflist < nface && L.nflist > 0) CK(upload(L.flist, fl, h->stream));
+    }
     CK(upload(L.fslot, slot[l], h->stream));
     CK(upload(L.ghost_of, ghost_col[l], h->stream));
     const size_t nc = L.cells.size();
@@ -1086,6 +1203,7 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
   }
   for (auto& r : I.ghosts) CK(upload(r.items_d, r.items, h->stream));
   for (auto& r : I.fluxes) CK(upload(r.items_d, r.items, h->stream));
+  CK(ops_for(h->cfg.storage, D).ghost_batch(h, I));
   I.order.resize(nlev);
   for (int l = 0; l < nlev; ++l) I.order[l] = l;
   std::stable_sort(I.order.begin(), I.order.end(), [&](int a, int b) {
