@@ -273,6 +273,53 @@ def _selector_leg():
             "workload": "periodic random states, 64^2 cells, base 41^2, four radial levels"}
 
 
+def _cylinder_leg(storage="f32", warm_steps=1000, taus=(1.0, 0.07, 0.05, 0.04, 0.035), run_steps=400):
+    """Ma 5 flow past a cylinder (O-grid 256 x 128, Kn 0.1, base 201^2 on [-15, 15]^2): UVS and
+    MLVS advanced from the same start; after `warm_steps` (the impulsive start's near-vacuum
+    wake has filled) MLVS adapts with each clustering threshold in turn (C_split 0.01, C_merge
+    0.005, up to four depths) and is timed for 50 steps; then, with tau 0.05 and re-adaptation
+    every 100 steps, both run `run_steps` more and their fields are compared."""
+    import numpy as np
+    from paper_2609_35258_b300 import mlvs as M, workloads
+    from paper_2609_35258_b300.solver import Solver
+    nt, nr = 256, 128
+    d = workloads.cylinder(nt, nr, storage=storage)
+    u = Solver(d)
+    M.mlvs_set_graph(u.h, True)
+    s = Solver(d, adaptive=1)
+    M.mlvs_set_graph(s.h, True)
+    u.step(warm_steps)
+    s.step(warm_steps)
+    st = u.step(50)
+    uvs_ms = st.ms_total / 50
+    nv = st.cell_velocity_updates / 50 / (nt * nr)
+    sweep = []
+    for tau in taus:
+        a = M.mlvs_adapt(s.h, M.adapt_params(0.01, 0.005, 0.0, tau, 3))
+        s.step(2)
+        sm = s.step(50)
+        sweep.append({"tau_clust": tau, "spaces": a.n_levels, "distinct_masks": a.n_distinct,
+                      "mean_points_per_cell": a.updates_per_step / (nt * nr), "ms_per_step": sm.ms_total / 50,
+                      "speedup_vs_uvs": uvs_ms / (sm.ms_total / 50), "adapt_ms": a.ms_total})
+    u.step(52 * len(taus))
+    p = M.adapt_params(0.01, 0.005, 0.0, 0.05, 3)
+    M.mlvs_adapt(s.h, p)
+    M.mlvs_set_adaptation(s.h, p, 100)
+    sm = s.step(run_steps)
+    su = u.step(run_steps)
+    F = M.RHO | M.U | M.V | M.T | M.QX | M.QY
+    mu, ms = u.moments(F), s.moments(F)
+    u.close()
+    s.close()
+    return {"workload": f"cylinder O-grid {nt}x{nr}, Ma 5, Kn 0.1, base 201^2 on [-15,15]^2, {storage}",
+            "uvs_ms_per_step": uvs_ms, "uvs_points_per_cell": nv, "adapt_from_step": warm_steps,
+            "tau_sweep": sweep,
+            "run": {"tau_clust": 0.05, "adapt_interval": 100, "steps": run_steps,
+                    "mlvs_ms_per_step": sm.ms_total / run_steps, "uvs_ms_per_step": su.ms_total / run_steps,
+                    "rel_l2_vs_uvs": {"rho": _l2(ms[0], mu[0]), "u": _l2(np.hypot(ms[1], ms[2]), np.hypot(mu[1], mu[2])),
+                                      "T": _l2(ms[3], mu[3]), "q": _l2(np.hypot(ms[4], ms[5]), np.hypot(mu[4], mu[5]))}}}
+
+
 def _l2(a, b):
     import numpy as np
     return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
@@ -384,6 +431,7 @@ def run_ours(args, rank, world, local_rank):
     selector = None
     if not args.no_selector and rank == 0:
         selector = _selector_leg()
+    cylinder = _cylinder_leg() if (args.cylinder and rank == 0) else None
 
     # end-to-end through the public API: host init upload, steps, host moment reads
     e2e = None
@@ -424,7 +472,7 @@ def run_ours(args, rank, world, local_rank):
                          "peak_kind": f"{peak_kind} hbm_gbs", "traffic": traffic,
                          "algorithmic_bytes_per_update": algo_per_update},
             "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, phases)},
-            "mlvs": mlvs, "time_to_steady": steady, "selector": selector,
+            "mlvs": mlvs, "time_to_steady": steady, "selector": selector, "cylinder": cylinder,
             "clocks": clocks, "e2e": e2e, "gpu_launches": st.launches, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -443,6 +491,8 @@ def main():
     ap.add_argument("--no-steady", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
     ap.add_argument("--cells", type=int, default=64, help="cavity cells per side (default 64)")
+    ap.add_argument("--cylinder", action="store_true",
+                    help="add the Ma 5 cylinder leg (UVS vs MLVS over clustering thresholds, ~3 min)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
