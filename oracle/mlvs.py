@@ -19,7 +19,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import dugks, kinetic, mapping, vspace
-from .dugks import PERIODIC, WALL
+from .dugks import FREE, PERIODIC, WALL
 
 
 class SpaceBook:
@@ -147,7 +147,10 @@ def step(st: MLVSState):
         return dugks._limited(a, b, hh, opt.limiter)
 
     def face(dir_, jL, iL, jR, iR, wall_side=None):
-        """Flux (F^g, F^h) on V_f and V_f for the face between cells L and R (normal +x or +y)."""
+        """Flux (F^g, F^h) on V_f and V_f for the face between cells L and R (normal +x or +y).
+        wall_side = (side, inward normal sign) on a boundary face: a diffuse wall, or a freestream
+        side (the freestream Maxwellian, corrected like the face models, for velocities entering
+        the domain; the reconstructed phi-bar for those leaving), as in the uniform step."""
         cL = _cell_index(mesh, jL, iL)
         cR = _cell_index(mesh, jR, iR)
         key = book.refine(st.sp[cL], st.sp[cR])
@@ -186,6 +189,17 @@ def step(st: MLVSState):
             gf, hf = dugks._face_model_phi(bars[0], bars[1], xi, S.w, gas, s, opt.compat_face)
             m = kinetic.moments(bars[0], bars[1], xi, S.w, gas)
             Tb = m["T"]
+        elif mesh.bc[wall_side[0]] == FREE:
+            side, inward = wall_side
+            rho_f, ux_f, uy_f, T_f = mesh.far
+            vel = np.array([ux_f, uy_f])[:D]
+            gw, hw = kinetic.maxwell_gh(np.array(rho_f), vel, np.array(T_f), xi, gas)
+            if opt.compat_face:
+                gw, hw = kinetic.compat_correct4(gw, hw, np.array(rho_f), vel, np.array(T_f), xi, S.w, gas)
+            xn = inward * nrm
+            gf = np.where(xn > 0, gw, bars[0])
+            hf = np.where(xn > 0, hw, bars[1])
+            Tb = T_f
         else:
             side, inward = wall_side
             uw, vw, Tw = mesh.wall[side]
@@ -215,9 +229,9 @@ def step(st: MLVSState):
     for j in range(ny):
         for i in range(nfx):
             wall = None
-            if mesh.bc[0] == WALL and i == 0:
+            if mesh.bc[0] in (WALL, FREE) and i == 0:
                 wall = (0, +1.0)
-            if mesh.bc[1] == WALL and i == nx:
+            if mesh.bc[1] in (WALL, FREE) and i == nx:
                 wall = (1, -1.0)
             Fg, Fh, key, Tb = face(0, j, i - 1, j, i, wall)
             per = mesh.bc[0] == PERIODIC
@@ -236,9 +250,9 @@ def step(st: MLVSState):
         for j in range(nfy):
             for i in range(nx):
                 wall = None
-                if mesh.bc[2] == WALL and j == 0:
+                if mesh.bc[2] in (WALL, FREE) and j == 0:
                     wall = (2, +1.0)
-                if mesh.bc[3] == WALL and j == ny:
+                if mesh.bc[3] in (WALL, FREE) and j == ny:
                     wall = (3, -1.0)
                 Fg, Fh, key, Tb = face(1, j - 1, i, j, i, wall)
                 per = mesh.bc[2] == PERIODIC

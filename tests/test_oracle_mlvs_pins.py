@@ -204,6 +204,39 @@ def test_single_level_mlvs_equals_uvs_walls():
     np.testing.assert_allclose(np.stack(st.g), g.reshape(25, -1), rtol=1e-12, atol=1e-15)
 
 
+@pytest.mark.parametrize("walls", [False, True])
+def test_single_level_mlvs_equals_uvs_freestream(walls):
+    """Freestream sides (and diffuse walls): the multi-level step on one space is the uniform
+    step, whose freestream faces are pinned by the fixed-point and mirror tests."""
+    desc = workloads.supersonic_channel(6, 4, mach=1.5, n_base=13, umax=6.0, walls=walls)
+    o, st = _mlvs_from_desc(desc, [0] * 24, [0])
+    for _ in range(2):
+        mlvs.step(st)
+    g, h = oracle_run(o, 2)
+    np.testing.assert_allclose(np.stack(st.g), g.reshape(24, -1), rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(np.stack(st.h), h.reshape(24, -1), rtol=1e-12, atol=1e-15)
+
+
+def test_two_level_freestream_box_stays_mirror_symmetric():
+    """A gas at rest between two freestream sides at rest, with a centred bump and the outer
+    columns on the coarser space: the solution stays symmetric under x -> -x, so both sides'
+    inward normals and the cross-level faces on either side are consistent."""
+    nx, ny = 8, 4
+    desc = workloads.supersonic_channel(nx, ny, mach=0.0, n_base=13, umax=5.0, walls=True)
+    lev = [1 if (c % nx) in (0, 1, nx - 2, nx - 1) else 0 for c in range(nx * ny)]
+    o, st = _mlvs_from_desc(desc, lev, [0, 1])
+    for _ in range(3):
+        mlvs.step(st)
+    m = st.moments()
+    rho = np.array([x["rho"] for x in m]).reshape(ny, nx)
+    ux = np.array([x["u"][0] for x in m]).reshape(ny, nx)
+    T = np.array([x["T"] for x in m]).reshape(ny, nx)
+    np.testing.assert_allclose(rho[:, ::-1], rho, rtol=1e-12)
+    np.testing.assert_allclose(ux[:, ::-1], -ux, atol=1e-12)
+    np.testing.assert_allclose(T[:, ::-1], T, rtol=1e-12)
+    assert np.max(np.abs(ux)) > 1e-4                     # the bump spreads outwards
+
+
 def test_two_level_conservation_and_flux_matching():
     """Mixed levels on a periodic density wave: cross-level faces conserve exactly (Sec. 3.4)."""
     desc = workloads.periodic_random(8, 4, n_base=17, umax=5.0)
