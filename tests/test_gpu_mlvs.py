@@ -3,7 +3,8 @@
 Cells are put on different velocity spaces with mlvs_set_cell_levels; the oracle's
 mlvs.MLVSState runs the same assignment.  Covered: two uniform levels (cross faces evaluated
 on the finer space), two kappa spaces whose common refinement is neither (a cell-less face
-space), walls next to level interfaces, and the level switch of cells (remap).
+space), walls next to level interfaces, freestream sides on either level, and the level switch
+of cells (remap).
 Tolerances as in test_gpu_parity: FP64 1e-10 relative, FP32 1e-5.
 """
 import numpy as np
@@ -114,6 +115,26 @@ def test_three_levels_cavity_walls():
     _compare_cells(s, st, 144, 1e-9)
     m = s.moments(M.RHO)
     assert abs(m[0].sum() - st.totals()[0]) < 1e-12 * 144
+
+
+def test_two_levels_freestream_channel():
+    """Freestream inflow on the fine space, freestream outflow on the coarse one, diffuse walls
+    across the level interface (Ma 1.5 channel, FP64)."""
+    desc = workloads.supersonic_channel(12, 6, mach=1.5, n_base=17, umax=6.0, storage="f64", walls=True)
+    n = 72
+    lev = np.array([0 if (c % 12) < 6 else 1 for c in range(n)], dtype=np.int32)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(L) for L in (0, 1)]
+    st = _oracle_state(desc, o, [keys[0]] * n, book)
+    for c in range(n):
+        omlvs.remap(st, c, keys[lev[c]])
+    s = Solver(desc, levels=(0, 1))
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    for _ in range(3):
+        omlvs.step(st)
+    s.step(3)
+    _compare_cells(s, st, n, 1e-9)
 
 
 def test_level_switch_conserves_and_matches():
