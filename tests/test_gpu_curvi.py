@@ -7,6 +7,8 @@ C ABI, against the oracle's curvilinear step.
   (FP64 1e-10, FP32 1e-5) and the wall carries no net mass flux.
 * The cylinder configuration at full size (256 x 128 cells, 201^2 velocities) in FP32 and
   BF16: the flow stays mirror-symmetric about the x axis, and BF16 stays within 1e-3 of FP32.
+* Two velocity spaces on a small O-grid against the oracle's curvilinear multi-level step, and
+  adapted spaces on a closed annulus conserving mass.
 """
 import numpy as np
 import pytest
@@ -136,6 +138,34 @@ def test_selector_features_on_the_ogrid():
                              T_ref=1.0, mu_ref=o["gas"].mu_ref, omega=o["gas"].omega)
     assert np.max(np.abs(F - Fo) / np.maximum(1.0, np.abs(Fo))) < 1e-5
     assert np.max(Fo[:, 6]) > 1e-3            # gradients present
+
+
+def test_ogrid_two_spaces_match_oracle():
+    """Two spaces on a small O-grid (wall inside, freestream outside), cells switched from the
+    fine space as the library does, three steps against the oracle's curvilinear multi-level
+    step (FP64)."""
+    from oracle import mlvs as omlvs, mlvs_curvi
+    desc = workloads.cylinder(24, 8, mach=2.0, Kn=0.1, n_base=17, umax=8.0, r_out=4.0, storage="f64")
+    n = 24 * 8
+    lev = np.array([1 if 6 <= (c % 24) < 18 else 0 for c in range(n)], dtype=np.int32)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(L) for L in (0, 1)]
+    init = desc["init"]
+    st = omlvs.MLVSState.from_primitives(o["mesh"], o["gas"], book, [keys[0]] * n, init[..., 0],
+                                         init[..., 1:3], init[..., 3], o["dt"], o["opt"])
+    for c in range(n):
+        omlvs.remap(st, c, keys[lev[c]])
+    s = Solver(desc, levels=(0, 1))
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    for _ in range(3):
+        mlvs_curvi.step(st)
+    s.step(3)
+    for c in range(n):
+        g, _ = s.read_cells(c, 1, 10000)
+        gref = st.g[c]
+        np.testing.assert_allclose(g[0], gref, rtol=0, atol=1e-9 * np.max(np.abs(gref)))
+    s.close()
 
 
 def test_multilevel_spaces_on_a_closed_annulus_conserve():
