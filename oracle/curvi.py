@@ -142,7 +142,7 @@ def step(gt, ht, mesh: CurviMesh, xi, w, gas: Gas, dt: float, opt: Options = Opt
     ny, nx, nv = gt.shape
     G = geometry(mesh)
     st = cell_state(gt, ht, xi, w, gas, dt)
-    gS, hS = model_at(st, xi, w, gas, dt, opt.compat_cell)
+    gS, hS = model_at(st, xi, w, gas, dt, opt.compat_cell, opt.compat_moments)
     tau = st["tau"][..., None]
     gbp, hbp = bar_plus(gt, gS, tau, dt), bar_plus(ht, hS, tau, dt)
     gtp, htp = tilde_plus(gbp, gt), tilde_plus(hbp, ht)
@@ -185,7 +185,7 @@ def step(gt, ht, mesh: CurviMesh, xi, w, gas: Gas, dt: float, opt: Options = Opt
         for k in range(2):
             vL, vR = recon(k, jL, iL, xb), recon(k, jR, iR, xb)
             bars.append(np.where(xn > 0, vL, np.where(xn < 0, vR, 0.5 * (vL + vR))))
-        out = list(_face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face))
+        out = list(_face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face, opt.compat_moments))
         for idx, side, inward in sides:
             xin = inward * xn[idx]
             n = xin.shape[0]

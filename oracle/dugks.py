@@ -40,7 +40,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .kinetic import Gas, compat_correct4, moments, shakhov_gh, maxwell_gh, viscosity
+from .kinetic import Gas, compat_correct4, compat_correct8, moments, shakhov_gh, maxwell_gh, viscosity
 
 PERIODIC, ZEROGRAD, WALL, FREE = "periodic", "zerograd", "wall", "freestream"
 
@@ -65,6 +65,7 @@ class Options:
     compat_cell: bool = True
     compat_face: bool = True
     limiter: str = "vanleer"      # or "none" (central slope) for smooth tests
+    compat_moments: int = 4       # 4: collision invariants; 8: also heat flux and deviatoric stress (D = 2)
 
 
 def time_step(mesh: Mesh, xi: np.ndarray, cfl: float, D: int) -> float:
@@ -89,10 +90,15 @@ def recover(phib, phiS, tau, s):
     return 2.0 * tau / (2.0 * tau + s) * phib + s / (2.0 * tau + s) * phiS
 
 
-def model_at(W, xi, w, gas: Gas, dt_or_s: float, compat: bool):
-    """Model distribution at points with state W = dict(rho, u, T, q) (Eq. g_h_eq_Pr + Sec. 3.3.1)."""
+def model_at(W, xi, w, gas: Gas, dt_or_s: float, compat: bool, nmom: int = 4):
+    """Model distribution at points with state W = dict(rho, u, T, q) (Eq. g_h_eq_Pr + Sec. 3.3.1).
+    nmom = 8: the eight-moment correction, whose heat-flux target is the Shakhov model's own
+    heat flux (1 - Pr) q (Eq. g_h_eq_Pr)."""
     gS, hS = shakhov_gh(W["rho"], W["u"], W["T"], W["q"], xi, gas)
-    if compat:
+    if compat and nmom == 8:
+        q_tar = (1.0 - gas.Pr) * np.asarray(W["q"])
+        gS, hS = compat_correct8(gS, hS, W["rho"], W["u"], W["T"], q_tar, xi, w, gas)
+    elif compat:
         gS, hS = compat_correct4(gS, hS, W["rho"], W["u"], W["T"], xi, w, gas)
     return gS, hS
 
@@ -136,13 +142,13 @@ def _limited(a, b, h, limiter):
     return s / h
 
 
-def _face_model_phi(gb, hb, xi, w, gas: Gas, s: float, compat: bool):
+def _face_model_phi(gb, hb, xi, w, gas: Gas, s: float, compat: bool, nmom: int = 4):
     """Step 6 at a set of faces: face W, q, model distribution and Eq. recover_phi."""
     m = moments(gb, hb, xi, w, gas)
     tau = viscosity(m["T"], gas) / m["p"]
     q = (2.0 * tau / (2.0 * tau + s * gas.Pr))[..., None] * m["q"]
     W = {"rho": m["rho"], "u": m["u"], "T": m["T"], "q": q}
-    gS, hS = model_at(W, xi, w, gas, s, compat)
+    gS, hS = model_at(W, xi, w, gas, s, compat, nmom)
     t = tau[..., None]
     return recover(gb, gS, t, s), recover(hb, hS, t, s)
 
@@ -153,7 +159,7 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
     s = 0.5 * dt
     ny, nx, nv = gt.shape
     st = cell_state(gt, ht, xi, w, gas, dt)
-    gS, hS = model_at(st, xi, w, gas, dt, opt.compat_cell)
+    gS, hS = model_at(st, xi, w, gas, dt, opt.compat_cell, opt.compat_moments)
     tau = st["tau"][..., None]
     gbp = bar_plus(gt, gS, tau, dt)
     hbp = bar_plus(ht, hS, tau, dt)
@@ -209,7 +215,7 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
             neg = xi[:, 0] < 0
             bar = np.where(pos, vL, np.where(neg, vR, 0.5 * (vL + vR)))
             bars.append(bar)
-        phig, phih = _face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face)
+        phig, phih = _face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face, opt.compat_moments)
         out = [phig, phih]
         # freestream and walls on the x sides
         for side, idx, inward in ((0, 0, +1.0), (1, nfx - 1, -1.0)):
@@ -248,7 +254,7 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
             pos = xi[:, 1] > 0
             neg = xi[:, 1] < 0
             bars.append(np.where(pos, vS, np.where(neg, vN, 0.5 * (vS + vN))))
-        phig, phih = _face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face)
+        phig, phih = _face_model_phi(bars[0], bars[1], xi, w, gas, s, opt.compat_face, opt.compat_moments)
         out = [phig, phih]
         for side, idx, inward in ((2, 0, +1.0), (3, nfy - 1, -1.0)):
             if mesh.bc[side] == FREE:

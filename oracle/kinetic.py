@@ -114,6 +114,60 @@ def moments(g, h, xi, w, gas: Gas):
             "q": q, "P": P}
 
 
+def compat_correct8(gS, hS, rho, u, T, q_tar, xi, w, gas: Gas):
+    """Eight-moment linear compatibility correction of the model distribution (Sec. 3.3.1,
+    D = 2 only).
+
+    Eq. gh_model_correction with chi^g = g^S, chi^h = h^S, basis Eq. eq_eight_basis
+    phi = [1, xi_x, xi_y, E_xi, E_c c_x, E_c c_y, c_x^2 - c_y^2, c_x c_y] with c = xi - u and
+    E_c = 1/2 [(3-D+K) R T + c^2] (Eq. E_c_definition), joint matrix
+    Eq. joint_gh_correction_matrix with the kernels of Eq. eq_eight_moment_constraint, and
+    targets (rho, rho u, rho v, rho E, q_x^tar, q_y^tar, 0, 0): the collision invariants, the
+    heat flux the model prescribes and a vanishing deviatoric stress.  One 8 x 8 system.
+    """
+    if gas.D != 2:
+        raise ValueError("the eight-moment correction is two-dimensional")
+    rho = np.asarray(rho, dtype=np.float64)
+    u = np.asarray(u, dtype=np.float64)
+    T = np.asarray(T, dtype=np.float64)
+    q_tar = np.asarray(q_tar, dtype=np.float64)
+    RT = gas.R * T
+    xi2 = np.sum(xi * xi, axis=-1)
+    cx = xi[:, 0] - u[..., 0:1]                 # (..., Nv)
+    cy = xi[:, 1] - u[..., 1:2]
+    c2 = cx * cx + cy * cy
+    Exi = 0.5 * (gas.c_extra * RT[..., None] + xi2)
+    Ec = 0.5 * (gas.c_extra * RT[..., None] + c2)
+    shp = gS.shape
+    phi = np.empty(shp[:-1] + (8, shp[-1]))
+    phi[..., 0, :] = 1.0
+    phi[..., 1, :] = xi[:, 0]
+    phi[..., 2, :] = xi[:, 1]
+    phi[..., 3, :] = Exi
+    phi[..., 4, :] = Ec * cx
+    phi[..., 5, :] = Ec * cy
+    phi[..., 6, :] = cx * cx - cy * cy
+    phi[..., 7, :] = cx * cy
+    # kernels psi^g chi^g + psi^h chi^h of the eight constrained moments
+    kern = np.empty_like(phi)
+    kern[..., 0, :] = gS
+    kern[..., 1, :] = xi[:, 0] * gS
+    kern[..., 2, :] = xi[:, 1] * gS
+    kern[..., 3, :] = 0.5 * (xi2 * gS + hS)
+    kern[..., 4, :] = 0.5 * (c2 * gS + hS) * cx
+    kern[..., 5, :] = 0.5 * (c2 * gS + hS) * cy
+    kern[..., 6, :] = (cx * cx - cy * cy) * gS
+    kern[..., 7, :] = cx * cy * gS
+    A = np.einsum("...kv,...mv->...km", kern * w, phi)
+    rhoE = rho * (0.5 * np.sum(u * u, axis=-1) + gas.cv * T)
+    zero = np.zeros_like(rho)[..., None]
+    tar = np.concatenate([rho[..., None], rho[..., None] * u, rhoE[..., None], q_tar, zero, zero], axis=-1)
+    cur = np.sum(kern * w, axis=-1)
+    a = np.linalg.solve(A, (tar - cur)[..., None])[..., 0]
+    corr = np.einsum("...m,...mv->...v", a, phi)
+    return gS + gS * corr, hS + hS * corr
+
+
 def conserved(g, h, xi, w):
     """The collision-invariant moments (rho, rho u, rho E) stacked on the last axis."""
     rho = np.sum(w * g, axis=-1)

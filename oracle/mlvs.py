@@ -120,7 +120,7 @@ def step(st: MLVSState):
     for c in range(ncell):
         S = book.space(st.sp[c])
         cs = dugks.cell_state(st.g[c], st.h[c], S.xi, S.w, gas, dt)
-        gS, hS = dugks.model_at(cs, S.xi, S.w, gas, dt, opt.compat_cell)
+        gS, hS = dugks.model_at(cs, S.xi, S.w, gas, dt, opt.compat_cell, opt.compat_moments)
         a = dugks.bar_plus(st.g[c], gS, cs["tau"], dt)
         b = dugks.bar_plus(st.h[c], hS, cs["tau"], dt)
         state.append(cs)
@@ -186,7 +186,7 @@ def step(st: MLVSState):
                 recR = recR - tang * s * stR
             bars.append(np.where(nrm > 0, recL, np.where(nrm < 0, recR, 0.5 * (recL + recR))))
         if wall_side is None:
-            gf, hf = dugks._face_model_phi(bars[0], bars[1], xi, S.w, gas, s, opt.compat_face)
+            gf, hf = dugks._face_model_phi(bars[0], bars[1], xi, S.w, gas, s, opt.compat_face, opt.compat_moments)
             m = kinetic.moments(bars[0], bars[1], xi, S.w, gas)
             Tb = m["T"]
         elif mesh.bc[wall_side[0]] == FREE:

@@ -38,7 +38,7 @@ def step(st: MLVSState):
     for c in range(nx * ny):
         S = book.space(st.sp[c])
         cs = dugks.cell_state(st.g[c], st.h[c], S.xi, S.w, gas, dt)
-        gS, hS = dugks.model_at(cs, S.xi, S.w, gas, dt, opt.compat_cell)
+        gS, hS = dugks.model_at(cs, S.xi, S.w, gas, dt, opt.compat_cell, opt.compat_moments)
         a = dugks.bar_plus(st.g[c], gS, cs["tau"], dt)
         b = dugks.bar_plus(st.h[c], hS, cs["tau"], dt)
         state.append(cs)
@@ -90,7 +90,7 @@ def step(st: MLVSState):
             vR = recon(jR, iR, key, xb, xi, k)
             bars.append(np.where(xn > 0, vL, np.where(xn < 0, vR, 0.5 * (vL + vR))))
         if bnd is None:
-            gf, hf = dugks._face_model_phi(bars[0], bars[1], xi, S.w, gas, s, opt.compat_face)
+            gf, hf = dugks._face_model_phi(bars[0], bars[1], xi, S.w, gas, s, opt.compat_face, opt.compat_moments)
             Tb = kinetic.moments(bars[0], bars[1], xi, S.w, gas)["T"]
         elif mesh.bc[bnd[0]] == FREE:
             side, inward = bnd

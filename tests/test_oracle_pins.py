@@ -125,6 +125,82 @@ def test_compat_correction_E1_state():
     assert eps(gc, hc) < 1e-14
 
 
+def _quadtree_E1_space():
+    base = vspace.make_base(33, -4.0, 4.0, D=2)
+    N1 = len(vspace.axis_groups(33, 1))
+    yy, xx = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
+    r = np.hypot(xx - N1 // 2, yy - N1 // 2)
+    kappa = np.where(r < 3, 0, np.where(r < 5, 1, 2)).astype(np.int64)
+    return vspace.kappa_space(base, kappa)
+
+
+def test_compat8_hits_heat_flux_and_isotropic_stress():
+    """Sec. 3.3.1, eight constraints: on the nonuniform grid of the E1 test, a Shakhov model
+    with a heat flux carries after the correction the conserved moments, the heat flux the
+    model prescribes ((1 - Pr) q, the Shakhov property pinned above) and a vanishing deviatoric
+    stress, measured with the moment routine (not the correction's own kernels)."""
+    sp = _quadtree_E1_space()
+    gas = kinetic.Gas(D=2, R=0.5, Pr=2.0 / 3.0)
+    rho, u, T, q = np.array(1.0), np.array([1.0, 0.2]), np.array(1.0), np.array([0.05, -0.03])
+    g, h = kinetic.shakhov_gh(rho, u, T, q, sp.xi, gas)
+    q_tar = (1.0 - gas.Pr) * q
+    gc, hc = kinetic.compat_correct8(g, h, rho, u, T, q_tar, sp.xi, sp.w, gas)
+    m0 = kinetic.moments(g, h, sp.xi, sp.w, gas)
+    m = kinetic.moments(gc, hc, sp.xi, sp.w, gas)
+    p = rho * gas.R * T
+    assert abs(m0["P"][0, 0] - m0["P"][1, 1]) > 1e-6 * p             # the uncorrected model is off
+    assert abs(m["rho"] - rho) < 1e-14
+    np.testing.assert_allclose(m["u"], u, atol=1e-14)
+    assert abs(m["T"] - T) < 1e-13
+    np.testing.assert_allclose(m["q"], q_tar, atol=1e-13)
+    assert abs(m["P"][0, 0] - m["P"][1, 1]) < 1e-13 * p
+    assert abs(m["P"][0, 1]) < 1e-13 * p
+
+
+def test_compat8_is_compat4_for_a_symmetric_state_and_idempotent():
+    """A gas at rest without heat flux on a grid symmetric in xi_x, xi_y and under their swap:
+    the four extra constraints already hold and decouple, so the eight-moment correction is
+    the four-moment one; a corrected model is left unchanged by a second correction."""
+    base = vspace.make_base(25, -5.0, 5.0, D=2)
+    for L in (0, 1):
+        sp = vspace.uniform_space(base, L)
+        gas = kinetic.Gas(D=2, R=1.0, Pr=2.0 / 3.0)
+        rho, u, T = np.array(1.3), np.array([0.0, 0.0]), np.array(0.9)
+        g, h = kinetic.maxwell_gh(rho, u, T, sp.xi, gas)
+        g4, h4 = kinetic.compat_correct4(g, h, rho, u, T, sp.xi, sp.w, gas)
+        g8, h8 = kinetic.compat_correct8(g, h, rho, u, T, np.zeros(2), sp.xi, sp.w, gas)
+        assert np.max(np.abs(g4 - g)) > 1e-12 * np.max(g)             # the correction does act
+        np.testing.assert_allclose(g8, g4, rtol=0, atol=1e-14 * np.max(g4))
+        np.testing.assert_allclose(h8, h4, rtol=0, atol=1e-14 * np.max(h4))
+    sp = _quadtree_E1_space()
+    gas = kinetic.Gas(D=2, R=0.5, Pr=2.0 / 3.0)
+    rho, u, T, q = np.array(1.0), np.array([1.0, 0.2]), np.array(1.0), np.array([0.05, -0.03])
+    g, h = kinetic.shakhov_gh(rho, u, T, q, sp.xi, gas)
+    args = (rho, u, T, (1.0 - gas.Pr) * q, sp.xi, sp.w, gas)
+    g1, h1 = kinetic.compat_correct8(g, h, *args)
+    g2, h2 = kinetic.compat_correct8(g1, h1, *args)
+    np.testing.assert_allclose(g2, g1, rtol=0, atol=1e-14 * np.max(g1))
+    np.testing.assert_allclose(h2, h1, rtol=0, atol=1e-14 * np.max(h1))
+
+
+def test_step_with_eight_moment_correction_conserves():
+    """The step with the eight-moment correction at cells and faces: the four collision
+    invariants are still among the constraints, so a periodic run conserves to round-off,
+    and the result differs from the four-moment step."""
+    desc = workloads.periodic_random(8, 6, n_base=25, amp=0.2)
+    o = oracle_setup(desc)
+    sp = o["sp"]
+    W0 = kinetic.conserved(o["g"], o["h"], sp.xi, sp.w).sum(axis=(0, 1))
+    opt8 = dugks.Options(compat_moments=8)
+    g, h = o["g"], o["h"]
+    for _ in range(10):
+        g, h, _ = dugks.step(g, h, o["mesh"], sp.xi, sp.w, o["gas"], o["dt"], opt8)
+    W1 = kinetic.conserved(g, h, sp.xi, sp.w).sum(axis=(0, 1))
+    assert np.max(np.abs(W1 - W0)) < 1e-12 * np.max(np.abs(W0))
+    g4, _ = oracle_run(o, 10)
+    assert np.max(np.abs(g - g4)) > 1e-10 * np.max(g4)
+
+
 # ---------------------------------------------------------------- DUGKS (Sec. 2.2)
 
 def test_transformed_distribution_algebra():
