@@ -66,6 +66,8 @@ class Options:
     compat_face: bool = True
     limiter: str = "vanleer"      # or "none" (central slope) for smooth tests
     compat_moments: int = 4       # 4: collision invariants; 8: also heat flux and deviatoric stress (D = 2)
+    map_moments: int = 4          # cross-level mapping: 4 (conserved moments) or 9 (raw second moments and
+                                  # energy fluxes too, D = 2), for stencil states, fluxes and level switches
 
 
 def time_step(mesh: Mesh, xi: np.ndarray, cfl: float, D: int) -> float:

@@ -135,6 +135,8 @@ def step(st: MLVSState):
         """phi-bar-plus of cell c on space key (Eq. interface_state_moment_matching)."""
         if st.sp[c] == key:
             return gbp[c], hbp[c]
+        if (c, key) not in cache and opt.map_moments == 9:
+            cache[(c, key)] = mapping.map9(gbp[c], hbp[c], book.space(st.sp[c]), book.space(key))
         if (c, key) not in cache:
             src, dst = book.space(st.sp[c]), book.space(key)
             m = kinetic.moments(gbp[c], hbp[c], src.xi, src.w, gas)
@@ -218,8 +220,10 @@ def step(st: MLVSState):
         if st.sp[c] == key:
             return Fg, Fh
         src, dst = book.space(key), book.space(st.sp[c])
-        tar = kinetic.conserved(Fg, Fh, src.xi, src.w)
         gp, hp = mapping.project(Fg, Fh, src, dst)
+        if opt.map_moments == 9:
+            return mapping.correct9(gp, hp, mapping.raw9(Fg, Fh, src), dst)
+        tar = kinetic.conserved(Fg, Fh, src.xi, src.w)
         return mapping.correct4(gp, hp, tar, Tb, dst, gas)
 
     new_g = [x.copy() for x in gtp]
@@ -271,9 +275,13 @@ def step(st: MLVSState):
 
 
 def remap(st: MLVSState, c, new_key):
-    """Level switch of cell c (Eq. level_switch_conservation, four-moment form)."""
+    """Level switch of cell c (Eq. level_switch_conservation; four-moment form, or the
+    nine-moment form when st.opt.map_moments is 9)."""
     if st.sp[c] == new_key:
         return
     src, dst = st.book.space(st.sp[c]), st.book.space(new_key)
-    st.g[c], st.h[c] = mapping.map4(st.g[c], st.h[c], src, dst, st.gas)
+    if st.opt.map_moments == 9:
+        st.g[c], st.h[c] = mapping.map9(st.g[c], st.h[c], src, dst)
+    else:
+        st.g[c], st.h[c] = mapping.map4(st.g[c], st.h[c], src, dst, st.gas)
     st.sp[c] = new_key

@@ -53,6 +53,8 @@ def step(st: MLVSState):
         """phi-bar-plus of cell c on space key (Eq. interface_state_moment_matching)."""
         if st.sp[c] == key:
             return gbp[c], hbp[c]
+        if (c, key) not in cache and opt.map_moments == 9:
+            cache[(c, key)] = mapping.map9(gbp[c], hbp[c], book.space(st.sp[c]), book.space(key))
         if (c, key) not in cache:
             src, dst = book.space(st.sp[c]), book.space(key)
             m = kinetic.moments(gbp[c], hbp[c], src.xi, src.w, gas)
@@ -120,8 +122,10 @@ def step(st: MLVSState):
         if st.sp[c] == key:
             return Fg, Fh
         src, dst = book.space(key), book.space(st.sp[c])
-        tar = kinetic.conserved(Fg, Fh, src.xi, src.w)
         gp, hp = mapping.project(Fg, Fh, src, dst)
+        if opt.map_moments == 9:
+            return mapping.correct9(gp, hp, mapping.raw9(Fg, Fh, src), dst)
+        tar = kinetic.conserved(Fg, Fh, src.xi, src.w)
         return mapping.correct4(gp, hp, tar, Tb, dst, gas)
 
     def bside(side, inward):

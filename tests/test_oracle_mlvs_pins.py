@@ -237,6 +237,48 @@ def test_two_level_freestream_box_stays_mirror_symmetric():
     assert np.max(np.abs(ux)) > 1e-4                     # the bump spreads outwards
 
 
+def _raw9_totals(st):
+    book = st.book
+    return sum(mapping.raw9(g, h, book.space(k)) for g, h, k in zip(st.g, st.h, st.sp))
+
+
+def test_nine_moment_flux_matching_conserves_raw_moments_without_collisions():
+    """Free-molecular limit (Kn 1e12), two spaces on a periodic mesh: transport alone conserves
+    the global sum of every velocity moment, so the nine raw moments (mass, momentum, energy,
+    Gxx, Gyy, Gxy, Jx, Jy) are conserved to round-off exactly when every cross-level flux keeps
+    all nine on both sides (Sec. 3.4, the nine-moment treatment); with the four-moment
+    treatment the second moments drift."""
+    desc = workloads.periodic_random(8, 4, n_base=17, umax=5.0, Kn=1e12)
+    lev = [0 if (c % 8) < 4 else 1 for c in range(32)]
+    drift = {}
+    for nm in (4, 9):
+        o, st = _mlvs_from_desc(desc, lev, [0, 1])
+        st.opt = dugks.Options(map_moments=nm)
+        R0 = _raw9_totals(st)
+        for _ in range(4):
+            mlvs.step(st)
+        R1 = _raw9_totals(st)
+        drift[nm] = np.abs(R1 - R0) / np.max(np.abs(R0))
+    assert np.max(drift[9]) < 1e-13
+    assert np.min(drift[4][4:]) > 1e-6                    # Gxx .. Jy are not matched by 4 moments
+    assert np.max(drift[4][:4]) < 1e-13                   # the conserved ones are
+
+
+def test_nine_moment_mapping_keeps_the_freestream_box_symmetric():
+    nx, ny = 8, 4
+    desc = workloads.supersonic_channel(nx, ny, mach=0.0, n_base=13, umax=5.0, walls=True)
+    lev = [1 if (c % nx) in (0, 1, nx - 2, nx - 1) else 0 for c in range(nx * ny)]
+    o, st = _mlvs_from_desc(desc, lev, [0, 1])
+    st.opt = dugks.Options(map_moments=9)
+    for _ in range(3):
+        mlvs.step(st)
+    m = st.moments()
+    rho = np.array([x["rho"] for x in m]).reshape(ny, nx)
+    ux = np.array([x["u"][0] for x in m]).reshape(ny, nx)
+    np.testing.assert_allclose(rho[:, ::-1], rho, rtol=1e-12)
+    np.testing.assert_allclose(ux[:, ::-1], -ux, atol=1e-12)
+
+
 def test_two_level_conservation_and_flux_matching():
     """Mixed levels on a periodic density wave: cross-level faces conserve exactly (Sec. 3.4)."""
     desc = workloads.periodic_random(8, 4, n_base=17, umax=5.0)
