@@ -12,7 +12,9 @@ Sec. 3.3.2:
  * nine-moment block-triangular correction: g-block with basis Eq. raw_six_g_basis and
    targets (rho, rho u, rho v, G_xx, G_yy, G_xy) (Eq. source_second_raw_moments), then the
    h-block with basis Eq. raw_three_h_basis solving Eq. mapping_h_residual_correction for
-   (rho E, J_x, J_y) (Eq. source_energy_flux_moments).
+   (rho E, J_x, J_y) (Eq. source_energy_flux_moments);
+ * the exponential correction proposed as a positivity-preserving fallback
+   (Eq. exponential_moment_correction), four constraints, by Newton iteration.
 
 Both spaces are partitions of the same base grid (vspace.Space), so every target cell either
 lies inside one source cell (refinement) or is a union of source cells (coarsening).
@@ -105,6 +107,46 @@ def map4(g, h, src, dst, gas: Gas, M_tar=None, T_tar=None):
         M_tar = _conserved_targets(m["rho"], m["u"], m["T"], gas)
         T_tar = m["T"]
     return correct4(gp, hp, M_tar, T_tar, dst, gas)
+
+
+def correct_exp4(gp, hp, M_tar, space, tol=1e-14, maxit=60):
+    """Exponential moment-constrained correction (Eq. exponential_moment_correction), the
+    positivity-preserving alternative to the additive correction that Sec. 3.3.2 proposes:
+    phi* = phi^p exp(a . psi) with one factor for g and h, psi = [1, xi_x, xi_y, xi^2 / 2]
+    (2-D), and a solving the four constraints (rho, rho u, rho v, rho E) of Eq.
+    mapping_four_targets.  Damped Newton iteration from a = 0 (halving the step until the
+    residual norm decreases).  gp, hp of shape (Nv,); raises if it does not converge.
+    """
+    xi = space.xi
+    w = space.w
+    x, y = xi[:, 0], xi[:, 1]
+    xi2 = x * x + y * y
+    basis = np.stack([np.ones_like(x), x, y, 0.5 * xi2])                 # 4 x Nv
+    kern = np.stack([gp, x * gp, y * gp, 0.5 * (xi2 * gp + hp)])         # 4 x Nv, before the factor
+    M_tar = np.asarray(M_tar, dtype=np.float64)
+    scale = np.maximum(np.abs(M_tar), np.max(np.abs(M_tar)) * 1e-3)
+
+    def residual(a):
+        e = np.exp(a @ basis)
+        return (kern * e) @ w - M_tar, e
+
+    a = np.zeros(4)
+    r, e = residual(a)
+    for _ in range(maxit):
+        if np.max(np.abs(r) / scale) < tol:
+            return gp * e, hp * e
+        J = (kern * e * w) @ basis.T
+        da = np.linalg.solve(J, -r)
+        t = 1.0
+        while True:
+            r1, e1 = residual(a + t * da)
+            if np.linalg.norm(r1 / scale) < np.linalg.norm(r / scale) or t < 1e-8:
+                break
+            t *= 0.5
+        a, r, e = a + t * da, r1, e1
+    if np.max(np.abs(r) / scale) < tol:
+        return gp * e, hp * e
+    raise RuntimeError("exponential correction did not converge")
 
 
 def forced_conservation(gp, hp, g_src, h_src, src, dst, gas: Gas):

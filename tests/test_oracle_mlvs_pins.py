@@ -237,6 +237,49 @@ def test_two_level_freestream_box_stays_mirror_symmetric():
     assert np.max(np.abs(ux)) > 1e-4                     # the bump spreads outwards
 
 
+def _cold_beam_on_coarse_space():
+    """A narrow Maxwellian on the fine grid projected to level 2: the projection leaves
+    moment defects that a correction must remove."""
+    base = vspace.make_base(33, -6.0, 6.0, D=2)
+    src, dst = vspace.uniform_space(base, 0), vspace.uniform_space(base, 2)
+    gas = kinetic.Gas(D=2, R=1.0)
+    g, h = kinetic.maxwell_gh(np.array(1.0), np.array([1.7, -0.4]), np.array(0.15), src.xi, gas)
+    tar = kinetic.conserved(g, h, src.xi, src.w)
+    gp, hp = mapping.project(g, h, src, dst)
+    return gp, hp, tar, dst, gas
+
+
+def test_exponential_correction_meets_targets_and_keeps_signs():
+    """Eq. exponential_moment_correction: the corrected values meet the four targets, keep the
+    sign of every provisional value (the factor is positive; a nonnegative g stays nonnegative)
+    and leave zeros at zero, where the additive unit-weight correction of the same defect makes
+    tails negative."""
+    gp, hp, tar, dst, gas = _cold_beam_on_coarse_space()
+    gp = np.where(gp < 1e-300, 0.0, gp)
+    defect = np.abs(kinetic.conserved(gp, hp, dst.xi, dst.w) - tar) / np.abs(tar).max()
+    assert defect.max() > 1e-4                                       # a real defect
+    m = kinetic.moments(gp, hp, dst.xi, dst.w, gas)
+    gl, hl = mapping.correct4(gp, hp, tar, m["T"], dst, gas)
+    assert gl.min() < 0.0                                            # the additive correction goes negative
+    ge, he = mapping.correct_exp4(gp, hp, tar, dst)
+    M = kinetic.conserved(ge, he, dst.xi, dst.w)
+    np.testing.assert_allclose(M, tar, rtol=1e-13, atol=1e-13 * np.abs(tar).max())
+    assert gp.min() >= 0.0 and ge.min() >= 0.0                      # aggregation keeps g >= 0, and so does the factor
+    assert np.all(ge[gp == 0.0] == 0.0)
+    assert np.all(np.sign(ge) == np.sign(gp))
+    assert np.all(np.sign(he) == np.sign(hp))                        # h = H - xi^2 g may be slightly negative after projection
+
+
+def test_exponential_correction_without_defect_is_the_identity():
+    base = vspace.make_base(17, -5.0, 5.0, D=2)
+    sp = vspace.uniform_space(base, 1)
+    g, h = _rand_gh(sp, seed=3)
+    tar = kinetic.conserved(g, h, sp.xi, sp.w)
+    ge, he = mapping.correct_exp4(g, h, tar, sp)
+    np.testing.assert_allclose(ge, g, rtol=1e-13)
+    np.testing.assert_allclose(he, h, rtol=1e-13)
+
+
 def _raw9_totals(st):
     book = st.book
     return sum(mapping.raw9(g, h, book.space(k)) for g, h, k in zip(st.g, st.h, st.sp))
