@@ -1,8 +1,9 @@
 """Seeded synthetic workloads shaped like the paper's benchmarks.
 
 Each function returns a plain description: mesh, boundary kinds, gas constants, velocity
-grid and the initial primitive fields (rho, u, v, T) per cell.  Nothing here evaluates the
-kinetic method; the same description feeds the CUDA library and the test-side oracle.
+grid and the initial primitive fields (rho, u, v, T) per cell, or (for unstructured meshes)
+nodes and cells.  Nothing here evaluates the kinetic method; the same description feeds the
+CUDA library and the test-side oracle.
 
 Units are dimensionless: R = 1, T_ref = 1, rho_ref = 1, L_ref = 1, so velocity ranges are
 multiples of sqrt(R T_ref).
@@ -209,3 +210,59 @@ def selector_init(seed=SEED):
 SELECTOR_TRAIN = [(amp, Kn, seed) for amp, seed in ((0.2, 1), (0.2, 2), (0.2, 3), (0.35, 2), (0.35, 3),
                                                     (0.5, 2), (0.5, 3)) for Kn in (0.01, 1.0)]
 SELECTOR_HELD = [(0.35, 1.0, 4), (0.2, 0.01, 4)]
+
+
+# ------------------------------------------------------------------ unstructured meshes
+
+def quad_mesh(x_edges, y_edges):
+    """Nodes and counter-clockwise quads of a tensor grid, cells in row-major order."""
+    nx, ny = len(x_edges) - 1, len(y_edges) - 1
+    X, Y = np.meshgrid(x_edges, y_edges)
+    nodes = np.stack([X.ravel(), Y.ravel()], axis=-1)
+    idx = lambda i, j: j * (nx + 1) + i
+    cells = [(idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)) for j in range(ny) for i in range(nx)]
+    return nodes, cells
+
+
+def two_cavities(m, L=1.0, channel=1.0, width=0.125):
+    """Two square cavities of side L joined by a channel (length `channel`, width `width`),
+    centred on x = 0: square cells of side width / m on three blocks that share their nodes
+    (m even, so that the channel walls at +-width/2 are grid lines of the cavities).
+    Returns (nodes, cells)."""
+    if m % 2:
+        raise ValueError("m must be even")
+    h = width / m
+    n_cav, n_ch = int(round(L / h)), int(round(channel / h))
+    xs_left = -0.5 * channel - L + h * np.arange(n_cav + 1)
+    xs_ch = -0.5 * channel + h * np.arange(n_ch + 1)
+    xs_right = 0.5 * channel + h * np.arange(n_cav + 1)
+    ys_cav = -0.5 * L + h * np.arange(n_cav + 1)
+    ys_ch = -0.5 * width + h * np.arange(m + 1)
+    key = lambda x, y: (int(np.floor(x / h + 0.5)), int(np.floor(y / h + 0.5)))
+    nodes, index = [], {}
+
+    def node(x, y):
+        k = key(x, y)
+        if k not in index:
+            index[k] = len(nodes)
+            nodes.append((x, y))
+        return index[k]
+
+    cells = []
+    for xs, ys in ((xs_left, ys_cav), (xs_ch, ys_ch), (xs_right, ys_cav)):
+        for j in range(len(ys) - 1):
+            for i in range(len(xs) - 1):
+                cells.append((node(xs[i], ys[j]), node(xs[i + 1], ys[j]), node(xs[i + 1], ys[j + 1]),
+                              node(xs[i], ys[j + 1])))
+    return np.array(nodes), cells
+
+
+def triangulate(nodes, cells):
+    """Each quad split into two triangles along alternating diagonals."""
+    tri = []
+    for k, (a, b, c, d) in enumerate(cells):
+        if k % 2 == 0:
+            tri += [(a, b, c), (a, c, d)]
+        else:
+            tri += [(a, b, d), (b, c, d)]
+    return nodes, tri
