@@ -17,6 +17,7 @@ ascending index order), citing the section / equation it restates:
 * ``mlvs``      -- multi-level step with cross-level faces (Sec. 3.4)
 * ``mlvs_curvi`` -- the multi-level step on a structured curvilinear mesh (Sec. 3.4 on ``curvi``)
 * ``unstructured`` -- the DUGKS step on polygonal cells (the two-cavity case of Sec. 4)
+* ``mlvs_unstructured`` -- the multi-level step on polygonal cells (Sec. 3.4 on ``unstructured``)
 * ``mlp``       -- FP64 reference MLP level selector (not in the paper; used to check gradients)
 
 Functions without an independent pin say "parity unpinned" in their docstring.
