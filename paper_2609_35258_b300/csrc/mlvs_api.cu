@@ -130,6 +130,7 @@ struct Inst {
   DevBuf lvl_of_d, slot_of_d, ucell, W, err, stepctr;
   std::vector<Route> ghosts, fluxes;
   MapBatch gb;
+  std::vector<MapBatch> fb;  // flux routes by source level (only routes[0] is used)
   std::vector<int> order;    // levels by decreasing velocity count
 };
 
@@ -622,22 +623,12 @@ template <class S, class T, int D> struct Runner {
     B.ok = false;
     B.nwork = 0;
     std::vector<int> rs;
+    std::vector<const Route*> rp;
     for (int r = 0; r < (int)I.ghosts.size(); ++r)
-      if (!I.ghosts[r].items.empty()) rs.push_back(r);
+      if (!I.ghosts[r].items.empty()) { rs.push_back(r); rp.push_back(&I.ghosts[r]); }
     if (rs.empty()) return cudaSuccess;
-    auto groups = [&](int g) {
-      long n = 0;
-      for (int r : rs) n += ((long)I.ghosts[r].items.size() + g - 1) / g;
-      return n;
-    };
-    int G = 1;
-    for (int g : {8, 4, 2})
-      if (groups(g) >= 148 * 4) { G = g; break; }
     std::vector<MapWork> work;
-    for (int q = 0; q < (int)rs.size(); ++q) {
-      const int n = (int)I.ghosts[rs[q]].items.size();
-      for (int b = 0; b < n; b += G) work.push_back({q, b, std::min(G, n - b)});
-    }
+    const int G = group_items(rp, work);
     for (int par = 0; par < 4; ++par) {
       std::vector<MapArgs> tab;
       for (int r : rs) {
@@ -665,6 +656,62 @@ template <class S, class T, int D> struct Runner {
     B.nwork = (int)work.size();
     B.G = G;
     B.ok = true;
+    return cudaSuccess;
+  }
+
+  // item groups of a set of routes: the largest G whose group count still fills the GPU
+  static int group_items(const std::vector<const Route*>& rs, std::vector<MapWork>& work) {
+    auto groups = [&](int g) {
+      long n = 0;
+      for (const Route* r : rs) n += ((long)r->items.size() + g - 1) / g;
+      return n;
+    };
+    int G = 1;
+    for (int g : {8, 4, 2})
+      if (groups(g) >= 148 * 4) { G = g; break; }
+    work.clear();
+    for (int q = 0; q < (int)rs.size(); ++q) {
+      const int n = (int)rs[q]->items.size();
+      for (int b = 0; b < n; b += G) work.push_back({q, b, std::min(G, n - b)});
+    }
+    return G;
+  }
+
+  // route arguments and item groups of the batched flux launch of every source level
+  static cudaError_t flux_batch(mlvs_handle* h, Inst& I) {
+    I.fb.clear();
+    I.fb.resize(I.lv.size());
+    for (int src = 0; src < (int)I.lv.size(); ++src) {
+      std::vector<const Route*> rs;
+      for (auto& r : I.fluxes)
+        if (r.src == src && !r.items.empty()) rs.push_back(&r);
+      if (rs.empty()) continue;
+      MapBatch& B = I.fb[src];
+      std::vector<MapWork> work;
+      B.G = group_items(rs, work);
+      std::vector<MapArgs> tab;
+      for (const Route* r : rs) {
+        LevelRt& Ls = I.lv[r->src];
+        LevelRt& Ld = I.lv[r->dst];
+        CSR* c = nullptr;
+        if (get_csr(h, Ls.space, Ld.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
+        MapArgs m = margs(h, Ls.space, Ld.space, c);
+        m.src = Ls.X.p;
+        m.src_ld = Ls.nX;
+        m.dst = Ld.Y.p;
+        m.dst_ld = Ld.nY;
+        m.prm = Ls.fprm.p;
+        m.prm_ld = Ls.k.nface;
+        m.items = r->items_d.as<MapItem>();
+        m.nitems = (int)r->items.size();
+        tab.push_back(m);
+      }
+      cudaError_t e = upload(B.routes[0], tab, h->stream);
+      if (e != cudaSuccess) return e;
+      if ((e = upload(B.work, work, h->stream)) != cudaSuccess) return e;
+      B.nwork = (int)work.size();
+      B.ok = true;
+    }
     return cudaSuccess;
   }
 
@@ -719,6 +766,22 @@ template <class S, class T, int D> struct Runner {
   }
 
   static cudaError_t run_fluxes(mlvs_handle* h, Inst& I, int src) {
+    if (src < (int)I.fb.size() && I.fb[src].ok) {
+      const MapBatch& B = I.fb[src];
+      const MapArgs* rt = B.routes[0].as<MapArgs>();
+      const MapWork* wk = B.work.as<MapWork>();
+      const int nb = std::max(1, std::min(B.nwork, 148 * 16));
+      mark_begin(h, 5);
+      ++h->launches;
+      switch (B.G) {
+        case 8: k_map_multi<T, T, T, D, SRC_FLUX, 8><<<nb, 256, 0, h->stream>>>(rt, wk, B.nwork); break;
+        case 4: k_map_multi<T, T, T, D, SRC_FLUX, 4><<<nb, 256, 0, h->stream>>>(rt, wk, B.nwork); break;
+        case 2: k_map_multi<T, T, T, D, SRC_FLUX, 2><<<nb, 256, 0, h->stream>>>(rt, wk, B.nwork); break;
+        default: k_map_multi<T, T, T, D, SRC_FLUX, 1><<<nb, 256, 0, h->stream>>>(rt, wk, B.nwork); break;
+      }
+      mark_end(h);
+      return cudaGetLastError();
+    }
     for (auto& r : I.fluxes) {
       if (r.src != src || r.items.empty()) continue;
       LevelRt& Ls = I.lv[r.src];
@@ -886,7 +949,7 @@ template <class S, class T, int D> struct Runner {
   }
 
   // masks of the criterion (Sec. 3.2) of every cell of an instance into kout[ncell][N1*N1]
-  // sel: the global ids of the cells to judge (null: every cell)
+  // sel: the global ids of the cells to evaluate (null: every cell)
   static cudaError_t criterion(mlvs_handle* h, Inst& I, const mlvs_adapt_params& p, unsigned char* kout,
                                const std::vector<int>* sel) {
     const int nb = h->N1 * h->N1;
@@ -956,12 +1019,13 @@ struct Ops {
   cudaError_t (*criterion)(mlvs_handle*, Inst&, const mlvs_adapt_params&, unsigned char*, const std::vector<int>*);
   cudaError_t (*wall_table)(mlvs_handle*, LevelRt&);
   cudaError_t (*ghost_batch)(mlvs_handle*, Inst&);
+  cudaError_t (*flux_batch)(mlvs_handle*, Inst&);
 };
 
 template <class S, class T, int D> Ops make_ops() {
   using R = Runner<S, T, D>;
   return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion,
-             &R::wall_table, &R::ghost_batch};
+             &R::wall_table, &R::ghost_batch, &R::flux_batch};
 }
 
 Ops ops_for(int storage, int D) {
@@ -1204,6 +1268,7 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
   for (auto& r : I.ghosts) CK(upload(r.items_d, r.items, h->stream));
   for (auto& r : I.fluxes) CK(upload(r.items_d, r.items, h->stream));
   CK(ops_for(h->cfg.storage, D).ghost_batch(h, I));
+  CK(ops_for(h->cfg.storage, D).flux_batch(h, I));
   I.order.resize(nlev);
   for (int l = 0; l < nlev; ++l) I.order[l] = l;
   std::stable_sort(I.order.begin(), I.order.end(), [&](int a, int b) {
