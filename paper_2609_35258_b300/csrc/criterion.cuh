@@ -30,7 +30,7 @@
 namespace mlvs {
 
 struct CritArgs {
-  const int* sel;              // slots to judge, one CTA each (null: slot = CTA index)
+  const int* sel;              // slots to evaluate, one CTA each (null: slot = CTA index)
   const void* f;               // [2][nv][ns] phi~ of the level (storage type)
   int ns, nv;
   const int* ids;              // [ns] global cell of every slot

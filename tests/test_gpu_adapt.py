@@ -85,7 +85,7 @@ def test_criterion_hysteresis_and_inheritance():
     ko = _oracle_masks(o["base"], [st.g[c] for c in range(24)], [st.h[c] for c in range(24)], spaces,
                        kprev, C_split, C_merge, 0.0)
     np.testing.assert_array_equal(km, ko)
-    # the previous status matters: the same state judged from level 0 differs somewhere
+    # the previous status matters: the same state evaluated from level 0 differs somewhere
     km0 = _oracle_masks(o["base"], [st.g[c] for c in range(24)], [st.h[c] for c in range(24)], spaces,
                         [np.zeros((N1, N1), dtype=np.int64)] * 24, C_split, C_merge, 0.0)
     assert np.any(km0 != ko)
