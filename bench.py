@@ -332,6 +332,19 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
     return out
 
 
+def combine_ranks(ms, world, upd_step, steps, device="cuda"):
+    """The timed region's length as the maximum over ranks (every rank waits at a barrier
+    afterwards) and the whole-job throughput: the updates of all ranks over that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms = float(t.item())
+        tdist.barrier()
+    return ms, world * upd_step * steps / (ms / 1e3)
+
+
 def _l2(a, b):
     import numpy as np
     return float(np.sqrt(np.sum((a - b) ** 2)) / np.sqrt(np.sum(b ** 2)))
@@ -370,15 +383,9 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms = float(t.item())
-        tdist.barrier()
+    ms, value = combine_ranks(e0.elapsed_time(e1), world, upd_step, args.steps)
     torch.cuda.synchronize()
     ms_step = ms / args.steps
-    value = world * upd_step * args.steps / (ms / 1e3)
 
     # roofline of the dominant kernel (update pass or face-sum pass)
     phases = list(st.ms_phase)
