@@ -9,12 +9,15 @@
 // mass, momentum and energy fluxes are those of the face (Eq. native_flux_moment_matching).
 //
 // One step (Sec. 2.2) per instance, on the handle's stream:
-//   1. k_finalize (cells) per level: W, tau, q, model parameters + compatibility correction
-//   2. k_map (SRC_BARP) per (source level, level): ghosts
+//   1. finalisation of the cells per level (chunk sums, then k_finalize, or k_fin_pre /
+//      k_fin_sums / k_fin_post on spaces that are not tensor products): W, tau, q, model
+//      parameters + compatibility correction
+//   2. k_map_multi (SRC_BARP): the ghosts of every (source level, level) route in one launch
 //   3. k_tile MODE 0 per level: face phi-bar, face moment partials
-//   4. k_finalize (faces) per level: Eq. W_from_bar, Eq. recover_phi weights, wall densities
+//   4. finalisation of the faces each level evaluates: Eq. W_from_bar, Eq. recover_phi
+//      weights, wall densities
 //   5. per level, finest space first: k_tile MODE 1 (microfluxes, Eq. explicit_update), then
-//      k_map (SRC_FLUX) of its cross-level fluxes to the levels that receive them
+//      k_map_multi (SRC_FLUX) of its cross-level fluxes to the levels that receive them
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -607,7 +610,6 @@ template <class S, class T, int D> struct Runner {
   static void launch_map(mlvs_handle* h, const MapArgs& m) {
     const int g = map_items_per_cta(m.nitems);
     const int nb = map_grid((m.nitems + g - 1) / g);
-    ++h->launches;
     switch (g) {
       case 8: k_map<SrcT, DstT, T, D, KIND, 8><<<nb, 256, 0, h->stream>>>(m); break;
       case 4: k_map<SrcT, DstT, T, D, KIND, 4><<<nb, 256, 0, h->stream>>>(m); break;
@@ -732,7 +734,6 @@ template <class S, class T, int D> struct Runner {
         const MapWork* wk = I.gb.work.as<MapWork>();
         const int nb = std::max(1, std::min(I.gb.nwork, 148 * 16));
         mark_begin(h, 4);
-        ++h->launches;
         switch (I.gb.G) {
           case 8: k_map_multi<S, T, T, D, SRC_BARP, 8><<<nb, 256, 0, h->stream>>>(rt, wk, I.gb.nwork); break;
           case 4: k_map_multi<S, T, T, D, SRC_BARP, 4><<<nb, 256, 0, h->stream>>>(rt, wk, I.gb.nwork); break;
@@ -772,7 +773,6 @@ template <class S, class T, int D> struct Runner {
       const MapWork* wk = B.work.as<MapWork>();
       const int nb = std::max(1, std::min(B.nwork, 148 * 16));
       mark_begin(h, 5);
-      ++h->launches;
       switch (B.G) {
         case 8: k_map_multi<T, T, T, D, SRC_FLUX, 8><<<nb, 256, 0, h->stream>>>(rt, wk, B.nwork); break;
         case 4: k_map_multi<T, T, T, D, SRC_FLUX, 4><<<nb, 256, 0, h->stream>>>(rt, wk, B.nwork); break;
@@ -880,6 +880,7 @@ template <class S, class T, int D> struct Runner {
       LevelRt& L = I.lv[l];
       const int n = (int)L.cells.size();
       if (n == 0) continue;
+      h->launches += 2;
       k_set_shift<T><<<(n + 127) / 128, 128, 0, h->stream>>>(L.prm[L.pcur].as<T>(), n, L.ids.as<int>(),
                                                             I.ucell.as<T>(), h->nx * h->ny);
       dim3 gm((n + 127) / 128, L.k.nchunk);
@@ -906,6 +907,7 @@ template <class S, class T, int D> struct Runner {
       if (e != cudaSuccess) return e;
       const int ni = (int)g.second.size();
       if (Lo.space == Ln.space) {
+        ++h->launches;
         k_copy_cols<S><<<map_grid(ni), 256, 0, h->stream>>>(Lo.f[Lo.cur].as<S>(), (int)Lo.cells.size(),
                                                           Ln.f[0].as<S>(), (int)Ln.cells.size(), 2 * Ln.k.nv,
                                                           items.as<MapItem>(), ni);
@@ -921,6 +923,7 @@ template <class S, class T, int D> struct Runner {
         m.prm_ld = 0;
         m.items = items.as<MapItem>();
         m.nitems = ni;
+        ++h->launches;
         launch_map<S, S, SRC_TILDE>(h, m);
       }
       e = cudaStreamSynchronize(h->stream);   // items freed at scope end
@@ -940,6 +943,7 @@ template <class S, class T, int D> struct Runner {
         for (int j = 0; j < 3; ++j) wv[3 * s + j] = h->cfg.wall[s][j];
       DevBuf wd;
       if ((e = upload(wd, wv, h->stream)) != cudaSuccess) return e;
+      ++h->launches;
       k_wall_den_table<T, D><<<(L.k.nface * 32 + 127) / 128, 128, 0, h->stream>>>(
           L.k, h->gas, h->spaces[L.space].vt.as<T>(), h->fgeo_d.as<T>(), wd.as<double>(), L.wden.as<double>());
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
