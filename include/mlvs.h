@@ -182,6 +182,19 @@ mlvs_status mlvs_adapt(mlvs_handle* h, const mlvs_adapt_params* p, mlvs_adapt_st
  * p is copied. */
 mlvs_status mlvs_set_adaptation(mlvs_handle* h, const mlvs_adapt_params* p, int interval);
 
+/* Host-only: the velocity space of a coarsening mask (Sec. 3.1-3.2), built as the library
+ * builds a representative space.  The base grid has n_base points per axis on [umin, umax] with
+ * rule `quadrature` (MLVS_QUAD_*); kappa[nkappa] holds one byte per level-1 block (nkappa =
+ * n1 * n1, y major) and is first made parent-child consistent (a block keeps level L only if
+ * every level-1 block of its level-L parent allows L).  The space's points and weights (2-D,
+ * in the library's point order) go to xi_x, xi_y, w of capacity cap; *nv_out receives the point
+ * count and *n1_out (may be NULL) the level-1 groups per axis.  With kappa NULL only *n1_out is
+ * written; with all three outputs NULL only the sizes are.  Needs no GPU.
+ * Errors: MLVS_ERR_ARG (base size or rule invalid, nkappa != n1 * n1, cap too small). */
+mlvs_status mlvs_space_points(int n_base, double umin, double umax, int quadrature,
+                              const unsigned char* kappa, int nkappa, double* xi_x, double* xi_y,
+                              double* w, int cap, int* nv_out, int* n1_out);
+
 /* Host-only grouping of nrow masks of nb bytes each (Sec. 3.2): distinct masks by decreasing
  * frequency (ties: lexicographic order), each joins the nearest existing centre when the
  * graded distance sum|ka - kb| / (3 nb) is <= tau (ties: lowest cluster), else it seeds a new

@@ -2012,6 +2012,38 @@ extern "C" mlvs_status mlvs_cluster(const unsigned char* kappa, long nrow, int n
   return MLVS_OK;
 }
 
+extern "C" mlvs_status mlvs_space_points(int n_base, double umin, double umax, int quadrature,
+                                         const unsigned char* kappa, int nkappa, double* xi_x, double* xi_y,
+                                         double* w, int cap, int* nv_out, int* n1_out) {
+  if (!nv_out || !(umax > umin)) return fail(nullptr, MLVS_ERR_ARG, "mlvs_space_points: bad argument");
+  try {
+    const Base1D b = make_base_1d(n_base, umin, umax, quadrature);
+    const int N1 = (int)groups_1d(n_base, 1).size();
+    if (n1_out) *n1_out = N1;
+    *nv_out = 0;
+    if (!kappa) return MLVS_OK;
+    if (nkappa != N1 * N1) return fail(nullptr, MLVS_ERR_ARG, "mlvs_space_points: nkappa != n1 * n1");
+    std::vector<int> k(kappa, kappa + nkappa);
+    for (int x : k)
+      if (x < 0 || x > 3) return fail(nullptr, MLVS_ERR_ARG, "mlvs_space_points: kappa above 3");
+    const std::vector<int> keff = enforce_consistency(k, n_base, 2);
+    std::vector<int> owner;
+    const VSpace vs = kappa_vspace(b, 2, keff, owner);
+    *nv_out = vs.nv();
+    if (!xi_x && !xi_y && !w) return MLVS_OK;
+    if (!xi_x || !xi_y || !w || cap < vs.nv())
+      return fail(nullptr, MLVS_ERR_ARG, "mlvs_space_points: outputs missing or cap too small");
+    for (int i = 0; i < vs.nv(); ++i) {
+      xi_x[i] = vs.xix[i];
+      xi_y[i] = vs.xiy[i];
+      w[i] = vs.w[i];
+    }
+  } catch (const std::exception& e) {
+    return fail(nullptr, MLVS_ERR_ARG, std::string("mlvs_space_points: ") + e.what());
+  }
+  return MLVS_OK;
+}
+
 extern "C" mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out, int cap,
                                         int* nb_out) {
   if (!h || !nb_out) return MLVS_ERR_ARG;

@@ -84,6 +84,9 @@ def _load():
         "mlvs_cluster": (C.c_int, [C.c_void_p, C.c_long, C.c_int, C.c_double, C.POINTER(C.c_int),
                                    C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_level_kappa": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_space_points": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int)]),
         "mlvs_set_graph": (C.c_int, [H, C.c_int]),
         "mlvs_step_many": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int, C.POINTER(mlvs_step_stats)]),
         "mlvs_autotune": (C.c_int, [H, C.c_int, C.POINTER(C.c_int), C.c_void_p]),
@@ -247,6 +250,19 @@ def mlvs_cluster(kappa, tau):
     _check(_lib.mlvs_cluster(k.ctypes.data, nrow, nb, tau, labels.ctypes.data_as(C.POINTER(C.c_int)),
                              reps.ctypes.data, cap, C.byref(n)), None)
     return labels, reps[: n.value].copy()
+
+
+def mlvs_space_points(n_base, umin, umax, quadrature, kappa):
+    """Host-only: points (xi_x, xi_y) and weights of the space of a level-1 coarsening mask
+    (made parent-child consistent first), as the library builds it."""
+    k = np.ascontiguousarray(kappa, dtype=np.uint8).ravel()
+    nv, n1 = C.c_int(), C.c_int()
+    _check(_lib.mlvs_space_points(n_base, umin, umax, quadrature, k.ctypes.data, k.size, None, None, None, 0,
+                                  C.byref(nv), C.byref(n1)), None)
+    x, y, w = np.zeros(nv.value), np.zeros(nv.value), np.zeros(nv.value)
+    _check(_lib.mlvs_space_points(n_base, umin, umax, quadrature, k.ctypes.data, k.size, x.ctypes.data,
+                                  y.ctypes.data, w.ctypes.data, nv.value, C.byref(nv), C.byref(n1)), None)
+    return x, y, w
 
 
 def mlvs_set_graph(h, on=True):
