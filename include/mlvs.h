@@ -195,6 +195,20 @@ mlvs_status mlvs_space_points(int n_base, double umin, double umax, int quadratu
                               const unsigned char* kappa, int nkappa, double* xi_x, double* xi_y,
                               double* w, int cap, int* nv_out, int* n1_out);
 
+/* Host-only: the curvilinear geometry the library derives from a node grid (what a handle
+ * created with mesh_kind = 1 uses).  node_xy[(ny + 1) * (nx + 1)][2] row-major (row j = node
+ * row), cells counter-clockwise; periodic_x, periodic_y say which pairs of sides are periodic.
+ * cell_geo[5][nx * ny]: J^{-T} row-major (four rows; index-direction slopes times it give
+ * physical slopes), then the area.  face_geo[7][nface]: x-faces first (nfx * ny, nfx = nx if
+ * periodic_x else nx + 1), then y-faces (nx * nfy): unit normal (2 rows, towards the cell of
+ * higher index), length, midpoint minus the lower-index side's centroid (2), midpoint minus the
+ * higher-index side's centroid (2); a ghost's centroid is the boundary cell's reflected through
+ * the face midpoint, a periodic image's is moved by the mean offset of the periodic node rows.
+ * width[nx * ny] (may be NULL): area over the longest edge.  Needs no GPU.
+ * Errors: MLVS_ERR_ARG (null pointers, sizes below 1, a cell that is not counter-clockwise). */
+mlvs_status mlvs_mesh_geometry(int nx, int ny, int periodic_x, int periodic_y, const double* node_xy,
+                               double* cell_geo, double* face_geo, double* width);
+
 /* Host-only grouping of nrow masks of nb bytes each (Sec. 3.2): distinct masks by decreasing
  * frequency (ties: lexicographic order), each joins the nearest existing centre when the
  * graded distance sum|ka - kb| / (3 nb) is <= tau (ties: lowest cluster), else it seeds a new

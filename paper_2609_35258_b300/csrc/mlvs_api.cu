@@ -1373,6 +1373,25 @@ static mlvs_status build_geometry(mlvs_handle* h, const double* xy) {
   return MLVS_OK;
 }
 
+extern "C" mlvs_status mlvs_mesh_geometry(int nx, int ny, int periodic_x, int periodic_y, const double* node_xy,
+                                          double* cell_geo, double* face_geo, double* width) {
+  if (!node_xy || !cell_geo || !face_geo || nx < 1 || ny < 1)
+    return fail(nullptr, MLVS_ERR_ARG, "mlvs_mesh_geometry: bad argument");
+  // the same construction a handle runs, on a host-only handle (no device resources)
+  mlvs_handle tmp;
+  std::memset(&tmp.cfg, 0, sizeof(tmp.cfg));
+  tmp.nx = nx;
+  tmp.ny = ny;
+  tmp.cfg.bc[0] = tmp.cfg.bc[1] = periodic_x ? MLVS_BC_PERIODIC : MLVS_BC_WALL;
+  tmp.cfg.bc[2] = tmp.cfg.bc[3] = periodic_y ? MLVS_BC_PERIODIC : MLVS_BC_WALL;
+  const mlvs_status st = build_geometry(&tmp, node_xy);
+  if (st != MLVS_OK) return fail(nullptr, st, "mlvs_mesh_geometry: " + tmp.err);
+  std::memcpy(cell_geo, tmp.cgeo.data(), tmp.cgeo.size() * sizeof(double));
+  std::memcpy(face_geo, tmp.fgeo.data(), tmp.fgeo.size() * sizeof(double));
+  if (width) std::memcpy(width, tmp.width.data(), tmp.width.size() * sizeof(double));
+  return MLVS_OK;
+}
+
 // Device copies of the curvilinear geometry in the compute type; dt/|V| needs dt.
 static mlvs_status upload_geometry(mlvs_handle* h) {
   const size_t nc = (size_t)h->nx * h->ny;

@@ -84,6 +84,8 @@ def _load():
         "mlvs_cluster": (C.c_int, [C.c_void_p, C.c_long, C.c_int, C.c_double, C.POINTER(C.c_int),
                                    C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_level_kappa": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+        "mlvs_mesh_geometry": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p]),
         "mlvs_space_points": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int)]),
@@ -250,6 +252,20 @@ def mlvs_cluster(kappa, tau):
     _check(_lib.mlvs_cluster(k.ctypes.data, nrow, nb, tau, labels.ctypes.data_as(C.POINTER(C.c_int)),
                              reps.ctypes.data, cap, C.byref(n)), None)
     return labels, reps[: n.value].copy()
+
+
+def mlvs_mesh_geometry(node_xy, periodic_x, periodic_y):
+    """Host-only: (cell_geo [5][nc], face_geo [7][nface], width [nc]) of a node grid
+    node_xy [ny+1][nx+1][2], as a curvilinear handle builds it."""
+    xy = np.ascontiguousarray(node_xy, dtype=np.float64)
+    ny, nx = xy.shape[0] - 1, xy.shape[1] - 1
+    nfx = nx if periodic_x else nx + 1
+    nfy = ny if periodic_y else ny + 1
+    nc, nface = nx * ny, nfx * ny + nx * nfy
+    cg, fg, wd = np.zeros((5, nc)), np.zeros((7, nface)), np.zeros(nc)
+    _check(_lib.mlvs_mesh_geometry(nx, ny, int(bool(periodic_x)), int(bool(periodic_y)), xy.ctypes.data,
+                                   cg.ctypes.data, fg.ctypes.data, wd.ctypes.data), None)
+    return cg, fg, wd
 
 
 def mlvs_space_points(n_base, umin, umax, quadrature, kappa):
