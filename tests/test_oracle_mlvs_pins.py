@@ -94,6 +94,41 @@ def test_repeated_projection_invariants(kind, eps):
         assert abs(m0["q"][0]) > 0.1 * eps          # the perturbation carries a heat flux
 
 
+def test_repeated_projection_against_the_paper_table():
+    """tests/golden/e2_repeated_projection.json holds the 4- and 9-moment rows of the paper's
+    table for the repeated projection sequence.  Our perturbation delta is normalised
+    differently (q_x0 = 0.5 eps here, 0.7071 eps there), so what is compared is what does not
+    depend on it: the basic moments as printed (three decimals), the constrained moment of a
+    9-moment row back at its initial value (printed final / printed initial = 1.000) and the
+    other higher moment unchanged; in the 4-moment rows the higher moments are not kept."""
+    import json
+    import os
+    fx = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "e2_repeated_projection.json")))
+    base = vspace.make_base(65, -6, 6, D=2)
+    for row in fx["rows"]:
+        kind, eps = row["kind"], row["eps"]
+        sp0, gas, g, h = _e2_initial(base, kind, eps)
+        m0 = kinetic.moments(g, h, sp0.xi, sp0.w, gas)
+        cur = sp0
+        for Lx, Ly in _e2_sequence(base):
+            nxt = vspace.aniso_space(base, Lx, Ly)
+            g, h = mapping.map9(g, h, cur, nxt) if row["method"] == "9-moment" else mapping.map4(g, h, cur, nxt, gas)
+            cur = nxt
+        m = kinetic.moments(g, h, cur.xi, cur.w, gas)
+        assert round(float(m["rho"]), 3) == row["rho"]
+        assert round(float(m["mom"][0]), 3) == row["rhoU"]
+        assert round(float(m["rhoE"]), 3) == row["rhoE"]
+        dpi = lambda mm: mm["P"][0, 0] - mm["P"][1, 1]
+        con, other = (("q_x", lambda mm: mm["q"][0]), dpi) if kind == "heat" else (("dPi", dpi), lambda mm: mm["q"][0])
+        name, get = con
+        if row["method"] == "9-moment":
+            printed_ratio = row[name] / (fx["initial"][kind][name + "_over_eps"] * eps)
+            assert round(float(get(m) / get(m0)), 3) == round(printed_ratio, 3) == 1.0
+            assert abs(other(m) - other(m0)) < 1e-12
+        elif eps <= 1e-3:
+            assert abs(get(m) - get(m0)) > 10 * abs(get(m0))      # the table's "completely distorted"
+
+
 # ------------------------------------------------------------------ criterion and clustering
 
 def test_criterion_uniform_maxwellian():
