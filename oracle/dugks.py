@@ -36,7 +36,7 @@ Readings of points the paper leaves open (the same ones the CUDA library uses):
 """
 from __future__ import annotations
 
-from dataclasses import dataclass, field
+from dataclasses import dataclass
 
 import numpy as np
 

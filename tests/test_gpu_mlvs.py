@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 if not have_gpu():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
-from oracle import kinetic, mlvs as omlvs, vspace  # noqa: E402
+from oracle import mlvs as omlvs, vspace  # noqa: E402
 from paper_2609_35258_b300 import mlvs as M  # noqa: E402
 from paper_2609_35258_b300.solver import Solver  # noqa: E402
 

@@ -5,7 +5,6 @@ exactness of the quadrature, the definitions of the transformed distributions (S
 the Shakhov heat-flux property (Sec. 2.1), the compatibility-recovery test state of Sec. 4.1.1,
 conservation of the finite-volume update, and a brute-force free-molecular advection.
 """
-import math
 
 import numpy as np
 import pytest
