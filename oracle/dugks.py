@@ -68,6 +68,7 @@ class Options:
     compat_moments: int = 4       # 4: collision invariants; 8: also heat flux and deviatoric stress (D = 2)
     map_moments: int = 4          # cross-level mapping: 4 (conserved moments) or 9 (raw second moments and
                                   # energy fluxes too, D = 2), for stencil states, fluxes and level switches
+    positive_mapping: bool = False  # exponential fallback where the 4-moment state mapping makes g negative
 
 
 def time_step(mesh: Mesh, xi: np.ndarray, cfl: float, D: int) -> float:

@@ -109,6 +109,23 @@ def map4(g, h, src, dst, gas: Gas, M_tar=None, T_tar=None):
     return correct4(gp, hp, M_tar, T_tar, dst, gas)
 
 
+def map_state(g, h, src, dst, gas: Gas, nmom=4, positive=False):
+    """A cell state carried to another space with its own moments as targets: the projection
+    plus the four-moment correction (Eqs. interface_state_moment_matching and
+    level_switch_conservation), or the nine-moment correction (nmom = 9).  With `positive`, a
+    four-moment result with a negative g where the projection had none is replaced by the
+    exponential correction of the same targets (the fallback Sec. 3.3.2 proposes)."""
+    if nmom == 9:
+        return map9(g, h, src, dst)
+    m = moments(g, h, src.xi, src.w, gas)
+    tar = np.concatenate([[m["rho"]], m["rho"] * m["u"], [m["rhoE"]]])
+    gp, hp = project(g, h, src, dst)
+    gl, hl = correct4(gp, hp, tar, m["T"], dst, gas)
+    if positive and gl.min() < 0.0 <= gp.min():
+        return correct_exp4(gp, hp, tar, dst)
+    return gl, hl
+
+
 def correct_exp4(gp, hp, M_tar, space, tol=1e-14, maxit=60):
     """Exponential moment-constrained correction (Eq. exponential_moment_correction), the
     positivity-preserving alternative to the additive correction that Sec. 3.3.2 proposes:

@@ -135,14 +135,9 @@ def step(st: MLVSState):
         """phi-bar-plus of cell c on space key (Eq. interface_state_moment_matching)."""
         if st.sp[c] == key:
             return gbp[c], hbp[c]
-        if (c, key) not in cache and opt.map_moments == 9:
-            cache[(c, key)] = mapping.map9(gbp[c], hbp[c], book.space(st.sp[c]), book.space(key))
         if (c, key) not in cache:
-            src, dst = book.space(st.sp[c]), book.space(key)
-            m = kinetic.moments(gbp[c], hbp[c], src.xi, src.w, gas)
-            tar = np.concatenate([[m["rho"]], m["rho"] * m["u"], [m["rhoE"]]])
-            gp, hp = mapping.project(gbp[c], hbp[c], src, dst)
-            cache[(c, key)] = mapping.correct4(gp, hp, tar, m["T"], dst, gas)
+            cache[(c, key)] = mapping.map_state(gbp[c], hbp[c], book.space(st.sp[c]), book.space(key), gas,
+                                                opt.map_moments, opt.positive_mapping)
         return cache[(c, key)]
 
     def vl(a, b, hh):
@@ -276,12 +271,11 @@ def step(st: MLVSState):
 
 def remap(st: MLVSState, c, new_key):
     """Level switch of cell c (Eq. level_switch_conservation; four-moment form, or the
-    nine-moment form when st.opt.map_moments is 9)."""
+    nine-moment form when st.opt.map_moments is 9, with the exponential fallback when
+    st.opt.positive_mapping is set)."""
     if st.sp[c] == new_key:
         return
     src, dst = st.book.space(st.sp[c]), st.book.space(new_key)
-    if st.opt.map_moments == 9:
-        st.g[c], st.h[c] = mapping.map9(st.g[c], st.h[c], src, dst)
-    else:
-        st.g[c], st.h[c] = mapping.map4(st.g[c], st.h[c], src, dst, st.gas)
+    st.g[c], st.h[c] = mapping.map_state(st.g[c], st.h[c], src, dst, st.gas, st.opt.map_moments,
+                                         st.opt.positive_mapping)
     st.sp[c] = new_key

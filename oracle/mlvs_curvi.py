@@ -53,14 +53,9 @@ def step(st: MLVSState):
         """phi-bar-plus of cell c on space key (Eq. interface_state_moment_matching)."""
         if st.sp[c] == key:
             return gbp[c], hbp[c]
-        if (c, key) not in cache and opt.map_moments == 9:
-            cache[(c, key)] = mapping.map9(gbp[c], hbp[c], book.space(st.sp[c]), book.space(key))
         if (c, key) not in cache:
-            src, dst = book.space(st.sp[c]), book.space(key)
-            m = kinetic.moments(gbp[c], hbp[c], src.xi, src.w, gas)
-            tar = np.concatenate([[m["rho"]], m["rho"] * m["u"], [m["rhoE"]]])
-            gp, hp = mapping.project(gbp[c], hbp[c], src, dst)
-            cache[(c, key)] = mapping.correct4(gp, hp, tar, m["T"], dst, gas)
+            cache[(c, key)] = mapping.map_state(gbp[c], hbp[c], book.space(st.sp[c]), book.space(key), gas,
+                                                opt.map_moments, opt.positive_mapping)
         return cache[(c, key)]
 
     def recon(j, i, key, xb, xi, k):

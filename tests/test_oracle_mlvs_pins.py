@@ -315,6 +315,40 @@ def test_exponential_correction_without_defect_is_the_identity():
     np.testing.assert_allclose(he, h, rtol=1e-13)
 
 
+def test_positive_mapping_fallback_on_a_level_switch():
+    """The level switch of a cold narrow distribution to a coarse space: the four-moment
+    linear mapping makes tails of g negative; with the fallback the exponential correction
+    takes over, every value of g stays nonnegative and the conserved moments still match."""
+    base = vspace.make_base(33, -6.0, 6.0, D=2)
+    src, dst = vspace.uniform_space(base, 0), vspace.uniform_space(base, 2)
+    gas = kinetic.Gas(D=2, R=1.0)
+    g, h = kinetic.maxwell_gh(np.array(1.0), np.array([1.7, -0.4]), np.array(0.15), src.xi, gas)
+    tar = kinetic.conserved(g, h, src.xi, src.w)
+    gl, _ = mapping.map_state(g, h, src, dst, gas)
+    gp, hp = mapping.map_state(g, h, src, dst, gas, positive=True)
+    assert gl.min() < 0.0 <= g.min()
+    assert gp.min() >= 0.0
+    np.testing.assert_allclose(kinetic.conserved(gp, hp, dst.xi, dst.w), tar, rtol=1e-13, atol=1e-13)
+
+
+def test_positive_mapping_keeps_exact_conservation(monkeypatch):
+    """Two spaces with the fallback on: the exponential correction takes over for some mapped
+    stencil states (counted), and the run still conserves to round-off."""
+    calls = []
+    exp4 = mapping.correct_exp4
+    monkeypatch.setattr(mapping, "correct_exp4", lambda *a, **k: calls.append(1) or exp4(*a, **k))
+    desc = workloads.periodic_random(8, 4, n_base=17, umax=5.0)
+    lev = [0 if (c % 8) < 4 else 1 for c in range(32)]
+    o, st = _mlvs_from_desc(desc, lev, [0, 1])
+    st.opt = dugks.Options(positive_mapping=True)
+    W0 = st.totals()
+    for _ in range(4):
+        mlvs.step(st)
+    W1 = st.totals()
+    assert len(calls) > 0
+    assert np.max(np.abs(W1 - W0)) < 1e-12 * np.max(np.abs(W0))
+
+
 def _raw9_totals(st):
     book = st.book
     return sum(mapping.raw9(g, h, book.space(k)) for g, h, k in zip(st.g, st.h, st.sp))
