@@ -196,7 +196,9 @@ mlvs_status mlvs_space_points(int n_base, double umin, double umax, int quadratu
                               double* w, int cap, int* nv_out, int* n1_out);
 
 /* Host-only: the curvilinear geometry the library derives from a node grid (what a handle
- * created with mesh_kind = 1 uses).  node_xy[(ny + 1) * (nx + 1)][2] row-major (row j = node
+ * created with mesh_kind = 1 uses): the face areas and normals of Eq. explicit_update and the
+ * slope and offset geometry of Eq. reconstruction on the O-grid of the cylinder case (Sec. 4).
+ * node_xy[(ny + 1) * (nx + 1)][2] row-major (row j = node
  * row), cells counter-clockwise; periodic_x, periodic_y say which pairs of sides are periodic.
  * cell_geo[5][nx * ny]: J^{-T} row-major (four rows; index-direction slopes times it give
  * physical slopes), then the area.  face_geo[7][nface]: x-faces first (nfx * ny, nfx = nx if
