@@ -132,8 +132,8 @@ mlvs_status mlvs_step(mlvs_handle* h, int n_steps, mlvs_step_stats* stats);
  * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
 mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const int* levels);
 
-/* Extra: number of velocities of a level and (if the arrays are non-NULL, capacity cap) its
- * coordinates and weights. */
+/* Extra (the representative space of Sec. 3.2): number of velocities of a level and (if the
+ * arrays are non-NULL, capacity cap) its coordinates and weights. */
 mlvs_status mlvs_level_info(const mlvs_handle* h, int level, int* nv, double* xi_x, double* xi_y,
                             double* w, int cap);
 
@@ -178,7 +178,8 @@ mlvs_status mlvs_criterion(mlvs_handle* h, int instance, const mlvs_adapt_params
  * Errors: as mlvs_criterion, and MLVS_ERR_OOM. */
 mlvs_status mlvs_adapt(mlvs_handle* h, const mlvs_adapt_params* p, mlvs_adapt_stats* stats);
 
-/* Run mlvs_adapt with p after every `interval` steps taken by mlvs_step (interval 0: never).
+/* Run mlvs_adapt with p after every `interval` steps taken by mlvs_step (interval 0: never);
+ * the update interval of the representative spaces in the runs of Sec. 4.
  * p is copied. */
 mlvs_status mlvs_set_adaptation(mlvs_handle* h, const mlvs_adapt_params* p, int interval);
 
@@ -220,32 +221,32 @@ mlvs_status mlvs_mesh_geometry(int nx, int ny, int periodic_x, int periodic_y, c
 mlvs_status mlvs_cluster(const unsigned char* kappa, long nrow, int nb, double tau, int* labels,
                          unsigned char* reps, int reps_cap, int* n_reps);
 
-/* CUDA graphs for mlvs_step: on != 0 replays the launch sequence of two steps (the
- * ping-pong buffers return to their parity after two) as one graph, captured on first use
- * and again whenever the levels change; an adaptation or a moments call in between falls
- * back to regular launches for the step concerned.  Profiled steps never use graphs.
- * The handle's stream may be any stream, including the legacy default stream. */
+/* No counterpart in the paper (launch mechanics). CUDA graphs for mlvs_step: on != 0 replays the
+ * launch sequence of two steps (the ping-pong buffers return to their parity after two) as one
+ * graph, captured on first use and again whenever the levels change; an adaptation or a moments
+ * call in between falls back to regular launches for the step concerned. Profiled steps never
+ * use graphs. The handle's stream may be any stream, including the legacy default stream. */
 mlvs_status mlvs_set_graph(mlvs_handle* h, int on);
 
-/* Advance several handles (independent cases, e.g. different meshes and Knudsen numbers) by
- * n_steps together.  use_graph != 0: every two steps are one graph launch on hs[0]'s stream
- * whose branches are the instances of all handles, so their kernels can run concurrently;
- * the other handles' streams are ordered before and after it.  stats (may be NULL) sums
- * over the group; ms_phase is not filled.  A handle may appear only once.
- * Errors: as mlvs_step, for the first handle that fails. */
+/* No counterpart in the paper (batching). Advance several handles (independent cases, e.g.
+ * different meshes and Knudsen numbers) by n_steps together. use_graph != 0: every two steps are
+ * one graph launch on hs[0]'s stream whose branches are the instances of all handles, so their
+ * kernels can run concurrently; the other handles' streams are ordered before and after it.
+ * stats (may be NULL) sums over the group; ms_phase is not filled. A handle may appear only
+ * once. Errors: as mlvs_step, for the first handle that fails. */
 mlvs_status mlvs_step_many(mlvs_handle* const* hs, int n_handles, int n_steps, int use_graph,
                            mlvs_step_stats* stats);
 
-/* Autotune the velocity chunking of the tile launches: for each candidate number of CTAs per
- * tile launch (148, 296, 444, 592, 888, 1184, 1776) re-chunk the velocities of every level,
- * run one warm step and `steps` timed steps, and keep the fastest.  *cta_target and
- * ms_table[7] (ms per step of every candidate) are written when non-NULL.  The state
- * advances by 7 (steps + 1) real steps.
- * Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
+/* No counterpart in the paper (launch tuning). Autotune the velocity chunking of the tile
+ * launches: for each candidate number of CTAs per tile launch (148, 296, 444, 592, 888, 1184,
+ * 1776) re-chunk the velocities of every level, run one warm step and `steps` timed steps, and
+ * keep the fastest. *cta_target and ms_table[7] (ms per step of every candidate) are written
+ * when non-NULL. The state advances by 7 (steps + 1) real steps. Errors: MLVS_ERR_ARG,
+ * MLVS_ERR_STATE, MLVS_ERR_OOM, MLVS_ERR_CUDA. */
 mlvs_status mlvs_autotune(mlvs_handle* h, int steps, int* cta_target, float* ms_table);
 
-/* Set the chunking target directly (one of the values mlvs_autotune chooses from, or any
- * other positive CTA count). */
+/* No counterpart in the paper. Set the chunking target directly (one of the values mlvs_autotune
+ * chooses from, or any other positive CTA count). */
 mlvs_status mlvs_set_tuning(mlvs_handle* h, int cta_target);
 
 /* ----------------------------------------------------------------------------------------
@@ -261,24 +262,27 @@ typedef struct mlvs_mlp mlvs_mlp;
 /* Create a network with zero weights; its work is ordered on `stream` (cudaStream_t). */
 mlvs_status mlvs_mlp_create(void* stream, mlvs_mlp** out);
 void mlvs_mlp_destroy(mlvs_mlp* m);
-/* host w[5124]: FP32 master weights (the BF16 copy is their nearest-even rounding); resets
- * the momentum. */
+/* Selector, no counterpart in the paper. host w[5124]: FP32 master weights (the BF16 copy is
+ * their nearest-even rounding); resets the momentum. */
 mlvs_status mlvs_mlp_set_weights(mlvs_mlp* m, const float* w, int n);
-/* host master[5124] and/or bf16_values[5124] (the BF16 weights as floats); either may be NULL. */
+/* Selector, no counterpart in the paper. host master[5124] and/or bf16_values[5124] (the BF16
+ * weights as floats); either may be NULL. */
 mlvs_status mlvs_mlp_get_weights(const mlvs_mlp* m, float* master, float* bf16_values, int n);
-/* device X[n][10] -> device logits[n][4] and/or softmax prob[n][4] (either may be NULL);
- * asynchronous on the network's stream. */
+/* Selector, no counterpart in the paper. device X[n][10] -> device logits[n][4] and/or softmax
+ * prob[n][4] (either may be NULL); asynchronous on the network's stream. */
 mlvs_status mlvs_mlp_forward(mlvs_mlp* m, const float* X, int n, float* logits, float* prob);
-/* Gradient of the mean softmax cross-entropy of device X[n][10], labels y[n] (0..3) into
- * device grad[5124]; *loss (host, may be NULL) receives the loss.  Synchronous.
- * Errors: MLVS_ERR_ARG (a label outside 0..3), MLVS_ERR_OOM, MLVS_ERR_CUDA. */
+/* Selector, no counterpart in the paper. Gradient of the mean softmax cross-entropy of device
+ * X[n][10], labels y[n] (0..3) into device grad[5124]; *loss (host, may be NULL) receives the
+ * loss. Synchronous. Errors: MLVS_ERR_ARG (a label outside 0..3), MLVS_ERR_OOM, MLVS_ERR_CUDA. */
 mlvs_status mlvs_mlp_gradient(mlvs_mlp* m, const float* X, const int* y, int n, float* grad, float* loss);
-/* One SGD step with momentum on the same batch: v = momentum v + grad, w -= lr v (FP32
- * master), BF16 copy refreshed.  *loss (host, may be NULL): the loss before the step. */
+/* Selector, no counterpart in the paper. One SGD step with momentum on the same batch: v =
+ * momentum v + grad, w -= lr v (FP32 master), BF16 copy refreshed. *loss (host, may be NULL):
+ * the loss before the step. */
 mlvs_status mlvs_mlp_train_step(mlvs_mlp* m, const float* X, const int* y, int n, float lr, float momentum,
                                 float* loss);
 
-/* The ten selector features of every cell of one instance (out [ny*nx][10] floats, host or
+/* Selector, no counterpart in the paper (features from the moments of Sec. 2.1).  The ten
+ * selector features of every cell of one instance (out [ny*nx][10] floats, host or
  * device): log rho, u / sqrt(R T_ref), v / sqrt(R T_ref), log(T / T_ref),
  * q / (rho (RT)^1.5) (two), dx |grad rho| / rho, dx |grad T| / T, dx |grad u| / sqrt(RT),
  * log10 Kn_local (lambda = (mu/p) sqrt(pi R T / 2) over L_ref); gradients by central
@@ -286,13 +290,14 @@ mlvs_status mlvs_mlp_train_step(mlvs_mlp* m, const float* X, const int* y, int n
  * dx = min(dx, dy).  Errors: MLVS_ERR_ARG, MLVS_ERR_STATE, MLVS_ERR_CUDA. */
 mlvs_status mlvs_features(mlvs_handle* h, int instance, float* out, int out_on_device);
 
-/* The level the fixed-level-set rule (mlvs_set_velocity_levels, adaptive = 0) gives every cell
- * of one instance from its criterion mask (host levels[ny*nx]); the cells do not move.
- * Errors: as mlvs_criterion. */
+/* Sec. 3.2 masks read with the fixed-level-set rule. The level the fixed-level-set rule
+ * (mlvs_set_velocity_levels, adaptive = 0) gives every cell of one instance from its criterion
+ * mask (host levels[ny*nx]); the cells do not move. Errors: as mlvs_criterion. */
 mlvs_status mlvs_criterion_levels(mlvs_handle* h, int instance, const mlvs_adapt_params* p, int* levels);
 
-/* Fixed-level-set adaptation (adaptive = 0, four levels) with the selector: every cell whose
- * largest softmax probability reaches `confidence` takes the predicted level; the others
+/* Selector, no counterpart in the paper.  Fixed-level-set adaptation (adaptive = 0, four levels)
+ * with the selector: every cell whose largest softmax probability reaches `confidence` takes
+ * the predicted level; the others
  * take the level of the criterion (run on those cells only).  stats->n_distinct receives the
  * number of cells that fell back to the criterion.
  * Errors: MLVS_ERR_ARG (not four levels, adaptive = 1, confidence outside [0, 1]), and as
@@ -300,8 +305,8 @@ mlvs_status mlvs_criterion_levels(mlvs_handle* h, int instance, const mlvs_adapt
 mlvs_status mlvs_adapt_mlp(mlvs_handle* h, mlvs_mlp* m, const mlvs_adapt_params* p, float confidence,
                            mlvs_adapt_stats* stats);
 
-/* Extra: the parent-child consistent coarsening index of a level's space.  *nb_out receives
- * its length (N1*N1 in 2-D, N1 in 1-D); out (capacity cap) may be NULL to query it. */
+/* Extra: the parent-child consistent coarsening index (Sec. 3.2) of a level's space. *nb_out
+ * receives its length (N1*N1 in 2-D, N1 in 1-D); out (capacity cap) may be NULL to query it. */
 mlvs_status mlvs_level_kappa(const mlvs_handle* h, int level, unsigned char* out, int cap,
                              int* nb_out);
 
@@ -318,13 +323,13 @@ enum {
 mlvs_status mlvs_moments(mlvs_handle* h, int instance, unsigned fields, double* out,
                          int out_on_device);
 
-/* Extra (tests): copy the distributions g~, h~ of cells [cell0, cell0+ncells) of one
- * instance to host arrays out_g/out_h laid out [ncells][nv] (nv of the cell's level; all
- * cells in the range must share a level).  *nv_out receives nv. */
+/* No counterpart in the paper (a test accessor). Copy the distributions g~, h~ of cells [cell0,
+ * cell0+ncells) of one instance to host arrays out_g/out_h laid out [ncells][nv] (nv of the
+ * cell's level; all cells in the range must share a level). *nv_out receives nv. */
 mlvs_status mlvs_read_cells(mlvs_handle* h, int instance, int cell0, int ncells,
                             double* out_g, double* out_h, int cap, int* nv_out);
 
-/* Extra: the time step in use. */
+/* Extra: the time step in use (the CFL 0.5 reading of Sec. 4). */
 mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt);
 
 /* Conservative moments without device allocation.  The paper has no counterpart: this entry
@@ -353,10 +358,11 @@ mlvs_status mlvs_moments_noalloc(const float* g, const float* h, int nv, int nce
                                  const float* xi_x, const float* xi_y, const float* w_x,
                                  const float* w_y, double* out, void* stream);
 
-/* Release everything the handle owns.  NULL is allowed. */
+/* No counterpart in the paper.  Release everything the handle owns.  NULL is allowed. */
 void mlvs_destroy(mlvs_handle* h);
 
-/* Diagnostic text of the last failing call on h (or of the last failing create if h is NULL). */
+/* No counterpart in the paper. Diagnostic text of the last failing call on h (or of the last
+ * failing create if h is NULL). */
 const char* mlvs_last_error(const mlvs_handle* h);
 
 #ifdef __cplusplus
