@@ -101,7 +101,8 @@ typedef struct {
                                 mapping and flux mapping launches                            */
 } mlvs_step_stats;
 
-/* Create a handle for the problem in cfg.  No velocity space exists yet.
+/* Create a handle for the problem in cfg (Sec. 2.1-2.2: mesh, gas model, boundaries, initial
+ * state).  No velocity space exists yet.
  * Errors: MLVS_ERR_ARG (bad sizes/kinds), MLVS_ERR_CUDA, MLVS_ERR_OOM. */
 mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out);
 
@@ -259,7 +260,8 @@ mlvs_status mlvs_set_tuning(mlvs_handle* h, int cta_target);
  * -------------------------------------------------------------------------------------- */
 typedef struct mlvs_mlp mlvs_mlp;
 
-/* Create a network with zero weights; its work is ordered on `stream` (cudaStream_t). */
+/* Selector, no counterpart in the paper.  Create a network with zero weights; its work is
+ * ordered on `stream` (cudaStream_t). */
 mlvs_status mlvs_mlp_create(void* stream, mlvs_mlp** out);
 void mlvs_mlp_destroy(mlvs_mlp* m);
 /* Selector, no counterpart in the paper. host w[5124]: FP32 master weights (the BF16 copy is

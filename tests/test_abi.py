@@ -62,3 +62,16 @@ def test_create_rejects_nonpositive_state():
 def test_destroy_null_is_safe():
     from paper_2609_35258_b300 import mlvs
     mlvs.mlvs_destroy(None)
+
+
+def test_every_entry_point_cites_its_passage_or_says_it_has_none():
+    """Each declaration's comment names the section or equation it implements, or says that the
+    paper has no counterpart (utilities, the selector, the allocation-free variant)."""
+    src = open(os.path.join(ROOT, "include", "mlvs.h")).read()
+    missing = []
+    for m in re.finditer(r"/\*((?:(?!\*/).)*)\*/\s*(?:enum\s*\{[^}]*\};\s*/\*((?:(?!\*/).)*)\*/\s*)?"
+                         r"(?:const\s+)?(?:mlvs_status|void|const char\s*\*)\s*\*?\s*(mlvs_[a-z_]+)\s*\(", src, re.S):
+        com = m.group(2) or m.group(1)
+        if not re.search(r"Sec\.|Eqs?\.|counterpart|Not part of the paper", com):
+            missing.append(m.group(3))
+    assert not missing, missing
