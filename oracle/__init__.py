@@ -13,10 +13,10 @@ ascending index order), citing the section / equation it restates:
 * ``mapping``   -- hierarchical projection and moment-constrained mapping (Sec. 3.3.2)
 * ``criterion`` -- contribution / transport criterion and hysteresis (Sec. 3.2)
 * ``cluster``   -- mask decoding, graded distance, greedy clustering, enclosing masks (Sec. 3.2)
-* ``curvi``     -- the DUGKS step on a structured curvilinear mesh (O-grid of the cylinder case, Sec. 4)
+* ``curvi``     -- the DUGKS step on a structured curvilinear mesh (O-grid of the cylinder case, Sec. 4.4)
 * ``mlvs``      -- multi-level step with cross-level faces (Sec. 3.4)
 * ``mlvs_curvi`` -- the multi-level step on a structured curvilinear mesh (Sec. 3.4 on ``curvi``)
-* ``unstructured`` -- the DUGKS step on polygonal cells (the two-cavity case of Sec. 4)
+* ``unstructured`` -- the DUGKS step on polygonal cells (the two-cavity case of Sec. 4.5)
 * ``mlvs_unstructured`` -- the multi-level step on polygonal cells (Sec. 3.4 on ``unstructured``)
 * ``mlp``       -- FP64 reference MLP level selector (not in the paper; used to check gradients)
 

@@ -17,13 +17,15 @@ import numpy as np
 
 
 def graded_distance(ka, kb):
+    """Graded distance between two masks, Sec. 3.2 (the equation after the kappa definition)."""
     ka = np.asarray(ka).ravel()
     kb = np.asarray(kb).ravel()
     return float(np.sum(np.abs(ka.astype(np.int64) - kb.astype(np.int64)))) / (3.0 * ka.size)
 
 
 def cluster(kappas, tau):
-    """kappas: [ncell, Nb] integer array.  Returns (labels [ncell], reps [ncluster, Nb])."""
+    """kappas: [ncell, Nb] integer array.  Returns (labels [ncell], reps [ncluster, Nb]).
+    Sec. 3.2, Eq. kappa_rep."""
     K = np.asarray(kappas, dtype=np.int64)
     ncell = K.shape[0]
     uniq, inv, counts = np.unique(K, axis=0, return_inverse=True, return_counts=True)

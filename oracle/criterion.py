@@ -46,7 +46,9 @@ def _m_vectors(g, h, xs):
 
 
 def criterion_2d(g, h, base, kappa_prev, C_split, C_merge, eps_merge=None, max_level=3):
-    """kappa (per level-1 block, [N1, N1] = [by, bx]) for one cell from base-grid (g, h) [ny, nx]."""
+    """kappa (per level-1 block, [N1, N1] = [by, bx]) for one cell from base-grid (g, h) [ny, nx].
+    Sec. 3.2, Eqs. block-contribution-indicator, block-hysteresis-rule, merge-transport-error,
+    combined-merge-condition."""
     n = base.n
     M1, M2 = _contrib(g, h, base)
     groups = {L: vspace.axis_groups(n, L) for L in range(1, max_level + 1)}
@@ -128,5 +130,5 @@ def criterion_2d(g, h, base, kappa_prev, C_split, C_merge, eps_merge=None, max_l
 
 
 def kappa_min(kappa):
-    """min over blocks: the coarsest uniform level that encloses the requirement."""
+    """min over blocks: the coarsest uniform level that encloses the requirement.  Sec. 3.2."""
     return int(np.min(kappa))

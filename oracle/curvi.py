@@ -38,6 +38,8 @@ from .kinetic import Gas, compat_correct4, maxwell_gh
 
 @dataclass
 class CurviMesh:
+    """Structured curvilinear mesh of the cylinder case (Sec. 4.4): nodes, side kinds, wall and
+    freestream states."""
     X: np.ndarray            # [ny+1][nx+1] node x
     Y: np.ndarray            # [ny+1][nx+1] node y
     bc: tuple                # x-low (i = 0), x-high (i = nx), y-low (j = 0), y-high (j = ny)
@@ -54,7 +56,8 @@ class CurviMesh:
 
 
 def geometry(mesh: CurviMesh):
-    """Cell areas, centroids and J^{-T}; face normals, lengths and midpoints."""
+    """Cell areas, centroids and J^{-T}; face normals, lengths and midpoints.
+    Face lengths and normals of Eq. explicit_update, offsets and J^{-T} of Eq. reconstruction."""
     X, Y = mesh.X, mesh.Y
     A = np.stack([X[:-1, :-1], Y[:-1, :-1]], -1)
     B = np.stack([X[:-1, 1:], Y[:-1, 1:]], -1)
@@ -91,6 +94,7 @@ def geometry(mesh: CurviMesh):
 
 
 def time_step(mesh: CurviMesh, xi, cfl):
+    """Time step: the reading of 'CFL = 0.5' (Sec. 4) with the cell width area / longest face."""
     G = geometry(mesh)
     longest = np.maximum(np.maximum(G["li"][:, :-1], G["li"][:, 1:]), np.maximum(G["lj"][:-1, :], G["lj"][1:, :]))
     L = np.min(G["area"] / longest)
@@ -108,7 +112,8 @@ def _pad_cells(a, mesh: CurviMesh):
 
 def period_shifts(mesh: CurviMesh):
     """Translation of the periodic image across the x and the y sides (node column nx minus
-    column 0, node row ny minus row 0, averaged; zero on an O-grid)."""
+    column 0, node row ny minus row 0, averaged; zero on an O-grid).
+    Periodic images of Eq. reconstruction."""
     sx = np.array([np.mean(mesh.X[:, -1] - mesh.X[:, 0]), np.mean(mesh.Y[:, -1] - mesh.Y[:, 0])])
     sy = np.array([np.mean(mesh.X[-1, :] - mesh.X[0, :]), np.mean(mesh.Y[-1, :] - mesh.Y[0, :])])
     return sx, sy
@@ -137,7 +142,8 @@ def _ghost_centroids(G, mesh: CurviMesh):
 
 
 def step(gt, ht, mesh: CurviMesh, xi, w, gas: Gas, dt: float, opt: Options = Options()):
-    """Advance (g~, h~) [ny][nx][Nv] by one time step on the curvilinear mesh."""
+    """Advance (g~, h~) [ny][nx][Nv] by one time step on the curvilinear mesh.
+    Sec. 2.2 on curvilinear cells."""
     s = 0.5 * dt
     ny, nx, nv = gt.shape
     G = geometry(mesh)
@@ -230,7 +236,8 @@ def ogrid(ntheta, nr, r_in=1.0, r_out=11.0):
     """O-grid nodes around a cylinder of radius r_in: ntheta cells around (periodic in i,
     i running clockwise so that cells are counter-clockwise with j outward), nr cells out to
     r_out with geometric stretching; the first cell height is r_in * 2 pi / ntheta (cells of
-    aspect ratio one at the wall).  Returns X, Y of shape [nr+1][ntheta+1]."""
+    aspect ratio one at the wall).  Returns X, Y of shape [nr+1][ntheta+1].
+    The cylinder case of Sec. 4.4."""
     h0 = r_in * 2.0 * np.pi / ntheta
     # ratio q with h0 (q^nr - 1)/(q - 1) = r_out - r_in, by bisection
     lo, hi = 1.0 + 1e-12, 2.0

@@ -47,6 +47,8 @@ PERIODIC, ZEROGRAD, WALL, FREE = "periodic", "zerograd", "wall", "freestream"
 
 @dataclass
 class Mesh:
+    """Structured Cartesian mesh of Sec. 2.2 with the boundary kinds and wall / freestream states
+    of the readings above."""
     nx: int
     ny: int
     dx: float
@@ -61,6 +63,8 @@ class Mesh:
 
 @dataclass
 class Options:
+    """Switches of the step: compatibility correction (Sec. 3.3.1), inter-level mapping (Sec.
+    3.3.2), limiter (Sec. 2.2)."""
     cfl: float = 0.5
     compat_cell: bool = True
     compat_face: bool = True
@@ -119,6 +123,7 @@ def initial_tilde(rho, u, T, xi, w, gas: Gas, compat: bool = True):
     """phi~ at t = 0 for a gas at rest in local equilibrium: phi~ = phi^eq (Omega = 0).
 
     With compat the Maxwellian is corrected so its discrete moments equal (rho, u, T).
+    Sec. 2.2 with Omega = 0 at t = 0; Sec. 3.3.1.
     """
     geq, heq = maxwell_gh(rho, u, T, xi, gas)
     if compat:
@@ -157,7 +162,8 @@ def _face_model_phi(gb, hb, xi, w, gas: Gas, s: float, compat: bool, nmom: int =
 
 
 def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options()):
-    """Advance (g~, h~) by one time step.  Returns (g~^{n+1}, h~^{n+1}, cell state at t_n)."""
+    """Advance (g~, h~) by one time step.  Returns (g~^{n+1}, h~^{n+1}, cell state at t_n).
+    Sec. 2.2, Eqs. phi_update ... recover_phi."""
     D = gas.D
     s = 0.5 * dt
     ny, nx, nv = gt.shape
@@ -305,6 +311,7 @@ def step(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, opt: Options = Options(
 
 
 def run(gt, ht, mesh: Mesh, xi, w, gas: Gas, dt: float, nsteps: int, opt: Options = Options()):
+    """N steps of `step` (Sec. 2.2)."""
     for _ in range(nsteps):
         gt, ht, _ = step(gt, ht, mesh, xi, w, gas, dt, opt)
     return gt, ht

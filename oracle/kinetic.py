@@ -169,7 +169,8 @@ def compat_correct8(gS, hS, rho, u, T, q_tar, xi, w, gas: Gas):
 
 
 def conserved(g, h, xi, w):
-    """The collision-invariant moments (rho, rho u, rho E) stacked on the last axis."""
+    """The collision-invariant moments (rho, rho u, rho E) stacked on the last axis.
+    Eq. discrete_W."""
     rho = np.sum(w * g, axis=-1)
     mom = np.einsum("...v,vd->...d", w * g, xi)
     xi2 = np.sum(xi * xi, axis=-1)

@@ -28,7 +28,8 @@ from .kinetic import Gas, maxwell_gh, moments
 
 
 def projection_matrix(src, dst) -> np.ndarray:
-    """Dense (Nt x Ns) matrix of P_{s->t}: rows average (coarsen) or pick (refine)."""
+    """Dense (Nt x Ns) matrix of P_{s->t}: rows average (coarsen) or pick (refine).
+    Eq. hierarchical_projection_operator."""
     P = np.zeros((dst.nv, src.nv))
     for i in range(dst.nv):
         r = dst.rect[i]
@@ -176,7 +177,8 @@ def forced_conservation(gp, hp, g_src, h_src, src, dst, gas: Gas):
 
 
 def raw9(g, h, space):
-    """The nine raw target moments (rho, rho u, rho v, rho E, Gxx, Gyy, Gxy, Jx, Jy) (2-D)."""
+    """The nine raw target moments (rho, rho u, rho v, rho E, Gxx, Gyy, Gxy, Jx, Jy) (2-D).
+    Eqs. source_second_raw_moments, source_energy_flux_moments."""
     xi, w = space.xi, space.w
     x, y = xi[:, 0], xi[:, 1]
     xi2 = x * x + y * y
@@ -213,5 +215,7 @@ def correct9(gp, hp, M_tar, space):
 
 
 def map9(g, h, src, dst):
+    """Projection plus the nine-moment correction with the source's raw moments as targets (Sec.
+    3.3.2)."""
     gp, hp = project(g, h, src, dst)
     return correct9(gp, hp, raw9(g, h, src), dst)

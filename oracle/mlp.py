@@ -34,6 +34,7 @@ N_PARAM = sum(int(np.prod(s)) for _, s in SIZES)
 
 
 def unpack(w):
+    """Parameter vector to named arrays (selector; no counterpart in the paper)."""
     out, o = {}, 0
     for name, shape in SIZES:
         n = int(np.prod(shape))
@@ -43,11 +44,13 @@ def unpack(w):
 
 
 def pack(p):
+    """Named arrays to the parameter vector (selector; no counterpart in the paper)."""
     return np.concatenate([np.asarray(p[name], dtype=np.float64).ravel() for name, _ in SIZES])
 
 
 def bf16_round(x):
-    """Round to the nearest BF16 value (ties to even), returned as float64."""
+    """Round to the nearest BF16 value (ties to even), returned as float64.
+    Selector; no counterpart in the paper."""
     f = np.asarray(x, dtype=np.float32)
     u = f.view(np.uint32).astype(np.uint64)
     u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
@@ -55,7 +58,8 @@ def bf16_round(x):
 
 
 def init_weights(seed):
-    """He-uniform weights, zero biases (a fixed recipe shared with the tests)."""
+    """He-uniform weights, zero biases (a fixed recipe shared with the tests).
+    Selector; no counterpart in the paper."""
     rng = np.random.default_rng(seed)
     p = {}
     for name, shape in SIZES:
@@ -68,7 +72,8 @@ def init_weights(seed):
 
 
 def forward(w, X):
-    """Activations of a batch X [n][10]: (z1, h1, z2, h2, logits)."""
+    """Activations of a batch X [n][10]: (z1, h1, z2, h2, logits).
+    Selector; no counterpart in the paper."""
     p = unpack(w)
     z1 = X @ p["W1"].T + p["b1"]
     h1 = np.maximum(z1, 0.0)
@@ -79,13 +84,15 @@ def forward(w, X):
 
 
 def softmax(logits):
+    """Row-wise softmax of the logits (selector; no counterpart in the paper)."""
     m = logits - np.max(logits, axis=1, keepdims=True)
     e = np.exp(m)
     return e / np.sum(e, axis=1, keepdims=True)
 
 
 def loss_and_grad(w, X, y):
-    """Mean softmax cross-entropy over the batch and its gradient with respect to w."""
+    """Mean softmax cross-entropy over the batch and its gradient with respect to w.
+    Selector; no counterpart in the paper."""
     n = X.shape[0]
     p = unpack(w)
     z1, h1, z2, h2, logits = forward(w, X)
@@ -105,13 +112,14 @@ def loss_and_grad(w, X, y):
 
 
 def sgd_momentum(w, v, grad, lr, mu):
-    """v <- mu v + grad;  w <- w - lr v."""
+    """v <- mu v + grad;  w <- w - lr v.  (selector; no counterpart in the paper)."""
     v = mu * v + grad
     return w - lr * v, v
 
 
 def features(rho, u, v, T, qx, qy, dx, dy, periodic_x, periodic_y, R, T_ref, mu_ref, omega, L_ref=1.0):
-    """The ten features of every cell of a [ny][nx] mesh, returned as [ny*nx][10]."""
+    """The ten features of every cell of a [ny][nx] mesh, returned as [ny*nx][10].
+    Selector, no counterpart in the paper; moments of Sec. 2.1."""
     def ddx(f):
         if periodic_x:
             fp, fm = np.roll(f, -1, axis=1), np.roll(f, 1, axis=1)
@@ -149,7 +157,8 @@ def features_curvi(rho, u, v, T, qx, qy, Jt, width, periodic_x, periodic_y, R, T
     """The same features on a structured curvilinear mesh: gradients from central differences
     along the index directions (neighbours wrapped or clamped) turned physical with the cell's
     J^{-T} [ny][nx][4] (row-major), and the cell width |V| / max |S| [ny][nx] for dx.  On a
-    Cartesian mesh this is `features`."""
+    Cartesian mesh this is `features`.
+    Selector, no counterpart in the paper; moments of Sec. 2.1."""
     def d_i(f):
         if periodic_x:
             fp, fm = np.roll(f, -1, axis=1), np.roll(f, 1, axis=1)

@@ -23,7 +23,8 @@ from .dugks import FREE, PERIODIC, WALL
 
 
 class SpaceBook:
-    """Spaces keyed by their kappa array (uniform level L == kappa identically L)."""
+    """Spaces keyed by their kappa array (uniform level L == kappa identically L).
+    The representative spaces of Sec. 3.2 and the common refinement of Sec. 3.4."""
 
     def __init__(self, base):
         self.base = base
@@ -58,7 +59,7 @@ class SpaceBook:
 
 
 class MLVSState:
-    """Cells [ny][nx] (flat index j*nx+i), each with a space key and (g~, h~) on it."""
+    """Cells [ny][nx] (flat index j*nx+i), each with a space key and (g~, h~) on it.  Sec. 3.4."""
 
     def __init__(self, mesh, gas, book, space_of_cell, g, h, dt, opt):
         self.mesh, self.gas, self.book = mesh, gas, book
@@ -110,6 +111,7 @@ def _cell_index(mesh, j, i):
 
 
 def step(st: MLVSState):
+    """One multi-level step: Sec. 3.4 on the step of Sec. 2.2."""
     mesh, gas, book, dt, opt = st.mesh, st.gas, st.book, st.dt, st.opt
     D = gas.D
     s = 0.5 * dt

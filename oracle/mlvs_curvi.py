@@ -25,7 +25,8 @@ from .mlvs import MLVSState, _cell_index
 
 
 def step(st: MLVSState):
-    """Advance every cell of st (whose mesh is a `curvi.CurviMesh`) by one time step."""
+    """Advance every cell of st (whose mesh is a `curvi.CurviMesh`) by one time step.
+    Sec. 3.4 on the curvilinear step."""
     mesh, gas, book, dt, opt = st.mesh, st.gas, st.book, st.dt, st.opt
     s = 0.5 * dt
     nx, ny = mesh.nx, mesh.ny

@@ -60,7 +60,8 @@ def _gradient(c, vals, mesh, G, limiter):
 
 
 def step(st: MLVSState, limiter: str = "venkat"):
-    """Advance every cell of st (whose mesh is an `unstructured.UMesh`) by one time step."""
+    """Advance every cell of st (whose mesh is an `unstructured.UMesh`) by one time step.
+    Sec. 3.4 on the unstructured step."""
     mesh, gas, book, dt, opt = st.mesh, st.gas, st.book, st.dt, st.opt
     s = 0.5 * dt
     G = geometry(mesh)

@@ -34,6 +34,7 @@ from .kinetic import Gas, maxwell_gh
 
 @dataclass
 class UMesh:
+    """Polygonal cells of the two-cavity case (Sec. 4.5) with wall indices and wall states."""
     nodes: np.ndarray                 # (Nn, 2)
     cells: list                       # counter-clockwise node index tuples
     wall_of: object = None            # boundary face midpoint (2,) -> wall index (default 0)
@@ -47,7 +48,8 @@ class UMesh:
 
 def geometry(mesh: UMesh):
     """Areas, centroids, faces (L, R, unit normal out of L, length, midpoint, wall index) and
-    every cell's faces with the sign of its outward normal.  Cached on the mesh."""
+    every cell's faces with the sign of its outward normal.  Cached on the mesh.
+    (face lengths and normals of Eq. explicit_update)."""
     if mesh.geo is not None:
         return mesh.geo
     X = mesh.nodes
@@ -92,6 +94,7 @@ def geometry(mesh: UMesh):
 
 
 def time_step(mesh: UMesh, xi, cfl):
+    """Time step: the reading of 'CFL = 0.5' (Sec. 4) with the cell width area / longest face."""
     G = geometry(mesh)
     longest = np.zeros(mesh.ncell)
     for c, fs in enumerate(G["cell_faces"]):
@@ -138,7 +141,8 @@ def _gradients(P, mesh: UMesh, limiter: str):
 
 
 def step(gt, ht, mesh: UMesh, xi, w, gas: Gas, dt: float, opt: Options = Options(), limiter: str = "venkat"):
-    """Advance (g~, h~) (Nc, Nv) by one time step on the unstructured mesh."""
+    """Advance (g~, h~) (Nc, Nv) by one time step on the unstructured mesh.
+    Sec. 2.2 on polygonal cells."""
     s = 0.5 * dt
     G = geometry(mesh)
     st = cell_state(gt, ht, xi, w, gas, dt)

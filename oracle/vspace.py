@@ -94,6 +94,7 @@ class Space:
     w    (Nv,)     quadrature weights (sums of the covered base weights)
     rect (Nv, 2D)  covered base index ranges [x0, x1) (and [y0, y1))
     owner          base-shaped array: index of the cell covering each base node
+    Secs. 3.1-3.2.
     """
     xi: np.ndarray
     w: np.ndarray
@@ -138,14 +139,16 @@ def uniform_space(base: Base, L: int) -> Space:
 
 
 def aniso_space(base: Base, Lx: int, Ly: int) -> Space:
-    """Tensor-product space with the x axis grouped at level Lx and the y axis at Ly (2-D)."""
+    """Tensor-product space with the x axis grouped at level Lx and the y axis at Ly (2-D).
+    (the projection sequence of Sec. 4.1.2)."""
     gx, gy = axis_groups(base.n, Lx), axis_groups(base.n, Ly)
     rect = np.array([(a[0], a[-1] + 1, b[0], b[-1] + 1) for b in gy for a in gx], dtype=np.int64)
     return space_from_rects(base, rect)
 
 
 def level1_parent_maps(n: int, max_level: int = 3):
-    """For each level L (1..max_level) the level-L group index of every level-1 group."""
+    """For each level L (1..max_level) the level-L group index of every level-1 group.
+    (the quadtree of Sec. 3.2)."""
     g1 = axis_groups(n, 1)
     maps = {1: np.arange(len(g1))}
     for L in range(2, max_level + 1):
@@ -266,5 +269,6 @@ def space_from_rects(base: Base, rect: np.ndarray) -> Space:
 
 
 def make_base(n: int, umin: float, umax: float, D: int = 2, rule: str = "boole") -> Base:
+    """Base grid of Sec. 2.3: Newton-Cotes nodes and weights per axis, their tensor product in 2-D."""
     x, w = newton_cotes_1d(n, umin, umax, rule)
     return Base(x, w, D)
