@@ -1,6 +1,7 @@
 """Every public function and class of the oracle names the passage of the paper it follows
 (a section, an equation, a table or an algorithm), the reading it takes where the paper is
-silent, or says that it has no counterpart in the paper (the selector).  Every module's header says that it is test infrastructure."""
+silent, or says that it has no counterpart in the paper (the selector).  Every module's header
+says that it is test infrastructure."""
 import ast
 import os
 import re
