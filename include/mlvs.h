@@ -213,6 +213,38 @@ mlvs_status mlvs_space_points(int n_base, double umin, double umax, int quadratu
 mlvs_status mlvs_mesh_geometry(int nx, int ny, int periodic_x, int periodic_y, const double* node_xy,
                                double* cell_geo, double* face_geo, double* width);
 
+/* Host-only: the geometry of an unstructured mesh of polygonal cells, what the update of
+ * Eq. explicit_update and the reconstruction of Eq. reconstruction need on general polygons
+ * (the two-cavity expansion of Sec. 4.5 runs on unstructured cells).  node_xy[n_node][2];
+ * cell c has the counter-clockwise nodes cell_nodes[cell_ptr[c] .. cell_ptr[c + 1]) (at least
+ * three; cell_ptr[0] = 0).  A face is an edge used by one cell (boundary) or by two cells in
+ * opposite directions; faces are numbered in the order of (smaller node, larger node); L is
+ * the lower-numbered cell using the edge and the unit normal points out of L.  Outputs, all
+ * NULL to get *n_face only, else all given (caller-owned, host memory):
+ *   cell_geo[7][n_cell]: area, centroid x, y, width (area over the longest edge), and the
+ *     inverse of the least-squares normal matrix sum d d^T (xx, xy, yy), d the centroid across
+ *     each face minus the cell's, or twice the face midpoint minus the centroid on a boundary
+ *     face (the cell reflected through the face);
+ *   cell_face[cell_ptr[n_cell]]: per cell, in the order of its edges, f when the cell is L
+ *     of face f and -f - 1 when it is R;
+ *   face_cells[2][face_cap]: L, then R (-1 on a boundary face), rows face_cap apart;
+ *   face_nodes[2][face_cap]: the edge's nodes in L's direction of traversal;
+ *   face_geo[5][face_cap]: unit normal x, y, length, midpoint x, y.
+ * Needs no GPU.  Errors: MLVS_ERR_ARG (null pointers, a node index out of range, a cell with
+ * fewer than three nodes or with area <= 0, an edge used by more than two cells or twice in
+ * the same direction, a singular normal matrix, face_cap below the face count). */
+mlvs_status mlvs_umesh_geometry(int n_node, const double* node_xy, int n_cell, const int* cell_ptr,
+                                const int* cell_nodes, int face_cap, int* n_face, double* cell_geo,
+                                int* cell_face, int* face_cells, int* face_nodes, double* face_geo);
+
+/* Host-only, no counterpart in the paper (data layout): a cell order along a Hilbert curve
+ * through the bounding box of the centroids cx[n_cell], cy[n_cell] (16 bits per axis), so
+ * that consecutive cells are spatially compact when the cells are renumbered in this order.
+ * order[k] receives the cell visited k-th (caller-owned, n_cell entries); cells on the same
+ * curve position keep their order.  Needs no GPU.
+ * Errors: MLVS_ERR_ARG (null pointers, n_cell < 1, a non-finite centroid). */
+mlvs_status mlvs_umesh_order(int n_cell, const double* cx, const double* cy, int* order);
+
 /* Host-only grouping of nrow masks of nb bytes each (Sec. 3.2): distinct masks by decreasing
  * frequency (ties: lexicographic order), each joins the nearest existing centre when the
  * graded distance sum|ka - kb| / (3 nb) is <= tau (ties: lowest cluster), else it seeds a new

@@ -102,28 +102,44 @@ def time_step(mesh: UMesh, xi, cfl):
     return cfl * np.min(G["area"] / longest) / np.max(np.abs(xi))
 
 
+def _offsets(G, c):
+    """(face, cell across or -1, d) per face of cell c: d the offset of the centroid across
+    the face, or on a boundary face of the centroid reflected through the face midpoint."""
+    cen = G["cen"]
+    out = []
+    for f, sgn in G["cell_faces"][c]:
+        o = G["fR"][f] if sgn > 0 else G["fL"][f]
+        d = cen[o] - cen[c] if o >= 0 else 2.0 * (G["fb"][f] - cen[c])
+        out.append((f, o, d))
+    return out
+
+
+def ls_normal_matrix(mesh: UMesh):
+    """Normal matrices sum d d^T (Nc, 2, 2) of the least-squares gradients of Eq.
+    reconstruction on polygons (the reading in the module header)."""
+    G = geometry(mesh)
+    M = np.zeros((mesh.ncell, 2, 2))
+    for c in range(mesh.ncell):
+        for _, _, d in _offsets(G, c):
+            M[c] += np.outer(d, d)
+    return M
+
+
 def _gradients(P, mesh: UMesh, limiter: str):
     """Least-squares gradient (Nc, Nv, 2) of P (Nc, Nv), limited per velocity."""
     G = geometry(mesh)
     cen = G["cen"]
     nc, nv = P.shape
     grad = np.zeros((nc, nv, 2))
+    Ms = ls_normal_matrix(mesh)
     for c, fs in enumerate(G["cell_faces"]):
-        M = np.zeros((2, 2))
         rhs = np.zeros((nv, 2))
         nb = []
-        for f, sgn in fs:
-            o = G["fR"][f] if sgn > 0 else G["fL"][f]
-            if o >= 0:
-                d = cen[o] - cen[c]
-                du = P[o] - P[c]
+        for f, o, d in _offsets(G, c):
+            if o >= 0:                                       # a boundary ghost copies the cell: du = 0
+                rhs += (P[o] - P[c])[:, None] * d[None, :]
                 nb.append(P[o])
-            else:
-                d = 2.0 * (G["fb"][f] - cen[c])             # the reflected ghost, a copy of the cell
-                du = np.zeros(nv)
-            M += np.outer(d, d)
-            rhs += du[:, None] * d[None, :]
-        g = np.linalg.solve(M, rhs.T).T                      # (Nv, 2)
+        g = np.linalg.solve(Ms[c], rhs.T).T                  # (Nv, 2)
         if limiter == "venkat":
             umax = np.max(np.stack(nb + [P[c]]), axis=0) - P[c]
             umin = np.min(np.stack(nb + [P[c]]), axis=0) - P[c]

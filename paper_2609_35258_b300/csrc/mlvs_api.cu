@@ -43,6 +43,7 @@
 #include "features.cuh"
 #include "cluster_host.hpp"
 #include "vspace_host.hpp"
+#include "umesh_host.hpp"
 
 using namespace mlvs;
 
@@ -2028,6 +2029,43 @@ extern "C" mlvs_status mlvs_cluster(const unsigned char* kappa, long nrow, int n
   if ((int)C.reps.size() > reps_cap) return fail(nullptr, MLVS_ERR_ARG, "mlvs_cluster: reps_cap too small");
   for (long r = 0; r < nrow; ++r) labels[r] = C.labels[r];
   for (size_t c = 0; c < C.reps.size(); ++c) std::memcpy(reps + c * nb, C.reps[c].data(), nb);
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_umesh_geometry(int n_node, const double* node_xy, int n_cell, const int* cell_ptr,
+                                           const int* cell_nodes, int face_cap, int* n_face,
+                                           double* cell_geo, int* cell_face, int* face_cells,
+                                           int* face_nodes, double* face_geo) {
+  if (!node_xy || !cell_ptr || !cell_nodes || !n_face || n_node < 3 || n_cell < 1)
+    return fail(nullptr, MLVS_ERR_ARG, "mlvs_umesh_geometry: bad argument");
+  UMeshGeo g;
+  const std::string why = build_umesh(n_node, node_xy, n_cell, cell_ptr, cell_nodes, g);
+  if (!why.empty()) return fail(nullptr, MLVS_ERR_ARG, "mlvs_umesh_geometry: " + why);
+  const int nf = (int)g.fL.size();
+  *n_face = nf;
+  if (!cell_geo && !cell_face && !face_cells && !face_nodes && !face_geo) return MLVS_OK;
+  if (!cell_geo || !cell_face || !face_cells || !face_nodes || !face_geo)
+    return fail(nullptr, MLVS_ERR_ARG, "mlvs_umesh_geometry: outputs must be all given or all NULL");
+  if (face_cap < nf) return fail(nullptr, MLVS_ERR_ARG, "mlvs_umesh_geometry: face_cap too small");
+  const size_t nc = n_cell;
+  const std::vector<double>* crow[7] = {&g.area, &g.cx, &g.cy, &g.width, &g.mxx, &g.mxy, &g.myy};
+  for (int r = 0; r < 7; ++r) std::memcpy(cell_geo + r * nc, crow[r]->data(), nc * sizeof(double));
+  std::memcpy(cell_face, g.cf.data(), g.cf.size() * sizeof(int));
+  std::memcpy(face_cells, g.fL.data(), nf * sizeof(int));
+  std::memcpy(face_cells + nf, g.fR.data(), nf * sizeof(int));
+  std::memcpy(face_nodes, g.fn0.data(), nf * sizeof(int));
+  std::memcpy(face_nodes + nf, g.fn1.data(), nf * sizeof(int));
+  const std::vector<double>* frow[5] = {&g.nx, &g.ny, &g.len, &g.midx, &g.midy};
+  for (int r = 0; r < 5; ++r) std::memcpy(face_geo + (size_t)r * nf, frow[r]->data(), nf * sizeof(double));
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_umesh_order(int n_cell, const double* cx, const double* cy, int* order) {
+  if (!cx || !cy || !order || n_cell < 1) return fail(nullptr, MLVS_ERR_ARG, "mlvs_umesh_order: bad argument");
+  for (int i = 0; i < n_cell; ++i)
+    if (!std::isfinite(cx[i]) || !std::isfinite(cy[i]))
+      return fail(nullptr, MLVS_ERR_ARG, "mlvs_umesh_order: non-finite centroid");
+  hilbert_order(n_cell, cx, cy, order);
   return MLVS_OK;
 }
 

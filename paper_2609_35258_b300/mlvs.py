@@ -86,6 +86,10 @@ def _load():
         "mlvs_level_kappa": (C.c_int, [H, C.c_int, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
         "mlvs_mesh_geometry": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
                                          C.c_void_p, C.c_void_p]),
+        "mlvs_umesh_geometry": (C.c_int, [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                                          C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]),
+        "mlvs_umesh_order": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
         "mlvs_space_points": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int)]),
@@ -266,6 +270,39 @@ def mlvs_mesh_geometry(node_xy, periodic_x, periodic_y):
     _check(_lib.mlvs_mesh_geometry(nx, ny, int(bool(periodic_x)), int(bool(periodic_y)), xy.ctypes.data,
                                    cg.ctypes.data, fg.ctypes.data, wd.ctypes.data), None)
     return cg, fg, wd
+
+
+def mlvs_umesh_geometry(node_xy, cells):
+    """Host-only: geometry of an unstructured mesh (nodes [Nn][2], cells as counter-clockwise
+    node lists) as a dict: cell rows area, cx, cy, width, mxx, mxy, myy (inverse least-squares
+    normal matrix); cell_ptr, cell_face (f, or -f - 1 where the cell is R); per face L, R, n0,
+    n1, nx, ny, length, midx, midy."""
+    xy = np.ascontiguousarray(node_xy, dtype=np.float64)
+    ptr = np.zeros(len(cells) + 1, dtype=np.int32)
+    ptr[1:] = np.cumsum([len(c) for c in cells])
+    nodes = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in cells]))
+    nc = len(cells)
+    nf = C.c_int()
+    args = (xy.shape[0], xy.ctypes.data, nc, ptr.ctypes.data, nodes.ctypes.data)
+    _check(_lib.mlvs_umesh_geometry(*args, 0, C.byref(nf), None, None, None, None, None), None)
+    m = nf.value
+    cg, cf = np.zeros((7, nc)), np.zeros(int(ptr[-1]), dtype=np.int32)
+    fc, fnd, fg = np.zeros((2, m), dtype=np.int32), np.zeros((2, m), dtype=np.int32), np.zeros((5, m))
+    _check(_lib.mlvs_umesh_geometry(*args, m, C.byref(nf), cg.ctypes.data, cf.ctypes.data, fc.ctypes.data,
+                                    fnd.ctypes.data, fg.ctypes.data), None)
+    out = dict(zip(("area", "cx", "cy", "width", "mxx", "mxy", "myy"), cg))
+    out.update(cell_ptr=ptr, cell_face=cf, L=fc[0], R=fc[1], n0=fnd[0], n1=fnd[1])
+    out.update(zip(("nx", "ny", "length", "midx", "midy"), fg))
+    return out
+
+
+def mlvs_umesh_order(cx, cy):
+    """Host-only: the cells in the order of a Hilbert curve through their centroids."""
+    x = np.ascontiguousarray(cx, dtype=np.float64)
+    y = np.ascontiguousarray(cy, dtype=np.float64)
+    order = np.zeros(x.size, dtype=np.int32)
+    _check(_lib.mlvs_umesh_order(x.size, x.ctypes.data, y.ctypes.data, order.ctypes.data), None)
+    return order
 
 
 def mlvs_space_points(n_base, umin, umax, quadrature, kappa):
