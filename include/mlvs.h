@@ -47,8 +47,8 @@ enum { MLVS_BC_PERIODIC = 0, MLVS_BC_ZEROGRAD = 1, MLVS_BC_WALL = 2, MLVS_BC_FRE
 enum { MLVS_F64 = 0, MLVS_F32 = 1, MLVS_BF16 = 2 };
 /* Newton--Cotes rule of the base grid (Sec. 2.3; the order is not named in the paper) */
 enum { MLVS_QUAD_BOOLE = 0, MLVS_QUAD_SIMPSON = 1, MLVS_QUAD_TRAPZ = 2 };
-/* slope limiter of Eq. reconstruction */
-enum { MLVS_LIMITER_VANLEER = 0, MLVS_LIMITER_NONE = 1 };
+/* slope limiter of Eq. reconstruction (Venkatakrishnan: unstructured meshes only) */
+enum { MLVS_LIMITER_VANLEER = 0, MLVS_LIMITER_NONE = 1, MLVS_LIMITER_VENKAT = 2 };
 
 typedef struct {
   int dim;              /* velocity/space dimension D: 1 or 2 (Sec. 2.1)                      */
@@ -391,6 +391,61 @@ mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt);
 mlvs_status mlvs_moments_noalloc(const float* g, const float* h, int nv, int ncell,
                                  const float* xi_x, const float* xi_y, const float* w_x,
                                  const float* w_y, double* out, void* stream);
+
+/* ---- Unstructured meshes of polygonal cells, one velocity space ----
+ * The DUGKS step of Sec. 2.2 on general polygons (the two-cavity expansion of Sec. 4.5 runs on
+ * unstructured cells): Eq. explicit_update with each face's length and outward normal, Eq.
+ * reconstruction with a least-squares gradient per cell and velocity (a boundary face adds the
+ * cell reflected through it, a zero difference) limited by Venkatakrishnan's function with
+ * eps^2 = (K h)^3 P_c^2, K = 1, h = sqrt(area), P_c the cell's value; every boundary face is a
+ * diffuse isothermal wall. */
+typedef struct mlvs_uhandle mlvs_uhandle;
+
+typedef struct {
+  int storage;          /* MLVS_F64 | MLVS_F32: storage and compute type                     */
+  double R, K_internal, Pr, omega, mu_ref, T_ref;  /* gas; mu = mu_ref (T/T_ref)^omega, mu_ref > 0 */
+  double cfl;           /* dt = cfl * min over cells (area / longest edge) / max |xi|_inf      */
+  double dt;            /* > 0: fixed time step instead                                      */
+  int compat_cell;      /* 1: four-moment compatibility correction at cells (Sec. 3.3.1)      */
+  int compat_face;      /* 1: the same correction of the face model distribution              */
+  int limiter;          /* MLVS_LIMITER_VENKAT | MLVS_LIMITER_NONE                            */
+  int n_base;           /* velocity space: the n_base x n_base tensor product (Sec. 2.3)      */
+  double umin, umax;    /* on [umin, umax]^2                                                  */
+  int quadrature;       /* MLVS_QUAD_*                                                        */
+  int n_wall;           /* walls named by edge_wall, 1..8                                     */
+  double wall[8][3];    /* (u_w, v_w, T_w) of each wall                                       */
+  int vpc;              /* velocities per chunk of the moment sums (0: 64)                    */
+  void* stream;         /* cudaStream_t the handle orders its work on                         */
+} mlvs_uconfig;
+
+/* Sec. 2.2 on polygons; the two-cavity case of Sec. 4.5.  Create a handle on the mesh of
+ * mlvs_umesh_geometry (node_xy[n_node][2], counter-clockwise cells in CSR cell_ptr /
+ * cell_nodes) with the initial state phi~ = the Maxwellian of init_W[n_cell][4] = (rho, u, v, T),
+ * corrected as compat_cell says.  edge_wall[cell_ptr[n_cell]] (NULL: all 0) names the wall of
+ * every boundary edge, in the order of cell_nodes (entries of interior edges are ignored).  All
+ * inputs are copied.  Device memory: about (8 n_cell + 4 n_face) x nv values of the storage type.
+ * Errors: MLVS_ERR_ARG (any defect mlvs_umesh_geometry reports, bad gas constants or space, a
+ * boundary edge naming no wall, non-positive initial density or temperature), MLVS_ERR_OOM,
+ * MLVS_ERR_CUDA, MLVS_ERR_SINGULAR; the message is available from mlvs_last_error(NULL). */
+mlvs_status mlvs_ucreate(const mlvs_uconfig* cfg, int n_node, const double* node_xy, int n_cell,
+                         const int* cell_ptr, const int* cell_nodes, const int* edge_wall,
+                         const double* init_W, mlvs_uhandle** out);
+
+/* Sec. 2.2, Eqs. phi_update to recover_phi on polygons.  Advance n_steps steps, ordered on the
+ * handle's stream; returns after they completed.  *ms (may be NULL) receives their device time.
+ * Errors: MLVS_ERR_NONFINITE / MLVS_ERR_POSITIVITY / MLVS_ERR_SINGULAR when a cell or face state
+ * failed (the handle then refuses further steps with MLVS_ERR_STATE), MLVS_ERR_CUDA. */
+mlvs_status mlvs_ustep(mlvs_uhandle* h, int n_steps, float* ms);
+
+/* No counterpart in the paper.  Copy (g~, h~) to host g[n_cell][nv], hh[n_cell][nv] in the
+ * caller's cell order, velocity v = iy * n_base + ix.  Errors: MLVS_ERR_ARG, MLVS_ERR_CUDA. */
+mlvs_status mlvs_uread(const mlvs_uhandle* h, double* g, double* hh);
+
+/* No counterpart in the paper.  Sizes and time step (each pointer may be NULL). */
+mlvs_status mlvs_uinfo(const mlvs_uhandle* h, int* nv, int* n_face, double* dt);
+
+/* No counterpart in the paper.  Release everything the handle owns.  NULL is allowed. */
+void mlvs_udestroy(mlvs_uhandle* h);
 
 /* No counterpart in the paper.  Release everything the handle owns.  NULL is allowed. */
 void mlvs_destroy(mlvs_handle* h);

@@ -8,7 +8,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libmlvs.so")
-SOURCES = ["mlvs_api.cu", "moments_noalloc.cu", "mlp.cu"]
+SOURCES = ["mlvs_api.cu", "moments_noalloc.cu", "mlp.cu", "ustep_api.cu"]
 
 
 def _newest_source_mtime() -> float:

@@ -645,8 +645,8 @@ __global__ void k_fin_post(const PointArgs a) {
 // Sums of the velocity-chunk partials in chunk order, one thread per (moment, point): the
 // same values a finalisation thread would form, with the FP64 chains spread over many warps.
 // pts (null: every point) lists the nwork points to sum; npt is the stride of part and out.
-__global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int npt, const int* __restrict__ pts,
-                             int nwork, double* __restrict__ out) {
+static __global__ void k_sum_chunks(const double* __restrict__ part, int nchunk, int npt, const int* __restrict__ pts,
+                                    int nwork, double* __restrict__ out) {
   const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long)NMOM * nwork) return;
   const int m = (int)(t / nwork), w = (int)(t % nwork);

@@ -20,7 +20,7 @@ STATUS = {0: "MLVS_OK", -1: "MLVS_ERR_ARG", -2: "MLVS_ERR_OOM", -3: "MLVS_ERR_CU
 BC_PERIODIC, BC_ZEROGRAD, BC_WALL, BC_FREESTREAM = 0, 1, 2, 3
 F64, F32, BF16 = 0, 1, 2
 QUAD_BOOLE, QUAD_SIMPSON, QUAD_TRAPZ = 0, 1, 2
-LIMITER_VANLEER, LIMITER_NONE = 0, 1
+LIMITER_VANLEER, LIMITER_NONE, LIMITER_VENKAT = 0, 1, 2
 RHO, U, V, T, QX, QY, LEVEL, RHOE, SXX, SXY, SYY = 1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024
 
 
@@ -59,6 +59,16 @@ class mlvs_adapt_stats(C.Structure):
                 ("ms_group", C.c_float), ("ms_remap", C.c_float), ("ms_total", C.c_float)]
 
 
+class mlvs_uconfig(C.Structure):
+    _fields_ = [
+        ("storage", C.c_int), ("R", C.c_double), ("K_internal", C.c_double), ("Pr", C.c_double),
+        ("omega", C.c_double), ("mu_ref", C.c_double), ("T_ref", C.c_double), ("cfl", C.c_double),
+        ("dt", C.c_double), ("compat_cell", C.c_int), ("compat_face", C.c_int), ("limiter", C.c_int),
+        ("n_base", C.c_int), ("umin", C.c_double), ("umax", C.c_double), ("quadrature", C.c_int),
+        ("n_wall", C.c_int), ("wall", (C.c_double * 3) * 8), ("vpc", C.c_int), ("stream", C.c_void_p),
+    ]
+
+
 def _load():
     if not os.path.exists(_LIB_PATH):
         raise ImportError(f"libmlvs.so not built at {_LIB_PATH}; run __graft_entry__.build()")
@@ -90,6 +100,12 @@ def _load():
                                           C.POINTER(C.c_int), C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]),
         "mlvs_umesh_order": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
+        "mlvs_ucreate": (C.c_int, [C.POINTER(mlvs_uconfig), C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                   C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(H)]),
+        "mlvs_ustep": (C.c_int, [H, C.c_int, C.POINTER(C.c_float)]),
+        "mlvs_uread": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+        "mlvs_uinfo": (C.c_int, [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+        "mlvs_udestroy": (None, [H]),
         "mlvs_space_points": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int)]),
@@ -303,6 +319,60 @@ def mlvs_umesh_order(cx, cy):
     order = np.zeros(x.size, dtype=np.int32)
     _check(_lib.mlvs_umesh_order(x.size, x.ctypes.data, y.ctypes.data, order.ctypes.data), None)
     return order
+
+
+def umesh_arrays(cells, edge_wall=None):
+    """CSR (cell_ptr, cell_nodes) of a list of node tuples, and edge_wall flattened alike."""
+    ptr = np.zeros(len(cells) + 1, dtype=np.int32)
+    ptr[1:] = np.cumsum([len(c) for c in cells])
+    nodes = np.ascontiguousarray(np.concatenate([np.asarray(c, dtype=np.int32) for c in cells]))
+    ew = None
+    if edge_wall is not None:
+        ew = np.ascontiguousarray(np.concatenate([np.asarray(e, dtype=np.int32) for e in edge_wall]))
+        if ew.size != nodes.size:
+            raise ValueError("edge_wall needs one entry per cell edge")
+    return ptr, nodes, ew
+
+
+def mlvs_ucreate(cfg: mlvs_uconfig, node_xy, cells, init_W, edge_wall=None):
+    """Unstructured handle: nodes [Nn][2], counter-clockwise cells (node tuples), init_W [Nc][4]
+    = (rho, u, v, T), edge_wall per cell edge (None: wall 0 everywhere)."""
+    xy = np.ascontiguousarray(node_xy, dtype=np.float64)
+    ptr, nodes, ew = umesh_arrays(cells, edge_wall)
+    W0 = np.ascontiguousarray(init_W, dtype=np.float64)
+    if W0.shape != (len(cells), 4):
+        raise ValueError("init_W must be [n_cell][4]")
+    h = C.c_void_p()
+    _check(_lib.mlvs_ucreate(C.byref(cfg), xy.shape[0], xy.ctypes.data, len(cells), ptr.ctypes.data,
+                             nodes.ctypes.data, None if ew is None else ew.ctypes.data, W0.ctypes.data,
+                             C.byref(h)), None)
+    return h
+
+
+def mlvs_ustep(h, n_steps):
+    """Advance n_steps steps; returns their device time in ms."""
+    ms = C.c_float()
+    _check(_lib.mlvs_ustep(h, n_steps, C.byref(ms)), None)
+    return ms.value
+
+
+def mlvs_uinfo(h):
+    """(nv, n_face, dt) of an unstructured handle."""
+    nv, nf, dt = C.c_int(), C.c_int(), C.c_double()
+    _check(_lib.mlvs_uinfo(h, C.byref(nv), C.byref(nf), C.byref(dt)), None)
+    return nv.value, nf.value, dt.value
+
+
+def mlvs_uread(h, n_cell):
+    """(g~, h~) as [n_cell][nv] FP64 arrays."""
+    nv = mlvs_uinfo(h)[0]
+    g, hh = np.zeros((n_cell, nv)), np.zeros((n_cell, nv))
+    _check(_lib.mlvs_uread(h, g.ctypes.data, hh.ctypes.data), None)
+    return g, hh
+
+
+def mlvs_udestroy(h):
+    _lib.mlvs_udestroy(h)
 
 
 def mlvs_space_points(n_base, umin, umax, quadrature, kappa):
