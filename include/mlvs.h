@@ -441,6 +441,11 @@ mlvs_status mlvs_ustep(mlvs_uhandle* h, int n_steps, float* ms);
  * caller's cell order, velocity v = iy * n_base + ix.  Errors: MLVS_ERR_ARG, MLVS_ERR_CUDA. */
 mlvs_status mlvs_uread(const mlvs_uhandle* h, double* g, double* hh);
 
+/* Eqs. discrete_W, discrete_q: the cell state at the start of the last step taken (after
+ * mlvs_ucreate: zeros), W[11][n_cell] = rho, u, v, T, q_x, q_y, rho E, tau, then the stress
+ * deviator of phi (xx, xy, yy), caller's cell order.  Errors: MLVS_ERR_ARG, MLVS_ERR_CUDA. */
+mlvs_status mlvs_ucells(const mlvs_uhandle* h, double* W);
+
 /* No counterpart in the paper.  Sizes and time step (each pointer may be NULL). */
 mlvs_status mlvs_uinfo(const mlvs_uhandle* h, int* nv, int* n_face, double* dt);
 

@@ -91,7 +91,7 @@ template <class T> mlvs_status u_setup(mlvs_uhandle* h, const double* W0) {
     if (!tv.empty()) e = cudaMemcpy(p[b], tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice);
     if (!iv.empty()) e = cudaMemcpy(p[b], iv.data(), iv.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (b == UB_W0) e = cudaMemcpy(p[b], W0, bytes, cudaMemcpyHostToDevice);
-    if (b == UB_ERR) e = cudaMemset(p[b], 0, sizeof(int));
+    if (b == UB_ERR || b == UB_W) e = cudaMemset(p[b], 0, bytes);
     if (e != cudaSuccess) return ufail(MLVS_ERR_CUDA, std::string("mlvs_ucreate: ") + cudaGetErrorString(e));
   }
   UArgs<T> a = u_wire<T>(h->u, h->c, p);
@@ -205,6 +205,14 @@ extern "C" mlvs_status mlvs_uread(const mlvs_uhandle* h, double* g, double* hh) 
       g[i * nv + v] = f[v * nc + i];
       hh[i * nv + v] = f[(nv + v) * nc + i];
     }
+  return MLVS_OK;
+}
+
+extern "C" mlvs_status mlvs_ucells(const mlvs_uhandle* h, double* W) {
+  if (!h || !W) return ufail(MLVS_ERR_ARG, "mlvs_ucells: null argument");
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = cudaMemcpy(W, h->buf[UB_W].p, 11 * sizeof(double) * h->u.nc, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return ufail(MLVS_ERR_CUDA, std::string("mlvs_ucells: ") + cudaGetErrorString(e));
   return MLVS_OK;
 }
 

@@ -104,6 +104,7 @@ def _load():
                                    C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(H)]),
         "mlvs_ustep": (C.c_int, [H, C.c_int, C.POINTER(C.c_float)]),
         "mlvs_uread": (C.c_int, [H, C.c_void_p, C.c_void_p]),
+        "mlvs_ucells": (C.c_int, [H, C.c_void_p]),
         "mlvs_uinfo": (C.c_int, [H, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "mlvs_udestroy": (None, [H]),
         "mlvs_space_points": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_int, C.c_void_p, C.c_int,
@@ -369,6 +370,14 @@ def mlvs_uread(h, n_cell):
     g, hh = np.zeros((n_cell, nv)), np.zeros((n_cell, nv))
     _check(_lib.mlvs_uread(h, g.ctypes.data, hh.ctypes.data), None)
     return g, hh
+
+
+def mlvs_ucells(h, n_cell):
+    """Cell state [11][n_cell] at the start of the last step (rho, u, v, T, qx, qy, rhoE, tau,
+    sxx, sxy, syy)."""
+    W = np.zeros((11, n_cell))
+    _check(_lib.mlvs_ucells(h, W.ctypes.data), None)
+    return W
 
 
 def mlvs_udestroy(h):
