@@ -332,6 +332,54 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
     return out
 
 
+def _unstructured_leg(storage="f32", m=10, n_base=101, umax=6.0, steps=50, warm=5):
+    """Two connected cavities (13,600 quads for m = 10; the paper's mesh has 12,012 cells)
+    with the paper's density ratio of 1000, gas at rest at T = 1, closed walls at T = 1, one
+    velocity space of n_base^2 points: device time per step of the unstructured step and its
+    cell-velocity update rate, plus the mass drift over the timed steps."""
+    import numpy as np
+    from paper_2609_35258_b300 import mlvs as M, workloads
+    nodes, cells = workloads.two_cavities(m)
+    geo = M.mlvs_umesh_geometry(nodes, cells)
+    nc = len(cells)
+    W0 = np.zeros((nc, 4))
+    W0[:, 0] = np.where(geo["cx"] < 0.0, 1.0, 1e-3)
+    W0[:, 3] = 1.0
+    c = M.mlvs_uconfig()
+    c.storage = {"f32": M.F32, "f64": M.F64}[storage]
+    c.R, c.K_internal, c.Pr, c.omega, c.T_ref = 1.0, 0.0, 2.0 / 3.0, 0.81, 1.0
+    c.mu_ref, c.Kn = 0.0, 0.05
+    c.cfl, c.dt = 0.5, 0.0
+    c.compat_cell = c.compat_face = 1
+    c.limiter = M.LIMITER_VENKAT
+    c.n_base, c.umin, c.umax, c.quadrature = n_base, -umax, umax, M.QUAD_BOOLE
+    c.n_wall = 1
+    c.wall[0][0], c.wall[0][1], c.wall[0][2] = 0.0, 0.0, 1.0
+    c.vpc = 64
+    out = {"workload": f"two cavities, {nc} quads, {n_base}^2 velocities on [-{umax:g},{umax:g}]^2, "
+                       f"density ratio 1000, {storage}", "cells": nc, "faces": len(geo["L"])}
+    h = M.mlvs_ucreate(c, nodes, cells, W0)
+    try:
+        M.mlvs_ustep(h, warm)
+        W1 = M.mlvs_ucells(h, nc)
+        ms = M.mlvs_ustep(h, steps)
+        M.mlvs_ustep(h, 1)
+        W2 = M.mlvs_ucells(h, nc)
+        nv = M.mlvs_uinfo(h)[0]
+        m1, m2 = np.sum(geo["area"] * W1[0]), np.sum(geo["area"] * W2[0])
+        out.update({"ms_per_step": ms / steps, "velocities": nv,
+                    "updates_per_s": nc * nv * steps / (ms * 1e-3), "steps": steps,
+                    "rel_mass_drift": abs(m2 - m1) / m1,
+                    "launches_per_step": 9,
+                    "hbm_bytes_per_update_this_version": 264 if storage == "f32" else 528,
+                    "algorithmic_bytes_per_update": 16 if storage == "f32" else 32})
+    except M.MLVSError as e:
+        out["error"] = str(e)
+    finally:
+        M.mlvs_udestroy(h)
+    return out
+
+
 def combine_ranks(ms, world, upd_step, steps, device="cuda"):
     """The timed region's length as the maximum over ranks (every rank waits at a barrier
     afterwards) and the whole-job throughput: the updates of all ranks over that time."""
@@ -451,6 +499,7 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_selector and rank == 0:
         selector = _selector_leg()
     cylinder = _cylinder_leg() if (args.cylinder and rank == 0) else None
+    unstructured = _unstructured_leg() if (args.unstructured and rank == 0) else None
 
     # end-to-end through the public API: host init upload, steps, host moment reads
     e2e = None
@@ -492,6 +541,7 @@ def run_ours(args, rank, world, local_rank):
                          "algorithmic_bytes_per_update": algo_per_update},
             "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, phases)},
             "mlvs": mlvs, "time_to_steady": steady, "selector": selector, "cylinder": cylinder,
+            "unstructured": unstructured,
             "clocks": clocks, "e2e": e2e, "gpu_launches": st.launches, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -512,6 +562,8 @@ def main():
     ap.add_argument("--cells", type=int, default=64, help="cavity cells per side (default 64)")
     ap.add_argument("--cylinder", action="store_true",
                     help="add the Ma 5 cylinder leg (UVS vs MLVS over clustering thresholds, ~3 min)")
+    ap.add_argument("--unstructured", action="store_true",
+                    help="add the two-cavity unstructured-mesh leg (13,600 quads, 101^2 velocities)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -403,7 +403,9 @@ typedef struct mlvs_uhandle mlvs_uhandle;
 
 typedef struct {
   int storage;          /* MLVS_F64 | MLVS_F32: storage and compute type                     */
-  double R, K_internal, Pr, omega, mu_ref, T_ref;  /* gas; mu = mu_ref (T/T_ref)^omega, mu_ref > 0 */
+  double R, K_internal, Pr, omega, mu_ref, T_ref;  /* gas; mu = mu_ref (T/T_ref)^omega (Sec. 4)  */
+  double Kn;            /* used when mu_ref <= 0: the VHS relation with alpha = 1, rho_ref = 1,
+                           L_ref = 1 (as mlvs_config's Kn)                                    */
   double cfl;           /* dt = cfl * min over cells (area / longest edge) / max |xi|_inf      */
   double dt;            /* > 0: fixed time step instead                                      */
   int compat_cell;      /* 1: four-moment compatibility correction at cells (Sec. 3.3.1)      */

@@ -44,6 +44,7 @@
 #include "cluster_host.hpp"
 #include "vspace_host.hpp"
 #include "umesh_host.hpp"
+#include "gas_host.hpp"
 
 using namespace mlvs;
 
@@ -248,13 +249,6 @@ unsigned hash_host(unsigned x) {
 constexpr int kTX2 = 16, kTY2 = 16, kTX1 = 128;
 int tile_w(int D) { return D == 2 ? kTX2 : kTX1; }
 int tile_h(int D) { return D == 2 ? kTY2 : 1; }
-
-double vhs_mu_ref(double Kn, double omega, double rho_ref, double R, double T_ref, double L_ref) {
-  const double alpha = 1.0;
-  const double c = 5.0 * (alpha + 1.0) * (alpha + 2.0) * std::sqrt(M_PI) /
-                   (4.0 * alpha * (5.0 - 2.0 * omega) * (7.0 - 2.0 * omega));
-  return c * Kn * rho_ref * std::sqrt(2.0 * R * T_ref) * L_ref;
-}
 
 // Inverse of the T-independent four-moment mapping matrix of a space (raw basis, unit
 // weighting): rows (sum w phi, sum w xi_x phi, sum w xi_y phi, 1/2 sum w xi^2 phi),

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/mlvs.h"
+#include "gas_host.hpp"
 #include "umesh_host.hpp"
 #include "ustep.cuh"
 #include "vspace_host.hpp"
@@ -46,7 +47,8 @@ inline std::string u_config(const mlvs_uconfig& c, UHostConfig& u) {
   if (c.storage != MLVS_F64 && c.storage != MLVS_F32) return "storage must be MLVS_F64 or MLVS_F32";
   if (c.limiter != MLVS_LIMITER_VENKAT && c.limiter != MLVS_LIMITER_NONE)
     return "limiter must be MLVS_LIMITER_VENKAT or MLVS_LIMITER_NONE";
-  u.R = c.R; u.K = c.K_internal; u.Pr = c.Pr; u.omega = c.omega; u.mu_ref = c.mu_ref; u.T_ref = c.T_ref;
+  u.R = c.R; u.K = c.K_internal; u.Pr = c.Pr; u.omega = c.omega; u.T_ref = c.T_ref;
+  u.mu_ref = c.mu_ref > 0 ? c.mu_ref : (c.Kn > 0 ? vhs_mu_ref(c.Kn, c.omega, 1.0, c.R, c.T_ref, 1.0) : 0.0);
   u.cfl = c.cfl; u.dt = c.dt;
   u.compat_cell = c.compat_cell != 0;
   u.compat_face = c.compat_face != 0;

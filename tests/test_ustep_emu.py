@@ -185,3 +185,15 @@ def test_every_pass_stays_inside_its_buffers_under_address_sanitizer():
     r = subprocess.run([sys.executable, "-c", CHILD, so, root], env=env, capture_output=True, text=True,
                        timeout=600, cwd=root)
     assert r.returncode == 0 and "clean" in r.stdout, r.stderr[-3000:]
+
+
+def test_knudsen_number_gives_the_oracles_reference_viscosity(emu):
+    """mu_ref <= 0 with Kn set: the library's VHS relation gives the oracle's mu_ref, so the
+    run equals the one with mu_ref given."""
+    nodes, cells, _, W0 = _two_cavity(True)
+    by_mu = _cfg(M.F64, [(0.0, 0.0, 1.0)])
+    by_kn = _cfg(M.F64, [(0.0, 0.0, 1.0)])
+    by_kn.mu_ref, by_kn.Kn = 0.0, 0.05
+    a = _run_emu(emu, by_mu, nodes, cells, W0, 2)
+    b = _run_emu(emu, by_kn, nodes, cells, W0, 2)
+    np.testing.assert_allclose(b[0], a[0], rtol=0, atol=1e-14 * np.max(np.abs(a[0])))
