@@ -411,6 +411,9 @@ typedef struct {
   int compat_cell;      /* 1: four-moment compatibility correction at cells (Sec. 3.3.1)      */
   int compat_face;      /* 1: the same correction of the face model distribution              */
   int limiter;          /* MLVS_LIMITER_VENKAT | MLVS_LIMITER_NONE                            */
+  int compat_moments;   /* 4 (or 0): Eq. eq_four_basis; 8: the eight-moment correction of
+                           Eq. eq_eight_basis, whose heat-flux target is the model's own
+                           (1 - Pr) q and whose deviatoric-stress target is zero            */
   int n_base;           /* velocity space: the n_base x n_base tensor product (Sec. 2.3)      */
   double umin, umax;    /* on [umin, umax]^2                                                  */
   int quadrature;       /* MLVS_QUAD_*                                                        */

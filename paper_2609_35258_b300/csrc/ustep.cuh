@@ -40,6 +40,7 @@ enum { ULIM_NONE = 0, ULIM_VENKAT = 1 };
 template <class T> struct UArgs {
   PointArgs pa;         // velocity tables, gas, constants (k.nv, k.nax, k.dt, k.c0, k.twoK), err
   int nc, nf, nv, vpc, nchunk, limiter, compat_face;
+  int compat8;          // 1: the eight-moment correction at cells and faces (compat flags on)
   double dt;
   double wall[8][3];    // (u_w, v_w, T_w) per wall index
   const T* cgeo;        // [UC_N][nc]
@@ -58,6 +59,8 @@ template <class T> struct UArgs {
   double* part_f;
   T* cprm;
   T* fprm;
+  T* cprm8;             // [4][nc] eight-moment coefficients b4..b7 (zero without it)
+  T* fprm8;             // [4][nf]
   double* W;            // [11][nc] cell state at the start of the step
   double* wden;         // [nf] sum_{xi.n_in > 0} w (xi.n_in) g_w of the unit-density wall Maxwellian
 };
@@ -108,6 +111,188 @@ __device__ __forceinline__ T u_recon(const UArgs<T>& a, int comp, int v, int c, 
   return P + (ox - xs) * gx + (oy - ys) * gy;
 }
 
+// ---- eight-moment compatibility correction (Sec. 3.3.1, Eq. eq_eight_basis) ----
+// The correction factor 1 + sum_m b_m phi_m uses the basis, in peculiar velocity c = xi - u,
+//   {1, c_x, c_y, |c|^2, |c|^2 c_x, |c|^2 c_y, c_x^2 - c_y^2, c_x c_y},
+// the span of Eq. eq_eight_basis {1, xi_x, xi_y, E_xi, E_c c_x, E_c c_y, c_x^2 - c_y^2, c_x c_y}.
+// The constraint rows are (g, c g, (|c|^2 g + h)/2, (|c|^2 g + h) c / 2, (c_x^2 - c_y^2) g,
+// c_x c_y g) with targets (rho, rho (u - u_p), rho e + rho |u - u_p|^2 / 2, q^tar, 0, 0), u_p the
+// velocity of the parameters: the conserved rows combine the paper's, and the heat-flux and
+// stress rows are the paper's about u (u_p = u up to the rounding of the stored velocity).
+
+// one-axis sums S[a] = sum_i W_i gauss(X_i - u) (X_i - u)^a, a = 0..9
+template <class T>
+__device__ inline void u_axis_sums10(const T* ax, int nax, T u, T inv2RT, T lnh, double S[10]) {
+  KSum<T> acc[10];
+  for (int k = 0; k < 10; ++k) acc[k].zero();
+  for (int i = 0; i < nax; ++i) {
+    const T c = ax[i] - u;
+    T p = ax[nax + i] * Num<T>::gauss(c, inv2RT, lnh);
+    for (int k = 0; k < 10; ++k) {
+      acc[k].add(p);
+      p *= c;
+    }
+  }
+  for (int k = 0; k < 10; ++k) S[k] = acc[k].val();
+}
+
+// peculiar moments of the uncorrected Shakhov model on the tensor-product space:
+//   G[a][b] = sum w g^S c_x^a c_y^b (a + b <= 6),  H[a][b] = sum w h^S c_x^a c_y^b (a + b <= 4)
+template <class T>
+__device__ inline void u_moments8(const PointArgs& A, const MP<T>& mp, double G[7][7], double H[5][5]) {
+  const T* ax = reinterpret_cast<const T*>(A.ax);
+  double Sx[10], Sy[10];
+  u_axis_sums10<T>(ax, A.k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
+  u_axis_sums10<T>(ax, A.k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
+  const double kx = (double)mp.kqx, ky = (double)mp.kqy;
+  const double i2 = 2.0 * (double)mp.inv2RT, RT = (double)mp.RT, c0 = A.k.c0;
+  const double al = RT * c0 * i2, be = RT * (2.0 * c0 + A.k.twoK);
+  for (int x = 0; x < 7; ++x)
+    for (int y = 0; y < 7; ++y) G[x][y] = 0.0;
+  for (int x = 0; x < 5; ++x)
+    for (int y = 0; y < 5; ++y) H[x][y] = 0.0;
+  for (int x = 0; x < 7; ++x)
+    for (int y = 0; x + y < 7; ++y) {
+      const double cub = kx * (Sx[x + 3] * Sy[y] + Sx[x + 1] * Sy[y + 2]) + ky * (Sx[x + 2] * Sy[y + 1] + Sx[x] * Sy[y + 3]);
+      const double lin = kx * Sx[x + 1] * Sy[y] + ky * Sx[x] * Sy[y + 1];
+      G[x][y] = Sx[x] * Sy[y] - 4.0 * lin + i2 * cub;
+      if (x + y < 5) H[x][y] = RT * c0 * Sx[x] * Sy[y] + al * cub - be * lin;
+    }
+}
+
+// Polynomials in (c_x, c_y): up to four terms (coefficient, power of c_x, power of c_y).
+struct UPoly {
+  int n;
+  double c[4];
+  int px[4], py[4];
+};
+
+__device__ inline UPoly u_basis8(int m) {
+  UPoly p;
+  switch (m) {
+    case 0: p = {1, {1, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}; break;
+    case 1: p = {1, {1, 0, 0, 0}, {1, 0, 0, 0}, {0, 0, 0, 0}}; break;
+    case 2: p = {1, {1, 0, 0, 0}, {0, 0, 0, 0}, {1, 0, 0, 0}}; break;
+    case 3: p = {2, {1, 1, 0, 0}, {2, 0, 0, 0}, {0, 2, 0, 0}}; break;
+    case 4: p = {2, {1, 1, 0, 0}, {3, 1, 0, 0}, {0, 2, 0, 0}}; break;
+    case 5: p = {2, {1, 1, 0, 0}, {2, 0, 0, 0}, {1, 3, 0, 0}}; break;
+    case 6: p = {2, {1, -1, 0, 0}, {2, 0, 0, 0}, {0, 2, 0, 0}}; break;
+    default: p = {1, {1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}}; break;
+  }
+  return p;
+}
+
+// constraint row k: g-part and h-part polynomials (the h-part of rows 3..5 is h/2 times c^e)
+__device__ inline void u_row8(int k, UPoly& pg, UPoly& ph) {
+  ph.n = 0;
+  if (k <= 2) {
+    pg = u_basis8(k);
+  } else if (k == 3) {
+    pg = {2, {0.5, 0.5, 0, 0}, {2, 0, 0, 0}, {0, 2, 0, 0}};
+    ph = {1, {0.5, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  } else if (k == 4) {
+    pg = {2, {0.5, 0.5, 0, 0}, {3, 1, 0, 0}, {0, 2, 0, 0}};
+    ph = {1, {0.5, 0, 0, 0}, {1, 0, 0, 0}, {0, 0, 0, 0}};
+  } else if (k == 5) {
+    pg = {2, {0.5, 0.5, 0, 0}, {2, 0, 0, 0}, {1, 3, 0, 0}};
+    ph = {1, {0.5, 0, 0, 0}, {0, 0, 0, 0}, {1, 0, 0, 0}};
+  } else {
+    pg = u_basis8(k);
+  }
+}
+
+// Gaussian elimination with partial pivoting, n = 8, in place (b receives the solution).
+__device__ inline bool u_solve8(double M[8][8], double b[8]) {
+  for (int c = 0; c < 8; ++c) {
+    int p = c;
+    double best = fabs(M[c][c]);
+    for (int q = c + 1; q < 8; ++q)
+      if (fabs(M[q][c]) > best) { best = fabs(M[q][c]); p = q; }
+    if (!(best > 1e-300)) return false;
+    if (p != c) {
+      for (int j = 0; j < 8; ++j) { const double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
+      const double t = b[c]; b[c] = b[p]; b[p] = t;
+    }
+    for (int q = c + 1; q < 8; ++q) {
+      const double f = M[q][c] / M[c][c];
+      for (int j = c; j < 8; ++j) M[q][j] -= f * M[c][j];
+      b[q] -= f * b[c];
+    }
+  }
+  for (int c = 7; c >= 0; --c) {
+    double s = b[c];
+    for (int j = c + 1; j < 8; ++j) s -= M[c][j] * b[j];
+    b[c] = s / M[c][c];
+  }
+  return true;
+}
+
+// b0..b7 of the eight-moment correction of mp (uncorrected Shakhov parameters of the state
+// rho, u, T with heat-flux target q_tar); b0..b3 go to mp, b4..b7 to b8.
+template <class T>
+__device__ inline bool u_correct8(const PointArgs& A, double rho, double ux, double uy, double Tm, double qtx,
+                                  double qty, MP<T>& mp, T b8[4]) {
+  double G[7][7], H[5][5];
+  u_moments8<T>(A, mp, G, H);
+  double M[8][8], r[8];
+  for (int k = 0; k < 8; ++k) {
+    UPoly pg, ph;
+    u_row8(k, pg, ph);
+    for (int m = 0; m < 8; ++m) {
+      const UPoly q = u_basis8(m);
+      double s = 0.0;
+      for (int i = 0; i < pg.n; ++i)
+        for (int j = 0; j < q.n; ++j) s += pg.c[i] * q.c[j] * G[pg.px[i] + q.px[j]][pg.py[i] + q.py[j]];
+      for (int i = 0; i < ph.n; ++i)
+        for (int j = 0; j < q.n; ++j) s += ph.c[i] * q.c[j] * H[ph.px[i] + q.px[j]][ph.py[i] + q.py[j]];
+      M[k][m] = s;
+    }
+  }
+  const double RT = A.gas.R * Tm;
+  const double dux = ux - (double)mp.ux, duy = uy - (double)mp.uy;
+  const double tar[8] = {rho, rho * dux, rho * duy,
+                         0.5 * (3.0 + A.gas.K) * rho * RT + 0.5 * rho * (dux * dux + duy * duy), qtx, qty, 0.0, 0.0};
+  for (int k = 0; k < 8; ++k) r[k] = tar[k] - M[k][0];
+  if (!u_solve8(M, r)) return false;
+  mp.b0 = T(r[0]); mp.b1 = T(r[1]); mp.b2 = T(r[2]); mp.b3 = T(r[3]);
+  for (int m = 0; m < 4; ++m) b8[m] = T(r[4 + m]);
+  return true;
+}
+
+// Shakhov model times the eight-term correction factor (model_eval's operation order for the
+// model itself, then the factor).
+template <class T>
+__device__ __forceinline__ void u_model_eval8(const MP<T>& p, const T* b8, T xix, T xiy, T c0, T twoK, T& g,
+                                              T& h) {
+  using N = Num<T>;
+  const T cx = N::sub(xix, p.ux), cy = N::sub(xiy, p.uy);
+  const T geq = maxwell_sep<T, 2>(p, cx, cy);
+  const T cc = N::fma(cy, cy, N::mul(cx, cx));
+  const T cq = N::fma(p.kqy, cy, N::mul(p.kqx, cx));
+  const T t = N::mul(N::mul(T(2), p.inv2RT), cc);
+  const T gs = N::mul(geq, N::fma(cq, N::sub(t, T(4)), T(1)));
+  const T hs = N::mul(N::mul(p.RT, geq), N::fma(cq, N::fma(N::sub(t, T(2)), c0, -twoK), c0));
+  T corr = N::fma(p.b3, cc, N::fma(p.b2, cy, N::fma(p.b1, cx, p.b0)));
+  corr = N::fma(N::mul(b8[0], cc), cx, corr);
+  corr = N::fma(N::mul(b8[1], cc), cy, corr);
+  corr = N::fma(b8[2], N::fma(cx, cx, -N::mul(cy, cy)), corr);
+  corr = N::fma(N::mul(b8[3], cx), cy, corr);
+  g = N::fma(gs, corr, gs);
+  h = N::fma(hs, corr, hs);
+}
+
+// the model of point i with parameters P[NP][n] and, in eight-moment mode, P8[4][n]
+template <class T>
+__device__ __forceinline__ void u_model(const UArgs<T>& a, const MP<T>& m, const T* P8, long n, long i, T xx, T yy,
+                                        T& g, T& h) {
+  if (a.compat8) {
+    const T b8[4] = {P8[i], P8[n + i], P8[2 * n + i], P8[3 * n + i]};
+    u_model_eval8<T>(m, b8, xx, yy, T(a.pa.k.c0), T(a.pa.k.twoK), g, h);
+  } else {
+    model_eval<T, 2>(m, xx, yy, T(a.pa.k.c0), T(a.pa.k.twoK), g, h);
+  }
+}
+
 template <int E, class T>
 __device__ inline void u_elem(const UArgs<T>& a, long i) {
   const long nc = a.nc, nf = a.nf, nv = a.nv;
@@ -119,12 +304,29 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
                        a.part_c + (long)chunk * NMOM * nc + c, nc);
   } else if constexpr (E == U_CELL_FIN) {
     finalize_point<T, 2, 0>(a.pa, (int)i);
+    if (a.compat8 && a.pa.compat) {
+      const double* W = a.W;
+      const double rho = W[i], ux = W[nc + i], uy = W[2 * nc + i], Tm = W[3 * nc + i];
+      if (!(rho > 0.0) || !(Tm > 0.0) || !isfinite(rho) || !isfinite(Tm)) return;   // flagged already
+      MP<T> mp;
+      mp.load(a.cprm, nc, i);
+      const T c1 = mp.c1, c2 = mp.c2;
+      point_params<T, 2>(a.pa.gas, rho, ux, uy, Tm, W[4 * nc + i], W[5 * nc + i], mp);
+      T b8[4];
+      const double pr = 1.0 - a.pa.gas.Pr;
+      if (!u_correct8<T>(a.pa, rho, ux, uy, Tm, pr * W[4 * nc + i], pr * W[5 * nc + i], mp, b8))
+        atomicOr(a.pa.err, ERR_SINGULAR);
+      mp.c1 = c1;
+      mp.c2 = c2;
+      store_mp<T>(a.cprm, nc, i, mp, T(0));
+      for (int m = 0; m < 4; ++m) a.cprm8[m * nc + i] = b8[m];
+    }
   } else if constexpr (E == U_BARP) {
     const int c = (int)(i % nc), v = (int)(i / nc);
     MP<T> m;
     m.load(a.cprm, nc, c);
     T gS, hS;
-    model_eval<T, 2>(m, u_xi(a, v, 0), u_xi(a, v, 1), T(a.pa.k.c0), T(a.pa.k.twoK), gS, hS);
+    u_model<T>(a, m, a.cprm8, nc, c, u_xi(a, v, 0), u_xi(a, v, 1), gS, hS);
     const T gt = a.f[(long)v * nc + c], ht = a.f[(nv + v) * nc + c];
     a.barp[(long)v * nc + c] = N::fma(m.c1, N::sub(gS, gt), gt);
     a.barp[(nv + v) * nc + c] = N::fma(m.c1, N::sub(hS, ht), ht);
@@ -240,7 +442,16 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
     }
     PointArgs pf = a.pa;
     pf.compat = a.compat_face;
-    const bool ok = point_model<T, 2>(pf, rho, ux, uy, Tm, qx, qy, mp);
+    bool ok;
+    if (a.compat8 && a.compat_face) {
+      point_params<T, 2>(pf.gas, rho, ux, uy, Tm, qx, qy, mp);
+      T b8[4];
+      const double pr = 1.0 - g.Pr;
+      ok = u_correct8<T>(pf, rho, ux, uy, Tm, pr * qx, pr * qy, mp, b8);
+      for (int m = 0; m < 4; ++m) a.fprm8[m * nf + fi] = b8[m];
+    } else {
+      ok = point_model<T, 2>(pf, rho, ux, uy, Tm, qx, qy, mp);
+    }
     mp.c1 = T(2.0 * tau / (2.0 * tau + s));
     mp.c2 = T(s / (2.0 * tau + s));
     store_mp<T>(a.fprm, nf, fi, mp, T(FK_INTERIOR));
@@ -253,7 +464,8 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
     const T xn = a.fgeo[UF_NX * nf + fi] * xx + a.fgeo[UF_NY * nf + fi] * yy;
     const T scale = xn * a.fgeo[UF_LEN * nf + fi];
     T gS, hS;
-    model_eval<T, 2>(m, xx, yy, T(a.pa.k.c0), T(a.pa.k.twoK), gS, hS);
+    if (a.fwall[fi] >= 0) model_eval<T, 2>(m, xx, yy, T(a.pa.k.c0), T(a.pa.k.twoK), gS, hS);
+    else u_model<T>(a, m, a.fprm8, nf, fi, xx, yy, gS, hS);
     const T gb = a.fbar[(long)v * nf + fi], hb = a.fbar[(nv + v) * nf + fi];
     T gp, hp;
     if (a.fwall[fi] >= 0) {

@@ -91,7 +91,7 @@ template <class T> mlvs_status u_setup(mlvs_uhandle* h, const double* W0) {
     if (!tv.empty()) e = cudaMemcpy(p[b], tv.data(), tv.size() * sizeof(T), cudaMemcpyHostToDevice);
     if (!iv.empty()) e = cudaMemcpy(p[b], iv.data(), iv.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (b == UB_W0) e = cudaMemcpy(p[b], W0, bytes, cudaMemcpyHostToDevice);
-    if (b == UB_ERR || b == UB_W) e = cudaMemset(p[b], 0, bytes);
+    if (b == UB_ERR || b == UB_W || b == UB_CPRM8 || b == UB_FPRM8) e = cudaMemset(p[b], 0, bytes);
     if (e != cudaSuccess) return ufail(MLVS_ERR_CUDA, std::string("mlvs_ucreate: ") + cudaGetErrorString(e));
   }
   UArgs<T> a = u_wire<T>(h->u, h->c, p);

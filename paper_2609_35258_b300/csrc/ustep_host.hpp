@@ -27,6 +27,7 @@ struct UHostConfig {
   double R, K, Pr, omega, mu_ref, T_ref;
   double cfl, dt;                 // dt > 0: fixed
   int compat_cell, compat_face, limiter;
+  int compat_moments;             // 4 or 8
   int n_base, quadrature;
   double umin, umax;
   int n_wall;
@@ -53,6 +54,9 @@ inline std::string u_config(const mlvs_uconfig& c, UHostConfig& u) {
   u.compat_cell = c.compat_cell != 0;
   u.compat_face = c.compat_face != 0;
   u.limiter = c.limiter == MLVS_LIMITER_VENKAT ? 1 : 0;
+  if (c.compat_moments != 0 && c.compat_moments != 4 && c.compat_moments != 8)
+    return "compat_moments must be 4 or 8 (0: 4)";
+  u.compat_moments = c.compat_moments == 8 ? 8 : 4;
   u.n_base = c.n_base; u.quadrature = c.quadrature; u.umin = c.umin; u.umax = c.umax;
   u.n_wall = c.n_wall;
   for (int w = 0; w < 8; ++w)
@@ -148,7 +152,8 @@ inline std::string u_build_host(int n_node, const double* xy, int n_cell, const 
 
 // Buffers of the step: type (0 = compute type T, 1 = int, 2 = double) and element count.
 enum { UB_CGEO = 0, UB_FGEO, UB_VT, UB_AX, UB_FCELL, UB_FWALL, UB_CFPTR, UB_CF, UB_W0, UB_F, UB_BARP, UB_GRAD,
-       UB_FBAR, UB_FLUX, UB_PARTC, UB_PARTF, UB_CPRM, UB_FPRM, UB_W, UB_WDEN, UB_ERR, UB_N };
+       UB_FBAR, UB_FLUX, UB_PARTC, UB_PARTF, UB_CPRM, UB_FPRM, UB_W, UB_WDEN, UB_ERR, UB_CPRM8, UB_FPRM8,
+       UB_N };
 
 inline void u_buffer(const UHost& u, int b, int& type, size_t& count) {
   const size_t nc = u.nc, nf = u.nf, nv = u.nv, ch = u.nchunk;
@@ -172,6 +177,8 @@ inline void u_buffer(const UHost& u, int b, int& type, size_t& count) {
     case UB_W: type = 2; count = 11 * nc; return;
     case UB_WDEN: type = 2; count = nf; return;
     case UB_ERR: type = 1; count = 1; return;
+    case UB_CPRM8: type = 0; count = 4 * nc; return;
+    case UB_FPRM8: type = 0; count = 4 * nf; return;
   }
   type = 0;
   count = 0;
@@ -203,6 +210,7 @@ inline UArgs<T> u_wire(const UHost& u, const UHostConfig& c, void* const* p) {
   pa.compat = c.compat_cell;
   pa.err = static_cast<int*>(p[UB_ERR]);
   a.compat_face = c.compat_face;
+  a.compat8 = c.compat_moments == 8;
   a.nc = u.nc;
   a.nf = u.nf;
   a.nv = u.nv;
@@ -228,6 +236,8 @@ inline UArgs<T> u_wire(const UHost& u, const UHostConfig& c, void* const* p) {
   a.part_f = static_cast<double*>(p[UB_PARTF]);
   a.cprm = static_cast<T*>(p[UB_CPRM]);
   a.fprm = static_cast<T*>(p[UB_FPRM]);
+  a.cprm8 = static_cast<T*>(p[UB_CPRM8]);
+  a.fprm8 = static_cast<T*>(p[UB_FPRM8]);
   a.W = static_cast<double*>(p[UB_W]);
   a.wden = static_cast<double*>(p[UB_WDEN]);
   return a;

@@ -65,7 +65,8 @@ class mlvs_uconfig(C.Structure):
         ("omega", C.c_double), ("mu_ref", C.c_double), ("T_ref", C.c_double), ("Kn", C.c_double),
         ("cfl", C.c_double),
         ("dt", C.c_double), ("compat_cell", C.c_int), ("compat_face", C.c_int), ("limiter", C.c_int),
-        ("n_base", C.c_int), ("umin", C.c_double), ("umax", C.c_double), ("quadrature", C.c_int),
+        ("compat_moments", C.c_int), ("n_base", C.c_int), ("umin", C.c_double), ("umax", C.c_double),
+        ("quadrature", C.c_int),
         ("n_wall", C.c_int), ("wall", (C.c_double * 3) * 8), ("vpc", C.c_int), ("stream", C.c_void_p),
     ]
 

@@ -4,6 +4,7 @@ step (the two-cavity expansion runs on unstructured cells).
 * Two-cavity meshes of quads and of triangles at the paper's density ratio of 1000: FP64
   within 1e-11 and FP32 within 2e-5 of the largest value after three steps.
 * A quad cavity with a moving lid (a second wall index), FP64.
+* The eight-moment compatibility correction at cells and faces, FP64 and FP32.
 * The two-cavity mesh at full size (13,600 cells, close to the paper's 12,012) with 61^2
   velocities, FP32, 20 steps: the mass stays constant (closed walls) and the flow stays
   mirror-symmetric about the channel axis (the mesh and the initial state are).
@@ -91,3 +92,14 @@ def test_full_size_two_cavities_conserve_mass_and_mirror_symmetry():
     mirror = np.array([key[(round(x, 9), round(-y, 9))] for x, y in zip(geo["cx"], geo["cy"])])
     np.testing.assert_allclose(W2[0][mirror], W2[0], rtol=1e-4)
     np.testing.assert_allclose(W2[2][mirror], -W2[2], rtol=0, atol=1e-4 * np.max(np.abs(W2[1])))
+
+
+@pytest.mark.parametrize("storage,tol", [(M.F64, 1e-11), (M.F32, 2e-5)], ids=["f64", "f32"])
+def test_eight_moment_correction(storage, tol):
+    nodes, cells, mesh, W0 = E._two_cavity(True)
+    cfg = E._cfg(storage, [(0.0, 0.0, 1.0)])
+    cfg.compat_moments = 8
+    g, h, _ = _run_gpu(cfg, nodes, cells, W0, 3)
+    go, ho, _ = E._run_oracle(mesh, W0, 3, nmom=8)
+    np.testing.assert_allclose(g, go, rtol=0, atol=tol * np.max(np.abs(go)))
+    np.testing.assert_allclose(h, ho, rtol=0, atol=tol * np.max(np.abs(ho)))

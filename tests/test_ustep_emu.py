@@ -4,6 +4,8 @@ compiled as host C++ (tests/emu).  Cases:
   * two-cavity meshes of quads and of triangles at the paper's density ratio of 1000, FP64;
   * a quad cavity with a moving lid, a second wall index, FP64;
   * the triangulated two-cavity mesh in FP32;
+  * the eight-moment compatibility correction at cells and faces (FP64 and FP32), which the
+    four-moment run differs from by far more than the bound;
   * one run under AddressSanitizer, which checks every buffer access of every pass.
 Velocity sums run in a different order than the oracle's and the FP32 case rounds every
 operation, so the bounds are 1e-12 (FP64) and 1e-5 (FP32) of the largest value (measured:
@@ -91,12 +93,12 @@ def _run_emu(lib, cfg, nodes, cells, W0, steps, edge_wall=None):
         lib.emu_destroy(e)
 
 
-def _run_oracle(mesh, W0, steps, n_base=13, umax=5.0, limiter="venkat"):
+def _run_oracle(mesh, W0, steps, n_base=13, umax=5.0, limiter="venkat", nmom=4):
     sp = vspace.uniform_space(vspace.make_base(n_base, -umax, umax, D=2), 0)
     g, h = dugks.initial_tilde(W0[:, 0], W0[:, 1:3], W0[:, 3], sp.xi, sp.w, GAS)
     dt = un.time_step(mesh, sp.xi, 0.5)
     for _ in range(steps):
-        g, h, _ = un.step(g, h, mesh, sp.xi, sp.w, GAS, dt, dugks.Options(), limiter=limiter)
+        g, h, _ = un.step(g, h, mesh, sp.xi, sp.w, GAS, dt, dugks.Options(compat_moments=nmom), limiter=limiter)
     return g, h, dt
 
 
@@ -197,3 +199,16 @@ def test_knudsen_number_gives_the_oracles_reference_viscosity(emu):
     a = _run_emu(emu, by_mu, nodes, cells, W0, 2)
     b = _run_emu(emu, by_kn, nodes, cells, W0, 2)
     np.testing.assert_allclose(b[0], a[0], rtol=0, atol=1e-14 * np.max(np.abs(a[0])))
+
+
+@pytest.mark.parametrize("storage,tol", [(M.F64, 1e-12), (M.F32, 1e-5)], ids=["f64", "f32"])
+def test_eight_moment_correction_matches_the_oracle(emu, storage, tol):
+    nodes, cells, mesh, W0 = _two_cavity(True)
+    cfg = _cfg(storage, [(0.0, 0.0, 1.0)])
+    cfg.compat_moments = 8
+    g, h, _ = _run_emu(emu, cfg, nodes, cells, W0, 3)
+    go, ho, _ = _run_oracle(mesh, W0, 3, nmom=8)
+    np.testing.assert_allclose(g, go, rtol=0, atol=tol * np.max(np.abs(go)))
+    np.testing.assert_allclose(h, ho, rtol=0, atol=tol * np.max(np.abs(ho)))
+    g4, _, _ = _run_oracle(mesh, W0, 3, nmom=4)
+    assert np.max(np.abs(g4 - go)) > 10 * tol * np.max(np.abs(go))
