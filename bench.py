@@ -370,8 +370,8 @@ def _unstructured_leg(storage="f32", m=10, n_base=101, umax=6.0, steps=50, warm=
         out.update({"ms_per_step": ms / steps, "velocities": nv,
                     "updates_per_s": nc * nv * steps / (ms * 1e-3), "steps": steps,
                     "rel_mass_drift": abs(m2 - m1) / m1,
-                    "launches_per_step": 9,
-                    "hbm_bytes_per_update_this_version": 264 if storage == "f32" else 528,
+                    "launches_per_step": 7,
+                    "hbm_bytes_per_update_this_version": 240 if storage == "f32" else 480,
                     "algorithmic_bytes_per_update": 16 if storage == "f32" else 32})
     except M.MLVSError as e:
         out["error"] = str(e)

@@ -4,21 +4,26 @@
 // Every pass is a per-element function u_elem<E>(args, i) over a flat index; the CUDA kernel
 // of a pass is a grid-stride loop over it, so the step's arithmetic and indexing are one
 // piece of code whatever runs the loop.  Passes of one step, in order:
-//   U_CELL_SUMS  (cell, chunk)  velocity-chunk partial moments of phi~ in the cell's frame
 //   U_CELL_FIN   cell           Eqs. discrete_W, discrete_q, tau, model + compatibility
-//                               correction (Sec. 3.3.1), blending weights
+//                               correction (Sec. 3.3.1), blending weights, from the
+//                               velocity-chunk partial moments of phi~ in the cell's frame
 //   U_BARP       (v, cell)      phi-bar-plus = phi~ + b (phi^S - phi~)
 //   U_GRAD       (v, cell)      least-squares gradient of phi-bar-plus over the face
 //                               neighbours (a boundary face adds the cell reflected through it,
 //                               a zero difference), Venkatakrishnan-limited
-//   U_FACE_BAR   (v, face)      Eq. reconstruction from the upwind side (a boundary face's
-//                               ghost: the cell's own data at the reflected centroid)
-//   U_FACE_SUMS  (face, chunk)  face moments of phi-bar (Eq. W_from_bar), or on a wall face
-//                               the outgoing normal mass flux
+//   U_FACE_BAR   (face, chunk)  Eq. reconstruction from the upwind side (a boundary face's
+//                               ghost: the cell's own data at the reflected centroid) over the
+//                               chunk's velocities, and their face moments (Eq. W_from_bar), or
+//                               on a wall face their outgoing normal mass flux
 //   U_FACE_FIN   face           face state, model + correction, Eq. recover_phi weights; on a
 //                               wall face rho_w from zero net mass flux
 //   U_FLUX       (v, face)      (xi.n) |f| phi_face (a wall face emits rho_w g_w inward)
-//   U_UPDATE     (v, cell)      Eq. explicit_update: phi~+ - dt/|V| sum_faces flux
+//   U_UPDATE     (cell, chunk)  Eq. explicit_update: phi~+ - dt/|V| sum_faces flux over the
+//                               chunk's velocities, and the partial moments of the new phi~
+//                               that the next step's U_CELL_FIN sums
+// U_CELL_SUMS forms those partial moments once after the initial state.  A (face, chunk) or
+// (cell, chunk) pass takes consecutive faces or cells on consecutive threads, so at each
+// velocity of its loop a warp's loads and stores stay coalesced.
 // Layouts (flat, cells and faces contiguous within a velocity plane):
 //   f, barp  [comp][v][cell];  grad [comp][dir][v][cell];  fbar, flux [comp][v][face]
 //   part_c [chunk][NMOM][cell], part_f [chunk][NMOM][face] (double)
@@ -29,7 +34,7 @@
 
 namespace mlvs {
 
-enum { U_CELL_SUMS = 0, U_CELL_FIN, U_BARP, U_GRAD, U_FACE_BAR, U_FACE_SUMS, U_FACE_FIN, U_FLUX, U_UPDATE,
+enum { U_CELL_SUMS = 0, U_CELL_FIN, U_BARP, U_GRAD, U_FACE_BAR, U_FACE_FIN, U_FLUX, U_UPDATE,
        U_INIT_PARAMS, U_INIT_F, U_WALL_DEN, U_NPASS };
 // per-cell geometry rows: area, centroid, inverse least-squares normal matrix, area^{3/2}
 enum { UC_AREA = 0, UC_CX, UC_CY, UC_MXX, UC_MXY, UC_MYY, UC_H3, UC_N };
@@ -70,16 +75,17 @@ __device__ __forceinline__ T u_xi(const UArgs<T>& a, int v, int d) {
   return reinterpret_cast<const T*>(a.pa.vt)[(long)d * a.nv + v];
 }
 
-// chunk partial moments of the phi-bar data of one point over [v0, v1), in the frame (ux, uy)
-template <class T>
-__device__ inline void u_chunk_moments(const UArgs<T>& a, const T* src, long n, long i, int v0, int v1, T ux,
-                                       T uy, double* out, long stride) {
+// Partial moments of one point's values over a run of velocities, in the frame (ux, uy):
+// M0 = sum w g, M_x, M_y = sum w c g, E = sum w (|c|^2 g + h), G = sum w c c g,
+// J = sum w c (|c|^2 g + h) (compensated where the finalisation subtracts large terms).
+template <class T> struct UMom {
   KSum<T> a0, ax, ay, ae;
-  a0.zero(); ax.zero(); ay.zero(); ae.zero();
-  T gxx = 0, gxy = 0, gyy = 0, jx = 0, jy = 0;
-  const long nv = a.nv;
-  for (int v = v0; v < v1; ++v) {
-    const T gq = src[(long)v * n + i], hq = src[(nv + v) * n + i];
+  T gxx, gxy, gyy, jx, jy;
+  __device__ __forceinline__ void zero() {
+    a0.zero(); ax.zero(); ay.zero(); ae.zero();
+    gxx = gxy = gyy = jx = jy = T(0);
+  }
+  __device__ __forceinline__ void add(const UArgs<T>& a, int v, T gq, T hq, T ux, T uy) {
     const T xp = u_xi(a, v, 0) - ux, yp = u_xi(a, v, 1) - uy;
     const T wxv = u_xi(a, v, 2), wyv = u_xi(a, v, 3);
     const T wg = wxv * (wyv * gq);
@@ -88,10 +94,12 @@ __device__ inline void u_chunk_moments(const UArgs<T>& a, const T* src, long n, 
     gxx += wg * xp * xp; gxy += wg * xp * yp; gyy += wg * yp * yp;
     jx += e * xp; jy += e * yp;
   }
-  out[MO_0 * stride] = a0.val(); out[MO_X * stride] = ax.val(); out[MO_Y * stride] = ay.val();
-  out[MO_E * stride] = ae.val(); out[MO_GXX * stride] = gxx; out[MO_GXY * stride] = gxy;
-  out[MO_GYY * stride] = gyy; out[MO_JX * stride] = jx; out[MO_JY * stride] = jy;
-}
+  __device__ __forceinline__ void store(double* out, long stride) const {
+    out[MO_0 * stride] = a0.val(); out[MO_X * stride] = ax.val(); out[MO_Y * stride] = ay.val();
+    out[MO_E * stride] = ae.val(); out[MO_GXX * stride] = gxx; out[MO_GXY * stride] = gxy;
+    out[MO_GYY * stride] = gyy; out[MO_JX * stride] = jx; out[MO_JY * stride] = jy;
+  }
+};
 
 // frame of a face's moments: the mean of its cells' velocities (its only cell on a boundary)
 template <class T>
@@ -300,8 +308,11 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
   if constexpr (E == U_CELL_SUMS) {
     const int c = (int)(i % nc), chunk = (int)(i / nc);
     const int v0 = chunk * a.vpc, v1 = min(a.nv, v0 + a.vpc);
-    u_chunk_moments<T>(a, a.f, nc, c, v0, v1, a.cprm[P_UX * nc + c], a.cprm[P_UY * nc + c],
-                       a.part_c + (long)chunk * NMOM * nc + c, nc);
+    const T ux = a.cprm[P_UX * nc + c], uy = a.cprm[P_UY * nc + c];
+    UMom<T> acc;
+    acc.zero();
+    for (int v = v0; v < v1; ++v) acc.add(a, v, a.f[(long)v * nc + c], a.f[(nv + v) * nc + c], ux, uy);
+    acc.store(a.part_c + (long)chunk * NMOM * nc + c, nc);
   } else if constexpr (E == U_CELL_FIN) {
     finalize_point<T, 2, 0>(a.pa, (int)i);
     if (a.compat8 && a.pa.compat) {
@@ -370,40 +381,46 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
       a.grad[(((long)comp * 2 + 1) * nv + v) * nc + c] = gy;
     }
   } else if constexpr (E == U_FACE_BAR) {
-    const int fi = (int)(i % nf), v = (int)(i / nf);
+    const int fi = (int)(i % nf), chunk = (int)(i / nf);
+    const int v0 = chunk * a.vpc, v1 = min(a.nv, v0 + a.vpc);
     const T s = T(0.5 * a.dt);
-    const T xx = u_xi(a, v, 0), yy = u_xi(a, v, 1);
-    const T xn = a.fgeo[UF_NX * nf + fi] * xx + a.fgeo[UF_NY * nf + fi] * yy;
+    const T nx = a.fgeo[UF_NX * nf + fi], ny = a.fgeo[UF_NY * nf + fi];
     const T mx = a.fgeo[UF_MX * nf + fi], my = a.fgeo[UF_MY * nf + fi];
     const int L = a.fcell[fi], R = a.fcell[nf + fi];
     const T oxL = mx - a.cgeo[UC_CX * nc + L], oyL = my - a.cgeo[UC_CY * nc + L];
-    for (int comp = 0; comp < 2; ++comp) {
-      const T vL = u_recon<T>(a, comp, v, L, oxL, oyL, xx * s, yy * s);
-      const T vR = R >= 0 ? u_recon<T>(a, comp, v, R, mx - a.cgeo[UC_CX * nc + R], my - a.cgeo[UC_CY * nc + R],
-                                       xx * s, yy * s)
-                          : u_recon<T>(a, comp, v, L, -oxL, -oyL, xx * s, yy * s);
-      a.fbar[((long)comp * nv + v) * nf + fi] = xn > T(0) ? vL : (xn < T(0) ? vR : T(0.5) * (vL + vR));
-    }
-  } else if constexpr (E == U_FACE_SUMS) {
-    const int fi = (int)(i % nf), chunk = (int)(i / nf);
-    const int v0 = chunk * a.vpc, v1 = min(a.nv, v0 + a.vpc);
-    double* out = a.part_f + (long)chunk * NMOM * nf + fi;
-    if (a.fwall[fi] >= 0) {
-      // outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) phi-bar_g (xi.n_in = -xi.n)
-      KSum<T> m0;
-      m0.zero();
-      const T nx = a.fgeo[UF_NX * nf + fi], ny = a.fgeo[UF_NY * nf + fi];
-      for (int v = v0; v < v1; ++v) {
-        const T xin = -(nx * u_xi(a, v, 0) + ny * u_xi(a, v, 1));
-        if (xin <= T(0)) m0.add(u_xi(a, v, 2) * (u_xi(a, v, 3) * (xin * a.fbar[(long)v * nf + fi])));
+    const T oxR = R >= 0 ? mx - a.cgeo[UC_CX * nc + R] : -oxL, oyR = R >= 0 ? my - a.cgeo[UC_CY * nc + R] : -oyL;
+    const int Rc = R >= 0 ? R : L;                  // a boundary face's ghost carries L's data
+    const bool wall = a.fwall[fi] >= 0;
+    T sx = T(0), sy = T(0);
+    if (!wall) u_face_shift<T>(a, fi, sx, sy);
+    UMom<T> acc;
+    acc.zero();
+    KSum<T> out0;                                   // wall: sum_{xi.n_in <= 0} w (xi.n_in) phi-bar_g
+    out0.zero();
+    for (int v = v0; v < v1; ++v) {
+      const T xx = u_xi(a, v, 0), yy = u_xi(a, v, 1);
+      const T xn = nx * xx + ny * yy;
+      T bar[2];
+      for (int comp = 0; comp < 2; ++comp) {
+        const T vL = u_recon<T>(a, comp, v, L, oxL, oyL, xx * s, yy * s);
+        const T vR = u_recon<T>(a, comp, v, Rc, oxR, oyR, xx * s, yy * s);
+        bar[comp] = xn > T(0) ? vL : (xn < T(0) ? vR : T(0.5) * (vL + vR));
+        a.fbar[((long)comp * nv + v) * nf + fi] = bar[comp];
       }
-      out[MO_0 * nf] = m0.val();
-      for (int m = 1; m < NMOM; ++m) out[m * nf] = 0.0;
-      return;
+      if (wall) {
+        const T xin = -xn;
+        if (xin <= T(0)) out0.add(u_xi(a, v, 2) * (u_xi(a, v, 3) * (xin * bar[0])));
+      } else {
+        acc.add(a, v, bar[0], bar[1], sx, sy);
+      }
     }
-    T sx, sy;
-    u_face_shift<T>(a, fi, sx, sy);
-    u_chunk_moments<T>(a, a.fbar, nf, fi, v0, v1, sx, sy, out, nf);
+    double* out = a.part_f + (long)chunk * NMOM * nf + fi;
+    if (wall) {
+      out[MO_0 * nf] = out0.val();
+      for (int m = 1; m < NMOM; ++m) out[m * nf] = 0.0;
+    } else {
+      acc.store(out, nf);
+    }
   } else if constexpr (E == U_FACE_FIN) {
     const int fi = (int)i;
     double M[NMOM];
@@ -483,20 +500,31 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
     a.flux[(long)v * nf + fi] = scale * gp;
     a.flux[(nv + v) * nf + fi] = scale * hp;
   } else if constexpr (E == U_UPDATE) {
-    const int c = (int)(i % nc), v = (int)(i / nc);
+    const int c = (int)(i % nc), chunk = (int)(i / nc);
+    const int v0 = chunk * a.vpc, v1 = min(a.nv, v0 + a.vpc);
     const T dtA = T(a.dt / (double)a.cgeo[UC_AREA * nc + c]);
-    for (int comp = 0; comp < 2; ++comp) {
-      const long at = ((long)comp * nv + v) * nc + c;
-      const T t = a.f[at], bp = a.barp[at];
-      T div = T(0);
-      for (int k = a.cf_ptr[c]; k < a.cf_ptr[c + 1]; ++k) {
-        const int s = a.cf[k];
-        const T F = a.flux[((long)comp * nv + v) * nf + (s >= 0 ? s : -s - 1)];
-        div = s >= 0 ? div + F : div - F;
+    const T ux = a.cprm[P_UX * nc + c], uy = a.cprm[P_UY * nc + c];   // the next step's frame
+    const int k0 = a.cf_ptr[c], k1 = a.cf_ptr[c + 1];
+    UMom<T> acc;
+    acc.zero();
+    for (int v = v0; v < v1; ++v) {
+      T nw[2];
+      for (int comp = 0; comp < 2; ++comp) {
+        const long at = ((long)comp * nv + v) * nc + c;
+        const T t = a.f[at], bp = a.barp[at];
+        T div = T(0);
+        for (int k = k0; k < k1; ++k) {
+          const int sg = a.cf[k];
+          const T F = a.flux[((long)comp * nv + v) * nf + (sg >= 0 ? sg : -sg - 1)];
+          div = sg >= 0 ? div + F : div - F;
+        }
+        const T tp = t + T(4.0 / 3.0) * (bp - t);   // phi~+ = 4/3 phi-bar-plus - 1/3 phi~
+        nw[comp] = tp - dtA * div;
+        a.f[at] = nw[comp];
       }
-      const T tp = t + T(4.0 / 3.0) * (bp - t);   // phi~+ = 4/3 phi-bar-plus - 1/3 phi~
-      a.f[at] = tp - dtA * div;
+      acc.add(a, v, nw[0], nw[1], ux, uy);
     }
+    acc.store(a.part_c + (long)chunk * NMOM * nc + c, nc);
   } else if constexpr (E == U_INIT_PARAMS) {
     const int c = (int)i;
     const double* w = a.W0 + 4 * (long)c;
@@ -543,11 +571,11 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
 template <class T>
 inline long u_extent(const UArgs<T>& a, int E) {
   switch (E) {
-    case U_CELL_SUMS: return (long)a.nc * a.nchunk;
+    case U_CELL_SUMS: case U_UPDATE: return (long)a.nc * a.nchunk;
     case U_CELL_FIN: case U_INIT_PARAMS: return a.nc;
-    case U_BARP: case U_GRAD: case U_UPDATE: case U_INIT_F: return (long)a.nv * a.nc;
-    case U_FACE_BAR: case U_FLUX: return (long)a.nv * a.nf;
-    case U_FACE_SUMS: return (long)a.nf * a.nchunk;
+    case U_BARP: case U_GRAD: case U_INIT_F: return (long)a.nv * a.nc;
+    case U_FLUX: return (long)a.nv * a.nf;
+    case U_FACE_BAR: return (long)a.nf * a.nchunk;
     case U_FACE_FIN: case U_WALL_DEN: return a.nf;
   }
   return 0;
@@ -557,22 +585,22 @@ inline long u_extent(const UArgs<T>& a, int E) {
 // elements (a kernel launch, or a loop).
 template <class T, class Run>
 inline void u_step_sequence(Run& run, const UArgs<T>& a) {
-  run.template pass<U_CELL_SUMS>(u_extent(a, U_CELL_SUMS));
   run.template pass<U_CELL_FIN>(u_extent(a, U_CELL_FIN));
   run.template pass<U_BARP>(u_extent(a, U_BARP));
   run.template pass<U_GRAD>(u_extent(a, U_GRAD));
   run.template pass<U_FACE_BAR>(u_extent(a, U_FACE_BAR));
-  run.template pass<U_FACE_SUMS>(u_extent(a, U_FACE_SUMS));
   run.template pass<U_FACE_FIN>(u_extent(a, U_FACE_FIN));
   run.template pass<U_FLUX>(u_extent(a, U_FLUX));
   run.template pass<U_UPDATE>(u_extent(a, U_UPDATE));
 }
 
-// Initial state phi~ = corrected Maxwellian of W0, and the wall normalisations.
+// Initial state phi~ = corrected Maxwellian of W0, its partial moments, and the wall
+// normalisations.
 template <class T, class Run>
 inline void u_init_sequence(Run& run, const UArgs<T>& a) {
   run.template pass<U_INIT_PARAMS>(u_extent(a, U_INIT_PARAMS));
   run.template pass<U_INIT_F>(u_extent(a, U_INIT_F));
+  run.template pass<U_CELL_SUMS>(u_extent(a, U_CELL_SUMS));
   run.template pass<U_WALL_DEN>(u_extent(a, U_WALL_DEN));
 }
 
