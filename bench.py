@@ -310,6 +310,8 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
         ms = s.moments(F)
         out["run"] = {"tau_clust": 0.05, "eps_merge": 5e-5, "adapt_interval": 100, "steps": run_steps,
                       "compared_at_step": warm_steps + run_steps, "spaces_first": a.n_levels,
+                      "adapt_ms_first": a.ms_total,
+                      "cross_fraction_first": a.n_cross_faces / max(1, a.n_interior_faces),
                       "mean_points_per_cell_first": a.updates_per_step / (nt * nr),
                       "mlvs_ms_per_step": sm.ms_total / run_steps, "uvs_ms_per_step": uvs_ms,
                       "speedup_vs_uvs": uvs_ms / (sm.ms_total / run_steps),
@@ -324,8 +326,19 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
             sm = s.step(50)
             out["tau_sweep"].append({"tau_clust": tau, "spaces": a.n_levels, "distinct_masks": a.n_distinct,
                                      "mean_points_per_cell": a.updates_per_step / (nt * nr),
+                                     "cross_faces": a.n_cross_faces, "interior_faces": a.n_interior_faces,
                                      "ms_per_step": sm.ms_total / 50, "speedup_vs_uvs": uvs_ms / (sm.ms_total / 50),
                                      "adapt_ms": a.ms_total})
+        # the paper's runtime model t/t_UVS ~ r + lambda_cross f + c, calibrated on this sweep
+        from paper_2609_35258_b300 import runtime_model as RM
+        sw = out["tau_sweep"]
+        r = [x["mean_points_per_cell"] / nv for x in sw]
+        f = [x["cross_faces"] / max(1, x["interior_faces"]) for x in sw]
+        m = RM.fit(r, f, [x["ms_per_step"] / uvs_ms for x in sw])
+        out["runtime_model"] = {"lambda_cross": m["lambda_cross"], "c": m["c"], "r2": m["r2"],
+                                "r": r, "f": f, "t_rel": [x["ms_per_step"] / uvs_ms for x in sw],
+                                "t_rel_model": [float(v) for v in m["t_rel_model"]],
+                                "update_term_at_interval_100": out["run"]["adapt_ms_first"] / (100.0 * uvs_ms)}
     except M.MLVSError as e:
         out["error"] = str(e)
     s.close()

@@ -156,6 +156,8 @@ typedef struct {
   float ms_group;                /* wall time of the mask download and the grouping       */
   float ms_remap;                /* wall time of the level rebuild and the remap          */
   float ms_total;                /* wall time of the call                                 */
+  int n_interior_faces;          /* faces between two cells, all instances (N_int, Sec. 3.5) */
+  int n_cross_faces;             /* of those, faces between two levels (N_cross)          */
 } mlvs_adapt_stats;
 
 /* Velocity-space requirement of every cell of one instance (Sec. 3.2, criterion only): the

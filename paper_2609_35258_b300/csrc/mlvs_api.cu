@@ -137,6 +137,7 @@ struct Inst {
   MapBatch gb;
   std::vector<MapBatch> fb;  // flux routes by source level (only routes[0] is used)
   std::vector<int> order;    // levels by decreasing velocity count
+  int n_int = 0, n_cross = 0;  // interior faces, and those between two levels (Sec. 3.5)
 };
 
 // Event pairs recorded around launches when a step is profiled.
@@ -1088,6 +1089,8 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
   auto bump = [&](std::vector<int>& v, int l) { if ((int)v.size() <= l) v.resize(l + 1, 0); return v[l]++; };
   std::map<std::pair<int, int>, std::vector<MapItem>> flux_items;
   std::vector<std::array<int, 3>> face_cells(nface);   // cL, cR, wall-side (-1 none)
+  I.n_int = 0;
+  I.n_cross = 0;
   for (int f = 0; f < nface; ++f) {
     int cL, cR, wall = -1;
     if (f < nfx * ny) {
@@ -1110,7 +1113,9 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
       role[lvl_of[c]][f] = FR_NORMAL;
       continue;
     }
+    ++I.n_int;
     if (lL == lR) { role[lL][f] = FR_NORMAL; continue; }
+    ++I.n_cross;
     // cross-level face: evaluated on the common refinement of the two spaces (Sec. 3.4)
     const SpaceRt& SL = h->spaces[h->level_space[lL]];
     const SpaceRt& SR = h->spaces[h->level_space[lR]];
@@ -1820,6 +1825,12 @@ static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_spac
     stats->n_levels = h->n_levels;
     stats->n_changed = changed;
     stats->updates_per_step = upd;
+    stats->n_interior_faces = 0;
+    stats->n_cross_faces = 0;
+    for (auto& I : h->inst) {
+      stats->n_interior_faces += I.n_int;
+      stats->n_cross_faces += I.n_cross;
+    }
   }
   return same ? MLVS_OK : check_flags(h);
 }

@@ -56,7 +56,8 @@ class mlvs_adapt_params(C.Structure):
 class mlvs_adapt_stats(C.Structure):
     _fields_ = [("n_levels", C.c_int), ("n_distinct", C.c_int), ("n_changed", C.c_int),
                 ("updates_per_step", C.c_longlong), ("ms_criterion", C.c_float),
-                ("ms_group", C.c_float), ("ms_remap", C.c_float), ("ms_total", C.c_float)]
+                ("ms_group", C.c_float), ("ms_remap", C.c_float), ("ms_total", C.c_float),
+                ("n_interior_faces", C.c_int), ("n_cross_faces", C.c_int)]
 
 
 class mlvs_uconfig(C.Structure):

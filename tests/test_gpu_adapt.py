@@ -117,6 +117,11 @@ def test_adapt_matches_oracle_grouping_and_conserves():
     for c in range(64):
         np.testing.assert_array_equal(M.mlvs_level_kappa(s.h, lv[c]), keff[lab[c]])
     assert st.n_distinct == len(np.unique(ko, axis=0))
+    # N_int and N_cross of Sec. 3.5: every face of the doubly periodic 8 x 8 mesh is interior;
+    # a face is cross-level when its two cells sit on different levels
+    L2 = lv.reshape(8, 8)
+    assert st.n_interior_faces == 128
+    assert st.n_cross_faces == int(np.sum(L2 != np.roll(L2, -1, axis=1)) + np.sum(L2 != np.roll(L2, -1, axis=0)))
     # and the adapted run keeps conserving
     assert st.n_levels > 1
     s.step(5)
