@@ -116,3 +116,21 @@ def test_chunking_changes_only_the_rounding(storage):
     ma, mb = a.moments(), b.moments()
     tol = 1e-12 if storage == "f64" else 1e-6
     assert np.max(np.abs(ma - mb)) < tol * np.max(np.abs(ma))
+
+
+def test_step_many_with_each_case_reclustering_on_its_own():
+    """Independent cases with their own criterion thresholds, clustering thresholds and
+    adaptation intervals (so their numbers of representative spaces change independently)
+    advance through the batched launch exactly as they do alone."""
+    descs = [workloads.cavity(16, n_base=41, storage="f32"), workloads.periodic_random(20, 12, n_base=41)]
+    params = [(M.adapt_params(5e-3, 2.5e-3, 5e-5, 0.05, 2), 5), (M.adapt_params(1e-2, 5e-3, 0.0, 0.2, 3), 7)]
+    alone = [Solver(d, adaptive=1) for d in descs]
+    group = [Solver(d, adaptive=1) for d in descs]
+    for s, (p, k) in zip(alone + group, params + params):
+        M.mlvs_set_adaptation(s.h, p, k)
+    for s in alone:
+        s.step(23)
+    M.mlvs_step_many([s.h for s in group], 23, use_graph=True)
+    F = M.RHO | M.U | M.V | M.T | M.LEVEL
+    for s1, s2 in zip(alone, group):
+        np.testing.assert_array_equal(s1.moments(F), s2.moments(F))
