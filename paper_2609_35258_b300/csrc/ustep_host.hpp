@@ -61,6 +61,7 @@ inline std::string u_config(const mlvs_uconfig& c, UHostConfig& u) {
   u.n_wall = c.n_wall;
   for (int w = 0; w < 8; ++w)
     for (int j = 0; j < 3; ++j) u.wall[w][j] = c.wall[w][j];
+  if (c.vpc < 0) return "vpc must be >= 0 (0: 64)";
   u.vpc = c.vpc > 0 ? c.vpc : 64;
   return "";
 }
