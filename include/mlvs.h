@@ -81,6 +81,10 @@ typedef struct {
                            on a periodic side the last node column/row repeats the first (an
                            O-grid) or is its translate.  Slopes along the index directions
                            become physical through J^{-T}; dt = cfl min |V|/max|S| / max|xi| */
+  int positive_mapping; /* 1 (dim 2): a level switch whose additive four-moment result has a
+                           negative g where the projection has none takes the exponential
+                           correction of the same targets instead (Sec. 3.3.2,
+                           Eq. exponential_moment_correction)                               */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */
@@ -158,6 +162,10 @@ typedef struct {
   float ms_total;                /* wall time of the call                                 */
   int n_interior_faces;          /* faces between two cells, all instances (N_int, Sec. 3.5) */
   int n_cross_faces;             /* of those, faces between two levels (N_cross)          */
+  int n_exp_corrected;           /* positive_mapping: cells remapped with the exponential
+                                    correction                                            */
+  int n_exp_failed;              /* positive_mapping: cells whose Newton iteration did not
+                                    converge (they keep the additive result)              */
 } mlvs_adapt_stats;
 
 /* Velocity-space requirement of every cell of one instance (Sec. 3.2, criterion only): the

@@ -40,6 +40,7 @@
 #include "finalize.cuh"
 #include "mapping.cuh"
 #include "criterion.cuh"
+#include "expmap.cuh"
 #include "features.cuh"
 #include "cluster_host.hpp"
 #include "vspace_host.hpp"
@@ -162,6 +163,7 @@ struct Prof {
 
 struct mlvs_handle {
   mlvs_config cfg;
+  int exp_corrected = 0, exp_failed = 0;   // positivity fallback of the last remap
   Prof prof;
   bool profiling = false;
   int launches = 0;
@@ -890,6 +892,7 @@ template <class S, class T, int D> struct Runner {
   // move every cell's phi~ from the old levels to the new ones (copy or level switch)
   static cudaError_t transfer(mlvs_handle* h, Inst& Old, Inst& New) {
     const int ncell = h->nx * h->ny;
+    cudaError_t e = cudaSuccess;
     std::map<std::pair<int, int>, std::vector<MapItem>> groups;
     for (int c = 0; c < ncell; ++c) {
       const int lo = Old.lvl_of[c], ln = New.lvl_of[c];
@@ -899,7 +902,7 @@ template <class S, class T, int D> struct Runner {
       LevelRt& Lo = Old.lv[g.first.first];
       LevelRt& Ln = New.lv[g.first.second];
       DevBuf items;
-      cudaError_t e = upload(items, g.second, h->stream);
+      e = upload(items, g.second, h->stream);
       if (e != cudaSuccess) return e;
       const int ni = (int)g.second.size();
       if (Lo.space == Ln.space) {
@@ -921,6 +924,20 @@ template <class S, class T, int D> struct Runner {
         m.nitems = ni;
         ++h->launches;
         launch_map<S, S, SRC_TILDE>(h, m);
+        if (D == 2 && h->cfg.positive_mapping) {
+          // the exponential correction where the additive result went negative (Sec. 3.3.2)
+          DevBuf cnt;
+          if ((e = cnt.alloc(2 * sizeof(int))) != cudaSuccess) return e;
+          if ((e = cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int), h->stream)) != cudaSuccess) return e;
+          ++h->launches;
+          k_expmap<S, T><<<(ni + 127) / 128, 128, 0, h->stream>>>(m, cnt.as<int>());
+          int hc[2] = {0, 0};
+          if ((e = cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+            return e;
+          if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return e;
+          h->exp_corrected += hc[0];
+          h->exp_failed += hc[1];
+        }
       }
       e = cudaStreamSynchronize(h->stream);   // items freed at scope end
       if (e != cudaSuccess) return e;
@@ -1786,6 +1803,7 @@ static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_spac
   for (int i = 0; i < ninst && same; ++i)
     for (int c = 0; c < ncell && same; ++c) same = cell_level[(size_t)i * ncell + c] == h->inst[i].lvl_of[c];
   int changed = 0;
+  h->exp_corrected = h->exp_failed = 0;
   if (!same) {
     // the current state's moments and parameters (for the shifts), then the new level set
     for (auto& I : h->inst)
@@ -1825,6 +1843,8 @@ static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_spac
     stats->n_levels = h->n_levels;
     stats->n_changed = changed;
     stats->updates_per_step = upd;
+    stats->n_exp_corrected = h->exp_corrected;
+    stats->n_exp_failed = h->exp_failed;
     stats->n_interior_faces = 0;
     stats->n_cross_faces = 0;
     for (auto& I : h->inst) {

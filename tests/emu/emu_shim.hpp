@@ -10,6 +10,10 @@
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
+#ifndef __launch_bounds__
+#define __launch_bounds__(...)
+#endif
+
 using std::isfinite;
 using std::max;
 using std::min;
@@ -28,6 +32,7 @@ static inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f
 template <class X> static inline X __shfl_xor_sync(unsigned, X v, int, int = 32) { return v; }
 static inline void __syncthreads() {}
 static inline int atomicOr(int* p, int v) { const int o = *p; *p |= v; return o; }
+static inline int atomicAdd(int* p, int v) { const int o = *p; *p += v; return o; }
 // launch coordinates: referenced by kernels the emulator compiles but never runs
 static const uint3 threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0};
 static const dim3 blockDim(1, 1, 1), gridDim(1, 1, 1);
