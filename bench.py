@@ -273,7 +273,8 @@ def _selector_leg():
             "workload": "periodic random states, 64^2 cells, base 41^2, four radial levels"}
 
 
-def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07, 0.05, 0.04, 0.035)):
+def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07, 0.05, 0.04, 0.035),
+                  positive_mapping=0):
     """Ma 5 flow past a cylinder (O-grid 256 x 128, Kn 0.1, base 201^2 on [-15, 15]^2).  UVS runs
     first and keeps its fields at the comparison step.  MLVS then starts from the same initial
     state and, once the impulsive start's near-vacuum wake has filled (`warm_steps`), runs the
@@ -281,7 +282,8 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
     rebuilt every 100 steps) with the transport test on (eps_merge 5e-5, the cavity's value; the
     paper gives none for the cylinder) for `run_steps` steps; its fields are compared with UVS at
     the same step.  Afterwards the same state is adapted with each clustering threshold in turn and timed
-    for 50 steps.  A failing MLVS step is reported in the result instead of ending the benchmark."""
+    for 50 steps.  A failing MLVS step is reported in the result instead of ending the benchmark.
+    positive_mapping = 1 gives the level switches the exponential fallback (Sec. 3.3.2)."""
     import numpy as np
     from paper_2609_35258_b300 import mlvs as M, workloads
     from paper_2609_35258_b300.solver import Solver
@@ -299,7 +301,8 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
     out = {"workload": f"cylinder O-grid {nt}x{nr}, Ma 5, Kn 0.1, base 201^2 on [-15,15]^2, {storage}",
            "uvs_ms_per_step": uvs_ms, "uvs_points_per_cell": nv, "adapt_from_step": warm_steps,
            "run": None, "tau_sweep": []}
-    s = Solver(d, adaptive=1)
+    s = Solver(d, adaptive=1, positive_mapping=positive_mapping)
+    out["positive_mapping"] = positive_mapping
     M.mlvs_set_graph(s.h, True)
     try:
         s.step(warm_steps)
@@ -511,7 +514,8 @@ def run_ours(args, rank, world, local_rank):
     selector = None
     if not args.no_selector and rank == 0:
         selector = _selector_leg()
-    cylinder = _cylinder_leg() if (args.cylinder and rank == 0) else None
+    cylinder = (_cylinder_leg(positive_mapping=int(args.positive_mapping))
+                if (args.cylinder and rank == 0) else None)
     unstructured = _unstructured_leg() if (args.unstructured and rank == 0) else None
 
     # end-to-end through the public API: host init upload, steps, host moment reads
@@ -575,6 +579,8 @@ def main():
     ap.add_argument("--cells", type=int, default=64, help="cavity cells per side (default 64)")
     ap.add_argument("--cylinder", action="store_true",
                     help="add the Ma 5 cylinder leg (UVS vs MLVS over clustering thresholds, ~3 min)")
+    ap.add_argument("--positive-mapping", action="store_true",
+                    help="cylinder leg: exponential fallback for level switches that go negative")
     ap.add_argument("--unstructured", action="store_true",
                     help="add the two-cavity unstructured-mesh leg (13,600 quads, 101^2 velocities)")
     args = ap.parse_args()
