@@ -314,6 +314,7 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
         out["run"] = {"tau_clust": 0.05, "eps_merge": 5e-5, "adapt_interval": 100, "steps": run_steps,
                       "compared_at_step": warm_steps + run_steps, "spaces_first": a.n_levels,
                       "adapt_ms_first": a.ms_total,
+                      "exp_corrected_first": a.n_exp_corrected, "exp_failed_first": a.n_exp_failed,
                       "cross_fraction_first": a.n_cross_faces / max(1, a.n_interior_faces),
                       "mean_points_per_cell_first": a.updates_per_step / (nt * nr),
                       "mlvs_ms_per_step": sm.ms_total / run_steps, "uvs_ms_per_step": uvs_ms,
