@@ -85,6 +85,10 @@ typedef struct {
                            negative g where the projection has none takes the exponential
                            correction of the same targets instead (Sec. 3.3.2,
                            Eq. exponential_moment_correction)                               */
+  int map_moments;      /* 9 (dim 2): level switches use the nine-moment mapping (Sec. 3.3.2,
+                           Eqs. mapping_nine_targets to mapping_h_residual_correction: the
+                           source's raw moments up to G and J as targets); 0 or 4: the
+                           four-moment mapping.  Ghost-state and flux mappings keep four      */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */

@@ -40,7 +40,7 @@
 #include "finalize.cuh"
 #include "mapping.cuh"
 #include "criterion.cuh"
-#include "expmap.cuh"
+#include "map9.cuh"
 #include "features.cuh"
 #include "cluster_host.hpp"
 #include "vspace_host.hpp"
@@ -164,6 +164,7 @@ struct Prof {
 struct mlvs_handle {
   mlvs_config cfg;
   int exp_corrected = 0, exp_failed = 0;   // positivity fallback of the last remap
+  int map9_singular = 0;                    // nine-moment level switches with a singular block
   Prof prof;
   bool profiling = false;
   int launches = 0;
@@ -922,6 +923,20 @@ template <class S, class T, int D> struct Runner {
         m.prm_ld = 0;
         m.items = items.as<MapItem>();
         m.nitems = ni;
+        if (D == 2 && h->cfg.map_moments == 9) {
+          // the nine-moment level switch (Sec. 3.3.2): projection plus the block correction
+          DevBuf cnt;
+          if ((e = cnt.alloc(sizeof(int))) != cudaSuccess) return e;
+          if ((e = cudaMemsetAsync(cnt.p, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
+          ++h->launches;
+          k_map9<S, T><<<(ni + 127) / 128, 128, 0, h->stream>>>(m, cnt.as<int>());
+          int hc = 0;
+          if ((e = cudaMemcpyAsync(&hc, cnt.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
+            return e;
+          if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return e;
+          h->map9_singular += hc;
+          continue;
+        }
         ++h->launches;
         launch_map<S, S, SRC_TILDE>(h, m);
         if (D == 2 && h->cfg.positive_mapping) {
@@ -1447,6 +1462,10 @@ extern "C" mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out) {
       (cfg->dim == 2 && (cfg->bc[2] == MLVS_BC_PERIODIC) != (cfg->bc[3] == MLVS_BC_PERIODIC)))
     return fail(nullptr, MLVS_ERR_ARG, "periodic sides must come in pairs");
   if (cfg->storage < 0 || cfg->storage > 2) return fail(nullptr, MLVS_ERR_ARG, "unknown storage type");
+  if (cfg->map_moments != 0 && cfg->map_moments != 4 && cfg->map_moments != 9)
+    return fail(nullptr, MLVS_ERR_ARG, "map_moments must be 4 or 9 (0: 4)");
+  if (cfg->positive_mapping != 0 && cfg->positive_mapping != 1)
+    return fail(nullptr, MLVS_ERR_ARG, "positive_mapping must be 0 or 1");
   if (!(cfg->R > 0) || !(cfg->Pr > 0) || cfg->K_internal < 0) return fail(nullptr, MLVS_ERR_ARG, "bad gas constants");
   if (!(cfg->mu_ref > 0) && !(cfg->Kn > 0)) return fail(nullptr, MLVS_ERR_ARG, "need mu_ref > 0 or Kn > 0");
   if (!(cfg->dt > 0) && !(cfg->cfl > 0)) return fail(nullptr, MLVS_ERR_ARG, "need dt > 0 or cfl > 0");
@@ -1804,6 +1823,7 @@ static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_spac
     for (int c = 0; c < ncell && same; ++c) same = cell_level[(size_t)i * ncell + c] == h->inst[i].lvl_of[c];
   int changed = 0;
   h->exp_corrected = h->exp_failed = 0;
+  h->map9_singular = 0;
   if (!same) {
     // the current state's moments and parameters (for the shifts), then the new level set
     for (auto& I : h->inst)
@@ -1832,6 +1852,10 @@ static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_spac
       if (e != cudaSuccess) {
         h->sticky = MLVS_ERR_CUDA;
         return fail(h, MLVS_ERR_CUDA, std::string("adaptation remap: ") + cudaGetErrorString(e));
+      }
+      if (h->map9_singular) {
+        h->sticky = MLVS_ERR_SINGULAR;
+        return fail(h, MLVS_ERR_SINGULAR, "nine-moment level switch: singular correction block");
       }
       h->inst[i] = std::move(New);
     }

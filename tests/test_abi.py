@@ -42,7 +42,8 @@ def _cfg(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(dim=3), dict(nx=0), dict(bc=[0, 2, 0, 0]),
-                                 dict(Kn=0.0, mu_ref=0.0), dict(storage=7), dict(dim=1, ny=4)])
+                                 dict(Kn=0.0, mu_ref=0.0), dict(storage=7), dict(dim=1, ny=4),
+                                 dict(map_moments=8), dict(positive_mapping=2)])
 def test_create_rejects_bad_config(bad):
     from paper_2609_35258_b300 import mlvs
     with pytest.raises(mlvs.MLVSError) as e:

@@ -1,6 +1,9 @@
-"""The library's positivity fallback of the state mapping, run on the CPU (the per-item function
-its CUDA kernel calls, compiled as host C++), against the oracle's exponential correction
-(Sec. 3.3.2, Eq. exponential_moment_correction; `mapping.correct_exp4`).
+"""The library's per-item state mappings, run on the CPU (the functions its CUDA kernels call,
+compiled as host C++): the positivity fallback against the oracle's exponential correction
+(Sec. 3.3.2, Eq. exponential_moment_correction; `mapping.correct_exp4`), and the nine-moment
+mapping against the oracle's (`mapping.map9`; Eqs. mapping_nine_targets ...
+mapping_h_residual_correction), both ways between two masked spaces, which keeps the nine raw
+moments of the source to 1e-12.
 
 A post-shock state of the Mach 5 cylinder (hot Maxwellian carrying a cold beam) lives on one
 masked space and moves to another with the additive four-moment correction, which leaves
@@ -28,8 +31,9 @@ def lib():
     subprocess.run(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-I", CUDA_INC,
                     os.path.join(HERE, "emu", "expmap_emu.cpp"), "-o", out], check=True, capture_output=True)
     L = C.CDLL(out)
-    L.emu_expmap.argtypes = [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
-                             C.c_void_p, C.c_void_p]
+    for fn in (L.emu_expmap, L.emu_map9):
+        fn.argtypes = [C.c_int, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                       C.c_void_p, C.c_void_p]
     return L
 
 
@@ -70,13 +74,13 @@ def _csr(src, dst):
     return off, np.asarray(idx, dtype=np.int32), np.asarray(wgt, dtype=np.float64)
 
 
-def _run(lib, A, B, gA, hA, gl, hl):
+def _run(lib, A, B, gA, hA, gl, hl, fn="emu_expmap"):
     off, idx, wgt = _csr(A, B)
     sv, tv = _vt(A), _vt(B)
     src = np.ascontiguousarray(np.concatenate([gA, hA]))
     dst = np.ascontiguousarray(np.concatenate([gl, hl]))
-    code = lib.emu_expmap(A.nv, sv.ctypes.data, B.nv, tv.ctypes.data, off.ctypes.data, idx.ctypes.data,
-                          wgt.ctypes.data, src.ctypes.data, dst.ctypes.data)
+    code = getattr(lib, fn)(A.nv, sv.ctypes.data, B.nv, tv.ctypes.data, off.ctypes.data, idx.ctypes.data,
+                            wgt.ctypes.data, src.ctypes.data, dst.ctypes.data)
     return code, dst[:B.nv], dst[B.nv:]
 
 
@@ -124,3 +128,19 @@ def test_negative_projection_keeps_the_additive_result(lib, spaces):
     code, g, _ = _run(lib, A, B, gA, hA, gl, hl)
     assert code == 0
     np.testing.assert_array_equal(g, gl)
+
+
+@pytest.mark.parametrize("frac", [0.2, 0.05])
+@pytest.mark.parametrize("direction", ["A_to_B", "B_to_A"])
+def test_nine_moment_mapping_matches_the_oracle(lib, spaces, frac, direction):
+    bsp, state, A, B = spaces
+    if direction == "B_to_A":
+        A, B = B, A
+    gA, hA = mapping.project(*state(frac), bsp, A)
+    ge, he = mapping.map9(gA, hA, A, B)
+    code, g, h = _run(lib, A, B, gA, hA, np.zeros(B.nv), np.zeros(B.nv), fn="emu_map9")
+    assert code == 1
+    np.testing.assert_allclose(g, ge, rtol=0, atol=1e-12 * np.max(np.abs(ge)))
+    np.testing.assert_allclose(h, he, rtol=0, atol=1e-12 * np.max(np.abs(he)))
+    R0, R1 = mapping.raw9(gA, hA, A), mapping.raw9(g, h, B)
+    np.testing.assert_allclose(R1, R0, rtol=0, atol=1e-12 * np.max(np.abs(R0)))

@@ -192,3 +192,23 @@ def test_positive_mapping_keeps_conservation_and_changes_only_corrected_cells():
         runs.append((st.n_exp_corrected, s.moments(M.RHO | M.U | M.V | M.T | M.LEVEL)))
     if runs[1][0] == 0:
         np.testing.assert_array_equal(runs[0][1], runs[1][1])
+
+
+def test_nine_moment_level_switch_conserves():
+    """map_moments = 9: the level switches of an adaptation take the nine-moment mapping
+    (Sec. 3.3.2); it keeps the conserved moments to FP64 rounding, and differs from the
+    four-moment switch only in the cells whose space changed."""
+    desc = workloads.periodic_random(8, 8, n_base=41, umax=6.0, storage="f64", amp=0.3)
+    p = M.adapt_params(PAPER["C_split"], PAPER["C_merge"], PAPER["eps_merge"], 0.05, 3)
+    out = []
+    for nm in (4, 9):
+        s = Solver(desc, adaptive=1, map_moments=nm)
+        s.step(2)
+        tot0 = _totals(s)
+        st = M.mlvs_adapt(s.h, p)
+        assert st.n_changed > 0
+        assert np.max(np.abs(_totals(s) - tot0)) < 1e-12 * np.max(np.abs(tot0))
+        s.step(3)
+        assert np.max(np.abs(_totals(s) - tot0)) < 1e-12 * np.max(np.abs(tot0))
+        out.append(s.moments(M.RHO | M.T))
+    assert np.max(np.abs(out[0] - out[1])) > 0.0
