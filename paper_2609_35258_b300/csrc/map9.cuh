@@ -48,35 +48,69 @@ __device__ __forceinline__ void map9_add(double R[9], double w, double x, double
   R[7] += 0.5 * w * x * e; R[8] += 0.5 * w * y * e;
 }
 
-// Maps one item (a phi~ column from space s to space t) with the nine-moment correction into
-// dst; returns false if a block is singular (dst then holds the projection).
-template <class S, class T>
+// Source value j of an item in FP64: the stored value, or for SRC_BARP phi-bar-plus formed from
+// phi~ and the cell's parameters m (as k_map forms it).
+template <class SrcT, class T, int KIND>
+__device__ __forceinline__ void map9_src(const MapArgs& a, const MP<T>& m, int slot, int j, double& g, double& h) {
+  T gt, ht;
+  src_value<SrcT, T, 2, KIND>(a, slot, m, j, gt, ht);
+  g = (double)gt;
+  h = (double)ht;
+}
+
+// Projection of the item's source values onto target point i (coarsening averages g and
+// H = h + |xi|^2 g with the CSR weights, refinement inherits them; h = H - |xi_t|^2 g).
+template <class SrcT, class T, int KIND>
+__device__ inline void map9_project(const MapArgs& a, const MP<T>& m, int slot, int i, double& g, double& h) {
+  const T* vs = reinterpret_cast<const T*>(a.s.vt);
+  const T* vt = reinterpret_cast<const T*>(a.t.vt);
+  const T* wgt = reinterpret_cast<const T*>(a.wgt);
+  const int ns = a.s.nv, nt = a.t.nv;
+  double G = 0.0, H = 0.0;
+  for (int q = a.off[i]; q < a.off[i + 1]; ++q) {
+    const int j = a.idx[q];
+    double gj, hj;
+    map9_src<SrcT, T, KIND>(a, m, slot, j, gj, hj);
+    const double xj = (double)vs[j], yj = (double)vs[ns + j];
+    G += (double)wgt[q] * gj;
+    H += (double)wgt[q] * (hj + (xj * xj + yj * yj) * gj);
+  }
+  const double xi = (double)vt[i], yi = (double)vt[nt + i];
+  g = G;
+  h = H - (xi * xi + yi * yi) * G;
+}
+
+// Maps one item (a column of source kind KIND from space s to space t) with the nine-moment
+// correction into dst; returns false if a block is singular (dst then holds the projection).
+template <class SrcT, class DstT, class T, int KIND>
 __device__ inline bool map9_item(const MapArgs& a, int item) {
   const MapItem it = a.items[item];
   const T* vs = reinterpret_cast<const T*>(a.s.vt);
   const T* vt = reinterpret_cast<const T*>(a.t.vt);
-  const S* src = reinterpret_cast<const S*>(a.src);
-  S* dst = reinterpret_cast<S*>(a.dst);
+  DstT* dst = reinterpret_cast<DstT*>(a.dst);
   const int ns = a.s.nv, nt = a.t.nv;
-  const long sld = a.src_ld, dld = a.dst_ld;
+  const long dld = a.dst_ld;
+  MP<T> m;
+  if (KIND == SRC_BARP) m.load(reinterpret_cast<const T*>(a.prm), a.prm_ld, it.prm_slot);
   double tar[9] = {0}, cur[9] = {0};
   for (int j = 0; j < ns; ++j) {
     const double w = (double)vs[2 * ns + j] * (double)vs[3 * ns + j];
-    map9_add(tar, w, (double)vs[j], (double)vs[ns + j], (double)ldf<S, T>(src + (long)j * sld + it.src_slot),
-             (double)ldf<S, T>(src + ((long)ns + j) * sld + it.src_slot));
+    double g, h;
+    map9_src<SrcT, T, KIND>(a, m, it.src_slot, j, g, h);
+    map9_add(tar, w, (double)vs[j], (double)vs[ns + j], g, h);
   }
   double Ag[6][6] = {{0}}, Ah[6][6] = {{0}};
   for (int i = 0; i < nt; ++i) {
     double gp, hp;
-    expmap_project<S, T>(a, it.src_slot, i, gp, hp);
+    map9_project<SrcT, T, KIND>(a, m, it.src_slot, i, gp, hp);
     const double x = (double)vt[i], y = (double)vt[nt + i];
     const double w = (double)vt[2 * nt + i] * (double)vt[3 * nt + i];
     map9_add(cur, w, x, y, gp, hp);
     const double ph[6] = {1.0, x, y, x * x, y * y, x * y};
     for (int r = 0; r < 6; ++r)
-      for (int m = 0; m < 6; ++m) Ag[r][m] += w * ph[r] * ph[m];
+      for (int q = 0; q < 6; ++q) Ag[r][q] += w * ph[r] * ph[q];
     for (int r = 0; r < 3; ++r)
-      for (int m = 0; m < 3; ++m) Ah[r][m] += 0.5 * w * ph[r] * ph[m];
+      for (int q = 0; q < 3; ++q) Ah[r][q] += 0.5 * w * ph[r] * ph[q];
   }
   // g-block: defects of (rho, rho u, rho v, G_xx, G_yy, G_xy)
   const int gk[6] = {0, 1, 2, 4, 5, 6};
@@ -99,24 +133,25 @@ __device__ inline bool map9_item(const MapArgs& a, int item) {
   }
   for (int i = 0; i < nt; ++i) {
     double gp, hp;
-    expmap_project<S, T>(a, it.src_slot, i, gp, hp);
+    map9_project<SrcT, T, KIND>(a, m, it.src_slot, i, gp, hp);
     if (ok) {
       const double x = (double)vt[i], y = (double)vt[nt + i];
       gp += ag[0] + ag[1] * x + ag[2] * y + ag[3] * x * x + ag[4] * y * y + ag[5] * x * y;
       hp += bh[0] + bh[1] * x + bh[2] * y;
     }
-    stf<S, T>(dst + (long)i * dld + it.dst_slot, T(gp));
-    stf<S, T>(dst + ((long)nt + i) * dld + it.dst_slot, T(hp));
+    stf<DstT, T>(dst + (long)i * dld + it.dst_slot, T(gp));
+    stf<DstT, T>(dst + ((long)nt + i) * dld + it.dst_slot, T(hp));
   }
   return ok;
 }
 
-// The nine-moment level switch over the items of one route; counts[0] += singular items.
-template <class S, class T>
-__global__ void k_map9(const MapArgs a, int* counts) {
+// The nine-moment mapping over the items of one route (a level switch, the ghost states of a
+// stencil, or the microfluxes of cross-level faces); a singular block sets ERR_SINGULAR in err.
+template <class SrcT, class DstT, class T, int KIND>
+__global__ void k_map9(const MapArgs a, int* err) {
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= a.nitems) return;
-  if (!map9_item<S, T>(a, it)) atomicAdd(counts, 1);
+  if (!map9_item<SrcT, DstT, T, KIND>(a, it)) atomicOr(err, ERR_SINGULAR);
 }
 
 }  // namespace mlvs

@@ -717,8 +717,9 @@ template <class S, class T, int D> struct Runner {
   }
 
   static cudaError_t run_ghosts(mlvs_handle* h, Inst& I) {
+    const bool nine = D == 2 && h->cfg.map_moments == 9;
     // one launch for every route when all source levels are on the same buffer parity
-    if (I.gb.ok) {
+    if (I.gb.ok && !nine) {
       int par = -1;
       bool same = true;
       for (auto& r : I.ghosts) {
@@ -759,14 +760,16 @@ template <class S, class T, int D> struct Runner {
       m.items = r.items_d.as<MapItem>();
       m.nitems = (int)r.items.size();
       mark_begin(h, 4);
-      launch_map<S, T, SRC_BARP>(h, m);
+      if (nine) k_map9<S, T, T, SRC_BARP><<<(m.nitems + 127) / 128, 128, 0, h->stream>>>(m, I.err.as<int>());
+      else launch_map<S, T, SRC_BARP>(h, m);
       mark_end(h);
     }
     return cudaGetLastError();
   }
 
   static cudaError_t run_fluxes(mlvs_handle* h, Inst& I, int src) {
-    if (src < (int)I.fb.size() && I.fb[src].ok) {
+    const bool nine = D == 2 && h->cfg.map_moments == 9;
+    if (src < (int)I.fb.size() && I.fb[src].ok && !nine) {
       const MapBatch& B = I.fb[src];
       const MapArgs* rt = B.routes[0].as<MapArgs>();
       const MapWork* wk = B.work.as<MapWork>();
@@ -797,7 +800,8 @@ template <class S, class T, int D> struct Runner {
       m.items = r.items_d.as<MapItem>();
       m.nitems = (int)r.items.size();
       mark_begin(h, 5);
-      launch_map<T, T, SRC_FLUX>(h, m);
+      if (nine) k_map9<T, T, T, SRC_FLUX><<<(m.nitems + 127) / 128, 128, 0, h->stream>>>(m, I.err.as<int>());
+      else launch_map<T, T, SRC_FLUX>(h, m);
       mark_end(h);
     }
     return cudaGetLastError();
@@ -929,12 +933,12 @@ template <class S, class T, int D> struct Runner {
           if ((e = cnt.alloc(sizeof(int))) != cudaSuccess) return e;
           if ((e = cudaMemsetAsync(cnt.p, 0, sizeof(int), h->stream)) != cudaSuccess) return e;
           ++h->launches;
-          k_map9<S, T><<<(ni + 127) / 128, 128, 0, h->stream>>>(m, cnt.as<int>());
+          k_map9<S, S, T, SRC_TILDE><<<(ni + 127) / 128, 128, 0, h->stream>>>(m, cnt.as<int>());
           int hc = 0;
           if ((e = cudaMemcpyAsync(&hc, cnt.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
             return e;
           if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) return e;
-          h->map9_singular += hc;
+          if (hc) ++h->map9_singular;
           continue;
         }
         ++h->launches;

@@ -34,7 +34,7 @@ extern "C" int emu_map9(int ns, const double* svt, int nt, const double* tvt, co
                         const double* wgt, const double* src, double* dst) {
   const MapItem it = {0, 0, 0};
   const MapArgs a = one_item(ns, svt, nt, tvt, off, idx, wgt, src, dst, &it);
-  return map9_item<double, double>(a, 0) ? 1 : 0;
+  return map9_item<double, double, double, SRC_TILDE>(a, 0) ? 1 : 0;
 }
 
 extern "C" int emu_expmap(int ns, const double* svt, int nt, const double* tvt, const int* off, const int* idx,

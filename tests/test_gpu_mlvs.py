@@ -7,6 +7,8 @@ space), walls next to level interfaces, freestream sides on either level, and th
 of cells (remap).
 Tolerances as in test_gpu_parity: FP64 1e-10 relative, FP32 1e-5.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -150,3 +152,26 @@ def test_level_switch_conserves_and_matches():
     M.mlvs_set_cell_levels(s.h, 0, np.zeros(64, dtype=np.int32))
     back = s.moments(M.RHO | M.U | M.V | M.RHOE)
     np.testing.assert_allclose(back, before, rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 2e-5)])
+def test_two_uniform_levels_periodic_nine_moments(storage, tol):
+    """map_moments = 9: level switches, ghost states and cross-level microfluxes take the
+    nine-moment mapping (Sec. 3.3.2), as the oracle's multi-level step does with
+    Options(map_moments=9)."""
+    desc = workloads.periodic_random(16, 8, n_base=17, umax=5.0, storage=storage)
+    lev = np.array([0 if (c % 16) < 8 else 1 for c in range(128)], dtype=np.int32)
+    o = oracle_setup(desc)
+    o["opt"] = dataclasses.replace(o["opt"], map_moments=9)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(0), book.uniform(1)]
+    st = _oracle_state(desc, o, [keys[0]] * 128, book)
+    for c in range(128):
+        omlvs.remap(st, c, keys[lev[c]])
+    s = Solver(desc, levels=(0, 1), map_moments=9)
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    _compare_cells(s, st, 128, tol)
+    for _ in range(3):
+        omlvs.step(st)
+    s.step(3)
+    _compare_cells(s, st, 128, tol * 10)
