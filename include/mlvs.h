@@ -85,10 +85,11 @@ typedef struct {
                            negative g where the projection has none takes the exponential
                            correction of the same targets instead (Sec. 3.3.2,
                            Eq. exponential_moment_correction)                               */
-  int map_moments;      /* 9 (dim 2): level switches use the nine-moment mapping (Sec. 3.3.2,
-                           Eqs. mapping_nine_targets to mapping_h_residual_correction: the
-                           source's raw moments up to G and J as targets); 0 or 4: the
-                           four-moment mapping.  Ghost-state and flux mappings keep four      */
+  int map_moments;      /* 9 (dim 2): level switches, cross-level ghost states and cross-level
+                           microfluxes use the nine-moment mapping (Sec. 3.3.2, Eqs.
+                           mapping_nine_targets to mapping_h_residual_correction: the source's
+                           raw moments up to G and J as targets), one launch per route;
+                           0 or 4: the four-moment mapping                                   */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */
