@@ -81,10 +81,11 @@ typedef struct {
                            on a periodic side the last node column/row repeats the first (an
                            O-grid) or is its translate.  Slopes along the index directions
                            become physical through J^{-T}; dt = cfl min |V|/max|S| / max|xi| */
-  int positive_mapping; /* 1 (dim 2): a level switch whose additive four-moment result has a
-                           negative g where the projection has none takes the exponential
-                           correction of the same targets instead (Sec. 3.3.2,
-                           Eq. exponential_moment_correction)                               */
+  int positive_mapping; /* 1 (dim 2): a level switch or a cross-level ghost state whose additive
+                           four-moment result has a negative g where the projection has none
+                           takes the exponential correction of the same targets instead
+                           (Sec. 3.3.2, Eq. exponential_moment_correction); ghost routes are
+                           then launched one by one                                         */
   int map_moments;      /* 9 (dim 2): level switches, cross-level ghost states and cross-level
                            microfluxes use the nine-moment mapping (Sec. 3.3.2, Eqs.
                            mapping_nine_targets to mapping_h_residual_correction: the source's

@@ -9,7 +9,8 @@
 //
 // One item per call (one thread per item): the projection of the source column onto every
 // target point is recomputed from the CSR table in each residual evaluation, so the pass
-// needs no scratch memory; it is a fallback for the items that need it.
+// needs no scratch memory; it is a fallback for the items that need it.  The source values
+// are the stored phi~ (a level switch) or phi-bar-plus formed as k_map forms it (SRC_BARP).
 #pragma once
 #include "finalize.cuh"
 #include "mapping.cuh"
@@ -18,20 +19,29 @@ namespace mlvs {
 
 enum { EXPMAP_KEPT = 0, EXPMAP_REPLACED = 1, EXPMAP_FAILED = 2 };
 
-// Projection (g^p, h^p) of the item's source column onto target point i, in FP64.
-template <class S, class T>
-__device__ inline void expmap_project(const MapArgs& a, int slot, int i, double& g, double& h) {
+// Source value j of an item in FP64: the stored value, or for SRC_BARP phi-bar-plus formed from
+// phi~ and the cell's parameters m (as k_map forms it).
+template <class SrcT, class T, int KIND>
+__device__ __forceinline__ void map_src(const MapArgs& a, const MP<T>& m, int slot, int j, double& g, double& h) {
+  T gt, ht;
+  src_value<SrcT, T, 2, KIND>(a, slot, m, j, gt, ht);
+  g = (double)gt;
+  h = (double)ht;
+}
+
+// Projection of the item's source values onto target point i (coarsening averages g and
+// H = h + |xi|^2 g with the CSR weights, refinement inherits them; h = H - |xi_t|^2 g).
+template <class SrcT, class T, int KIND>
+__device__ inline void map_project(const MapArgs& a, const MP<T>& m, int slot, int i, double& g, double& h) {
   const T* vs = reinterpret_cast<const T*>(a.s.vt);
   const T* vt = reinterpret_cast<const T*>(a.t.vt);
   const T* wgt = reinterpret_cast<const T*>(a.wgt);
-  const S* src = reinterpret_cast<const S*>(a.src);
-  const long ld = a.src_ld;
   const int ns = a.s.nv, nt = a.t.nv;
   double G = 0.0, H = 0.0;
   for (int q = a.off[i]; q < a.off[i + 1]; ++q) {
     const int j = a.idx[q];
-    const double gj = (double)ldf<S, T>(src + (long)j * ld + slot);
-    const double hj = (double)ldf<S, T>(src + ((long)ns + j) * ld + slot);
+    double gj, hj;
+    map_src<SrcT, T, KIND>(a, m, slot, j, gj, hj);
     const double xj = (double)vs[j], yj = (double)vs[ns + j];
     G += (double)wgt[q] * gj;
     H += (double)wgt[q] * (hj + (xj * xj + yj * yj) * gj);
@@ -43,15 +53,15 @@ __device__ inline void expmap_project(const MapArgs& a, int slot, int i, double&
 
 // Residuals F_k = sum_i w_i kern_k(i) e_i - tar_k of the factor exp(a . psi), and with J the
 // Jacobian J_km = sum_i w_i kern_k(i) e_i psi_m(i).
-template <class S, class T>
-__device__ inline void expmap_residual(const MapArgs& a, int slot, const double c[4], const double tar[4],
-                                       double F[4], double (*J)[4]) {
+template <class SrcT, class T, int KIND>
+__device__ inline void expmap_residual(const MapArgs& a, const MP<T>& mp, int slot, const double c[4],
+                                       const double tar[4], double F[4], double (*J)[4]) {
   const T* vt = reinterpret_cast<const T*>(a.t.vt);
   const int nt = a.t.nv;
   double acc[4] = {0, 0, 0, 0}, jac[4][4] = {{0}};
   for (int i = 0; i < nt; ++i) {
     double gp, hp;
-    expmap_project<S, T>(a, slot, i, gp, hp);
+    map_project<SrcT, T, KIND>(a, mp, slot, i, gp, hp);
     const double x = (double)vt[i], y = (double)vt[nt + i];
     const double w = (double)vt[2 * nt + i] * (double)vt[3 * nt + i];
     const double psi[4] = {1.0, x, y, 0.5 * (x * x + y * y)};
@@ -70,30 +80,31 @@ __device__ inline void expmap_residual(const MapArgs& a, int slot, const double 
   }
 }
 
-// The fallback for one item of a level switch (a phi~ column mapped from space s to t): the
+// The fallback for one item (a level switch, or a ghost state with KIND = SRC_BARP): the
 // additive result in dst is kept unless it has a negative g where the projection has none.
-template <class S, class T>
+template <class SrcT, class DstT, class T, int KIND>
 __device__ inline int expmap_item(const MapArgs& a, int item) {
   const MapItem it = a.items[item];
   const T* vs = reinterpret_cast<const T*>(a.s.vt);
   const T* vt = reinterpret_cast<const T*>(a.t.vt);
-  const S* src = reinterpret_cast<const S*>(a.src);
-  S* dst = reinterpret_cast<S*>(a.dst);
+  DstT* dst = reinterpret_cast<DstT*>(a.dst);
   const int ns = a.s.nv, nt = a.t.nv;
-  const long sld = a.src_ld, dld = a.dst_ld;
+  const long dld = a.dst_ld;
+  MP<T> mp;
+  if (KIND == SRC_BARP) mp.load(reinterpret_cast<const T*>(a.prm), a.prm_ld, it.prm_slot);
   bool neg = false, proj_neg = false;
   for (int i = 0; i < nt && !proj_neg; ++i) {
-    if ((double)ldf<S, T>(dst + (long)i * dld + it.dst_slot) < 0.0) neg = true;
+    if ((double)ldf<DstT, T>(dst + (long)i * dld + it.dst_slot) < 0.0) neg = true;
     double gp, hp;
-    expmap_project<S, T>(a, it.src_slot, i, gp, hp);
+    map_project<SrcT, T, KIND>(a, mp, it.src_slot, i, gp, hp);
     if (gp < 0.0) proj_neg = true;
   }
   if (!neg || proj_neg) return EXPMAP_KEPT;
   // targets: the source moments (rho, rho u, rho v, rho E)
   double tar[4] = {0, 0, 0, 0};
   for (int j = 0; j < ns; ++j) {
-    const double g = (double)ldf<S, T>(src + (long)j * sld + it.src_slot);
-    const double h = (double)ldf<S, T>(src + ((long)ns + j) * sld + it.src_slot);
+    double g, h;
+    map_src<SrcT, T, KIND>(a, mp, it.src_slot, j, g, h);
     const double x = (double)vs[j], y = (double)vs[ns + j];
     const double w = (double)vs[2 * ns + j] * (double)vs[3 * ns + j];
     tar[0] += w * g;
@@ -116,7 +127,7 @@ __device__ inline int expmap_item(const MapArgs& a, int item) {
     return true;
   };
   double c[4] = {0, 0, 0, 0}, F[4], J[4][4];
-  expmap_residual<S, T>(a, it.src_slot, c, tar, F, J);
+  expmap_residual<SrcT, T, KIND>(a, mp, it.src_slot, c, tar, F, J);
   bool ok = done(F);
   for (int iter = 0; iter < 60 && !ok; ++iter) {
     double M[4][4], d[4];
@@ -130,35 +141,35 @@ __device__ inline int expmap_item(const MapArgs& a, int item) {
     const double n0 = norm(F);
     for (;;) {
       for (int r = 0; r < 4; ++r) c1[r] = c[r] + t * d[r];
-      expmap_residual<S, T>(a, it.src_slot, c1, tar, F1, nullptr);
+      expmap_residual<SrcT, T, KIND>(a, mp, it.src_slot, c1, tar, F1, nullptr);
       if (norm(F1) < n0 || t < 1e-8) break;
       t *= 0.5;
     }
     for (int r = 0; r < 4; ++r) c[r] = c1[r];
-    expmap_residual<S, T>(a, it.src_slot, c, tar, F, J);
+    expmap_residual<SrcT, T, KIND>(a, mp, it.src_slot, c, tar, F, J);
     ok = done(F);
   }
   if (!ok) return EXPMAP_FAILED;
   for (int i = 0; i < nt; ++i) {
     double gp, hp;
-    expmap_project<S, T>(a, it.src_slot, i, gp, hp);
+    map_project<SrcT, T, KIND>(a, mp, it.src_slot, i, gp, hp);
     const double x = (double)vt[i], y = (double)vt[nt + i];
     const double e = exp(c[0] + c[1] * x + c[2] * y + c[3] * 0.5 * (x * x + y * y));
-    stf<S, T>(dst + (long)i * dld + it.dst_slot, T(gp * e));
-    stf<S, T>(dst + ((long)nt + i) * dld + it.dst_slot, T(hp * e));
+    stf<DstT, T>(dst + (long)i * dld + it.dst_slot, T(gp * e));
+    stf<DstT, T>(dst + ((long)nt + i) * dld + it.dst_slot, T(hp * e));
   }
   return EXPMAP_REPLACED;
 }
 
-// The fallback over the items of one level-switch route; counts[0] += replaced items,
-// counts[1] += items whose iteration did not converge.
-template <class S, class T>
+// The fallback over the items of one route; counts (may be null): counts[0] += replaced
+// items, counts[1] += items whose iteration did not converge.
+template <class SrcT, class DstT, class T, int KIND>
 __global__ void k_expmap(const MapArgs a, int* counts) {
   const int it = blockIdx.x * blockDim.x + threadIdx.x;
   if (it >= a.nitems) return;
-  const int r = expmap_item<S, T>(a, it);
-  if (r == EXPMAP_REPLACED) atomicAdd(counts, 1);
-  if (r == EXPMAP_FAILED) atomicAdd(counts + 1, 1);
+  const int r = expmap_item<SrcT, DstT, T, KIND>(a, it);
+  if (counts && r == EXPMAP_REPLACED) atomicAdd(counts, 1);
+  if (counts && r == EXPMAP_FAILED) atomicAdd(counts + 1, 1);
 }
 
 }  // namespace mlvs

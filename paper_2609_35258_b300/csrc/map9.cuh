@@ -48,38 +48,6 @@ __device__ __forceinline__ void map9_add(double R[9], double w, double x, double
   R[7] += 0.5 * w * x * e; R[8] += 0.5 * w * y * e;
 }
 
-// Source value j of an item in FP64: the stored value, or for SRC_BARP phi-bar-plus formed from
-// phi~ and the cell's parameters m (as k_map forms it).
-template <class SrcT, class T, int KIND>
-__device__ __forceinline__ void map9_src(const MapArgs& a, const MP<T>& m, int slot, int j, double& g, double& h) {
-  T gt, ht;
-  src_value<SrcT, T, 2, KIND>(a, slot, m, j, gt, ht);
-  g = (double)gt;
-  h = (double)ht;
-}
-
-// Projection of the item's source values onto target point i (coarsening averages g and
-// H = h + |xi|^2 g with the CSR weights, refinement inherits them; h = H - |xi_t|^2 g).
-template <class SrcT, class T, int KIND>
-__device__ inline void map9_project(const MapArgs& a, const MP<T>& m, int slot, int i, double& g, double& h) {
-  const T* vs = reinterpret_cast<const T*>(a.s.vt);
-  const T* vt = reinterpret_cast<const T*>(a.t.vt);
-  const T* wgt = reinterpret_cast<const T*>(a.wgt);
-  const int ns = a.s.nv, nt = a.t.nv;
-  double G = 0.0, H = 0.0;
-  for (int q = a.off[i]; q < a.off[i + 1]; ++q) {
-    const int j = a.idx[q];
-    double gj, hj;
-    map9_src<SrcT, T, KIND>(a, m, slot, j, gj, hj);
-    const double xj = (double)vs[j], yj = (double)vs[ns + j];
-    G += (double)wgt[q] * gj;
-    H += (double)wgt[q] * (hj + (xj * xj + yj * yj) * gj);
-  }
-  const double xi = (double)vt[i], yi = (double)vt[nt + i];
-  g = G;
-  h = H - (xi * xi + yi * yi) * G;
-}
-
 // Maps one item (a column of source kind KIND from space s to space t) with the nine-moment
 // correction into dst; returns false if a block is singular (dst then holds the projection).
 template <class SrcT, class DstT, class T, int KIND>
@@ -96,13 +64,13 @@ __device__ inline bool map9_item(const MapArgs& a, int item) {
   for (int j = 0; j < ns; ++j) {
     const double w = (double)vs[2 * ns + j] * (double)vs[3 * ns + j];
     double g, h;
-    map9_src<SrcT, T, KIND>(a, m, it.src_slot, j, g, h);
+    map_src<SrcT, T, KIND>(a, m, it.src_slot, j, g, h);
     map9_add(tar, w, (double)vs[j], (double)vs[ns + j], g, h);
   }
   double Ag[6][6] = {{0}}, Ah[6][6] = {{0}};
   for (int i = 0; i < nt; ++i) {
     double gp, hp;
-    map9_project<SrcT, T, KIND>(a, m, it.src_slot, i, gp, hp);
+    map_project<SrcT, T, KIND>(a, m, it.src_slot, i, gp, hp);
     const double x = (double)vt[i], y = (double)vt[nt + i];
     const double w = (double)vt[2 * nt + i] * (double)vt[3 * nt + i];
     map9_add(cur, w, x, y, gp, hp);
@@ -133,7 +101,7 @@ __device__ inline bool map9_item(const MapArgs& a, int item) {
   }
   for (int i = 0; i < nt; ++i) {
     double gp, hp;
-    map9_project<SrcT, T, KIND>(a, m, it.src_slot, i, gp, hp);
+    map_project<SrcT, T, KIND>(a, m, it.src_slot, i, gp, hp);
     if (ok) {
       const double x = (double)vt[i], y = (double)vt[nt + i];
       gp += ag[0] + ag[1] * x + ag[2] * y + ag[3] * x * x + ag[4] * y * y + ag[5] * x * y;

@@ -718,8 +718,9 @@ template <class S, class T, int D> struct Runner {
 
   static cudaError_t run_ghosts(mlvs_handle* h, Inst& I) {
     const bool nine = D == 2 && h->cfg.map_moments == 9;
+    const bool positive = D == 2 && h->cfg.positive_mapping && !nine;
     // one launch for every route when all source levels are on the same buffer parity
-    if (I.gb.ok && !nine) {
+    if (I.gb.ok && !nine && !positive) {
       int par = -1;
       bool same = true;
       for (auto& r : I.ghosts) {
@@ -763,6 +764,12 @@ template <class S, class T, int D> struct Runner {
       if (nine) k_map9<S, T, T, SRC_BARP><<<(m.nitems + 127) / 128, 128, 0, h->stream>>>(m, I.err.as<int>());
       else launch_map<S, T, SRC_BARP>(h, m);
       mark_end(h);
+      if (positive) {
+        // ghost states whose additive mapping went negative: the exponential correction
+        mark_begin(h, 4);
+        k_expmap<S, T, T, SRC_BARP><<<(m.nitems + 127) / 128, 128, 0, h->stream>>>(m, nullptr);
+        mark_end(h);
+      }
     }
     return cudaGetLastError();
   }
@@ -949,7 +956,7 @@ template <class S, class T, int D> struct Runner {
           if ((e = cnt.alloc(2 * sizeof(int))) != cudaSuccess) return e;
           if ((e = cudaMemsetAsync(cnt.p, 0, 2 * sizeof(int), h->stream)) != cudaSuccess) return e;
           ++h->launches;
-          k_expmap<S, T><<<(ni + 127) / 128, 128, 0, h->stream>>>(m, cnt.as<int>());
+          k_expmap<S, S, T, SRC_TILDE><<<(ni + 127) / 128, 128, 0, h->stream>>>(m, cnt.as<int>());
           int hc[2] = {0, 0};
           if ((e = cudaMemcpyAsync(hc, cnt.p, sizeof(hc), cudaMemcpyDeviceToHost, h->stream)) != cudaSuccess)
             return e;

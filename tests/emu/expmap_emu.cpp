@@ -55,5 +55,5 @@ extern "C" int emu_expmap(int ns, const double* svt, int nt, const double* tvt, 
   const MapItem it = {0, 0, 0};
   a.items = &it;
   a.nitems = 1;
-  return expmap_item<double, double>(a, 0);
+  return expmap_item<double, double, double, SRC_TILDE>(a, 0);
 }

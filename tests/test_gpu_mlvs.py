@@ -175,3 +175,26 @@ def test_two_uniform_levels_periodic_nine_moments(storage, tol):
         omlvs.step(st)
     s.step(3)
     _compare_cells(s, st, 128, tol * 10)
+
+
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 2e-5)])
+def test_two_uniform_levels_periodic_positive_mapping(storage, tol):
+    """positive_mapping = 1: level switches and cross-level ghost states whose additive mapping
+    goes negative take the exponential correction (Sec. 3.3.2), as the oracle's multi-level
+    step does with Options(positive_mapping=True)."""
+    desc = workloads.periodic_random(16, 8, n_base=17, umax=5.0, storage=storage)
+    lev = np.array([0 if (c % 16) < 8 else 1 for c in range(128)], dtype=np.int32)
+    o = oracle_setup(desc)
+    o["opt"] = dataclasses.replace(o["opt"], positive_mapping=True)
+    book = omlvs.SpaceBook(o["base"])
+    keys = [book.uniform(0), book.uniform(1)]
+    st = _oracle_state(desc, o, [keys[0]] * 128, book)
+    for c in range(128):
+        omlvs.remap(st, c, keys[lev[c]])
+    s = Solver(desc, levels=(0, 1), positive_mapping=1)
+    M.mlvs_set_cell_levels(s.h, 0, lev)
+    _compare_cells(s, st, 128, tol)
+    for _ in range(3):
+        omlvs.step(st)
+    s.step(3)
+    _compare_cells(s, st, 128, tol * 10)
