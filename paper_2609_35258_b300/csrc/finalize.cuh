@@ -105,6 +105,34 @@ __device__ inline bool solve_small(double A[4][4], double b[4], const int* idx, 
   return true;
 }
 
+// Gaussian elimination with partial pivoting on the leading n x n block of M (row stride N),
+// in place; b receives the solution.  Returns false on a zero pivot.
+template <int N>
+__device__ inline bool solve_pivoted(double (*M)[N], double* b, int n) {
+  for (int c = 0; c < n; ++c) {
+    int p = c;
+    double best = fabs(M[c][c]);
+    for (int q = c + 1; q < n; ++q)
+      if (fabs(M[q][c]) > best) { best = fabs(M[q][c]); p = q; }
+    if (!(best > 1e-300)) return false;
+    if (p != c) {
+      for (int j = 0; j < n; ++j) { const double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
+      const double t = b[c]; b[c] = b[p]; b[p] = t;
+    }
+    for (int q = c + 1; q < n; ++q) {
+      const double f = M[q][c] / M[c][c];
+      for (int j = c; j < n; ++j) M[q][j] -= f * M[c][j];
+      b[q] -= f * b[c];
+    }
+  }
+  for (int c = n - 1; c >= 0; --c) {
+    double s = b[c];
+    for (int j = c + 1; j < n; ++j) s -= M[c][j] * b[j];
+    b[c] = s / M[c][c];
+  }
+  return true;
+}
+
 // One-axis sums S[a] = sum_i W_i gauss(X_i - u) (X_i - u)^a, a = 0..7.
 template <class T>
 __device__ inline void axis_sums(const T* ax, int nax, T u, T inv2RT, T lnh, double S[8]) {

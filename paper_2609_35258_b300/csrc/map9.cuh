@@ -14,32 +14,6 @@
 
 namespace mlvs {
 
-// Gaussian elimination with partial pivoting on an n x n system (n <= 6), in place.
-__device__ inline bool map9_solve(double (*M)[6], double* b, int n) {
-  for (int c = 0; c < n; ++c) {
-    int p = c;
-    double best = fabs(M[c][c]);
-    for (int q = c + 1; q < n; ++q)
-      if (fabs(M[q][c]) > best) { best = fabs(M[q][c]); p = q; }
-    if (!(best > 1e-300)) return false;
-    if (p != c) {
-      for (int j = 0; j < n; ++j) { const double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
-      const double t = b[c]; b[c] = b[p]; b[p] = t;
-    }
-    for (int q = c + 1; q < n; ++q) {
-      const double f = M[q][c] / M[c][c];
-      for (int j = c; j < n; ++j) M[q][j] -= f * M[c][j];
-      b[q] -= f * b[c];
-    }
-  }
-  for (int c = n - 1; c >= 0; --c) {
-    double s = b[c];
-    for (int j = c + 1; j < n; ++j) s -= M[c][j] * b[j];
-    b[c] = s / M[c][c];
-  }
-  return true;
-}
-
 // nine raw moments of (g, h) at one point, weighted, added to R
 __device__ __forceinline__ void map9_add(double R[9], double w, double x, double y, double g, double h) {
   const double e = h + (x * x + y * y) * g;
@@ -84,7 +58,7 @@ __device__ inline bool map9_item(const MapArgs& a, int item) {
   const int gk[6] = {0, 1, 2, 4, 5, 6};
   double ag[6];
   for (int r = 0; r < 6; ++r) ag[r] = tar[gk[r]] - cur[gk[r]];
-  bool ok = map9_solve(Ag, ag, 6);
+  bool ok = solve_pivoted<6>(Ag, ag, 6);
   // h-block: defects of (rho E, J_x, J_y) less what dg contributes to them
   double bh[6] = {tar[3] - cur[3], tar[7] - cur[7], tar[8] - cur[8], 0, 0, 0};
   if (ok) {
@@ -97,7 +71,7 @@ __device__ inline bool map9_item(const MapArgs& a, int item) {
       bh[1] -= 0.5 * w * x * x2 * dg;
       bh[2] -= 0.5 * w * y * x2 * dg;
     }
-    ok = map9_solve(Ah, bh, 3);
+    ok = solve_pivoted<6>(Ah, bh, 3);
   }
   for (int i = 0; i < nt; ++i) {
     double gp, hp;

@@ -209,32 +209,6 @@ __device__ inline void u_row8(int k, UPoly& pg, UPoly& ph) {
   }
 }
 
-// Gaussian elimination with partial pivoting, n = 8, in place (b receives the solution).
-__device__ inline bool u_solve8(double M[8][8], double b[8]) {
-  for (int c = 0; c < 8; ++c) {
-    int p = c;
-    double best = fabs(M[c][c]);
-    for (int q = c + 1; q < 8; ++q)
-      if (fabs(M[q][c]) > best) { best = fabs(M[q][c]); p = q; }
-    if (!(best > 1e-300)) return false;
-    if (p != c) {
-      for (int j = 0; j < 8; ++j) { const double t = M[c][j]; M[c][j] = M[p][j]; M[p][j] = t; }
-      const double t = b[c]; b[c] = b[p]; b[p] = t;
-    }
-    for (int q = c + 1; q < 8; ++q) {
-      const double f = M[q][c] / M[c][c];
-      for (int j = c; j < 8; ++j) M[q][j] -= f * M[c][j];
-      b[q] -= f * b[c];
-    }
-  }
-  for (int c = 7; c >= 0; --c) {
-    double s = b[c];
-    for (int j = c + 1; j < 8; ++j) s -= M[c][j] * b[j];
-    b[c] = s / M[c][c];
-  }
-  return true;
-}
-
 // b0..b7 of the eight-moment correction of mp (uncorrected Shakhov parameters of the state
 // rho, u, T with heat-flux target q_tar); b0..b3 go to mp, b4..b7 to b8.
 template <class T>
@@ -261,7 +235,7 @@ __device__ inline bool u_correct8(const PointArgs& A, double rho, double ux, dou
   const double tar[8] = {rho, rho * dux, rho * duy,
                          0.5 * (3.0 + A.gas.K) * rho * RT + 0.5 * rho * (dux * dux + duy * duy), qtx, qty, 0.0, 0.0};
   for (int k = 0; k < 8; ++k) r[k] = tar[k] - M[k][0];
-  if (!u_solve8(M, r)) return false;
+  if (!solve_pivoted<8>(M, r, 8)) return false;
   mp.b0 = T(r[0]); mp.b1 = T(r[1]); mp.b2 = T(r[2]); mp.b3 = T(r[3]);
   for (int m = 0; m < 4; ++m) b8[m] = T(r[4 + m]);
   return true;
