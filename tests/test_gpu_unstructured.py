@@ -87,11 +87,15 @@ def test_full_size_two_cavities_conserve_mass_and_mirror_symmetry():
     assert abs(m2 - m1) < 1e-5 * m1
     right = geo["cx"] > 0.0                                     # gas crosses x = 0 into the thin side
     assert np.sum((geo["area"] * W2[0])[right]) > 1.2 * np.sum((geo["area"] * W1[0])[right])
-    # mirror pairs (x, y) <-> (x, -y): density equal, v opposite
+    # mirror pairs (x, y) <-> (x, -y): density equal, v opposite.  The bounds are of the largest
+    # value: FP32 rounding is relative to the dense side, and the generated mesh's centroids are
+    # mirrored only to about 2e-13 (shoelace cancellation), which 21 steps of the expansion
+    # amplify to 1e-8 even in FP64, in the oracle as in these passes.  The passes compiled for
+    # the CPU give 4.7e-7 and 4.1e-5 on this mesh with 13^2 velocities.
     key = {(round(x, 9), round(y, 9)): i for i, (x, y) in enumerate(zip(geo["cx"], geo["cy"]))}
     mirror = np.array([key[(round(x, 9), round(-y, 9))] for x, y in zip(geo["cx"], geo["cy"])])
-    np.testing.assert_allclose(W2[0][mirror], W2[0], rtol=1e-4)
-    np.testing.assert_allclose(W2[2][mirror], -W2[2], rtol=0, atol=1e-4 * np.max(np.abs(W2[1])))
+    np.testing.assert_allclose(W2[0][mirror], W2[0], rtol=0, atol=2e-5 * np.max(W2[0]))
+    np.testing.assert_allclose(W2[2][mirror], -W2[2], rtol=0, atol=5e-4 * np.max(np.abs(W2[1])))
 
 
 @pytest.mark.parametrize("storage,tol", [(M.F64, 1e-11), (M.F32, 2e-5)], ids=["f64", "f32"])
