@@ -6,7 +6,9 @@
  * (physical cell x discrete velocity) pair, on one or several velocity spaces built on a
  * quadtree-structured Newton--Cotes base grid (Sec. 2.3, 3.1-3.2).  Multi-level parts follow
  * Sec. 3.2 (criterion, grouping), Sec. 3.3 (linear moment-constrained correction) and
- * Sec. 3.4 (inter-level coupling).
+ * Sec. 3.4 (inter-level coupling).  Cartesian and structured curvilinear meshes use
+ * mlvs_handle; unstructured meshes of polygonal cells (one velocity space) use mlvs_uhandle
+ * (mlvs_ucreate ... mlvs_udestroy), whose errors are read with mlvs_last_error(NULL).
  *
  * Conventions
  *  - Every entry point returns an mlvs_status; MLVS_OK is 0 and errors are negative.
