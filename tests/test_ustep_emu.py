@@ -212,3 +212,19 @@ def test_eight_moment_correction_matches_the_oracle(emu, storage, tol):
     np.testing.assert_allclose(h, ho, rtol=0, atol=tol * np.max(np.abs(ho)))
     g4, _, _ = _run_oracle(mesh, W0, 3, nmom=4)
     assert np.max(np.abs(g4 - go)) > 10 * tol * np.max(np.abs(go))
+
+
+@pytest.mark.parametrize("shape", ["square", "triangle"])
+def test_single_cell_closed_box_matches_the_oracle(emu, shape):
+    """The degenerate mesh of one cell: every face a wall, the least-squares matrix from the
+    reflected ghosts alone (all gradients zero), a gas off equilibrium relaxing in the box."""
+    if shape == "square":
+        nodes, cells = np.array([[0.0, 0.0], [1.0, 0.0], [1.0, 1.0], [0.0, 1.0]]), [(0, 1, 2, 3)]
+    else:
+        nodes, cells = np.array([[0.0, 0.0], [1.0, 0.0], [0.3, 0.8]]), [(0, 1, 2)]
+    mesh = un.UMesh(nodes, cells)
+    W0 = np.array([[1.2, 0.3, -0.2, 1.4]])
+    g, h, _ = _run_emu(emu, _cfg(M.F64, [(0.0, 0.0, 1.0)]), nodes, cells, W0, 3)
+    go, ho, _ = _run_oracle(mesh, W0, 3)
+    np.testing.assert_allclose(g, go, rtol=0, atol=1e-12 * np.max(np.abs(go)))
+    np.testing.assert_allclose(h, ho, rtol=0, atol=1e-12 * np.max(np.abs(ho)))
