@@ -254,43 +254,6 @@ constexpr int kTX2 = 16, kTY2 = 16, kTX1 = 128;
 int tile_w(int D) { return D == 2 ? kTX2 : kTX1; }
 int tile_h(int D) { return D == 2 ? kTY2 : 1; }
 
-// Inverse of the T-independent four-moment mapping matrix of a space (raw basis, unit
-// weighting): rows (sum w phi, sum w xi_x phi, sum w xi_y phi, 1/2 sum w xi^2 phi),
-// phi = (1, xi_x, xi_y, xi^2).  In 1-D the y row/column is the identity.
-bool mapping_inverse(const VSpace& vs, int D, double inv[16]) {
-  double A[4][4] = {{0}};
-  for (int v = 0; v < vs.nv(); ++v) {
-    const double w = vs.wx[v] * vs.wy[v], x = vs.xix[v], y = vs.xiy[v], x2 = x * x + y * y;
-    const double phi[4] = {1.0, x, y, x2};
-    const double psi[4] = {1.0, x, y, 0.5 * x2};
-    for (int r = 0; r < 4; ++r)
-      for (int c = 0; c < 4; ++c) A[r][c] += w * psi[r] * phi[c];
-  }
-  if (D == 1) {
-    for (int c = 0; c < 4; ++c) { A[2][c] = 0.0; A[c][2] = 0.0; }
-    A[2][2] = 1.0;
-  }
-  double M[4][8];
-  for (int r = 0; r < 4; ++r)
-    for (int c = 0; c < 8; ++c) M[r][c] = (c < 4) ? A[r][c] : (c - 4 == r ? 1.0 : 0.0);
-  for (int c = 0; c < 4; ++c) {
-    int p = c;
-    for (int r = c + 1; r < 4; ++r)
-      if (std::fabs(M[r][c]) > std::fabs(M[p][c])) p = r;
-    if (!(std::fabs(M[p][c]) > 1e-300)) return false;
-    for (int j = 0; j < 8; ++j) std::swap(M[c][j], M[p][j]);
-    const double d = M[c][c];
-    for (int j = 0; j < 8; ++j) M[c][j] /= d;
-    for (int r = 0; r < 4; ++r)
-      if (r != c) {
-        const double f = M[r][c];
-        for (int j = 0; j < 8; ++j) M[r][j] -= f * M[c][j];
-      }
-  }
-  for (int r = 0; r < 4; ++r)
-    for (int c = 0; c < 4; ++c) inv[4 * r + c] = M[r][4 + c];
-  return true;
-}
 
 }  // namespace
 
