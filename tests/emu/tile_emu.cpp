@@ -1,0 +1,195 @@
+// Runs the library's Cartesian single-level step on the CPU: the tile kernels (MODE 0 face sums,
+// MODE 1 update) on emulated thread blocks (a block's threads as std::threads, a std::barrier
+// for __syncthreads, the dynamic shared memory as one buffer for the running block), with the
+// initialisation, chunk-sum and finalisation kernels around them in the order the handle
+// launches them for a level that holds every cell.  FP64 storage.  Test infrastructure.
+#include <atomic>
+#include <barrier>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <vector>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#ifndef __launch_bounds__
+#define __launch_bounds__(...)
+#endif
+#undef __shared__
+#define __shared__
+
+using std::isfinite;
+using std::max;
+using std::min;
+float __expf(float a) { return std::exp(a); }
+static inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
+static inline float __fmul_rn(float a, float b) { return a * b; }
+static inline float __fadd_rn(float a, float b) { return a + b; }
+static inline float __fsub_rn(float a, float b) { return a - b; }
+static inline float __fdividef(float a, float b) { return a / b; }
+static inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
+static inline double __dmul_rn(double a, double b) { return a * b; }
+static inline double __dadd_rn(double a, double b) { return a + b; }
+static inline double __dsub_rn(double a, double b) { return a - b; }
+template <class X> static inline X __ldg(const X* p) { return *p; }
+static inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
+template <class X> static inline X __shfl_xor_sync(unsigned, X v, int, int = 32) { return v; }
+static inline int atomicOr(int* p, int v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
+static inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
+
+thread_local uint3 threadIdx, blockIdx;
+static dim3 blockDim, gridDim;
+static std::barrier<>* g_bar = nullptr;
+static inline void __syncthreads() { g_bar->arrive_and_wait(); }
+
+namespace mlvs {
+alignas(16) unsigned char smem[256 * 1024];   // the dynamic shared memory of the running block
+}
+
+template <class F> void emu_launch(dim3 grid, unsigned block, F body) {
+  gridDim = grid;
+  blockDim = dim3(block, 1, 1);
+  for (unsigned by = 0; by < grid.y; ++by)
+    for (unsigned bx = 0; bx < grid.x; ++bx) {
+      std::barrier<> bar(block);
+      g_bar = &bar;
+      std::vector<std::thread> th;
+      for (unsigned t = 0; t < block; ++t)
+        th.emplace_back([&body, t, bx, by] {
+          threadIdx = {t, 0, 0};
+          blockIdx = {bx, by, 0};
+          body();
+        });
+      for (auto& x : th) x.join();
+    }
+}
+
+#include "../../paper_2609_35258_b300/csrc/dugks_tile.cuh"
+#include "../../paper_2609_35258_b300/csrc/finalize.cuh"
+#include "../../paper_2609_35258_b300/csrc/mapping.cuh"
+#include "../../paper_2609_35258_b300/csrc/vspace_host.hpp"
+
+using namespace mlvs;
+using T = double;
+using S = double;
+constexpr int D = 2, TX = 16, TY = 16, VB = 2, FIN_BLOCK = 64;
+
+extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc, const double* wall,
+                            const double* gas6, int n_base, double umin, double umax, int rule, double dt,
+                            int compat_cell, int compat_face, int limiter, const double* far, const double* W0,
+                            int steps, int vpc,
+                            double* fout /* [2][nv][ncell] */, int* nv_out) {
+  const Base1D b = make_base_1d(n_base, umin, umax, rule);
+  const int N1 = (int)groups_1d(n_base, 1).size();
+  std::vector<int> keff(N1 * N1, 0), owner;
+  const VSpace vs = kappa_vspace(b, D, keff, owner);
+  const int nv = vs.nv();
+  *nv_out = nv;
+  std::vector<double> vt(4 * (size_t)nv), ax;
+  for (int v = 0; v < nv; ++v) {
+    vt[v] = vs.xix[v]; vt[nv + v] = vs.xiy[v]; vt[2 * nv + v] = vs.wx[v]; vt[3 * nv + v] = vs.wy[v];
+  }
+  {
+    auto gr = groups_1d(n_base, 0);
+    ax.resize(2 * gr.size());
+    for (size_t g = 0; g < gr.size(); ++g) merged(b, gr[g].first, gr[g].second, ax[g], ax[gr.size() + g]);
+  }
+  const int ncell = nx * ny;
+  const int px = bc[0] == 0, py = bc[2] == 0;
+  const int nfx = px ? nx : nx + 1, nfy = py ? ny : ny + 1, nface = nfx * ny + nx * nfy;
+  StepConst k;
+  std::memset(&k, 0, sizeof(k));
+  k.nx = nx; k.ny = ny; k.px = px; k.py = py;
+  for (int s = 0; s < 4; ++s) k.bc[s] = bc[s];
+  k.nfx = nfx; k.nfy = nfy; k.ncell = ncell; k.nface = nface;
+  k.nv = nv; k.nax = (int)ax.size() / 2;
+  k.dx = Lx / nx; k.dy = Ly / ny; k.dt = dt;
+  k.c0 = gas6[1] + 3.0 - D; k.twoK = 2.0 * gas6[1];
+  k.vpc = vpc; k.nchunk = (nv + vpc - 1) / vpc;
+  GasDev gas{gas6[0], gas6[1], gas6[2], gas6[3], gas6[4], gas6[5]};
+  const int ntx = (nx + TX - 1) / TX, nty = (ny + TY - 1) / TY, ntiles = ntx * nty;
+  std::vector<int> tiles(ntiles), ids(ncell), lvl(ncell, 0), slot(ncell), gho(ncell, -1), fslot(nface, -1);
+  for (int i = 0; i < ntiles; ++i) tiles[i] = i;
+  for (int c = 0; c < ncell; ++c) ids[c] = slot[c] = c;
+  std::vector<unsigned char> frole(nface, FR_NORMAL);
+  std::vector<T> f[2] = {std::vector<T>(2 * (size_t)nv * ncell), std::vector<T>(2 * (size_t)nv * ncell)};
+  std::vector<T> prm[2] = {std::vector<T>((size_t)NP * ncell), std::vector<T>((size_t)NP * ncell)};
+  std::vector<T> fprm((size_t)NP * nface, 0.0), ucell(2 * (size_t)ncell);
+  std::vector<double> cpart((size_t)k.nchunk * NMOM * ncell), fpart((size_t)k.nchunk * NMOM * nface);
+  std::vector<double> msum((size_t)NMOM * std::max(nface, ncell)), W(11 * (size_t)ncell);
+  int err = 0;
+  unsigned stepctr = 0;
+  auto pargs = [&](bool face) {
+    PointArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.k = k; a.gas = gas; a.is_face = face; a.npt = face ? nface : ncell; a.pts = nullptr;
+    a.nwork = a.npt; a.part = face ? fpart.data() : cpart.data(); a.vt = vt.data(); a.ax = ax.data();
+    a.ids = ids.data(); a.frole = frole.data(); a.ucell = ucell.data();
+    a.compat = face ? compat_face : compat_cell;
+    for (int s = 0; s < 4; ++s)
+      for (int j = 0; j < 3; ++j) a.wall[s][j] = wall[3 * s + j];
+    for (int j = 0; j < 4; ++j) a.far[j] = far[j];
+    a.err = &err;
+    return a;
+  };
+  auto fin_grid = [](int n) { return dim3(std::max(1, (n + FIN_BLOCK - 1) / FIN_BLOCK), 1, 1); };
+  auto finalize = [&](PointArgs a) {
+    const long nt = (long)NMOM * a.nwork;
+    emu_launch(dim3((unsigned)((nt + 255) / 256), 1, 1), 256,
+               [&] { k_sum_chunks(a.part, a.k.nchunk, a.npt, a.pts, a.nwork, msum.data()); });
+    a.msum = msum.data();
+    emu_launch(fin_grid(a.nwork), FIN_BLOCK, [&] { k_finalize<T, D>(a); });
+  };
+  // initial state (as the handle's init: parameters, phi~, velocities, chunk moments)
+  int cur = 0, pcur = 0;
+  {
+    PointArgs a = pargs(false);
+    a.prm_out = prm[0].data();
+    emu_launch(fin_grid(ncell), FIN_BLOCK, [&] { k_init_params<T, D>(a, W0); });
+    emu_launch(dim3((ncell + 127) / 128, std::min(nv, 1024), 1), 128,
+               [&] { k_init_f<S, T, D>(k, ncell, prm[0].data(), vt.data(), f[0].data()); });
+    emu_launch(dim3((ncell + 127) / 128, 1, 1), 128,
+               [&] { k_scatter_velocity<T>(prm[0].data(), ncell, ids.data(), ucell.data(), ncell); });
+    emu_launch(dim3((ncell + 127) / 128, 1, 1), 128,
+               [&] { k_set_shift<T>(prm[0].data(), ncell, ids.data(), ucell.data(), ncell); });
+    emu_launch(dim3((ncell + 127) / 128, k.nchunk, 1), 128,
+               [&] { k_moments<S, T, D>(k, ncell, prm[0].data(), vt.data(), f[0].data(), cpart.data()); });
+  }
+  using L0 = TileSmem<T, TX, TY, D, VB, 0>;
+  using L1 = TileSmem<T, TX, TY, D, VB, 1>;
+  if (L0::BYTES > sizeof(smem) || L1::BYTES > sizeof(smem)) return 2;
+  for (int s = 0; s < steps; ++s) {
+    {
+      PointArgs a = pargs(false);
+      a.cprm = prm[pcur].data();
+      a.prm_out = prm[pcur ^ 1].data();
+      a.W = W.data();
+      finalize(a);
+      emu_launch(dim3((ncell + 127) / 128, 1, 1), 128,
+                 [&] { k_scatter_velocity<T>(prm[pcur ^ 1].data(), ncell, ids.data(), ucell.data(), ncell); });
+      pcur ^= 1;
+    }
+    TileArgs t;
+    std::memset(&t, 0, sizeof(t));
+    t.k = k; t.f_in = f[cur].data(); t.f_out = f[cur ^ 1].data(); t.nslot = ncell;
+    t.cparam = prm[pcur].data(); t.fparam = fprm.data(); t.vt = vt.data(); t.tiles = tiles.data();
+    t.ntx = ntx; t.nty = nty; t.level = 0; t.lvl_of = lvl.data(); t.slot_of = slot.data();
+    t.ghost_of = nullptr; t.ghost = nullptr; t.nghost = 0; t.frole = frole.data(); t.fslot = fslot.data();
+    t.ucell = ucell.data(); t.step = &stepctr;
+    t.part = fpart.data();
+    emu_launch(dim3(ntiles, k.nchunk, 1), TX * TY,
+               [&] { k_tile<S, T, D, TX, TY, VB, 0, false, false>(t, limiter); });
+    {
+      PointArgs a = pargs(true);
+      a.cprm = prm[pcur].data();
+      a.prm_out = fprm.data();
+      finalize(a);
+    }
+    t.part = cpart.data();
+    emu_launch(dim3(ntiles, k.nchunk, 1), TX * TY,
+               [&] { k_tile<S, T, D, TX, TY, VB, 1, false, false>(t, limiter); });
+    cur ^= 1;
+  }
+  std::memcpy(fout, f[cur].data(), f[cur].size() * sizeof(T));
+  return err;
+}
