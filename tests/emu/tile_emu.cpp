@@ -2,7 +2,8 @@
 // MODE 1 update) on emulated thread blocks (a block's threads as std::threads, a std::barrier
 // for __syncthreads, the dynamic shared memory as one buffer for the running block), with the
 // initialisation, chunk-sum and finalisation kernels around them in the order the handle
-// launches them for a level that holds every cell.  FP64 storage.  Test infrastructure.
+// launches them for a level that holds every cell.  FP64 storage, or FP32 when compiled with
+// EMU_FP32.  Test infrastructure.
 #include <atomic>
 #include <barrier>
 #include <cmath>
@@ -70,8 +71,13 @@ template <class F> void emu_launch(dim3 grid, unsigned block, F body) {
 #include "../../paper_2609_35258_b300/csrc/vspace_host.hpp"
 
 using namespace mlvs;
+#ifdef EMU_FP32
+using T = float;
+using S = float;
+#else
 using T = double;
 using S = double;
+#endif
 constexpr int D = 2, TX = 16, TY = 16, VB = 2, FIN_BLOCK = 64;
 
 extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc, const double* wall,
@@ -85,14 +91,19 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
   const VSpace vs = kappa_vspace(b, D, keff, owner);
   const int nv = vs.nv();
   *nv_out = nv;
-  std::vector<double> vt(4 * (size_t)nv), ax;
+  std::vector<T> vt(4 * (size_t)nv), ax;
   for (int v = 0; v < nv; ++v) {
     vt[v] = vs.xix[v]; vt[nv + v] = vs.xiy[v]; vt[2 * nv + v] = vs.wx[v]; vt[3 * nv + v] = vs.wy[v];
   }
   {
     auto gr = groups_1d(n_base, 0);
     ax.resize(2 * gr.size());
-    for (size_t g = 0; g < gr.size(); ++g) merged(b, gr[g].first, gr[g].second, ax[g], ax[gr.size() + g]);
+    for (size_t g = 0; g < gr.size(); ++g) {
+      double X, Wg;
+      merged(b, gr[g].first, gr[g].second, X, Wg);
+      ax[g] = T(X);
+      ax[gr.size() + g] = T(Wg);
+    }
   }
   const int ncell = nx * ny;
   const int px = bc[0] == 0, py = bc[2] == 0;
@@ -190,6 +201,6 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
                [&] { k_tile<S, T, D, TX, TY, VB, 1, false, false>(t, limiter); });
     cur ^= 1;
   }
-  std::memcpy(fout, f[cur].data(), f[cur].size() * sizeof(T));
+  for (size_t i = 0; i < f[cur].size(); ++i) fout[i] = (double)f[cur][i];
   return err;
 }

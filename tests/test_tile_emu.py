@@ -3,7 +3,7 @@ Cartesian step (Sec. 2.2).  The tile kernels (MODE 0 face sums and MODE 1 update
 staging of a 16 x 16 tile with its two-cell halo, slopes, upwind faces and barrier rounds of two
 velocities) run on emulated thread blocks (tests/emu/tile_emu.cpp), with the initialisation,
 chunk-sum and finalisation kernels the handle launches around them.  FP64, 1e-13 of the largest
-value after two steps, on meshes that leave partial tiles: doubly periodic, a lid-driven cavity
+value after two steps (FP32 on the cavity, 1e-5), on meshes that leave partial tiles: doubly periodic, a lid-driven cavity
 (walls, one moving), and a supersonic channel (freestream inflow and outflow, walls)."""
 import ctypes as C
 import os
@@ -23,10 +23,9 @@ RULE = {"boole": 0, "simpson": 1, "trapz": 2}
 LIM = {"vanleer": 0, "none": 1}
 
 
-@pytest.fixture(scope="module")
-def lib():
+def _build(fp32):
     out = os.path.join(tempfile.mkdtemp(prefix="tile_emu_"), "emu.so")
-    subprocess.run(["g++", "-std=c++20", "-O1", "-fPIC", "-shared", "-I", CUDA_INC,
+    subprocess.run(["g++", "-std=c++20", "-O1", "-fPIC", "-shared", "-I", CUDA_INC, *(["-DEMU_FP32"] if fp32 else []),
                     os.path.join(HERE, "emu", "tile_emu.cpp"), "-o", out, "-lpthread"],
                    check=True, capture_output=True)
     L = C.CDLL(out)
@@ -35,6 +34,16 @@ def lib():
                                C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, P, P, C.c_int,
                                C.c_int, P, C.POINTER(C.c_int)]
     return L
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return _build(False)
+
+
+@pytest.fixture(scope="module")
+def lib32():
+    return _build(True)
 
 
 def _run(lib, desc, steps, vpc):
@@ -69,3 +78,11 @@ def test_tile_kernels_match_the_oracle(lib, case):
     g, h, g_o, h_o = _run(lib, desc, 2, vpc=40)                  # 169 velocities: a ragged last chunk
     np.testing.assert_allclose(g, g_o, rtol=0, atol=1e-13 * np.max(np.abs(g_o)))
     np.testing.assert_allclose(h, h_o, rtol=0, atol=1e-13 * np.max(np.abs(h_o)))
+
+
+def test_tile_kernels_fp32_match_the_oracle(lib32):
+    """FP32 storage and arithmetic (the benchmark's): within 1e-5 of the largest value."""
+    desc = workloads.cavity(18, n_base=13, umax=5.0, storage="f32")
+    g, h, g_o, h_o = _run(lib32, desc, 2, vpc=40)
+    np.testing.assert_allclose(g, g_o, rtol=0, atol=1e-5 * np.max(np.abs(g_o)))
+    np.testing.assert_allclose(h, h_o, rtol=0, atol=1e-5 * np.max(np.abs(h_o)))
