@@ -401,6 +401,9 @@ mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt);
  * ncell above 16384 is rejected with MLVS_ERR_ARG.  The library calls no cudaMalloc, cudaFree or
  * other allocating routine here.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any stream capture.
+ * The address found is kept per device ordinal for the life of the process and belongs to the
+ * device's primary context: a host program that destroys that context (cudaDeviceReset) must not
+ * call this entry point again on that device.
  * All calls share the one array and leave their partial sums in it; every call overwrites all the
  * entries it later reads, so nothing needs clearing, but calls that overlap on the GPU (on
  * different streams, or different threads) race on the array and must be serialised by the caller.

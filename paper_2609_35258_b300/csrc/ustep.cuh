@@ -373,7 +373,9 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
     out0.zero();
     for (int v = v0; v < v1; ++v) {
       const T xx = u_xi(a, v, 0), yy = u_xi(a, v, 1);
-      const T xn = nx * xx + ny * yy;
+      // two rounded products and a rounded sum (no contraction): a velocity tangential to
+      // the face gives an exact zero, as in the oracle, and takes the mean of both sides
+      const T xn = N::add(N::mul(nx, xx), N::mul(ny, yy));
       T bar[2];
       for (int comp = 0; comp < 2; ++comp) {
         const T vL = u_recon<T>(a, comp, v, L, oxL, oyL, xx * s, yy * s);
@@ -452,7 +454,7 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
     MP<T> m;
     m.load(a.fprm, nf, fi);
     const T xx = u_xi(a, v, 0), yy = u_xi(a, v, 1);
-    const T xn = a.fgeo[UF_NX * nf + fi] * xx + a.fgeo[UF_NY * nf + fi] * yy;
+    const T xn = N::add(N::mul(a.fgeo[UF_NX * nf + fi], xx), N::mul(a.fgeo[UF_NY * nf + fi], yy));
     const T scale = xn * a.fgeo[UF_LEN * nf + fi];
     T gS, hS;
     if (a.fwall[fi] >= 0) model_eval<T, 2>(m, xx, yy, T(a.pa.k.c0), T(a.pa.k.twoK), gS, hS);
@@ -531,7 +533,7 @@ __device__ inline void u_elem(const UArgs<T>& a, long i) {
     double den = 0.0;
     for (int v = 0; v < a.nv; ++v) {
       const T xx = u_xi(a, v, 0), yy = u_xi(a, v, 1);
-      const T xin = -(nx * xx + ny * yy);
+      const T xin = -N::add(N::mul(nx, xx), N::mul(ny, yy));
       if (!(xin > T(0))) continue;
       T g, h;
       model_eval<T, 2>(m, xx, yy, T(a.pa.k.c0), T(a.pa.k.twoK), g, h);

@@ -4,65 +4,11 @@
 // initialisation, chunk-sum and finalisation kernels around them in the order the handle
 // launches them for a level that holds every cell.  FP64 storage, or FP32 when compiled with
 // EMU_FP32.  Test infrastructure.
-#include <atomic>
-#include <barrier>
-#include <cmath>
-#include <cstring>
-#include <thread>
-#include <vector>
-#include <cuda_runtime.h>
-#include <cuda_bf16.h>
-
-#ifndef __launch_bounds__
-#define __launch_bounds__(...)
-#endif
-#undef __shared__
-#define __shared__
-
-using std::isfinite;
-using std::max;
-using std::min;
-float __expf(float a) { return std::exp(a); }
-static inline float __fmaf_rn(float a, float b, float c) { return std::fma(a, b, c); }
-static inline float __fmul_rn(float a, float b) { return a * b; }
-static inline float __fadd_rn(float a, float b) { return a + b; }
-static inline float __fsub_rn(float a, float b) { return a - b; }
-static inline float __fdividef(float a, float b) { return a / b; }
-static inline double __fma_rn(double a, double b, double c) { return std::fma(a, b, c); }
-static inline double __dmul_rn(double a, double b) { return a * b; }
-static inline double __dadd_rn(double a, double b) { return a + b; }
-static inline double __dsub_rn(double a, double b) { return a - b; }
-template <class X> static inline X __ldg(const X* p) { return *p; }
-static inline unsigned __float_as_uint(float f) { unsigned u; std::memcpy(&u, &f, 4); return u; }
-template <class X> static inline X __shfl_xor_sync(unsigned, X v, int, int = 32) { return v; }
-static inline int atomicOr(int* p, int v) { return __atomic_fetch_or(p, v, __ATOMIC_SEQ_CST); }
-static inline int atomicAdd(int* p, int v) { return __atomic_fetch_add(p, v, __ATOMIC_SEQ_CST); }
-
-thread_local uint3 threadIdx, blockIdx;
-static dim3 blockDim, gridDim;
-static std::barrier<>* g_bar = nullptr;
-static inline void __syncthreads() { g_bar->arrive_and_wait(); }
+#define EMU_SHARED_SPEC
+#include "cta_shim.hpp"
 
 namespace mlvs {
 alignas(16) unsigned char smem[256 * 1024];   // the dynamic shared memory of the running block
-}
-
-template <class F> void emu_launch(dim3 grid, unsigned block, F body) {
-  gridDim = grid;
-  blockDim = dim3(block, 1, 1);
-  for (unsigned by = 0; by < grid.y; ++by)
-    for (unsigned bx = 0; bx < grid.x; ++bx) {
-      std::barrier<> bar(block);
-      g_bar = &bar;
-      std::vector<std::thread> th;
-      for (unsigned t = 0; t < block; ++t)
-        th.emplace_back([&body, t, bx, by] {
-          threadIdx = {t, 0, 0};
-          blockIdx = {bx, by, 0};
-          body();
-        });
-      for (auto& x : th) x.join();
-    }
 }
 
 #include "../../paper_2609_35258_b300/csrc/dugks_tile.cuh"

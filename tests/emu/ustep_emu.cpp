@@ -7,6 +7,15 @@
 #include <string>
 #include <vector>
 
+#ifdef EMU_CONTRACT
+// The device functions only: fuse a * b + c into one rounding wherever the source leaves the
+// compiler free to, as nvcc does for device code (with -mfma).  The host geometry stays
+// uncontracted, as the library's host compiler builds it.
+#pragma GCC push_options
+#pragma GCC optimize("fp-contract=fast")
+#include "../../paper_2609_35258_b300/csrc/ustep.cuh"
+#pragma GCC pop_options
+#endif
 #include "../../paper_2609_35258_b300/csrc/ustep_host.hpp"
 
 using namespace mlvs;

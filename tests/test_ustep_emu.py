@@ -28,9 +28,13 @@ EMU = os.path.join(HERE, "emu")
 CUDA_INC = os.path.join(os.environ.get("CUDA_HOME", "/usr/local/cuda"), "include")
 
 
-def _compile(asan):
+def _compile(asan, contract=False):
+    """contract: let the compiler fuse a * b + c into one rounding, as nvcc does for device
+    code, so that a sign decision that depends on an unfused product shows up on the CPU."""
     out = os.path.join(tempfile.mkdtemp(prefix="ustep_emu_"), "emu.so")
     flags = ["-O1", "-g", "-fsanitize=address", "-fno-omit-frame-pointer"] if asan else ["-O2"]
+    if contract:
+        flags += ["-mfma", "-ffp-contract=off", "-DEMU_CONTRACT"]
     cmd = ["g++", "-std=c++17", *flags, "-fPIC", "-shared", "-I", CUDA_INC,
            os.path.join(EMU, "ustep_emu.cpp"), "-o", out]
     subprocess.run(cmd, check=True, capture_output=True)
@@ -114,10 +118,21 @@ def _two_cavity(tri):
     return nodes, cells, mesh, W0
 
 
+@pytest.fixture(scope="module")
+def emu_fma():
+    return _bind(_compile(asan=False, contract=True))
+
+
 @pytest.mark.parametrize("tri", [False, True], ids=["quads", "triangles"])
-def test_two_cavities_fp64_match_the_oracle(emu, tri):
+@pytest.mark.parametrize("contract", [False, True], ids=["ieee", "fma"])
+def test_two_cavities_fp64_match_the_oracle(emu, emu_fma, tri, contract):
+    """The "fma" build contracts products into fused multiply-adds wherever the source leaves
+    it free to, as the GPU build does.  The triangles' diagonal faces have n = (1, -1)/sqrt(2),
+    so velocities with xi_x = xi_y are tangential to them: xi.n must come out as an exact zero
+    (the mean of both sides), which a fused product would turn into a rounding residue whose
+    sign picks one side."""
     nodes, cells, mesh, W0 = _two_cavity(tri)
-    g, h, dt = _run_emu(emu, _cfg(M.F64, [(0.0, 0.0, 1.0)]), nodes, cells, W0, 3)
+    g, h, dt = _run_emu(emu_fma if contract else emu, _cfg(M.F64, [(0.0, 0.0, 1.0)]), nodes, cells, W0, 3)
     go, ho, dto = _run_oracle(mesh, W0, 3)
     assert dt == pytest.approx(dto, rel=1e-15)
     np.testing.assert_allclose(g, go, rtol=0, atol=1e-12 * np.max(np.abs(go)))

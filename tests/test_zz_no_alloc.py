@@ -64,6 +64,47 @@ def test_noalloc_matches_handle_moments_twice():
     _noalloc_vs_handle(s, nv, axes)
 
 
+def _numpy_moments(g, h, xi_x, xi_y, w_x, w_y):
+    """(rho, rho u, rho v, rho E) of FP32 arrays [nv][ncell], summed in FP64."""
+    w = (w_x.astype(np.float64) * w_y.astype(np.float64))[:, None]
+    x, y = xi_x.astype(np.float64)[:, None], xi_y.astype(np.float64)[:, None]
+    g, h = g.astype(np.float64), h.astype(np.float64)
+    return np.stack([np.sum(w * g, 0), np.sum(w * x * g, 0), np.sum(w * y * g, 0),
+                     np.sum(0.5 * w * ((x * x + y * y) * g + h), 0)])
+
+
+def _call(g, h, axes):
+    nv, ncell = g.shape
+    dev = [torch.tensor(a, device="cuda") for a in (g, h, *axes)]
+    out = torch.full((4, ncell), float("nan"), dtype=torch.float64, device="cuda")
+    M.mlvs_moments_noalloc(*dev[:2], nv, ncell, *dev[2:], out, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def test_noalloc_sizes_against_numpy():
+    """Fewer velocities than chunks (nv = 5: most chunks empty, their rows still written), the
+    largest accepted cell count, and a large call followed by a smaller one that must not pick
+    up the larger call's partial sums."""
+    rng = np.random.default_rng(20261202)
+
+    def case(nv, ncell):
+        g = rng.random((nv, ncell), dtype=np.float32)
+        h = rng.random((nv, ncell), dtype=np.float32)
+        axes = [rng.standard_normal(nv).astype(np.float32) for _ in range(2)] + \
+               [rng.random(nv, dtype=np.float32) for _ in range(2)]
+        got = _call(g, h, axes)
+        ref = _numpy_moments(g, h, *axes)
+        scale = np.max(np.abs(ref), axis=1, keepdims=True)
+        assert np.all(np.isfinite(got))
+        assert np.max(np.abs(got - ref) / scale) < 1e-12
+
+    case(5, 300)
+    case(37, 16384)
+    case(3, 1000)
+    case(40, 200)
+
+
 def test_noalloc_rejects_too_many_cells():
     dummy = torch.zeros(4, dtype=torch.float32, device="cuda")
     out = torch.zeros(4, dtype=torch.float64, device="cuda")
