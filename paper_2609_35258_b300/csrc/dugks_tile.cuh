@@ -1,15 +1,18 @@
 // Tile kernels of one DUGKS step on a structured Cartesian mesh (Sec. 2.2).
 //
-// A CTA owns a TX x TY tile of cells and a contiguous chunk of velocities, processed VB
-// velocities per barrier round.  Per round it stages in shared memory
+// k_faces: a CTA owns a TX x TY tile of cells and a contiguous chunk of velocities, processed
+// VB velocities per barrier round.  Per round it stages in shared memory
 //   phase 1  phi-bar-plus of the tile and its two-cell halo (the derived conversion
 //            phi-bar-plus = phi~ + b (phi^S - phi~) of Sec. 2.2);
 //   phase 2  limited slopes (Eq. reconstruction) of the cells that can be upwind of a face;
 //   phase 3  the face phi-bar of the upwind side by the characteristic
-//            (Eq. bar_phi_transport).  MODE 0 accumulates the face moments over the chunk
-//            (input of Eq. W_from_bar).  MODE 1 recovers the face phi (Eq. recover_phi);
-//   phase 4  (MODE 1) Eq. explicit_update of the tile's cells, the store of phi~^{n+1} and
-//            the cell moments of the stored values (input of Eq. discrete_W / discrete_q).
+//            (Eq. bar_phi_transport) for the faces the tile owns: stored to the face buffer
+//            and accumulated into the face moments over the chunk (input of Eq. W_from_bar).
+// k_update: the same tiles and chunks, no halo.  Per round each thread evaluates the face
+// phi (Eq. recover_phi) of its cell's low-side faces (and the tile's high-side boundary faces)
+// from the stored face phi-bar and the face model, the microflux (xi.n) phi, and after a
+// barrier Eq. explicit_update of its cell, the store of phi~^{n+1} and the cell moments of
+// the stored values (input of Eq. discrete_W / discrete_q).
 // Velocity is uniform across the CTA inside a round, so the upwind choice by sign(xi.n) is
 // a uniform branch.  Halo sources are wrapped (periodic sides) or clamped (ghost copies of
 // the boundary cell on the other sides).
@@ -41,6 +44,8 @@ struct TileArgs {
   int nX;
   const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
   int nY;
+  void* fbar;            // (T) [2][nv][nface] face phi-bar of the faces this level evaluates
+                         // (k_faces writes the faces its tile owns, k_update reads them)
   const void* ucell;     // (T) [2][ncell] cell velocities (face moment shifts)
   const void* cgeo;      // curvilinear (T) [5][ncell]: J^{-T} (4, row-major), dt/|V|
   const void* fgeo;      // curvilinear (T) [7][nface]: normal (2), |S|, x_b - x_L (2), x_b - x_R (2)
@@ -95,18 +100,76 @@ template <int TX, int TY, int D> struct TileGeom {
   }
 };
 
-// Shared-memory layout of a tile kernel (bytes), identical on host and device.
-template <class T, int TX, int TY, int D, int VB, int MODE, bool CV = false> struct TileSmem {
+// The box of cells k_faces stages per round: the tile and a halo of two cells on the low
+// sides and one on the high sides, x in [-2, TX], y in [-2, TY].  That covers every upwind
+// cell of the faces the tile owns (low-side faces li in [0, TX), lj in [0, TY), and the last
+// face of a non-periodic axis when it falls on the tile's edge) with the neighbours of its
+// slopes.  A slope at the high edge of the box belongs to a ghost cell beyond a non-periodic
+// mesh end, whose neighbour beyond is the same ghost copy.
+template <int TX, int TY, int D> struct FaceBox {
+  static constexpr int NT = TX * TY;
+  static constexpr int BW = TX + 3;
+  static constexpr int BH = (D == 2) ? TY + 3 : 1;
+  static constexpr int NB = BW * BH;
+  static constexpr int NH = NB - NT;     // halo cells
+  static constexpr int SW = TX + 2;      // curvilinear J^{-T} rectangle, x in [-1, TX], y in [-1, TY]
+  static constexpr int SH = (D == 2) ? TY + 2 : 1;
+  static constexpr int NSL = SW * SH;
+  static __device__ __forceinline__ int bidx(int x, int y) { return (D == 2) ? (y + 2) * BW + (x + 2) : (x + 2); }
+  static __device__ __forceinline__ int sidx(int x, int y) { return (D == 2) ? (y + 1) * SW + (x + 1) : (x + 1); }
+  // k-th halo cell: the two rows below the tile, the row above it, then per tile row the two
+  // cells on the left and the one on the right
+  static __device__ __forceinline__ void halo_pos(int k, int& x, int& y) {
+    if (D == 1) {
+      x = (k < 2) ? k - 2 : TX;
+      y = 0;
+      return;
+    }
+    if (k < 2 * BW) { y = k / BW - 2; x = k % BW - 2; return; }
+    k -= 2 * BW;
+    if (k < BW) { y = TY; x = k - 2; return; }
+    k -= BW;
+    y = k / 3;
+    const int c = k % 3;
+    x = (c < 2) ? c - 2 : TX;
+  }
+};
+
+// Shared-memory layout of k_faces (bytes), identical on host and device: the chunk's velocity
+// table by pairs; phi-bar-plus of the box by pairs, double-buffered (one barrier per round);
+// the accumulators of the high-edge faces (warp 0, mesh-end tiles); on curvilinear meshes
+// J^{-T} of the possible upwind cells and the geometry of the tile's faces.
+constexpr int kVpcMax = 384;   // largest velocity chunk of a tile launch (even)
+
+template <class T, int TX, int TY, int D, bool CV = false> struct TileSmem {
+  using B = FaceBox<TX, TY, D>;
   using G = TileGeom<TX, TY, D>;
-  static constexpr size_t P = 0;                                           // T [VB][2][NEXT]
-  static constexpr size_t SL = P + sizeof(T) * VB * 2 * G::NEXT;            // T [VB][4][NSL]
-  static constexpr size_t F = SL + sizeof(T) * VB * 4 * G::NSL;             // T [VB][2][NF]   (MODE 1)
-  static constexpr size_t FP = F + (MODE == 1 ? sizeof(T) * VB * 2 * G::NF : 0);  // T [16][NF] (MODE 1)
-  static constexpr size_t ACC = FP + (MODE == 1 ? sizeof(T) * 16 * G::NF : 0);     // T [16][NF] (MODE 0)
-  static constexpr size_t META = ACC + (MODE == 0 ? sizeof(T) * 16 * G::NF : 0);   // int [2][NF]
-  static constexpr size_t JT = META + sizeof(int) * 2 * G::NF;                      // T [4][NSL] (CV)
-  static constexpr size_t FG = JT + (CV ? sizeof(T) * 4 * G::NSL : 0);               // T [7][NF]  (CV)
+  using V = V2<T>;
+  static constexpr int NX3 = (D == 2) ? TX + TY : 1;
+  static constexpr size_t VT = 0;                                          // V [kVpcMax/2][4]
+  static constexpr size_t P = VT + sizeof(V) * 4 * (kVpcMax / 2);           // V [2][2][NB]
+  static constexpr size_t ACC = P + sizeof(V) * 2 * 2 * B::NB;              // T [13][NX3]
+  static constexpr size_t JT = ACC + sizeof(T) * 13 * NX3;                  // T [4][NSL] (CV)
+  static constexpr size_t FG = JT + (CV ? sizeof(T) * 4 * B::NSL : 0);      // T [7][NF]  (CV)
   static constexpr size_t BYTES = FG + (CV ? sizeof(T) * 7 * G::NF : 0);
+};
+
+// Shared-memory layout of k_update (bytes): the microfluxes of the faces A and B of a round
+// by pairs, double-buffered so one barrier per round suffices; the microfluxes of the tile's
+// high-side faces C over a sub-chunk of SC pairs, double-buffered; the chunk's velocity table
+// by pairs (padded to whole sub-chunks); the parameters and ids of the faces C.
+template <class T, int TX, int TY, int D, int VPC> struct UpdSmem {
+  using G = TileGeom<TX, TY, D>;
+  using V = V2<T>;
+  static constexpr int NX3 = (D == 2) ? TX + TY : 1;                        // high-side faces
+  static constexpr int SC = 16;                                            // pairs per sub-chunk
+  static constexpr int NPT = ((VPC / 2) + SC - 1) / SC * SC;               // padded pairs
+  static constexpr size_t F = 0;                                           // V [2][2][NF]
+  static constexpr size_t C = F + sizeof(V) * 2 * 2 * G::NF;               // V [2][2][SC][NX3]
+  static constexpr size_t VT = C + sizeof(V) * 2 * 2 * SC * NX3;           // V [NPT][4]
+  static constexpr size_t XP = VT + sizeof(V) * 4 * NPT;                   // T [16][NX3]
+  static constexpr size_t XI = XP + sizeof(T) * 16 * NX3;                  // long [4][NX3]
+  static constexpr size_t BYTES = (XI + sizeof(long) * 4 * NX3 + 15) / 16 * 16;
 };
 
 __device__ __forceinline__ int wrap_or_clamp(int g, int n, int periodic) {
@@ -115,13 +178,17 @@ __device__ __forceinline__ int wrap_or_clamp(int g, int n, int periodic) {
 }
 
 // van Leer limited slope (reading of Eq. reconstruction): 2ab/(a+b)/h for a, b of equal
-// strict sign (ab > 0; an underflowing product counts as 0), else 0.  limiter == 1: central difference (a+b)/(2h).
+// strict sign (ab > 0; an underflowing product counts as 0), else 0.  limiter == 1: central
+// difference (a+b)/(2h).  Both are formed and one is selected (no branch); a quotient of a
+// pair that is not selected may be infinite or NaN.
 template <class T>
 __device__ __forceinline__ T limited(T a, T b, T inv_h, int limiter) {
   using N = Num<T>;
-  if (limiter) return N::mul(N::mul(T(0.5), N::add(a, b)), inv_h);
   const T ab = N::mul(a, b);
-  return (ab > T(0)) ? N::mul(N::dv(N::mul(T(2), ab), N::add(a, b)), inv_h) : T(0);
+  const T sum = N::add(a, b);
+  const T vl = N::mul(N::dv(N::mul(T(2), ab), sum), inv_h);
+  const T ce = N::mul(N::mul(T(0.5), sum), inv_h);
+  return limiter ? ce : ((ab > T(0)) ? vl : T(0));
 }
 
 // face metadata word: bit 0 valid, bit 1 owned (MODE 0 accumulates), bits 2-4 kind, role above
@@ -180,30 +247,105 @@ __device__ __forceinline__ void write_partials_smem(const T* acc, int sa, double
   P[MO_JY * st] = (double)acc[12 * sa];
 }
 
+// Metadata of tile-local face f of the tile at (x0, y0): returns the meta word (bit 0 valid,
+// bit 1 owned by this tile, bits 2-4 boundary kind, role above) and the global face id (-1 if
+// the face is outside the mesh).  A face is owned by the tile on its high side (its li < TX),
+// the last face of a non-periodic axis by the last tile.
+template <int TX, int TY, int D, bool ML>
+__device__ __forceinline__ int face_meta(const TileArgs& a, int x0, int y0, int f, int& fid) {
+  using G = TileGeom<TX, TY, D>;
+  const StepConst& k = a.k;
+  int dir, li, lj;
+  G::face_pos(f, dir, li, lj);
+  const int gi = x0 + li, gj = y0 + lj;
+  int meta = 0, role = FR_NONE;
+  fid = -1;
+  if (dir == 0) {
+    if (gi <= k.nx && (D == 1 || gj < k.ny)) {
+      const int pi = (k.px && gi == k.nx) ? 0 : gi;
+      fid = ((D == 2) ? gj : 0) * k.nfx + pi;
+      role = ML ? a.frole[fid] : FR_NORMAL;
+      meta = FM_VALID;
+      if ((gi < k.nx) ? (li < TX) : !k.px) meta |= FM_OWNED;
+      if (!k.px && gi == 0 && k.bc[0] == BC_WALL) meta |= FK_WALL_LO << 2;
+      if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) meta |= FK_WALL_HI << 2;
+      if (!k.px && gi == 0 && k.bc[0] == BC_FREE) meta |= FK_FREE_LO << 2;
+      if (!k.px && gi == k.nx && k.bc[1] == BC_FREE) meta |= FK_FREE_HI << 2;
+    }
+  } else {
+    if (gi < k.nx && gj <= k.ny) {
+      const int pj = (k.py && gj == k.ny) ? 0 : gj;
+      fid = k.nfx * k.ny + pj * k.nx + gi;
+      role = ML ? a.frole[fid] : FR_NORMAL;
+      meta = FM_VALID;
+      if ((gj < k.ny) ? (lj < TY) : !k.py) meta |= FM_OWNED;
+      if (!k.py && gj == 0 && k.bc[2] == BC_WALL) meta |= FK_WALL_LO << 2;
+      if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) meta |= FK_WALL_HI << 2;
+      if (!k.py && gj == 0 && k.bc[2] == BC_FREE) meta |= FK_FREE_LO << 2;
+      if (!k.py && gj == k.ny && k.bc[3] == BC_FREE) meta |= FK_FREE_HI << 2;
+    }
+  }
+  if (role == FR_NONE) meta = 0;
+  return meta | (role << 5);
+}
+
+// ---------------------------------------------------------------------------------------
+// Velocity pairs.  Both tile kernels process the velocities of their chunk two at a time,
+// lanes (v, v+1) of one thread, with the packed two-lane arithmetic of Pk<T>; chunks start
+// at even velocities, and a pair past the end of the velocity set has a padding lane (its
+// loads repeat the last velocity, its weight is zero and nothing of it is stored).  The face
+// buffer interleaves the pair: fbar[comp][v / 2][face][v % 2].
+__device__ __forceinline__ long fbar_at(long comp, long v, long fid, long nvp, long nfc) {
+  return ((comp * nvp + (v >> 1)) * nfc + fid) * 2 + (v & 1);
+}
+
+// van Leer limited slopes of a pair (limited() lane by lane, the quotient per lane).
+template <class T>
+__device__ __forceinline__ V2<T> limited2(V2<T> a, V2<T> b, T inv_h, int limiter) {
+  using P = Pk<T>;
+  using N = Num<T>;
+  const V2<T> ab = P::mul(a, b);
+  const V2<T> sum = P::add(a, b);
+  const V2<T> n2 = P::mul(P::splat(T(2)), ab);
+  const V2<T> vl = P::mul(P::mk(N::dv(n2.x, sum.x), N::dv(n2.y, sum.y)), P::splat(inv_h));
+  const V2<T> ce = P::mul(P::mul(P::splat(T(0.5)), sum), P::splat(inv_h));
+  V2<T> r;
+  r.x = limiter ? ce.x : ((ab.x > T(0)) ? vl.x : T(0));
+  r.y = limiter ? ce.y : ((ab.y > T(0)) ? vl.y : T(0));
+  return r;
+}
+
 // ML = false: the level holds every cell of the mesh (one velocity space), so every stencil
 // position is an own cell in natural order and every face is a normal face; the level
 // tables are not read.
 // CV: structured curvilinear mesh (2-D): slopes along the index directions turned into
 // physical slopes with the cell's J^{-T}, faces with their own normals, areas and centroid
-// offsets (precomputed per face, so the two tiles of a face read the same values), and the
-// update scaled by dt/|V|.
-template <class S, class T, int D, int TX, int TY, int VB, int MODE, bool ML, bool CV>
-__global__ void __launch_bounds__(TX * TY)
-k_tile(const TileArgs a, int limiter) {
+// offsets (precomputed per face, so the two tiles of a face read the same values).
+//
+// Per round (one velocity pair): every thread stages phi-bar-plus of its own cell, and the
+// first NH threads of one halo cell, into the box (one barrier; the box is double-buffered);
+// then each thread reconstructs its cell's two low-side faces (A: x-face, B: y-face) from the
+// upwind cell, whose two limited slopes it evaluates from the box, stores the face phi-bar to
+// the face buffer and accumulates the face moments.  When the two lanes of a face have the
+// same strict sign of xi.n (nearly every pair) the pair takes one upwind cell; otherwise each
+// lane is reconstructed on its own.  Warp 0 of a tile whose high edge is a non-periodic mesh
+// end does the same for the faces on that edge.
+template <class S, class T, int D, int TX, int TY, bool ML, bool CV>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_faces(const TileArgs a, int limiter) {
   using G = TileGeom<TX, TY, D>;
-  using L = TileSmem<T, TX, TY, D, VB, MODE, CV>;
-  static_assert(!CV || D == 2, "curvilinear meshes are two-dimensional");
+  using B = FaceBox<TX, TY, D>;
+  using L = TileSmem<T, TX, TY, D, CV>;
+  using V = V2<T>;
+  using P = Pk<T>;
   using N = Num<T>;
-  static_assert(G::NHALO <= G::NT, "halo larger than the thread count");
-  static_assert(G::NSL <= 2 * G::NT, "slope rectangle larger than two per thread");
-  static_assert(G::NF <= 3 * G::NT, "faces larger than three per thread");
+  static_assert(!CV || D == 2, "curvilinear meshes are two-dimensional");
+  static_assert(B::NH <= G::NT, "more halo cells than threads");
+  static_assert(L::NX3 <= 32, "high-edge faces beyond warp 0");
   extern __shared__ __align__(16) unsigned char smem[];
-  T* sP = reinterpret_cast<T*>(smem + L::P);
-  T* sS = reinterpret_cast<T*>(smem + L::SL);
-  T* sF = reinterpret_cast<T*>(smem + L::F);
-  T* sFP = reinterpret_cast<T*>(smem + L::FP);
+  V* sVT = reinterpret_cast<V*>(smem + L::VT);
+  V* sP = reinterpret_cast<V*>(smem + L::P);
   T* sAcc = reinterpret_cast<T*>(smem + L::ACC);
-  int* sMeta = reinterpret_cast<int*>(smem + L::META);
   T* sJt = reinterpret_cast<T*>(smem + L::JT);
   T* sFG = reinterpret_cast<T*>(smem + L::FG);
   const T* __restrict__ cg = reinterpret_cast<const T*>(a.cgeo);
@@ -212,503 +354,661 @@ k_tile(const TileArgs a, int limiter) {
   const StepConst& k = a.k;
   const S* __restrict__ fin = reinterpret_cast<const S*>(a.f_in);
   const T* __restrict__ cp = reinterpret_cast<const T*>(a.cparam);
-  const T* __restrict__ fp = reinterpret_cast<const T*>(a.fparam);
   const T* __restrict__ vt = reinterpret_cast<const T*>(a.vt);
   const T* __restrict__ gst = reinterpret_cast<const T*>(a.ghost);
   const T* __restrict__ uc = reinterpret_cast<const T*>(a.ucell);
+  T* __restrict__ fbo = reinterpret_cast<T*>(a.fbar);
   const long ns = a.nslot;
   const long ng = a.nghost;
   const long nv = k.nv;
+  const long nvp = (k.nv + 1) / 2;
+  const long nfc = k.nface;
 
   const int tid = threadIdx.x;
-  const int tx = tid % TX, ty = tid / TX;
-  unsigned seed = 0;
-  if constexpr (MODE == 1 && sizeof(S) == 2) seed = hash32(*a.step * 0x632be5abu + a.salt);
+  const int tx = tid % TX, ty = (D == 2) ? tid / TX : 0;
   const int tile = a.tiles[blockIdx.x];
   const int bx = tile % a.ntx, by = tile / a.ntx;
   const int x0 = bx * TX, y0 = by * TY;
   const int chunk = blockIdx.y;
-  const int v0 = chunk * k.vpc;
+  const int v0 = chunk * k.vpc;               // even: k.vpc is even
   const int v1 = min(k.nv, v0 + k.vpc);
+  const int npr = (v1 - v0 + 1) / 2;          // pairs of the chunk
 
-  // ---- extended positions: own cell + at most one halo cell.  A position holds a cell of
-  // this level (phi~ + parameters -> phi-bar-plus), a ghost (phi-bar-plus mapped to this
-  // space), or nothing (never read by a face evaluated here).
-  auto classify = [&](int ex, int ey, int& kind, long& base, long& ld) {
+  // the chunk's velocity table by pairs: (xi_x, xi_y, w_x, w_y), a padding lane with zeros
+  for (int j = tid; j < npr; j += G::NT) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int v = v0 + 2 * j;
+      const T e0 = (r == 1 && D == 1) ? T(0) : vt[r * nv + v];
+      const T e1 = (v + 1 < v1 && !(r == 1 && D == 1)) ? vt[r * nv + v + 1] : T(0);
+      sVT[4 * j + r] = P::mk(e0, e1);
+    }
+  }
+
+  // ---- box positions: the own cell, and one halo cell for the first NH threads.  A position
+  // holds a cell of this level (phi~ + parameters -> phi-bar-plus), a ghost (phi-bar-plus
+  // mapped to this space), or nothing (never read by a face evaluated here).  Loads: a base
+  // pointer and a velocity stride (0: a dummy element).
+  auto classify = [&](int ex, int ey, int& kind, long& col) {
     const int c = wrap_or_clamp(y0 + ey, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + ex, k.nx, k.px);
-    kind = 0; base = 0; ld = 0;
-    if (!ML) { kind = 1; base = c; ld = ns; }
-    else if (a.lvl_of[c] == a.level) { kind = 1; base = a.slot_of[c]; ld = ns; }
-    else if (a.ghost_of && a.ghost_of[c] >= 0) { kind = 2; base = a.ghost_of[c]; ld = ng; }
-    return c;
+    kind = 0; col = 0;
+    if (!ML) { kind = 1; col = c; }
+    else if (a.lvl_of[c] == a.level) { kind = 1; col = a.slot_of[c]; }
+    else if (a.ghost_of && a.ghost_of[c] >= 0) { kind = 2; col = a.ghost_of[c]; }
   };
-  const int ey0 = (D == 2) ? ty : 0;
   int kind0, kind1 = 0;
-  long col0, ld0, col1 = 0, ld1 = 0;
-  const int c0g = classify(tx, ey0, kind0, col0, ld0);
-  const bool own_active = (x0 + tx < k.nx) && (D == 1 || y0 + ty < k.ny) && kind0 == 1 &&
-                          c0g == (y0 + ey0) * k.nx + (x0 + tx);
-  int ex1 = 0, ey1 = 0;
-  if (tid < G::NHALO) {
-    G::halo_pos(tid, ex1, ey1);
-    classify(ex1, ey1, kind1, col1, ld1);
+  long col0, col1 = 0;
+  classify(tx, ty, kind0, col0);
+  const bool halo = tid < B::NH;
+  int e1 = 0;
+  if (halo) {
+    int ex1, ey1;
+    B::halo_pos(tid, ex1, ey1);
+    classify(ex1, ey1, kind1, col1);
+    e1 = B::bidx(ex1, ey1);
   }
   MP<T> m0, m1;
+  m0.zero();
+  m1.zero();
   if (kind0 == 1) m0.load(cp, ns, col0);
   if (kind1 == 1) m1.load(cp, ns, col1);
-  const int e0 = G::eidx(tx, ey0);
-  const int e1 = (tid < G::NHALO) ? G::eidx(ex1, ey1) : 0;
-
-  // ---- face metadata (and MODE 1 parameters, MODE 0 shifts/accumulators) in shared memory
-  for (int f = tid; f < G::NF; f += G::NT) {
-    int dir, li, lj;
-    G::face_pos(f, dir, li, lj);
-    const int gi = x0 + li, gj = y0 + lj;
-    int meta = 0, fid = -1, role = FR_NONE;
-    if (dir == 0) {
-      if (gi <= k.nx && (D == 1 || gj < k.ny)) {
-        const int pi = (k.px && gi == k.nx) ? 0 : gi;
-        fid = ((D == 2) ? gj : 0) * k.nfx + pi;
-        role = ML ? a.frole[fid] : FR_NORMAL;
-        meta = FM_VALID;
-        if ((gi < k.nx) ? (li < TX) : !k.px) meta |= FM_OWNED;
-        if (!k.px && gi == 0 && k.bc[0] == BC_WALL) meta |= FK_WALL_LO << 2;
-        if (!k.px && gi == k.nx && k.bc[1] == BC_WALL) meta |= FK_WALL_HI << 2;
-        if (!k.px && gi == 0 && k.bc[0] == BC_FREE) meta |= FK_FREE_LO << 2;
-        if (!k.px && gi == k.nx && k.bc[1] == BC_FREE) meta |= FK_FREE_HI << 2;
-      }
+  const int e0 = B::bidx(tx, ty);
+  const void* p0 = fin;
+  long st0 = 0;
+  if (kind0 == 1) { p0 = fin + col0; st0 = ns; }
+  else if (ML && kind0 == 2) { p0 = gst + col0; st0 = ng; }
+  const void* p1 = fin;
+  long st1 = 0;
+  if (kind1 == 1) { p1 = fin + col1; st1 = ns; }
+  else if (ML && kind1 == 2) { p1 = gst + col1; st1 = ng; }
+  // the pair of lanes at velocities (v, v+1) of a position: g at p[v st], h at p[(nv + v) st]
+  auto ld2 = [&](int kind, const void* p, long st, int v, V& g, V& h) {
+    const long va = v, vb = min(v + 1, v1 - 1);
+    if (!ML || kind != 2) {
+      const S* q = reinterpret_cast<const S*>(p);
+      g = P::mk(ldf<S, T>(q + va * st), ldf<S, T>(q + vb * st));
+      h = P::mk(ldf<S, T>(q + (nv + va) * st), ldf<S, T>(q + (nv + vb) * st));
     } else {
-      if (gi < k.nx && gj <= k.ny) {
-        const int pj = (k.py && gj == k.ny) ? 0 : gj;
-        fid = k.nfx * k.ny + pj * k.nx + gi;
-        role = ML ? a.frole[fid] : FR_NORMAL;
-        meta = FM_VALID;
-        if ((gj < k.ny) ? (lj < TY) : !k.py) meta |= FM_OWNED;
-        if (!k.py && gj == 0 && k.bc[2] == BC_WALL) meta |= FK_WALL_LO << 2;
-        if (!k.py && gj == k.ny && k.bc[3] == BC_WALL) meta |= FK_WALL_HI << 2;
-        if (!k.py && gj == 0 && k.bc[2] == BC_FREE) meta |= FK_FREE_LO << 2;
-        if (!k.py && gj == k.ny && k.bc[3] == BC_FREE) meta |= FK_FREE_HI << 2;
-      }
+      const T* q = reinterpret_cast<const T*>(p);
+      g = P::mk(q[va * st], q[vb * st]);
+      h = P::mk(q[(nv + va) * st], q[(nv + vb) * st]);
     }
-    if (role == FR_NONE) meta = 0;
-    meta |= role << 5;
-    sMeta[f] = meta;
-    sMeta[G::NF + f] = (role == FR_CROSS || role == FR_RECV) ? a.fslot[fid] : fid;
-    if constexpr (CV) {
+  };
+
+  // ---- faces: A (x-face li = tx, lj = ty), B (2-D: y-face li = tx, lj = ty), C (warp 0 of a
+  // tile whose high edge is a non-periodic mesh end: the faces on that edge)
+  struct FaceQ {
+    int meta, kind, dir, li, lj, f;
+    long fid;
+    T shx, shy;
+  };
+  auto setup = [&](int f, FaceQ& F) {
+    int fid;
+    F.f = f;
+    G::face_pos(f, F.dir, F.li, F.lj);
+    F.meta = face_meta<TX, TY, D, ML>(a, x0, y0, f, fid);
+    F.fid = fid;
+    F.kind = (F.meta >> 2) & 7;
+    const int role = F.meta >> 5;
+    // evaluated here: owned, and a normal or cross face of this level
+    if (!(F.meta & FM_VALID) || !(F.meta & FM_OWNED) || (ML && role == FR_RECV)) F.meta = 0;
+    F.shx = F.shy = T(0);
+    if (F.meta) {
+      const int xl = (F.dir == 0) ? F.li - 1 : F.li, yl = (F.dir == 0) ? F.lj : F.lj - 1;
+      const int sL = wrap_or_clamp(y0 + yl, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + xl, k.nx, k.px);
+      const int sR = wrap_or_clamp(y0 + F.lj, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + F.li, k.nx, k.px);
+      F.shx = T(0.5) * (uc[sL] + uc[sR]);
+      if (D == 2) F.shy = T(0.5) * (uc[k.ncell + sL] + uc[k.ncell + sR]);
+    }
+  };
+  FaceQ FA, FB;
+  setup(ty * (TX + 1) + tx, FA);
+  if (D == 2) setup(G::NFXL + ty * TX + tx, FB);
+  else FB.meta = 0;
+  const bool edgeC = (!k.px && x0 + TX == k.nx) || (D == 2 && !k.py && y0 + TY == k.ny);
+  FaceQ FC;
+  FC.meta = 0;
+  if (edgeC && tid < L::NX3) {
+    const int fC = (D == 1) ? TX : (tid < TY ? tid * (TX + 1) + TX : G::NFXL + TY * TX + (tid - TY));
+    setup(fC, FC);
+#pragma unroll
+    for (int p = 0; p < 13; ++p) sAcc[p * L::NX3 + tid] = T(0);
+  }
+  if constexpr (CV) {
+    for (int f = tid; f < G::NF; f += G::NT) {
+      int fid;
+      face_meta<TX, TY, D, ML>(a, x0, y0, f, fid);
 #pragma unroll
       for (int p = 0; p < 7; ++p) sFG[p * G::NF + f] = fid >= 0 ? fg[(long)p * k.nface + fid] : T(0);
     }
-    if (MODE == 1 && (role == FR_NORMAL || role == FR_CROSS)) {
-#pragma unroll
-      for (int p = 0; p < 13; ++p) sFP[p * G::NF + f] = fp[(long)p * k.nface + fid];
-    }
-    if (MODE == 0) {
-      T shx = T(0), shy = T(0);
-      if (fid >= 0) {
-        const int xl = (dir == 0) ? li - 1 : li, yl = (dir == 0) ? lj : lj - 1;
-        const int sL = wrap_or_clamp(y0 + yl, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + xl, k.nx, k.px);
-        const int sR = wrap_or_clamp(y0 + lj, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + li, k.nx, k.px);
-        shx = T(0.5) * (uc[sL] + uc[sR]);
-        if (D == 2) shy = T(0.5) * (uc[k.ncell + sL] + uc[k.ncell + sR]);
-      }
-#pragma unroll
-      for (int p = 0; p < 13; ++p) sAcc[p * G::NF + f] = T(0);
-      sAcc[13 * G::NF + f] = shx;   // slots 13, 14 hold the shift (never accumulated)
-      sAcc[14 * G::NF + f] = shy;
-      // the face partials of this level are read only where the role says so
-      if (fid >= 0 && (role == FR_NORMAL || role == FR_CROSS)) sMeta[G::NF + f] = fid;
-    }
-  }
-
-  // curvilinear: J^{-T} of the slope rectangle (ghost positions take the boundary cell's)
-  if constexpr (CV) {
-    for (int q = tid; q < G::NSL; q += G::NT) {
-      const int sx = q % G::SW - 1, sy = q / G::SW - 1;
+    // J^{-T} of the possible upwind cells (ghost positions take the boundary cell's)
+    for (int q = tid; q < B::NSL; q += G::NT) {
+      const int sx = q % B::SW - 1, sy = q / B::SW - 1;
       const int c = wrap_or_clamp(y0 + sy, k.ny, k.py) * k.nx + wrap_or_clamp(x0 + sx, k.nx, k.px);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) sJt[p * G::NSL + q] = cg[(long)p * k.ncell + c];
+      for (int p = 0; p < 4; ++p) sJt[p * B::NSL + q] = cg[(long)p * k.ncell + c];
     }
   }
-  // MODE 0 accumulators of the thread's first two faces in registers:
-  // Kahan (s, c) for M0, MX, MY, E, plain for Gxx, Gxy, Gyy, Jx, Jy
+  // accumulators of faces A and B: Kahan (s, c) for M0, MX, MY, E, plain for Gxx, Gxy, Gyy, Jx, Jy
   T ra[2][13];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int p = 0; p < 13; ++p) ra[q][p] = T(0);
-  // MODE 1 accumulators of the own cell
-  KSum<T> c0k, cxk, cyk, cek;
-  c0k.zero(); cxk.zero(); cyk.zero(); cek.zero();
-  T cgxx = T(0), cgxy = T(0), cgyy = T(0), cjx = T(0), cjy = T(0);
 
   const T c0 = T(k.c0), twoK = T(k.twoK);
   const T s = T(0.5 * k.dt);
   const T hdx = T(0.5 * k.dx), hdy = T(0.5 * k.dy);
   const T idx_ = T(1.0 / k.dx), idy_ = T(1.0 / k.dy);
-  T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
-  if constexpr (CV) {
-    if (own_active) lamx = lamy = cg[4L * k.ncell + c0g];   // dt / |V| of the own cell
-  }
-  S* __restrict__ fout = reinterpret_cast<S*>(a.f_out);
-  T* __restrict__ Xo = reinterpret_cast<T*>(a.X);
-  const T* __restrict__ Yi = reinterpret_cast<const T*>(a.Y);
-  __syncthreads();
-  // shifts of the thread's register-held faces (MODE 0)
-  T fshx[2] = {T(0), T(0)}, fshy[2] = {T(0), T(0)};
-  if (MODE == 0) {
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const int f = tid + q * G::NT;
-      if (f < G::NF) { fshx[q] = sAcc[13 * G::NF + f]; fshy[q] = sAcc[14 * G::NF + f]; }
-    }
-  }
 
-  // loads of one velocity for a position of each kind
-  auto load_pos = [&](int kind, long col, int v, T& g, T& h) {
-    if (!ML || kind == 1) {
-      g = ldf<S, T>(fin + (long)v * ns + col);
-      h = ldf<S, T>(fin + (nv + v) * ns + col);
-    } else if (kind == 2) {
-      g = gst[(long)v * ng + col];
-      h = gst[(nv + v) * ng + col];
+  // limited slopes of box cell (cx, cy) along x and y (index directions on curvilinear
+  // meshes): lane by lane from one plane of the box
+  auto slopes = [&](const V* Pl, int cx, int cy, T hx, T hy, V& sx, V& sy) {
+    const int e = B::bidx(cx, cy);
+    const V pc = Pl[e];
+    const V pxp = Pl[(cx < TX) ? e + 1 : e];
+    sx = limited2<T>(P::sub(pxp, pc), P::sub(pc, Pl[e - 1]), hx, limiter);
+    sy = P::splat(T(0));
+    if (D == 2) {
+      const V pyp = Pl[(cy < TY) ? e + B::BW : e];
+      sy = limited2<T>(P::sub(pyp, pc), P::sub(pc, Pl[e - B::BW]), hy, limiter);
+    }
+  };
+  // phi-bar of face F (Eq. bar_phi_transport with Eq. reconstruction), both lanes from one
+  // upwind cell; (ox, oy) is x_b - x_up
+  auto rec2 = [&](const FaceQ& F, const V* Pg, const V* Ph, int cx, int cy, V ox, V oy, V bx_, V by_, V& gb,
+                  V& hb) {
+    const int e = B::bidx(cx, cy);
+    V gx, gy, hx, hy;
+    if constexpr (CV) {
+      V gi, gj, hi, hj;
+      slopes(Pg, cx, cy, T(1), T(1), gi, gj);
+      slopes(Ph, cx, cy, T(1), T(1), hi, hj);
+      const int si = B::sidx(cx, cy);
+      const V j00 = P::splat(sJt[si]), j01 = P::splat(sJt[B::NSL + si]);
+      const V j10 = P::splat(sJt[2 * B::NSL + si]), j11 = P::splat(sJt[3 * B::NSL + si]);
+      gx = P::fma(j01, gj, P::mul(j00, gi));
+      hx = P::fma(j01, hj, P::mul(j00, hi));
+      gy = P::fma(j11, gj, P::mul(j10, gi));
+      hy = P::fma(j11, hj, P::mul(j10, hi));
+      gb = P::fma(P::add(oy, by_), gy, P::fma(P::add(ox, bx_), gx, Pg[e]));
+      hb = P::fma(P::add(oy, by_), hy, P::fma(P::add(ox, bx_), hx, Ph[e]));
+      return;
+    }
+    slopes(Pg, cx, cy, idx_, idy_, gx, gy);
+    slopes(Ph, cx, cy, idx_, idy_, hx, hy);
+    (void)F;
+    if (F.dir == 0) {
+      gb = P::fma(P::add(ox, bx_), gx, Pg[e]);
+      hb = P::fma(P::add(ox, bx_), hx, Ph[e]);
+      if (D == 2) {
+        gb = P::fma(by_, gy, gb);
+        hb = P::fma(by_, hy, hb);
+      }
     } else {
-      g = T(0);
-      h = T(0);
+      gb = P::fma(P::add(oy, by_), gy, P::fma(bx_, gx, Pg[e]));
+      hb = P::fma(P::add(oy, by_), hy, P::fma(bx_, hx, Ph[e]));
+    }
+  };
+  // xi.n of face F for a pair, and the face phi-bar
+  auto face_bar = [&](const FaceQ& F, const V* Pg, const V* Ph, V xix, V xiy, V& gb, V& hb, V& xn) {
+    const V bx_ = P::mul(P::mk(-xix.x, -xix.y), P::splat(s)), by_ = P::mul(P::mk(-xiy.x, -xiy.y), P::splat(s));
+    const int lx = F.dir == 0 ? F.li - 1 : F.li, ly = F.dir == 0 ? F.lj : F.lj - 1;
+    V oLx, oLy, oRx, oRy;
+    if constexpr (CV) {
+      // xi.n as two rounded products and a rounded sum: its sign picks the upwind side, and a
+      // velocity tangential to the face gives the same rounded value wherever this is evaluated
+      xn = P::add(P::mul(xix, P::splat(sFG[F.f])), P::mul(xiy, P::splat(sFG[G::NF + F.f])));
+      oLx = P::splat(sFG[3 * G::NF + F.f]); oLy = P::splat(sFG[4 * G::NF + F.f]);
+      oRx = P::splat(sFG[5 * G::NF + F.f]); oRy = P::splat(sFG[6 * G::NF + F.f]);
+    } else if (F.dir == 0) {
+      xn = xix;
+      oLx = P::splat(hdx); oRx = P::splat(-hdx); oLy = oRy = P::splat(T(0));
+    } else {
+      xn = xiy;
+      oLy = P::splat(hdy); oRy = P::splat(-hdy); oLx = oRx = P::splat(T(0));
+    }
+    if ((xn.x > T(0) && xn.y > T(0)) || (xn.x < T(0) && xn.y < T(0))) {
+      // one upwind cell for both lanes
+      if (xn.x > T(0)) rec2(F, Pg, Ph, lx, ly, oLx, oLy, bx_, by_, gb, hb);
+      else rec2(F, Pg, Ph, F.li, F.lj, oRx, oRy, bx_, by_, gb, hb);
+    } else {
+      // lane by lane: the upwind side of each lane, the mean of both sides where xi.n = 0
+      V gL, hL, gR, hR;
+      rec2(F, Pg, Ph, lx, ly, oLx, oLy, bx_, by_, gL, hL);
+      rec2(F, Pg, Ph, F.li, F.lj, oRx, oRy, bx_, by_, gR, hR);
+      const V gm = P::mul(P::splat(T(0.5)), P::add(gL, gR)), hm = P::mul(P::splat(T(0.5)), P::add(hL, hR));
+      gb.x = xn.x > T(0) ? gL.x : (xn.x < T(0) ? gR.x : gm.x);
+      gb.y = xn.y > T(0) ? gL.y : (xn.y < T(0) ? gR.y : gm.y);
+      hb.x = xn.x > T(0) ? hL.x : (xn.x < T(0) ? hR.x : hm.x);
+      hb.y = xn.y > T(0) ? hL.y : (xn.y < T(0) ? hR.y : hm.y);
+    }
+  };
+  // the face's contribution of a pair to its moment partials (interior faces), or to the
+  // outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) g-bar (wall faces): lanes
+  // summed in order, as scalar accumulation of the two velocities would
+  auto face_part = [&](const FaceQ& F, V gb, V hb, V xn, V xix, V xiy, V wxv, V wyv, T (&part)[9]) {
+    if (F.kind == FK_INTERIOR) {
+      const V xp = P::sub(xix, P::splat(F.shx));
+      const V yp = (D == 2) ? P::sub(xiy, P::splat(F.shy)) : P::splat(T(0));
+      const V wg = P::mul(wxv, P::mul(wyv, gb));
+      const V e = P::mul(wxv, P::mul(wyv, P::fma(P::fma(yp, yp, P::mul(xp, xp)), gb, hb)));
+      const V q1 = P::mul(wg, xp), q2 = P::mul(wg, yp);
+      const V q4 = P::mul(q1, xp), q5 = P::mul(q1, yp), q6 = P::mul(q2, yp);
+      const V q7 = P::mul(e, xp), q8 = P::mul(e, yp);
+      part[0] = wg.x + wg.y; part[1] = q1.x + q1.y; part[2] = q2.x + q2.y; part[3] = e.x + e.y;
+      part[4] = q4.x + q4.y; part[5] = q5.x + q5.y; part[6] = q6.x + q6.y;
+      part[7] = q7.x + q7.y; part[8] = q8.x + q8.y;
+    } else {
+#pragma unroll
+      for (int p = 0; p < 9; ++p) part[p] = T(0);
+      if (F.kind == FK_WALL_LO || F.kind == FK_WALL_HI) {
+        const V xin = (F.kind == FK_WALL_LO) ? xn : P::mk(-xn.x, -xn.y);
+        const V o = P::mul(wxv, P::mul(wyv, P::mul(xin, gb)));
+        part[0] = (xin.x <= T(0) ? o.x : T(0)) + (xin.y <= T(0) ? o.y : T(0));
+      }
     }
   };
 
-  // register prefetch of the first round
-  T ng0[VB], nh0[VB], ng1[VB], nh1[VB];
-#pragma unroll
-  for (int b = 0; b < VB; ++b) {
-    const int v = v0 + b;
-    ng0[b] = nh0[b] = ng1[b] = nh1[b] = T(0);
-    if (v < v1) {
-      load_pos(kind0, col0, v, ng0[b], nh0[b]);
-      load_pos(kind1, col1, v, ng1[b], nh1[b]);
-    }
-  }
+  // register prefetch of the first pair
+  V ng0, nh0, ng1 = P::splat(T(0)), nh1 = P::splat(T(0));
+  ld2(kind0, p0, st0, v0, ng0, nh0);
+  if (halo) ld2(kind1, p1, st1, v0, ng1, nh1);
 
-  for (int vb0 = v0; vb0 < v1; vb0 += VB) {
-    T g0[VB], h0[VB], dg0[VB], dh0[VB];
-    T xixb[VB], xiyb[VB], wxb[VB], wyb[VB];
-    // ---- phase 1: phi-bar-plus on the extended tile, and the prefetch of the next round
-#pragma unroll
-    for (int b = 0; b < VB; ++b) {
-      const int v = vb0 + b;
-      const bool on = v < v1;
-      const int vv = on ? v : v0;
-      xixb[b] = vt[vv];
-      xiyb[b] = (D == 2) ? vt[nv + vv] : T(0);
-      wxb[b] = vt[2 * nv + vv];
-      wyb[b] = vt[3 * nv + vv];
-      g0[b] = ng0[b]; h0[b] = nh0[b];
-      const T g1 = ng1[b], h1 = nh1[b];
-      const int vn = v + VB;
-      if (vn < v1) {
-        load_pos(kind0, col0, vn, ng0[b], nh0[b]);
-        load_pos(kind1, col1, vn, ng1[b], nh1[b]);
-      }
-      T* Pg = sP + (b * 2 + 0) * G::NEXT;
-      T* Ph = sP + (b * 2 + 1) * G::NEXT;
-      T gs, hs;
-      if (!ML || kind0 == 1) {
-        model_eval<T, D>(m0, xixb[b], xiyb[b], c0, twoK, gs, hs);
-        dg0[b] = N::sub(gs, g0[b]);
-        dh0[b] = N::sub(hs, h0[b]);
-        Pg[e0] = N::fma(m0.c1, dg0[b], g0[b]);
-        Ph[e0] = N::fma(m0.c1, dh0[b], h0[b]);
+  __syncthreads();   // velocity table in place
+  int buf = 0;
+  for (int j = 0; j < npr; ++j, buf ^= 1) {
+    const int v = v0 + 2 * j;
+    V* Pg = sP + (buf * 2 + 0) * B::NB;
+    V* Ph = sP + (buf * 2 + 1) * B::NB;
+    const V g0 = ng0, h0 = nh0, g1 = ng1, h1 = nh1;
+    if (j + 1 < npr) {
+      ld2(kind0, p0, st0, v + 2, ng0, nh0);
+      if (halo) ld2(kind1, p1, st1, v + 2, ng1, nh1);
+    }
+    const V xix = sVT[4 * j], xiy = sVT[4 * j + 1];
+    // ---- phi-bar-plus = phi~ + b (phi^S - phi~) of the own cell and the halo cell
+    if (!ML || kind0 == 1) {
+      V gs, hs;
+      model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
+      Pg[e0] = P::fma(P::splat(m0.c1), P::sub(gs, g0), g0);
+      Ph[e0] = P::fma(P::splat(m0.c1), P::sub(hs, h0), h0);
+    } else {
+      Pg[e0] = g0;
+      Ph[e0] = h0;
+    }
+    if (halo) {
+      if (!ML || kind1 == 1) {
+        V gs, hs;
+        model_eval2<T, D>(m1, xix, xiy, c0, twoK, gs, hs);
+        Pg[e1] = P::fma(P::splat(m1.c1), P::sub(gs, g1), g1);
+        Ph[e1] = P::fma(P::splat(m1.c1), P::sub(hs, h1), h1);
       } else {
-        dg0[b] = T(0);
-        dh0[b] = T(0);
-        Pg[e0] = g0[b];
-        Ph[e0] = h0[b];
-      }
-      if (tid < G::NHALO) {
-        if (!ML || kind1 == 1) {
-          model_eval<T, D>(m1, xixb[b], xiyb[b], c0, twoK, gs, hs);
-          Pg[e1] = N::fma(m1.c1, N::sub(gs, g1), g1);
-          Ph[e1] = N::fma(m1.c1, N::sub(hs, h1), h1);
-        } else {
-          Pg[e1] = g1;
-          Ph[e1] = h1;
-        }
+        Pg[e1] = g1;
+        Ph[e1] = h1;
       }
     }
     __syncthreads();
-    // ---- phase 2: limited slopes
-    for (int q = tid; q < G::NSL; q += G::NT) {
-      const int sx = q % G::SW - 1, sy = (D == 2) ? q / G::SW - 1 : 0;
-      const int e = G::eidx(sx, sy);
-#pragma unroll
-      for (int b = 0; b < VB; ++b) {
-        const T* Pg = sP + (b * 2 + 0) * G::NEXT;
-        const T* Ph = sP + (b * 2 + 1) * G::NEXT;
-        T* Sb = sS + b * 4 * G::NSL;
-        if constexpr (CV) {
-          // index-direction slopes (unit spacing) -> physical slopes: sigma = J^{-T} (d_i, d_j)
-          const T one = T(1);
-          const T gi = limited(N::sub(Pg[e + 1], Pg[e]), N::sub(Pg[e], Pg[e - 1]), one, limiter);
-          const T hi = limited(N::sub(Ph[e + 1], Ph[e]), N::sub(Ph[e], Ph[e - 1]), one, limiter);
-          const T gj = limited(N::sub(Pg[e + G::EW], Pg[e]), N::sub(Pg[e], Pg[e - G::EW]), one, limiter);
-          const T hj = limited(N::sub(Ph[e + G::EW], Ph[e]), N::sub(Ph[e], Ph[e - G::EW]), one, limiter);
-          const T j00 = sJt[q], j01 = sJt[G::NSL + q], j10 = sJt[2 * G::NSL + q], j11 = sJt[3 * G::NSL + q];
-          Sb[q] = N::fma(j01, gj, N::mul(j00, gi));
-          Sb[G::NSL + q] = N::fma(j01, hj, N::mul(j00, hi));
-          Sb[2 * G::NSL + q] = N::fma(j11, gj, N::mul(j10, gi));
-          Sb[3 * G::NSL + q] = N::fma(j11, hj, N::mul(j10, hi));
-          continue;
-        }
-        Sb[q] = limited(N::sub(Pg[e + 1], Pg[e]), N::sub(Pg[e], Pg[e - 1]), idx_, limiter);
-        Sb[G::NSL + q] = limited(N::sub(Ph[e + 1], Ph[e]), N::sub(Ph[e], Ph[e - 1]), idx_, limiter);
-        if (D == 2) {
-          Sb[2 * G::NSL + q] = limited(N::sub(Pg[e + G::EW], Pg[e]), N::sub(Pg[e], Pg[e - G::EW]), idy_, limiter);
-          Sb[3 * G::NSL + q] = limited(N::sub(Ph[e + G::EW], Ph[e]), N::sub(Ph[e], Ph[e - G::EW]), idy_, limiter);
-        }
-      }
-    }
-    __syncthreads();
-    // ---- phase 3: faces
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int f = tid + q * G::NT;
-      if (f >= G::NF) break;
-      const int meta = sMeta[f];
-      if (!(meta & FM_VALID)) continue;
-      const int role = meta >> 5;
-      if (MODE == 0 && (!(meta & FM_OWNED) || (ML && role == FR_RECV))) continue;
-      const int kind = (meta >> 2) & 7;
-      int dir, li, lj;
-      G::face_pos(f, dir, li, lj);
-      if (ML && MODE == 1 && role == FR_RECV) {
-        // microflux mapped from the face's own space (Eq. native_flux_moment_matching)
-        const int col = sMeta[G::NF + f];
-#pragma unroll
-        for (int b = 0; b < VB; ++b) {
-          const int v = vb0 + b;
-          if (v >= v1) break;
-          sF[(b * 2 + 0) * G::NF + f] = Yi[(long)v * a.nY + col];
-          sF[(b * 2 + 1) * G::NF + f] = Yi[(nv + v) * a.nY + col];
-        }
-        continue;
-      }
-      MP<T> fm;
-      if (MODE == 1) {
-        fm.load(sFP, G::NF, f);
-      }
-      T part[9];
-#pragma unroll
-      for (int p = 0; p < 9; ++p) part[p] = T(0);
-      T fsx = T(0), fsy = T(0);
-      if (MODE == 0) {
-        if (q < 2) { fsx = fshx[q < 2 ? q : 0]; fsy = fshy[q < 2 ? q : 0]; }
-        else { fsx = sAcc[13 * G::NF + f]; fsy = sAcc[14 * G::NF + f]; }
-      }
-#pragma unroll
-      for (int b = 0; b < VB; ++b) {
-        const int v = vb0 + b;
-        if (v >= v1) break;
-        const T* Pg = sP + (b * 2 + 0) * G::NEXT;
-        const T* Ph = sP + (b * 2 + 1) * G::NEXT;
-        const T* Sb = sS + b * 4 * G::NSL;
-        const T xix = xixb[b], xiy = xiyb[b];
-        const T bx_ = N::mul(-xix, s), by_ = N::mul(-xiy, s);
-        T gb, hb, xn;
-        // upwind side only (the mean of both sides when xi.n = 0)
-        if constexpr (CV) {
-          // xi.n as two rounded products and a rounded sum: its sign picks the upwind side,
-          // and a velocity tangential to the face gives the same rounded value wherever
-          // this is evaluated
-          xn = N::add(N::mul(xix, sFG[f]), N::mul(xiy, sFG[G::NF + f]));
-          auto rec = [&](int cx, int cy, T ox, T oy, T& gg, T& hh) {
-            const int e = G::eidx(cx, cy), si = G::sidx(cx, cy);
-            gg = N::fma(N::add(oy, by_), Sb[2 * G::NSL + si], N::fma(N::add(ox, bx_), Sb[si], Pg[e]));
-            hh = N::fma(N::add(oy, by_), Sb[3 * G::NSL + si], N::fma(N::add(ox, bx_), Sb[G::NSL + si], Ph[e]));
-          };
-          const int lx = dir == 0 ? li - 1 : li, ly = dir == 0 ? lj : lj - 1;
-          const T dLx = sFG[3 * G::NF + f], dLy = sFG[4 * G::NF + f];
-          const T dRx = sFG[5 * G::NF + f], dRy = sFG[6 * G::NF + f];
-          if (xn > T(0)) rec(lx, ly, dLx, dLy, gb, hb);
-          else if (xn < T(0)) rec(li, lj, dRx, dRy, gb, hb);
-          else {
-            T g2, h2;
-            rec(lx, ly, dLx, dLy, gb, hb);
-            rec(li, lj, dRx, dRy, g2, h2);
-            gb = N::mul(T(0.5), N::add(gb, g2));
-            hb = N::mul(T(0.5), N::add(hb, h2));
-          }
-        } else if (dir == 0) {
-          xn = xix;
-          auto rec = [&](int cx, T off, T& gg, T& hh) {
-            const int e = G::eidx(cx, lj), si = G::sidx(cx, lj);
-            gg = N::fma(N::add(off, bx_), Sb[si], Pg[e]);
-            hh = N::fma(N::add(off, bx_), Sb[G::NSL + si], Ph[e]);
-            if (D == 2) {
-              gg = N::fma(by_, Sb[2 * G::NSL + si], gg);
-              hh = N::fma(by_, Sb[3 * G::NSL + si], hh);
-            }
-          };
-          if (xix > T(0)) rec(li - 1, hdx, gb, hb);
-          else if (xix < T(0)) rec(li, -hdx, gb, hb);
-          else {
-            T g2, h2;
-            rec(li - 1, hdx, gb, hb);
-            rec(li, -hdx, g2, h2);
-            gb = N::mul(T(0.5), N::add(gb, g2));
-            hb = N::mul(T(0.5), N::add(hb, h2));
-          }
-        } else {
-          xn = xiy;
-          auto rec = [&](int cy, T off, T& gg, T& hh) {
-            const int e = G::eidx(li, cy), si = G::sidx(li, cy);
-            gg = N::fma(N::add(off, by_), Sb[2 * G::NSL + si], N::fma(bx_, Sb[si], Pg[e]));
-            hh = N::fma(N::add(off, by_), Sb[3 * G::NSL + si], N::fma(bx_, Sb[G::NSL + si], Ph[e]));
-          };
-          if (xiy > T(0)) rec(lj - 1, hdy, gb, hb);
-          else if (xiy < T(0)) rec(lj, -hdy, gb, hb);
-          else {
-            T g2, h2;
-            rec(lj - 1, hdy, gb, hb);
-            rec(lj, -hdy, g2, h2);
-            gb = N::mul(T(0.5), N::add(gb, g2));
-            hb = N::mul(T(0.5), N::add(hb, h2));
-          }
-        }
-        if (MODE == 0) {
-          const T wxv = wxb[b], wyv = wyb[b];
-          if (kind == FK_INTERIOR) {
-            const T xp = xix - fsx, yp = (D == 2) ? xiy - fsy : T(0);
-            const T wg = wxv * (wyv * gb);
-            const T e = wxv * (wyv * ((xp * xp + yp * yp) * gb + hb));
-            part[0] += wg;
-            part[1] += wg * xp;
-            part[2] += wg * yp;
-            part[3] += e;
-            part[4] += wg * xp * xp;
-            part[5] += wg * xp * yp;
-            part[6] += wg * yp * yp;
-            part[7] += e * xp;
-            part[8] += e * yp;
-          } else if (kind == FK_WALL_LO || kind == FK_WALL_HI) {
-            // wall: outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) g-bar
-            const T xin = (kind == FK_WALL_LO) ? xn : -xn;
-            if (xin <= T(0)) part[0] += wxv * (wyv * (xin * gb));
-          }
-        } else {
-          T gf, hf;
-          if (kind == FK_INTERIOR) {
-            T gs, hs;
-            model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
-            // Eq. recover_phi with weights summing to one; explicitly rounded so the two tiles
-            // that evaluate a shared face produce the same bits (exact flux telescoping)
-            gf = N::fma(fm.c2, N::sub(gs, gb), gb);
-            hf = N::fma(fm.c2, N::sub(hs, hb), hb);
-          } else {
-            // boundary: the model enters (wall: rho_w = c1 + c2 times the unit-density wall
-            // Maxwellian; freestream: c1 = 1, c2 = 0 and the corrected freestream Maxwellian),
-            // the reconstruction leaves
-            const T xin = fk_low(kind) ? xn : -xn;
-            if (xin > T(0)) {
-              T gs, hs;
-              model_eval<T, D>(fm, xix, xiy, c0, twoK, gs, hs);
-              gf = N::fma(fm.c1, gs, N::mul(fm.c2, gs));
-              hf = N::fma(fm.c1, hs, N::mul(fm.c2, hs));
-            } else {
-              gf = gb;
-              hf = hb;
-            }
-          }
-          // microflux (xi.n) phi on this space (Eq. interface_reduced_fluxes), times |S| on
-          // curvilinear meshes
-          T xs = xn;
-          if constexpr (CV) xs = N::mul(xn, sFG[2 * G::NF + f]);
-          const T Fg = N::mul(xs, gf), Fh = N::mul(xs, hf);
-          sF[(b * 2 + 0) * G::NF + f] = Fg;
-          sF[(b * 2 + 1) * G::NF + f] = Fh;
-          if (ML && role == FR_CROSS && (meta & FM_OWNED)) {
-            const int col = sMeta[G::NF + f];
-            Xo[(long)v * a.nX + col] = Fg;
-            Xo[(nv + v) * a.nX + col] = Fh;
-          }
-        }
-      }
-      if (MODE == 0) {
-        // fold the round's partial sums into the chunk accumulators (compensated for M0..E)
-        if (q < 2) fold_partials<T>(ra[q < 2 ? q : 0], part);
-        else fold_partials_smem<T>(sAcc + f, G::NF, part);
-      }
-    }
-    __syncthreads();
-    if (MODE == 1) {
-      // ---- phase 4: update of the tile's cells of this level (Eq. explicit_update)
-      if (own_active) {
-        const int wI = (D == 2) ? ty * (TX + 1) + tx : tx;
-        const int sI = G::NFXL + ty * TX + tx;
-#pragma unroll
-        for (int b = 0; b < VB; ++b) {
-          const int v = vb0 + b;
-          if (v >= v1) break;
-          const T* Fg = sF + (b * 2 + 0) * G::NF;
-          const T* Fh = sF + (b * 2 + 1) * G::NF;
-          const T xix = xixb[b], xiy = xiyb[b];
-          // phi~+ = phi~ + (4/3) b (phi^S - phi~), then the microflux divergence
-          T gn = g0[b] + m0.c2 * dg0[b] - lamx * (Fg[wI + 1] - Fg[wI]);
-          T hn = h0[b] + m0.c2 * dh0[b] - lamx * (Fh[wI + 1] - Fh[wI]);
-          if (D == 2) {
-            gn -= lamy * (Fg[sI + TX] - Fg[sI]);
-            hn -= lamy * (Fh[sI + TX] - Fh[sI]);
-          }
-          unsigned rb = 0;
-          if constexpr (sizeof(S) == 2) rb = hash32(seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)v));
-          const S sg = Stored<S, T>::enc(gn, rb), sh = Stored<S, T>::enc(hn, rb >> 16);
-          fout[(long)v * ns + col0] = sg;
-          fout[(nv + v) * ns + col0] = sh;
-          const T gq = Stored<S, T>::dec(sg), hq = Stored<S, T>::dec(sh);
-          const T wxv = wxb[b], wyv = wyb[b];
-          const T xp = xix - m0.ux, yp = (D == 2) ? xiy - m0.uy : T(0);
-          const T wg = wxv * (wyv * gq);
-          const T e = wxv * (wyv * ((xp * xp + yp * yp) * gq + hq));
-          c0k.add(wg);
-          cxk.add(wg * xp);
-          cek.add(e);
-          cgxx += wg * xp * xp;
-          cjx += e * xp;
-          if (D == 2) {
-            cyk.add(wg * yp);
-            cgxy += wg * xp * yp;
-            cgyy += wg * yp * yp;
-            cjy += e * yp;
-          }
-        }
-      }
-    }
+    // ---- the faces this thread evaluates
+    const V wxv = sVT[4 * j + 2], wyv = sVT[4 * j + 3];
+    // the pair of a face: phi-bar to the face buffer (read by k_update of the same level; a
+    // padding lane is stored too, so that every lane k_update reads is finite), its moments
+    auto one = [&](const FaceQ& F, T (&part)[9]) {
+      V gb, hb, xn;
+      face_bar(F, Pg, Ph, xix, xiy, gb, hb, xn);
+      T* o = fbo + fbar_at(0, v, F.fid, nvp, nfc);
+      *reinterpret_cast<V*>(o) = gb;
+      *reinterpret_cast<V*>(o + 2 * nvp * nfc) = hb;
+      face_part(F, gb, hb, xn, xix, xiy, wxv, wyv, part);
+    };
+    T part[9];
+    if (FA.meta) { one(FA, part); fold_partials<T>(ra[0], part); }
+    if (D == 2 && FB.meta) { one(FB, part); fold_partials<T>(ra[1], part); }
+    if (FC.meta) { one(FC, part); fold_partials_smem<T>(sAcc + tid, L::NX3, part); }
   }
 
   // ---- write the chunk's partial moments
-  if (MODE == 0) {
+  if (FA.meta) write_partials<T, D>(ra[0], a.part + (long)chunk * NMOM * k.nface + FA.fid, k.nface);
+  if (D == 2 && FB.meta) write_partials<T, D>(ra[1], a.part + (long)chunk * NMOM * k.nface + FB.fid, k.nface);
+  if (FC.meta) write_partials_smem<T, D>(sAcc + tid, L::NX3, a.part + (long)chunk * NMOM * k.nface + FC.fid, k.nface);
+}
+
+// One face of k_update as a thread holds it: metadata, the model parameters of an evaluated
+// face, and on curvilinear meshes its unit normal and area.
+template <class T> struct UFace {
+  int meta = 0;   // face_meta word, 0 if the thread has no such face
+  int kind = 0, role = FR_NONE;
+  long fid = 0;   // global face id (face buffer column)
+  long col = 0;   // column in X (FR_CROSS) or Y (FR_RECV)
+  MP<T> m;
+  T nx = T(0), ny = T(0), area = T(1);
+};
+
+// Microflux (xi.n) phi (Eq. interface_reduced_fluxes, times |S| on curvilinear meshes) of an
+// evaluated face for a velocity pair from its stored phi-bar (gb, hb): Eq. recover_phi on
+// interior faces; on boundary faces the model enters (wall: rho_w = c1 + c2 times the
+// unit-density wall Maxwellian; freestream: c1 = 1, c2 = 0 and the corrected freestream
+// Maxwellian) and the reconstruction leaves, lane by lane.
+template <class T, int D, bool CV>
+__device__ __forceinline__ void face_flux2(const UFace<T>& F, int dir, V2<T> xix, V2<T> xiy, V2<T> gb, V2<T> hb,
+                                           T c0, T twoK, V2<T>& Fg, V2<T>& Fh) {
+  using P = Pk<T>;
+  V2<T> xn;
+  // xi.n as two rounded products and a rounded sum (curvilinear): the same value in every
+  // kernel that evaluates this face
+  if constexpr (CV) xn = P::add(P::mul(xix, P::splat(F.nx)), P::mul(xiy, P::splat(F.ny)));
+  else xn = (dir == 0) ? xix : xiy;
+  V2<T> gs, hs, gf, hf;
+  model_eval2<T, D>(F.m, xix, xiy, c0, twoK, gs, hs);
+  if (F.kind == FK_INTERIOR) {
+    // weights summing to one, explicitly rounded: the two tiles that evaluate a shared face
+    // produce the same bits (exact flux telescoping)
+    gf = P::fma(P::splat(F.m.c2), P::sub(gs, gb), gb);
+    hf = P::fma(P::splat(F.m.c2), P::sub(hs, hb), hb);
+  } else {
+    const V2<T> xin = fk_low(F.kind) ? xn : P::mk(-xn.x, -xn.y);
+    const V2<T> gw = P::fma(P::splat(F.m.c1), gs, P::mul(P::splat(F.m.c2), gs));
+    const V2<T> hw = P::fma(P::splat(F.m.c1), hs, P::mul(P::splat(F.m.c2), hs));
+    gf.x = xin.x > T(0) ? gw.x : gb.x;
+    gf.y = xin.y > T(0) ? gw.y : gb.y;
+    hf.x = xin.x > T(0) ? hw.x : hb.x;
+    hf.y = xin.y > T(0) ? hw.y : hb.y;
+  }
+  V2<T> xs = xn;
+  if constexpr (CV) xs = P::mul(xn, P::splat(F.area));
+  Fg = P::mul(xs, gf);
+  Fh = P::mul(xs, hf);
+}
+
+// Eq. explicit_update on a tile: phi~^{n+1} = phi~+ - dt/|V| sum_faces (xi.n) phi |S|, with the
+// face phi from the face buffer written by k_faces, then the cell moments of the stored values
+// over the chunk.  One velocity pair per round.  Thread (tx, ty) holds its cell and the cell's
+// low-side faces (A: x-face tx, B: y-face ty in 2-D), whose microfluxes go through shared
+// memory (double-buffered: one barrier per round).  The tile's high-side faces C (the column
+// li = TX and the row lj = TY) are evaluated for a sub-chunk of SC pairs at a time by every
+// thread (face tid % NX3, pairs tid / NX3 + k NT / NX3), so the work per round is the same in
+// every warp.  Requires k.vpc <= VPC.
+template <class S, class T, int D, int TX, int TY, int VPC, bool ML, bool CV>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_update(const TileArgs a) {
+  using G = TileGeom<TX, TY, D>;
+  using L = UpdSmem<T, TX, TY, D, VPC>;
+  using V = V2<T>;
+  using P = Pk<T>;
+  static_assert(!CV || D == 2, "curvilinear meshes are two-dimensional");
+  static_assert(L::NX3 <= G::NT && G::NT % L::NX3 == 0, "high-side faces must divide the threads");
+  constexpr int NT = G::NT, NX3 = L::NX3, SC = L::SC;
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* sF = reinterpret_cast<V*>(smem + L::F);       // [2][2][NF] by pair
+  V* sC = reinterpret_cast<V*>(smem + L::C);       // [2][2][SC][NX3] by pair
+  V* sVT = reinterpret_cast<V*>(smem + L::VT);
+  T* sXP = reinterpret_cast<T*>(smem + L::XP);
+  long* sXI = reinterpret_cast<long*>(smem + L::XI);
+
+  const StepConst& k = a.k;
+  const S* __restrict__ fin = reinterpret_cast<const S*>(a.f_in);
+  S* __restrict__ fout = reinterpret_cast<S*>(a.f_out);
+  const T* __restrict__ cp = reinterpret_cast<const T*>(a.cparam);
+  const T* __restrict__ fp = reinterpret_cast<const T*>(a.fparam);
+  const T* __restrict__ vt = reinterpret_cast<const T*>(a.vt);
+  const T* __restrict__ fbi = reinterpret_cast<const T*>(a.fbar);
+  const T* __restrict__ fg = reinterpret_cast<const T*>(a.fgeo);
+  const T* __restrict__ cg = reinterpret_cast<const T*>(a.cgeo);
+  T* __restrict__ Xo = reinterpret_cast<T*>(a.X);
+  const T* __restrict__ Yi = reinterpret_cast<const T*>(a.Y);
+  const long ns = a.nslot;
+  const long nv = k.nv;
+  const long nvp = (k.nv + 1) / 2;
+  const long nfc = k.nface;
+
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = (D == 2) ? tid / TX : 0;
+  unsigned seed = 0;
+  if constexpr (sizeof(S) == 2) seed = hash32(*a.step * 0x632be5abu + a.salt);
+  const int tile = a.tiles[blockIdx.x];
+  const int bx = tile % a.ntx, by = tile / a.ntx;
+  const int x0 = bx * TX, y0 = by * TY;
+  const int chunk = blockIdx.y;
+  const int v0 = chunk * k.vpc;               // even: k.vpc is even
+  const int v1 = min(k.nv, v0 + k.vpc);
+  const int npr = (v1 - v0 + 1) / 2;
+
+  // the chunk's velocity table by pairs, padded with zeros to whole sub-chunks
+  for (int j = tid; j < L::NPT; j += NT) {
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int f = tid + q * G::NT;
-      if (f >= G::NF) break;
-      const int meta = sMeta[f];
-      const int role = meta >> 5;
-      if (!(meta & FM_VALID) || !(meta & FM_OWNED) || role == FR_RECV) continue;
-      const int fid = sMeta[G::NF + f];
-      double* P = a.part + (long)chunk * NMOM * k.nface + fid;
-      if (q < 2) write_partials<T, D>(ra[q < 2 ? q : 0], P, k.nface);
-      else write_partials_smem<T, D>(sAcc + f, G::NF, P, k.nface);
+    for (int r = 0; r < 4; ++r) {
+      const int v = v0 + 2 * j;
+      const T e0 = (v < v1 && !(r == 1 && D == 1)) ? vt[r * nv + v] : T(0);
+      const T e1 = (v + 1 < v1 && !(r == 1 && D == 1)) ? vt[r * nv + v + 1] : T(0);
+      sVT[4 * j + r] = P::mk(e0, e1);
     }
-  } else if (own_active) {
-    double* P = a.part + (long)chunk * NMOM * ns + col0;
-    P[MO_0 * ns] = c0k.val();
-    P[MO_X * ns] = cxk.val();
-    P[MO_Y * ns] = (D == 2) ? cyk.val() : 0.0;
-    P[MO_E * ns] = cek.val();
-    P[MO_GXX * ns] = (double)cgxx;
-    P[MO_GXY * ns] = (double)cgxy;
-    P[MO_GYY * ns] = (double)cgyy;
-    P[MO_JX * ns] = (double)cjx;
-    P[MO_JY * ns] = (double)cjy;
+  }
+
+  // ---- own cell
+  const int gx = x0 + tx, gy = y0 + ty;
+  bool own_active = gx < k.nx && (D == 1 || gy < k.ny);
+  long col0 = 0;
+  if (own_active) {
+    const int c = ((D == 2) ? gy : 0) * k.nx + gx;
+    if (!ML) col0 = c;
+    else if (a.lvl_of[c] == a.level) col0 = a.slot_of[c];
+    else own_active = false;
+  }
+  MP<T> m0;
+  if (own_active) m0.load(cp, ns, col0);
+  else m0.zero();
+  T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
+  if constexpr (CV) {
+    if (own_active) lamx = lamy = cg[4L * k.ncell + ((D == 2) ? gy : 0) * k.nx + gx];   // dt / |V|
+  }
+  // loads of the own cell: base pointer and velocity stride (0: a dummy element, never stored)
+  const S* pO = fin + (own_active ? col0 : 0);
+  const long so = own_active ? ns : 0;
+
+  auto setup = [&](int f, UFace<T>& F) {
+    int fid;
+    F.meta = face_meta<TX, TY, D, ML>(a, x0, y0, f, fid);
+    F.fid = fid;
+    F.kind = (F.meta >> 2) & 7;
+    F.role = F.meta >> 5;
+    F.col = 0;
+    F.m.zero();
+    if (!(F.meta & FM_VALID)) { F.meta = 0; F.role = FR_NONE; return; }
+    if (F.role == FR_CROSS || F.role == FR_RECV) F.col = a.fslot[fid];
+    if (F.role == FR_NORMAL || F.role == FR_CROSS) F.m.load(fp, nfc, fid);
+    if constexpr (CV) {
+      F.nx = fg[fid];
+      F.ny = fg[nfc + fid];
+      F.area = fg[2 * nfc + fid];
+    }
+  };
+  // a face's loaded pair at velocities (v, v+1): face phi-bar (evaluated faces), mapped
+  // microflux (received faces) or zeros
+  auto ldface = [&](int role, long fid, long col, int v, V& g, V& h) {
+    if (role == FR_NORMAL || role == FR_CROSS) {
+      const T* q = fbi + fbar_at(0, v, fid, nvp, nfc);
+      g = *reinterpret_cast<const V*>(q);
+      h = *reinterpret_cast<const V*>(q + 2 * nvp * nfc);
+    } else if (ML && role == FR_RECV) {
+      const long vb = min(v + 1, v1 - 1);
+      g = P::mk(Yi[(long)v * a.nY + col], Yi[vb * a.nY + col]);
+      h = P::mk(Yi[(nv + v) * a.nY + col], Yi[(nv + vb) * a.nY + col]);
+    } else {
+      g = h = P::splat(T(0));
+    }
+  };
+  // the cross-level microflux of an exported face (the lanes that exist)
+  auto export_x = [&](long col, int v, V Fg, V Fh) {
+    Xo[(long)v * a.nX + col] = Fg.x;
+    Xo[(nv + v) * a.nX + col] = Fh.x;
+    if (v + 1 < v1) {
+      Xo[(long)(v + 1) * a.nX + col] = Fg.y;
+      Xo[(nv + v + 1) * a.nX + col] = Fh.y;
+    }
+  };
+
+  // ---- faces C: parameters and ids in shared memory
+  if (tid < NX3) {
+    const int fC = (D == 1) ? TX : (tid < TY ? tid * (TX + 1) + TX : G::NFXL + TY * TX + (tid - TY));
+    UFace<T> FC;
+    setup(fC, FC);
+    const T pv[16] = {FC.m.ux, FC.m.uy, FC.m.lnh, FC.m.inv2RT, FC.m.kqx, FC.m.kqy, FC.m.RT, FC.m.b0,
+                      FC.m.b1, FC.m.b2, FC.m.b3, FC.m.c1, FC.m.c2, FC.nx, FC.ny, FC.area};
+#pragma unroll
+    for (int p = 0; p < 16; ++p) sXP[p * NX3 + tid] = pv[p];
+    sXI[tid] = FC.meta;
+    sXI[NX3 + tid] = FC.kind;
+    sXI[2 * NX3 + tid] = FC.fid;
+    sXI[3 * NX3 + tid] = FC.col;
+  }
+  // ---- faces A and B in registers
+  const int fA = ty * (TX + 1) + tx;
+  const int fB = G::NFXL + ty * TX + tx;
+  UFace<T> FA, FB;
+  setup(fA, FA);
+  if (D == 2) setup(fB, FB);
+  else FB.meta = 0, FB.role = FR_NONE;
+  const bool evA = FA.role == FR_NORMAL || FA.role == FR_CROSS;
+  const bool evB = D == 2 && (FB.role == FR_NORMAL || FB.role == FR_CROSS);
+  const bool xA = ML && FA.role == FR_CROSS && (FA.meta & FM_OWNED);
+  const bool xB = ML && D == 2 && FB.role == FR_CROSS && (FB.meta & FM_OWNED);
+  // where the fluxes of the own cell's high-side faces are: a face A / B of a neighbour in
+  // the tile, or a face C (index ty in the column, TY + tx in the row)
+  const bool eInTile = tx < TX - 1, nInTile = ty < TY - 1;
+  const int cE = (D == 1) ? 0 : ty, cN = TY + tx;
+
+  // moments of the updated cell (the next step's partials), in the cell's frame
+  KSum<T> c0k, cxk, cyk, cek;
+  c0k.zero(); cxk.zero(); cyk.zero(); cek.zero();
+  T cgxx = T(0), cgxy = T(0), cgyy = T(0), cjx = T(0), cjy = T(0);
+  const T c0 = T(k.c0), twoK = T(k.twoK);
+  __syncthreads();   // velocity table and faces C in place
+
+  // the faces C of this thread in the pre-pass: face tid % NX3, pairs tid / NX3 + k NT / NX3
+  const int qc = tid % NX3, jc0 = tid / NX3;
+  const int dirC = (D == 1 || qc < TY) ? 0 : 1;
+  int cbuf = 0, buf = 0;
+  for (int jb = 0; jb < npr; jb += SC, cbuf ^= 1) {
+    // ---- pre-pass: the microfluxes of the faces C over the sub-chunk
+    {
+      const long metaC = sXI[qc];
+      const int roleC = (int)(metaC >> 5);
+      const bool evC = roleC == FR_NORMAL || roleC == FR_CROSS;
+      const bool xC = ML && roleC == FR_CROSS && (metaC & FM_OWNED);
+      const long fidC = sXI[2 * NX3 + qc], colC = sXI[3 * NX3 + qc];
+      UFace<T> FC;
+      const T* X3p = sXP + qc;
+      FC.kind = (int)sXI[NX3 + qc];
+      FC.m.ux = X3p[0]; FC.m.uy = X3p[NX3]; FC.m.lnh = X3p[2 * NX3]; FC.m.inv2RT = X3p[3 * NX3];
+      FC.m.kqx = X3p[4 * NX3]; FC.m.kqy = X3p[5 * NX3]; FC.m.RT = X3p[6 * NX3]; FC.m.b0 = X3p[7 * NX3];
+      FC.m.b1 = X3p[8 * NX3]; FC.m.b2 = X3p[9 * NX3]; FC.m.b3 = X3p[10 * NX3]; FC.m.c1 = X3p[11 * NX3];
+      FC.m.c2 = X3p[12 * NX3]; FC.nx = X3p[13 * NX3]; FC.ny = X3p[14 * NX3]; FC.area = X3p[15 * NX3];
+      V* Cg = sC + (cbuf * 2 + 0) * SC * NX3;
+      V* Ch = sC + (cbuf * 2 + 1) * SC * NX3;
+      for (int jj = jc0; jj < SC; jj += NT / NX3) {
+        const int jp = min(jb + jj, npr - 1);
+        const int v = v0 + 2 * jp;
+        V gl, hl;
+        ldface(roleC, fidC, colC, v, gl, hl);
+        V Fg = gl, Fh = hl;
+        if (evC) face_flux2<T, D, CV>(FC, dirC, sVT[4 * (jb + jj)], sVT[4 * (jb + jj) + 1], gl, hl, c0, twoK, Fg, Fh);
+        Cg[jj * NX3 + qc] = Fg;
+        Ch[jj * NX3 + qc] = Fh;
+        if (xC && jb + jj < npr) export_x(colC, v, Fg, Fh);
+      }
+    }
+    const int je = min(jb + SC, npr);
+    for (int j = jb; j < je; ++j, buf ^= 1) {
+      const int v = v0 + 2 * j;
+      const long vb = min(v + 1, v1 - 1);
+      const V g0 = P::mk(ldf<S, T>(pO + (long)v * so), ldf<S, T>(pO + vb * so));
+      const V h0 = P::mk(ldf<S, T>(pO + (nv + v) * so), ldf<S, T>(pO + (nv + vb) * so));
+      V ga, ha, gbb, hbb;
+      ldface(FA.role, FA.fid, FA.col, v, ga, ha);
+      if (D == 2) ldface(FB.role, FB.fid, FB.col, v, gbb, hbb);
+      const V xix = sVT[4 * j], xiy = sVT[4 * j + 1];
+      V* Fg = sF + (buf * 2 + 0) * G::NF;
+      V* Fh = sF + (buf * 2 + 1) * G::NF;
+      V FAg = ga, FAh = ha;
+      if (evA) face_flux2<T, D, CV>(FA, 0, xix, xiy, ga, ha, c0, twoK, FAg, FAh);
+      Fg[fA] = FAg;
+      Fh[fA] = FAh;
+      if (xA) export_x(FA.col, v, FAg, FAh);
+      if (D == 2) {
+        V FBg = gbb, FBh = hbb;
+        if (evB) face_flux2<T, D, CV>(FB, 1, xix, xiy, gbb, hbb, c0, twoK, FBg, FBh);
+        Fg[fB] = FBg;
+        Fh[fB] = FBh;
+        if (xB) export_x(FB.col, v, FBg, FBh);
+      }
+      // phi~+ = phi~ + (4/3) b (phi^S - phi~)
+      V gs, hs;
+      model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
+      const V gp = P::fma(P::splat(m0.c2), P::sub(gs, g0), g0);
+      const V hp = P::fma(P::splat(m0.c2), P::sub(hs, h0), h0);
+      __syncthreads();
+      // phi~+ minus the microflux divergence
+      const V* Cg = sC + (cbuf * 2 + 0) * SC * NX3 + (j - jb) * NX3;
+      const V* Ch = sC + (cbuf * 2 + 1) * SC * NX3 + (j - jb) * NX3;
+      const V FEg = eInTile ? Fg[fA + 1] : Cg[cE], FEh = eInTile ? Fh[fA + 1] : Ch[cE];
+      V gn = P::fma(P::splat(-lamx), P::sub(FEg, Fg[fA]), gp);
+      V hn = P::fma(P::splat(-lamx), P::sub(FEh, Fh[fA]), hp);
+      if (D == 2) {
+        const V FNg = nInTile ? Fg[fB + TX] : Cg[cN], FNh = nInTile ? Fh[fB + TX] : Ch[cN];
+        gn = P::fma(P::splat(-lamy), P::sub(FNg, Fg[fB]), gn);
+        hn = P::fma(P::splat(-lamy), P::sub(FNh, Fh[fB]), hn);
+      }
+      unsigned rb0 = 0, rb1 = 0;
+      if constexpr (sizeof(S) == 2) {
+        rb0 = hash32(seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)v));
+        rb1 = hash32(seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)(v + 1)));
+      }
+      const S sg0 = Stored<S, T>::enc(gn.x, rb0), sh0 = Stored<S, T>::enc(hn.x, rb0 >> 16);
+      const S sg1 = Stored<S, T>::enc(gn.y, rb1), sh1 = Stored<S, T>::enc(hn.y, rb1 >> 16);
+      if (own_active) {
+        fout[(long)v * ns + col0] = sg0;
+        fout[(nv + v) * ns + col0] = sh0;
+        if (v + 1 < v1) {
+          fout[(long)(v + 1) * ns + col0] = sg1;
+          fout[(nv + v + 1) * ns + col0] = sh1;
+        }
+      }
+      const V gq = P::mk(Stored<S, T>::dec(sg0), Stored<S, T>::dec(sg1));
+      const V hq = P::mk(Stored<S, T>::dec(sh0), Stored<S, T>::dec(sh1));
+      const V wxv = sVT[4 * j + 2], wyv = sVT[4 * j + 3];
+      const V xp = P::sub(xix, P::splat(m0.ux));
+      const V yp = (D == 2) ? P::sub(xiy, P::splat(m0.uy)) : P::splat(T(0));
+      const V wg = P::mul(wxv, P::mul(wyv, gq));
+      const V e = P::mul(wxv, P::mul(wyv, P::fma(P::fma(yp, yp, P::mul(xp, xp)), gq, hq)));
+      const V q1 = P::mul(wg, xp), q7 = P::mul(e, xp);
+      c0k.add(wg.x); c0k.add(wg.y);
+      cxk.add(q1.x); cxk.add(q1.y);
+      cek.add(e.x); cek.add(e.y);
+      const V q4 = P::mul(q1, xp);
+      cgxx += q4.x + q4.y;
+      cjx += q7.x + q7.y;
+      if (D == 2) {
+        const V q2 = P::mul(wg, yp), q5 = P::mul(q1, yp), q6 = P::mul(q2, yp), q8 = P::mul(e, yp);
+        cyk.add(q2.x); cyk.add(q2.y);
+        cgxy += q5.x + q5.y;
+        cgyy += q6.x + q6.y;
+        cjy += q8.x + q8.y;
+      }
+    }
+  }
+
+  // ---- write the chunk's partial moments of the own cell
+  if (own_active) {
+    double* Pp = a.part + (long)chunk * NMOM * ns + col0;
+    Pp[MO_0 * ns] = c0k.val();
+    Pp[MO_X * ns] = cxk.val();
+    Pp[MO_Y * ns] = (D == 2) ? cyk.val() : 0.0;
+    Pp[MO_E * ns] = cek.val();
+    Pp[MO_GXX * ns] = (double)cgxx;
+    Pp[MO_GXY * ns] = (double)cgxy;
+    Pp[MO_GYY * ns] = (double)cgyy;
+    Pp[MO_JX * ns] = (double)cjx;
+    Pp[MO_JY * ns] = (double)cjy;
   }
 }
 

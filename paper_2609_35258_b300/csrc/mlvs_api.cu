@@ -13,10 +13,11 @@
 //      k_fin_sums / k_fin_post on spaces that are not tensor products): W, tau, q, model
 //      parameters + compatibility correction
 //   2. k_map_multi (SRC_BARP): the ghosts of every (source level, level) route in one launch
-//   3. k_tile MODE 0 per level: face phi-bar, face moment partials
+//   3. k_faces per level: face phi-bar (stored to the level's face buffer), face moment partials
 //   4. finalisation of the faces each level evaluates: Eq. W_from_bar, Eq. recover_phi
 //      weights, wall densities
-//   5. per level, finest space first: k_tile MODE 1 (microfluxes, Eq. explicit_update), then
+//   5. per level, finest space first: k_update (microfluxes from the face buffer,
+//      Eq. explicit_update), then
 //      k_map_multi (SRC_FLUX) of its cross-level fluxes to the levels that receive them
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
@@ -105,6 +106,7 @@ struct LevelRt {
   std::vector<int> cells;    // global cell id of every slot
   StepConst k;
   DevBuf f[2], prm[2], fprm, cpart, fpart, ids, frole, fslot, ghost_of, ghost, X, Y, tiles;
+  DevBuf fbar;               // [2][nv][nface] face phi-bar of the faces the level evaluates
   DevBuf fscr, fneed;        // split finalisation scratch (spaces that are not tensor products)
   DevBuf wden;               // curvilinear walls: [nface] wall-Maxwellian normalisation
   DevBuf msum;               // [NMOM][max(cells, faces)] chunk sums for the finalisation
@@ -251,6 +253,7 @@ unsigned hash_host(unsigned x) {
 }
 
 constexpr int kTX2 = 16, kTY2 = 16, kTX1 = 128;
+constexpr int kMaxVpc = kVpcMax;   // largest velocity chunk of a tile launch
 int tile_w(int D) { return D == 2 ? kTX2 : kTX1; }
 int tile_h(int D) { return D == 2 ? kTY2 : 1; }
 
@@ -377,11 +380,10 @@ namespace {
 template <class S, class T, int D> struct Runner {
   static constexpr int TX = (D == 2) ? kTX2 : kTX1;
   static constexpr int TY = (D == 2) ? kTY2 : 1;
-  static constexpr int VB = 2;   // velocities per barrier round
-  static constexpr size_t SM0 = TileSmem<T, TX, TY, D, VB, 0>::BYTES;
-  static constexpr size_t SM1 = TileSmem<T, TX, TY, D, VB, 1>::BYTES;
-  static constexpr size_t SM0C = TileSmem<T, TX, TY, D, VB, 0, true>::BYTES;
-  static constexpr size_t SM1C = TileSmem<T, TX, TY, D, VB, 1, true>::BYTES;
+  static constexpr int VPC = kMaxVpc;
+  static constexpr size_t SM0 = TileSmem<T, TX, TY, D>::BYTES;
+  static constexpr size_t SM0C = TileSmem<T, TX, TY, D, true>::BYTES;
+  static constexpr size_t SMU = UpdSmem<T, TX, TY, D, VPC>::BYTES;
   static constexpr int FIN_BLOCK = 64;
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
   // tensor-product spaces: one kernel (one-axis sums per thread); others: the split path
@@ -409,44 +411,53 @@ template <class S, class T, int D> struct Runner {
   }
 
   static cudaError_t set_smem_limits() {
-    const void* fn[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false, false>,
-                         (const void*)k_tile<S, T, D, TX, TY, VB, 0, true, false>,
-                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, false, false>,
-                         (const void*)k_tile<S, T, D, TX, TY, VB, 1, true, false>};
+    const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false, false>,
+                         (const void*)k_faces<S, T, D, TX, TY, true, false>,
+                         (const void*)k_update<S, T, D, TX, TY, VPC, false, false>,
+                         (const void*)k_update<S, T, D, TX, TY, VPC, true, false>};
     for (int i = 0; i < 4; ++i) {
       cudaError_t e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(i < 2 ? SM0 : SM1));
+                                           (int)(i < 2 ? SM0 : SMU));
       if (e != cudaSuccess) return e;
     }
     if constexpr (D == 2) {
-      const void* fc[4] = {(const void*)k_tile<S, T, D, TX, TY, VB, 0, false, true>,
-                           (const void*)k_tile<S, T, D, TX, TY, VB, 0, true, true>,
-                           (const void*)k_tile<S, T, D, TX, TY, VB, 1, false, true>,
-                           (const void*)k_tile<S, T, D, TX, TY, VB, 1, true, true>};
+      const void* fc[4] = {(const void*)k_faces<S, T, D, TX, TY, false, true>,
+                           (const void*)k_faces<S, T, D, TX, TY, true, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, false, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, true, true>};
       for (int i = 0; i < 4; ++i) {
         cudaError_t e = cudaFuncSetAttribute(fc[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)(i < 2 ? SM0C : SM1C));
+                                             (int)(i < 2 ? SM0C : SMU));
         if (e != cudaSuccess) return e;
       }
     }
     return cudaSuccess;
   }
 
-  // one tile pass: with or without level tables, Cartesian or curvilinear
+  // one tile pass (MODE 0: k_faces, MODE 1: k_update): with or without level tables,
+  // Cartesian or curvilinear
   template <int MODE>
   static void launch_tile(mlvs_handle* h, const LevelRt& L, dim3 grid, const TileArgs& t, int limiter) {
     const bool one = single(h, L);
     if constexpr (D == 2) {
       if (h->curvi) {
-        constexpr size_t sm = MODE == 0 ? SM0C : SM1C;
-        if (one) k_tile<S, T, D, TX, TY, VB, MODE, false, true><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
-        else k_tile<S, T, D, TX, TY, VB, MODE, true, true><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
+        if constexpr (MODE == 0) {
+          if (one) k_faces<S, T, D, TX, TY, false, true><<<grid, TX * TY, SM0C, h->stream>>>(t, limiter);
+          else k_faces<S, T, D, TX, TY, true, true><<<grid, TX * TY, SM0C, h->stream>>>(t, limiter);
+        } else {
+          if (one) k_update<S, T, D, TX, TY, VPC, false, true><<<grid, TX * TY, SMU, h->stream>>>(t);
+          else k_update<S, T, D, TX, TY, VPC, true, true><<<grid, TX * TY, SMU, h->stream>>>(t);
+        }
         return;
       }
     }
-    constexpr size_t sm = MODE == 0 ? SM0 : SM1;
-    if (one) k_tile<S, T, D, TX, TY, VB, MODE, false, false><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
-    else k_tile<S, T, D, TX, TY, VB, MODE, true, false><<<grid, TX * TY, sm, h->stream>>>(t, limiter);
+    if constexpr (MODE == 0) {
+      if (one) k_faces<S, T, D, TX, TY, false, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+      else k_faces<S, T, D, TX, TY, true, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+    } else {
+      if (one) k_update<S, T, D, TX, TY, VPC, false, false><<<grid, TX * TY, SMU, h->stream>>>(t);
+      else k_update<S, T, D, TX, TY, VPC, true, false><<<grid, TX * TY, SMU, h->stream>>>(t);
+    }
   }
 
   // a level that holds every cell runs the tile kernels without level tables
@@ -521,6 +532,7 @@ template <class S, class T, int D> struct Runner {
     t.nX = L.nX;
     t.Y = L.Y.p;
     t.nY = L.nY;
+    t.fbar = L.fbar.p;
     t.ucell = I.ucell.p;
     t.cgeo = h->curvi ? h->cgeo_d.p : nullptr;
     t.fgeo = h->curvi ? h->fgeo_d.p : nullptr;
@@ -1045,7 +1057,8 @@ int choose_vpc(int tile_ctas, int nv, int target) {
   int nchunk = std::max(1, (target + std::max(tile_ctas, 1) - 1) / std::max(tile_ctas, 1));
   nchunk = std::min(nchunk, nv);
   int vpc = (nv + nchunk - 1) / nchunk;
-  return std::max(1, std::min(vpc, 384));
+  vpc = (vpc + 1) & ~1;   // even: the tile kernels take the velocities in pairs
+  return std::max(2, std::min(vpc, kMaxVpc));
 }
 
 }  // namespace
@@ -1263,7 +1276,8 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
         L.fpart.alloc((size_t)k.nchunk * NMOM * nface * 8) != cudaSuccess ||
         L.ghost.alloc(2ull * k.nv * L.nghost * h->tsize) != cudaSuccess ||
         L.X.alloc(2ull * k.nv * L.nX * h->tsize) != cudaSuccess ||
-        L.Y.alloc(2ull * k.nv * L.nY * h->tsize) != cudaSuccess)
+        L.Y.alloc(2ull * k.nv * L.nY * h->tsize) != cudaSuccess ||
+        L.fbar.alloc(L.ntiles > 0 ? 2ull * ((k.nv + 1) / 2) * 2 * nface * h->tsize : 0) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     CK(cudaMemsetAsync(L.fprm.p, 0, L.fprm.n, h->stream));
     if (h->curvi) CK(ops_for(h->cfg.storage, D).wall_table(h, L));

@@ -128,6 +128,9 @@ template <class T> struct MP {
     b2 = P[P_B2 * n + i];     b3 = P[P_B3 * n + i];   c1 = P[P_C1 * n + i];
     c2 = P[P_C2 * n + i];
   }
+  __device__ __forceinline__ void zero() {
+    ux = uy = lnh = inv2RT = kqx = kqy = RT = b0 = b1 = b2 = b3 = c1 = c2 = T(0);
+  }
 };
 
 // Maxwellian of a point as a product of one factor per axis (D = 2) or one factor (D = 1):
@@ -161,6 +164,61 @@ __device__ __forceinline__ void model_eval(const MP<T>& p, T xix, T xiy, T c0, T
   const T corr = N::fma(p.b3, cc, N::fma(p.b2, cy, N::fma(p.b1, cx, p.b0)));
   g = N::fma(gs, corr, gs);
   h = N::fma(hs, corr, hs);
+}
+
+// A pair of lanes: two velocities processed together by one thread.  Every lane operation is
+// the explicitly rounded operation of Num<T> on that lane (a - b as a + (-b), the same IEEE
+// result), so a pair gives the same bits as two scalar evaluations.  FP32 pairs use the
+// packed two-lane FP32 instructions of sm_100 and later (one instruction per lane pair).
+template <class T> struct Pk;
+template <> struct Pk<float> {
+  using V = float2;
+  static __device__ __forceinline__ V mk(float a, float b) { return make_float2(a, b); }
+  static __device__ __forceinline__ V splat(float a) { return make_float2(a, a); }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd2_rn(a, b); }
+  static __device__ __forceinline__ V sub(V a, V b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+  static __device__ __forceinline__ V mul(V a, V b) { return __fmul2_rn(a, b); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) { return __ffma2_rn(a, b, c); }
+  static __device__ __forceinline__ float ex(float a) { return __expf(a); }
+};
+template <> struct Pk<double> {
+  using V = double2;
+  static __device__ __forceinline__ V mk(double a, double b) { return make_double2(a, b); }
+  static __device__ __forceinline__ V splat(double a) { return make_double2(a, a); }
+  static __device__ __forceinline__ V add(V a, V b) { return make_double2(__dadd_rn(a.x, b.x), __dadd_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V sub(V a, V b) { return make_double2(__dsub_rn(a.x, b.x), __dsub_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V mul(V a, V b) { return make_double2(__dmul_rn(a.x, b.x), __dmul_rn(a.y, b.y)); }
+  static __device__ __forceinline__ V fma(V a, V b, V c) {
+    return make_double2(__fma_rn(a.x, b.x, c.x), __fma_rn(a.y, b.y, c.y));
+  }
+  static __device__ __forceinline__ double ex(double a) { return exp(a); }
+};
+template <class T> using V2 = typename Pk<T>::V;
+
+// model_eval on a pair of velocities: the same operations, lane by lane.
+template <class T, int D>
+__device__ __forceinline__ void model_eval2(const MP<T>& p, V2<T> xix, V2<T> xiy, T c0, T twoK, V2<T>& g,
+                                            V2<T>& h) {
+  using P = Pk<T>;
+  using N = Num<T>;
+  const V2<T> cx = P::sub(xix, P::splat(p.ux));
+  const V2<T> cy = (D == 2) ? P::sub(xiy, P::splat(p.uy)) : P::splat(T(0));
+  const V2<T> cx2 = P::mul(cx, cx);
+  const V2<T> ax = P::fma(cx2, P::splat(-p.inv2RT), P::splat(p.lnh));
+  V2<T> geq = P::mk(P::ex(ax.x), P::ex(ax.y));
+  if (D == 2) {
+    const V2<T> ay = P::fma(P::mul(cy, cy), P::splat(-p.inv2RT), P::splat(p.lnh));
+    geq = P::mul(geq, P::mk(P::ex(ay.x), P::ex(ay.y)));
+  }
+  const V2<T> cc = P::fma(cy, cy, cx2);
+  const V2<T> cq = P::fma(P::splat(p.kqy), cy, P::mul(P::splat(p.kqx), cx));
+  const V2<T> t = P::mul(P::splat(N::mul(T(2), p.inv2RT)), cc);
+  const V2<T> gs = P::mul(geq, P::fma(cq, P::sub(t, P::splat(T(D + 2))), P::splat(T(1))));
+  const V2<T> hs = P::mul(P::mul(P::splat(p.RT), geq),
+                          P::fma(cq, P::fma(P::sub(t, P::splat(T(D))), P::splat(c0), P::splat(-twoK)), P::splat(c0)));
+  const V2<T> corr = P::fma(P::splat(p.b3), cc, P::fma(P::splat(p.b2), cy, P::fma(P::splat(p.b1), cx, P::splat(p.b0))));
+  g = P::fma(gs, corr, gs);
+  h = P::fma(hs, corr, hs);
 }
 
 // Compensated (Kahan) accumulation for sums that must keep FP64-level accuracy in FP32.

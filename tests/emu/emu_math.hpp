@@ -45,3 +45,9 @@ template <class X> static inline X __shfl_xor_sync(unsigned, X v, int, int = 32)
   std::abort();
   return v;
 }
+// packed two-lane FP32 (sm_100 and later): each lane an IEEE operation, as on the GPU
+static inline float2 __fadd2_rn(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
+static inline float2 __fmul2_rn(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
+static inline float2 __ffma2_rn(float2 a, float2 b, float2 c) {
+  return make_float2(std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y));
+}

@@ -1,6 +1,7 @@
-// Runs the library's Cartesian single-level step on the CPU: the tile kernels (MODE 0 face sums,
-// MODE 1 update) on emulated thread blocks (a block's threads as std::threads, a std::barrier
-// for __syncthreads, the dynamic shared memory as one buffer for the running block), with the
+// Runs the library's Cartesian single-level step on the CPU: the tile kernels (k_faces: the
+// face phi-bar into the face buffer and the face sums; k_update: the update from the face
+// buffer) on emulated thread blocks (a block's threads as std::threads, a std::barrier for
+// __syncthreads, the dynamic shared memory as one buffer for the running block), with the
 // initialisation, chunk-sum and finalisation kernels around them in the order the handle
 // launches them for a level that holds every cell.  FP64 storage, or FP32 when compiled with
 // EMU_FP32.  Test infrastructure.
@@ -24,7 +25,7 @@ using S = float;
 using T = double;
 using S = double;
 #endif
-constexpr int D = 2, TX = 16, TY = 16, VB = 2, FIN_BLOCK = 64;
+constexpr int D = 2, TX = 16, TY = 16, VPC = 384, FIN_BLOCK = 64;
 
 extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc, const double* wall,
                             const double* gas6, int n_base, double umin, double umax, int rule, double dt,
@@ -112,9 +113,10 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     emu_launch(dim3((ncell + 127) / 128, k.nchunk, 1), 128,
                [&] { k_moments<S, T, D>(k, ncell, prm[0].data(), vt.data(), f[0].data(), cpart.data()); });
   }
-  using L0 = TileSmem<T, TX, TY, D, VB, 0>;
-  using L1 = TileSmem<T, TX, TY, D, VB, 1>;
-  if (L0::BYTES > sizeof(smem) || L1::BYTES > sizeof(smem)) return 2;
+  using L0 = TileSmem<T, TX, TY, D>;
+  using L1 = UpdSmem<T, TX, TY, D, VPC>;
+  if (L0::BYTES > sizeof(smem) || L1::BYTES > sizeof(smem) || vpc > VPC || vpc % 2) return 2;
+  std::vector<T> fbar(2 * (size_t)((nv + 1) / 2) * 2 * nface, 0.0);
   for (int s = 0; s < steps; ++s) {
     {
       PointArgs a = pargs(false);
@@ -132,10 +134,10 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     t.cparam = prm[pcur].data(); t.fparam = fprm.data(); t.vt = vt.data(); t.tiles = tiles.data();
     t.ntx = ntx; t.nty = nty; t.level = 0; t.lvl_of = lvl.data(); t.slot_of = slot.data();
     t.ghost_of = nullptr; t.ghost = nullptr; t.nghost = 0; t.frole = frole.data(); t.fslot = fslot.data();
-    t.ucell = ucell.data(); t.step = &stepctr;
+    t.ucell = ucell.data(); t.step = &stepctr; t.fbar = fbar.data();
     t.part = fpart.data();
     emu_launch(dim3(ntiles, k.nchunk, 1), TX * TY,
-               [&] { k_tile<S, T, D, TX, TY, VB, 0, false, false>(t, limiter); });
+               [&] { k_faces<S, T, D, TX, TY, false, false>(t, limiter); });
     {
       PointArgs a = pargs(true);
       a.cprm = prm[pcur].data();
@@ -144,7 +146,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     }
     t.part = cpart.data();
     emu_launch(dim3(ntiles, k.nchunk, 1), TX * TY,
-               [&] { k_tile<S, T, D, TX, TY, VB, 1, false, false>(t, limiter); });
+               [&] { k_update<S, T, D, TX, TY, VPC, false, false>(t); });
     cur ^= 1;
   }
   for (size_t i = 0; i < f[cur].size(); ++i) fout[i] = (double)f[cur][i];
