@@ -587,26 +587,23 @@ k_faces(const TileArgs a, int limiter) {
   // the face's contribution of a pair to its moment partials (interior faces), or to the
   // outgoing normal mass flux sum_{xi.n_in <= 0} w (xi.n_in) g-bar (wall faces): lanes
   // summed in order, as scalar accumulation of the two velocities would
+  // (no branch: a face that is not evaluated here contributes zeros)
   auto face_part = [&](const FaceQ& F, V gb, V hb, V xn, V xix, V xiy, V wxv, V wyv, T (&part)[9]) {
-    if (F.kind == FK_INTERIOR) {
-      const V xp = P::sub(xix, P::splat(F.shx));
-      const V yp = (D == 2) ? P::sub(xiy, P::splat(F.shy)) : P::splat(T(0));
-      const V wg = P::mul(wxv, P::mul(wyv, gb));
-      const V e = P::mul(wxv, P::mul(wyv, P::fma(P::fma(yp, yp, P::mul(xp, xp)), gb, hb)));
-      const V q1 = P::mul(wg, xp), q2 = P::mul(wg, yp);
-      const V q4 = P::mul(q1, xp), q5 = P::mul(q1, yp), q6 = P::mul(q2, yp);
-      const V q7 = P::mul(e, xp), q8 = P::mul(e, yp);
-      part[0] = wg.x + wg.y; part[1] = q1.x + q1.y; part[2] = q2.x + q2.y; part[3] = e.x + e.y;
-      part[4] = q4.x + q4.y; part[5] = q5.x + q5.y; part[6] = q6.x + q6.y;
-      part[7] = q7.x + q7.y; part[8] = q8.x + q8.y;
-    } else {
-#pragma unroll
-      for (int p = 0; p < 9; ++p) part[p] = T(0);
-      if (F.kind == FK_WALL_LO || F.kind == FK_WALL_HI) {
-        const V xin = (F.kind == FK_WALL_LO) ? xn : P::mk(-xn.x, -xn.y);
-        const V o = P::mul(wxv, P::mul(wyv, P::mul(xin, gb)));
-        part[0] = (xin.x <= T(0) ? o.x : T(0)) + (xin.y <= T(0) ? o.y : T(0));
-      }
+    const V xp = P::sub(xix, P::splat(F.shx));
+    const V yp = (D == 2) ? P::sub(xiy, P::splat(F.shy)) : P::splat(T(0));
+    const V wg = P::mul(wxv, P::mul(wyv, gb));
+    const V e = P::mul(wxv, P::mul(wyv, P::fma(P::fma(yp, yp, P::mul(xp, xp)), gb, hb)));
+    const V q1 = P::mul(wg, xp), q2 = P::mul(wg, yp);
+    const V q4 = P::mul(q1, xp), q5 = P::mul(q1, yp), q6 = P::mul(q2, yp);
+    const V q7 = P::mul(e, xp), q8 = P::mul(e, yp);
+    const bool in = F.meta && F.kind == FK_INTERIOR;
+    part[0] = in ? wg.x + wg.y : T(0); part[1] = in ? q1.x + q1.y : T(0); part[2] = in ? q2.x + q2.y : T(0);
+    part[3] = in ? e.x + e.y : T(0); part[4] = in ? q4.x + q4.y : T(0); part[5] = in ? q5.x + q5.y : T(0);
+    part[6] = in ? q6.x + q6.y : T(0); part[7] = in ? q7.x + q7.y : T(0); part[8] = in ? q8.x + q8.y : T(0);
+    if (F.meta && (F.kind == FK_WALL_LO || F.kind == FK_WALL_HI)) {
+      const V xin = (F.kind == FK_WALL_LO) ? xn : P::mk(-xn.x, -xn.y);
+      const V o = P::mul(wxv, P::mul(wyv, P::mul(xin, gb)));
+      part[0] = (xin.x <= T(0) ? o.x : T(0)) + (xin.y <= T(0) ? o.y : T(0));
     }
   };
 
@@ -653,17 +650,25 @@ k_faces(const TileArgs a, int limiter) {
     const V wxv = sVT[4 * j + 2], wyv = sVT[4 * j + 3];
     // the pair of a face: phi-bar to the face buffer (read by k_update of the same level; a
     // padding lane is stored too, so that every lane k_update reads is finite), its moments
+    // faces A and B are evaluated without a branch (so that their work interleaves); only a
+    // face evaluated here is stored and accumulates nonzero moments
     auto one = [&](const FaceQ& F, T (&part)[9]) {
       V gb, hb, xn;
       face_bar(F, Pg, Ph, xix, xiy, gb, hb, xn);
-      T* o = fbo + fbar_at(0, v, F.fid, nvp, nfc);
-      *reinterpret_cast<V*>(o) = gb;
-      *reinterpret_cast<V*>(o + 2 * nvp * nfc) = hb;
+      if (F.meta) {
+        T* o = fbo + fbar_at(0, v, F.fid, nvp, nfc);
+        *reinterpret_cast<V*>(o) = gb;
+        *reinterpret_cast<V*>(o + 2 * nvp * nfc) = hb;
+      }
       face_part(F, gb, hb, xn, xix, xiy, wxv, wyv, part);
     };
     T part[9];
-    if (FA.meta) { one(FA, part); fold_partials<T>(ra[0], part); }
-    if (D == 2 && FB.meta) { one(FB, part); fold_partials<T>(ra[1], part); }
+    one(FA, part);
+    fold_partials<T>(ra[0], part);
+    if (D == 2) {
+      one(FB, part);
+      fold_partials<T>(ra[1], part);
+    }
     if (FC.meta) { one(FC, part); fold_partials_smem<T>(sAcc + tid, L::NX3, part); }
   }
 
@@ -929,14 +934,17 @@ k_update(const TileArgs a) {
       const V xix = sVT[4 * j], xiy = sVT[4 * j + 1];
       V* Fg = sF + (buf * 2 + 0) * G::NF;
       V* Fh = sF + (buf * 2 + 1) * G::NF;
-      V FAg = ga, FAh = ha;
-      if (evA) face_flux2<T, D, CV>(FA, 0, xix, xiy, ga, ha, c0, twoK, FAg, FAh);
+      // faces A and B evaluated without a branch (a received face takes its mapped flux)
+      V FAg, FAh;
+      face_flux2<T, D, CV>(FA, 0, xix, xiy, ga, ha, c0, twoK, FAg, FAh);
+      if (!evA) { FAg = ga; FAh = ha; }
       Fg[fA] = FAg;
       Fh[fA] = FAh;
       if (xA) export_x(FA.col, v, FAg, FAh);
       if (D == 2) {
-        V FBg = gbb, FBh = hbb;
-        if (evB) face_flux2<T, D, CV>(FB, 1, xix, xiy, gbb, hbb, c0, twoK, FBg, FBh);
+        V FBg, FBh;
+        face_flux2<T, D, CV>(FB, 1, xix, xiy, gbb, hbb, c0, twoK, FBg, FBh);
+        if (!evB) { FBg = gbb; FBh = hbb; }
         Fg[fB] = FBg;
         Fh[fB] = FBh;
         if (xB) export_x(FB.col, v, FBg, FBh);
