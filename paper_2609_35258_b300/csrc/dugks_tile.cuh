@@ -768,8 +768,9 @@ k_update(const TileArgs a) {
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = (D == 2) ? tid / TX : 0;
+  // random bits of the stochastic rounding of stored values (BF16 and FP32 storage)
   unsigned seed = 0;
-  if constexpr (sizeof(S) == 2) seed = hash32(*a.step * 0x632be5abu + a.salt);
+  if constexpr (sizeof(S) <= 4) seed = hash32(*a.step * 0x632be5abu + a.salt);
   const int tile = a.tiles[blockIdx.x];
   const int bx = tile % a.ntx, by = tile / a.ntx;
   const int x0 = bx * TX, y0 = by * TY;
@@ -949,30 +950,41 @@ k_update(const TileArgs a) {
         Fh[fB] = FBh;
         if (xB) export_x(FB.col, v, FBg, FBh);
       }
-      // phi~+ = phi~ + (4/3) b (phi^S - phi~)
+      // the collision part of phi~+ - phi~ = (4/3) b (phi^S - phi~)
       V gs, hs;
       model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
-      const V gp = P::fma(P::splat(m0.c2), P::sub(gs, g0), g0);
-      const V hp = P::fma(P::splat(m0.c2), P::sub(hs, h0), h0);
+      V dg = P::mul(P::splat(m0.c2), P::sub(gs, g0));
+      V dh = P::mul(P::splat(m0.c2), P::sub(hs, h0));
       __syncthreads();
-      // phi~+ minus the microflux divergence
+      // minus the microflux divergence: the increment of the step
       const V* Cg = sC + (cbuf * 2 + 0) * SC * NX3 + (j - jb) * NX3;
       const V* Ch = sC + (cbuf * 2 + 1) * SC * NX3 + (j - jb) * NX3;
       const V FEg = eInTile ? Fg[fA + 1] : Cg[cE], FEh = eInTile ? Fh[fA + 1] : Ch[cE];
-      V gn = P::fma(P::splat(-lamx), P::sub(FEg, Fg[fA]), gp);
-      V hn = P::fma(P::splat(-lamx), P::sub(FEh, Fh[fA]), hp);
+      dg = P::fma(P::splat(-lamx), P::sub(FEg, Fg[fA]), dg);
+      dh = P::fma(P::splat(-lamx), P::sub(FEh, Fh[fA]), dh);
       if (D == 2) {
         const V FNg = nInTile ? Fg[fB + TX] : Cg[cN], FNh = nInTile ? Fh[fB + TX] : Ch[cN];
-        gn = P::fma(P::splat(-lamy), P::sub(FNg, Fg[fB]), gn);
-        hn = P::fma(P::splat(-lamy), P::sub(FNh, Fh[fB]), hn);
+        dg = P::fma(P::splat(-lamy), P::sub(FNg, Fg[fB]), dg);
+        dh = P::fma(P::splat(-lamy), P::sub(FNh, Fh[fB]), dh);
       }
+      // random bits: one hash of (step, level, cell, velocity pair) per 32 bits
       unsigned rb0 = 0, rb1 = 0;
-      if constexpr (sizeof(S) == 2) {
-        rb0 = hash32(seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)v));
-        rb1 = hash32(seed ^ hash32((unsigned)col0 * 0x9e3779b1u + (unsigned)(v + 1)));
+      if constexpr (sizeof(S) <= 4) {
+        const unsigned key = seed ^ ((unsigned)col0 * 0x9e3779b1u + (unsigned)v);
+        rb0 = hash32(key);
+        rb1 = hash32(key ^ 0x5bd1e995u);
       }
-      const S sg0 = Stored<S, T>::enc(gn.x, rb0), sh0 = Stored<S, T>::enc(hn.x, rb0 >> 16);
-      const S sg1 = Stored<S, T>::enc(gn.y, rb1), sh1 = Stored<S, T>::enc(hn.y, rb1 >> 16);
+      // phi~^{n+1} = phi~ + increment, rounded to the storage: stochastically for FP32 (the sum
+      // itself) and BF16 (the FP32 sum), to nearest for FP64
+      S sg0, sh0, sg1, sh1;
+      if constexpr (sizeof(S) == 4) {
+        const float2 gq2 = sr_add2(g0, dg, rb0, rb1), hq2 = sr_add2(h0, dh, rb0 >> 16, rb1 >> 16);
+        sg0 = gq2.x; sg1 = gq2.y; sh0 = hq2.x; sh1 = hq2.y;
+      } else {
+        const V gn = P::add(g0, dg), hn = P::add(h0, dh);
+        sg0 = Stored<S, T>::enc(gn.x, rb0); sh0 = Stored<S, T>::enc(hn.x, rb0 >> 16);
+        sg1 = Stored<S, T>::enc(gn.y, rb1); sh1 = Stored<S, T>::enc(hn.y, rb1 >> 16);
+      }
       if (own_active) {
         fout[(long)v * ns + col0] = sg0;
         fout[(nv + v) * ns + col0] = sh0;

@@ -791,7 +791,7 @@ template <class S, class T, int D> struct Runner {
 
   static cudaError_t step(mlvs_handle* h, Inst& I) {
     cudaError_t e;
-    if constexpr (sizeof(S) == 2) {
+    if constexpr (sizeof(S) <= 4) {   // random bits of the stochastic rounding (BF16, FP32)
       ++h->launches;
       k_step_counter<<<1, 1, 0, h->stream>>>(I.stepctr.as<unsigned>());
     }

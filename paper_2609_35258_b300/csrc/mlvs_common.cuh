@@ -221,6 +221,28 @@ __device__ __forceinline__ void model_eval2(const MP<T>& p, V2<T> xix, V2<T> xiy
   h = P::fma(hs, corr, hs);
 }
 
+// a + b rounded stochastically to FP32 with 16 random bits r (FP32 storage of phi~^{n+1}):
+// given s = RN(a + b) and its rounding error e, the neighbour of s towards the
+// exact sum is taken with probability |e| / gap, so the stored value is unbiased: near a
+// steady state the increments below half an ulp are not lost step after step, and the
+// rounding errors of successive steps are independent.
+__device__ __forceinline__ float sr_pick(float s, float e, unsigned r) {
+  const unsigned us = __float_as_uint(s);
+  const float sn = __uint_as_float(((s > 0.0f) == (e > 0.0f)) ? us + 1u : us - 1u);
+  const float gap = fabsf(__fsub_rn(sn, s));
+  const float u = __fmul_rn(__uint2float_rn(r & 0xffffu) + 0.5f, 1.0f / 65536.0f);
+  return (e != 0.0f && s != 0.0f && __fmul_rn(u, gap) < fabsf(e)) ? sn : s;
+}
+// a + b for a pair of lanes, a the stored value and b its increment: the rounding error by
+// Dekker's Fast2Sum, e = b - (s - a), exact whenever |a| >= |b| (every value that does not
+// more than double in a step), in packed arithmetic
+__device__ __forceinline__ float2 sr_add2(float2 a, float2 b, unsigned r0, unsigned r1) {
+  using P = Pk<float>;
+  const float2 s = P::add(a, b);
+  const float2 e = P::sub(b, P::sub(s, a));
+  return make_float2(sr_pick(s.x, e.x, r0), sr_pick(s.y, e.y, r1));
+}
+
 // Compensated (Kahan) accumulation for sums that must keep FP64-level accuracy in FP32.
 template <class T> struct KSum {
   T s, c;

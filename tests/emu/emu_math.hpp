@@ -51,3 +51,9 @@ static inline float2 __fmul2_rn(float2 a, float2 b) { return make_float2(__fmul_
 static inline float2 __ffma2_rn(float2 a, float2 b, float2 c) {
   return make_float2(std::fma(a.x, b.x, c.x), std::fma(a.y, b.y, c.y));
 }
+static inline float __uint_as_float(unsigned u) {
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+static inline float __uint2float_rn(unsigned u) { return (float)u; }
