@@ -64,6 +64,23 @@ enum { FS_RHO = 0, FS_UX, FS_UY, FS_T, FS_G = 4, FS_H = 29, FS_DEN = 38, FIN_SCR
 
 enum { ERR_NONFINITE = 1, ERR_POSITIVITY = 2, ERR_SINGULAR = 4 };
 
+// The device error word and, behind it, the first failing point of a finalisation:
+//   int [0] error bits, [1] claim, [2] point index, [3] 1 for a face; double [2] rho, T.
+constexpr int ERR_WORDS = 8;   // ints (the two doubles start at int 4)
+
+// Record a failing point state: the error bit, and the first such point with its density and
+// temperature (the host adds them to the error message).
+__device__ __forceinline__ void report_point(int* err, int bit, int i, int is_face, double rho, double Tm) {
+  atomicOr(err, bit);
+  if (atomicCAS(err + 1, 0, 1) == 0) {
+    err[2] = i;
+    err[3] = is_face;
+    double* d = reinterpret_cast<double*>(err + 4);
+    d[0] = rho;
+    d[1] = Tm;
+  }
+}
+
 // Sum over the LANES lanes of a warp segment (all lanes receive the same value).
 template <int LANES>
 __device__ __forceinline__ double lane_sum(double x) {
@@ -193,46 +210,64 @@ __device__ inline void axis_moments(const PointArgs& A, const MP<T>& mp, double 
     }
 }
 
-// The same moments summed directly over the velocities [lane, nv) with stride LANES and
-// combined over the lanes (compensated sums in FP64, the others in the compute type).
+// The same moments summed directly over the velocities, two at a time: lane `lane` of LANES
+// takes the velocity pairs (v, v+1), v = 2 (lane + j LANES), in packed two-lane arithmetic (a
+// pair past the last velocity has a zero-weight lane), and the lanes are combined at the end
+// (compensated sums in FP64, the others in the compute type).
 template <class T, int D, int LANES>
 __device__ inline void direct_moments(const PointArgs& A, const MP<T>& mp, int lane, double G[5][5],
                                       double H[3][3]) {
+  using P = Pk<T>;
+  using V = V2<T>;
   const StepConst& k = A.k;
   const T* vt = reinterpret_cast<const T*>(A.vt);
   const int nv = k.nv;
   const T c0 = T(k.c0), twoK = T(k.twoK);
-  KSum<T> g00, g10, g01, e0;
-  g00.zero(); g10.zero(); g01.zero(); e0.zero();
-  T gs[15], hs[6];
+  // packed Kahan pairs (s, c) of the four conserved rows
+  V ks[4], kc[4];
 #pragma unroll
-  for (int j = 0; j < 15; ++j) gs[j] = T(0);
+  for (int r = 0; r < 4; ++r) ks[r] = kc[r] = P::splat(T(0));
+  V gs[15], hs[6];
 #pragma unroll
-  for (int j = 0; j < 6; ++j) hs[j] = T(0);
-  for (int v = lane; v < nv; v += LANES) {
-    const T xx = vt[v], yy = (D == 2) ? vt[nv + v] : T(0), wxv = vt[2 * nv + v], wyv = vt[3 * nv + v];
-    T gv, hv;
-    model_eval<T, D>(mp, xx, yy, c0, twoK, gv, hv);
-    const T cx = xx - mp.ux, cy = (D == 2) ? yy - mp.uy : T(0);
-    const T wg = wxv * (wyv * gv), wh = wxv * (wyv * hv);
-    g00.add(wg);
-    g10.add(wg * cx);
-    g01.add(wg * cy);
-    e0.add(T(0.5) * ((cx * cx + cy * cy) * wg + wh));
+  for (int j = 0; j < 15; ++j) gs[j] = P::splat(T(0));
+#pragma unroll
+  for (int j = 0; j < 6; ++j) hs[j] = P::splat(T(0));
+  const V ux = P::splat(mp.ux), uy = P::splat(mp.uy);
+  for (int v = 2 * lane; v < nv; v += 2 * LANES) {
+    const int v2 = v + 1 < nv ? v + 1 : v;
+    const T on = v + 1 < nv ? T(1) : T(0);
+    const V xx = P::mk(vt[v], vt[v2]);
+    const V yy = (D == 2) ? P::mk(vt[nv + v], vt[nv + v2]) : P::splat(T(0));
+    const V wxv = P::mk(vt[2 * nv + v], on * vt[2 * nv + v2]);
+    const V wyv = P::mk(vt[3 * nv + v], vt[3 * nv + v2]);
+    V gv, hv;
+    model_eval2<T, D>(mp, xx, yy, c0, twoK, gv, hv);
+    const V cx = P::sub(xx, ux), cy = (D == 2) ? P::sub(yy, uy) : P::splat(T(0));
+    const V wg = P::mul(wxv, P::mul(wyv, gv)), wh = P::mul(wxv, P::mul(wyv, hv));
+    const V x4[4] = {wg, P::mul(wg, cx), P::mul(wg, cy),
+                     P::mul(P::splat(T(0.5)), P::fma(P::fma(cy, cy, P::mul(cx, cx)), wg, wh))};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const V y = P::sub(x4[r], kc[r]);
+      const V t = P::add(ks[r], y);
+      kc[r] = P::sub(P::sub(t, ks[r]), y);
+      ks[r] = t;
+    }
     int j = 0, jh = 0;
-    T px = wg, qx = wh;
+    V px = wg, qx = wh;
 #pragma unroll
     for (int a = 0; a < 5; ++a) {
-      T p = px, q = qx;
+      V pp = px, q = qx;
 #pragma unroll
       for (int b = 0; a + b < 5; ++b) {
-        gs[j++] += p;
-        if (a + b < 3) hs[jh++] += q;
-        p *= cy;
-        q *= cy;
+        gs[j] = P::add(gs[j], pp);
+        ++j;
+        if (a + b < 3) { hs[jh] = P::add(hs[jh], q); ++jh; }
+        pp = P::mul(pp, cy);
+        q = P::mul(q, cy);
       }
-      px *= cx;
-      qx *= cx;
+      px = P::mul(px, cx);
+      qx = P::mul(qx, cx);
     }
   }
   for (int a = 0; a < 5; ++a)
@@ -244,14 +279,22 @@ __device__ inline void direct_moments(const PointArgs& A, const MP<T>& mp, int l
   for (int a = 0; a < 5; ++a)
 #pragma unroll
     for (int b = 0; a + b < 5; ++b) {
-      G[a][b] = (double)lane_sum_t<LANES, T>(gs[j++]);
-      if (a + b < 3) H[a][b] = (double)lane_sum_t<LANES, T>(hs[jh++]);
+      G[a][b] = (double)lane_sum_t<LANES, T>(gs[j].x + gs[j].y);
+      ++j;
+      if (a + b < 3) {
+        H[a][b] = (double)lane_sum_t<LANES, T>(hs[jh].x + hs[jh].y);
+        ++jh;
+      }
     }
-  G[0][0] = lane_sum<LANES>(g00.val());
-  G[1][0] = lane_sum<LANES>(g10.val());
-  G[0][1] = lane_sum<LANES>(g01.val());
+  double kv[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+    kv[r] = lane_sum<LANES>(((double)ks[r].x - (double)kc[r].x) + ((double)ks[r].y - (double)kc[r].y));
+  G[0][0] = kv[0];
+  G[1][0] = kv[1];
+  G[0][1] = kv[2];
   // keep the compensated energy-row sum: fold it into the H[0][0] slot
-  H[0][0] = 2.0 * lane_sum<LANES>(e0.val()) - G[2][0] - G[0][2];
+  H[0][0] = 2.0 * kv[3] - G[2][0] - G[0][2];
 }
 
 // Model parameters of a point with state (rho, u, T, q), before the correction.
@@ -584,9 +627,10 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
     a.W[9 * nc + wi] = sf * (M[MO_GXY] - rho * upx * upy);
     a.W[10 * nc + wi] = (D == 2) ? sf * (M[MO_GYY] - rho * upy * upy - pr) : 0.0;
   }
-  if (!ok) atomicOr(a.err, ERR_SINGULAR);
-  if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy)) atomicOr(a.err, ERR_NONFINITE);
-  else if (!(rho > 0.0) || !(Tm > 0.0)) atomicOr(a.err, ERR_POSITIVITY);
+  if (!ok) report_point(a.err, ERR_SINGULAR, i, a.is_face, rho, Tm);
+  if (!isfinite(rho) || !isfinite(Tm) || !isfinite(ux) || !isfinite(uy))
+    report_point(a.err, ERR_NONFINITE, i, a.is_face, rho, Tm);
+  else if (!(rho > 0.0) || !(Tm > 0.0)) report_point(a.err, ERR_POSITIVITY, i, a.is_face, rho, Tm);
 }
 
 template <class T, int D>

@@ -1545,15 +1545,26 @@ extern "C" mlvs_status mlvs_time_step(const mlvs_handle* h, double* dt) {
 }
 
 static mlvs_status check_flags(mlvs_handle* h) {
-  for (auto& I : h->inst) {
-    int eflag = 0;
-    CK(cudaMemcpyAsync(&eflag, I.err.p, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  for (size_t n = 0; n < h->inst.size(); ++n) {
+    Inst& I = h->inst[n];
+    int e[ERR_WORDS] = {0};
+    CK(cudaMemcpyAsync(e, I.err.p, sizeof(e), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (eflag) {
-      mlvs_status s = (eflag & ERR_NONFINITE) ? MLVS_ERR_NONFINITE
-                      : (eflag & ERR_POSITIVITY) ? MLVS_ERR_POSITIVITY : MLVS_ERR_SINGULAR;
+    if (e[0]) {
+      mlvs_status s = (e[0] & ERR_NONFINITE) ? MLVS_ERR_NONFINITE
+                      : (e[0] & ERR_POSITIVITY) ? MLVS_ERR_POSITIVITY : MLVS_ERR_SINGULAR;
       h->sticky = s;
-      return fail(h, s, "device reported a non-finite, non-positive or singular state");
+      char msg[256];
+      if (e[1]) {
+        double d[2];
+        std::memcpy(d, e + 4, sizeof(d));
+        std::snprintf(msg, sizeof(msg),
+                      "device reported a non-finite, non-positive or singular state (instance %zu, first at "
+                      "%s %d of its level: rho = %.6g, T = %.6g)", n, e[3] ? "face" : "cell", e[2], d[0], d[1]);
+      } else {
+        std::snprintf(msg, sizeof(msg), "device reported a non-finite, non-positive or singular state (instance %zu)", n);
+      }
+      return fail(h, s, msg);
     }
   }
   return MLVS_OK;
@@ -1666,9 +1677,9 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
     mlvs_status st = build_levels(h, std::vector<int>(ncell, 0), I);
     if (st != MLVS_OK) return st;
     if (I.ucell.alloc(2ull * ncell * h->tsize) != cudaSuccess || I.W.alloc(11ull * ncell * 8) != cudaSuccess ||
-        I.err.alloc(sizeof(int)) != cudaSuccess || I.stepctr.alloc(sizeof(unsigned)) != cudaSuccess)
+        I.err.alloc(ERR_WORDS * sizeof(int)) != cudaSuccess || I.stepctr.alloc(sizeof(unsigned)) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation failed");
-    CK(cudaMemsetAsync(I.err.p, 0, sizeof(int), h->stream));
+    CK(cudaMemsetAsync(I.err.p, 0, ERR_WORDS * sizeof(int), h->stream));
     CK(cudaMemsetAsync(I.stepctr.p, 0, sizeof(unsigned), h->stream));
     CK(cudaMemsetAsync(I.W.p, 0, I.W.n, h->stream));
     DevBuf dW0;

@@ -177,7 +177,7 @@ inline void u_buffer(const UHost& u, int b, int& type, size_t& count) {
     case UB_FPRM: type = 0; count = (size_t)NP * nf; return;
     case UB_W: type = 2; count = 11 * nc; return;
     case UB_WDEN: type = 2; count = nf; return;
-    case UB_ERR: type = 1; count = 1; return;
+    case UB_ERR: type = 1; count = ERR_WORDS; return;   // error bits and the first failing point
     case UB_CPRM8: type = 0; count = 4 * nc; return;
     case UB_FPRM8: type = 0; count = 4 * nf; return;
   }

@@ -10,6 +10,7 @@
 static inline void __syncthreads() {}
 static inline int atomicOr(int* p, int v) { const int o = *p; *p |= v; return o; }
 static inline int atomicAdd(int* p, int v) { const int o = *p; *p += v; return o; }
+static inline int atomicCAS(int* p, int cmp, int v) { const int o = *p; if (o == cmp) *p = v; return o; }
 // launch coordinates: referenced by kernels the emulator compiles but never runs
 static const uint3 threadIdx = {0, 0, 0}, blockIdx = {0, 0, 0};
 static const dim3 blockDim(1, 1, 1), gridDim(1, 1, 1);

@@ -75,7 +75,8 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
   std::vector<T> fprm((size_t)NP * nface, 0.0), ucell(2 * (size_t)ncell);
   std::vector<double> cpart((size_t)k.nchunk * NMOM * ncell), fpart((size_t)k.nchunk * NMOM * nface);
   std::vector<double> msum((size_t)NMOM * std::max(nface, ncell)), W(11 * (size_t)ncell);
-  int err = 0;
+  int err_words[ERR_WORDS] = {0};
+  int& err = err_words[0];
   unsigned stepctr = 0;
   auto pargs = [&](bool face) {
     PointArgs a;
@@ -87,7 +88,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     for (int s = 0; s < 4; ++s)
       for (int j = 0; j < 3; ++j) a.wall[s][j] = wall[3 * s + j];
     for (int j = 0; j < 4; ++j) a.far[j] = far[j];
-    a.err = &err;
+    a.err = err_words;
     return a;
   };
   auto fin_grid = [](int n) { return dim3(std::max(1, (n + FIN_BLOCK - 1) / FIN_BLOCK), 1, 1); };
