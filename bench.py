@@ -293,12 +293,13 @@ def _selector_leg():
             "workload": "periodic random states, 64^2 cells, base 41^2, four radial levels"}
 
 
-def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07, 0.05, 0.04, 0.035),
+def _cylinder_leg(storage="f32", warm_steps=300, run_steps=300, taus=(1.0, 0.07, 0.05, 0.04, 0.035),
                   positive_mapping=0):
-    """Ma 5 flow past a cylinder (O-grid 256 x 128, Kn 0.1, base 201^2 on [-15, 15]^2).  UVS runs
-    first and keeps its fields at the comparison step.  MLVS then starts from the same initial
-    state and, once the impulsive start's near-vacuum wake has filled (`warm_steps`), runs the
-    paper's setting (C_split 0.01, C_merge 0.005, tau_clust 0.05, up to four depths, spaces
+    """Ma 5 flow past a cylinder (O-grid 256 x 128, Kn 0.1, base 201^2 on [-15, 15]^2), from the
+    smooth start of `workloads.cylinder(start="ramp")` (speed rising from the wall over two
+    radii at the freestream's total enthalpy and pressure).  UVS runs first and keeps its fields
+    at the comparison step.  MLVS then starts from the same initial state and, after
+    `warm_steps` steps on the full space, runs the paper's setting (C_split 0.01, C_merge 0.005, tau_clust 0.05, up to four depths, spaces
     rebuilt every 100 steps) with the transport test on (eps_merge 5e-5, the cavity's value; the
     paper gives none for the cylinder) for `run_steps` steps; its fields are compared with UVS at
     the same step.  Afterwards the same state is adapted with each clustering threshold in turn and timed
@@ -308,7 +309,7 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
     from paper_2609_35258_b300 import mlvs as M, workloads
     from paper_2609_35258_b300.solver import Solver
     nt, nr = 256, 128
-    d = workloads.cylinder(nt, nr, storage=storage)
+    d = workloads.cylinder(nt, nr, storage=storage, start="ramp")
     F = M.RHO | M.U | M.V | M.T | M.QX | M.QY
     u = Solver(d)
     M.mlvs_set_graph(u.h, True)
@@ -318,7 +319,8 @@ def _cylinder_leg(storage="f32", warm_steps=1000, run_steps=400, taus=(1.0, 0.07
     nv = su.cell_velocity_updates / run_steps / (nt * nr)
     mu = u.moments(F)
     u.close()
-    out = {"workload": f"cylinder O-grid {nt}x{nr}, Ma 5, Kn 0.1, base 201^2 on [-15,15]^2, {storage}",
+    out = {"workload": f"cylinder O-grid {nt}x{nr}, Ma 5, Kn 0.1, base 201^2 on [-15,15]^2, {storage}, "
+                       f"smooth start",
            "uvs_ms_per_step": uvs_ms, "uvs_points_per_cell": nv, "adapt_from_step": warm_steps,
            "run": None, "tau_sweep": []}
     s = Solver(d, adaptive=1, positive_mapping=positive_mapping)
@@ -554,8 +556,10 @@ def run_ours(args, rank, world, local_rank):
     selector = None
     if not args.no_selector and rank == 0:
         selector = _selector_leg()
-    cylinder = (_cylinder_leg(positive_mapping=int(args.positive_mapping))
-                if (args.cylinder and rank == 0) else None)
+    cylinder = None
+    if not args.no_cylinder and rank == 0:
+        cylinder = {st_: _cylinder_leg(storage=st_, positive_mapping=int(args.positive_mapping))
+                    for st_ in ("f32", "bf16")}
     unstructured = _unstructured_isolated() if (not args.no_unstructured and rank == 0) else None
 
     # end-to-end through the public API: host init upload, steps, host moment reads
@@ -630,8 +634,9 @@ def main():
     ap.add_argument("--no-steady", action="store_true")
     ap.add_argument("--no-selector", action="store_true")
     ap.add_argument("--cells", type=int, default=64, help="cavity cells per side (default 64)")
-    ap.add_argument("--cylinder", action="store_true",
-                    help="add the Ma 5 cylinder leg (UVS vs MLVS over clustering thresholds, ~3 min)")
+    ap.add_argument("--no-cylinder", action="store_true",
+                    help="skip the Ma 5 cylinder legs (FP32 and BF16: UVS vs MLVS, clustering-threshold "
+                         "sweep and runtime-model fit, about 45 s each)")
     ap.add_argument("--positive-mapping", action="store_true",
                     help="cylinder leg: exponential fallback for level switches that go negative")
     ap.add_argument("--no-unstructured", action="store_true",

@@ -96,16 +96,32 @@ def ogrid_nodes(ntheta, nr, r_in=1.0, r_out=11.0):
     return xy
 
 
-def cylinder(ntheta=256, nr=128, mach=5.0, Kn=0.1, n_base=201, umax=15.0, r_out=11.0, storage="f32"):
+def cylinder(ntheta=256, nr=128, mach=5.0, Kn=0.1, n_base=201, umax=15.0, r_out=11.0, storage="f32",
+             start="impulsive", ramp=2.0):
     """Flow past a cylinder of radius 1 on an O-grid: periodic around, a diffuse wall at
     T_w = T_inf on the cylinder (j = 0), freestream (rho, T = 1, u = Ma sqrt(gamma R T),
-    gamma = 5/3) at the outer boundary; the gas starts as the freestream."""
+    gamma = 5/3) at the outer boundary.  start = "impulsive": the gas starts as the freestream
+    everywhere.  start = "ramp": the speed rises from zero at the wall to the freestream's over
+    about `ramp` radii, u = u_inf (1 - exp(-((r - 1) / ramp)^2)), at the freestream's total
+    enthalpy (T = T_inf + (u_inf^2 - u^2) / (2 c_p), c_p = 5R/2) and pressure (rho T = 1): the
+    gas near the cylinder starts near its stagnation state instead of striking the wall at the
+    freestream speed and leaving a near-vacuum behind it."""
     u = mach * math.sqrt(5.0 / 3.0)
     nodes = ogrid_nodes(ntheta, nr, 1.0, r_out)
     init = np.zeros((nr, ntheta, 4))
     init[..., 0] = 1.0
     init[..., 1] = u
     init[..., 3] = 1.0
+    if start == "ramp":
+        c = 0.25 * (nodes[:-1, :-1] + nodes[1:, :-1] + nodes[:-1, 1:] + nodes[1:, 1:])   # cell centres
+        r = np.hypot(c[..., 0], c[..., 1])
+        uc = u * (1.0 - np.exp(-((r - 1.0) / ramp) ** 2))
+        T = 1.0 + (u * u - uc * uc) / 5.0
+        init[..., 1] = uc
+        init[..., 3] = T
+        init[..., 0] = 1.0 / T
+    elif start != "impulsive":
+        raise ValueError("start must be 'impulsive' or 'ramp'")
     d = _desc("cylinder", 2, ntheta, nr, 1.0, 1.0, ("periodic", "periodic", "wall", "freestream"), init,
               Kn=Kn, n_base=n_base, umin=-umax, umax=umax, storage=storage)
     d["far"] = (1.0, u, 0.0, 1.0)

@@ -35,3 +35,21 @@ def test_two_cavity_cell_count_near_the_paper():
     assert len(cells) == 13600                                  # the paper's mesh has 12,012 cells
     with pytest.raises(ValueError):
         workloads.two_cavities(3)
+
+
+def test_cylinder_smooth_start():
+    """The smooth start keeps the freestream's pressure (rho T = 1) and total enthalpy
+    (T + u^2/5 for gamma = 5/3, R = 1) in every cell, is near rest at the wall and is the
+    freestream far from it."""
+    d = workloads.cylinder(64, 32, start="ramp")
+    W = d["init"]
+    u_inf = 5.0 * np.sqrt(5.0 / 3.0)
+    assert np.allclose(W[..., 0] * W[..., 3], 1.0, rtol=1e-14)
+    assert np.allclose(W[..., 3] + W[..., 1] ** 2 / 5.0, 1.0 + u_inf ** 2 / 5.0, rtol=1e-14)
+    assert np.all(W[..., 2] == 0.0)
+    assert np.all(W[0, :, 1] < 0.01 * u_inf) and np.allclose(W[-1, :, 1], u_inf, rtol=1e-12)
+    assert np.all(np.diff(W[..., 1], axis=0) > 0.0)            # speed rises with the radius
+    imp = workloads.cylinder(64, 32)["init"]
+    assert np.all(imp[..., 1] == u_inf) and np.all(imp[..., 0] == 1.0)
+    with pytest.raises(ValueError):
+        workloads.cylinder(64, 32, start="nope")
