@@ -42,6 +42,7 @@ struct TileArgs {
   const int* fslot;      // [nface] column in X (FR_CROSS) or Y (FR_RECV)
   void* X;               // (T) [2][nv][nX] microfluxes of the cross faces evaluated here
   int nX;
+  const int* xfid;       // [nX] face id of every column of X
   const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
   int nY;
   void* fbar;            // (T) [2][nv][nface] face phi-bar of the faces this level evaluates
@@ -331,8 +332,7 @@ __device__ __forceinline__ V2<T> limited2(V2<T> a, V2<T> b, T inv_h, int limiter
 // lane is reconstructed on its own.  Warp 0 of a tile whose high edge is a non-periodic mesh
 // end does the same for the faces on that edge.
 template <class S, class T, int D, int TX, int TY, bool ML, bool CV>
-__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
-k_faces(const TileArgs a, int limiter) {
+__device__ __forceinline__ void faces_tile(const TileArgs& a, const int tile, const int chunk, int limiter) {
   using G = TileGeom<TX, TY, D>;
   using B = FaceBox<TX, TY, D>;
   using L = TileSmem<T, TX, TY, D, CV>;
@@ -366,10 +366,8 @@ k_faces(const TileArgs a, int limiter) {
 
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = (D == 2) ? tid / TX : 0;
-  const int tile = a.tiles[blockIdx.x];
   const int bx = tile % a.ntx, by = tile / a.ntx;
   const int x0 = bx * TX, y0 = by * TY;
-  const int chunk = blockIdx.y;
   const int v0 = chunk * k.vpc;               // even: k.vpc is even
   const int v1 = min(k.nv, v0 + k.vpc);
   const int npr = (v1 - v0 + 1) / 2;          // pairs of the chunk
@@ -678,6 +676,33 @@ k_faces(const TileArgs a, int limiter) {
   if (FC.meta) write_partials_smem<T, D>(sAcc + tid, L::NX3, a.part + (long)chunk * NMOM * k.nface + FC.fid, k.nface);
 }
 
+// Copy a level's tile arguments into shared memory (all threads; a barrier must follow).
+__device__ __forceinline__ void load_args(TileArgs& dst, const TileArgs* __restrict__ src) {
+  static_assert(sizeof(TileArgs) % 8 == 0, "tile arguments are copied in 8-byte words");
+  constexpr int NW = (int)(sizeof(TileArgs) / 8);
+  for (int i = threadIdx.x; i < NW; i += blockDim.x)
+    reinterpret_cast<unsigned long long*>(&dst)[i] = reinterpret_cast<const unsigned long long*>(src)[i];
+}
+
+// The faces pass of a level that holds every cell: CTA (tile list index, velocity chunk).
+template <class S, class T, int D, int TX, int TY, bool CV>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_faces(const TileArgs a, int limiter) {
+  faces_tile<S, T, D, TX, TY, false, CV>(a, a.tiles[blockIdx.x], (int)blockIdx.y, limiter);
+}
+
+// The faces pass of every level of a multi-level instance in one launch: CTA b takes work
+// item (level, tile list index, velocity chunk) = work[b] with the level's arguments tab[level].
+template <class S, class T, int D, int TX, int TY, bool CV>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_faces_lv(const TileArgs* __restrict__ tab, const int4* __restrict__ work, int limiter) {
+  __shared__ __align__(16) TileArgs sa;
+  const int4 w = work[blockIdx.x];
+  load_args(sa, tab + w.x);
+  __syncthreads();
+  faces_tile<S, T, D, TX, TY, true, CV>(sa, sa.tiles[w.y], w.z, limiter);
+}
+
 // One face of k_update as a thread holds it: metadata, the model parameters of an evaluated
 // face, and on curvilinear meshes its unit normal and area.
 template <class T> struct UFace {
@@ -734,8 +759,7 @@ __device__ __forceinline__ void face_flux2(const UFace<T>& F, int dir, V2<T> xix
 // thread (face tid % NX3, pairs tid / NX3 + k NT / NX3), so the work per round is the same in
 // every warp.  Requires k.vpc <= VPC.
 template <class S, class T, int D, int TX, int TY, int VPC, bool ML, bool CV>
-__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
-k_update(const TileArgs a) {
+__device__ __forceinline__ void update_tile(const TileArgs& a, const int tile, const int chunk) {
   using G = TileGeom<TX, TY, D>;
   using L = UpdSmem<T, TX, TY, D, VPC>;
   using V = V2<T>;
@@ -759,7 +783,6 @@ k_update(const TileArgs a) {
   const T* __restrict__ fbi = reinterpret_cast<const T*>(a.fbar);
   const T* __restrict__ fg = reinterpret_cast<const T*>(a.fgeo);
   const T* __restrict__ cg = reinterpret_cast<const T*>(a.cgeo);
-  T* __restrict__ Xo = reinterpret_cast<T*>(a.X);
   const T* __restrict__ Yi = reinterpret_cast<const T*>(a.Y);
   const long ns = a.nslot;
   const long nv = k.nv;
@@ -771,10 +794,8 @@ k_update(const TileArgs a) {
   // random bits of the stochastic rounding of stored values (BF16 and FP32 storage)
   unsigned seed = 0;
   if constexpr (sizeof(S) <= 4) seed = hash32(*a.step * 0x632be5abu + a.salt);
-  const int tile = a.tiles[blockIdx.x];
   const int bx = tile % a.ntx, by = tile / a.ntx;
   const int x0 = bx * TX, y0 = by * TY;
-  const int chunk = blockIdx.y;
   const int v0 = chunk * k.vpc;               // even: k.vpc is even
   const int v1 = min(k.nv, v0 + k.vpc);
   const int npr = (v1 - v0 + 1) / 2;
@@ -843,15 +864,6 @@ k_update(const TileArgs a) {
       g = h = P::splat(T(0));
     }
   };
-  // the cross-level microflux of an exported face (the lanes that exist)
-  auto export_x = [&](long col, int v, V Fg, V Fh) {
-    Xo[(long)v * a.nX + col] = Fg.x;
-    Xo[(nv + v) * a.nX + col] = Fh.x;
-    if (v + 1 < v1) {
-      Xo[(long)(v + 1) * a.nX + col] = Fg.y;
-      Xo[(nv + v + 1) * a.nX + col] = Fh.y;
-    }
-  };
 
   // ---- faces C: parameters and ids in shared memory
   if (tid < NX3) {
@@ -876,8 +888,6 @@ k_update(const TileArgs a) {
   else FB.meta = 0, FB.role = FR_NONE;
   const bool evA = FA.role == FR_NORMAL || FA.role == FR_CROSS;
   const bool evB = D == 2 && (FB.role == FR_NORMAL || FB.role == FR_CROSS);
-  const bool xA = ML && FA.role == FR_CROSS && (FA.meta & FM_OWNED);
-  const bool xB = ML && D == 2 && FB.role == FR_CROSS && (FB.meta & FM_OWNED);
   // where the fluxes of the own cell's high-side faces are: a face A / B of a neighbour in
   // the tile, or a face C (index ty in the column, TY + tx in the row)
   const bool eInTile = tx < TX - 1, nInTile = ty < TY - 1;
@@ -900,7 +910,6 @@ k_update(const TileArgs a) {
       const long metaC = sXI[qc];
       const int roleC = (int)(metaC >> 5);
       const bool evC = roleC == FR_NORMAL || roleC == FR_CROSS;
-      const bool xC = ML && roleC == FR_CROSS && (metaC & FM_OWNED);
       const long fidC = sXI[2 * NX3 + qc], colC = sXI[3 * NX3 + qc];
       UFace<T> FC;
       const T* X3p = sXP + qc;
@@ -920,7 +929,6 @@ k_update(const TileArgs a) {
         if (evC) face_flux2<T, D, CV>(FC, dirC, sVT[4 * (jb + jj)], sVT[4 * (jb + jj) + 1], gl, hl, c0, twoK, Fg, Fh);
         Cg[jj * NX3 + qc] = Fg;
         Ch[jj * NX3 + qc] = Fh;
-        if (xC && jb + jj < npr) export_x(colC, v, Fg, Fh);
       }
     }
     const int je = min(jb + SC, npr);
@@ -941,14 +949,12 @@ k_update(const TileArgs a) {
       if (!evA) { FAg = ga; FAh = ha; }
       Fg[fA] = FAg;
       Fh[fA] = FAh;
-      if (xA) export_x(FA.col, v, FAg, FAh);
       if (D == 2) {
         V FBg, FBh;
         face_flux2<T, D, CV>(FB, 1, xix, xiy, gbb, hbb, c0, twoK, FBg, FBh);
         if (!evB) { FBg = gbb; FBh = hbb; }
         Fg[fB] = FBg;
         Fh[fB] = FBh;
-        if (xB) export_x(FB.col, v, FBg, FBh);
       }
       // the collision part of phi~+ - phi~ = (4/3) b (phi^S - phi~)
       V gs, hs;
@@ -1029,6 +1035,83 @@ k_update(const TileArgs a) {
     Pp[MO_GYY * ns] = (double)cgyy;
     Pp[MO_JX * ns] = (double)cjx;
     Pp[MO_JY * ns] = (double)cjy;
+  }
+}
+
+// The update of a level that holds every cell: CTA (tile list index, velocity chunk).
+template <class S, class T, int D, int TX, int TY, int VPC, bool CV>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_update(const TileArgs a) {
+  update_tile<S, T, D, TX, TY, VPC, false, CV>(a, a.tiles[blockIdx.x], (int)blockIdx.y);
+}
+
+// The update of every cell level of a multi-level instance in one launch (work items and
+// argument table as k_faces_lv).  The microfluxes of cross-level faces come from the mapped
+// fluxes (Y) of the levels that evaluate them, which k_cross_flux and the mapping produce
+// before this launch.
+template <class S, class T, int D, int TX, int TY, int VPC, bool CV>
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_update_lv(const TileArgs* __restrict__ tab, const int4* __restrict__ work) {
+  __shared__ __align__(16) TileArgs sa;
+  const int4 w = work[blockIdx.x];
+  load_args(sa, tab + w.x);
+  __syncthreads();
+  update_tile<S, T, D, TX, TY, VPC, true, CV>(sa, sa.tiles[w.y], w.z);
+}
+
+// Microfluxes (xi.n) phi of the cross-level faces a level evaluates (Eq. interface_reduced_fluxes
+// on the faces' common refinement space, Sec. 3.4) into the level's X array, from which the
+// mapping takes them to the neighbouring levels.  The faces are interior faces: Eq. recover_phi
+// from the face buffer and the face model, with the operations of k_update's evaluation of
+// the same face, so both sides of the face see one flux.  One thread per X column, kXPairs
+// velocity pairs per CTA; work item (level, first column, first pair, 0).
+constexpr int kXPairs = 32;
+template <class T, int D, bool CV>
+__global__ void __launch_bounds__(128) k_cross_flux(const TileArgs* __restrict__ tab, const int4* __restrict__ work) {
+  using V = V2<T>;
+  using P = Pk<T>;
+  __shared__ __align__(16) TileArgs sa;
+  const int4 w = work[blockIdx.x];
+  load_args(sa, tab + w.x);
+  __syncthreads();
+  const TileArgs& a = sa;
+  const StepConst& k = a.k;
+  const int col = w.y + (int)threadIdx.x;
+  if (col >= a.nX) return;
+  const long nv = k.nv, nvp = (k.nv + 1) / 2, nfc = k.nface;
+  const long fid = a.xfid[col];
+  const T* __restrict__ fp = reinterpret_cast<const T*>(a.fparam);
+  const T* __restrict__ vt = reinterpret_cast<const T*>(a.vt);
+  const T* __restrict__ fbi = reinterpret_cast<const T*>(a.fbar);
+  T* __restrict__ Xo = reinterpret_cast<T*>(a.X);
+  UFace<T> F;
+  F.kind = FK_INTERIOR;
+  F.m.load(fp, nfc, fid);
+  if constexpr (CV) {
+    const T* __restrict__ fg = reinterpret_cast<const T*>(a.fgeo);
+    F.nx = fg[fid];
+    F.ny = fg[nfc + fid];
+    F.area = fg[2 * nfc + fid];
+  }
+  const int dir = fid < (long)k.nfx * k.ny ? 0 : 1;
+  const T c0 = T(k.c0), twoK = T(k.twoK);
+  const int j1 = min((int)nvp, w.z + kXPairs);
+  for (int j = w.z; j < j1; ++j) {
+    const int v = 2 * j;
+    const bool hi = v + 1 < nv;
+    const V xix = P::mk(vt[v], hi ? vt[v + 1] : T(0));
+    const V xiy = (D == 2) ? P::mk(vt[nv + v], hi ? vt[nv + v + 1] : T(0)) : P::splat(T(0));
+    const T* q = fbi + fbar_at(0, v, fid, nvp, nfc);
+    const V gb = *reinterpret_cast<const V*>(q);
+    const V hb = *reinterpret_cast<const V*>(q + 2 * nvp * nfc);
+    V Fg, Fh;
+    face_flux2<T, D, CV>(F, dir, xix, xiy, gb, hb, c0, twoK, Fg, Fh);
+    Xo[(long)v * a.nX + col] = Fg.x;
+    Xo[(nv + v) * a.nX + col] = Fh.x;
+    if (hi) {
+      Xo[(long)(v + 1) * a.nX + col] = Fg.y;
+      Xo[(nv + v + 1) * a.nX + col] = Fh.y;
+    }
   }
 }
 

@@ -111,6 +111,8 @@ struct LevelRt {
   DevBuf wden;               // curvilinear walls: [nface] wall-Maxwellian normalisation
   DevBuf msum;               // [NMOM][max(cells, faces)] chunk sums for the finalisation
   DevBuf flist;              // faces the level evaluates (normal and cross), when not all
+  DevBuf xfid;               // [nX] face id of every column of X
+  std::vector<int> tiles_h;  // the tile list (host copy)
   int nflist = 0;
   int nghost = 0, nX = 0, nY = 0, ntiles = 0;
   int cur = 0, pcur = 0;
@@ -138,8 +140,13 @@ struct Inst {
   DevBuf lvl_of_d, slot_of_d, ucell, W, err, stepctr;
   std::vector<Route> ghosts, fluxes;
   MapBatch gb;
-  std::vector<MapBatch> fb;  // flux routes by source level (only routes[0] is used)
-  std::vector<int> order;    // levels by decreasing velocity count
+  MapBatch fb;               // every flux route in one launch (only routes[0] is used)
+  // multi-level instances: tile arguments [pass][buffer parity 2 cur + pcur][level]; work
+  // items (level, tile list index, velocity chunk, 0) of the faces pass (every level with
+  // tiles) and of the update (tiles with a cell of a cell level); cross-flux items (level,
+  // first X column, first velocity pair, 0)
+  DevBuf tab, wf, wu, wx;
+  int nwf = 0, nwu = 0, nwx = 0;
   int n_int = 0, n_cross = 0;  // interior faces, and those between two levels (Sec. 3.5)
 };
 
@@ -411,20 +418,18 @@ template <class S, class T, int D> struct Runner {
   }
 
   static cudaError_t set_smem_limits() {
-    const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false, false>,
-                         (const void*)k_faces<S, T, D, TX, TY, true, false>,
-                         (const void*)k_update<S, T, D, TX, TY, VPC, false, false>,
-                         (const void*)k_update<S, T, D, TX, TY, VPC, true, false>};
+    const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false>, (const void*)k_faces_lv<S, T, D, TX, TY, false>,
+                         (const void*)k_update<S, T, D, TX, TY, VPC, false>,
+                         (const void*)k_update_lv<S, T, D, TX, TY, VPC, false>};
     for (int i = 0; i < 4; ++i) {
       cudaError_t e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(i < 2 ? SM0 : SMU));
       if (e != cudaSuccess) return e;
     }
     if constexpr (D == 2) {
-      const void* fc[4] = {(const void*)k_faces<S, T, D, TX, TY, false, true>,
-                           (const void*)k_faces<S, T, D, TX, TY, true, true>,
-                           (const void*)k_update<S, T, D, TX, TY, VPC, false, true>,
-                           (const void*)k_update<S, T, D, TX, TY, VPC, true, true>};
+      const void* fc[4] = {(const void*)k_faces<S, T, D, TX, TY, true>, (const void*)k_faces_lv<S, T, D, TX, TY, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, true>,
+                           (const void*)k_update_lv<S, T, D, TX, TY, VPC, true>};
       for (int i = 0; i < 4; ++i) {
         cudaError_t e = cudaFuncSetAttribute(fc[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(i < 2 ? SM0C : SMU));
@@ -434,36 +439,41 @@ template <class S, class T, int D> struct Runner {
     return cudaSuccess;
   }
 
-  // one tile pass (MODE 0: k_faces, MODE 1: k_update): with or without level tables,
+  // one tile pass (MODE 0: k_faces, MODE 1: k_update) of a level that holds every cell,
   // Cartesian or curvilinear
   template <int MODE>
-  static void launch_tile(mlvs_handle* h, const LevelRt& L, dim3 grid, const TileArgs& t, int limiter) {
-    const bool one = single(h, L);
+  static void launch_tile(mlvs_handle* h, dim3 grid, const TileArgs& t, int limiter) {
     if constexpr (D == 2) {
       if (h->curvi) {
-        if constexpr (MODE == 0) {
-          if (one) k_faces<S, T, D, TX, TY, false, true><<<grid, TX * TY, SM0C, h->stream>>>(t, limiter);
-          else k_faces<S, T, D, TX, TY, true, true><<<grid, TX * TY, SM0C, h->stream>>>(t, limiter);
-        } else {
-          if (one) k_update<S, T, D, TX, TY, VPC, false, true><<<grid, TX * TY, SMU, h->stream>>>(t);
-          else k_update<S, T, D, TX, TY, VPC, true, true><<<grid, TX * TY, SMU, h->stream>>>(t);
-        }
+        if constexpr (MODE == 0) k_faces<S, T, D, TX, TY, true><<<grid, TX * TY, SM0C, h->stream>>>(t, limiter);
+        else k_update<S, T, D, TX, TY, VPC, true><<<grid, TX * TY, SMU, h->stream>>>(t);
         return;
       }
     }
-    if constexpr (MODE == 0) {
-      if (one) k_faces<S, T, D, TX, TY, false, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
-      else k_faces<S, T, D, TX, TY, true, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
-    } else {
-      if (one) k_update<S, T, D, TX, TY, VPC, false, false><<<grid, TX * TY, SMU, h->stream>>>(t);
-      else k_update<S, T, D, TX, TY, VPC, true, false><<<grid, TX * TY, SMU, h->stream>>>(t);
+    if constexpr (MODE == 0) k_faces<S, T, D, TX, TY, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
+    else k_update<S, T, D, TX, TY, VPC, false><<<grid, TX * TY, SMU, h->stream>>>(t);
+  }
+
+  // one tile pass over every level of a multi-level instance: n work items, argument table tab
+  template <int MODE>
+  static void launch_lv(mlvs_handle* h, int n, const TileArgs* tab, const int4* w, int limiter) {
+    if constexpr (D == 2) {
+      if (h->curvi) {
+        if constexpr (MODE == 0) k_faces_lv<S, T, D, TX, TY, true><<<n, TX * TY, SM0C, h->stream>>>(tab, w, limiter);
+        else k_update_lv<S, T, D, TX, TY, VPC, true><<<n, TX * TY, SMU, h->stream>>>(tab, w);
+        return;
+      }
     }
+    if constexpr (MODE == 0) k_faces_lv<S, T, D, TX, TY, false><<<n, TX * TY, SM0, h->stream>>>(tab, w, limiter);
+    else k_update_lv<S, T, D, TX, TY, VPC, false><<<n, TX * TY, SMU, h->stream>>>(tab, w);
   }
 
   // a level that holds every cell runs the tile kernels without level tables
   static bool single(const mlvs_handle* h, const LevelRt& L) {
     return L.cells.size() == (size_t)h->nx * h->ny && L.nghost == 0 && L.nX == 0 && L.nY == 0;
   }
+  // every other instance steps through the level-batched launches
+  static bool batched(const mlvs_handle* h, const Inst& I) { return I.lv.size() > 1 || !single(h, I.lv[0]); }
 
   static void mark_begin(mlvs_handle* h, int ph) {
     ++h->launches;
@@ -530,6 +540,7 @@ template <class S, class T, int D> struct Runner {
     t.fslot = L.fslot.as<int>();
     t.X = L.X.p;
     t.nX = L.nX;
+    t.xfid = L.xfid.as<int>();
     t.Y = L.Y.p;
     t.nY = L.nY;
     t.fbar = L.fbar.p;
@@ -653,41 +664,97 @@ template <class S, class T, int D> struct Runner {
     return G;
   }
 
-  // route arguments and item groups of the batched flux launch of every source level
+  // route arguments and item groups of the batched flux launch (every route)
   static cudaError_t flux_batch(mlvs_handle* h, Inst& I) {
-    I.fb.clear();
-    I.fb.resize(I.lv.size());
-    for (int src = 0; src < (int)I.lv.size(); ++src) {
-      std::vector<const Route*> rs;
-      for (auto& r : I.fluxes)
-        if (r.src == src && !r.items.empty()) rs.push_back(&r);
-      if (rs.empty()) continue;
-      MapBatch& B = I.fb[src];
-      std::vector<MapWork> work;
-      B.G = group_items(rs, work);
-      std::vector<MapArgs> tab;
-      for (const Route* r : rs) {
-        LevelRt& Ls = I.lv[r->src];
-        LevelRt& Ld = I.lv[r->dst];
-        CSR* c = nullptr;
-        if (get_csr(h, Ls.space, Ld.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
-        MapArgs m = margs(h, Ls.space, Ld.space, c);
-        m.src = Ls.X.p;
-        m.src_ld = Ls.nX;
-        m.dst = Ld.Y.p;
-        m.dst_ld = Ld.nY;
-        m.prm = Ls.fprm.p;
-        m.prm_ld = Ls.k.nface;
-        m.items = r->items_d.as<MapItem>();
-        m.nitems = (int)r->items.size();
-        tab.push_back(m);
-      }
-      cudaError_t e = upload(B.routes[0], tab, h->stream);
-      if (e != cudaSuccess) return e;
-      if ((e = upload(B.work, work, h->stream)) != cudaSuccess) return e;
-      B.nwork = (int)work.size();
-      B.ok = true;
+    MapBatch& B = I.fb;
+    B.ok = false;
+    B.nwork = 0;
+    std::vector<const Route*> rs;
+    for (auto& r : I.fluxes)
+      if (!r.items.empty()) rs.push_back(&r);
+    if (rs.empty()) return cudaSuccess;
+    std::vector<MapWork> work;
+    B.G = group_items(rs, work);
+    std::vector<MapArgs> tab;
+    for (const Route* r : rs) {
+      LevelRt& Ls = I.lv[r->src];
+      LevelRt& Ld = I.lv[r->dst];
+      CSR* c = nullptr;
+      if (get_csr(h, Ls.space, Ld.space, &c) != MLVS_OK) return cudaErrorInvalidValue;
+      MapArgs m = margs(h, Ls.space, Ld.space, c);
+      m.src = Ls.X.p;
+      m.src_ld = Ls.nX;
+      m.dst = Ld.Y.p;
+      m.dst_ld = Ld.nY;
+      m.prm = Ls.fprm.p;
+      m.prm_ld = Ls.k.nface;
+      m.items = r->items_d.as<MapItem>();
+      m.nitems = (int)r->items.size();
+      tab.push_back(m);
     }
+    cudaError_t e = upload(B.routes[0], tab, h->stream);
+    if (e != cudaSuccess) return e;
+    if ((e = upload(B.work, work, h->stream)) != cudaSuccess) return e;
+    B.nwork = (int)work.size();
+    B.ok = true;
+    return cudaSuccess;
+  }
+
+  // argument table and work items of the level-batched tile launches (multi-level
+  // instances).  Items go in decreasing order of their velocity count, so that the longest
+  // start first.  The instance must be in h->inst with all its buffers allocated (the table
+  // holds their addresses and the instance's random-bit salt).
+  static cudaError_t tile_batch(mlvs_handle* h, Inst& I) {
+    I.nwf = I.nwu = I.nwx = 0;
+    const int nl = (int)I.lv.size();
+    if (!batched(h, I)) return cudaSuccess;
+    std::vector<TileArgs> tab((size_t)2 * 4 * nl);
+    for (int mode = 0; mode < 2; ++mode)
+      for (int par = 0; par < 4; ++par)
+        for (int l = 0; l < nl; ++l) {
+          LevelRt& L = I.lv[l];
+          const int cur = L.cur, pcur = L.pcur;
+          L.cur = par >> 1;
+          L.pcur = par & 1;
+          TileArgs t = targs(h, I, L, l);
+          L.cur = cur;
+          L.pcur = pcur;
+          t.part = mode == 0 ? L.fpart.as<double>() : L.cpart.as<double>();
+          // every address a kernel of the work lists dereferences must exist
+          const bool cells = !L.cells.empty(), tiles = L.ntiles > 0;
+          if ((tiles && (!t.tiles || !t.lvl_of || !t.slot_of || !t.frole || !t.fslot || !t.vt || !t.part ||
+                         !t.fparam || !t.fbar || !t.ucell || !t.step)) ||
+              (tiles && h->curvi && (!t.cgeo || !t.fgeo)) ||
+              (cells && (!t.f_in || !t.f_out || !t.cparam)) || (L.nghost > 0 && (!t.ghost || !t.ghost_of)) ||
+              (L.nX > 0 && (!t.X || !t.xfid)) || (L.nY > 0 && !t.Y))
+            return cudaErrorInvalidValue;
+          tab[((size_t)mode * 4 + par) * nl + l] = t;
+        }
+    std::vector<int> ord(nl);
+    for (int l = 0; l < nl; ++l) ord[l] = l;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return I.lv[a].k.vpc > I.lv[b].k.vpc; });
+    std::vector<int4> wf, wu, wx;
+    for (int l : ord) {
+      const LevelRt& L = I.lv[l];
+      std::set<int> with_cells;
+      for (int c : L.cells) with_cells.insert(((c / h->nx) / TY) * ((h->nx + TX - 1) / TX) + (c % h->nx) / TX);
+      for (int c = 0; c < L.k.nchunk; ++c)
+        for (int ti = 0; ti < L.ntiles; ++ti) {
+          wf.push_back(make_int4(l, ti, c, 0));
+          if (with_cells.count(L.tiles_h[ti])) wu.push_back(make_int4(l, ti, c, 0));
+        }
+      const int npair = (L.k.nv + 1) / 2;
+      for (int c0 = 0; c0 < L.nX; c0 += 128)
+        for (int p0 = 0; p0 < npair; p0 += kXPairs) wx.push_back(make_int4(l, c0, p0, 0));
+    }
+    cudaError_t e;
+    if ((e = upload(I.tab, tab, h->stream)) != cudaSuccess) return e;
+    if ((e = upload(I.wf, wf, h->stream)) != cudaSuccess) return e;
+    if ((e = upload(I.wu, wu, h->stream)) != cudaSuccess) return e;
+    if ((e = upload(I.wx, wx, h->stream)) != cudaSuccess) return e;
+    I.nwf = (int)wf.size();
+    I.nwu = (int)wu.size();
+    I.nwx = (int)wx.size();
     return cudaSuccess;
   }
 
@@ -749,10 +816,11 @@ template <class S, class T, int D> struct Runner {
     return cudaGetLastError();
   }
 
-  static cudaError_t run_fluxes(mlvs_handle* h, Inst& I, int src) {
+  // the cross-level microfluxes X of every level mapped to the receiving levels' Y
+  static cudaError_t run_fluxes(mlvs_handle* h, Inst& I) {
     const bool nine = D == 2 && h->cfg.map_moments == 9;
-    if (src < (int)I.fb.size() && I.fb[src].ok && !nine) {
-      const MapBatch& B = I.fb[src];
+    if (I.fb.ok && !nine) {
+      const MapBatch& B = I.fb;
       const MapArgs* rt = B.routes[0].as<MapArgs>();
       const MapWork* wk = B.work.as<MapWork>();
       const int nb = std::max(1, std::min(B.nwork, 148 * 16));
@@ -767,7 +835,7 @@ template <class S, class T, int D> struct Runner {
       return cudaGetLastError();
     }
     for (auto& r : I.fluxes) {
-      if (r.src != src || r.items.empty()) continue;
+      if (r.items.empty()) continue;
       LevelRt& Ls = I.lv[r.src];
       LevelRt& Ld = I.lv[r.dst];
       CSR* c = nullptr;
@@ -789,6 +857,51 @@ template <class S, class T, int D> struct Runner {
     return cudaGetLastError();
   }
 
+  // faces of every level, face finalisation, cross-level microfluxes and their mapping, then
+  // the update of every cell level: one launch per tile pass over all levels' work items.
+  // The cell levels' buffers advance together, so one parity selects the argument table.
+  static cudaError_t step_levels(mlvs_handle* h, Inst& I, int limiter) {
+    int par = -1;
+    for (const LevelRt& L : I.lv) {
+      if (L.cells.empty()) continue;
+      const int p = 2 * L.cur + L.pcur;
+      if (par < 0) par = p;
+      else if (p != par) return cudaErrorInvalidValue;
+    }
+    par = std::max(par, 0);
+    const size_t nl = I.lv.size();
+    const TileArgs* tab = I.tab.as<TileArgs>();
+    if (I.nwf > 0) {
+      mark_begin(h, 1);
+      launch_lv<0>(h, I.nwf, tab + (size_t)par * nl, I.wf.as<int4>(), limiter);
+      mark_end(h);
+    }
+    for (LevelRt& L : I.lv) {
+      if (L.ntiles == 0) continue;
+      PointArgs a = pargs(h, I, L, true);
+      a.cprm = L.prm[L.pcur].p;
+      a.prm_out = L.fprm.p;
+      mark_begin(h, 2);
+      launch_finalize(h, a, L);
+      mark_end(h);
+    }
+    if (I.nwx > 0) {
+      mark_begin(h, 5);
+      const TileArgs* t1 = tab + (size_t)(4 + par) * nl;
+      if (D == 2 && h->curvi) k_cross_flux<T, D, true><<<I.nwx, 128, 0, h->stream>>>(t1, I.wx.as<int4>());
+      else k_cross_flux<T, D, false><<<I.nwx, 128, 0, h->stream>>>(t1, I.wx.as<int4>());
+      mark_end(h);
+    }
+    cudaError_t e = run_fluxes(h, I);
+    if (e != cudaSuccess) return e;
+    if (I.nwu > 0) {
+      mark_begin(h, 3);
+      launch_lv<1>(h, I.nwu, tab + (size_t)(4 + par) * nl, I.wu.as<int4>(), limiter);
+      mark_end(h);
+    }
+    return cudaGetLastError();
+  }
+
   static cudaError_t step(mlvs_handle* h, Inst& I) {
     cudaError_t e;
     if constexpr (sizeof(S) <= 4) {   // random bits of the stochastic rounding (BF16, FP32)
@@ -799,37 +912,27 @@ template <class S, class T, int D> struct Runner {
       if (!I.lv[l].fresh && (e = finalize_cells(h, I, I.lv[l])) != cudaSuccess) return e;
     if ((e = run_ghosts(h, I)) != cudaSuccess) return e;
     const int limiter = h->cfg.limiter;
-    for (int l = 0; l < (int)I.lv.size(); ++l) {
-      LevelRt& L = I.lv[l];
-      if (L.ntiles == 0) continue;
-      TileArgs t = targs(h, I, L, l);
+    if (batched(h, I)) {
+      if ((e = step_levels(h, I, limiter)) != cudaSuccess) return e;
+    } else if (I.lv[0].ntiles > 0) {
+      // one level holding every cell: the tile kernels without level tables
+      LevelRt& L = I.lv[0];
+      TileArgs t = targs(h, I, L, 0);
       t.part = L.fpart.as<double>();
-      dim3 grid(L.ntiles, L.k.nchunk);
+      const dim3 grid(L.ntiles, L.k.nchunk);
       mark_begin(h, 1);
-      launch_tile<0>(h, L, grid, t, limiter);
+      launch_tile<0>(h, grid, t, limiter);
       mark_end(h);
-    }
-    for (int l = 0; l < (int)I.lv.size(); ++l) {
-      LevelRt& L = I.lv[l];
-      if (L.ntiles == 0) continue;
       PointArgs a = pargs(h, I, L, true);
       a.cprm = L.prm[L.pcur].p;
       a.prm_out = L.fprm.p;
       mark_begin(h, 2);
       launch_finalize(h, a, L);
       mark_end(h);
-    }
-    for (int l : I.order) {
-      LevelRt& L = I.lv[l];
-      if (L.ntiles > 0) {
-        TileArgs t = targs(h, I, L, l);
-        t.part = L.cpart.as<double>();
-        dim3 grid(L.ntiles, L.k.nchunk);
-        mark_begin(h, 3);
-        launch_tile<1>(h, L, grid, t, limiter);
-        mark_end(h);
-      }
-      if ((e = run_fluxes(h, I, l)) != cudaSuccess) return e;
+      t.part = L.cpart.as<double>();
+      mark_begin(h, 3);
+      launch_tile<1>(h, grid, t, limiter);
+      mark_end(h);
     }
     for (int l = 0; l < h->n_levels; ++l) {
       LevelRt& L = I.lv[l];
@@ -1038,12 +1141,13 @@ struct Ops {
   cudaError_t (*wall_table)(mlvs_handle*, LevelRt&);
   cudaError_t (*ghost_batch)(mlvs_handle*, Inst&);
   cudaError_t (*flux_batch)(mlvs_handle*, Inst&);
+  cudaError_t (*tile_batch)(mlvs_handle*, Inst&);
 };
 
 template <class S, class T, int D> Ops make_ops() {
   using R = Runner<S, T, D>;
   return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion,
-             &R::wall_table, &R::ghost_batch, &R::flux_batch};
+             &R::wall_table, &R::ghost_batch, &R::flux_batch, &R::tile_batch};
 }
 
 Ops ops_for(int storage, int D) {
@@ -1225,6 +1329,8 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     I.fluxes.push_back(std::move(r));
   }
   // tiles: tiles with a cell of the level or owning a face evaluated on it
+  std::vector<std::vector<int>> tls(nlev);
+  int all_tiles = 0;
   for (int l = 0; l < nlev; ++l) {
     std::set<int> ts;
     for (int c : I.lv[l].cells) ts.insert(((c / nx) / TY) * ntx + (c % nx) / TX);
@@ -1235,8 +1341,13 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
       else { const int r = f - nfx * ny; col = r % nx; row = std::min(r / nx, ny - 1); }
       ts.insert((row / TY) * ntx + col / TX);
     }
-    std::vector<int> tl(ts.begin(), ts.end());
+    tls[l].assign(ts.begin(), ts.end());
+    all_tiles += (int)tls[l].size();
+  }
+  for (int l = 0; l < nlev; ++l) {
+    const std::vector<int>& tl = tls[l];
     I.lv[l].ntiles = (int)tl.size();
+    I.lv[l].tiles_h = tl;
     I.lv[l].nX = nX[l];
     I.lv[l].nY = nY[l];
     LevelRt& L = I.lv[l];
@@ -1251,7 +1362,8 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     k.dx = h->dx; k.dy = h->dy; k.dt = h->dt;
     k.c0 = h->gas.K + 3.0 - D;
     k.twoK = 2.0 * h->gas.K;
-    k.vpc = choose_vpc(L.ntiles, k.nv, h->cta_target);
+    // every level's tiles go in one launch: the chunking aims at the CTA target over all of them
+    k.vpc = choose_vpc(all_tiles, k.nv, h->cta_target);
     k.nchunk = (k.nv + k.vpc - 1) / k.vpc;
     // device tables
     CK(upload(L.tiles, tl, h->stream));
@@ -1266,6 +1378,12 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     }
     CK(upload(L.fslot, slot[l], h->stream));
     CK(upload(L.ghost_of, ghost_col[l], h->stream));
+    {
+      std::vector<int> xf(nX[l], 0);
+      for (int f = 0; f < nface; ++f)
+        if (role[l][f] == FR_CROSS) xf[slot[l][f]] = f;
+      CK(upload(L.xfid, xf, h->stream));
+    }
     const size_t nc = L.cells.size();
     const size_t fbytes = 2ull * k.nv * nc * h->ssize;
     if (L.f[0].alloc(fbytes) != cudaSuccess || L.f[1].alloc(fbytes) != cudaSuccess ||
@@ -1293,11 +1411,6 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
   for (auto& r : I.fluxes) CK(upload(r.items_d, r.items, h->stream));
   CK(ops_for(h->cfg.storage, D).ghost_batch(h, I));
   CK(ops_for(h->cfg.storage, D).flux_batch(h, I));
-  I.order.resize(nlev);
-  for (int l = 0; l < nlev; ++l) I.order[l] = l;
-  std::stable_sort(I.order.begin(), I.order.end(), [&](int a, int b) {
-    return h->spaces[I.lv[a].space].vs.nv() > h->spaces[I.lv[b].space].vs.nv();
-  });
   CK(upload(I.lvl_of_d, I.lvl_of, h->stream));
   CK(upload(I.slot_of_d, I.slot_of, h->stream));
   return MLVS_OK;
@@ -1682,6 +1795,7 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
     CK(cudaMemsetAsync(I.err.p, 0, ERR_WORDS * sizeof(int), h->stream));
     CK(cudaMemsetAsync(I.stepctr.p, 0, sizeof(unsigned), h->stream));
     CK(cudaMemsetAsync(I.W.p, 0, I.W.n, h->stream));
+    CK(ops.tile_batch(h, I));   // the instance in place, every buffer allocated
     DevBuf dW0;
     CK(upload(dW0, std::vector<double>(h->initW.begin() + 4ull * ncell * i, h->initW.begin() + 4ull * ncell * (i + 1)),
               h->stream));
@@ -1720,6 +1834,7 @@ extern "C" mlvs_status mlvs_set_cell_levels(mlvs_handle* h, int instance, const 
   CK(ops.moments_of_levels(h, New));
   CK(cudaStreamSynchronize(h->stream));
   h->inst[instance] = std::move(New);
+  CK(ops.tile_batch(h, h->inst[instance]));   // the instance in place, every buffer allocated
   return check_flags(h);
 }
 
@@ -1857,6 +1972,10 @@ static mlvs_status apply_levels(mlvs_handle* h, const std::vector<int>& new_spac
         return fail(h, MLVS_ERR_SINGULAR, "nine-moment level switch: singular correction block");
       }
       h->inst[i] = std::move(New);
+      if ((e = ops.tile_batch(h, h->inst[i])) != cudaSuccess) {   // the instance in place
+        h->sticky = MLVS_ERR_CUDA;
+        return fail(h, MLVS_ERR_CUDA, std::string("tile tables: ") + cudaGetErrorString(e));
+      }
     }
   }
   if (stats) {
@@ -2369,15 +2488,18 @@ static mlvs_status rechunk(mlvs_handle* h) {
   for (auto& I : h->inst) {
     for (int l = 0; l < h->n_levels; ++l)
       if (!I.lv[l].fresh) CK(ops.finalize_cells(h, I, I.lv[l]));
+    int all_tiles = 0;
+    for (auto& L : I.lv) all_tiles += L.ntiles;
     for (auto& L : I.lv) {
       StepConst& k = L.k;
-      k.vpc = choose_vpc(L.ntiles, k.nv, h->cta_target);
+      k.vpc = choose_vpc(all_tiles, k.nv, h->cta_target);
       k.nchunk = (k.nv + k.vpc - 1) / k.vpc;
       const size_t nc = std::max<size_t>(L.cells.size(), 1);
       if (L.cpart.alloc((size_t)k.nchunk * NMOM * nc * 8) != cudaSuccess ||
           L.fpart.alloc((size_t)k.nchunk * NMOM * k.nface * 8) != cudaSuccess)
         return fail(h, MLVS_ERR_OOM, "device allocation of partial sums failed");
     }
+    CK(ops.tile_batch(h, I));
     CK(ops.moments_of_levels(h, I));
   }
   CK(cudaStreamSynchronize(h->stream));
