@@ -323,6 +323,20 @@ __device__ __forceinline__ V2<T> limited2(V2<T> a, V2<T> b, T inv_h, int limiter
 // physical slopes with the cell's J^{-T}, faces with their own normals, areas and centroid
 // offsets (precomputed per face, so the two tiles of a face read the same values).
 //
+// Copy a level's tile arguments into shared memory (all threads; a barrier must follow).
+__device__ __forceinline__ void load_args(TileArgs& dst, const TileArgs* __restrict__ src) {
+  static_assert(sizeof(TileArgs) % 8 == 0, "tile arguments are copied in 8-byte words");
+  constexpr int NW = (int)(sizeof(TileArgs) / 8);
+  for (int i = threadIdx.x; i < NW; i += blockDim.x)
+    reinterpret_cast<unsigned long long*>(&dst)[i] = reinterpret_cast<const unsigned long long*>(src)[i];
+}
+
+// The tile passes run in two forms.  ML = false (a level that holds every cell): the level's
+// arguments are the kernel parameter a_, CTA (tile list index, velocity chunk) = (blockIdx.x,
+// blockIdx.y).  ML = true (every level of a multi-level instance in one launch): CTA b takes
+// work item work[b] = (level, tile list index, velocity chunk, 0) and the level's arguments
+// tab[level], copied to shared memory.
+
 // Per round (one velocity pair): every thread stages phi-bar-plus of its own cell, and the
 // first NH threads of one halo cell, into the box (one barrier; the box is double-buffered);
 // then each thread reconstructs its cell's two low-side faces (A: x-face, B: y-face) from the
@@ -332,7 +346,21 @@ __device__ __forceinline__ V2<T> limited2(V2<T> a, V2<T> b, T inv_h, int limiter
 // lane is reconstructed on its own.  Warp 0 of a tile whose high edge is a non-periodic mesh
 // end does the same for the faces on that edge.
 template <class S, class T, int D, int TX, int TY, bool ML, bool CV>
-__device__ __forceinline__ void faces_tile(const TileArgs& a, const int tile, const int chunk, int limiter) {
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restrict__ work, int limiter) {
+  __shared__ __align__(16) TileArgs sa;
+  int tile, chunk;
+  if constexpr (ML) {
+    const int4 w = work[blockIdx.x];
+    load_args(sa, tab + w.x);
+    __syncthreads();
+    tile = sa.tiles[w.y];
+    chunk = w.z;
+  } else {
+    tile = a_.tiles[blockIdx.x];
+    chunk = (int)blockIdx.y;
+  }
+  const TileArgs& a = ML ? sa : a_;
   using G = TileGeom<TX, TY, D>;
   using B = FaceBox<TX, TY, D>;
   using L = TileSmem<T, TX, TY, D, CV>;
@@ -676,33 +704,6 @@ __device__ __forceinline__ void faces_tile(const TileArgs& a, const int tile, co
   if (FC.meta) write_partials_smem<T, D>(sAcc + tid, L::NX3, a.part + (long)chunk * NMOM * k.nface + FC.fid, k.nface);
 }
 
-// Copy a level's tile arguments into shared memory (all threads; a barrier must follow).
-__device__ __forceinline__ void load_args(TileArgs& dst, const TileArgs* __restrict__ src) {
-  static_assert(sizeof(TileArgs) % 8 == 0, "tile arguments are copied in 8-byte words");
-  constexpr int NW = (int)(sizeof(TileArgs) / 8);
-  for (int i = threadIdx.x; i < NW; i += blockDim.x)
-    reinterpret_cast<unsigned long long*>(&dst)[i] = reinterpret_cast<const unsigned long long*>(src)[i];
-}
-
-// The faces pass of a level that holds every cell: CTA (tile list index, velocity chunk).
-template <class S, class T, int D, int TX, int TY, bool CV>
-__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
-k_faces(const TileArgs a, int limiter) {
-  faces_tile<S, T, D, TX, TY, false, CV>(a, a.tiles[blockIdx.x], (int)blockIdx.y, limiter);
-}
-
-// The faces pass of every level of a multi-level instance in one launch: CTA b takes work
-// item (level, tile list index, velocity chunk) = work[b] with the level's arguments tab[level].
-template <class S, class T, int D, int TX, int TY, bool CV>
-__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
-k_faces_lv(const TileArgs* __restrict__ tab, const int4* __restrict__ work, int limiter) {
-  __shared__ __align__(16) TileArgs sa;
-  const int4 w = work[blockIdx.x];
-  load_args(sa, tab + w.x);
-  __syncthreads();
-  faces_tile<S, T, D, TX, TY, true, CV>(sa, sa.tiles[w.y], w.z, limiter);
-}
-
 // One face of k_update as a thread holds it: metadata, the model parameters of an evaluated
 // face, and on curvilinear meshes its unit normal and area.
 template <class T> struct UFace {
@@ -757,9 +758,24 @@ __device__ __forceinline__ void face_flux2(const UFace<T>& F, int dir, V2<T> xix
 // memory (double-buffered: one barrier per round).  The tile's high-side faces C (the column
 // li = TX and the row lj = TY) are evaluated for a sub-chunk of SC pairs at a time by every
 // thread (face tid % NX3, pairs tid / NX3 + k NT / NX3), so the work per round is the same in
-// every warp.  Requires k.vpc <= VPC.
+// every warp.  A face received from another level takes the microflux mapped to this level
+// (Y), which k_cross_flux and the mapping produce before the launch.  Requires k.vpc <= VPC.
 template <class S, class T, int D, int TX, int TY, int VPC, bool ML, bool CV>
-__device__ __forceinline__ void update_tile(const TileArgs& a, const int tile, const int chunk) {
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
+k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restrict__ work) {
+  __shared__ __align__(16) TileArgs sa;
+  int tile, chunk;
+  if constexpr (ML) {
+    const int4 w = work[blockIdx.x];
+    load_args(sa, tab + w.x);
+    __syncthreads();
+    tile = sa.tiles[w.y];
+    chunk = w.z;
+  } else {
+    tile = a_.tiles[blockIdx.x];
+    chunk = (int)blockIdx.y;
+  }
+  const TileArgs& a = ML ? sa : a_;
   using G = TileGeom<TX, TY, D>;
   using L = UpdSmem<T, TX, TY, D, VPC>;
   using V = V2<T>;
@@ -1036,27 +1052,6 @@ __device__ __forceinline__ void update_tile(const TileArgs& a, const int tile, c
     Pp[MO_JX * ns] = (double)cjx;
     Pp[MO_JY * ns] = (double)cjy;
   }
-}
-
-// The update of a level that holds every cell: CTA (tile list index, velocity chunk).
-template <class S, class T, int D, int TX, int TY, int VPC, bool CV>
-__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
-k_update(const TileArgs a) {
-  update_tile<S, T, D, TX, TY, VPC, false, CV>(a, a.tiles[blockIdx.x], (int)blockIdx.y);
-}
-
-// The update of every cell level of a multi-level instance in one launch (work items and
-// argument table as k_faces_lv).  The microfluxes of cross-level faces come from the mapped
-// fluxes (Y) of the levels that evaluate them, which k_cross_flux and the mapping produce
-// before this launch.
-template <class S, class T, int D, int TX, int TY, int VPC, bool CV>
-__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
-k_update_lv(const TileArgs* __restrict__ tab, const int4* __restrict__ work) {
-  __shared__ __align__(16) TileArgs sa;
-  const int4 w = work[blockIdx.x];
-  load_args(sa, tab + w.x);
-  __syncthreads();
-  update_tile<S, T, D, TX, TY, VPC, true, CV>(sa, sa.tiles[w.y], w.z);
 }
 
 // Microfluxes (xi.n) phi of the cross-level faces a level evaluates (Eq. interface_reduced_fluxes

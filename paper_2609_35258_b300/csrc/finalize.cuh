@@ -57,9 +57,9 @@ struct PointArgs {
   int* need;            // split finalisation: [npt] what the velocity sums are for
 };
 
-// Split finalisation of spaces that are not tensor products: k_fin_pre (thread per point:
-// state, uncorrected model), k_fin_sums (warp per point: the velocity sums), k_fin_post
-// (thread per point: correction).  Scratch rows: rho ux uy T, then G[5][5], H[3][3], den.
+// Split finalisation: k_fin_pre (thread per point: state, uncorrected model), k_fin_sums (warp
+// per point: the velocity sums, or on tensor-product spaces the one-axis sums), k_fin_post
+// (thread per point: correction).  k_finalize does all three in one thread per point.  Scratch rows: rho ux uy T, then G[5][5], H[3][3], den.
 enum { FS_RHO = 0, FS_UX, FS_UY, FS_T, FS_G = 4, FS_H = 29, FS_DEN = 38, FIN_SCR = 39 };
 
 enum { ERR_NONFINITE = 1, ERR_POSITIVITY = 2, ERR_SINGULAR = 4 };
@@ -169,6 +169,51 @@ __device__ inline void axis_sums(const T* ax, int nax, T u, T inv2RT, T lnh, dou
   for (int a = 0; a < 8; ++a) S[a] = acc[a].val();
 }
 
+// A compensated sum merged over the LANES lanes of a warp segment (xor butterfly): each merge
+// keeps its own rounding error exactly (TwoSum) in the compensation, and every lane receives
+// the same value.  FP64 sums carry no compensation and are added directly.
+template <int LANES, class T>
+__device__ __forceinline__ double ksum_lanes(const KSum<T>& k) {
+  if constexpr (sizeof(T) == 8) {
+    double x = k.val();
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  } else {
+    T s = k.s, c = k.c;
+#pragma unroll
+    for (int o = LANES / 2; o > 0; o >>= 1) {
+      const T so = __shfl_xor_sync(0xffffffffu, s, o), co = __shfl_xor_sync(0xffffffffu, c, o);
+      const T t = s + so;
+      const T bb = t - s;
+      const T e = (s - (t - bb)) + (so - bb);   // t + e = s + so exactly
+      c = (c + co) - e;
+      s = t;
+    }
+    return (double)s - (double)c;
+  }
+}
+
+// axis_sums split over the LANES lanes of a warp segment: lane j takes the points j, j + LANES,
+// ...; every lane receives S.
+template <class T, int LANES>
+__device__ inline void axis_sums_lanes(const T* ax, int nax, T u, T inv2RT, T lnh, int lane, double S[8]) {
+  KSum<T> acc[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) acc[a].zero();
+  for (int i = lane; i < nax; i += LANES) {
+    const T c = ax[i] - u;
+    T p = ax[nax + i] * Num<T>::gauss(c, inv2RT, lnh);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      acc[a].add(p);
+      p *= c;
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) S[a] = ksum_lanes<LANES, T>(acc[a]);
+}
+
 // Sum over the LANES lanes of a warp segment in the compute type (all lanes receive it).
 template <int LANES, class T>
 __device__ __forceinline__ T lane_sum_t(T x) {
@@ -181,17 +226,9 @@ __device__ __forceinline__ T lane_sum_t(T x) {
 //   G[a][b] = sum w g^S c_x^a c_y^b (a+b <= 4),  H[a][b] = sum w h^S c_x^a c_y^b (a+b <= 2),
 // on a tensor-product space from the one-axis sums.
 template <class T, int D>
-__device__ inline void axis_moments(const PointArgs& A, const MP<T>& mp, double G[5][5], double H[3][3]) {
+__device__ inline void axis_combine(const PointArgs& A, const MP<T>& mp, const double Sx[8], const double Sy[8],
+                                    double G[5][5], double H[3][3]) {
   const StepConst& k = A.k;
-  const T* ax = reinterpret_cast<const T*>(A.ax);
-  double Sx[8], Sy[8];
-  axis_sums<T>(ax, k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
-  if (D == 2) {
-    axis_sums<T>(ax, k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
-  } else {
-    Sy[0] = 1.0;
-    for (int b = 1; b < 8; ++b) Sy[b] = 0.0;
-  }
   const double kx = (double)mp.kqx, ky = (double)mp.kqy;
   const double i2 = 2.0 * (double)mp.inv2RT;      // 1/RT as the tile kernels form it
   const double RT = (double)mp.RT, c0 = k.c0;
@@ -208,6 +245,21 @@ __device__ inline void axis_moments(const PointArgs& A, const MP<T>& mp, double 
       G[a][b] = Sx[a] * Sy[b] - (D + 2) * lin + i2 * cub;
       if (a + b < 3) H[a][b] = RT * c0 * Sx[a] * Sy[b] + al * cub - be * lin;
     }
+}
+
+template <class T, int D>
+__device__ inline void axis_moments(const PointArgs& A, const MP<T>& mp, double G[5][5], double H[3][3]) {
+  const StepConst& k = A.k;
+  const T* ax = reinterpret_cast<const T*>(A.ax);
+  double Sx[8], Sy[8];
+  axis_sums<T>(ax, k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
+  if (D == 2) {
+    axis_sums<T>(ax, k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
+  } else {
+    Sy[0] = 1.0;
+    for (int b = 1; b < 8; ++b) Sy[b] = 0.0;
+  }
+  axis_combine<T, D>(A, mp, Sx, Sy, G, H);
 }
 
 // The same moments summed directly over the velocities, two at a time: lane `lane` of LANES
@@ -671,7 +723,22 @@ __global__ void k_fin_sums(const PointArgs a) {
     return;
   }
   double G[5][5], H[3][3];
-  direct_moments<T, D, 32>(a, q, lane, G, H);
+  if (a.k.nax > 0) {
+    // tensor-product space: the one-axis sums over the lanes, combined on lane 0
+    const T* ax = reinterpret_cast<const T*>(a.ax);
+    double Sx[8], Sy[8];
+    axis_sums_lanes<T, 32>(ax, a.k.nax, q.ux, q.inv2RT, q.lnh, lane, Sx);
+    if (D == 2) {
+      axis_sums_lanes<T, 32>(ax, a.k.nax, q.uy, q.inv2RT, q.lnh, lane, Sy);
+    } else {
+      Sy[0] = 1.0;
+      for (int b = 1; b < 8; ++b) Sy[b] = 0.0;
+    }
+    if (lane != 0) return;
+    axis_combine<T, D>(a, q, Sx, Sy, G, H);
+  } else {
+    direct_moments<T, D, 32>(a, q, lane, G, H);
+  }
   if (lane == 0) {
 #pragma unroll
     for (int r = 0; r < 25; ++r) a.scr[(FS_G + r) * n + i] = G[r / 5][r % 5];

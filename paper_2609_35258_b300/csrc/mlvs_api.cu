@@ -393,8 +393,11 @@ template <class S, class T, int D> struct Runner {
   static constexpr size_t SMU = UpdSmem<T, TX, TY, D, VPC>::BYTES;
   static constexpr int FIN_BLOCK = 64;
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
-  // tensor-product spaces: one kernel (one-axis sums per thread); others: the split path
-  // (state per thread, velocity sums per warp, correction per thread)
+  // Tensor-product spaces with many points: one thread per point (one-axis sums in the
+  // thread).  Otherwise the split path: state per thread, velocity sums per warp (on tensor-
+  // product spaces the one-axis sums over the warp's lanes), correction per thread, which
+  // spreads a small launch's sums over more of the GPU.
+  static constexpr int kFinThreadMin = 4096;
   static void launch_finalize(mlvs_handle* h, PointArgs a, LevelRt& L) {
     // chunk sums first (many threads), then the finalisation reads them
     if (a.nwork <= 0) return;
@@ -405,7 +408,7 @@ template <class S, class T, int D> struct Runner {
                                                                          L.msum.as<double>());
       a.msum = L.msum.as<double>();
     }
-    if (a.k.nax > 0) {
+    if (a.k.nax > 0 && a.nwork >= kFinThreadMin) {
       k_finalize<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
       return;
     }
@@ -418,18 +421,20 @@ template <class S, class T, int D> struct Runner {
   }
 
   static cudaError_t set_smem_limits() {
-    const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false>, (const void*)k_faces_lv<S, T, D, TX, TY, false>,
-                         (const void*)k_update<S, T, D, TX, TY, VPC, false>,
-                         (const void*)k_update_lv<S, T, D, TX, TY, VPC, false>};
+    const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false, false>,
+                         (const void*)k_faces<S, T, D, TX, TY, true, false>,
+                         (const void*)k_update<S, T, D, TX, TY, VPC, false, false>,
+                         (const void*)k_update<S, T, D, TX, TY, VPC, true, false>};
     for (int i = 0; i < 4; ++i) {
       cudaError_t e = cudaFuncSetAttribute(fn[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)(i < 2 ? SM0 : SMU));
       if (e != cudaSuccess) return e;
     }
     if constexpr (D == 2) {
-      const void* fc[4] = {(const void*)k_faces<S, T, D, TX, TY, true>, (const void*)k_faces_lv<S, T, D, TX, TY, true>,
-                           (const void*)k_update<S, T, D, TX, TY, VPC, true>,
-                           (const void*)k_update_lv<S, T, D, TX, TY, VPC, true>};
+      const void* fc[4] = {(const void*)k_faces<S, T, D, TX, TY, false, true>,
+                           (const void*)k_faces<S, T, D, TX, TY, true, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, false, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, true, true>};
       for (int i = 0; i < 4; ++i) {
         cudaError_t e = cudaFuncSetAttribute(fc[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)(i < 2 ? SM0C : SMU));
@@ -445,27 +450,30 @@ template <class S, class T, int D> struct Runner {
   static void launch_tile(mlvs_handle* h, dim3 grid, const TileArgs& t, int limiter) {
     if constexpr (D == 2) {
       if (h->curvi) {
-        if constexpr (MODE == 0) k_faces<S, T, D, TX, TY, true><<<grid, TX * TY, SM0C, h->stream>>>(t, limiter);
-        else k_update<S, T, D, TX, TY, VPC, true><<<grid, TX * TY, SMU, h->stream>>>(t);
+        if constexpr (MODE == 0)
+          k_faces<S, T, D, TX, TY, false, true><<<grid, TX * TY, SM0C, h->stream>>>(t, nullptr, nullptr, limiter);
+        else k_update<S, T, D, TX, TY, VPC, false, true><<<grid, TX * TY, SMU, h->stream>>>(t, nullptr, nullptr);
         return;
       }
     }
-    if constexpr (MODE == 0) k_faces<S, T, D, TX, TY, false><<<grid, TX * TY, SM0, h->stream>>>(t, limiter);
-    else k_update<S, T, D, TX, TY, VPC, false><<<grid, TX * TY, SMU, h->stream>>>(t);
+    if constexpr (MODE == 0)
+      k_faces<S, T, D, TX, TY, false, false><<<grid, TX * TY, SM0, h->stream>>>(t, nullptr, nullptr, limiter);
+    else k_update<S, T, D, TX, TY, VPC, false, false><<<grid, TX * TY, SMU, h->stream>>>(t, nullptr, nullptr);
   }
 
   // one tile pass over every level of a multi-level instance: n work items, argument table tab
   template <int MODE>
   static void launch_lv(mlvs_handle* h, int n, const TileArgs* tab, const int4* w, int limiter) {
+    const TileArgs none{};
     if constexpr (D == 2) {
       if (h->curvi) {
-        if constexpr (MODE == 0) k_faces_lv<S, T, D, TX, TY, true><<<n, TX * TY, SM0C, h->stream>>>(tab, w, limiter);
-        else k_update_lv<S, T, D, TX, TY, VPC, true><<<n, TX * TY, SMU, h->stream>>>(tab, w);
+        if constexpr (MODE == 0) k_faces<S, T, D, TX, TY, true, true><<<n, TX * TY, SM0C, h->stream>>>(none, tab, w, limiter);
+        else k_update<S, T, D, TX, TY, VPC, true, true><<<n, TX * TY, SMU, h->stream>>>(none, tab, w);
         return;
       }
     }
-    if constexpr (MODE == 0) k_faces_lv<S, T, D, TX, TY, false><<<n, TX * TY, SM0, h->stream>>>(tab, w, limiter);
-    else k_update_lv<S, T, D, TX, TY, VPC, false><<<n, TX * TY, SMU, h->stream>>>(tab, w);
+    if constexpr (MODE == 0) k_faces<S, T, D, TX, TY, true, false><<<n, TX * TY, SM0, h->stream>>>(none, tab, w, limiter);
+    else k_update<S, T, D, TX, TY, VPC, true, false><<<n, TX * TY, SMU, h->stream>>>(none, tab, w);
   }
 
   // a level that holds every cell runs the tile kernels without level tables
@@ -1401,7 +1409,7 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     if (h->curvi) CK(ops_for(h->cfg.storage, D).wall_table(h, L));
     if (L.msum.alloc((size_t)NMOM * std::max<size_t>(std::max<size_t>(nface, nc), 1) * sizeof(double)) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
-    if (sp.nax == 0) {
+    {
       const size_t np = std::max<size_t>(std::max<size_t>(nface, nc), 1);
       if (L.fscr.alloc(FIN_SCR * np * sizeof(double)) != cudaSuccess || L.fneed.alloc(np * sizeof(int)) != cudaSuccess)
         return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");

@@ -138,7 +138,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     t.ucell = ucell.data(); t.step = &stepctr; t.fbar = fbar.data();
     t.part = fpart.data();
     emu_launch(dim3(ntiles, k.nchunk, 1), TX * TY,
-               [&] { k_faces<S, T, D, TX, TY, false>(t, limiter); });
+               [&] { k_faces<S, T, D, TX, TY, false, false>(t, nullptr, nullptr, limiter); });
     {
       PointArgs a = pargs(true);
       a.cprm = prm[pcur].data();
@@ -147,7 +147,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     }
     t.part = cpart.data();
     emu_launch(dim3(ntiles, k.nchunk, 1), TX * TY,
-               [&] { k_update<S, T, D, TX, TY, VPC, false>(t); });
+               [&] { k_update<S, T, D, TX, TY, VPC, false, false>(t, nullptr, nullptr); });
     cur ^= 1;
   }
   for (size_t i = 0; i < f[cur].size(); ++i) fout[i] = (double)f[cur][i];
