@@ -371,6 +371,78 @@ def _cylinder_leg(storage="f32", warm_steps=300, run_steps=300, taus=(1.0, 0.07,
     return out
 
 
+def _sod_leg(steps=500):
+    """The 1-D shock tube (200 cells, 101 velocities on [-10, 10], FP64, BGK, Kn 1e-3, CFL 0.5):
+    device time per step over `steps` steps replayed as two-step CUDA graphs, and launched one
+    kernel at a time, with the host's wall time per step beside each."""
+    import time
+    from paper_2609_35258_b300 import mlvs as M, workloads
+    from paper_2609_35258_b300.solver import Solver
+    d = workloads.sod_1d()
+    out = {"workload": "Sod shock tube, 200 cells, 101 velocities on [-10,10], FP64, BGK, Kn 1e-3, CFL 0.5",
+           "steps": steps}
+    for graph in (True, False):
+        s = Solver(d)
+        M.mlvs_set_graph(s.h, graph)
+        s.step(10)                                  # warm: tables, graph capture
+        t0 = time.perf_counter()
+        st = s.step(steps)
+        wall = (time.perf_counter() - t0) / steps
+        rho = s.moments(M.RHO)[0]
+        out["graph" if graph else "eager"] = {"ms_per_step": st.ms_total / steps, "wall_ms_per_step": 1e3 * wall,
+                                              "launches_per_step": st.launches / steps,
+                                              "updates_per_s": st.cell_velocity_updates / (st.ms_total / 1e3)}
+        out["rho_range"] = [float(rho.min()), float(rho.max())]
+        s.close()
+    return out
+
+
+def _batch_leg(n_inst=64, warm=50, steps=40):
+    """Independent lid-driven cavities (Kn log-uniform in [1e-3, 10], sizes drawn from 32^2 ..
+    128^2, 101^2 base grid, FP32), each adapting on its own (the cavity thresholds, up to two
+    coarsening depths: spaces between 101^2 and 25^2 points, rebuilt every `warm` steps).  After
+    `warm` steps and the first adaptation, `steps` steps of the whole group run as one graph per
+    two steps (mlvs_step_many; every instance's tile passes are level-batched launches), then
+    the same steps one handle after another."""
+    import time
+    import torch
+    from paper_2609_35258_b300 import mlvs as M, workloads
+    from paper_2609_35258_b300.solver import Solver
+    descs = workloads.batched_cavities(n_inst)
+    ss = [Solver(d, adaptive=1) for d in descs]
+    hs = [s.h for s in ss]
+    p = M.adapt_params(5e-3, 2.5e-3, 5e-5, 0.05, 2)
+    for s in ss:
+        M.mlvs_set_adaptation(s.h, p, warm)
+    out = {"workload": f"{n_inst} cavities, Kn log-uniform [1e-3, 10], sizes 32^2..128^2, base 101^2, FP32, "
+                       f"adaptive (spaces 101^2..25^2)",
+           "instances": n_inst, "cells": int(sum(d["nx"] * d["ny"] for d in descs))}
+    try:
+        M.mlvs_step_many(hs, warm + 2, use_graph=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = M.mlvs_step_many(hs, steps, use_graph=True)
+        torch.cuda.synchronize()
+        tb = time.perf_counter() - t0
+        upd = st.cell_velocity_updates
+        t0 = time.perf_counter()
+        for h in hs:
+            M.mlvs_step(h, steps)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        out.update({"steps": steps, "updates_per_step": upd / steps,
+                    "mean_points_per_cell": upd / steps / out["cells"],
+                    "batched": {"ms_per_step": 1e3 * tb / steps, "updates_per_s": upd / tb,
+                                "launches_per_step": st.launches / steps},
+                    "one_by_one": {"ms_per_step": 1e3 * ts / steps, "updates_per_s": upd / ts},
+                    "batching_gain": ts / tb})
+    except M.MLVSError as e:
+        out["error"] = str(e)
+    for s in ss:
+        s.close()
+    return out
+
+
 def _unstructured_leg(storage="f32", m=10, n_base=101, umax=6.0, steps=50, warm=5):
     """Two connected cavities (13,600 quads for m = 10; the paper's mesh has 12,012 cells)
     with the paper's density ratio of 1000, gas at rest at T = 1, closed walls at T = 1, one
@@ -561,6 +633,8 @@ def run_ours(args, rank, world, local_rank):
         cylinder = {st_: _cylinder_leg(storage=st_, positive_mapping=int(args.positive_mapping))
                     for st_ in ("f32", "bf16")}
     unstructured = _unstructured_isolated() if (not args.no_unstructured and rank == 0) else None
+    sod = _sod_leg() if (not args.no_sod and rank == 0) else None
+    batch = _batch_leg() if (not args.no_batch and rank == 0) else None
 
     # end-to-end through the public API: host init upload, steps, host moment reads
     e2e = None
@@ -615,7 +689,7 @@ def run_ours(args, rank, world, local_rank):
                               "algorithmic_bytes_per_update": 4 * fbytes,
                               "note": "the whole step (every launch) against reading and writing f once"},
             "mlvs": mlvs, "time_to_steady": steady, "selector": selector, "cylinder": cylinder,
-            "unstructured": unstructured,
+            "unstructured": unstructured, "sod": sod, "batch": batch,
             "clocks": clocks, "e2e": e2e, "gpu_launches": st.launches, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
@@ -639,6 +713,9 @@ def main():
                          "sweep and runtime-model fit, about 45 s each)")
     ap.add_argument("--positive-mapping", action="store_true",
                     help="cylinder leg: exponential fallback for level switches that go negative")
+    ap.add_argument("--no-sod", action="store_true", help="skip the shock-tube latency leg")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-cavity batch leg (adaptive instances stepped as one group)")
     ap.add_argument("--no-unstructured", action="store_true",
                     help="skip the two-cavity unstructured-mesh leg (13,600 quads, 101^2 velocities, "
                          "run in a child process)")
