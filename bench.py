@@ -221,76 +221,104 @@ def _steady(desc, stream, mlvs):
             "updates": upd}, out
 
 
-def _selector_leg():
+def _selector_leg(kns=(0.01, 0.1, 1.0), snaps=20, every=20, held=4, epochs=300, conf=0.9, warm=200,
+                  interval=100):
+    """The level selector on the Ma 5 cylinder (O-grid 256 x 128, base 201^2 on [-15, 15]^2, FP32,
+    smooth start) with the four uniform levels 201^2 / 101^2 / 51^2 / 25^2 and the paper's
+    cylinder criterion (C_split 0.01, C_merge 0.005).  Labels: the fixed-level-set rule on the
+    criterion's masks for every cell of `snaps` snapshots, `every` steps apart, of one UVS run
+    per Knudsen number in `kns`; features: the library's ten cell features.  The last `held`
+    snapshots of every run are held out; the network trains on the rest (full batch, SGD with
+    momentum, on the GPU).  In the solve: two runs at Kn 0.1 take `warm` UVS steps, then adapt
+    every `interval` steps up to step snaps * every, one with the criterion, one with the
+    selector (the criterion on the cells below confidence `conf`); both are compared with the
+    UVS run at Kn 0.1 (the training run, which never adapts) at that step."""
     import numpy as np
     import torch
     from paper_2609_35258_b300 import mlvs as M
     from paper_2609_35258_b300 import workloads
     from paper_2609_35258_b300.solver import Solver
-    nb = 41
-    levels = list(workloads.radial_levels(nb))
-    p = M.adapt_params(5e-3, 2.5e-3, 0.0, 0.05, 3)
-
-    def labelled(d, steps):
-        s = Solver(d, levels=levels, adaptive=0)
-        n = d["nx"] * d["ny"]
-        X, y = [], []
-        for k in steps:
-            if k:
-                s.step(k)
-            X.append(M.mlvs_features(s.h, 0, n))
-            y.append(M.mlvs_criterion_levels(s.h, 0, p, n))
+    nt, nr = 256, 128
+    n = nt * nr
+    levels = [0, 1, 2, 3]
+    p = M.adapt_params(0.01, 0.005, 0.0, 0.05, 3)
+    F = M.RHO | M.T
+    Xtr, ytr, Xho, yho = [], [], [], []
+    t_label, ref = 0.0, None
+    for Kn in kns:
+        s = Solver(workloads.cylinder(nt, nr, Kn=Kn, storage="f32", start="ramp"), levels=levels, adaptive=0)
+        M.mlvs_set_graph(s.h, True)
+        for k in range(snaps):
+            s.step(every)
+            t0 = time.perf_counter()
+            X = M.mlvs_features(s.h, 0, n)
+            y = M.mlvs_criterion_levels(s.h, 0, p, n)
+            t_label += time.perf_counter() - t0
+            (Xtr if k < snaps - held else Xho).append(X)
+            (ytr if k < snaps - held else yho).append(y)
+        if Kn == 0.1:
+            ref = s.moments(F)
         s.close()
-        return np.concatenate(X), np.concatenate(y)
-
-    X, y = [], []
-    for amp, Kn, seed in workloads.SELECTOR_TRAIN:
-        a, b = labelled(workloads.periodic_random(24, 24, n_base=nb, amp=amp, Kn=Kn, seed=seed), (0, 4, 4))
-        X.append(a)
-        y.append(b)
-    X, y = np.concatenate(X), np.concatenate(y)
+    X, y = np.concatenate(Xtr), np.concatenate(ytr)
+    Xh, yh = np.concatenate(Xho), np.concatenate(yho)
     m = M.mlvs_mlp_create()
     M.mlvs_mlp_set_weights(m, workloads.selector_init())
     Xd, yd = torch.from_numpy(X).cuda(), torch.from_numpy(y).cuda()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    first = M.mlvs_mlp_train_step(m, Xd, yd, len(y), 0.02, 0.9)
-    epochs = 1500
+    first = last = M.mlvs_mlp_train_step(m, Xd, yd, len(y), 0.02, 0.9)
     for _ in range(epochs - 1):
         last = M.mlvs_mlp_train_step(m, Xd, yd, len(y), 0.02, 0.9)
+    torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    acc = []
-    for amp, Kn, seed in workloads.SELECTOR_HELD:
-        Xh, yh = labelled(workloads.periodic_random(24, 24, n_base=nb, amp=amp, Kn=Kn, seed=seed), (0,))
-        pr = torch.zeros(len(yh), 4, device="cuda")
-        M.mlvs_mlp_forward(m, torch.from_numpy(Xh).cuda(), len(yh), None, pr)
-        torch.cuda.synchronize()
-        acc.append(float(np.mean(np.argmax(pr.cpu().numpy(), 1) == yh)))
-    amp, Kn, seed = workloads.SELECTOR_HELD[0]
-    d = workloads.periodic_random(64, 64, n_base=nb, amp=amp, Kn=Kn, seed=seed)
-    a = Solver(d, levels=levels, adaptive=0)
-    b = Solver(d, levels=levels, adaptive=0)
-    a.step(2)
-    b.step(2)
-    ta, tb = [], []
-    for _ in range(4):
-        ta.append(M.mlvs_adapt(a.h, p).ms_total)
-        sb = M.mlvs_adapt_mlp(b.h, m, p, 0.9)
-        tb.append(sb.ms_total)
-    la, lb = a.moments(M.LEVEL)[0], b.moments(M.LEVEL)[0]
-    a.step(10)
-    b.step(10)
-    ma, mb = a.moments(M.RHO | M.T), b.moments(M.RHO | M.T)
-    a.close()
-    b.close()
+    prob = torch.zeros(len(yh), 4, device="cuda")
+    M.mlvs_mlp_forward(m, torch.from_numpy(Xh).cuda(), len(yh), None, prob)
+    pr = prob.cpu().numpy()
+    pred, top = np.argmax(pr, 1), np.max(pr, 1)
+    sure = top >= conf
+    out = {"workload": f"cylinder O-grid {nt}x{nr}, Ma 5, base 201^2 on [-15,15]^2, FP32, smooth start, "
+                       f"uniform levels 201^2/101^2/51^2/25^2", "network": "10-64-64-4 ReLU, BF16 weights, FP32 accumulation",
+           "kn": list(kns), "train_samples": int(len(y)), "heldout_samples": int(len(yh)),
+           "label_counts": np.bincount(np.concatenate([y, yh]), minlength=4).tolist(),
+           "label_seconds": t_label, "epochs": epochs, "train_seconds": t_train,
+           "loss_first": first, "loss_last": last,
+           "heldout_accuracy": float(np.mean(pred == yh)),
+           "heldout_confident_fraction": float(np.mean(sure)),
+           "heldout_confident_accuracy": float(np.mean(pred[sure] == yh[sure])) if sure.any() else None,
+           "confidence": conf, "solve": {}}
+    for mode in ("criterion", "selector"):
+        s = Solver(workloads.cylinder(nt, nr, Kn=0.1, storage="f32", start="ramp"), levels=levels, adaptive=0)
+        M.mlvs_set_graph(s.h, True)
+        s.step(warm)
+        ta, ts, fb, pts = [], 0.0, [], []
+        try:
+            for _ in range((snaps * every - warm) // interval):
+                if mode == "criterion":
+                    a = M.mlvs_adapt(s.h, p)
+                else:
+                    a = M.mlvs_adapt_mlp(s.h, m, p, conf)
+                    fb.append(int(a.n_distinct))
+                ta.append(a.ms_total)
+                pts.append(a.updates_per_step / n)
+                ts += s.step(interval).ms_total
+            mo = s.moments(F)
+            out["solve"][mode] = {"adapt_ms": ta, "mean_points_per_cell": pts,
+                                  "ms_per_step": ts / (snaps * every - warm),
+                                  "rel_l2_vs_uvs": {"rho": _l2(mo[0], ref[0]), "T": _l2(mo[1], ref[1])},
+                                  "levels": np.bincount(s.moments(M.LEVEL)[0].astype(int), minlength=4).tolist()}
+            if fb:
+                out["solve"][mode]["fallback_cells"] = fb
+        except M.MLVSError as e:
+            out["solve"][mode] = {"error": str(e)}
+        s.close()
     M.mlvs_mlp_destroy(m)
-    return {"network": "10-64-64-4 ReLU, BF16 weights, FP32 accumulation", "train_samples": int(len(y)),
-            "label_counts": np.bincount(y, minlength=4).tolist(), "epochs": epochs,
-            "train_seconds": t_train, "loss_first": first, "loss_last": last, "heldout_accuracy": acc,
-            "adapt_ms_criterion": float(np.median(ta[1:])), "adapt_ms_selector": float(np.median(tb[1:])),
-            "fallback_cells": int(sb.n_distinct), "cells": 4096, "level_agreement": float(np.mean(la == lb)),
-            "rel_diff_rho_T_after_10_steps": float(np.max(np.abs(ma - mb) / ma)),
-            "workload": "periodic random states, 64^2 cells, base 41^2, four radial levels"}
+    c, q = out["solve"].get("criterion", {}), out["solve"].get("selector", {})
+    if "adapt_ms" in c and "adapt_ms" in q:
+        out["adapt_speedup"] = float(np.sum(c["adapt_ms"]) / np.sum(q["adapt_ms"]))
+        tc = np.sum(c["adapt_ms"]) + c["ms_per_step"] * (snaps * every - warm)
+        tq = np.sum(q["adapt_ms"]) + q["ms_per_step"] * (snaps * every - warm)
+        out["end_to_end_speedup"] = float(tc / tq)
+    return out
 
 
 def _cylinder_leg(storage="f32", warm_steps=300, run_steps=300, taus=(1.0, 0.07, 0.05, 0.04, 0.035),
