@@ -8,8 +8,10 @@
 //  * the representative (enclosing) mask is the blockwise minimum over the members.
 #pragma once
 #include <algorithm>
+#include <climits>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 #if defined(__SSE2__)
@@ -23,6 +25,25 @@ struct Clustering {
   std::vector<std::vector<uint8_t>> reps;  // per cluster, N_b entries
   int n_distinct = 0;
 };
+
+// f(begin, end) over [0, n) split across the host's cores (serially when `work`, a byte count,
+// is too small to pay for threads)
+template <class F>
+inline void host_parallel(long n, double work, F f) {
+  const unsigned hc = std::thread::hardware_concurrency();
+  const long nt = std::min<long>({(long)(hc ? hc : 1), 32L, n});
+  if (nt <= 1 || work < 4e6) {
+    f(0L, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  const long chunk = (n + nt - 1) / nt;
+  for (long t = 0; t < nt; ++t) {
+    const long b = t * chunk, e = std::min(n, b + chunk);
+    if (b < e) th.emplace_back(f, b, e);
+  }
+  for (auto& x : th) x.join();
+}
 
 // sum_k |a_k - b_k| over n bytes
 inline long l1_bytes(const uint8_t* a, const uint8_t* b, int n) {
@@ -64,18 +85,26 @@ inline Clustering cluster_masks(const uint8_t* kappa, long nrow, int nb, double 
   std::vector<int> row_u(nrow);
   std::vector<const uint8_t*> uptr;
   std::vector<long> cnt;
+  // row hashes: a sum of independently mixed words (no serial chain, so the loop pipelines)
+  std::vector<uint64_t> hashes(nrow);
+  host_parallel(nrow, (double)nrow * nb, [&](long r0, long r1) {
+    for (long r = r0; r < r1; ++r) {
+      const uint8_t* p = kappa + (size_t)r * nb;
+      uint64_t hsh = 0;
+      int k = 0;
+      for (; k + 8 <= nb; k += 8) {
+        uint64_t w;
+        std::memcpy(&w, p + k, 8);
+        const uint64_t z = (w ^ (0x9e3779b97f4a7c15ull * (uint64_t)(k + 1))) * 0xbf58476d1ce4e5b9ull;
+        hsh += z ^ (z >> 32);
+      }
+      for (; k < nb; ++k) hsh = hsh * 31u + p[k];
+      hashes[r] = hsh;
+    }
+  });
   for (long r = 0; r < nrow; ++r) {
     const uint8_t* p = kappa + (size_t)r * nb;
-    // sum of independently mixed words (no serial chain, so the loop pipelines)
-    uint64_t hsh = 0;
-    int k = 0;
-    for (; k + 8 <= nb; k += 8) {
-      uint64_t w;
-      std::memcpy(&w, p + k, 8);
-      const uint64_t z = (w ^ (0x9e3779b97f4a7c15ull * (uint64_t)(k + 1))) * 0xbf58476d1ce4e5b9ull;
-      hsh += z ^ (z >> 32);
-    }
-    for (; k < nb; ++k) hsh = hsh * 31u + p[k];
+    const uint64_t hsh = hashes[r];
     int u = -1;
     auto range = idx.equal_range(hsh);
     for (auto it = range.first; it != range.second; ++it)
@@ -97,30 +126,43 @@ inline Clustering cluster_masks(const uint8_t* kappa, long nrow, int nb, double 
     if (cnt[a] != cnt[b]) return cnt[a] > cnt[b];
     return std::memcmp(uptr[a], uptr[b], nb) < 0;
   });
+  // In that order, a mask joins the nearest centre created before it, or seeds a new one.
+  // When a centre is created its distance to every later mask is evaluated (in parallel), and
+  // each mask keeps the nearest centre so far (the lowest index on equal distances), so a mask
+  // meets exactly the centres created before it, compared in creation order.
   std::vector<int> centre;                 // distinct-mask index of every centre
   std::vector<int> ulabel(nu, 0);
+  std::vector<long> bestd(nu, LONG_MAX);   // L1 distance to the nearest centre so far
+  std::vector<int> bestc(nu, -1);
   const double denom = 3.0 * nb;
-  for (int u : order) {
-    if (centre.empty()) {
-      centre.push_back(u);
-      ulabel[u] = 0;
+  for (int pos = 0; pos < nu; ++pos) {
+    const int u = order[pos];
+    if (!centre.empty() && (double)bestd[u] / denom <= tau) {
+      ulabel[u] = bestc[u];
       continue;
     }
-    int best = -1;
-    double bd = 0.0;
-    for (size_t c = 0; c < centre.size(); ++c) {
-      const double d = (double)l1_bytes(uptr[u], uptr[centre[c]], nb) / denom;
-      if (best < 0 || d < bd) { best = (int)c; bd = d; }
-    }
-    if (bd <= tau) {
-      ulabel[u] = best;
-    } else {
-      ulabel[u] = (int)centre.size();
-      centre.push_back(u);
-    }
+    const int c = (int)centre.size();
+    centre.push_back(u);
+    ulabel[u] = c;
+    host_parallel(nu - pos - 1, (double)(nu - pos - 1) * nb, [&](long k0, long k1) {
+      for (long k = pos + 1 + k0; k < pos + 1 + k1; ++k) {
+        const int v = order[k];
+        const long d = l1_bytes(uptr[v], uptr[u], nb);
+        if (bestc[v] < 0 || d < bestd[v]) {
+          bestd[v] = d;
+          bestc[v] = c;
+        }
+      }
+    });
   }
   out.reps.assign(centre.size(), std::vector<uint8_t>(nb, 255));
-  for (int u = 0; u < nu; ++u) min_bytes(out.reps[ulabel[u]].data(), uptr[u], nb);
+  // blockwise minima over the members, the blocks split across the cores (16-byte aligned
+  // ranges)
+  const long nseg = (nb + 1023) / 1024;
+  host_parallel(nseg, (double)nu * nb, [&](long s0, long s1) {
+    const int k0 = (int)(s0 * 1024), k1 = (int)std::min<long>(nb, s1 * 1024);
+    for (int u = 0; u < nu; ++u) min_bytes(out.reps[ulabel[u]].data() + k0, uptr[u] + k0, k1 - k0);
+  });
   for (long r = 0; r < nrow; ++r) out.labels[r] = ulabel[row_u[r]];
   return out;
 }
