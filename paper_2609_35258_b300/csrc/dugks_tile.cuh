@@ -919,6 +919,21 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
   // the faces C of this thread in the pre-pass: face tid % NX3, pairs tid / NX3 + k NT / NX3
   const int qc = tid % NX3, jc0 = tid / NX3;
   const int dirC = (D == 1 || qc < TY) ? 0 : 1;
+  // the own cell's pair and the faces A and B of a round, loaded one round ahead in registers
+  // where registers allow (FP32 arithmetic on a level that holds every cell; the level-batched
+  // and FP64 forms would spill)
+  constexpr bool PF = !ML && sizeof(T) == 4;
+  auto ld_round = [&](int j, V& g0, V& h0, V& ga, V& ha, V& gbb, V& hbb) {
+    const int v = v0 + 2 * j;
+    const long vb = min(v + 1, v1 - 1);
+    g0 = P::mk(ldf<S, T>(pO + (long)v * so), ldf<S, T>(pO + vb * so));
+    h0 = P::mk(ldf<S, T>(pO + (nv + v) * so), ldf<S, T>(pO + (nv + vb) * so));
+    ldface(FA.role, FA.fid, FA.col, v, ga, ha);
+    if (D == 2) ldface(FB.role, FB.fid, FB.col, v, gbb, hbb);
+    else gbb = hbb = P::splat(T(0));
+  };
+  V ng0, nh0, nga, nha, ngb, nhb;
+  if constexpr (PF) ld_round(0, ng0, nh0, nga, nha, ngb, nhb);
   int cbuf = 0, buf = 0;
   for (int jb = 0; jb < npr; jb += SC, cbuf ^= 1) {
     // ---- pre-pass: the microfluxes of the faces C over the sub-chunk
@@ -950,12 +965,13 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
     const int je = min(jb + SC, npr);
     for (int j = jb; j < je; ++j, buf ^= 1) {
       const int v = v0 + 2 * j;
-      const long vb = min(v + 1, v1 - 1);
-      const V g0 = P::mk(ldf<S, T>(pO + (long)v * so), ldf<S, T>(pO + vb * so));
-      const V h0 = P::mk(ldf<S, T>(pO + (nv + v) * so), ldf<S, T>(pO + (nv + vb) * so));
-      V ga, ha, gbb, hbb;
-      ldface(FA.role, FA.fid, FA.col, v, ga, ha);
-      if (D == 2) ldface(FB.role, FB.fid, FB.col, v, gbb, hbb);
+      V g0, h0, ga, ha, gbb, hbb;
+      if constexpr (PF) {
+        g0 = ng0; h0 = nh0; ga = nga; ha = nha; gbb = ngb; hbb = nhb;
+        if (j + 1 < npr) ld_round(j + 1, ng0, nh0, nga, nha, ngb, nhb);
+      } else {
+        ld_round(j, g0, h0, ga, ha, gbb, hbb);
+      }
       const V xix = sVT[4 * j], xiy = sVT[4 * j + 1];
       V* Fg = sF + (buf * 2 + 0) * G::NF;
       V* Fh = sF + (buf * 2 + 1) * G::NF;
