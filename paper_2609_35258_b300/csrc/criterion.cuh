@@ -17,10 +17,10 @@
 // per candidate block, sums of w xi_d m_r over the nodes on each side of xi_d = 0; a level-1
 // block never straddles xi = 0 (the centre node is a group of its own), so these sums add up
 // over level-1 blocks: the node pass stores seven more per-block sums (x g, y g, x^2 g,
-// x y g, y^2 g, x H, y H) when shared memory holds them (tblk), and a candidate block adds
-// its members' sums.  Otherwise the test walks the block's nodes.  The scale S_r of the test
-// uses per-point geometric sums of the cell's space (inherited values are constant on a
-// point's rectangle).  A level-1 block inside one point of the cell's space takes its sums
+// x y g, y^2 g, x H, y H) in shared memory when it holds them (tblk = 1), else in a global
+// scratch slice per CTA (tblk = 2), and a candidate block adds its members' sums.  The scale
+// S_r of the test uses per-point geometric sums of the cell's space (inherited values are
+// constant on a point's rectangle).  A level-1 block inside one point of the cell's space takes its sums
 // from that point's g and H times the block's geometric sums.  Thresholds are applied as
 // products (s1 < C T1 for s1/T1 < C, |F - F~| <= eps S_r for the relative error), which is
 // the same test up to rounding.
@@ -50,7 +50,10 @@ struct CritArgs {
   const double* geo;           // [5][nv] per point: sum w|x|, sum w|y|, sum w x^2, sum w y^2, sum w|x||y|
   double C_split, C_merge, eps;
   int max_level;
-  int tblk;                    // 1: per-block transport sums in shared memory
+  int tblk;                    // per-block transport sums: 0 none (the test walks the nodes),
+                               // 1 in shared memory, 2 in global scratch (TBg)
+  double* TBg;                 // tblk == 2: [gridDim.x][CB_N][N1*N1], one slice per CTA
+  int sel0;                    // first entry of sel (or first slot) of this launch
   unsigned char* kout;         // [ncell][N1*N1]
 };
 
@@ -62,7 +65,7 @@ struct CritCtx {
   const CritArgs* a;
   const double* S1;
   const double* S2;
-  const double* TB;            // [CB_N][nb] when a->tblk
+  const double* TB;            // [CB_N][nb] when a->tblk != 0
   double T1, T2;
   double Sr[4];
   double epsSr[4];             // eps * S_r
@@ -246,9 +249,10 @@ __global__ void __launch_bounds__(CRIT_THREADS) k_criterion(const CritArgs a) {
   double* S1 = csm;
   double* S2 = csm + nb;
   __shared__ double red[10][CRIT_THREADS / 32];
-  const int slot = a.sel ? a.sel[blockIdx.x] : blockIdx.x;
+  const int slot = a.sel ? a.sel[a.sel0 + blockIdx.x] : a.sel0 + (int)blockIdx.x;
   const int tid = threadIdx.x;
-  double* TB = csm + 2 * nb;   // [CB_N][nb] when tblk
+  // [CB_N][nb] per-block transport sums: shared memory, or this CTA's slice of the scratch
+  double* TB = a.tblk == 2 ? a.TBg + (size_t)blockIdx.x * CB_N * nb : csm + 2 * nb;
   // level-1 block sums of w g and w H (and of the transport moments) on the base grid
   for (int b = tid; b < nb; b += CRIT_THREADS) {
     const int by = b / a.N1, bx = b % a.N1;

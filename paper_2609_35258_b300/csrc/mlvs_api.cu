@@ -197,6 +197,7 @@ struct mlvs_handle {
   int N1 = 0;
   int ng[4] = {0, 0, 0, 0};
   DevBuf bx_d, bw_d, g1_d, pstart_d, cstart_d, w1_d, x1_d, xx1_d, kbuf, sel_d, feat_d, prob_d;
+  DevBuf crit_tb;                       // criterion: per-block transport sums, one slice per CTA
   unsigned char* kbuf_host = nullptr;   // pinned copy of the masks
   size_t kbuf_host_n = 0;
   mlvs_adapt_params adapt{};
@@ -1095,9 +1096,15 @@ template <class S, class T, int D> struct Runner {
       cudaError_t e = upload(h->sel_d, slots, h->stream);
       if (e != cudaSuccess) return e;
     }
-    // per-block transport sums in shared memory when they fit
-    const int tblk = (p.eps_merge > 0.0 && (2ull + CB_N) * nb * sizeof(double) <= 220ull * 1024) ? 1 : 0;
-    const size_t smem = (2ull + (tblk ? CB_N : 0)) * nb * sizeof(double);
+    // per-block transport sums in shared memory when they fit, else in a global scratch slice
+    // per CTA, the cells then launched in batches of kCritBatch
+    int tblk = 0;
+    if (p.eps_merge > 0.0) tblk = (2ull + CB_N) * nb * sizeof(double) <= 220ull * 1024 ? 1 : 2;
+    const size_t smem = (2ull + (tblk == 1 ? CB_N : 0)) * nb * sizeof(double);
+    constexpr int kCritBatch = 2048;
+    const size_t tb_bytes = (size_t)kCritBatch * CB_N * nb * sizeof(double);
+    if (tblk == 2 && h->crit_tb.n < tb_bytes && h->crit_tb.alloc(tb_bytes) != cudaSuccess)
+      return cudaErrorMemoryAllocation;
     cudaError_t e = cudaFuncSetAttribute(k_criterion<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     for (int l = 0; l < h->n_levels; ++l) {
@@ -1127,13 +1134,18 @@ template <class S, class T, int D> struct Runner {
       a.XX1 = h->xx1_d.as<double>();
       a.geo = sp.geo.as<double>();
       a.tblk = tblk;
+      a.TBg = tblk == 2 ? h->crit_tb.as<double>() : nullptr;
       a.C_split = p.C_split;
       a.C_merge = p.C_merge;
       a.eps = p.eps_merge;
       a.max_level = p.max_level;
       a.kout = kout;
-      ++h->launches;
-      k_criterion<S><<<nsel, CRIT_THREADS, smem, h->stream>>>(a);
+      const int batch = tblk == 2 ? kCritBatch : nsel;
+      for (int b0 = 0; b0 < nsel; b0 += batch) {
+        a.sel0 = b0;
+        ++h->launches;
+        k_criterion<S><<<std::min(batch, nsel - b0), CRIT_THREADS, smem, h->stream>>>(a);
+      }
     }
     return cudaGetLastError();
   }
@@ -1209,6 +1221,7 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
   }
   // faces: roles, cross-level routes
   std::map<int, int> face_level_of_space;   // face levels (no cells) by space
+  std::map<std::pair<int, int>, int> space_of_pair;   // common refinement of two cell levels
   std::vector<std::vector<unsigned char>> role(h->n_levels);
   std::vector<std::vector<int>> slot(h->n_levels);
   auto ensure = [&](int l) {
@@ -1247,14 +1260,22 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     ++I.n_int;
     if (lL == lR) { role[lL][f] = FR_NORMAL; continue; }
     ++I.n_cross;
-    // cross-level face: evaluated on the common refinement of the two spaces (Sec. 3.4)
-    const SpaceRt& SL = h->spaces[h->level_space[lL]];
-    const SpaceRt& SR = h->spaces[h->level_space[lR]];
-    std::vector<int> km(SL.keff.size());
-    for (size_t b = 0; b < km.size(); ++b) km[b] = std::min(SL.keff[b], SR.keff[b]);
+    // cross-level face: evaluated on the common refinement of the two spaces (Sec. 3.4),
+    // which depends only on the pair of levels
     int sf;
-    mlvs_status st = get_space(h, km, &sf);
-    if (st != MLVS_OK) return st;
+    const std::pair<int, int> pair_key(std::min(lL, lR), std::max(lL, lR));
+    auto pit = space_of_pair.find(pair_key);
+    if (pit != space_of_pair.end()) {
+      sf = pit->second;
+    } else {
+      const SpaceRt& SL = h->spaces[h->level_space[lL]];
+      const SpaceRt& SR = h->spaces[h->level_space[lR]];
+      std::vector<int> km(SL.keff.size());
+      for (size_t b = 0; b < km.size(); ++b) km[b] = std::min(SL.keff[b], SR.keff[b]);
+      mlvs_status st = get_space(h, km, &sf);
+      if (st != MLVS_OK) return st;
+      space_of_pair[pair_key] = sf;
+    }
     int lf;
     if (sf == h->level_space[lL]) lf = lL;
     else if (sf == h->level_space[lR]) lf = lR;

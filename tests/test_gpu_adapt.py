@@ -43,7 +43,9 @@ def _totals(s):
     return np.array([m[0].sum(), (m[0] * m[1]).sum(), (m[0] * m[2]).sum(), m[3].sum()])
 
 
-@pytest.mark.parametrize("n_base,eps,steps", [(41, 5e-5, 3), (41, 0.0, 0), (101, 5e-5, 2)])
+# the per-block transport sums of the criterion sit in shared memory up to the 101^2 base and
+# in a global scratch slice per CTA beyond it (201^2)
+@pytest.mark.parametrize("n_base,eps,steps", [(41, 5e-5, 3), (41, 0.0, 0), (101, 5e-5, 2), (201, 5e-5, 2)])
 def test_criterion_matches_oracle_uniform(n_base, eps, steps):
     desc = workloads.cavity(8, n_base=n_base, Kn=0.075, storage="f64")
     o = oracle_setup(desc)
