@@ -55,6 +55,16 @@ struct PointArgs {
   const double* wden;   // curvilinear walls: [nface] normalisation of the wall Maxwellian (or null)
   double* scr;          // split finalisation: [FIN_SCR][npt] state and velocity sums
   int* need;            // split finalisation: [npt] what the velocity sums are for
+  // rows of a 2-D space that is not a tensor product (null: the direct sums): the distinct
+  // axis ranges of its points (entries, grouped by level: block L = [lst[L], lst[L+1])), the
+  // rows (points sharing a y entry: {y entry, first segment, segments, 0}) and the segments of
+  // a row (runs of consecutive x entries of one level, as prefix positions {e0 + L, e1 + L})
+  const void* e1;       // (T) [2][n1] entry abscissa X and weight W
+  int n1;
+  const int* lst;       // [5]
+  const int4* rows;
+  int nrows;
+  const int2* segs;
 };
 
 // Split finalisation: k_fin_pre (thread per point: state, uncorrected model), k_fin_sums (warp
@@ -225,9 +235,11 @@ __device__ __forceinline__ T lane_sum_t(T x) {
 // Peculiar moments of the uncorrected model of mp:
 //   G[a][b] = sum w g^S c_x^a c_y^b (a+b <= 4),  H[a][b] = sum w h^S c_x^a c_y^b (a+b <= 2),
 // on a tensor-product space from the one-axis sums.
+// G and H of the uncorrected model from its pair moments P[i][j] = sum w gauss c_x^i c_y^j
+// (i + j <= 7; on a tensor-product space P[i][j] = Sx[i] Sy[j]).
 template <class T, int D>
-__device__ inline void axis_combine(const PointArgs& A, const MP<T>& mp, const double Sx[8], const double Sy[8],
-                                    double G[5][5], double H[3][3]) {
+__device__ inline void pair_combine(const PointArgs& A, const MP<T>& mp, const double P[8][8], double G[5][5],
+                                    double H[3][3]) {
   const StepConst& k = A.k;
   const double kx = (double)mp.kqx, ky = (double)mp.kqy;
   const double i2 = 2.0 * (double)mp.inv2RT;      // 1/RT as the tile kernels form it
@@ -239,12 +251,20 @@ __device__ inline void axis_combine(const PointArgs& A, const MP<T>& mp, const d
     for (int b = 0; b < 3; ++b) H[a][b] = 0.0;
   for (int a = 0; a < 5; ++a)
     for (int b = 0; a + b < 5; ++b) {
-      const double cub = kx * (Sx[a + 3] * Sy[b] + Sx[a + 1] * Sy[b + 2]) +
-                         ky * (Sx[a + 2] * Sy[b + 1] + Sx[a] * Sy[b + 3]);
-      const double lin = kx * Sx[a + 1] * Sy[b] + ky * Sx[a] * Sy[b + 1];
-      G[a][b] = Sx[a] * Sy[b] - (D + 2) * lin + i2 * cub;
-      if (a + b < 3) H[a][b] = RT * c0 * Sx[a] * Sy[b] + al * cub - be * lin;
+      const double cub = kx * (P[a + 3][b] + P[a + 1][b + 2]) + ky * (P[a + 2][b + 1] + P[a][b + 3]);
+      const double lin = kx * P[a + 1][b] + ky * P[a][b + 1];
+      G[a][b] = P[a][b] - (D + 2) * lin + i2 * cub;
+      if (a + b < 3) H[a][b] = RT * c0 * P[a][b] + al * cub - be * lin;
     }
+}
+
+template <class T, int D>
+__device__ inline void axis_combine(const PointArgs& A, const MP<T>& mp, const double Sx[8], const double Sy[8],
+                                    double G[5][5], double H[3][3]) {
+  double P[8][8];
+  for (int i = 0; i < 8; ++i)
+    for (int j = 0; j < 8; ++j) P[i][j] = (i + j <= 7) ? Sx[i] * Sy[j] : 0.0;
+  pair_combine<T, D>(A, mp, P, G, H);
 }
 
 template <class T, int D>
@@ -347,6 +367,188 @@ __device__ inline void direct_moments(const PointArgs& A, const MP<T>& mp, int l
   G[0][1] = kv[2];
   // keep the compensated energy-row sum: fold it into the H[0][0] slot
   H[0][0] = 2.0 * kv[3] - G[2][0] - G[0][2];
+}
+
+// Compensated sum helpers (value s - c; FP64 sums carry no compensation).
+template <class T> __device__ __forceinline__ void csum_add(T& s, T& c, T x) {
+  if constexpr (sizeof(T) == 8) {
+    s += x;
+  } else {
+    const T y = x - c;
+    const T t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+}
+// (s, c) = (so, co) + (s, c), the rounding error of the sum kept exactly (TwoSum)
+template <class T> __device__ __forceinline__ void csum_merge(T& s, T& c, T so, T co) {
+  if constexpr (sizeof(T) == 8) {
+    s += so;
+  } else {
+    const T t = so + s;
+    const T bb = t - so;
+    const T e = (so - (t - bb)) + (s - bb);
+    c = (co + c) - e;
+    s = t;
+  }
+}
+
+// Shared-memory values (type T) a warp needs for row_moments on a space with n1 entries.
+__host__ __device__ inline int row_smem_values(int n1) {
+  const int q = 16 * (n1 + 4);
+  return q > 36 * 32 + 72 ? q : 36 * 32 + 72;
+}
+
+// The pair moments P[i][j] = sum over the space of w gauss(c_x) gauss(c_y) c_x^i c_y^j
+// (i + j <= 7) of a 2-D space that is not a tensor product, from its rows, by one warp (the
+// result on lane 0).  For every entry e (a distinct axis range, abscissa X_e, weight W_e) the
+// factor W_e gauss(X_e - u_x) (X_e - u_x)^i is summed into prefix sums per level block of
+// entries (compensated; the block's entries split into one contiguous run per lane, the runs
+// joined by a warp scan), so that a row's x sums are differences of prefix sums over its
+// segments; a row's y factor is one Gaussian.  P = sum over rows of Rx[i] Ry[j], summed per
+// lane and then over the lanes (compensated): entry k (i-major, i + j <= 7) as the unevaluated
+// difference wsm[36 * 32 + k] - wsm[36 * 32 + 36 + k], for every lane to read.
+// wsm: row_smem_values(n1) values of this warp.
+template <class T>
+__device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane, T* wsm) {
+  const T* e1 = reinterpret_cast<const T*>(A.e1);
+  const int n1 = A.n1, nq = n1 + 4;
+  T* Qs = wsm;            // [8][nq] prefix sums (s)
+  T* Qc = wsm + 8 * nq;   // [8][nq] their compensation (c)
+  for (int L = 0; L < 4; ++L) {
+    const int ls = A.lst[L], n = A.lst[L + 1] - ls;
+    if (n == 0) continue;
+    const int cs = (n + 31) / 32;
+    const int i0 = ls + min(n, lane * cs), i1 = ls + min(n, (lane + 1) * cs);
+    T s[8], c[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) s[a] = c[a] = T(0);
+    for (int e = i0; e < i1; ++e) {
+      const T x = e1[e] - mp.ux;
+      T p = e1[n1 + e] * Num<T>::gauss(x, mp.inv2RT, mp.lnh);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (a < 3) csum_add(s[a], c[a], p);
+        else s[a] += p;
+        p *= x;
+      }
+    }
+    // exclusive scan over the lanes: the start of every lane's run (compensated for the
+    // moments of order 0..2 in x, which the conserved rows take)
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      T ss = s[a], cc = c[a];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const T so = __shfl_up_sync(0xffffffffu, ss, o);
+        if (a < 3) {
+          const T co = __shfl_up_sync(0xffffffffu, cc, o);
+          if (lane >= o) csum_merge(ss, cc, so, co);
+        } else if (lane >= o) {
+          ss += so;
+        }
+      }
+      T xs = __shfl_up_sync(0xffffffffu, ss, 1), xc = T(0);
+      if (a < 3) xc = __shfl_up_sync(0xffffffffu, cc, 1);
+      if (lane == 0) xs = xc = T(0);
+      s[a] = xs;
+      c[a] = xc;
+    }
+    if (lane == 0)
+#pragma unroll
+      for (int a = 0; a < 8; ++a) Qs[a * nq + ls + L] = Qc[a * nq + ls + L] = T(0);
+    for (int e = i0; e < i1; ++e) {
+      const T x = e1[e] - mp.ux;
+      T p = e1[n1 + e] * Num<T>::gauss(x, mp.inv2RT, mp.lnh);
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        if (a < 3) {
+          csum_add(s[a], c[a], p);
+          Qc[a * nq + e + L + 1] = c[a];
+        } else {
+          s[a] += p;
+        }
+        Qs[a * nq + e + L + 1] = s[a];
+        p *= x;
+      }
+    }
+  }
+  __syncwarp();
+  // rows: Rx from the segments, Ry from the row's y entry; the first-order entries compensated
+  T M[36], Mc[3];
+#pragma unroll
+  for (int k = 0; k < 36; ++k) M[k] = T(0);
+  Mc[0] = Mc[1] = Mc[2] = T(0);
+  for (int r = lane; r < A.nrows; r += 32) {
+    const int4 R = A.rows[r];
+    const T y = e1[R.x] - mp.uy;
+    T py = e1[n1 + R.x] * Num<T>::gauss(y, mp.inv2RT, mp.lnh);
+    T Ry[8], Rs[8], Rc[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      Ry[b] = py;
+      py *= y;
+      Rs[b] = Rc[b] = T(0);
+    }
+    for (int sg = R.y; sg < R.y + R.z; ++sg) {
+      const int2 q = A.segs[sg];
+#pragma unroll
+      for (int a = 0; a < 8; ++a) {
+        Rs[a] += Qs[a * nq + q.y] - Qs[a * nq + q.x];
+        if (a < 3) Rc[a] += Qc[a * nq + q.y] - Qc[a * nq + q.x];
+      }
+    }
+    int k = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; i + j < 8; ++j, ++k) {
+        const T v = (Rs[i] - Rc[i]) * Ry[j];
+        if (k == 0 || k == 1 || k == 8) csum_add(M[k], Mc[k == 0 ? 0 : (k == 1 ? 1 : 2)], v);
+        else M[k] += v;
+      }
+  }
+  __syncwarp();
+  // over the lanes: through shared memory, one entry per lane (compensated)
+#pragma unroll
+  for (int k = 0; k < 36; ++k) {
+    const T cm = (k == 0) ? Mc[0] : (k == 1) ? Mc[1] : (k == 8) ? Mc[2] : T(0);
+    wsm[k * 32 + lane] = M[k] - cm;
+  }
+  __syncwarp();
+  for (int k = lane; k < 36; k += 32) {
+    T as = T(0), ac = T(0);
+    for (int l = 0; l < 32; ++l) csum_add(as, ac, wsm[k * 32 + l]);
+    wsm[36 * 32 + k] = as;
+    wsm[36 * 32 + 36 + k] = ac;
+  }
+  __syncwarp();
+}
+
+// The G and H entries of pair_combine from row_moments' pair moments, one entry per lane (FP64
+// work spread over the warp), stored to the split finalisation's scratch of point i: lane l <
+// 25 writes G slot l, lanes 25..31 H slots 0..6, lanes 0 and 1 also H slots 7 and 8.
+template <class T, int D>
+__device__ inline void row_store_gh(const PointArgs& A, const MP<T>& mp, int lane, const T* wsm, long i) {
+  auto P = [&](int a, int b) -> double {
+    const int k = 8 * a - a * (a - 1) / 2 + b;
+    return (double)wsm[36 * 32 + k] - (double)wsm[36 * 32 + 36 + k];
+  };
+  const StepConst& k = A.k;
+  const double kx = (double)mp.kqx, ky = (double)mp.kqy;
+  const double i2 = 2.0 * (double)mp.inv2RT;
+  const double RT = (double)mp.RT, c0 = k.c0;
+  const double al = RT * c0 * i2, be = RT * (D * c0 + k.twoK);
+  const long n = A.npt;
+  auto entry = [&](int a, int b, bool h) -> double {
+    if (a + b > (h ? 2 : 4)) return 0.0;
+    const double cub = kx * (P(a + 3, b) + P(a + 1, b + 2)) + ky * (P(a + 2, b + 1) + P(a, b + 3));
+    const double lin = kx * P(a + 1, b) + ky * P(a, b + 1);
+    return h ? RT * c0 * P(a, b) + al * cub - be * lin : P(a, b) - (D + 2) * lin + i2 * cub;
+  };
+  if (lane < 25) A.scr[(FS_G + lane) * n + i] = entry(lane / 5, lane % 5, false);
+  else A.scr[(FS_H + lane - 25) * n + i] = entry((lane - 25) / 3, (lane - 25) % 3, true);
+  if (lane < 2) A.scr[(FS_H + 7 + lane) * n + i] = 0.0;
 }
 
 // Model parameters of a point with state (rho, u, T, q), before the correction.
@@ -736,6 +938,13 @@ __global__ void k_fin_sums(const PointArgs a) {
     }
     if (lane != 0) return;
     axis_combine<T, D>(a, q, Sx, Sy, G, H);
+  } else if (D == 2 && a.rows) {
+    // a space that is not a tensor product, from its rows
+    extern __shared__ __align__(16) unsigned char fsm[];
+    T* wsm = reinterpret_cast<T*>(fsm) + (size_t)(threadIdx.x >> 5) * row_smem_values(a.n1);
+    row_moments<T>(a, q, lane, wsm);
+    row_store_gh<T, D>(a, q, lane, wsm, i);
+    return;
   } else {
     direct_moments<T, D, 32>(a, q, lane, G, H);
   }

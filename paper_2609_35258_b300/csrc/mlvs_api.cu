@@ -92,6 +92,10 @@ struct SpaceRt {
   DevBuf vt, ax, ainv;
   DevBuf owner_d, xid, kp_d; // criterion tables: owner, FP64 coordinates, keff (bytes)
   DevBuf geo;                // [5][nv] geometric sums of every point's rectangle
+  // 2-D spaces that are not tensor products: the row tables of the finalisation's velocity
+  // sums (entries [2][n1] X, W; level blocks [5]; rows; segments)
+  DevBuf e1, lst, rows, segs;
+  int n1 = 0, nrows = 0;
 };
 
 struct CSR {
@@ -271,6 +275,74 @@ int tile_h(int D) { return D == 2 ? kTY2 : 1; }
 // ---------------------------------------------------------------------------------------
 // spaces and projection tables
 
+// Row tables of a 2-D space that is not a tensor product (the split finalisation's velocity
+// sums): entries = the distinct axis ranges of its points, each at the lowest level whose
+// groups contain it, ordered by (level, first base node); rows = the points sharing a y
+// entry; a row's segments = its runs of consecutive x entries of one level.  Every point lies
+// in exactly one segment of its row.
+static cudaError_t row_tables(mlvs_handle* h, SpaceRt& S) {
+  const int n = h->n_base, nv = S.vs.nv();
+  std::map<std::pair<int, int>, int> level_of;
+  for (int L = 3; L >= 0; --L)
+    for (const auto& g : groups_1d(n, L)) level_of[g] = L;
+  std::set<std::pair<int, std::pair<int, int>>> used;   // (level, range)
+  for (int v = 0; v < nv; ++v)
+    for (int d = 0; d < 2; ++d) {
+      const std::pair<int, int> r(S.vs.rect[4 * v + 2 * d], S.vs.rect[4 * v + 2 * d + 1]);
+      auto it = level_of.find(r);
+      if (it == level_of.end()) return cudaSuccess;   // not a union of level groups: direct sums
+      used.insert({it->second, r});
+    }
+  std::map<std::pair<int, int>, int> ent;
+  std::vector<int> lvl;
+  std::vector<double> ex, ew;
+  std::vector<int> lst(5, 0);
+  for (const auto& u : used) {
+    ent[u.second] = (int)ex.size();
+    lvl.push_back(u.first);
+    double X, W;
+    merged(h->base, u.second.first, u.second.second, X, W);
+    ex.push_back(X);
+    ew.push_back(W);
+    for (int L = u.first + 1; L <= 4; ++L) lst[L] = (int)ex.size();
+  }
+  const int n1 = (int)ex.size();
+  std::map<int, std::vector<int>> row_of;   // y entry -> x entries
+  for (int v = 0; v < nv; ++v)
+    row_of[ent.at({S.vs.rect[4 * v + 2], S.vs.rect[4 * v + 3]})].push_back(
+        ent.at({S.vs.rect[4 * v], S.vs.rect[4 * v + 1]}));
+  std::vector<int4> rows;
+  std::vector<int2> segs;
+  long covered = 0;
+  for (auto& r : row_of) {
+    std::vector<int>& xs = r.second;
+    std::sort(xs.begin(), xs.end());
+    const int first = (int)segs.size();
+    for (size_t i = 0; i < xs.size();) {
+      size_t j = i + 1;
+      while (j < xs.size() && xs[j] == xs[j - 1] + 1 && lvl[xs[j]] == lvl[xs[i]]) ++j;
+      const int L = lvl[xs[i]];
+      segs.push_back(make_int2(xs[i] + L, xs[j - 1] + 1 + L));
+      covered += (long)(j - i);
+      i = j;
+    }
+    rows.push_back(make_int4(r.first, first, (int)segs.size() - first, 0));
+  }
+  if (covered != nv) return cudaSuccess;
+  std::vector<double> e1(2 * (size_t)n1);
+  for (int e = 0; e < n1; ++e) { e1[e] = ex[e]; e1[n1 + e] = ew[e]; }
+  cudaError_t err;
+  if (h->tsize == 8) err = upload(S.e1, e1, h->stream);
+  else err = upload(S.e1, std::vector<float>(e1.begin(), e1.end()), h->stream);
+  if (err != cudaSuccess) return err;
+  if ((err = upload(S.lst, lst, h->stream)) != cudaSuccess) return err;
+  if ((err = upload(S.rows, rows, h->stream)) != cudaSuccess) return err;
+  if ((err = upload(S.segs, segs, h->stream)) != cudaSuccess) return err;
+  S.n1 = n1;
+  S.nrows = (int)rows.size();
+  return cudaSuccess;
+}
+
 static mlvs_status get_space(mlvs_handle* h, const std::vector<int>& kappa, int* out) {
   std::vector<int> keff = enforce_consistency(kappa, h->n_base, h->D);
   auto it = h->space_of_key.find(keff);
@@ -333,6 +405,7 @@ static mlvs_status get_space(mlvs_handle* h, const std::vector<int>& kappa, int*
     }
     CK(upload(S.geo, geo, h->stream));
   }
+  if (!uni && h->D == 2) CK(row_tables(h, S));
   h->spaces.push_back(std::move(S));
   *out = (int)h->spaces.size() - 1;
   h->space_of_key[keff] = *out;
@@ -417,11 +490,30 @@ template <class S, class T, int D> struct Runner {
     a.need = L.fneed.as<int>();
     h->launches += 2;
     k_fin_pre<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
-    k_fin_sums<T, D><<<std::max(1, (a.nwork * 32 + 127) / 128), 128, 0, h->stream>>>(a);
+    size_t sm = 0;
+    if (a.rows) {   // the row tables' prefix sums: shared memory per warp (4 warps per CTA)
+      sm = (size_t)4 * row_smem_values(a.n1) * sizeof(T);
+      if (sm > (size_t)smem_optin()) {
+        a.rows = nullptr;   // the direct sums need none
+        sm = 0;
+      }
+    }
+    k_fin_sums<T, D><<<std::max(1, (a.nwork * 32 + 127) / 128), 128, sm, h->stream>>>(a);
     k_fin_post<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
   }
 
+  // largest dynamic shared memory a CTA may opt in to on the current device
+  static int smem_optin() {
+    int dev = 0, v = 48 * 1024;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+  }
+
   static cudaError_t set_smem_limits() {
+    {
+      cudaError_t e = cudaFuncSetAttribute(k_fin_sums<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+      if (e != cudaSuccess) return e;
+    }
     const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false, false>,
                          (const void*)k_faces<S, T, D, TX, TY, true, false>,
                          (const void*)k_update<S, T, D, TX, TY, VPC, false, false>,
@@ -522,6 +614,12 @@ template <class S, class T, int D> struct Runner {
     a.need = nullptr;
     a.msum = nullptr;
     a.wden = h->curvi ? L.wden.as<double>() : nullptr;
+    a.e1 = sp.nrows > 0 ? sp.e1.p : nullptr;
+    a.n1 = sp.n1;
+    a.lst = sp.lst.as<int>();
+    a.rows = sp.nrows > 0 ? sp.rows.as<int4>() : nullptr;
+    a.nrows = sp.nrows;
+    a.segs = sp.segs.as<int2>();
     return a;
   }
 
