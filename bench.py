@@ -195,11 +195,13 @@ STEADY_MAX = 10000       # the paper's cavity runs stop at 10,000 steps
 
 
 def _steady(desc, stream, mlvs):
-    """Steps (100 at a time) until the residual falls below STEADY_TOL; device time."""
+    """Steps (100 at a time, as two-step CUDA graphs) until the residual falls below STEADY_TOL;
+    device time."""
     from paper_2609_35258_b300 import mlvs as M
     from paper_2609_35258_b300.solver import Solver
     import numpy as np
     s = Solver(desc, stream=stream, adaptive=1)
+    M.mlvs_set_graph(s.h, True)                 # both runs as two-step CUDA graphs
     if mlvs:
         M.mlvs_set_adaptation(s.h, M.adapt_params(*MLVS_PARAMS), ADAPT_INTERVAL)
     F = M.RHO | M.U | M.V | M.T
@@ -569,6 +571,7 @@ def run_ours(args, rank, world, local_rank):
     nv = 101 * 101
     upd_step = ncell * nv
     s = Solver(desc, stream=stream.cuda_stream)
+    M.mlvs_set_graph(s.h, True)                 # two-step CUDA graphs (per-phase runs launch eagerly)
     s.step(args.warmup)
     torch.cuda.synchronize()
     if dist:
@@ -611,6 +614,7 @@ def run_ours(args, rank, world, local_rank):
     mlvs = None
     if not args.no_mlvs:
         sm_ = Solver(desc, stream=stream.cuda_stream, adaptive=1)
+        M.mlvs_set_graph(sm_.h, True)
         sm_.step(max(args.warmup, 200))
         ast = M.mlvs_adapt(sm_.h, M.adapt_params(*MLVS_PARAMS))
         M.mlvs_set_adaptation(sm_.h, M.adapt_params(*MLVS_PARAMS), ADAPT_INTERVAL)

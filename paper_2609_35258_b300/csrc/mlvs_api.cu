@@ -1410,21 +1410,21 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
     std::set<int> gset;
     for (int f = 0; f < nface; ++f) {
       if (role[l][f] != FR_NORMAL && role[l][f] != FR_CROSS) continue;
-      std::vector<int> st;
+      int st[8], ns = 0;   // the face's stencil cells: four normal, four tangential
       if (f < nfx * ny) {
         const int gj = f / nfx, gi = f % nfx;
-        for (int d = -2; d <= 1; ++d) st.push_back(wrapc(gj, ny, py) * nx + wrapc(gi + d, nx, px));
+        for (int d = -2; d <= 1; ++d) st[ns++] = wrapc(gj, ny, py) * nx + wrapc(gi + d, nx, px);
         if (D == 2)
           for (int d : {-1, 1})
-            for (int e : {-1, 0}) st.push_back(wrapc(gj + d, ny, py) * nx + wrapc(gi + e, nx, px));
+            for (int e : {-1, 0}) st[ns++] = wrapc(gj + d, ny, py) * nx + wrapc(gi + e, nx, px);
       } else {
         const int r = f - nfx * ny, gj = r / nx, gi = r % nx;
-        for (int d = -2; d <= 1; ++d) st.push_back(wrapc(gj + d, ny, py) * nx + gi);
+        for (int d = -2; d <= 1; ++d) st[ns++] = wrapc(gj + d, ny, py) * nx + gi;
         for (int d : {-1, 1})
-          for (int e : {-1, 0}) st.push_back(wrapc(gj + e, ny, py) * nx + wrapc(gi + d, nx, px));
+          for (int e : {-1, 0}) st[ns++] = wrapc(gj + e, ny, py) * nx + wrapc(gi + d, nx, px);
       }
-      for (int c : st)
-        if (lvl_of[c] != l) gset.insert(c);
+      for (int q = 0; q < ns; ++q)
+        if (lvl_of[st[q]] != l) gset.insert(st[q]);
     }
     I.lv[l].ghost_cells.assign(gset.begin(), gset.end());
     ghost_col[l].assign(ncell, -1);

@@ -45,6 +45,15 @@ template <class X> static inline X __shfl_xor_sync(unsigned, X v, int, int = 32)
   std::abort();
   return v;
 }
+template <class X> static inline X __shfl_up_sync(unsigned, X v, unsigned, int = 32) {
+  std::fprintf(stderr, "emulation: a warp shuffle was reached; lanes are not emulated\n");
+  std::abort();
+  return v;
+}
+static inline void __syncwarp(unsigned = 0xffffffffu) {
+  std::fprintf(stderr, "emulation: a warp barrier was reached; lanes are not emulated\n");
+  std::abort();
+}
 // packed two-lane FP32 (sm_100 and later): each lane an IEEE operation, as on the GPU
 static inline float2 __fadd2_rn(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
 static inline float2 __fmul2_rn(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }
