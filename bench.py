@@ -512,7 +512,8 @@ def _unstructured_leg(storage="f32", m=10, n_base=101, umax=6.0, steps=50, warm=
                     "updates_per_s": nc * nv * steps / (ms * 1e-3), "steps": steps,
                     "rel_mass_drift": abs(m2 - m1) / m1,
                     "launches_per_step": 7,
-                    "hbm_bytes_per_update_this_version": 240 if storage == "f32" else 480,
+                    # DRAM traffic per update measured with ncu on two_cavities(4) in FP32
+                    "hbm_bytes_per_update_measured": 152 if storage == "f32" else None,
                     "algorithmic_bytes_per_update": 16 if storage == "f32" else 32})
     except M.MLVSError as e:
         out["error"] = str(e)
@@ -751,9 +752,16 @@ def main():
     ap.add_argument("--no-unstructured", action="store_true",
                     help="skip the two-cavity unstructured-mesh leg (13,600 quads, 101^2 velocities, "
                          "run in a child process)")
+    ap.add_argument("--only-unstructured", type=int, default=0, metavar="M",
+                    help="run only the two-cavity unstructured leg, in this process, on the mesh "
+                         "two_cavities(M) (M = 10: 13,600 quads), for --steps steps after --warmup "
+                         "steps, and print its JSON (for profiling a smaller case)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.only_unstructured:
+        print(json.dumps(_unstructured_leg(m=args.only_unstructured, steps=args.steps, warm=args.warmup)))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
