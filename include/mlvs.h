@@ -93,6 +93,14 @@ typedef struct {
                            mapping_nine_targets to mapping_h_residual_correction: the source's
                            raw moments up to G and J as targets), one launch per route;
                            0 or 4: the four-moment mapping                                   */
+  int compat_moments;   /* 8 (dim 2): the compatibility correction at cells and faces
+                           (compat_cell, compat_face) is the eight-moment correction of Sec.
+                           3.3.1 (Eq. eq_eight_basis, Eq. eq_eight_moment_constraint), whose
+                           heat-flux target is the Shakhov model's own heat flux (1 - Pr) q;
+                           freestream sides keep the four-moment correction.  Runs on one
+                           level whose space is a tensor product (mlvs_set_velocity_levels with
+                           one uniform level and adaptive = 0; else MLVS_ERR_ARG).  0 or 4:
+                           the four-moment correction                                        */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */

@@ -43,6 +43,8 @@ struct TileArgs {
   void* X;               // (T) [2][nv][nX] microfluxes of the cross faces evaluated here
   int nX;
   const int* xfid;       // [nX] face id of every column of X
+  const void* cparam8;   // eight-moment correction (C8): (T) [4][nslot] b4..b7 of the cells
+  const void* fparam8;   //                                (T) [4][nface] b4..b7 of the faces
   const void* Y;         // (T) [2][nv][nY] microfluxes mapped here from other face spaces
   int nY;
   void* fbar;            // (T) [2][nv][nface] face phi-bar of the faces this level evaluates
@@ -168,8 +170,8 @@ template <class T, int TX, int TY, int D, int VPC> struct UpdSmem {
   static constexpr size_t F = 0;                                           // V [2][2][NF]
   static constexpr size_t C = F + sizeof(V) * 2 * 2 * G::NF;               // V [2][2][SC][NX3]
   static constexpr size_t VT = C + sizeof(V) * 2 * 2 * SC * NX3;           // V [NPT][4]
-  static constexpr size_t XP = VT + sizeof(V) * 4 * NPT;                   // T [16][NX3]
-  static constexpr size_t XI = XP + sizeof(T) * 16 * NX3;                  // long [4][NX3]
+  static constexpr size_t XP = VT + sizeof(V) * 4 * NPT;                   // T [20][NX3]
+  static constexpr size_t XI = XP + sizeof(T) * 20 * NX3;                  // long [4][NX3]
   static constexpr size_t BYTES = (XI + sizeof(long) * 4 * NX3 + 15) / 16 * 16;
 };
 
@@ -345,7 +347,7 @@ __device__ __forceinline__ void load_args(TileArgs& dst, const TileArgs* __restr
 // same strict sign of xi.n (nearly every pair) the pair takes one upwind cell; otherwise each
 // lane is reconstructed on its own.  Warp 0 of a tile whose high edge is a non-periodic mesh
 // end does the same for the faces on that edge.
-template <class S, class T, int D, int TX, int TY, bool ML, bool CV>
+template <class S, class T, int D, int TX, int TY, bool ML, bool CV, bool C8 = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
 k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restrict__ work, int limiter) {
   __shared__ __align__(16) TileArgs sa;
@@ -438,6 +440,16 @@ k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restr
   m1.zero();
   if (kind0 == 1) m0.load(cp, ns, col0);
   if (kind1 == 1) m1.load(cp, ns, col1);
+  // b4..b7 of the eight-moment correction (C8)
+  T b80[4] = {T(0), T(0), T(0), T(0)}, b81[4] = {T(0), T(0), T(0), T(0)};
+  if constexpr (C8) {
+    const T* __restrict__ cp8 = reinterpret_cast<const T*>(a.cparam8);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (kind0 == 1) b80[m] = cp8[m * ns + col0];
+      if (kind1 == 1) b81[m] = cp8[m * ns + col1];
+    }
+  }
   const int e0 = B::bidx(tx, ty);
   const void* p0 = fin;
   long st0 = 0;
@@ -653,7 +665,8 @@ k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restr
     // ---- phi-bar-plus = phi~ + b (phi^S - phi~) of the own cell and the halo cell
     if (!ML || kind0 == 1) {
       V gs, hs;
-      model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
+      if constexpr (C8) model_eval2c8<T>(m0, b80, xix, xiy, c0, twoK, gs, hs);
+      else model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
       Pg[e0] = P::fma(P::splat(m0.c1), P::sub(gs, g0), g0);
       Ph[e0] = P::fma(P::splat(m0.c1), P::sub(hs, h0), h0);
     } else {
@@ -663,7 +676,8 @@ k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restr
     if (halo) {
       if (!ML || kind1 == 1) {
         V gs, hs;
-        model_eval2<T, D>(m1, xix, xiy, c0, twoK, gs, hs);
+        if constexpr (C8) model_eval2c8<T>(m1, b81, xix, xiy, c0, twoK, gs, hs);
+        else model_eval2<T, D>(m1, xix, xiy, c0, twoK, gs, hs);
         Pg[e1] = P::fma(P::splat(m1.c1), P::sub(gs, g1), g1);
         Ph[e1] = P::fma(P::splat(m1.c1), P::sub(hs, h1), h1);
       } else {
@@ -713,6 +727,7 @@ template <class T> struct UFace {
   long col = 0;   // column in X (FR_CROSS) or Y (FR_RECV)
   MP<T> m;
   T nx = T(0), ny = T(0), area = T(1);
+  T b8[4] = {T(0), T(0), T(0), T(0)};   // eight-moment correction (C8)
 };
 
 // Microflux (xi.n) phi (Eq. interface_reduced_fluxes, times |S| on curvilinear meshes) of an
@@ -720,7 +735,7 @@ template <class T> struct UFace {
 // interior faces; on boundary faces the model enters (wall: rho_w = c1 + c2 times the
 // unit-density wall Maxwellian; freestream: c1 = 1, c2 = 0 and the corrected freestream
 // Maxwellian) and the reconstruction leaves, lane by lane.
-template <class T, int D, bool CV>
+template <class T, int D, bool CV, bool C8 = false>
 __device__ __forceinline__ void face_flux2(const UFace<T>& F, int dir, V2<T> xix, V2<T> xiy, V2<T> gb, V2<T> hb,
                                            T c0, T twoK, V2<T>& Fg, V2<T>& Fh) {
   using P = Pk<T>;
@@ -730,7 +745,8 @@ __device__ __forceinline__ void face_flux2(const UFace<T>& F, int dir, V2<T> xix
   if constexpr (CV) xn = P::add(P::mul(xix, P::splat(F.nx)), P::mul(xiy, P::splat(F.ny)));
   else xn = (dir == 0) ? xix : xiy;
   V2<T> gs, hs, gf, hf;
-  model_eval2<T, D>(F.m, xix, xiy, c0, twoK, gs, hs);
+  if constexpr (C8) model_eval2c8<T>(F.m, F.b8, xix, xiy, c0, twoK, gs, hs);
+  else model_eval2<T, D>(F.m, xix, xiy, c0, twoK, gs, hs);
   if (F.kind == FK_INTERIOR) {
     // weights summing to one, explicitly rounded: the two tiles that evaluate a shared face
     // produce the same bits (exact flux telescoping)
@@ -760,7 +776,7 @@ __device__ __forceinline__ void face_flux2(const UFace<T>& F, int dir, V2<T> xix
 // thread (face tid % NX3, pairs tid / NX3 + k NT / NX3), so the work per round is the same in
 // every warp.  A face received from another level takes the microflux mapped to this level
 // (Y), which k_cross_flux and the mapping produce before the launch.  Requires k.vpc <= VPC.
-template <class S, class T, int D, int TX, int TY, int VPC, bool ML, bool CV>
+template <class S, class T, int D, int TX, int TY, int VPC, bool ML, bool CV, bool C8 = false>
 __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256) ? 2 : 4)
 k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restrict__ work) {
   __shared__ __align__(16) TileArgs sa;
@@ -840,6 +856,12 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
   MP<T> m0;
   if (own_active) m0.load(cp, ns, col0);
   else m0.zero();
+  T b80[4] = {T(0), T(0), T(0), T(0)};   // b4..b7 of the eight-moment correction (C8)
+  if constexpr (C8) {
+    if (own_active)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) b80[m] = reinterpret_cast<const T*>(a.cparam8)[m * ns + col0];
+  }
   T lamx = T(k.dt / k.dx), lamy = T(k.dt / k.dy);
   if constexpr (CV) {
     if (own_active) lamx = lamy = cg[4L * k.ncell + ((D == 2) ? gy : 0) * k.nx + gx];   // dt / |V|
@@ -858,7 +880,12 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
     F.m.zero();
     if (!(F.meta & FM_VALID)) { F.meta = 0; F.role = FR_NONE; return; }
     if (F.role == FR_CROSS || F.role == FR_RECV) F.col = a.fslot[fid];
-    if (F.role == FR_NORMAL || F.role == FR_CROSS) F.m.load(fp, nfc, fid);
+    if (F.role == FR_NORMAL || F.role == FR_CROSS) {
+      F.m.load(fp, nfc, fid);
+      if constexpr (C8)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) F.b8[m] = reinterpret_cast<const T*>(a.fparam8)[m * nfc + fid];
+    }
     if constexpr (CV) {
       F.nx = fg[fid];
       F.ny = fg[nfc + fid];
@@ -890,6 +917,9 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
                       FC.m.b1, FC.m.b2, FC.m.b3, FC.m.c1, FC.m.c2, FC.nx, FC.ny, FC.area};
 #pragma unroll
     for (int p = 0; p < 16; ++p) sXP[p * NX3 + tid] = pv[p];
+    if constexpr (C8)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) sXP[(16 + m) * NX3 + tid] = FC.b8[m];
     sXI[tid] = FC.meta;
     sXI[NX3 + tid] = FC.kind;
     sXI[2 * NX3 + tid] = FC.fid;
@@ -949,6 +979,9 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
       FC.m.kqx = X3p[4 * NX3]; FC.m.kqy = X3p[5 * NX3]; FC.m.RT = X3p[6 * NX3]; FC.m.b0 = X3p[7 * NX3];
       FC.m.b1 = X3p[8 * NX3]; FC.m.b2 = X3p[9 * NX3]; FC.m.b3 = X3p[10 * NX3]; FC.m.c1 = X3p[11 * NX3];
       FC.m.c2 = X3p[12 * NX3]; FC.nx = X3p[13 * NX3]; FC.ny = X3p[14 * NX3]; FC.area = X3p[15 * NX3];
+      if constexpr (C8)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) FC.b8[m] = X3p[(16 + m) * NX3];
       V* Cg = sC + (cbuf * 2 + 0) * SC * NX3;
       V* Ch = sC + (cbuf * 2 + 1) * SC * NX3;
       for (int jj = jc0; jj < SC; jj += NT / NX3) {
@@ -957,7 +990,7 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
         V gl, hl;
         ldface(roleC, fidC, colC, v, gl, hl);
         V Fg = gl, Fh = hl;
-        if (evC) face_flux2<T, D, CV>(FC, dirC, sVT[4 * (jb + jj)], sVT[4 * (jb + jj) + 1], gl, hl, c0, twoK, Fg, Fh);
+        if (evC) face_flux2<T, D, CV, C8>(FC, dirC, sVT[4 * (jb + jj)], sVT[4 * (jb + jj) + 1], gl, hl, c0, twoK, Fg, Fh);
         Cg[jj * NX3 + qc] = Fg;
         Ch[jj * NX3 + qc] = Fh;
       }
@@ -977,20 +1010,21 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
       V* Fh = sF + (buf * 2 + 1) * G::NF;
       // faces A and B evaluated without a branch (a received face takes its mapped flux)
       V FAg, FAh;
-      face_flux2<T, D, CV>(FA, 0, xix, xiy, ga, ha, c0, twoK, FAg, FAh);
+      face_flux2<T, D, CV, C8>(FA, 0, xix, xiy, ga, ha, c0, twoK, FAg, FAh);
       if (!evA) { FAg = ga; FAh = ha; }
       Fg[fA] = FAg;
       Fh[fA] = FAh;
       if (D == 2) {
         V FBg, FBh;
-        face_flux2<T, D, CV>(FB, 1, xix, xiy, gbb, hbb, c0, twoK, FBg, FBh);
+        face_flux2<T, D, CV, C8>(FB, 1, xix, xiy, gbb, hbb, c0, twoK, FBg, FBh);
         if (!evB) { FBg = gbb; FBh = hbb; }
         Fg[fB] = FBg;
         Fh[fB] = FBh;
       }
       // the collision part of phi~+ - phi~ = (4/3) b (phi^S - phi~)
       V gs, hs;
-      model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
+      if constexpr (C8) model_eval2c8<T>(m0, b80, xix, xiy, c0, twoK, gs, hs);
+      else model_eval2<T, D>(m0, xix, xiy, c0, twoK, gs, hs);
       V dg = P::mul(P::splat(m0.c2), P::sub(gs, g0));
       V dh = P::mul(P::splat(m0.c2), P::sub(hs, h0));
       __syncthreads();

@@ -65,6 +65,10 @@ struct PointArgs {
   const int4* rows;
   int nrows;
   const int2* segs;
+  // the eight-moment correction (2-D, tensor-product spaces, one thread per point): b4..b7 of
+  // every point into prm8_out [4][npt] (T; zeros where the four-moment correction or none
+  // applies); null: the four-moment correction
+  void* prm8_out;
 };
 
 // Split finalisation: k_fin_pre (thread per point: state, uncorrected model), k_fin_sums (warp
@@ -551,6 +555,150 @@ __device__ inline void row_store_gh(const PointArgs& A, const MP<T>& mp, int lan
   if (lane < 2) A.scr[(FS_H + 7 + lane) * n + i] = 0.0;
 }
 
+// ---- eight-moment compatibility correction (Sec. 3.3.1, Eq. eq_eight_basis) ----
+// The correction factor 1 + sum_m b_m phi_m uses the basis, in peculiar velocity c = xi - u,
+//   {1, c_x, c_y, |c|^2, |c|^2 c_x, |c|^2 c_y, c_x^2 - c_y^2, c_x c_y},
+// the span of Eq. eq_eight_basis {1, xi_x, xi_y, E_xi, E_c c_x, E_c c_y, c_x^2 - c_y^2, c_x c_y}.
+// The constraint rows are (g, c g, (|c|^2 g + h)/2, (|c|^2 g + h) c / 2, (c_x^2 - c_y^2) g,
+// c_x c_y g) with targets (rho, rho (u - u_p), rho e + rho |u - u_p|^2 / 2, q^tar, 0, 0), u_p the
+// velocity of the parameters: the conserved rows combine the paper's, and the heat-flux and
+// stress rows are the paper's about u (u_p = u up to the rounding of the stored velocity).
+
+// one-axis sums S[a] = sum_i W_i gauss(X_i - u) (X_i - u)^a, a = 0..9
+template <class T>
+__device__ inline void u_axis_sums10(const T* ax, int nax, T u, T inv2RT, T lnh, double S[10]) {
+  KSum<T> acc[10];
+  for (int k = 0; k < 10; ++k) acc[k].zero();
+  for (int i = 0; i < nax; ++i) {
+    const T c = ax[i] - u;
+    T p = ax[nax + i] * Num<T>::gauss(c, inv2RT, lnh);
+    for (int k = 0; k < 10; ++k) {
+      acc[k].add(p);
+      p *= c;
+    }
+  }
+  for (int k = 0; k < 10; ++k) S[k] = acc[k].val();
+}
+
+// peculiar moments of the uncorrected Shakhov model on the tensor-product space:
+//   G[a][b] = sum w g^S c_x^a c_y^b (a + b <= 6),  H[a][b] = sum w h^S c_x^a c_y^b (a + b <= 4)
+template <class T>
+__device__ inline void u_moments8(const PointArgs& A, const MP<T>& mp, double G[7][7], double H[5][5]) {
+  const T* ax = reinterpret_cast<const T*>(A.ax);
+  double Sx[10], Sy[10];
+  u_axis_sums10<T>(ax, A.k.nax, mp.ux, mp.inv2RT, mp.lnh, Sx);
+  u_axis_sums10<T>(ax, A.k.nax, mp.uy, mp.inv2RT, mp.lnh, Sy);
+  const double kx = (double)mp.kqx, ky = (double)mp.kqy;
+  const double i2 = 2.0 * (double)mp.inv2RT, RT = (double)mp.RT, c0 = A.k.c0;
+  const double al = RT * c0 * i2, be = RT * (2.0 * c0 + A.k.twoK);
+  for (int x = 0; x < 7; ++x)
+    for (int y = 0; y < 7; ++y) G[x][y] = 0.0;
+  for (int x = 0; x < 5; ++x)
+    for (int y = 0; y < 5; ++y) H[x][y] = 0.0;
+  for (int x = 0; x < 7; ++x)
+    for (int y = 0; x + y < 7; ++y) {
+      const double cub = kx * (Sx[x + 3] * Sy[y] + Sx[x + 1] * Sy[y + 2]) + ky * (Sx[x + 2] * Sy[y + 1] + Sx[x] * Sy[y + 3]);
+      const double lin = kx * Sx[x + 1] * Sy[y] + ky * Sx[x] * Sy[y + 1];
+      G[x][y] = Sx[x] * Sy[y] - 4.0 * lin + i2 * cub;
+      if (x + y < 5) H[x][y] = RT * c0 * Sx[x] * Sy[y] + al * cub - be * lin;
+    }
+}
+
+// Polynomials in (c_x, c_y): up to four terms (coefficient, power of c_x, power of c_y).
+struct UPoly {
+  int n;
+  double c[4];
+  int px[4], py[4];
+};
+
+__device__ inline UPoly u_basis8(int m) {
+  UPoly p;
+  switch (m) {
+    case 0: p = {1, {1, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}}; break;
+    case 1: p = {1, {1, 0, 0, 0}, {1, 0, 0, 0}, {0, 0, 0, 0}}; break;
+    case 2: p = {1, {1, 0, 0, 0}, {0, 0, 0, 0}, {1, 0, 0, 0}}; break;
+    case 3: p = {2, {1, 1, 0, 0}, {2, 0, 0, 0}, {0, 2, 0, 0}}; break;
+    case 4: p = {2, {1, 1, 0, 0}, {3, 1, 0, 0}, {0, 2, 0, 0}}; break;
+    case 5: p = {2, {1, 1, 0, 0}, {2, 0, 0, 0}, {1, 3, 0, 0}}; break;
+    case 6: p = {2, {1, -1, 0, 0}, {2, 0, 0, 0}, {0, 2, 0, 0}}; break;
+    default: p = {1, {1, 0, 0, 0}, {1, 0, 0, 0}, {1, 0, 0, 0}}; break;
+  }
+  return p;
+}
+
+// constraint row k: g-part and h-part polynomials (the h-part of rows 3..5 is h/2 times c^e)
+__device__ inline void u_row8(int k, UPoly& pg, UPoly& ph) {
+  ph.n = 0;
+  if (k <= 2) {
+    pg = u_basis8(k);
+  } else if (k == 3) {
+    pg = {2, {0.5, 0.5, 0, 0}, {2, 0, 0, 0}, {0, 2, 0, 0}};
+    ph = {1, {0.5, 0, 0, 0}, {0, 0, 0, 0}, {0, 0, 0, 0}};
+  } else if (k == 4) {
+    pg = {2, {0.5, 0.5, 0, 0}, {3, 1, 0, 0}, {0, 2, 0, 0}};
+    ph = {1, {0.5, 0, 0, 0}, {1, 0, 0, 0}, {0, 0, 0, 0}};
+  } else if (k == 5) {
+    pg = {2, {0.5, 0.5, 0, 0}, {2, 0, 0, 0}, {1, 3, 0, 0}};
+    ph = {1, {0.5, 0, 0, 0}, {0, 0, 0, 0}, {1, 0, 0, 0}};
+  } else {
+    pg = u_basis8(k);
+  }
+}
+
+// b0..b7 of the eight-moment correction of mp (uncorrected Shakhov parameters of the state
+// rho, u, T with heat-flux target q_tar); b0..b3 go to mp, b4..b7 to b8.
+template <class T>
+__device__ inline bool u_correct8(const PointArgs& A, double rho, double ux, double uy, double Tm, double qtx,
+                                  double qty, MP<T>& mp, T b8[4]) {
+  double G[7][7], H[5][5];
+  u_moments8<T>(A, mp, G, H);
+  double M[8][8], r[8];
+  for (int k = 0; k < 8; ++k) {
+    UPoly pg, ph;
+    u_row8(k, pg, ph);
+    for (int m = 0; m < 8; ++m) {
+      const UPoly q = u_basis8(m);
+      double s = 0.0;
+      for (int i = 0; i < pg.n; ++i)
+        for (int j = 0; j < q.n; ++j) s += pg.c[i] * q.c[j] * G[pg.px[i] + q.px[j]][pg.py[i] + q.py[j]];
+      for (int i = 0; i < ph.n; ++i)
+        for (int j = 0; j < q.n; ++j) s += ph.c[i] * q.c[j] * H[ph.px[i] + q.px[j]][ph.py[i] + q.py[j]];
+      M[k][m] = s;
+    }
+  }
+  const double RT = A.gas.R * Tm;
+  const double dux = ux - (double)mp.ux, duy = uy - (double)mp.uy;
+  const double tar[8] = {rho, rho * dux, rho * duy,
+                         0.5 * (3.0 + A.gas.K) * rho * RT + 0.5 * rho * (dux * dux + duy * duy), qtx, qty, 0.0, 0.0};
+  for (int k = 0; k < 8; ++k) r[k] = tar[k] - M[k][0];
+  if (!solve_pivoted<8>(M, r, 8)) return false;
+  mp.b0 = T(r[0]); mp.b1 = T(r[1]); mp.b2 = T(r[2]); mp.b3 = T(r[3]);
+  for (int m = 0; m < 4; ++m) b8[m] = T(r[4 + m]);
+  return true;
+}
+
+// Shakhov model times the eight-term correction factor (model_eval's operation order for the
+// model itself, then the factor).
+template <class T>
+__device__ __forceinline__ void u_model_eval8(const MP<T>& p, const T* b8, T xix, T xiy, T c0, T twoK, T& g,
+                                              T& h) {
+  using N = Num<T>;
+  const T cx = N::sub(xix, p.ux), cy = N::sub(xiy, p.uy);
+  const T geq = maxwell_sep<T, 2>(p, cx, cy);
+  const T cc = N::fma(cy, cy, N::mul(cx, cx));
+  const T cq = N::fma(p.kqy, cy, N::mul(p.kqx, cx));
+  const T t = N::mul(N::mul(T(2), p.inv2RT), cc);
+  const T gs = N::mul(geq, N::fma(cq, N::sub(t, T(4)), T(1)));
+  const T hs = N::mul(N::mul(p.RT, geq), N::fma(cq, N::fma(N::sub(t, T(2)), c0, -twoK), c0));
+  T corr = N::fma(p.b3, cc, N::fma(p.b2, cy, N::fma(p.b1, cx, p.b0)));
+  corr = N::fma(N::mul(b8[0], cc), cx, corr);
+  corr = N::fma(N::mul(b8[1], cc), cy, corr);
+  corr = N::fma(b8[2], N::fma(cx, cx, -N::mul(cy, cy)), corr);
+  corr = N::fma(N::mul(b8[3], cx), cy, corr);
+  g = N::fma(gs, corr, gs);
+  h = N::fma(hs, corr, hs);
+}
+
 // Model parameters of a point with state (rho, u, T, q), before the correction.
 template <class T, int D>
 __device__ inline void point_params(const GasDev& g, double rho, double ux, double uy, double Tm, double qx,
@@ -820,14 +968,20 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
   }
   double den = 0.0;
   double G[5][5], H[3][3];
+  // the eight-moment correction replaces the four-moment one at cells and faces (not on
+  // freestream sides, which keep the four-moment correction)
+  const bool c8 = D == 2 && PART == 0 && a.prm8_out && !free_ && !wall;
+  T* p8 = reinterpret_cast<T*>(a.prm8_out);
   if (PART == 0) {
     if (need == 1)
       den = a.wden ? a.wden[i] : wall_den<T, D, 1>(a, mp, side < 2, (kind == FK_WALL_LO) ? T(1) : T(-1), 0);
-    if (need == 2) {
+    if (need == 2 && !c8) {
       if (k.nax > 0) axis_moments<T, D>(a, mp, G, H);
       else direct_moments<T, D, 1>(a, mp, 0, G, H);
     }
   }
+  if (p8 && PART == 0)
+    for (int m = 0; m < 4; ++m) p8[m * (long)a.npt + i] = T(0);
   if (wall) {
     if (PART == 1) {   // rho_w in k_fin_post
       store_mp<T>(po, a.npt, i, mp, T(kind));
@@ -849,7 +1003,21 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
     return;
   }
   bool ok = true;
-  if (PART == 0 && need == 2) ok = point_correct<T, D>(g, rho, ux, uy, Tm, G, H, mp);
+  if (PART == 0 && need == 2) {
+    if constexpr (D == 2) {
+      if (c8) {
+        // heat-flux target: the Shakhov model's own heat flux (1 - Pr) q
+        T b8[4];
+        const double pr = 1.0 - g.Pr;
+        ok = u_correct8<T>(a, rho, ux, uy, Tm, pr * qx, pr * qy, mp, b8);
+        for (int m = 0; m < 4; ++m) p8[m * (long)a.npt + i] = b8[m];
+      } else {
+        ok = point_correct<T, D>(g, rho, ux, uy, Tm, G, H, mp);
+      }
+    } else {
+      ok = point_correct<T, D>(g, rho, ux, uy, Tm, G, H, mp);
+    }
+  }
   const double s = 0.5 * k.dt;
   if (free_) {
     mp.c1 = T(1);

@@ -110,6 +110,7 @@ struct LevelRt {
   std::vector<int> cells;    // global cell id of every slot
   StepConst k;
   DevBuf f[2], prm[2], fprm, cpart, fpart, ids, frole, fslot, ghost_of, ghost, X, Y, tiles;
+  DevBuf prm8[2], fprm8;     // eight-moment correction: b4..b7 of the cells and the faces
   DevBuf fbar;               // [2][nv][nface] face phi-bar of the faces the level evaluates
   DevBuf fscr, fneed;        // split finalisation scratch (spaces that are not tensor products)
   DevBuf wden;               // curvilinear walls: [nface] wall-Maxwellian normalisation
@@ -482,7 +483,7 @@ template <class S, class T, int D> struct Runner {
                                                                          L.msum.as<double>());
       a.msum = L.msum.as<double>();
     }
-    if (a.k.nax > 0 && a.nwork >= kFinThreadMin) {
+    if (a.k.nax > 0 && (a.nwork >= kFinThreadMin || a.prm8_out)) {   // the eight-moment solve per thread
       k_finalize<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
       return;
     }
@@ -533,6 +534,15 @@ template <class S, class T, int D> struct Runner {
                                              (int)(i < 2 ? SM0C : SMU));
         if (e != cudaSuccess) return e;
       }
+      const void* f8[4] = {(const void*)k_faces<S, T, D, TX, TY, false, false, true>,
+                           (const void*)k_faces<S, T, D, TX, TY, false, true, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, false, false, true>,
+                           (const void*)k_update<S, T, D, TX, TY, VPC, false, true, true>};
+      for (int i = 0; i < 4; ++i) {
+        cudaError_t e = cudaFuncSetAttribute(f8[i], cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(i == 0 ? SM0 : (i == 1 ? SM0C : SMU)));
+        if (e != cudaSuccess) return e;
+      }
     }
     return cudaSuccess;
   }
@@ -542,6 +552,18 @@ template <class S, class T, int D> struct Runner {
   template <int MODE>
   static void launch_tile(mlvs_handle* h, dim3 grid, const TileArgs& t, int limiter) {
     if constexpr (D == 2) {
+      if (h->cfg.compat_moments == 8) {   // the eight-moment correction's model
+        if (h->curvi) {
+          if constexpr (MODE == 0)
+            k_faces<S, T, D, TX, TY, false, true, true><<<grid, TX * TY, SM0C, h->stream>>>(t, nullptr, nullptr, limiter);
+          else k_update<S, T, D, TX, TY, VPC, false, true, true><<<grid, TX * TY, SMU, h->stream>>>(t, nullptr, nullptr);
+        } else {
+          if constexpr (MODE == 0)
+            k_faces<S, T, D, TX, TY, false, false, true><<<grid, TX * TY, SM0, h->stream>>>(t, nullptr, nullptr, limiter);
+          else k_update<S, T, D, TX, TY, VPC, false, false, true><<<grid, TX * TY, SMU, h->stream>>>(t, nullptr, nullptr);
+        }
+        return;
+      }
       if (h->curvi) {
         if constexpr (MODE == 0)
           k_faces<S, T, D, TX, TY, false, true><<<grid, TX * TY, SM0C, h->stream>>>(t, nullptr, nullptr, limiter);
@@ -620,6 +642,7 @@ template <class S, class T, int D> struct Runner {
     a.rows = sp.nrows > 0 ? sp.rows.as<int4>() : nullptr;
     a.nrows = sp.nrows;
     a.segs = sp.segs.as<int2>();
+    a.prm8_out = nullptr;
     return a;
   }
 
@@ -648,6 +671,8 @@ template <class S, class T, int D> struct Runner {
     t.X = L.X.p;
     t.nX = L.nX;
     t.xfid = L.xfid.as<int>();
+    t.cparam8 = L.prm8[L.pcur].p;
+    t.fparam8 = L.fprm8.p;
     t.Y = L.Y.p;
     t.nY = L.nY;
     t.fbar = L.fbar.p;
@@ -666,6 +691,7 @@ template <class S, class T, int D> struct Runner {
     PointArgs a = pargs(h, I, L, false);
     a.cprm = L.prm[L.pcur].p;
     a.prm_out = L.prm[L.pcur ^ 1].p;
+    a.prm8_out = L.prm8[L.pcur ^ 1].p;   // null without the eight-moment correction
     a.W = I.W.as<double>();
     mark_begin(h, 0);
     ++h->launches;
@@ -1033,6 +1059,7 @@ template <class S, class T, int D> struct Runner {
       PointArgs a = pargs(h, I, L, true);
       a.cprm = L.prm[L.pcur].p;
       a.prm_out = L.fprm.p;
+      a.prm8_out = L.fprm8.p;
       mark_begin(h, 2);
       launch_finalize(h, a, L);
       mark_end(h);
@@ -1525,6 +1552,15 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
         L.fbar.alloc(L.ntiles > 0 ? 2ull * ((k.nv + 1) / 2) * 2 * nface * h->tsize : 0) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     CK(cudaMemsetAsync(L.fprm.p, 0, L.fprm.n, h->stream));
+    if (h->cfg.compat_moments == 8) {
+      const size_t n8 = 4ull * std::max<size_t>(nc, 1) * h->tsize;
+      if (L.prm8[0].alloc(n8) != cudaSuccess || L.prm8[1].alloc(n8) != cudaSuccess ||
+          L.fprm8.alloc(4ull * nface * h->tsize) != cudaSuccess)
+        return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
+      CK(cudaMemsetAsync(L.prm8[0].p, 0, n8, h->stream));
+      CK(cudaMemsetAsync(L.prm8[1].p, 0, n8, h->stream));
+      CK(cudaMemsetAsync(L.fprm8.p, 0, L.fprm8.n, h->stream));
+    }
     if (h->curvi) CK(ops_for(h->cfg.storage, D).wall_table(h, L));
     if (L.msum.alloc((size_t)NMOM * std::max<size_t>(std::max<size_t>(nface, nc), 1) * sizeof(double)) != cudaSuccess)
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
@@ -1692,6 +1728,10 @@ extern "C" mlvs_status mlvs_create(const mlvs_config* cfg, mlvs_handle** out) {
   if (cfg->storage < 0 || cfg->storage > 2) return fail(nullptr, MLVS_ERR_ARG, "unknown storage type");
   if (cfg->map_moments != 0 && cfg->map_moments != 4 && cfg->map_moments != 9)
     return fail(nullptr, MLVS_ERR_ARG, "map_moments must be 4 or 9 (0: 4)");
+  if (cfg->compat_moments != 0 && cfg->compat_moments != 4 && cfg->compat_moments != 8)
+    return fail(nullptr, MLVS_ERR_ARG, "compat_moments must be 4 or 8 (0: 4)");
+  if (cfg->compat_moments == 8 && cfg->dim != 2)
+    return fail(nullptr, MLVS_ERR_ARG, "the eight-moment correction is two-dimensional");
   if (cfg->positive_mapping != 0 && cfg->positive_mapping != 1)
     return fail(nullptr, MLVS_ERR_ARG, "positive_mapping must be 0 or 1");
   if (!(cfg->R > 0) || !(cfg->Pr > 0) || cfg->K_internal < 0) return fail(nullptr, MLVS_ERR_ARG, "bad gas constants");
@@ -1869,6 +1909,8 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
   if (n_levels < 1 || !levels) return fail(h, MLVS_ERR_ARG, "need at least one level");
   if (!(umax > umin)) return fail(h, MLVS_ERR_ARG, "umax must exceed umin");
   if (adaptive != 0 && adaptive != 1) return fail(h, MLVS_ERR_ARG, "adaptive must be 0 or 1");
+  if (h->cfg.compat_moments == 8 && (n_levels != 1 || adaptive != 0 || levels[0].uniform_L < 0))
+    return fail(h, MLVS_ERR_ARG, "the eight-moment correction runs on one uniform level (adaptive = 0)");
   h->adaptive = adaptive;
   try {
     h->base = make_base_1d(n_base, umin, umax, quadrature);

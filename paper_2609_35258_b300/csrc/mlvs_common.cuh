@@ -221,6 +221,36 @@ __device__ __forceinline__ void model_eval2(const MP<T>& p, V2<T> xix, V2<T> xiy
   h = P::fma(hs, corr, hs);
 }
 
+// model_eval2 with the eight-term correction factor 1 + b0 + b1 c_x + b2 c_y + b3 |c|^2 + b4 |c|^2 c_x
+// + b5 |c|^2 c_y + b6 (c_x^2 - c_y^2) + b7 c_x c_y (2-D; b8 = b4..b7), the factor formed in the
+// order of the scalar eight-moment evaluation.
+template <class T>
+__device__ __forceinline__ void model_eval2c8(const MP<T>& p, const T b8[4], V2<T> xix, V2<T> xiy, T c0, T twoK,
+                                              V2<T>& g, V2<T>& h) {
+  using P = Pk<T>;
+  using N = Num<T>;
+  const V2<T> cx = P::sub(xix, P::splat(p.ux));
+  const V2<T> cy = P::sub(xiy, P::splat(p.uy));
+  const V2<T> cx2 = P::mul(cx, cx);
+  const V2<T> ax = P::fma(cx2, P::splat(-p.inv2RT), P::splat(p.lnh));
+  const V2<T> ay = P::fma(P::mul(cy, cy), P::splat(-p.inv2RT), P::splat(p.lnh));
+  const V2<T> geq = P::mul(P::mk(P::ex(ax.x), P::ex(ax.y)), P::mk(P::ex(ay.x), P::ex(ay.y)));
+  const V2<T> cc = P::fma(cy, cy, cx2);
+  const V2<T> cq = P::fma(P::splat(p.kqy), cy, P::mul(P::splat(p.kqx), cx));
+  const V2<T> t = P::mul(P::splat(N::mul(T(2), p.inv2RT)), cc);
+  const V2<T> gs = P::mul(geq, P::fma(cq, P::sub(t, P::splat(T(4))), P::splat(T(1))));
+  const V2<T> hs = P::mul(P::mul(P::splat(p.RT), geq),
+                          P::fma(cq, P::fma(P::sub(t, P::splat(T(2))), P::splat(c0), P::splat(-twoK)), P::splat(c0)));
+  V2<T> corr = P::fma(P::splat(p.b3), cc, P::fma(P::splat(p.b2), cy, P::fma(P::splat(p.b1), cx, P::splat(p.b0))));
+  corr = P::fma(P::mul(P::splat(b8[0]), cc), cx, corr);
+  corr = P::fma(P::mul(P::splat(b8[1]), cc), cy, corr);
+  const V2<T> cyy = P::mul(cy, cy);
+  corr = P::fma(P::splat(b8[2]), P::fma(cx, cx, P::mk(-cyy.x, -cyy.y)), corr);
+  corr = P::fma(P::mul(P::splat(b8[3]), cx), cy, corr);
+  g = P::fma(gs, corr, gs);
+  h = P::fma(hs, corr, hs);
+}
+
 // a + b rounded stochastically to FP32 with 16 random bits r (FP32 storage of phi~^{n+1}):
 // given s = RN(a + b) and its rounding error e, the neighbour of s towards the
 // exact sum is taken with probability |e| / gap, so the stored value is unbiased: near a

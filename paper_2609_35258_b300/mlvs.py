@@ -35,6 +35,7 @@ class mlvs_config(C.Structure):
         ("compat_face", C.c_int), ("limiter", C.c_int), ("init_W", C.POINTER(C.c_double)),
         ("stream", C.c_void_p), ("far", C.c_double * 4), ("mesh_kind", C.c_int),
         ("node_xy", C.POINTER(C.c_double)), ("positive_mapping", C.c_int), ("map_moments", C.c_int),
+        ("compat_moments", C.c_int),
     ]
 
 
@@ -503,7 +504,7 @@ def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0
                 Pr=2.0 / 3.0, omega=0.81, Kn=0.0, mu_ref=0.0, cfl=0.5, dt=0.0, storage=F32,
                 compat_cell=1, compat_face=1, limiter=LIMITER_VANLEER, n_instances=1,
                 stream=None, T_ref=1.0, L_ref=1.0, rho_ref=1.0, far=(1.0, 0.0, 0.0, 1.0), nodes=None,
-                positive_mapping=0, map_moments=4):
+                positive_mapping=0, map_moments=4, compat_moments=4):
     """Fill an mlvs_config.  init_W: float64 array [n_instances][ny][nx][4].  The returned
     config keeps a reference to init_W (attribute `_keep`)."""
     cfg = mlvs_config()
@@ -519,6 +520,7 @@ def make_config(*, dim, nx, ny, Lx, Ly, bc, init_W, wall=((0, 0, 1),) * 4, R=1.0
     cfg.compat_cell, cfg.compat_face, cfg.limiter = compat_cell, compat_face, limiter
     cfg.positive_mapping = positive_mapping
     cfg.map_moments = map_moments
+    cfg.compat_moments = compat_moments
     W = np.ascontiguousarray(init_W, dtype=np.float64)
     cfg._keep = W
     cfg.init_W = W.ctypes.data_as(C.POINTER(C.c_double))

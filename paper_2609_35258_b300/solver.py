@@ -14,7 +14,7 @@ _LIM = {"vanleer": M.LIMITER_VANLEER, "none": M.LIMITER_NONE}
 
 class Solver:
     def __init__(self, desc, levels=(0,), stream=None, storage=None, compat_cell=1, compat_face=1,
-                 n_instances=1, init=None, adaptive=0, positive_mapping=0, map_moments=4):
+                 n_instances=1, init=None, adaptive=0, positive_mapping=0, map_moments=4, compat_moments=4):
         d = desc
         self.desc = d
         self.ncell = d["nx"] * d["ny"]
@@ -31,7 +31,7 @@ class Solver:
             storage=_ST[storage or d["storage"]], compat_cell=compat_cell, compat_face=compat_face,
             limiter=_LIM[d["limiter"]], n_instances=n_instances, stream=stream,
             far=d.get("far", (1.0, 0.0, 0.0, 1.0)), nodes=d.get("nodes"), positive_mapping=positive_mapping,
-            map_moments=map_moments)
+            map_moments=map_moments, compat_moments=compat_moments)
         self.h = M.mlvs_create(self.cfg)
         M.mlvs_set_velocity_levels(self.h, d["n_base"], d["umin"], d["umax"], _RULE[d["rule"]],
                                    list(levels), adaptive)
