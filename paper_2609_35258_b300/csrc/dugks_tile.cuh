@@ -645,6 +645,10 @@ k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restr
     }
   };
 
+  // a warp none of whose lanes evaluates a face here (a partly filled tile of a level) skips the
+  // face work of every round; it still stages its box positions
+  const bool wface = !ML || __any_sync(0xffffffffu, FA.meta != 0 || FB.meta != 0 || FC.meta != 0);
+
   // register prefetch of the first pair
   V ng0, nh0, ng1 = P::splat(T(0)), nh1 = P::splat(T(0));
   ld2(kind0, p0, st0, v0, ng0, nh0);
@@ -702,14 +706,16 @@ k_faces(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __restr
       }
       face_part(F, gb, hb, xn, xix, xiy, wxv, wyv, part);
     };
-    T part[9];
-    one(FA, part);
-    fold_partials<T>(ra[0], part);
-    if (D == 2) {
-      one(FB, part);
-      fold_partials<T>(ra[1], part);
+    if (wface) {
+      T part[9];
+      one(FA, part);
+      fold_partials<T>(ra[0], part);
+      if (D == 2) {
+        one(FB, part);
+        fold_partials<T>(ra[1], part);
+      }
+      if (FC.meta) { one(FC, part); fold_partials_smem<T>(sAcc + tid, L::NX3, part); }
     }
-    if (FC.meta) { one(FC, part); fold_partials_smem<T>(sAcc + tid, L::NX3, part); }
   }
 
   // ---- write the chunk's partial moments
@@ -999,15 +1005,15 @@ k_update(const TileArgs a_, const TileArgs* __restrict__ tab, const int4* __rest
     for (int j = jb; j < je; ++j, buf ^= 1) {
       const int v = v0 + 2 * j;
       V g0, h0, ga, ha, gbb, hbb;
+      const V xix = sVT[4 * j], xiy = sVT[4 * j + 1];
+      V* Fg = sF + (buf * 2 + 0) * G::NF;
+      V* Fh = sF + (buf * 2 + 1) * G::NF;
       if constexpr (PF) {
         g0 = ng0; h0 = nh0; ga = nga; ha = nha; gbb = ngb; hbb = nhb;
         if (j + 1 < npr) ld_round(j + 1, ng0, nh0, nga, nha, ngb, nhb);
       } else {
         ld_round(j, g0, h0, ga, ha, gbb, hbb);
       }
-      const V xix = sVT[4 * j], xiy = sVT[4 * j + 1];
-      V* Fg = sF + (buf * 2 + 0) * G::NF;
-      V* Fh = sF + (buf * 2 + 1) * G::NF;
       // faces A and B evaluated without a branch (a received face takes its mapped flux)
       V FAg, FAh;
       face_flux2<T, D, CV, C8>(FA, 0, xix, xiy, ga, ha, c0, twoK, FAg, FAh);

@@ -50,6 +50,11 @@ template <class X> static inline X __shfl_up_sync(unsigned, X v, unsigned, int =
   std::abort();
   return v;
 }
+static inline bool __any_sync(unsigned, int v) {
+  std::fprintf(stderr, "emulation: a warp vote was reached; lanes are not emulated\n");
+  std::abort();
+  return v != 0;
+}
 static inline void __syncwarp(unsigned = 0xffffffffu) {
   std::fprintf(stderr, "emulation: a warp barrier was reached; lanes are not emulated\n");
   std::abort();
