@@ -227,6 +227,14 @@ struct mlvs_handle {
   DevBuf cgeo_d, fgeo_d, featgeo_d;
   std::vector<double> width;      // |V| / max |S| per cell
   std::map<std::vector<long long>, std::pair<cudaGraphExec_t, std::vector<int>>> graphs;
+  // graphs of a group whose tile passes run as one launch over every handle's levels: their
+  // tile-argument tables (pinned host copy and device table per step) and work lists
+  struct GroupBufs {
+    TileArgs* host = nullptr;   // [2 steps][2 passes][levels] (pinned; read by the graph's copies)
+    DevBuf tab, wf, wu, wx;
+    int nwf = 0, nwu = 0, nwx = 0;
+  };
+  std::map<std::vector<long long>, GroupBufs> gbufs;
   cudaStream_t cap = nullptr;     // capture stream
   std::vector<cudaStream_t> branch;
   std::vector<cudaEvent_t> bev;   // join events, one per branch
@@ -990,6 +998,165 @@ template <class S, class T, int D> struct Runner {
     return cudaGetLastError();
   }
 
+  // Two steps of a group of handles (same storage and mesh kind), captured on hs[0]->cap: per
+  // instance (one graph branch each) the step counter, cell finalisation and ghost states; one
+  // faces launch over the work items of every level of every instance; per instance the face
+  // finalisations; one cross-flux launch; per instance the flux mapping; one update launch.
+  // The tile arguments of every level at each step's buffer parity go to a pinned table that
+  // the graph copies to the device before the step's tile passes.  kernels[j]: the kernels of
+  // handle j per two steps (the group launches counted on handle 0).
+  static cudaError_t group_capture(mlvs_handle* const* hs, int nh, mlvs_handle::GroupBufs& B,
+                                   std::vector<int>& kernels, cudaGraphExec_t* exec_out) {
+    mlvs_handle* h0 = hs[0];
+    struct Ref { mlvs_handle* h; Inst* I; int lvl0; };
+    std::vector<Ref> refs;
+    int nlt = 0;
+    for (int j = 0; j < nh; ++j)
+      for (auto& I : hs[j]->inst) {
+        refs.push_back({hs[j], &I, nlt});
+        nlt += (int)I.lv.size();
+      }
+    // work lists (the same for both steps), longest items first
+    std::vector<std::pair<int, int4>> wf, wu, wx;   // (velocities per chunk, item)
+    for (const Ref& r : refs)
+      for (int l = 0; l < (int)r.I->lv.size(); ++l) {
+        const LevelRt& L = r.I->lv[l];
+        const int g = r.lvl0 + l;
+        std::set<int> with_cells;
+        const int ntx = (r.h->nx + TX - 1) / TX;
+        for (int c : L.cells) with_cells.insert(((c / r.h->nx) / TY) * ntx + (c % r.h->nx) / TX);
+        for (int c = 0; c < L.k.nchunk; ++c)
+          for (int ti = 0; ti < L.ntiles; ++ti) {
+            wf.push_back({L.k.vpc, make_int4(g, ti, c, 0)});
+            if (with_cells.count(L.tiles_h[ti])) wu.push_back({L.k.vpc, make_int4(g, ti, c, 0)});
+          }
+        const int npair = (L.k.nv + 1) / 2;
+        for (int c0 = 0; c0 < L.nX; c0 += 128)
+          for (int p0 = 0; p0 < npair; p0 += kXPairs) wx.push_back({0, make_int4(g, c0, p0, 0)});
+      }
+    auto order = [](std::vector<std::pair<int, int4>>& v) {
+      std::stable_sort(v.begin(), v.end(), [](const std::pair<int, int4>& a, const std::pair<int, int4>& b) {
+        return a.first > b.first;
+      });
+      std::vector<int4> out(v.size());
+      for (size_t i = 0; i < v.size(); ++i) out[i] = v[i].second;
+      return out;
+    };
+    cudaError_t e;
+    if ((e = upload(B.wf, order(wf), h0->stream)) != cudaSuccess) return e;
+    if ((e = upload(B.wu, order(wu), h0->stream)) != cudaSuccess) return e;
+    if ((e = upload(B.wx, order(wx), h0->stream)) != cudaSuccess) return e;
+    B.nwf = (int)wf.size();
+    B.nwu = (int)wu.size();
+    B.nwx = (int)wx.size();
+    const size_t per_step = (size_t)2 * nlt;
+    if ((e = cudaMallocHost(&B.host, 2 * per_step * sizeof(TileArgs))) != cudaSuccess) return e;
+    if ((e = B.tab.alloc(2 * per_step * sizeof(TileArgs))) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(h0->stream)) != cudaSuccess) return e;   // uploads before the capture
+    std::vector<int> l0(nh);
+    for (int j = 0; j < nh; ++j) l0[j] = hs[j]->launches;
+    std::vector<cudaStream_t> saved(nh);
+    for (int j = 0; j < nh; ++j) saved[j] = hs[j]->stream;
+    // run f(h, I) for every instance on a branch of its own, joined into the capture stream
+    auto branches = [&](auto&& f) -> cudaError_t {
+      cudaError_t ee = cudaEventRecord(h0->ev_fork, h0->cap);
+      for (size_t b = 0; b < refs.size() && ee == cudaSuccess; ++b) {
+        cudaStream_t st = h0->branch[b];
+        if ((ee = cudaStreamWaitEvent(st, h0->ev_fork, 0)) != cudaSuccess) break;
+        refs[b].h->stream = st;
+        if ((ee = f(refs[b].h, *refs[b].I)) != cudaSuccess) break;
+        if ((ee = cudaEventRecord(h0->bev[b], st)) != cudaSuccess) break;
+        ee = cudaStreamWaitEvent(h0->cap, h0->bev[b], 0);
+      }
+      return ee;
+    };
+    if ((e = cudaStreamBeginCapture(h0->cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaError_t ce = cudaSuccess;
+    const int limiter = h0->cfg.limiter;
+    for (int step = 0; step < 2 && ce == cudaSuccess; ++step) {
+      ce = branches([&](mlvs_handle* h, Inst& I) -> cudaError_t {
+        if constexpr (sizeof(S) <= 4) {
+          ++h->launches;
+          k_step_counter<<<1, 1, 0, h->stream>>>(I.stepctr.as<unsigned>());
+        }
+        for (int l = 0; l < h->n_levels; ++l) {
+          cudaError_t e2;
+          if (!I.lv[l].fresh && (e2 = finalize_cells(h, I, I.lv[l])) != cudaSuccess) return e2;
+        }
+        return run_ghosts(h, I);
+      });
+      if (ce != cudaSuccess) break;
+      // the levels' arguments at this step's parity: pass 0 (face partials), pass 1 (cell partials)
+      TileArgs* ht = B.host + step * per_step;
+      for (const Ref& r : refs)
+        for (int l = 0; l < (int)r.I->lv.size(); ++l) {
+          LevelRt& L = r.I->lv[l];
+          TileArgs t = targs(r.h, *r.I, L, l);
+          t.part = L.fpart.as<double>();
+          ht[r.lvl0 + l] = t;
+          t.part = L.cpart.as<double>();
+          ht[nlt + r.lvl0 + l] = t;
+        }
+      TileArgs* dt = B.tab.as<TileArgs>() + step * per_step;
+      h0->stream = h0->cap;
+      if ((ce = cudaMemcpyAsync(dt, ht, per_step * sizeof(TileArgs), cudaMemcpyHostToDevice, h0->cap)) != cudaSuccess)
+        break;
+      if (B.nwf > 0) {
+        ++h0->launches;
+        launch_lv<0>(h0, B.nwf, dt, B.wf.as<int4>(), limiter);
+      }
+      ce = branches([&](mlvs_handle* h, Inst& I) -> cudaError_t {
+        for (LevelRt& L : I.lv) {
+          if (L.ntiles == 0) continue;
+          PointArgs a = pargs(h, I, L, true);
+          a.cprm = L.prm[L.pcur].p;
+          a.prm_out = L.fprm.p;
+          mark_begin(h, 2);
+          launch_finalize(h, a, L);
+          mark_end(h);
+        }
+        return cudaGetLastError();
+      });
+      if (ce != cudaSuccess) break;
+      h0->stream = h0->cap;
+      if (B.nwx > 0) {
+        ++h0->launches;
+        if (D == 2 && h0->curvi) k_cross_flux<T, D, true><<<B.nwx, 128, 0, h0->cap>>>(dt + nlt, B.wx.as<int4>());
+        else k_cross_flux<T, D, false><<<B.nwx, 128, 0, h0->cap>>>(dt + nlt, B.wx.as<int4>());
+      }
+      ce = branches([&](mlvs_handle* h, Inst& I) -> cudaError_t { return run_fluxes(h, I); });
+      if (ce != cudaSuccess) break;
+      h0->stream = h0->cap;
+      if (B.nwu > 0) {
+        ++h0->launches;
+        launch_lv<1>(h0, B.nwu, dt + nlt, B.wu.as<int4>(), limiter);
+      }
+      if ((ce = cudaGetLastError()) != cudaSuccess) break;
+      for (const Ref& r : refs)
+        for (int l = 0; l < r.h->n_levels; ++l) {
+          LevelRt& L = r.I->lv[l];
+          if (L.cells.empty()) continue;
+          L.cur ^= 1;
+          L.fresh = false;
+        }
+    }
+    for (int j = 0; j < nh; ++j) hs[j]->stream = saved[j];
+    cudaGraph_t graph = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(h0->cap, &graph);
+    if (ce == cudaSuccess) ce = ee;
+    cudaGraphExec_t exec = nullptr;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    kernels.assign(nh, 0);
+    for (int j = 0; j < nh; ++j) {
+      kernels[j] = hs[j]->launches - l0[j];
+      hs[j]->launches = l0[j];
+    }
+    if (ce != cudaSuccess) return ce;
+    *exec_out = exec;
+    return cudaSuccess;
+  }
+
   // faces of every level, face finalisation, cross-level microfluxes and their mapping, then
   // the update of every cell level: one launch per tile pass over all levels' work items.
   // The cell levels' buffers advance together, so one parity selects the argument table.
@@ -1287,12 +1454,14 @@ struct Ops {
   cudaError_t (*ghost_batch)(mlvs_handle*, Inst&);
   cudaError_t (*flux_batch)(mlvs_handle*, Inst&);
   cudaError_t (*tile_batch)(mlvs_handle*, Inst&);
+  cudaError_t (*group_capture)(mlvs_handle* const*, int, mlvs_handle::GroupBufs&, std::vector<int>&,
+                               cudaGraphExec_t*);
 };
 
 template <class S, class T, int D> Ops make_ops() {
   using R = Runner<S, T, D>;
   return Ops{&R::init_state, &R::finalize_cells, &R::step, &R::transfer, &R::moments_of_levels, &R::criterion,
-             &R::wall_table, &R::ghost_batch, &R::flux_batch, &R::tile_batch};
+             &R::wall_table, &R::ghost_batch, &R::flux_batch, &R::tile_batch, &R::group_capture};
 }
 
 Ops ops_for(int storage, int D) {
@@ -1802,6 +1971,8 @@ extern "C" void mlvs_destroy(mlvs_handle* h) {
   if (h->ea1) cudaEventDestroy(h->ea1);
   if (h->kbuf_host) cudaFreeHost(h->kbuf_host);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.second.first);
+  for (auto& g : h->gbufs)
+    if (g.second.host) cudaFreeHost(g.second.host);
   for (auto s : h->branch) cudaStreamDestroy(s);
   for (auto e : h->bev) cudaEventDestroy(e);
   for (auto e : h->ev_pre) cudaEventDestroy(e);
@@ -2516,10 +2687,39 @@ static cudaError_t ensure_capture_resources(mlvs_handle* h0, int nbranch, int nh
 // Two steps of every handle of the group as one graph launch on hs[0]'s stream.  The graph
 // forks one branch per instance (instances and handles are independent), so their kernels
 // may run concurrently.  Captured on first use for a key, replayed afterwards.
+// A group of several handles whose tile passes can share one launch: the same storage,
+// dimension, mesh kind and limiter, and no eight-moment correction (its kernels take one level).
+static bool group_batchable(mlvs_handle* const* hs, int nh) {
+  if (nh < 2) return false;
+  for (int j = 0; j < nh; ++j) {
+    const mlvs_handle* h = hs[j];
+    if (h->cfg.storage != hs[0]->cfg.storage || h->D != hs[0]->D || h->curvi != hs[0]->curvi ||
+        h->cfg.limiter != hs[0]->cfg.limiter || h->cfg.compat_moments == 8)
+      return false;
+  }
+  return true;
+}
+
 static mlvs_status graph_two_steps(mlvs_handle* const* hs, int nh) {
   mlvs_handle* h0 = hs[0];
   std::vector<long long> key = graph_key(hs, nh);
   auto it = h0->graphs.find(key);
+  if (it == h0->graphs.end() && group_batchable(hs, nh)) {
+    int nbranch = 0;
+    for (int j = 0; j < nh; ++j) nbranch += (int)hs[j]->inst.size();
+    cudaError_t e = ensure_capture_resources(h0, nbranch, nh);
+    if (e != cudaSuccess) return fail(h0, MLVS_ERR_CUDA, std::string("graph resources: ") + cudaGetErrorString(e));
+    std::vector<int> kernels;
+    cudaGraphExec_t exec = nullptr;
+    mlvs_handle::GroupBufs& B = h0->gbufs[key];
+    cudaError_t ce = ops_for(h0->cfg.storage, h0->D).group_capture(hs, nh, B, kernels, &exec);
+    if (ce != cudaSuccess) {
+      // the host state may have advanced by steps that never ran: the handles cannot continue
+      for (int j = 0; j < nh; ++j) hs[j]->sticky = MLVS_ERR_CUDA;
+      return fail(h0, MLVS_ERR_CUDA, std::string("group graph capture: ") + cudaGetErrorString(ce));
+    }
+    it = h0->graphs.emplace(key, std::make_pair(exec, kernels)).first;
+  }
   if (it == h0->graphs.end()) {
     int nbranch = 0;
     for (int j = 0; j < nh; ++j) nbranch += (int)hs[j]->inst.size();
