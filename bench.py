@@ -631,10 +631,15 @@ def run_ours(args, rank, world, local_rank):
         mupd = mst.cell_velocity_updates
         mstp = sm_.step(args.steps, profile=True)     # per-phase times, a second run
         torch.cuda.synchronize()
+        # one more adaptation of the developed state, as the periodic ones inside the run
+        rst = M.mlvs_adapt(sm_.h, M.adapt_params(*MLVS_PARAMS))
         mlvs = {"ms_per_step": mms / args.steps, "updates_per_s": mupd / (mms / 1e3),
                 "points_per_cell": mupd / args.steps / ncell, "levels": mst.n_levels,
                 "speedup_per_step_vs_uvs": ms_step / (mms / args.steps),
                 "adapt_ms": ast.ms_total, "criterion_ms": ast.ms_criterion,
+                "readapt_ms": {"total": rst.ms_total, "criterion": rst.ms_criterion,
+                               "grouping": rst.ms_group, "remap": rst.ms_remap,
+                               "cells_moved": rst.n_changed},
                 "phases_ms_per_step": {n: p / args.steps for n, p in zip(names, mstp.ms_phase)},
                 "includes": f"adaptation every {ADAPT_INTERVAL} steps"}
         sm_.close()

@@ -142,42 +142,35 @@ __device__ bool crit_transport_ok(const CritCtx& c, int xa, int xb, int ya, int 
   return true;
 }
 
-// The same test from the per-block sums of the member blocks.
-__device__ inline bool crit_transport_blocks(const CritCtx& c, int bxa, int bxb, int bya, int byb) {
+// The same test from the per-block sums of the member blocks.  The centre node is a group of
+// its own at every level, so a candidate block lies entirely on one side of xi_d = 0 in each
+// axis or is the centre group: the one-sided sums of the test are the block's own sums (on the
+// block's side, both sides for the centre group) or zero.  sum w and sum w xi_d are products
+// of one-axis sums over the block's group ranges; sum w g and sum w H are the block's s1, s2.
+__device__ inline bool crit_transport_blocks(const CritCtx& c, int bxa, int bxb, int bya, int byb, double s1,
+                                             double s2) {
   const CritArgs& a = *c.a;
   const int nb = a.N1 * a.N1, mid = a.N1 / 2;   // the centre group has x = 0
-  double wsum = 0, sxw = 0, syw = 0, sg = 0, sH = 0;
-  double F[2][2][4];
+  double w0x = 0, w1x = 0, w0y = 0, w1y = 0;
+  for (int bx = bxa; bx < bxb; ++bx) { w0x += a.W1[bx]; w1x += a.X1[bx]; }
+  for (int by = bya; by < byb; ++by) { w0y += a.W1[by]; w1y += a.X1[by]; }
+  double t[CB_N];
 #pragma unroll
-  for (int d = 0; d < 2; ++d)
-#pragma unroll
-    for (int s = 0; s < 2; ++s)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) F[d][s][r] = 0.0;
+  for (int r = 0; r < CB_N; ++r) t[r] = 0.0;
   for (int by = bya; by < byb; ++by)
     for (int bx = bxa; bx < bxb; ++bx) {
       const int b = by * a.N1 + bx;
-      wsum += a.W1[bx] * a.W1[by];
-      sxw += a.X1[bx] * a.W1[by];
-      syw += a.W1[bx] * a.X1[by];
-      sg += c.S1[b];
-      sH += c.S2[b];
-      const double t[CB_N] = {c.TB[CB_XG * nb + b], c.TB[CB_YG * nb + b], c.TB[CB_XXG * nb + b],
-                              c.TB[CB_XYG * nb + b], c.TB[CB_YYG * nb + b], c.TB[CB_XH * nb + b],
-                              c.TB[CB_YH * nb + b]};
-      const double mx[4] = {t[CB_XG], t[CB_XXG], t[CB_XYG], 0.5 * t[CB_XH]};
-      const double my[4] = {t[CB_YG], t[CB_XYG], t[CB_YYG], 0.5 * t[CB_YH]};
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        if (bx >= mid) F[0][0][r] += mx[r];
-        if (bx <= mid) F[0][1][r] += mx[r];
-        if (by >= mid) F[1][0][r] += my[r];
-        if (by <= mid) F[1][1][r] += my[r];
-      }
+      for (int r = 0; r < CB_N; ++r) t[r] += c.TB[r * nb + b];
     }
+  const double wsum = w0x * w0y, sxw = w1x * w0y, syw = w0x * w1y;
+  const double mx[4] = {t[CB_XG], t[CB_XXG], t[CB_XYG], 0.5 * t[CB_XH]};
+  const double my[4] = {t[CB_YG], t[CB_XYG], t[CB_YYG], 0.5 * t[CB_YH]};
+  // side s = 0 holds the members with xi_d >= 0 (group index >= mid), s = 1 those with xi_d <= 0
+  const bool in[2][2] = {{bxb - 1 >= mid, bxa <= mid}, {byb - 1 >= mid, bya <= mid}};
   const double iw = 1.0 / wsum;
   const double xbar = sxw * iw, ybar = syw * iw;
-  const double gb = sg * iw, Hb = sH * iw;
+  const double gb = s1 * iw, Hb = s2 * iw;
   const double xb2 = xbar * xbar + ybar * ybar;
   const double hb = Hb - xb2 * gb;
   const double mb[4] = {gb, xbar * gb, ybar * gb, 0.5 * (hb + xb2 * gb)};
@@ -189,8 +182,9 @@ __device__ inline bool crit_transport_blocks(const CritCtx& c, int bxa, int bxb,
       const bool on = (s == 0) ? (xd >= 0.0) : (-xd >= 0.0);
 #pragma unroll
       for (int r = 0; r < 4; ++r) {
+        const double F = in[d][s] ? (d ? my[r] : mx[r]) : 0.0;
         const double Ft = on ? wsum * xd * mb[r] : 0.0;
-        if (!(fabs(F[d][s][r] - Ft) <= c.epsSr[r])) return false;
+        if (!(fabs(F - Ft) <= c.epsSr[r])) return false;
       }
     }
   }
@@ -211,7 +205,7 @@ __device__ bool crit_decide(const CritCtx& c, int L, int px, int py) {
   // I_B = max(s1/T1, s2/T2) against the thresholds, as products
   if (s1 < a.C_merge * c.T1 && s2 < a.C_merge * c.T2) {
     if (!(a.eps > 0.0)) return true;
-    if (a.tblk) return crit_transport_blocks(c, bxa, bxb, bya, byb);
+    if (a.tblk) return crit_transport_blocks(c, bxa, bxb, bya, byb, s1, s2);
     return crit_transport_ok<S>(c, a.g1[bxa], a.g1[bxb], a.g1[bya], a.g1[byb]);
   }
   if (s1 <= a.C_split * c.T1 && s2 <= a.C_split * c.T2) {

@@ -398,10 +398,14 @@ template <class T> __device__ __forceinline__ void csum_merge(T& s, T& c, T so, 
 }
 
 // Shared-memory values (type T) a warp needs for row_moments on a space with n1 entries.
+// Above the prefix sums the same area later holds the lanes' pair moments (36 rows of 33, the
+// row padded so that a lane reading its row meets no other lane's bank) and then the 36 sums
+// as FP64 (8-byte aligned: every offset below is even in units of T).
 __host__ __device__ inline int row_smem_values(int n1) {
   const int q = 16 * (n1 + 4);
-  return q > 36 * 32 + 72 ? q : 36 * 32 + 72;
+  return q > 36 * 33 + 72 ? q : 36 * 33 + 72;
 }
+constexpr int kRowPd = 36 * 33;   // offset (units of T) of the FP64 pair moments
 
 // The pair moments P[i][j] = sum over the space of w gauss(c_x) gauss(c_y) c_x^i c_y^j
 // (i + j <= 7) of a 2-D space that is not a tensor product, from its rows, by one warp (the
@@ -410,8 +414,8 @@ __host__ __device__ inline int row_smem_values(int n1) {
 // entries (compensated; the block's entries split into one contiguous run per lane, the runs
 // joined by a warp scan), so that a row's x sums are differences of prefix sums over its
 // segments; a row's y factor is one Gaussian.  P = sum over rows of Rx[i] Ry[j], summed per
-// lane and then over the lanes (compensated): entry k (i-major, i + j <= 7) as the unevaluated
-// difference wsm[36 * 32 + k] - wsm[36 * 32 + 36 + k], for every lane to read.
+// lane and then over the lanes (compensated, four interleaved chains per entry): entry k
+// (i-major, i + j <= 7) as an FP64 value at wsm + kRowPd, for every lane to read.
 // wsm: row_smem_values(n1) values of this warp.
 template <class T>
 __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane, T* wsm) {
@@ -517,14 +521,22 @@ __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane
 #pragma unroll
   for (int k = 0; k < 36; ++k) {
     const T cm = (k == 0) ? Mc[0] : (k == 1) ? Mc[1] : (k == 8) ? Mc[2] : T(0);
-    wsm[k * 32 + lane] = M[k] - cm;
+    wsm[k * 33 + lane] = M[k] - cm;
   }
   __syncwarp();
+  double* Pd = reinterpret_cast<double*>(wsm + kRowPd);
   for (int k = lane; k < 36; k += 32) {
-    T as = T(0), ac = T(0);
-    for (int l = 0; l < 32; ++l) csum_add(as, ac, wsm[k * 32 + l]);
-    wsm[36 * 32 + k] = as;
-    wsm[36 * 32 + 36 + k] = ac;
+    T as[4], ac[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) as[j] = ac[j] = T(0);
+#pragma unroll
+    for (int l = 0; l < 32; l += 4)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) csum_add(as[j], ac[j], wsm[k * 33 + l + j]);
+    csum_merge(as[0], ac[0], as[1], ac[1]);
+    csum_merge(as[2], ac[2], as[3], ac[3]);
+    csum_merge(as[0], ac[0], as[2], ac[2]);
+    Pd[k] = (double)as[0] - (double)ac[0];
   }
   __syncwarp();
 }
@@ -534,10 +546,8 @@ __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane
 // 25 writes G slot l, lanes 25..31 H slots 0..6, lanes 0 and 1 also H slots 7 and 8.
 template <class T, int D>
 __device__ inline void row_store_gh(const PointArgs& A, const MP<T>& mp, int lane, const T* wsm, long i) {
-  auto P = [&](int a, int b) -> double {
-    const int k = 8 * a - a * (a - 1) / 2 + b;
-    return (double)wsm[36 * 32 + k] - (double)wsm[36 * 32 + 36 + k];
-  };
+  const double* Pd = reinterpret_cast<const double*>(wsm + kRowPd);
+  auto P = [&](int a, int b) -> double { return Pd[8 * a - a * (a - 1) / 2 + b]; };
   const StepConst& k = A.k;
   const double kx = (double)mp.kqx, ky = (double)mp.kqy;
   const double i2 = 2.0 * (double)mp.inv2RT;

@@ -474,7 +474,7 @@ template <class S, class T, int D> struct Runner {
   static constexpr size_t SM0 = TileSmem<T, TX, TY, D>::BYTES;
   static constexpr size_t SM0C = TileSmem<T, TX, TY, D, true>::BYTES;
   static constexpr size_t SMU = UpdSmem<T, TX, TY, D, VPC>::BYTES;
-  static constexpr int FIN_BLOCK = 64;
+  static constexpr int FIN_BLOCK = 32;   // small launches spread over more SMs (FP64 latency)
   static int fin_grid(int npt) { return std::max(1, (npt + FIN_BLOCK - 1) / FIN_BLOCK); }
   // Tensor-product spaces with many points: one thread per point (one-axis sums in the
   // thread).  Otherwise the split path: state per thread, velocity sums per warp (on tensor-
