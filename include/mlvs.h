@@ -98,9 +98,10 @@ typedef struct {
                            3.3.1 (Eq. eq_eight_basis, Eq. eq_eight_moment_constraint), whose
                            heat-flux target is the Shakhov model's own heat flux (1 - Pr) q;
                            freestream sides keep the four-moment correction.  Runs on one
-                           level whose space is a tensor product (mlvs_set_velocity_levels with
-                           one uniform level and adaptive = 0; else MLVS_ERR_ARG).  0 or 4:
-                           the four-moment correction                                        */
+                           level (mlvs_set_velocity_levels with one level and adaptive = 0;
+                           else MLVS_ERR_ARG): a uniform level or a kappa space, whose
+                           model sums come from its rows of level groups.  0 or 4: the
+                           four-moment correction                                            */
 } mlvs_config;
 
 /* One representative velocity space, described on the base grid (Sec. 3.2). */

@@ -26,13 +26,13 @@ struct Clustering {
   int n_distinct = 0;
 };
 
-// f(begin, end) over [0, n) split across the host's cores (serially when `work`, a byte count,
-// is too small to pay for threads)
+// f(begin, end) over [0, n) split across the host's cores, one thread per 2 MB of `work` (a
+// byte count) at most, so that starting threads never costs more than the pass they share
 template <class F>
 inline void host_parallel(long n, double work, F f) {
   const unsigned hc = std::thread::hardware_concurrency();
-  const long nt = std::min<long>({(long)(hc ? hc : 1), 32L, n});
-  if (nt <= 1 || work < 4e6) {
+  const long nt = std::min<long>({(long)(hc ? hc : 1), 32L, n, (long)(work / 2e6)});
+  if (nt <= 1) {
     f(0L, n);
     return;
   }

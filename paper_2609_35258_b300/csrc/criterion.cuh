@@ -125,7 +125,6 @@ __device__ bool crit_transport_ok(const CritCtx& c, int xa, int xb, int ya, int 
   const double xb2 = xbar * xbar + ybar * ybar;
   const double hb = Hb - xb2 * gb;
   const double mb[4] = {gb, xbar * gb, ybar * gb, 0.5 * (hb + xb2 * gb)};
-  double err = 0.0;
 #pragma unroll
   for (int d = 0; d < 2; ++d) {
     const double xd = d ? ybar : xbar;

@@ -75,6 +75,8 @@ struct PointArgs {
 // per point: the velocity sums, or on tensor-product spaces the one-axis sums), k_fin_post
 // (thread per point: correction).  k_finalize does all three in one thread per point.  Scratch rows: rho ux uy T, then G[5][5], H[3][3], den.
 enum { FS_RHO = 0, FS_UX, FS_UY, FS_T, FS_G = 4, FS_H = 29, FS_DEN = 38, FIN_SCR = 39 };
+// the eight-moment correction on the split path: heat-flux target, G[7][7] and H[5][5]
+enum { FS_QX = 39, FS_QY = 40, FS_G8 = 41, FS_H8 = 90, FIN_SCR8 = 115 };
 
 enum { ERR_NONFINITE = 1, ERR_POSITIVITY = 2, ERR_SINGULAR = 4 };
 
@@ -397,54 +399,55 @@ template <class T> __device__ __forceinline__ void csum_merge(T& s, T& c, T so, 
   }
 }
 
-// Shared-memory values (type T) a warp needs for row_moments on a space with n1 entries.
-// Above the prefix sums the same area later holds the lanes' pair moments (36 rows of 33, the
-// row padded so that a lane reading its row meets no other lane's bank) and then the 36 sums
-// as FP64 (8-byte aligned: every offset below is even in units of T).
-__host__ __device__ inline int row_smem_values(int n1) {
-  const int q = 16 * (n1 + 4);
-  return q > 36 * 33 + 72 ? q : 36 * 33 + 72;
+// Shared-memory values (type T) a warp needs for row_moments<T, NO> on a space with n1
+// entries: the prefix sums [NO + 3][n1 + 4] (NO orders, three of them compensated); the same
+// area later holds the lanes' pair moments (NE = NO (NO + 1) / 2 rows of 33, the row padded so
+// that a lane reading its row meets no other lane's bank) and then the NE sums as FP64 at the
+// even offset row_pd(NO), 8-byte aligned.
+__host__ __device__ constexpr int row_pd(int NO) { return ((NO * (NO + 1) / 2) * 33 + 1) & ~1; }
+__host__ __device__ inline int row_smem_values(int n1, int NO = 8) {
+  const int q = (NO + 3) * (n1 + 4), r = row_pd(NO) + NO * (NO + 1);
+  return q > r ? q : r;
 }
-constexpr int kRowPd = 36 * 33;   // offset (units of T) of the FP64 pair moments
 
 // The pair moments P[i][j] = sum over the space of w gauss(c_x) gauss(c_y) c_x^i c_y^j
-// (i + j <= 7) of a 2-D space that is not a tensor product, from its rows, by one warp (the
-// result on lane 0).  For every entry e (a distinct axis range, abscissa X_e, weight W_e) the
-// factor W_e gauss(X_e - u_x) (X_e - u_x)^i is summed into prefix sums per level block of
-// entries (compensated; the block's entries split into one contiguous run per lane, the runs
-// joined by a warp scan), so that a row's x sums are differences of prefix sums over its
-// segments; a row's y factor is one Gaussian.  P = sum over rows of Rx[i] Ry[j], summed per
-// lane and then over the lanes (compensated, four interleaved chains per entry): entry k
-// (i-major, i + j <= 7) as an FP64 value at wsm + kRowPd, for every lane to read.
-// wsm: row_smem_values(n1) values of this warp.
-template <class T>
+// (i + j < NO) of a 2-D space that is not a tensor product, from its rows, by one warp.  For
+// every entry e (a distinct axis range, abscissa X_e, weight W_e) the factor W_e gauss(X_e - u_x)
+// (X_e - u_x)^i is summed into prefix sums per level block of entries (compensated for the
+// orders 0..2 that the conserved rows take; the block's entries split into one contiguous run
+// per lane, the runs joined by a warp scan), so that a row's x sums are differences of prefix
+// sums over its segments; a row's y factor is one Gaussian.  P = sum over rows of Rx[i] Ry[j],
+// summed per lane and then over the lanes (compensated, four interleaved chains per entry):
+// entry k (i-major, i + j < NO) as an FP64 value at wsm + row_pd(NO), for every lane to read.
+// wsm: row_smem_values(n1, NO) values of this warp.
+template <class T, int NO = 8>
 __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane, T* wsm) {
+  constexpr int NE = NO * (NO + 1) / 2;
   const T* e1 = reinterpret_cast<const T*>(A.e1);
   const int n1 = A.n1, nq = n1 + 4;
-  T* Qs = wsm;            // [8][nq] prefix sums (s)
-  T* Qc = wsm + 8 * nq;   // [8][nq] their compensation (c)
+  T* Qs = wsm;             // [NO][nq] prefix sums (s)
+  T* Qc = wsm + NO * nq;   // [3][nq] their compensation (c), orders 0..2
   for (int L = 0; L < 4; ++L) {
     const int ls = A.lst[L], n = A.lst[L + 1] - ls;
     if (n == 0) continue;
     const int cs = (n + 31) / 32;
     const int i0 = ls + min(n, lane * cs), i1 = ls + min(n, (lane + 1) * cs);
-    T s[8], c[8];
+    T s[NO], c[NO];
 #pragma unroll
-    for (int a = 0; a < 8; ++a) s[a] = c[a] = T(0);
+    for (int a = 0; a < NO; ++a) s[a] = c[a] = T(0);
     for (int e = i0; e < i1; ++e) {
       const T x = e1[e] - mp.ux;
       T p = e1[n1 + e] * Num<T>::gauss(x, mp.inv2RT, mp.lnh);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < NO; ++a) {
         if (a < 3) csum_add(s[a], c[a], p);
         else s[a] += p;
         p *= x;
       }
     }
-    // exclusive scan over the lanes: the start of every lane's run (compensated for the
-    // moments of order 0..2 in x, which the conserved rows take)
+    // exclusive scan over the lanes: the start of every lane's run
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
+    for (int a = 0; a < NO; ++a) {
       T ss = s[a], cc = c[a];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -464,12 +467,15 @@ __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane
     }
     if (lane == 0)
 #pragma unroll
-      for (int a = 0; a < 8; ++a) Qs[a * nq + ls + L] = Qc[a * nq + ls + L] = T(0);
+      for (int a = 0; a < NO; ++a) {
+        Qs[a * nq + ls + L] = T(0);
+        if (a < 3) Qc[a * nq + ls + L] = T(0);
+      }
     for (int e = i0; e < i1; ++e) {
       const T x = e1[e] - mp.ux;
       T p = e1[n1 + e] * Num<T>::gauss(x, mp.inv2RT, mp.lnh);
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < NO; ++a) {
         if (a < 3) {
           csum_add(s[a], c[a], p);
           Qc[a * nq + e + L + 1] = c[a];
@@ -483,49 +489,50 @@ __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane
   }
   __syncwarp();
   // rows: Rx from the segments, Ry from the row's y entry; the first-order entries compensated
-  T M[36], Mc[3];
+  T M[NE], Mc[3];
 #pragma unroll
-  for (int k = 0; k < 36; ++k) M[k] = T(0);
+  for (int k = 0; k < NE; ++k) M[k] = T(0);
   Mc[0] = Mc[1] = Mc[2] = T(0);
   for (int r = lane; r < A.nrows; r += 32) {
     const int4 R = A.rows[r];
     const T y = e1[R.x] - mp.uy;
     T py = e1[n1 + R.x] * Num<T>::gauss(y, mp.inv2RT, mp.lnh);
-    T Ry[8], Rs[8], Rc[8];
+    T Ry[NO], Rs[NO], Rc[3];
 #pragma unroll
-    for (int b = 0; b < 8; ++b) {
+    for (int b = 0; b < NO; ++b) {
       Ry[b] = py;
       py *= y;
-      Rs[b] = Rc[b] = T(0);
+      Rs[b] = T(0);
+      if (b < 3) Rc[b] = T(0);
     }
     for (int sg = R.y; sg < R.y + R.z; ++sg) {
       const int2 q = A.segs[sg];
 #pragma unroll
-      for (int a = 0; a < 8; ++a) {
+      for (int a = 0; a < NO; ++a) {
         Rs[a] += Qs[a * nq + q.y] - Qs[a * nq + q.x];
         if (a < 3) Rc[a] += Qc[a * nq + q.y] - Qc[a * nq + q.x];
       }
     }
     int k = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < NO; ++i)
 #pragma unroll
-      for (int j = 0; i + j < 8; ++j, ++k) {
-        const T v = (Rs[i] - Rc[i]) * Ry[j];
-        if (k == 0 || k == 1 || k == 8) csum_add(M[k], Mc[k == 0 ? 0 : (k == 1 ? 1 : 2)], v);
+      for (int j = 0; i + j < NO; ++j, ++k) {
+        const T v = (i < 3 ? Rs[i] - Rc[i] : Rs[i]) * Ry[j];
+        if (k == 0 || k == 1 || k == NO) csum_add(M[k], Mc[k == 0 ? 0 : (k == 1 ? 1 : 2)], v);
         else M[k] += v;
       }
   }
   __syncwarp();
   // over the lanes: through shared memory, one entry per lane (compensated)
 #pragma unroll
-  for (int k = 0; k < 36; ++k) {
-    const T cm = (k == 0) ? Mc[0] : (k == 1) ? Mc[1] : (k == 8) ? Mc[2] : T(0);
+  for (int k = 0; k < NE; ++k) {
+    const T cm = (k == 0) ? Mc[0] : (k == 1) ? Mc[1] : (k == NO) ? Mc[2] : T(0);
     wsm[k * 33 + lane] = M[k] - cm;
   }
   __syncwarp();
-  double* Pd = reinterpret_cast<double*>(wsm + kRowPd);
-  for (int k = lane; k < 36; k += 32) {
+  double* Pd = reinterpret_cast<double*>(wsm + row_pd(NO));
+  for (int k = lane; k < NE; k += 32) {
     T as[4], ac[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) as[j] = ac[j] = T(0);
@@ -546,7 +553,7 @@ __device__ inline void row_moments(const PointArgs& A, const MP<T>& mp, int lane
 // 25 writes G slot l, lanes 25..31 H slots 0..6, lanes 0 and 1 also H slots 7 and 8.
 template <class T, int D>
 __device__ inline void row_store_gh(const PointArgs& A, const MP<T>& mp, int lane, const T* wsm, long i) {
-  const double* Pd = reinterpret_cast<const double*>(wsm + kRowPd);
+  const double* Pd = reinterpret_cast<const double*>(wsm + row_pd(8));
   auto P = [&](int a, int b) -> double { return Pd[8 * a - a * (a - 1) / 2 + b]; };
   const StepConst& k = A.k;
   const double kx = (double)mp.kqx, ky = (double)mp.kqy;
@@ -656,12 +663,11 @@ __device__ inline void u_row8(int k, UPoly& pg, UPoly& ph) {
 }
 
 // b0..b7 of the eight-moment correction of mp (uncorrected Shakhov parameters of the state
-// rho, u, T with heat-flux target q_tar); b0..b3 go to mp, b4..b7 to b8.
+// rho, u, T with heat-flux target q_tar) from the model's peculiar moments G, H; b0..b3 go to
+// mp, b4..b7 to b8.
 template <class T>
-__device__ inline bool u_correct8(const PointArgs& A, double rho, double ux, double uy, double Tm, double qtx,
-                                  double qty, MP<T>& mp, T b8[4]) {
-  double G[7][7], H[5][5];
-  u_moments8<T>(A, mp, G, H);
+__device__ inline bool u_solve8(const GasDev& gas, double rho, double ux, double uy, double Tm, double qtx,
+                                double qty, const double G[7][7], const double H[5][5], MP<T>& mp, T b8[4]) {
   double M[8][8], r[8];
   for (int k = 0; k < 8; ++k) {
     UPoly pg, ph;
@@ -676,15 +682,48 @@ __device__ inline bool u_correct8(const PointArgs& A, double rho, double ux, dou
       M[k][m] = s;
     }
   }
-  const double RT = A.gas.R * Tm;
+  const double RT = gas.R * Tm;
   const double dux = ux - (double)mp.ux, duy = uy - (double)mp.uy;
   const double tar[8] = {rho, rho * dux, rho * duy,
-                         0.5 * (3.0 + A.gas.K) * rho * RT + 0.5 * rho * (dux * dux + duy * duy), qtx, qty, 0.0, 0.0};
+                         0.5 * (3.0 + gas.K) * rho * RT + 0.5 * rho * (dux * dux + duy * duy), qtx, qty, 0.0, 0.0};
   for (int k = 0; k < 8; ++k) r[k] = tar[k] - M[k][0];
   if (!solve_pivoted<8>(M, r, 8)) return false;
   mp.b0 = T(r[0]); mp.b1 = T(r[1]); mp.b2 = T(r[2]); mp.b3 = T(r[3]);
   for (int m = 0; m < 4; ++m) b8[m] = T(r[4 + m]);
   return true;
+}
+
+// The eight-moment correction on a tensor-product space (the moments from one-axis sums).
+template <class T>
+__device__ inline bool u_correct8(const PointArgs& A, double rho, double ux, double uy, double Tm, double qtx,
+                                  double qty, MP<T>& mp, T b8[4]) {
+  double G[7][7], H[5][5];
+  u_moments8<T>(A, mp, G, H);
+  return u_solve8<T>(A.gas, rho, ux, uy, Tm, qtx, qty, G, H, mp, b8);
+}
+
+// G[7][7] and H[5][5] of u_moments8 from row_moments<T, 10>'s pair moments (P(i, j) in place
+// of the products of one-axis sums), one entry per lane and round, stored to the split
+// finalisation's scratch of point i (entries beyond the orders zero).
+template <class T>
+__device__ inline void row_store_gh8(const PointArgs& A, const MP<T>& mp, int lane, const T* wsm, long i) {
+  const double* Pd = reinterpret_cast<const double*>(wsm + row_pd(10));
+  auto P = [&](int a, int b) -> double { return Pd[10 * a - a * (a - 1) / 2 + b]; };
+  const double kx = (double)mp.kqx, ky = (double)mp.kqy;
+  const double i2 = 2.0 * (double)mp.inv2RT, RT = (double)mp.RT, c0 = A.k.c0;
+  const double al = RT * c0 * i2, be = RT * (2.0 * c0 + A.k.twoK);
+  const long n = A.npt;
+  for (int e = lane; e < 74; e += 32) {
+    const bool h = e >= 49;
+    const int x = h ? (e - 49) / 5 : e / 7, y = h ? (e - 49) % 5 : e % 7;
+    double v = 0.0;
+    if (x + y < (h ? 5 : 7)) {
+      const double cub = kx * (P(x + 3, y) + P(x + 1, y + 2)) + ky * (P(x + 2, y + 1) + P(x, y + 3));
+      const double lin = kx * P(x + 1, y) + ky * P(x, y + 1);
+      v = h ? RT * c0 * P(x, y) + al * cub - be * lin : P(x, y) - 4.0 * lin + i2 * cub;
+    }
+    A.scr[(FS_G8 + e) * n + i] = v;
+  }
 }
 
 // Shakhov model times the eight-term correction factor (model_eval's operation order for the
@@ -969,12 +1008,19 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
     }
   }
   if (PART == 1) {
-    // split path: the uncorrected model and what k_fin_sums / k_fin_post need
-    a.need[i] = need == 1 ? 16 + 4 * side + kind : need;
+    // split path: the uncorrected model and what k_fin_sums / k_fin_post need; need 3: the
+    // eight-moment correction (cells and faces, not freestream sides), with its heat-flux
+    // target (1 - Pr) q
+    const bool c8s = D == 2 && a.prm8_out && need == 2 && !free_;
+    a.need[i] = need == 1 ? 16 + 4 * side + kind : (c8s ? 3 : need);
     a.scr[FS_RHO * (long)a.npt + i] = wall ? M[MO_0] : rho;
     a.scr[FS_UX * (long)a.npt + i] = ux;
     a.scr[FS_UY * (long)a.npt + i] = uy;
     a.scr[FS_T * (long)a.npt + i] = Tm;
+    if (c8s) {
+      a.scr[FS_QX * (long)a.npt + i] = (1.0 - g.Pr) * qx;
+      a.scr[FS_QY * (long)a.npt + i] = (1.0 - g.Pr) * qy;
+    }
   }
   double den = 0.0;
   double G[5][5], H[3][3];
@@ -990,7 +1036,7 @@ __device__ __forceinline__ void finalize_point(const PointArgs& a, int i) {
       else direct_moments<T, D, 1>(a, mp, 0, G, H);
     }
   }
-  if (p8 && PART == 0)
+  if (p8)   // nonzero only where the eight-moment correction is solved
     for (int m = 0; m < 4; ++m) p8[m * (long)a.npt + i] = T(0);
   if (wall) {
     if (PART == 1) {   // rho_w in k_fin_post
@@ -1078,8 +1124,9 @@ __global__ void k_fin_pre(const PointArgs a) {
   finalize_point<T, D, 1>(a, i);
 }
 
-// Velocity sums of the split path, a warp per point (blockDim a multiple of 32).
-template <class T, int D>
+// Velocity sums of the split path, a warp per point (blockDim a multiple of 32).  C8: the form
+// with the eight-moment correction's sums (need 3, spaces with row tables).
+template <class T, int D, bool C8 = false>
 __global__ void k_fin_sums(const PointArgs a) {
   int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -1102,6 +1149,19 @@ __global__ void k_fin_sums(const PointArgs a) {
     if (lane == 0) a.scr[FS_DEN * n + i] = d;
     return;
   }
+  if constexpr (C8 && D == 2) {
+    if (need == 3) {
+      if (!a.rows) {   // the host checks that the level's space has row tables
+        if (lane == 0) atomicOr(a.err, ERR_SINGULAR);
+        return;
+      }
+      extern __shared__ __align__(16) unsigned char fsm8[];
+      T* wsm = reinterpret_cast<T*>(fsm8) + (size_t)(threadIdx.x >> 5) * row_smem_values(a.n1, 10);
+      row_moments<T, 10>(a, q, lane, wsm);
+      row_store_gh8<T>(a, q, lane, wsm, i);
+      return;
+    }
+  }
   double G[5][5], H[3][3];
   if (a.k.nax > 0) {
     // tensor-product space: the one-axis sums over the lanes, combined on lane 0
@@ -1119,7 +1179,7 @@ __global__ void k_fin_sums(const PointArgs a) {
   } else if (D == 2 && a.rows) {
     // a space that is not a tensor product, from its rows
     extern __shared__ __align__(16) unsigned char fsm[];
-    T* wsm = reinterpret_cast<T*>(fsm) + (size_t)(threadIdx.x >> 5) * row_smem_values(a.n1);
+    T* wsm = reinterpret_cast<T*>(fsm) + (size_t)(threadIdx.x >> 5) * row_smem_values(a.n1, C8 ? 10 : 8);
     row_moments<T>(a, q, lane, wsm);
     row_store_gh<T, D>(a, q, lane, wsm, i);
     return;
@@ -1134,8 +1194,9 @@ __global__ void k_fin_sums(const PointArgs a) {
   }
 }
 
-// Correction of the split path: wall densities and the four-moment solve.
-template <class T, int D>
+// Correction of the split path: wall densities and the four-moment solve (C8: the eight-moment
+// solve of need-3 points as well).
+template <class T, int D, bool C8 = false>
 __global__ void k_fin_post(const PointArgs a) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.nwork) return;
@@ -1154,6 +1215,24 @@ __global__ void k_fin_post(const PointArgs a) {
   }
   MP<T> mp;
   mp.load(po, n, i);
+  if constexpr (C8 && D == 2) {
+    if (need == 3) {
+      double G8[7][7], H8[5][5];
+      for (int r = 0; r < 49; ++r) G8[r / 7][r % 7] = a.scr[(FS_G8 + r) * n + i];
+      for (int r = 0; r < 25; ++r) H8[r / 5][r % 5] = a.scr[(FS_H8 + r) * n + i];
+      T b8[4];
+      const bool ok8 = u_solve8<T>(a.gas, a.scr[FS_RHO * n + i], a.scr[FS_UX * n + i], a.scr[FS_UY * n + i],
+                                   a.scr[FS_T * n + i], a.scr[FS_QX * n + i], a.scr[FS_QY * n + i], G8, H8, mp, b8);
+      po[P_B0 * n + i] = mp.b0;
+      po[P_B1 * n + i] = mp.b1;
+      po[P_B2 * n + i] = mp.b2;
+      po[P_B3 * n + i] = mp.b3;
+      T* p8 = reinterpret_cast<T*>(a.prm8_out);
+      for (int m = 0; m < 4; ++m) p8[m * n + i] = b8[m];
+      if (!ok8) atomicOr(a.err, ERR_SINGULAR);
+      return;
+    }
+  }
   double G[5][5], H[3][3];
 #pragma unroll
   for (int r = 0; r < 25; ++r) G[r / 5][r % 5] = a.scr[(FS_G + r) * n + i];

@@ -499,16 +499,25 @@ template <class S, class T, int D> struct Runner {
     a.need = L.fneed.as<int>();
     h->launches += 2;
     k_fin_pre<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
+    // the eight-moment correction on a space that is not a tensor product: its sums from the
+    // row tables (orders up to 9) and its solve per thread
+    const bool c8 = D == 2 && a.prm8_out;
     size_t sm = 0;
     if (a.rows) {   // the row tables' prefix sums: shared memory per warp (4 warps per CTA)
-      sm = (size_t)4 * row_smem_values(a.n1) * sizeof(T);
+      sm = (size_t)4 * row_smem_values(a.n1, c8 ? 10 : 8) * sizeof(T);
       if (sm > (size_t)smem_optin()) {
-        a.rows = nullptr;   // the direct sums need none
+        a.rows = nullptr;   // the direct sums need none (the eight-moment sums report an error)
         sm = 0;
       }
     }
-    k_fin_sums<T, D><<<std::max(1, (a.nwork * 32 + 127) / 128), 128, sm, h->stream>>>(a);
-    k_fin_post<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
+    const unsigned gs = (unsigned)std::max(1, (a.nwork * 32 + 127) / 128);
+    if (c8) {
+      k_fin_sums<T, D, true><<<gs, 128, sm, h->stream>>>(a);
+      k_fin_post<T, D, true><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
+    } else {
+      k_fin_sums<T, D><<<gs, 128, sm, h->stream>>>(a);
+      k_fin_post<T, D><<<fin_grid(a.nwork), FIN_BLOCK, 0, h->stream>>>(a);
+    }
   }
 
   // largest dynamic shared memory a CTA may opt in to on the current device
@@ -521,6 +530,8 @@ template <class S, class T, int D> struct Runner {
   static cudaError_t set_smem_limits() {
     {
       cudaError_t e = cudaFuncSetAttribute(k_fin_sums<T, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fin_sums<T, D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
       if (e != cudaSuccess) return e;
     }
     const void* fn[4] = {(const void*)k_faces<S, T, D, TX, TY, false, false>,
@@ -1735,7 +1746,8 @@ static mlvs_status build_levels(mlvs_handle* h, const std::vector<int>& lvl_of, 
       return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     {
       const size_t np = std::max<size_t>(std::max<size_t>(nface, nc), 1);
-      if (L.fscr.alloc(FIN_SCR * np * sizeof(double)) != cudaSuccess || L.fneed.alloc(np * sizeof(int)) != cudaSuccess)
+      const size_t nscr = h->cfg.compat_moments == 8 ? (size_t)FIN_SCR8 : (size_t)FIN_SCR;
+      if (L.fscr.alloc(nscr * np * sizeof(double)) != cudaSuccess || L.fneed.alloc(np * sizeof(int)) != cudaSuccess)
         return fail(h, MLVS_ERR_OOM, "device allocation of a level failed");
     }
   }
@@ -2080,8 +2092,8 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
   if (n_levels < 1 || !levels) return fail(h, MLVS_ERR_ARG, "need at least one level");
   if (!(umax > umin)) return fail(h, MLVS_ERR_ARG, "umax must exceed umin");
   if (adaptive != 0 && adaptive != 1) return fail(h, MLVS_ERR_ARG, "adaptive must be 0 or 1");
-  if (h->cfg.compat_moments == 8 && (n_levels != 1 || adaptive != 0 || levels[0].uniform_L < 0))
-    return fail(h, MLVS_ERR_ARG, "the eight-moment correction runs on one uniform level (adaptive = 0)");
+  if (h->cfg.compat_moments == 8 && (n_levels != 1 || adaptive != 0))
+    return fail(h, MLVS_ERR_ARG, "the eight-moment correction runs on one level (adaptive = 0)");
   h->adaptive = adaptive;
   try {
     h->base = make_base_1d(n_base, umin, umax, quadrature);
@@ -2120,6 +2132,9 @@ extern "C" mlvs_status mlvs_set_velocity_levels(mlvs_handle* h, int n_base, doub
     }
     mlvs_status st = get_space(h, kap, &h->level_space[l]);
     if (st != MLVS_OK) return st;
+    const SpaceRt& sp = h->spaces[h->level_space[l]];
+    if (h->cfg.compat_moments == 8 && sp.nax == 0 && !sp.rows.p)
+      return fail(h, MLVS_ERR_ARG, "the eight-moment correction needs a tensor-product space or one made of level groups");
   }
   Ops ops = ops_for(h->cfg.storage, D);
   const int ncell = h->nx * h->ny;
