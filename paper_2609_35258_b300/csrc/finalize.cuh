@@ -403,11 +403,12 @@ template <class T> __device__ __forceinline__ void csum_merge(T& s, T& c, T so, 
 // entries: the prefix sums [NO + 3][n1 + 4] (NO orders, three of them compensated); the same
 // area later holds the lanes' pair moments (NE = NO (NO + 1) / 2 rows of 33, the row padded so
 // that a lane reading its row meets no other lane's bank) and then the NE sums as FP64 at the
-// even offset row_pd(NO), 8-byte aligned.
+// even offset row_pd(NO).  The count is rounded up to an even number, so that every warp's
+// area, and with it the FP64 sums, starts on an 8-byte boundary.
 __host__ __device__ constexpr int row_pd(int NO) { return ((NO * (NO + 1) / 2) * 33 + 1) & ~1; }
 __host__ __device__ inline int row_smem_values(int n1, int NO = 8) {
   const int q = (NO + 3) * (n1 + 4), r = row_pd(NO) + NO * (NO + 1);
-  return q > r ? q : r;
+  return ((q > r ? q : r) + 1) & ~1;
 }
 
 // The pair moments P[i][j] = sum over the space of w gauss(c_x) gauss(c_y) c_x^i c_y^j

@@ -153,3 +153,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
   for (size_t i = 0; i < f[cur].size(); ++i) fout[i] = (double)f[cur][i];
   return err;
 }
+
+// The per-warp shared-memory layout of the finalisation's row sums, for the layout tests.
+extern "C" int emu_row_smem_values(int n1, int NO) { return row_smem_values(n1, NO); }
+extern "C" int emu_row_pd(int NO) { return row_pd(NO); }

@@ -128,3 +128,49 @@ def test_eight_moment_needs_one_level():
         Solver(desc, compat_moments=8, adaptive=1)
     with pytest.raises(M.MLVSError):
         Solver(desc, compat_moments=8, levels=(0, 1))
+
+
+def _cross_kappa(n_base):
+    """Level 0 on a band of blocks across every x, level 1 on a band across every y, levels
+    2 and 3 elsewhere: a cut space whose rows draw on the groups of every level along both axes
+    (about 180 distinct row entries on the 101^2 base)."""
+    N1 = len(vspace.axis_groups(n_base, 1))
+    mid = N1 // 2
+    yy, xx = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
+    r = np.hypot(xx - mid, yy - mid)
+    return np.where(np.abs(yy - mid) <= 2, 0,
+                    np.where(np.abs(xx - mid) <= 2, 1, np.where(r < N1 / 3, 2, 3))).astype(np.uint8)
+
+
+@pytest.mark.parametrize("compat_moments", [4, 8])
+@pytest.mark.parametrize("storage,tol", [("f64", 1e-10), ("f32", 2e-5)])
+def test_row_sums_with_many_entries_match_oracle(compat_moments, storage, tol):
+    """The row sums with many row entries (their shared memory per warp well above the pair
+    moments' area) on a 101^2 base, against the oracle's step on that space."""
+    n = 4
+    desc = workloads.periodic_random(n, n, n_base=101, umax=6.0, storage=storage, amp=0.2)
+    ka = _cross_kappa(101)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    S = book.space(book.get(ka.astype(np.int64)))
+    s = Solver(desc, levels=(ka,), compat_moments=compat_moments)
+    nv = S.xi.shape[0]
+    g0, h0 = [], []
+    for c in range(n * n):
+        g, h = s.read_cells(c, 1, nv)
+        g0.append(g[0].copy())
+        h0.append(h[0].copy())
+    steps = 3
+    s.step(steps)
+    G, H = np.stack(g0).reshape(n, n, nv), np.stack(h0).reshape(n, n, nv)
+    opt = dataclasses.replace(o["opt"], compat_moments=compat_moments)
+    for _ in range(steps):
+        G, H, _ = dugks.step(G, H, o["mesh"], S.xi, S.w, o["gas"], o["dt"], opt)
+    ref_g, ref_h = G.reshape(n * n, nv), H.reshape(n * n, nv)
+    gmax, hmax = np.max(np.abs(ref_g)), np.max(np.abs(ref_h))
+    worst = 0.0
+    for c in range(n * n):
+        g, h = s.read_cells(c, 1, nv)
+        worst = max(worst, np.max(np.abs(g[0] - ref_g[c])) / gmax, np.max(np.abs(h[0] - ref_h[c])) / hmax)
+    s.close()
+    assert worst < tol, worst

@@ -86,3 +86,19 @@ def test_tile_kernels_fp32_match_the_oracle(lib32):
     g, h, g_o, h_o = _run(lib32, desc, 2, vpc=40)
     np.testing.assert_allclose(g, g_o, rtol=0, atol=1e-5 * np.max(np.abs(g_o)))
     np.testing.assert_allclose(h, h_o, rtol=0, atol=1e-5 * np.max(np.abs(h_o)))
+
+
+def test_row_sum_layout_keeps_the_fp64_sums_aligned(lib, lib32):
+    """The warp areas of the finalisation's row sums (FP32 and FP64 storage): every warp's area
+    holds the prefix sums of NO orders (three compensated) over n1 + 4 slots, and above the
+    lanes' padded pair moments (NE rows of 33) the NE sums as FP64 at an offset that keeps them
+    8-byte aligned in every warp: an even count of values per warp and an even offset."""
+    for L in (lib, lib32):
+        for NO in (8, 10):
+            ne = NO * (NO + 1) // 2
+            pd = L.emu_row_pd(NO)
+            assert pd % 2 == 0 and pd >= ne * 33
+            for n1 in range(1, 700):
+                v = L.emu_row_smem_values(n1, NO)
+                assert v % 2 == 0, (n1, NO, v)
+                assert v >= (NO + 3) * (n1 + 4) and v >= pd + 2 * ne, (n1, NO, v)
