@@ -3,8 +3,9 @@
 // in the same precision (fma stays fused) and stay separately rounded even where the caller is
 // compiled with contraction on: an empty asm makes each result opaque to fusion, as the GPU
 // never fuses an explicitly rounded intrinsic.  The fast exponential maps to the C library's.
-// Warp shuffles are not emulated: a kernel that reaches one aborts, so an emulated launch
-// that needs lanes to exchange values cannot pass by accident.
+// Warp shuffles are not emulated here: a kernel that reaches one aborts, so an emulated launch
+// that needs lanes to exchange values cannot pass by accident; the block emulation of
+// cta_shim.hpp defines EMU_WARPS and provides them.
 #pragma once
 #include <cmath>
 #include <cstdio>
@@ -40,6 +41,7 @@ static inline unsigned __float_as_uint(float f) {
   std::memcpy(&u, &f, 4);
   return u;
 }
+#ifndef EMU_WARPS   // the block emulation (cta_shim.hpp) provides real warp exchanges
 template <class X> static inline X __shfl_xor_sync(unsigned, X v, int, int = 32) {
   std::fprintf(stderr, "emulation: a warp shuffle was reached; lanes are not emulated\n");
   std::abort();
@@ -59,6 +61,7 @@ static inline void __syncwarp(unsigned = 0xffffffffu) {
   std::fprintf(stderr, "emulation: a warp barrier was reached; lanes are not emulated\n");
   std::abort();
 }
+#endif
 // packed two-lane FP32 (sm_100 and later): each lane an IEEE operation, as on the GPU
 static inline float2 __fadd2_rn(float2 a, float2 b) { return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y)); }
 static inline float2 __fmul2_rn(float2 a, float2 b) { return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)); }

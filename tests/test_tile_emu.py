@@ -4,7 +4,10 @@ staging of a 16 x 16 tile with its two-cell halo, slopes, upwind faces and barri
 velocities) run on emulated thread blocks (tests/emu/tile_emu.cpp), with the initialisation,
 chunk-sum and finalisation kernels the handle launches around them.  FP64, 1e-13 of the largest
 value after two steps (FP32 on the cavity, 1e-5), on meshes that leave partial tiles: doubly periodic, a lid-driven cavity
-(walls, one moving), and a supersonic channel (freestream inflow and outflow, walls)."""
+(walls, one moving), and a supersonic channel (freestream inflow and outflow, walls).  On a space
+cut from the base grid the finalisation takes its split path, whose velocity sums run one warp
+per point from the space's row tables (warp shuffles emulated): the cavity with the four- and the
+eight-moment correction against the oracle's step on that space, FP64 1e-12 and FP32 2e-5."""
 import ctypes as C
 import os
 import subprocess
@@ -13,6 +16,7 @@ import tempfile
 import numpy as np
 import pytest
 
+from oracle import dugks, vspace
 from tests.helpers import oracle_run, oracle_setup
 from paper_2609_35258_b300 import workloads
 
@@ -32,7 +36,7 @@ def _build(fp32):
     P = C.c_void_p
     L.emu_tile_run.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, P, P, P, C.c_int, C.c_double,
                                C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, P, P, C.c_int,
-                               C.c_int, P, C.POINTER(C.c_int)]
+                               C.c_int, P, C.c_int, P, C.POINTER(C.c_int)]
     return L
 
 
@@ -46,9 +50,8 @@ def lib32():
     return _build(True)
 
 
-def _run(lib, desc, steps, vpc):
-    o = oracle_setup(desc)
-    g_o, h_o = oracle_run(o, steps)
+def _emu(lib, desc, o, steps, vpc, nv, kappa=None, compat_moments=4):
+    """The emulated step's distributions [ny][nx][nv] (g, h) after `steps` steps."""
     nx, ny = desc["nx"], desc["ny"]
     gas = o["gas"]
     bc = np.array([BC[b] for b in desc["bc"]], dtype=np.int32)
@@ -56,15 +59,23 @@ def _run(lib, desc, steps, vpc):
     gas6 = np.array([gas.R, gas.K, gas.Pr, gas.omega, gas.mu_ref, gas.T_ref])
     far = np.array(desc.get("far", (1.0, 0.0, 0.0, 1.0)), dtype=np.float64)
     W0 = np.ascontiguousarray(desc["init"].reshape(-1, 4), dtype=np.float64)
-    nv = g_o.shape[-1]
     out = np.zeros((2, nv, nx * ny))
     nvo = C.c_int()
+    kp = None if kappa is None else np.ascontiguousarray(kappa, dtype=np.uint8)
     err = lib.emu_tile_run(nx, ny, desc["Lx"], desc["Ly"], bc.ctypes.data, wall.ctypes.data, gas6.ctypes.data,
                            desc["n_base"], desc["umin"], desc["umax"], RULE[desc["rule"]], o["dt"],
                            int(o["opt"].compat_cell), int(o["opt"].compat_face), LIM[desc["limiter"]],
-                           far.ctypes.data, W0.ctypes.data, steps, vpc, out.ctypes.data, C.byref(nvo))
+                           far.ctypes.data, W0.ctypes.data, steps, vpc,
+                           None if kp is None else kp.ctypes.data, compat_moments, out.ctypes.data, C.byref(nvo))
     assert err == 0 and nvo.value == nv
-    return out[0].T.reshape(ny, nx, nv), out[1].T.reshape(ny, nx, nv), g_o, h_o
+    return out[0].T.reshape(ny, nx, nv), out[1].T.reshape(ny, nx, nv)
+
+
+def _run(lib, desc, steps, vpc):
+    o = oracle_setup(desc)
+    g_o, h_o = oracle_run(o, steps)
+    g, h = _emu(lib, desc, o, steps, vpc, g_o.shape[-1])
+    return g, h, g_o, h_o
 
 
 @pytest.mark.parametrize("case", ["periodic", "cavity", "channel"])
@@ -102,3 +113,40 @@ def test_row_sum_layout_keeps_the_fp64_sums_aligned(lib, lib32):
                 v = L.emu_row_smem_values(n1, NO)
                 assert v % 2 == 0, (n1, NO, v)
                 assert v >= (NO + 3) * (n1 + 4) and v >= pd + 2 * ne, (n1, NO, v)
+
+
+def _cut_kappa(n_base):
+    """Quadtree levels 0 near the origin, 1 around it, 2 outside: a space cut from the base grid."""
+    N1 = len(vspace.axis_groups(n_base, 1))
+    yy, xx = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
+    r = np.hypot(xx - N1 // 2, yy - N1 // 2)
+    return np.where(r < N1 / 5, 0, np.where(r < N1 / 3, 1, 2)).astype(np.uint8)
+
+
+@pytest.mark.parametrize("compat_moments,fp32", [(4, False), (8, False), (8, True)])
+def test_tile_step_on_a_cut_space_matches_the_oracle(lib, lib32, compat_moments, fp32):
+    """The step on a space cut from the base grid (not a tensor product): the finalisation's
+    split path with the velocity sums from the space's rows (warp shuffles emulated), the four-
+    or eight-moment correction at cells and faces, walls on every side; from the emulation's
+    own initial state, against the oracle's step on that space with the same correction."""
+    import dataclasses
+
+    from oracle import mlvs as omlvs
+    desc = workloads.cavity(8, n_base=25, Kn=0.075, storage="f64")
+    ka = _cut_kappa(25)
+    o = oracle_setup(desc)
+    book = omlvs.SpaceBook(o["base"])
+    S = book.space(book.get(ka.astype(np.int64)))
+    nv = S.xi.shape[0]
+    assert nv < 25 * 25
+    L = lib32 if fp32 else lib
+    tol = 2e-5 if fp32 else 1e-12
+    g0, h0 = _emu(L, desc, o, 0, 64, nv, ka, compat_moments)
+    steps = 2
+    g1, h1 = _emu(L, desc, o, steps, 64, nv, ka, compat_moments)
+    opt = dataclasses.replace(o["opt"], compat_moments=compat_moments)
+    G, H = g0, h0
+    for _ in range(steps):
+        G, H, _ = dugks.step(G, H, o["mesh"], S.xi, S.w, o["gas"], o["dt"], opt)
+    assert np.max(np.abs(g1 - G)) < tol * np.max(np.abs(G))
+    assert np.max(np.abs(h1 - H)) < tol * np.max(np.abs(H))
