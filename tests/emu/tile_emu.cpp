@@ -7,7 +7,8 @@
 // space is the uniform base space, or a space cut from the base grid by a coarsening mask:
 // then the finalisation takes the split path (state per thread, the velocity sums per warp
 // from the space's row tables, the correction per thread), with the four- or eight-moment
-// correction.  FP64 storage, or FP32 when compiled with EMU_FP32.  Test infrastructure.
+// correction.  `split` sends the uniform space's finalisation down the split path as well
+// (its velocity sums: one-axis sums over the lanes), as the handle does for small launches.  FP64 storage, or FP32 when compiled with EMU_FP32.  Test infrastructure.
 #define EMU_SHARED_SPEC
 #include "cta_shim.hpp"
 
@@ -41,7 +42,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
                             const double* gas6, int n_base, double umin, double umax, int rule, double dt,
                             int compat_cell, int compat_face, int limiter, const double* far, const double* W0,
                             int steps, int vpc, const unsigned char* kappa /* [N1*N1] or null */,
-                            int compat_moments, double* fout /* [2][nv][ncell] */, int* nv_out) {
+                            int compat_moments, int split, double* fout /* [2][nv][ncell] */, int* nv_out) {
   const Base1D b = make_base_1d(n_base, umin, umax, rule);
   const int N1 = (int)groups_1d(n_base, 1).size();
   std::vector<int> keff(N1 * N1, 0), owner;
@@ -172,7 +173,7 @@ extern "C" int emu_tile_run(int nx, int ny, double Lx, double Ly, const int* bc,
     emu_launch(dim3((unsigned)((nt + 255) / 256), 1, 1), 256,
                [&] { k_sum_chunks(a.part, a.k.nchunk, a.npt, a.pts, a.nwork, msum.data()); });
     a.msum = msum.data();
-    if (!cut) {
+    if (!cut && !split) {   // split: the split path on the tensor-product space too
       emu_launch(fin_grid(a.nwork), FIN_BLOCK, [&] { k_finalize<T, D>(a); });
       return;
     }

@@ -36,7 +36,7 @@ def _build(fp32):
     P = C.c_void_p
     L.emu_tile_run.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, P, P, P, C.c_int, C.c_double,
                                C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, P, P, C.c_int,
-                               C.c_int, P, C.c_int, P, C.POINTER(C.c_int)]
+                               C.c_int, P, C.c_int, C.c_int, P, C.POINTER(C.c_int)]
     return L
 
 
@@ -50,7 +50,7 @@ def lib32():
     return _build(True)
 
 
-def _emu(lib, desc, o, steps, vpc, nv, kappa=None, compat_moments=4):
+def _emu(lib, desc, o, steps, vpc, nv, kappa=None, compat_moments=4, split=False):
     """The emulated step's distributions [ny][nx][nv] (g, h) after `steps` steps."""
     nx, ny = desc["nx"], desc["ny"]
     gas = o["gas"]
@@ -66,7 +66,8 @@ def _emu(lib, desc, o, steps, vpc, nv, kappa=None, compat_moments=4):
                            desc["n_base"], desc["umin"], desc["umax"], RULE[desc["rule"]], o["dt"],
                            int(o["opt"].compat_cell), int(o["opt"].compat_face), LIM[desc["limiter"]],
                            far.ctypes.data, W0.ctypes.data, steps, vpc,
-                           None if kp is None else kp.ctypes.data, compat_moments, out.ctypes.data, C.byref(nvo))
+                           None if kp is None else kp.ctypes.data, compat_moments, int(split), out.ctypes.data,
+                           C.byref(nvo))
     assert err == 0 and nvo.value == nv
     return out[0].T.reshape(ny, nx, nv), out[1].T.reshape(ny, nx, nv)
 
@@ -150,3 +151,17 @@ def test_tile_step_on_a_cut_space_matches_the_oracle(lib, lib32, compat_moments,
         G, H, _ = dugks.step(G, H, o["mesh"], S.xi, S.w, o["gas"], o["dt"], opt)
     assert np.max(np.abs(g1 - G)) < tol * np.max(np.abs(G))
     assert np.max(np.abs(h1 - H)) < tol * np.max(np.abs(H))
+
+
+@pytest.mark.parametrize("case", ["periodic", "cavity"])
+def test_split_finalisation_on_the_uniform_space_matches_the_oracle(lib, case):
+    """The split finalisation on the tensor-product space (the handle's path for launches of
+    fewer than 4,096 points): the one-axis sums split over a warp's lanes and merged with exact
+    TwoSum compensation (warp shuffles emulated), FP64, against the oracle's step."""
+    desc = (workloads.periodic_random(10, 6, n_base=13, storage="f64") if case == "periodic"
+            else workloads.cavity(8, n_base=13, umax=5.0, storage="f64"))
+    o = oracle_setup(desc)
+    g_o, h_o = oracle_run(o, 2)
+    g, h = _emu(lib, desc, o, 2, 64, g_o.shape[-1], split=True)
+    assert np.max(np.abs(g - g_o)) < 1e-13 * np.max(np.abs(g_o))
+    assert np.max(np.abs(h - h_o)) < 1e-13 * np.max(np.abs(h_o))
